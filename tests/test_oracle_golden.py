@@ -1,0 +1,26 @@
+"""The oracle still reproduces its frozen record (tests/golden/oracle_small.json,
+written by tests/golden/make_golden.py from the oracle alone)."""
+import json
+import os
+
+import numpy as np
+
+from tests.golden.make_golden import compute
+
+HERE = os.path.dirname(os.path.abspath(__file__))
+
+
+def test_oracle_matches_frozen_record():
+    with open(os.path.join(HERE, "golden", "oracle_small.json")) as f:
+        want = json.load(f)
+    got = compute()
+    assert abs(got["loss"] - want["loss"]) < 1e-12
+    assert abs(got["image_sum"] - want["image_sum"]) < 1e-10
+    assert abs(got["final_T_sum"] - want["final_T_sum"]) < 1e-10
+    assert got["last_idx_sum"] == want["last_idx_sum"]
+    np.testing.assert_allclose([p[3] for p in got["pixels"]], [p[3] for p in want["pixels"]],
+                               atol=1e-13)
+    for k, v in want["grad_norms"].items():
+        assert abs(got["grad_norms"][k] - v) <= 1e-10 * max(1.0, abs(v))
+    np.testing.assert_allclose(got["grad_means_first"], want["grad_means_first"], rtol=1e-10,
+                               atol=1e-15)
