@@ -1,0 +1,384 @@
+"""Mapping-iteration throughput of the GB300 3DGS rasteriser.
+
+    python bench.py [--gpus N] [--steps K] [--warmup W] [--impl gb300|reference]
+
+One step = one whole mapping iteration on one batch of synthetic input:
+project -> bin/sort -> forward composite -> L1+SSIM loss -> backward ->
+Adam, all in libgs_gb300.so.  Default workload: 1M Gaussians (SH degree 3)
+in a seeded synthetic room, one 1200x680 view (the Replica-sized stand-in),
+target rendered from a perturbed copy of the map.  Inputs are resident in HBM
+for `value`; `e2e` adds, per step, the pinned-host -> device copy of the
+step's target image and pose and the device -> host read of the loss.
+
+The timed region replays the iteration as six CUDA graphs (one per stage)
+with CUDA events between them on the launching stream, so every stage's
+device time comes from the timed region itself.  The working set (map,
+gradients, Adam moments: ~0.95 GB, plus the workspace) is far larger than the
+129 MB L2, so no explicit flush is needed between steps.
+
+With torchrun (N > 1) every rank runs an independent replica of the same
+workload (the path shards over keyframes only through a gradient all-reduce,
+which this single-GPU build does not implement: replicas only); `value` is
+the sum of the ranks' iterations over the max-over-ranks time.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import math
+import os
+import statistics
+import subprocess
+import sys
+import tempfile
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = ("mapping iters/s (fwd+bwd+Adam) @1M Gaussians 1200×680; batched vs per-view; "
+          "%roofline")
+WORKLOAD = "room1M_1200x680"
+PAIR_FLOPS_FWD = 26.0  # FP32 operations per evaluated (pixel, Gaussian) pair, forward
+PAIR_FLOPS_BWD = 64.0  # and per pair of the adjoint
+
+
+def load_peaks():
+    path = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    try:
+        with open(path) as f:
+            d = json.load(f)
+        return dict(hbm_gbs=float(d["hbm_gbs"]), sm_max_mhz=float(d.get("sm_max_mhz", 2070.0)),
+                    source="measured")
+    except Exception:
+        return dict(hbm_gbs=6800.0, sm_max_mhz=2070.0, source="fallback")
+
+
+def fp32_peak_tflops(sm_mhz):
+    # 152 SMs x 128 FP32 lanes x 2 flops (FMA) per clock
+    return 152 * 128 * 2 * sm_mhz * 1e6 / 1e12
+
+
+class ClockSampler:
+    """nvidia-smi sampling of SM clock and throttle reasons around a region."""
+
+    Q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+         "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+         "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_index):
+        self.gpu = gpu_index
+        self.proc = None
+        self.path = None
+
+    def start(self):
+        fd, self.path = tempfile.mkstemp(suffix=".csv")
+        os.close(fd)
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", f"--id={self.gpu}", f"--query-gpu={self.Q}", "--format=csv,noheader,nounits",
+                 "-lms", "50"], stdout=open(self.path, "w"), stderr=subprocess.DEVNULL)
+        except Exception:
+            self.proc = None
+        time.sleep(0.15)
+
+    def stop(self):
+        if self.proc is None:
+            return dict(sm_mhz=None, sm_max_mhz=None, reasons=["nvidia-smi unavailable"], samples=0)
+        time.sleep(0.1)
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except Exception:
+            self.proc.kill()
+        rows = []
+        with open(self.path) as f:
+            for line in f:
+                parts = [x.strip() for x in line.split(",")]
+                if len(parts) >= 9:
+                    rows.append(parts)
+        os.unlink(self.path)
+        if not rows:
+            return dict(sm_mhz=None, sm_max_mhz=None, reasons=["no samples"], samples=0)
+
+        def num(x):
+            try:
+                return float(x)
+            except ValueError:
+                return float("nan")
+        sm = [num(r[1]) for r in rows]
+        mx = [num(r[2]) for r in rows]
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        reasons = sorted({names[k] for r in rows for k in range(4) if r[5 + k].lower() == "active"})
+        return dict(sm_mhz=statistics.median(sm), sm_max_mhz=max(mx), reasons=reasons,
+                    samples=len(rows), power_w_max=max(num(r[3]) for r in rows))
+
+
+def dist_setup():
+    ws = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return ws, rank, local
+
+
+def reduce_max(x, ws):
+    if ws == 1:
+        return x
+    import torch
+    import torch.distributed as dist
+    t = torch.tensor([x], dtype=torch.float64, device="cuda")
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def barrier(ws):
+    if ws > 1:
+        import torch.distributed as dist
+        dist.barrier()
+
+
+# ----------------------------------------------------------------------------
+# The CPU oracle (reference arm and cpu_baseline).
+# ----------------------------------------------------------------------------
+def oracle_iteration_seconds(p, view, target, lam):
+    import oracle
+    t0 = time.perf_counter()
+    L, g, _ = oracle.iteration(p, [view], [target], lam)
+    flat_p = np.concatenate([np.asarray(p[k], np.float64).ravel() for k in oracle.PARAM_GROUPS])
+    flat_g = np.concatenate([g[k].ravel() for k in oracle.PARAM_GROUPS])
+    m, v = np.zeros_like(flat_p), np.zeros_like(flat_p)
+    oracle.adam(flat_p, flat_g, m, v, 1e-3, 1)
+    return time.perf_counter() - t0
+
+
+def make_workload(seed_target=True):
+    from paper_2409_13055_gb300 import scenes
+    p = scenes.room_scene(1_000_000, seed=scenes.SEED_BASE + 3)
+    view = scenes.camera(1200, 680, 600.0, 600.0)
+    return p, view
+
+
+def run_reference(args, ws, rank):
+    if rank != 0:
+        return
+    from paper_2409_13055_gb300 import scenes
+    p, view = make_workload()
+    target = scenes.random_target(view, scenes.SEED_BASE + 13)
+    times = []
+    for _ in range(args.warmup if args.reference_warmup else 0):
+        oracle_iteration_seconds(p, view, target, 0.2)
+    for _ in range(args.steps):
+        times.append(oracle_iteration_seconds(p, view, target, 0.2))
+    t = float(np.mean(times))
+    v = 1.0 / t
+    out = dict(metric=METRIC, value=v, unit="iters/s", impl="reference", n_gpus=0,
+               steps=args.steps, warmup=0, ms_per_step=1e3 * t, higher_is_better=True,
+               scaling="weak", vs_baseline=None, dtype="f64", data="synthetic",
+               config=dict(workload=WORKLOAD, gaussians=1_000_000, width=1200, height=680,
+                           sh_degree=3, views=1, lam=0.2),
+               cpu_baseline=dict(value=v, unit="iters/s", cores=1, kind="oracle",
+                                 sample="one full FP64 mapping iteration of the workload per step "
+                                        "(target: seeded noise image)"),
+               e2e=dict(value=v, unit="iters/s", h2d_bytes_per_step=0, d2h_bytes_per_step=0))
+    print(json.dumps(out), flush=True)
+
+
+# ----------------------------------------------------------------------------
+# The GPU arm.
+# ----------------------------------------------------------------------------
+def tile_passes(total_tiles):
+    bits = max(1, math.ceil(math.log2(max(2, total_tiles))))
+    return (bits + 7) // 8
+
+
+def run_gpu(args, ws, rank, local):
+    import torch
+    from paper_2409_13055_gb300 import binding as B
+    from paper_2409_13055_gb300 import build as gsbuild
+    from paper_2409_13055_gb300 import mapping, scenes
+
+    torch.cuda.set_device(local)
+    if ws > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl")
+    gsbuild.build()
+    peaks = load_peaks()
+
+    p, view = make_workload()
+    lam = 0.2
+    # target: render of a perturbed copy of the map (set-up, untimed)
+    pert = scenes.perturbed(p, scenes.SEED_BASE + 23)
+    gt_map = mapping.GaussianMap(pert)
+    rast = mapping.fit_instance_capacity([view], gt_map, tile=(args.tile_w, args.tile_h),
+                                         smem_batch=args.batch)
+    rast.forward(gt_map.gs_map())
+    target = rast.images.clone()
+    del gt_map
+    gm = mapping.GaussianMap(p)
+    rast = mapping.fit_instance_capacity([view], gm, headroom=1.5, tile=(args.tile_w, args.tile_h),
+                                         smem_batch=args.batch)
+    step = mapping.MappingStep(gm, rast, target, lam)
+    m, g = gm.gs_map(), gm.gs_map_grad()
+    stages = [
+        ("project", lambda: rast.project(m)),
+        ("bin_sort", lambda: rast.bin_sort(gm.n)),
+        ("render_fwd", lambda: rast.render_fwd()),
+        ("loss_l1_ssim", lambda: rast.loss_l1_ssim(step.targets, lam)),
+        ("render_bwd", lambda: rast.render_bwd(m, g)),
+        ("adam", lambda: gm.adam_step()),
+    ]
+    # warm-up (eager), then capture one graph per stage
+    for _ in range(max(args.warmup, 3)):
+        for _, f in stages:
+            f()
+    torch.cuda.synchronize()
+    cs = torch.cuda.Stream()
+    cs.wait_stream(torch.cuda.current_stream())
+    graphs = []
+    with torch.cuda.stream(cs):
+        for name, f in stages:
+            gr = torch.cuda.CUDAGraph()
+            with torch.cuda.graph(gr, stream=cs):
+                f()
+            graphs.append((name, gr))
+    torch.cuda.current_stream().wait_stream(cs)
+    torch.cuda.synchronize()
+    for _ in range(max(args.warmup, 3)):
+        for _, gr in graphs:
+            gr.replay()
+    torch.cuda.synchronize()
+
+    # algorithmic counts of this workload (one probe, untimed)
+    c = rast.counters()
+    instances = int(c.n_instances)
+    pairs_bwd = int(rast.last_idx.to(torch.int64).sum().item())
+
+    # --- timed region: K steps of the six stage graphs --------------------
+    K = args.steps
+    stream = torch.cuda.current_stream()
+    ev = [[torch.cuda.Event(enable_timing=True) for _ in range(len(graphs) + 1)] for _ in range(K)]
+    sampler = ClockSampler(local)
+    sampler.start()
+    barrier(ws)
+    torch.cuda.synchronize()
+    for k in range(K):
+        ev[k][0].record(stream)
+        for j, (_, gr) in enumerate(graphs):
+            gr.replay()
+            ev[k][j + 1].record(stream)
+    barrier(ws)
+    torch.cuda.synchronize()
+    clocks = sampler.stop()
+    total_ms = ev[0][0].elapsed_time(ev[K - 1][len(graphs)])
+    stage_ms = {name: float(np.mean([ev[k][j].elapsed_time(ev[k][j + 1]) for k in range(K)]))
+                for j, (name, _) in enumerate(graphs)}
+    total_ms = reduce_max(total_ms, ws)
+    ms_step = total_ms / K
+    value = ws * K / (total_ms / 1e3)
+    status = rast.counters()
+    assert status.status == 0, f"device status {status.status}"
+
+    # --- end to end: per step, pinned H2D of the target and pose, D2H loss -
+    host_tgt = target.cpu().pin_memory()
+    host_views = rast.views_dev.cpu().pin_memory()
+    host_loss = torch.empty(1, dtype=torch.float32).pin_memory()
+    E = max(1, min(K, 50))
+    barrier(ws)
+    torch.cuda.synchronize()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    t_wall = time.perf_counter()
+    for _ in range(E):
+        step.targets.copy_(host_tgt, non_blocking=True)
+        rast.views_dev.copy_(host_views, non_blocking=True)
+        for _, gr in graphs:
+            gr.replay()
+        host_loss.copy_(rast.loss, non_blocking=True)
+        stream.synchronize()
+    e1.record(stream)
+    torch.cuda.synchronize()
+    e2e_ms = reduce_max(e0.elapsed_time(e1), ws) / E
+    h2d = host_tgt.numel() * 4 + host_views.numel()
+    assert math.isfinite(float(host_loss.item()))
+
+    # --- roofline of the dominant kernel ----------------------------------
+    n = gm.n
+    K_sh = (gm.degree + 1) ** 2
+    n_floats = gm.total
+    algo_bytes = dict(
+        project=n * (4 * (11 + 3 * K_sh)) + n * 72,
+        bin_sort=n * 4 * 16 + n * 12 + instances * 8 + tile_passes(rast.total_tiles) * instances * 16
+        + instances * 4 + rast.total_tiles * 8,
+        loss_l1_ssim=rast.total_values * 44,
+        adam=n_floats * 28,
+    )
+    dominant = max(stage_ms, key=stage_ms.get)
+    if dominant in algo_bytes:
+        achieved = algo_bytes[dominant] / (stage_ms[dominant] * 1e-3) / 1e9
+        roof = dict(bound="hbm", kernel=dominant, achieved=achieved, peak=peaks["hbm_gbs"],
+                    unit="GB/s", frac=achieved / peaks["hbm_gbs"],
+                    traffic=None, algorithmic=algo_bytes[dominant],
+                    peak_source=peaks["source"])
+    else:
+        flops = (pairs_bwd * PAIR_FLOPS_BWD) if dominant == "render_bwd" else (pairs_bwd * PAIR_FLOPS_FWD)
+        peak = fp32_peak_tflops(peaks["sm_max_mhz"])
+        achieved = flops / (stage_ms[dominant] * 1e-3) / 1e12
+        roof = dict(bound="alu", kernel=dominant, achieved=achieved, peak=peak, unit="TFLOP/s",
+                    frac=achieved / peak, traffic=None, algorithmic=flops,
+                    peak_source="152 SMs x 128 FP32 lanes x 2 x sm_max_mhz (%s)" % peaks["source"])
+
+    launches_per_step = 1 + (16 + 3 * tile_passes(rast.total_tiles)) + 1 + 2 + 2 + 2
+
+    out = dict(metric=METRIC, value=value, unit="iters/s", n_gpus=ws, steps=K, warmup=args.warmup,
+               ms_per_step=ms_step, higher_is_better=True, scaling="weak", vs_baseline=None,
+               dtype="f32", data="synthetic",
+               config=dict(workload=WORKLOAD, gaussians=n, width=1200, height=680, sh_degree=3,
+                           views=1, lam=0.2, tile=f"{args.tile_w}x{args.tile_h}",
+                           smem_batch=args.batch, cuda_graph="one graph per stage",
+                           l2="working set ~1.2 GB > 129 MB L2, no flush",
+                           instances=instances, pairs_bwd=pairs_bwd),
+               stages_ms=stage_ms, roofline=roof,
+               e2e=dict(value=1e3 / e2e_ms * ws, unit="iters/s", h2d_bytes_per_step=int(h2d),
+                        d2h_bytes_per_step=4),
+               clocks=clocks, gpu_launches=launches_per_step * K)
+
+    if rank == 0 and not args.no_cpu_baseline:
+        from paper_2409_13055_gb300 import scenes as sc
+        t = oracle_iteration_seconds(p, view, sc.random_target(view, sc.SEED_BASE + 13), lam)
+        out["cpu_baseline"] = dict(value=1.0 / t, unit="iters/s", cores=1, kind="oracle",
+                                   sample="one full FP64 mapping iteration of the workload "
+                                          "(target: seeded noise image), single thread")
+    if rank == 0:
+        print(json.dumps(out), flush=True)
+    if ws > 1:
+        import torch.distributed as dist
+        dist.destroy_process_group()
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=200)
+    ap.add_argument("--warmup", type=int, default=5)
+    ap.add_argument("--impl", default="gb300", choices=["gb300", "reference"])
+    ap.add_argument("--tile-w", type=int, default=16)
+    ap.add_argument("--tile-h", type=int, default=16)
+    ap.add_argument("--batch", type=int, default=128)
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--reference-warmup", action="store_true")
+    args = ap.parse_args()
+    if args.warmup < 3:
+        args.warmup = 3
+    ws, rank, local = dist_setup()
+    if args.impl == "reference":
+        if args.steps > 3:
+            args.steps = 3  # each oracle step is a full FP64 iteration (~15-30 s)
+        run_reference(args, ws, rank)
+        return
+    run_gpu(args, ws, rank, local)
+
+
+if __name__ == "__main__":
+    main()

@@ -1,0 +1,236 @@
+/*
+ * gs.h -- C-ABI of the GB300 (sm_103a) differentiable tile-based 3D Gaussian
+ * Splatting mapping step.
+ *
+ * The method: a map of anisotropic 3D Gaussians (opacity, rotation, location,
+ * scale, colour) is rendered with the differentiable tile-based rasteriser of
+ * 3DGS and optimised by gradient descent on the photometric loss of Eq. 2
+ * (paper Sec. III-B, "Dense Reconstruction"); rendering projects the Gaussians
+ * onto the camera plane, sorts them by depth and blends them front to back
+ * (paper Sec. II, 3DGS paragraph); the optimiser is the default 3DGS one, Adam
+ * (paper Sec. IV-A, "Experimental Setup").  One mapping iteration is
+ *
+ *   gs_project -> gs_bin_sort -> gs_render_fwd -> gs_loss_l1_ssim
+ *              -> gs_render_bwd -> gs_adam_step
+ *
+ * Conventions shared by every entry point
+ * ---------------------------------------
+ * - Pointers named *_dev, and every array argument not marked host, are
+ *   device memory owned by the caller.  The library allocates nothing, keeps
+ *   no pointer across calls and never synchronises, except gs_read_counters.
+ * - Every call enqueues asynchronously on `stream` (a cudaStream_t passed as
+ *   void*; NULL = the legacy default stream), so a whole iteration can be
+ *   captured in one CUDA graph.
+ * - Argument errors are reported synchronously (GS_ERR_INVALID, nothing is
+ *   enqueued); launch failures as GS_ERR_CUDA.  Errors found on the device
+ *   (instance-buffer overflow, non-finite parameters) set bits of a status
+ *   word inside the workspace, read with gs_read_counters after the stream
+ *   has been synchronised.  There is no CPU fallback.
+ * - All arithmetic is FP32, except the projected 2D means, which are carried
+ *   as an unevaluated sum of two floats (about 48 significant bits).
+ *
+ * Map layout (SoA, row-major, float32):
+ *   means[n][3], log_scales[n][3], quats[n][4] as (w, x, y, z) (need not be
+ *   normalised), opacity_logits[n], sh[K][n][3] with K = (sh_degree+1)^2,
+ *   coefficient-major so that each coefficient plane is contiguous.
+ * Images: planar [channels][height][width] per view, views packed back to
+ *   back in view order (gs_plan_view gives the offsets).  Per-pixel maps
+ *   (final_T, last_idx) are [height][width] per view, packed the same way.
+ */
+#ifndef GS_GB300_H
+#define GS_GB300_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+#define GS_MAX_VIEWS 64
+#define GS_MAX_GROUPS 8
+#define GS_PLAN_WORDS 1536
+
+typedef enum {
+    GS_OK = 0,
+    GS_ERR_INVALID = -1,     /* bad argument; nothing was enqueued */
+    GS_ERR_CUDA = -2,        /* a CUDA launch or copy failed */
+    GS_ERR_CAPACITY = -3,    /* a capacity given to gs_plan_init is too small */
+    GS_ERR_UNSUPPORTED = -4, /* configuration outside what the kernels handle */
+    GS_ERR_TIMEOUT = -5      /* reserved: a bounded device wait gave up */
+} gs_status;
+
+/* Bits of the device status word (gs_counters.status). */
+#define GS_DEV_CAPACITY 1u  /* more (Gaussian, tile) instances than instance_capacity;
+                               the surplus was dropped and the render is incomplete */
+#define GS_DEV_NONFINITE 2u /* a Gaussian with a non-finite parameter was culled */
+
+/* One camera.  x_cam = R x_world + t with R row-major (world -> camera), the
+ * camera looking along +z with y down; pixel (px, py) is sampled at its
+ * integer coordinates in the frame where a camera point projects to
+ * (fx x/z + cx, fy y/z + cy).  channels is 3 (RGB) or 1 (the mean of the
+ * three composited channels). */
+typedef struct {
+    float R[9];
+    float t[3];
+    float fx, fy, cx, cy;
+    int32_t width, height, channels, reserved;
+} gs_view;
+
+/* The Gaussian map (device pointers, layout above). */
+typedef struct {
+    const float *means, *log_scales, *quats, *opacity_logits, *sh;
+    int32_t n, sh_degree; /* sh_degree in 0..3 */
+} gs_map;
+
+/* Gradients, same layouts as gs_map (device pointers). */
+typedef struct {
+    float *means, *log_scales, *quats, *opacity_logits, *sh;
+} gs_map_grad;
+
+/* Rasteriser configuration.  Readings of what the paper leaves open:
+ *   tile_w x tile_h in {8x8, 16x16, 32x8} (other powers of two with
+ *     tile_w*tile_h in [64, 256] are accepted);
+ *   smem_batch: Gaussians staged per shared-memory batch, 32..256, a
+ *     multiple of 32;
+ *   near_z: Gaussians whose camera depth is not above near_z are culled
+ *     (default reading 0.2 m);
+ *   bg: background colour, entering the image as T_final * bg. */
+typedef struct {
+    int32_t tile_w, tile_h, smem_batch, reserved;
+    float near_z;
+    float bg[3];
+} gs_config;
+
+/* A plan: the sizes, tile grids and workspace layout of one batch of views.
+ * Caller-owned plain memory filled by gs_plan_init; opaque otherwise. */
+typedef struct {
+    uint64_t words[GS_PLAN_WORDS];
+} gs_plan;
+
+/* Device-side counters copied back by gs_read_counters. */
+typedef struct {
+    uint32_t status;           /* GS_DEV_* bits since the last gs_project */
+    uint32_t n_instances;      /* (Gaussian, tile) instances binned (<= capacity) */
+    uint64_t n_instances_raw;  /* instances requested before clamping to capacity */
+    float loss;                /* last value written by gs_loss_l1_ssim */
+    uint32_t reserved[3];
+} gs_counters;
+
+/* Fills *plan for n_views views (sizes taken from views_host, a HOST array;
+ * poses are read later from device copies, so they may change between
+ * calls), at most n_capacity Gaussians and instance_capacity (Gaussian,
+ * tile) instances.  Returns GS_ERR_INVALID for a bad view size, channel
+ * count or count, GS_ERR_UNSUPPORTED for a tile shape or batch outside the
+ * supported set. */
+gs_status gs_plan_init(gs_plan *plan, const gs_config *cfg, int32_t n_views,
+                       const gs_view *views_host, int32_t n_capacity, int64_t instance_capacity);
+
+/* Bytes of device workspace the plan needs (256-byte aligned base). */
+size_t gs_plan_workspace_bytes(const gs_plan *plan);
+
+/* Offsets of view v inside packed images (values: channels*H*W units) and
+ * per-pixel maps (pixels: H*W units), its first global tile id and grid. */
+gs_status gs_plan_view(const gs_plan *plan, int32_t v, int64_t *value_offset,
+                       int64_t *pixel_offset, int32_t *tile_offset, int32_t *tiles_x,
+                       int32_t *tiles_y);
+
+/* Totals over all views: values (sum C*H*W), pixels (sum H*W), tiles. */
+gs_status gs_plan_totals(const gs_plan *plan, int64_t *total_values, int64_t *total_pixels,
+                         int32_t *total_tiles);
+
+/* Location of an intermediate buffer inside the workspace, for inspection
+ * and testing: id is one of GS_BUF_*; *offset and *bytes in bytes. */
+enum {
+    GS_BUF_COUNTERS = 0, /* gs_counters-like header (device side) */
+    GS_BUF_PROJ = 1,     /* [V*n] x 12 floats: mean hi (2), mean lo (2),
+                            conic a,b,c, opacity, r, g, b, depth */
+    GS_BUF_RECT = 2,     /* [V*n] x 4 uint16: tile rect x0, y0, x1, y1 (x1, y1 exclusive) */
+    GS_BUF_TOUCHED = 3,  /* [V*n] uint32: tiles touched (0 = culled) */
+    GS_BUF_RADIUS = 4,   /* [V*n] int32: ceil(3 sqrt(lambda_max)) */
+    GS_BUF_DEPTH_ORDER = 5, /* [V*n] uint32: view*n + index sorted by (depth, view, index) */
+    GS_BUF_TILE_KEYS = 6,   /* [instance_capacity] uint32: sorted global tile ids */
+    GS_BUF_TILE_VALUES = 7, /* [instance_capacity] uint32: view*n + index per instance */
+    GS_BUF_RANGES = 8,      /* [total_tiles] x 2 uint32: [begin, end) of each tile */
+    GS_BUF_GRAD2D = 9,      /* [V*n] x 9 floats: dmean2d (2), dconic (3), dopacity,
+                               dcolour (3) accumulated by gs_render_bwd */
+    GS_BUF_COUNT = 16
+};
+gs_status gs_plan_buffer(const gs_plan *plan, int32_t id, size_t *offset, size_t *bytes);
+
+/* A1: projection (paper Sec. II "projecting Gaussians onto the camera plane";
+ * Sec. III-B original 3DGS rasteriser).  For every (view, Gaussian): camera
+ * transform, cull at near_z or on non-finite input, 3D covariance from the
+ * normalised quaternion and exp(log_scales), EWA 2D covariance with the
+ * Jacobian clamped to 1.3x the image extent and a 0.3 px^2 dilation, conic,
+ * radius ceil(3 sqrt(lambda_max)), tile rect, SH colour
+ * max(0, sum_k Y_k(dir) c_k + 0.5) and opacity sigmoid(logit).
+ * views_dev: device array of n_views gs_view (sizes must match the plan).
+ * Resets the device status word. */
+gs_status gs_project(const gs_plan *plan, const gs_map *map, const gs_view *views_dev, void *ws,
+                     void *stream);
+
+/* A2-A4: binning.  Deterministic (tile, depth, index) order: a stable LSD
+ * radix sort whose depth digits run once per (view, Gaussian) before the
+ * instances are emitted, followed by stable passes over the tile-id digits
+ * of the instances; then per-tile [begin, end) ranges.  n = map->n of the
+ * preceding gs_project.  The instance count stays on the device (no host
+ * synchronisation); overflow sets GS_DEV_CAPACITY. */
+gs_status gs_bin_sort(const gs_plan *plan, int32_t n, void *ws, void *stream);
+
+/* A5: forward compositing (paper Sec. II "blending them front-to-back").
+ * Per pixel, front to back over its tile's list: power = -(a dx^2 + c dy^2)/2
+ * - b dx dy, skipped when > 0; alpha = min(0.99, o e^power), skipped when
+ * < 1/255; the Gaussian that would take T below 1e-4 stops the pixel and is
+ * not added.  Writes images (packed planar), final_T and last_idx (one past
+ * the list position of the last blended Gaussian, 0 if none). */
+gs_status gs_render_fwd(const gs_plan *plan, const void *ws, float *images, float *final_T,
+                        int32_t *last_idx, void *stream);
+
+/* A6: photometric loss, Eq. 2 read as
+ *   L_v = (1 - lambda) mean|I - I_gt| + lambda (1 - mean SSIM(I, I_gt))
+ * (11x11 Gaussian window, sigma 1.5, zero padding, C1 = 0.01^2, C2 = 0.03^2,
+ * per channel, means over the C*H*W values of view v), and
+ *   L = view_weight * sum_v L_v
+ * (view_weight = 1/n_views gives the mean over the plan's views; a loop of
+ * single-view plans passes 1/V to reproduce a V-view mean).  Writes L to
+ * loss_dev[0] (device float) and dL/dimages (packed like images).  Uses the
+ * workspace for the SSIM partial maps.  lambda must lie in [0, 1] and
+ * view_weight be positive, else GS_ERR_INVALID. */
+gs_status gs_loss_l1_ssim(const gs_plan *plan, const float *images, const float *targets,
+                          float lambda, float view_weight, float *loss_dev, float *dL_dimages,
+                          void *ws, void *stream);
+
+/* A7-A8: backward.  The pixel adjoint walks each pixel's list back to front
+ * from last_idx, recovering T_i = T_{i+1} / (1 - alpha_i) from final_T,
+ * reduces each Gaussian's screen-space gradient over a warp with shuffles and
+ * adds it atomically; the projection adjoint then maps it to the parameter
+ * gradients, summed over views.  accumulate = 0 overwrites grads, 1 adds. */
+gs_status gs_render_bwd(const gs_plan *plan, const gs_map *map, const gs_view *views_dev,
+                        void *ws, const float *final_T, const int32_t *last_idx,
+                        const float *dL_dimages, const gs_map_grad *grads, int32_t accumulate,
+                        void *stream);
+
+/* A9: Adam (paper Sec. IV-A, default 3DGS optimiser) over one contiguous
+ * parameter buffer of n_floats split into n_groups contiguous groups:
+ * group g covers [group_offsets_host[g], group_offsets_host[g+1]) with
+ * learning rate group_lr_host[g] (HOST arrays of n_groups+1 and n_groups).
+ * *step_dev (device int32) is incremented first, then
+ *   m = b1 m + (1-b1) g;  v = b2 v + (1-b2) g^2;
+ *   p -= lr (m / (1 - b1^t)) / (sqrt(v / (1 - b2^t)) + eps),  t = *step_dev. */
+gs_status gs_adam_step(float *params, const float *grads, float *m, float *v, int64_t n_floats,
+                       int32_t n_groups, const int64_t *group_offsets_host,
+                       const float *group_lr_host, float beta1, float beta2, float eps,
+                       int32_t *step_dev, void *stream);
+
+/* Copies the device counters of the workspace to *out (host) and waits for
+ * `stream`. */
+gs_status gs_read_counters(const gs_plan *plan, const void *ws, gs_counters *out, void *stream);
+
+/* A static string naming a status. */
+const char *gs_status_string(gs_status s);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* GS_GB300_H */

@@ -1,0 +1,201 @@
+// gs_internal.cuh -- internal layout and device helpers of libgs_gb300.
+//
+// Not part of the C-ABI: the plan's private layout, the workspace carving and
+// the small device functions shared by the kernels of this library.
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include "../../include/gs.h"
+
+namespace gs {
+
+constexpr uint32_t kPlanMagic = 0x67733330u;  // "gs30"
+constexpr int kRadixBits = 8;
+constexpr int kRadix = 1 << kRadixBits;
+constexpr int kSortThreads = 256;
+constexpr int kSortItems = 16;
+constexpr int kSortTile = kSortThreads * kSortItems;  // elements per sort block
+constexpr int kScanThreads = 256;
+constexpr int kScanItems = 8;
+constexpr int kScanTile = kScanThreads * kScanItems;  // elements per scan block
+constexpr int kProjFloats = 12;                       // floats per projected record
+constexpr int kGrad2d = 9;                            // floats per screen-space gradient
+
+// Per-view geometry derived by gs_plan_init; passed to kernels by value.
+struct ViewGeom {
+    int32_t width, height, channels, tiles_x, tiles_y;
+    int32_t tile_offset;   // first global tile id of this view
+    int32_t loss_block_offset;  // first block of this view in the loss kernels
+    int64_t pixel_offset;  // offset in per-pixel maps (H*W units)
+    int64_t value_offset;  // offset in packed planar images (C*H*W units)
+};
+
+struct ViewTable {
+    int32_t n_views;
+    int32_t tile_w, tile_h, log2_tw, log2_th;
+    ViewGeom v[GS_MAX_VIEWS];
+};
+
+// Workspace buffers (ids >= GS_BUF_COUNT are private).
+enum PrivBuf {
+    B_DKEY_A = GS_BUF_COUNT,
+    B_DKEY_B,
+    B_DVAL_B,
+    B_SCAN_BLOCKS,
+    B_HIST,
+    B_IKEY_B,
+    B_IVAL_B,
+    B_LOSS_MAPS,
+    B_LOSS_BLOCKS,
+    B_TOTAL
+};
+
+struct Plan {
+    uint32_t magic;
+    gs_config cfg;
+    int32_t n_capacity;
+    int64_t inst_capacity;
+    int32_t total_tiles, tile_bits, tile_passes;
+    int64_t total_pixels, total_values;
+    int32_t depth_sort_blocks, inst_sort_blocks, scan_blocks, loss_blocks;
+    size_t ws_bytes;
+    size_t off[B_TOTAL];
+    size_t len[B_TOTAL];
+    ViewTable vt;
+};
+static_assert(sizeof(Plan) <= sizeof(gs_plan), "gs_plan too small for the private plan");
+
+// Device counters at the head of the workspace.
+struct DevCounters {
+    uint32_t status;
+    uint32_t n_instances;          // clamped to capacity
+    unsigned long long n_raw;      // before clamping
+    float loss;
+    uint32_t loss_blocks_done;     // last-block-done ticket of the loss reduction
+    uint32_t pad[2];
+};
+
+inline const Plan* P(const gs_plan* p) { return reinterpret_cast<const Plan*>(p); }
+
+template <typename T>
+inline T* buf(const Plan* p, void* ws, int id) {
+    return reinterpret_cast<T*>(static_cast<char*>(ws) + p->off[id]);
+}
+template <typename T>
+inline const T* cbuf(const Plan* p, const void* ws, int id) {
+    return reinterpret_cast<const T*>(static_cast<const char*>(ws) + p->off[id]);
+}
+
+inline cudaStream_t S(void* s) { return reinterpret_cast<cudaStream_t>(s); }
+
+inline gs_status launch_status() {
+    cudaError_t e = cudaGetLastError();
+    return e == cudaSuccess ? GS_OK : GS_ERR_CUDA;
+}
+
+// ---------------------------------------------------------------------------
+// Device helpers.
+// ---------------------------------------------------------------------------
+
+// View of a global tile id: views are few (<= 64), a linear scan is uniform
+// across the block.
+__device__ __forceinline__ int view_of_tile(const ViewTable& vt, int tile) {
+    int v = 0;
+    while (v + 1 < vt.n_views && tile >= vt.v[v + 1].tile_offset) ++v;
+    return v;
+}
+
+// Error-free transformations on floats (Knuth's TwoSum, Dekker's FastTwoSum,
+// and the fma-based exact product).
+__device__ __forceinline__ void two_sum(float a, float b, float& s, float& e) {
+    s = __fadd_rn(a, b);
+    float bb = __fsub_rn(s, a);
+    e = __fadd_rn(__fsub_rn(a, __fsub_rn(s, bb)), __fsub_rn(b, bb));
+}
+__device__ __forceinline__ void fast_two_sum(float a, float b, float& s, float& e) {
+    s = __fadd_rn(a, b);
+    e = __fsub_rn(b, __fsub_rn(s, a));
+}
+__device__ __forceinline__ void two_prod(float a, float b, float& p, float& e) {
+    p = __fmul_rn(a, b);
+    e = __fmaf_rn(a, b, -p);
+}
+
+// Compensated dot product r0*x0 + r1*x1 + r2*x2 + t (Ogita-Rump-Oishi Dot2),
+// returned as a normalised (hi, lo) pair.
+__device__ __forceinline__ void dot3_plus(float r0, float r1, float r2, float x0, float x1,
+                                          float x2, float t, float& hi, float& lo) {
+    float p, e, h, l, s, q;
+    two_prod(r0, x0, p, e);
+    two_prod(r1, x1, h, l);
+    two_sum(p, h, s, q);
+    e = __fadd_rn(e, __fadd_rn(q, l));
+    two_prod(r2, x2, h, l);
+    two_sum(s, h, p, q);
+    e = __fadd_rn(e, __fadd_rn(q, l));
+    two_sum(p, t, s, q);
+    e = __fadd_rn(e, q);
+    fast_two_sum(s, e, hi, lo);
+}
+
+// (xh + xl) / (zh + zl) as a (hi, lo) pair.
+__device__ __forceinline__ void df_div(float xh, float xl, float zh, float zl, float& qh,
+                                       float& ql) {
+    float q1 = __fdiv_rn(xh, zh);
+    // r = x - q1*z, with x - q1*zh exact through the fma
+    float r = __fmaf_rn(-q1, zh, xh);
+    r = __fadd_rn(r, __fmaf_rn(-q1, zl, xl));
+    float q2 = __fdiv_rn(r, zh);
+    fast_two_sum(q1, q2, qh, ql);
+}
+
+// f * (qh + ql) + c as a (hi, lo) pair.
+__device__ __forceinline__ void df_affine(float f, float qh, float ql, float c, float& hi,
+                                          float& lo) {
+    float p, e, s, q;
+    two_prod(f, qh, p, e);
+    e = __fmaf_rn(f, ql, e);
+    two_sum(p, c, s, q);
+    fast_two_sum(s, __fadd_rn(e, q), hi, lo);
+}
+
+// floor((hi + lo) / t) for a power-of-two t, exact for a normalised pair.
+__device__ __forceinline__ int df_floor_div(float hi, float lo, float inv_t) {
+    float a = __fmul_rn(hi, inv_t);  // exact: power-of-two scaling
+    float fa = floorf(a);
+    if (fa == a && lo < 0.0f) fa -= 1.0f;
+    return (int)fa;
+}
+
+// The Gaussian's weight at a pixel, evaluated identically by the forward and
+// the backward kernels: power = -(a dx^2 + c dy^2)/2 - b dx dy.
+__device__ __forceinline__ float gauss_power(float a, float b, float c, float dx, float dy) {
+    float q = __fmaf_rn(a, __fmul_rn(dx, dx), __fmul_rn(c, __fmul_rn(dy, dy)));
+    return __fmaf_rn(-0.5f, q, -__fmul_rn(b, __fmul_rn(dx, dy)));
+}
+
+constexpr float kAlphaMin = 1.0f / 255.0f;
+constexpr float kAlphaMax = 0.99f;
+constexpr float kTMin = 1e-4f;
+
+// ---------------------------------------------------------------------------
+// Host-side launch helpers implemented in the .cu files.
+// ---------------------------------------------------------------------------
+gs_status launch_project(const Plan* p, const gs_map* map, const gs_view* views_dev, void* ws,
+                         cudaStream_t st);
+gs_status launch_bin_sort(const Plan* p, int32_t n, void* ws, cudaStream_t st);
+gs_status launch_render_fwd(const Plan* p, const void* ws, float* images, float* final_T,
+                            int32_t* last_idx, cudaStream_t st);
+gs_status launch_loss(const Plan* p, const float* images, const float* targets, float lambda,
+                      float view_weight, float* loss_dev, float* dL, void* ws, cudaStream_t st);
+gs_status launch_render_bwd(const Plan* p, const gs_map* map, const gs_view* views_dev,
+                            void* ws, const float* final_T, const int32_t* last_idx,
+                            const float* dL, const gs_map_grad* grads, int32_t accumulate,
+                            cudaStream_t st);
+gs_status launch_adam(float* params, const float* grads, float* m, float* v, int64_t n,
+                      int32_t n_groups, const int64_t* offs, const float* lrs, float b1,
+                      float b2, float eps, int32_t* step_dev, cudaStream_t st);
+
+}  // namespace gs

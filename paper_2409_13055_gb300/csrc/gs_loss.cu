@@ -1,0 +1,250 @@
+// gs_loss.cu -- A6 photometric loss (paper Eq. 2) and its gradient.
+//
+// Eq. 2 as printed adds lambda * SSIM, which would reward dissimilarity, and
+// has no mean; it is read as
+//   L_v = (1 - lambda) mean|I - I_gt| + lambda (1 - mean SSIM(I, I_gt)),
+// SSIM with an 11x11 Gaussian window (sigma 1.5, unit sum), zero padding,
+// C1 = 0.01^2, C2 = 0.03^2, per channel, means over C*H*W of the view, and
+// L = view_weight * sum over views (1/n_views: the mean).
+//
+// Two kernels, each over 32x16 output tiles of every channel plane of every
+// view.  The forward stages the tile plus a 5-pixel halo of both images in
+// shared memory and forms the five window moments (E[x], E[y], E[x^2],
+// E[y^2], E[xy]) with separable 11-tap passes; per pixel it keeps the partial
+// derivatives of SSIM with respect to E[x], E[x^2] and E[xy].  The backward
+// correlates those three maps with the same window (the adjoint of a
+// zero-padded symmetric correlation is itself) and adds the L1 term.  The
+// loss is reduced deterministically: per-block partials, summed in block
+// order by whichever block finishes last (a ticket counter, no waiting).
+#include <math.h>
+
+#include "gs_internal.cuh"
+
+namespace gs {
+namespace {
+
+constexpr int kTX = 32, kTY = 16, kHalo = 5, kWin = 11;
+constexpr int kRows = kTY + 2 * kHalo;  // 26
+constexpr int kCols = kTX + 2 * kHalo;  // 42
+constexpr int kLossThreads = 256;       // 32 x 8
+
+struct Win {
+    float w[kWin];
+};
+
+struct BlockPos {
+    int view, ch, x0, y0, width, height;
+    int64_t plane;  // offset of the channel plane in packed images
+};
+
+__device__ __forceinline__ BlockPos block_pos(const ViewTable& vt, int b) {
+    int v = 0;
+    while (v + 1 < vt.n_views && b >= vt.v[v + 1].loss_block_offset) ++v;
+    const ViewGeom& g = vt.v[v];
+    const int bx = (g.width + kTX - 1) / kTX, by = (g.height + kTY - 1) / kTY;
+    int r = b - g.loss_block_offset;
+    BlockPos p;
+    p.view = v;
+    p.ch = r / (bx * by);
+    r -= p.ch * bx * by;
+    p.x0 = (r % bx) * kTX;
+    p.y0 = (r / bx) * kTY;
+    p.width = g.width;
+    p.height = g.height;
+    p.plane = g.value_offset + (int64_t)p.ch * g.width * g.height;
+    return p;
+}
+
+__device__ __forceinline__ float block_sum(float x, float* red) {
+    const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) x += __shfl_xor_sync(0xffffffffu, x, o);
+    if (lane == 0) red[w] = x;
+    __syncthreads();
+    float t = 0.0f;
+    if (threadIdx.x == 0)
+        for (int k = 0; k < (int)(blockDim.x >> 5); ++k) t += red[k];
+    __syncthreads();
+    return t;  // valid in thread 0
+}
+
+__global__ void __launch_bounds__(kLossThreads)
+k_ssim_fwd(ViewTable vt, Win win, const float* __restrict__ img, const float* __restrict__ tgt,
+           float lambda, float inv_views, int64_t total_values, float* __restrict__ maps,
+           float* __restrict__ partials, int nblocks, DevCounters* ctr,
+           float* __restrict__ loss_dev) {
+    __shared__ float sx[kRows][kCols + 1], sy[kRows][kCols + 1];
+    __shared__ float h[5][kRows][kTX + 1];
+    __shared__ float red[32];
+    __shared__ bool is_last;
+    const BlockPos bp = block_pos(vt, blockIdx.x);
+    for (int i = threadIdx.x; i < kRows * kCols; i += blockDim.x) {
+        const int r = i / kCols, c = i - r * kCols;
+        const int y = bp.y0 - kHalo + r, x = bp.x0 - kHalo + c;
+        float a = 0.0f, b = 0.0f;
+        if (x >= 0 && x < bp.width && y >= 0 && y < bp.height) {
+            a = img[bp.plane + (int64_t)y * bp.width + x];
+            b = tgt[bp.plane + (int64_t)y * bp.width + x];
+        }
+        sx[r][c] = a;
+        sy[r][c] = b;
+    }
+    __syncthreads();
+    for (int i = threadIdx.x; i < kRows * kTX; i += blockDim.x) {
+        const int r = i / kTX, c = i - r * kTX;
+        float mx = 0.f, my = 0.f, xx = 0.f, yy = 0.f, xy = 0.f;
+#pragma unroll
+        for (int k = 0; k < kWin; ++k) {
+            const float a = sx[r][c + k], b = sy[r][c + k], w = win.w[k];
+            mx = fmaf(w, a, mx);
+            my = fmaf(w, b, my);
+            xx = fmaf(w, a * a, xx);
+            yy = fmaf(w, b * b, yy);
+            xy = fmaf(w, a * b, xy);
+        }
+        h[0][r][c] = mx;
+        h[1][r][c] = my;
+        h[2][r][c] = xx;
+        h[3][r][c] = yy;
+        h[4][r][c] = xy;
+    }
+    __syncthreads();
+    const float C1 = 0.01f * 0.01f, C2 = 0.03f * 0.03f;
+    const int tx = threadIdx.x & 31, ty = threadIdx.x >> 5;
+    float l1 = 0.0f, ss = 0.0f;
+    for (int rr = ty; rr < kTY; rr += kLossThreads / 32) {
+        const int x = bp.x0 + tx, y = bp.y0 + rr;
+        if (x >= bp.width || y >= bp.height) continue;
+        float m[5] = {0.f, 0.f, 0.f, 0.f, 0.f};
+#pragma unroll
+        for (int k = 0; k < kWin; ++k) {
+            const float w = win.w[k];
+#pragma unroll
+            for (int q = 0; q < 5; ++q) m[q] = fmaf(w, h[q][rr + k][tx], m[q]);
+        }
+        const float mx = m[0], my = m[1];
+        const float vx = m[2] - mx * mx, vy = m[3] - my * my, cxy = m[4] - mx * my;
+        const float A = 2.0f * mx * my + C1, B = 2.0f * cxy + C2;
+        const float Cd = mx * mx + my * my + C1, D = vx + vy + C2;
+        const float iCD = 1.0f / (Cd * D);
+        const float s = A * B * iCD;
+        // dSSIM/dE[x], dSSIM/dE[x^2], dSSIM/dE[xy] (E[y], E[y^2] held fixed)
+        const float ds_dm = (2.0f * my * B - 2.0f * my * A) * iCD - s * (2.0f * mx / Cd - 2.0f * mx / D);
+        const float ds_dxx = -s / D;
+        const float ds_dxy = 2.0f * A * iCD;
+        const int64_t idx = bp.plane + (int64_t)y * bp.width + x;
+        maps[idx] = ds_dm;
+        maps[total_values + idx] = ds_dxx;
+        maps[2 * total_values + idx] = ds_dxy;
+        ss += s;
+        l1 += fabsf(sx[rr + kHalo][tx + kHalo] - sy[rr + kHalo][tx + kHalo]);
+    }
+    const ViewGeom& g = vt.v[bp.view];
+    const float invM = 1.0f / ((float)g.channels * (float)g.width * (float)g.height);
+    const float part = inv_views * invM * ((1.0f - lambda) * l1 - lambda * ss);
+    const float tot = block_sum(part, red);
+    if (threadIdx.x == 0) {
+        partials[blockIdx.x] = tot;
+        __threadfence();
+        const uint32_t ticket = atomicAdd(&ctr->loss_blocks_done, 1u);
+        is_last = (ticket == (uint32_t)nblocks - 1);
+    }
+    __syncthreads();
+    if (!is_last) return;
+    __threadfence();
+    float acc = 0.0f;
+    for (int i = threadIdx.x; i < nblocks; i += blockDim.x) acc += ((volatile float*)partials)[i];
+    const float all = block_sum(acc, red);
+    if (threadIdx.x == 0) {
+        const float L = lambda * inv_views * (float)vt.n_views + all;
+        *loss_dev = L;
+        ctr->loss = L;
+        ctr->loss_blocks_done = 0u;
+    }
+}
+
+__global__ void __launch_bounds__(kLossThreads)
+k_ssim_bwd(ViewTable vt, Win win, const float* __restrict__ img, const float* __restrict__ tgt,
+           float lambda, float inv_views, int64_t total_values, const float* __restrict__ maps,
+           float* __restrict__ dL) {
+    __shared__ float sm[3][kRows][kCols + 1];
+    __shared__ float h[3][kRows][kTX + 1];
+    const BlockPos bp = block_pos(vt, blockIdx.x);
+    for (int i = threadIdx.x; i < kRows * kCols; i += blockDim.x) {
+        const int r = i / kCols, c = i - r * kCols;
+        const int y = bp.y0 - kHalo + r, x = bp.x0 - kHalo + c;
+        float a = 0.f, b = 0.f, d = 0.f;
+        if (x >= 0 && x < bp.width && y >= 0 && y < bp.height) {
+            const int64_t idx = bp.plane + (int64_t)y * bp.width + x;
+            a = maps[idx];
+            b = maps[total_values + idx];
+            d = maps[2 * total_values + idx];
+        }
+        sm[0][r][c] = a;
+        sm[1][r][c] = b;
+        sm[2][r][c] = d;
+    }
+    __syncthreads();
+    for (int i = threadIdx.x; i < kRows * kTX; i += blockDim.x) {
+        const int r = i / kTX, c = i - r * kTX;
+        float a = 0.f, b = 0.f, d = 0.f;
+#pragma unroll
+        for (int k = 0; k < kWin; ++k) {
+            const float w = win.w[k];
+            a = fmaf(w, sm[0][r][c + k], a);
+            b = fmaf(w, sm[1][r][c + k], b);
+            d = fmaf(w, sm[2][r][c + k], d);
+        }
+        h[0][r][c] = a;
+        h[1][r][c] = b;
+        h[2][r][c] = d;
+    }
+    __syncthreads();
+    const ViewGeom& g = vt.v[bp.view];
+    const float scale = inv_views / ((float)g.channels * (float)g.width * (float)g.height);
+    const int tx = threadIdx.x & 31, ty = threadIdx.x >> 5;
+    for (int rr = ty; rr < kTY; rr += kLossThreads / 32) {
+        const int x = bp.x0 + tx, y = bp.y0 + rr;
+        if (x >= bp.width || y >= bp.height) continue;
+        float a = 0.f, b = 0.f, d = 0.f;
+#pragma unroll
+        for (int k = 0; k < kWin; ++k) {
+            const float w = win.w[k];
+            a = fmaf(w, h[0][rr + k][tx], a);
+            b = fmaf(w, h[1][rr + k][tx], b);
+            d = fmaf(w, h[2][rr + k][tx], d);
+        }
+        const int64_t idx = bp.plane + (int64_t)y * bp.width + x;
+        const float xv = img[idx], yv = tgt[idx];
+        const float diff = xv - yv;
+        const float sgn = diff > 0.0f ? 1.0f : (diff < 0.0f ? -1.0f : 0.0f);
+        const float dssim = a + 2.0f * xv * b + yv * d;
+        dL[idx] = scale * ((1.0f - lambda) * sgn - lambda * dssim);
+    }
+}
+
+}  // namespace
+
+gs_status launch_loss(const Plan* p, const float* images, const float* targets, float lambda,
+                      float view_weight, float* loss_dev, float* dL, void* ws, cudaStream_t st) {
+    Win win;
+    double g[kWin], s = 0.0;
+    for (int k = 0; k < kWin; ++k) {
+        const double d = k - kHalo;
+        g[k] = exp(-d * d / (2.0 * 1.5 * 1.5));
+        s += g[k];
+    }
+    for (int k = 0; k < kWin; ++k) win.w[k] = (float)(g[k] / s);
+    float* maps = buf<float>(p, ws, B_LOSS_MAPS);
+    float* partials = buf<float>(p, ws, B_LOSS_BLOCKS);
+    DevCounters* ctr = buf<DevCounters>(p, ws, GS_BUF_COUNTERS);
+    const float inv_views = view_weight;
+    k_ssim_fwd<<<p->loss_blocks, kLossThreads, 0, st>>>(p->vt, win, images, targets, lambda,
+                                                        inv_views, p->total_values, maps,
+                                                        partials, p->loss_blocks, ctr, loss_dev);
+    k_ssim_bwd<<<p->loss_blocks, kLossThreads, 0, st>>>(p->vt, win, images, targets, lambda,
+                                                        inv_views, p->total_values, maps, dL);
+    return launch_status();
+}
+
+}  // namespace gs

@@ -1,0 +1,547 @@
+// gs_project.cu -- A1 projection and A8 projection adjoint.
+//
+// Projection follows the original 3DGS rasteriser the method renders with
+// (paper Sec. III-B) and the projection step of Sec. II: per (view,
+// Gaussian) the camera transform, EWA splatting of the 3D covariance into a
+// dilated 2D covariance and its conic, a 3-sigma square extent and tile rect,
+// a spherical-harmonics colour and a sigmoid opacity.
+//
+// GB300 layout decisions:
+//  * one thread per Gaussian and per group of up to 4 views: the Gaussian's
+//    parameters and its 3D covariance are loaded/computed once and reused for
+//    every view of the group, so a 16-view batch reads the map 4 times, not 16;
+//  * the camera transform, the perspective divide and the projected mean are
+//    carried as float pairs (error-free transformations), so the projected
+//    mean is exact to ~1e-12 relative and the FP32 depth key is the correctly
+//    rounded depth; the renderers then evaluate every Gaussian in tile-local
+//    coordinates, where FP32 keeps ~1e-6 px;
+//  * the SH coefficients are stored coefficient-major ([K][N][3]), so each
+//    coefficient plane is read by a warp as one contiguous 384-byte run.
+#include "gs_internal.cuh"
+
+namespace gs {
+namespace {
+
+constexpr int kProjThreads = 256;
+constexpr int kViewsPerThread = 4;
+
+// Real spherical harmonics with the Condon-Shortley phase, degrees 0..3,
+// ordered m = -l..l, as polynomials of a unit direction.
+constexpr float kY0 = 0.28209479177387814f;
+constexpr float kY1 = 0.4886025119029199f;
+constexpr float kY2a = 1.0925484305920792f;
+constexpr float kY2b = 0.31539156525252005f;
+constexpr float kY2c = 0.5462742152960396f;
+constexpr float kY3a = 0.5900435899266435f;
+constexpr float kY3b = 2.890611442640554f;
+constexpr float kY3c = 0.4570457994644658f;
+constexpr float kY3d = 0.3731763325901154f;
+constexpr float kY3e = 1.445305721320277f;
+
+__device__ __forceinline__ void sh_eval(int degree, float x, float y, float z, float* Y) {
+    Y[0] = kY0;
+    if (degree < 1) return;
+    Y[1] = -kY1 * y;
+    Y[2] = kY1 * z;
+    Y[3] = -kY1 * x;
+    if (degree < 2) return;
+    const float xx = x * x, yy = y * y, zz = z * z;
+    Y[4] = kY2a * x * y;
+    Y[5] = -kY2a * y * z;
+    Y[6] = kY2b * (2.0f * zz - xx - yy);
+    Y[7] = -kY2a * x * z;
+    Y[8] = kY2c * (xx - yy);
+    if (degree < 3) return;
+    Y[9] = -kY3a * y * (3.0f * xx - yy);
+    Y[10] = kY3b * x * y * z;
+    Y[11] = -kY3c * y * (4.0f * zz - xx - yy);
+    Y[12] = kY3d * z * (2.0f * zz - 3.0f * xx - 3.0f * yy);
+    Y[13] = -kY3c * x * (4.0f * zz - xx - yy);
+    Y[14] = kY3e * z * (xx - yy);
+    Y[15] = -kY3a * x * (xx - 3.0f * yy);
+}
+
+// d/d(x,y,z) of the polynomials above, accumulated as g += w * grad Y_k.
+__device__ __forceinline__ void sh_grad_acc(int degree, float x, float y, float z,
+                                            const float* w, float& gx, float& gy, float& gz) {
+    if (degree < 1) return;
+    gx += -kY1 * w[3];
+    gy += -kY1 * w[1];
+    gz += kY1 * w[2];
+    if (degree < 2) return;
+    const float xx = x * x, yy = y * y, zz = z * z;
+    gx += kY2a * y * w[4] - kY2a * z * w[7] - 2.0f * kY2b * x * w[6] + 2.0f * kY2c * x * w[8];
+    gy += kY2a * x * w[4] - kY2a * z * w[5] - 2.0f * kY2b * y * w[6] - 2.0f * kY2c * y * w[8];
+    gz += -kY2a * y * w[5] - kY2a * x * w[7] + 4.0f * kY2b * z * w[6];
+    if (degree < 3) return;
+    gx += -kY3a * 6.0f * x * y * w[9] + kY3b * y * z * w[10] + kY3c * 2.0f * x * y * w[11] -
+          kY3d * 6.0f * x * z * w[12] - kY3c * (4.0f * zz - 3.0f * xx - yy) * w[13] +
+          kY3e * 2.0f * x * z * w[14] - kY3a * (3.0f * xx - 3.0f * yy) * w[15];
+    gy += -kY3a * (3.0f * xx - 3.0f * yy) * w[9] + kY3b * x * z * w[10] -
+          kY3c * (4.0f * zz - xx - 3.0f * yy) * w[11] - kY3d * 6.0f * y * z * w[12] +
+          kY3c * 2.0f * x * y * w[13] - kY3e * 2.0f * y * z * w[14] + kY3a * 6.0f * x * y * w[15];
+    gz += kY3b * x * y * w[10] - kY3c * 8.0f * y * z * w[11] +
+          kY3d * (6.0f * zz - 3.0f * xx - 3.0f * yy) * w[12] - kY3c * 8.0f * x * z * w[13] +
+          kY3e * (xx - yy) * w[14];
+}
+
+struct Cam {
+    float R[9], t[3], fx, fy, cx, cy, cc[3];
+    float ulo, uhi, vlo, vhi;
+    int width, height;
+};
+
+__device__ void load_cam(const gs_view& vw, Cam& c) {
+    for (int k = 0; k < 9; ++k) c.R[k] = vw.R[k];
+    for (int k = 0; k < 3; ++k) c.t[k] = vw.t[k];
+    c.fx = vw.fx;
+    c.fy = vw.fy;
+    c.cx = vw.cx;
+    c.cy = vw.cy;
+    // camera centre -R^T t
+    for (int k = 0; k < 3; ++k)
+        c.cc[k] = -(c.R[k] * c.t[0] + c.R[3 + k] * c.t[1] + c.R[6 + k] * c.t[2]);
+    c.width = vw.width;
+    c.height = vw.height;
+    // Jacobian clamp: x/z in [-1.3 cx/fx, 1.3 (W - cx)/fx], same for y.
+    c.ulo = -1.3f * c.cx / c.fx;
+    c.uhi = 1.3f * ((float)vw.width - c.cx) / c.fx;
+    c.vlo = -1.3f * c.cy / c.fy;
+    c.vhi = 1.3f * ((float)vw.height - c.cy) / c.fy;
+}
+
+// View-independent part of a Gaussian: normalised rotation, scales, 3D covariance.
+struct Shape {
+    float qn[4], qnorm, Rq[9], s[3];
+    float sig[6];  // 00 01 02 11 12 22
+    bool finite;
+};
+
+__device__ __forceinline__ void make_shape(const float* ls, const float* q4, Shape& sh) {
+    float w = q4[0], x = q4[1], y = q4[2], z = q4[3];
+    float nn = w * w + x * x + y * y + z * z;
+    sh.finite = isfinite(nn) && nn > 0.0f && isfinite(ls[0]) && isfinite(ls[1]) &&
+                isfinite(ls[2]);
+    sh.qnorm = sqrtf(nn);
+    float inv = 1.0f / sh.qnorm;
+    w *= inv; x *= inv; y *= inv; z *= inv;
+    sh.qn[0] = w; sh.qn[1] = x; sh.qn[2] = y; sh.qn[3] = z;
+    float* R = sh.Rq;
+    R[0] = 1.f - 2.f * (y * y + z * z); R[1] = 2.f * (x * y - w * z); R[2] = 2.f * (x * z + w * y);
+    R[3] = 2.f * (x * y + w * z); R[4] = 1.f - 2.f * (x * x + z * z); R[5] = 2.f * (y * z - w * x);
+    R[6] = 2.f * (x * z - w * y); R[7] = 2.f * (y * z + w * x); R[8] = 1.f - 2.f * (x * x + y * y);
+    for (int k = 0; k < 3; ++k) sh.s[k] = expf(ls[k]);
+    // Sigma = M M^T, M = Rq diag(s)
+    float M[9];
+    for (int r = 0; r < 3; ++r)
+        for (int c = 0; c < 3; ++c) M[3 * r + c] = R[3 * r + c] * sh.s[c];
+    auto dot = [&](int a, int b) {
+        return M[3 * a] * M[3 * b] + M[3 * a + 1] * M[3 * b + 1] + M[3 * a + 2] * M[3 * b + 2];
+    };
+    sh.sig[0] = dot(0, 0); sh.sig[1] = dot(0, 1); sh.sig[2] = dot(0, 2);
+    sh.sig[3] = dot(1, 1); sh.sig[4] = dot(1, 2); sh.sig[5] = dot(2, 2);
+}
+
+// Per-view projection of one Gaussian.
+struct Proj {
+    bool visible;
+    float xc[3];              // camera-space mean (hi parts)
+    float mxh, myh, mxl, myl; // projected mean as float pairs
+    float u, v;               // clamped x/z, y/z
+    bool uc, vc;              // clamp engaged
+    float T[6];               // J W, row-major 2x3
+    float a, b, c;            // dilated 2D covariance
+    float det, ca, cb, cc;    // conic
+    int radius;
+    int rect[4];
+    float dir[3], dist;
+};
+
+__device__ __forceinline__ void project_one(const float* mean, const Shape& sh, const Cam& cam,
+                                            float near_z, int log2_tw, int log2_th, int tiles_x,
+                                            int tiles_y, Proj& p) {
+    p.visible = false;
+    float xh, xl, yh, yl, zh, zl;
+    dot3_plus(cam.R[0], cam.R[1], cam.R[2], mean[0], mean[1], mean[2], cam.t[0], xh, xl);
+    dot3_plus(cam.R[3], cam.R[4], cam.R[5], mean[0], mean[1], mean[2], cam.t[1], yh, yl);
+    dot3_plus(cam.R[6], cam.R[7], cam.R[8], mean[0], mean[1], mean[2], cam.t[2], zh, zl);
+    p.xc[0] = xh; p.xc[1] = yh; p.xc[2] = zh;
+    if (!(isfinite(xh) && isfinite(yh) && isfinite(zh)) || !sh.finite) return;
+    if (!(zh > near_z)) return;
+    float uh, ul, vh, vl;
+    df_div(xh, xl, zh, zl, uh, ul);
+    df_div(yh, yl, zh, zl, vh, vl);
+    df_affine(cam.fx, uh, ul, cam.cx, p.mxh, p.mxl);
+    df_affine(cam.fy, vh, vl, cam.cy, p.myh, p.myl);
+
+    p.u = fminf(fmaxf(uh, cam.ulo), cam.uhi);
+    p.v = fminf(fmaxf(vh, cam.vlo), cam.vhi);
+    p.uc = (uh < cam.ulo) || (uh > cam.uhi);
+    p.vc = (vh < cam.vlo) || (vh > cam.vhi);
+    const float iz = 1.0f / zh;
+    const float J00 = cam.fx * iz, J02 = -cam.fx * p.u * iz;
+    const float J11 = cam.fy * iz, J12 = -cam.fy * p.v * iz;
+    const float* W = cam.R;
+    for (int k = 0; k < 3; ++k) {
+        p.T[k] = J00 * W[k] + J02 * W[6 + k];
+        p.T[3 + k] = J11 * W[3 + k] + J12 * W[6 + k];
+    }
+    const float* S = sh.sig;
+    // Sigma T0^T and Sigma T1^T
+    float s0[3], s1[3];
+    s0[0] = S[0] * p.T[0] + S[1] * p.T[1] + S[2] * p.T[2];
+    s0[1] = S[1] * p.T[0] + S[3] * p.T[1] + S[4] * p.T[2];
+    s0[2] = S[2] * p.T[0] + S[4] * p.T[1] + S[5] * p.T[2];
+    s1[0] = S[0] * p.T[3] + S[1] * p.T[4] + S[2] * p.T[5];
+    s1[1] = S[1] * p.T[3] + S[3] * p.T[4] + S[4] * p.T[5];
+    s1[2] = S[2] * p.T[3] + S[4] * p.T[4] + S[5] * p.T[5];
+    p.a = p.T[0] * s0[0] + p.T[1] * s0[1] + p.T[2] * s0[2] + 0.3f;
+    p.b = p.T[3] * s0[0] + p.T[4] * s0[1] + p.T[5] * s0[2];
+    p.c = p.T[3] * s1[0] + p.T[4] * s1[1] + p.T[5] * s1[2] + 0.3f;
+    // det = a c - b^2 with Kahan's fma-compensated 2x2 determinant
+    const float w = __fmul_rn(p.b, p.b);
+    const float e = __fmaf_rn(-p.b, p.b, w);
+    const float f = __fmaf_rn(p.a, p.c, -w);
+    p.det = __fadd_rn(f, e);
+    if (!(p.det > 0.0f)) return;
+    const float idet = 1.0f / p.det;
+    p.ca = p.c * idet;
+    p.cb = -p.b * idet;
+    p.cc = p.a * idet;
+    const float mid = 0.5f * (p.a + p.c);
+    const float lam = mid + sqrtf(fmaxf(0.0f, mid * mid - p.det));
+    p.radius = (int)ceilf(3.0f * sqrtf(lam));
+    const float rr = (float)p.radius;
+    const float itw = 1.0f / (float)(1 << log2_tw), ith = 1.0f / (float)(1 << log2_th);
+    const float tw1 = (float)((1 << log2_tw) - 1), th1 = (float)((1 << log2_th) - 1);
+    float sh_, sl;
+    float e2;
+    two_sum(p.mxh, -rr, sh_, e2);
+    fast_two_sum(sh_, __fadd_rn(e2, p.mxl), sh_, sl);
+    int x0 = df_floor_div(sh_, sl, itw);
+    two_sum(p.myh, -rr, sh_, e2);
+    fast_two_sum(sh_, __fadd_rn(e2, p.myl), sh_, sl);
+    int y0 = df_floor_div(sh_, sl, ith);
+    two_sum(p.mxh, rr + tw1, sh_, e2);
+    fast_two_sum(sh_, __fadd_rn(e2, p.mxl), sh_, sl);
+    int x1 = df_floor_div(sh_, sl, itw);
+    two_sum(p.myh, rr + th1, sh_, e2);
+    fast_two_sum(sh_, __fadd_rn(e2, p.myl), sh_, sl);
+    int y1 = df_floor_div(sh_, sl, ith);
+    p.rect[0] = min(max(x0, 0), tiles_x);
+    p.rect[1] = min(max(y0, 0), tiles_y);
+    p.rect[2] = min(max(x1, 0), tiles_x);
+    p.rect[3] = min(max(y1, 0), tiles_y);
+    if ((p.rect[2] - p.rect[0]) * (p.rect[3] - p.rect[1]) <= 0) return;
+    float d0 = mean[0] - cam.cc[0], d1 = mean[1] - cam.cc[1], d2 = mean[2] - cam.cc[2];
+    p.dist = sqrtf(d0 * d0 + d1 * d1 + d2 * d2);
+    float idist = p.dist > 0.0f ? 1.0f / p.dist : 0.0f;
+    p.dir[0] = d0 * idist; p.dir[1] = d1 * idist; p.dir[2] = d2 * idist;
+    p.visible = true;
+}
+
+template <int DEG>
+__global__ void __launch_bounds__(kProjThreads)
+k_project(const float* __restrict__ means, const float* __restrict__ log_scales,
+          const float* __restrict__ quats, const float* __restrict__ opacity_logits,
+          const float* __restrict__ sh, int n, const gs_view* __restrict__ views,
+          ViewTable vt, float near_z, float4* __restrict__ rec, uint16_t* __restrict__ rect_out,
+          uint32_t* __restrict__ touched, int32_t* __restrict__ radius_out,
+          uint32_t* __restrict__ dkey, uint32_t* __restrict__ dval, DevCounters* counters) {
+    __shared__ Cam cams[kViewsPerThread];
+    const int v0 = blockIdx.y * kViewsPerThread;
+    const int nv = min(kViewsPerThread, vt.n_views - v0);
+    if (threadIdx.x < nv) load_cam(views[v0 + threadIdx.x], cams[threadIdx.x]);
+    __syncthreads();
+    const int g = blockIdx.x * blockDim.x + threadIdx.x;
+    if (g >= n) return;
+    const float mean[3] = {means[3 * g], means[3 * g + 1], means[3 * g + 2]};
+    const float ls[3] = {log_scales[3 * g], log_scales[3 * g + 1], log_scales[3 * g + 2]};
+    const float4 q = reinterpret_cast<const float4*>(quats)[g];
+    const float q4[4] = {q.x, q.y, q.z, q.w};
+    Shape shp;
+    make_shape(ls, q4, shp);
+    const float logit = opacity_logits[g];
+    const bool finite = shp.finite && isfinite(logit) && isfinite(mean[0]) &&
+                        isfinite(mean[1]) && isfinite(mean[2]);
+    if (!finite && v0 == 0) atomicOr(&counters->status, (uint32_t)GS_DEV_NONFINITE);
+    const float opacity = 1.0f / (1.0f + expf(-logit));
+    constexpr int K = (DEG + 1) * (DEG + 1);
+    for (int j = 0; j < nv; ++j) {
+        const int v = v0 + j;
+        const size_t vg = (size_t)v * n + g;
+        const ViewGeom& geo = vt.v[v];
+        Proj p;
+        project_one(mean, shp, cams[j], near_z, vt.log2_tw, vt.log2_th, geo.tiles_x,
+                    geo.tiles_y, p);
+        const bool vis = finite && p.visible;
+        dval[vg] = (uint32_t)vg;
+        if (!vis) {
+            touched[vg] = 0u;
+            dkey[vg] = 0xFFFFFFFFu;
+            radius_out[vg] = 0;
+            reinterpret_cast<uint2*>(rect_out)[vg] = make_uint2(0u, 0u);
+            continue;
+        }
+        float Y[16];
+        sh_eval(DEG, p.dir[0], p.dir[1], p.dir[2], Y);
+        float col[3] = {0.f, 0.f, 0.f};
+#pragma unroll
+        for (int k = 0; k < K; ++k) {
+            const float* c = sh + ((size_t)k * n + g) * 3;
+            col[0] = fmaf(Y[k], c[0], col[0]);
+            col[1] = fmaf(Y[k], c[1], col[1]);
+            col[2] = fmaf(Y[k], c[2], col[2]);
+        }
+#pragma unroll
+        for (int ch = 0; ch < 3; ++ch) col[ch] = fmaxf(col[ch] + 0.5f, 0.0f);
+        float4* r = rec + vg * 3;
+        r[0] = make_float4(p.mxh, p.myh, p.mxl, p.myl);
+        r[1] = make_float4(p.ca, p.cb, p.cc, opacity);
+        r[2] = make_float4(col[0], col[1], col[2], p.xc[2]);
+        touched[vg] = (uint32_t)((p.rect[2] - p.rect[0]) * (p.rect[3] - p.rect[1]));
+        dkey[vg] = __float_as_uint(p.xc[2]);
+        radius_out[vg] = p.radius;
+        uint2 rc;
+        rc.x = (uint32_t)p.rect[0] | ((uint32_t)p.rect[1] << 16);
+        rc.y = (uint32_t)p.rect[2] | ((uint32_t)p.rect[3] << 16);
+        reinterpret_cast<uint2*>(rect_out)[vg] = rc;
+    }
+}
+
+// A8: chain rule of the projection, summed over views.  One thread per
+// Gaussian reads its screen-space gradient from every view it is visible in.
+template <int DEG>
+__global__ void __launch_bounds__(kProjThreads)
+k_project_bwd(const float* __restrict__ means, const float* __restrict__ log_scales,
+              const float* __restrict__ quats, const float* __restrict__ opacity_logits,
+              const float* __restrict__ sh, int n, const gs_view* __restrict__ views,
+              ViewTable vt, float near_z, const uint32_t* __restrict__ touched,
+              const float* __restrict__ grad2d, float* __restrict__ g_means,
+              float* __restrict__ g_ls, float* __restrict__ g_quats, float* __restrict__ g_logit,
+              float* __restrict__ g_sh, int accumulate) {
+    extern __shared__ Cam cam_all[];
+    for (int v = threadIdx.x; v < vt.n_views; v += blockDim.x) load_cam(views[v], cam_all[v]);
+    __syncthreads();
+    const int g = blockIdx.x * blockDim.x + threadIdx.x;
+    if (g >= n) return;
+    const float mean[3] = {means[3 * g], means[3 * g + 1], means[3 * g + 2]};
+    const float ls[3] = {log_scales[3 * g], log_scales[3 * g + 1], log_scales[3 * g + 2]};
+    const float4 q = reinterpret_cast<const float4*>(quats)[g];
+    const float q4[4] = {q.x, q.y, q.z, q.w};
+    Shape shp;
+    make_shape(ls, q4, shp);
+    const float logit = opacity_logits[g];
+    const float opacity = 1.0f / (1.0f + expf(-logit));
+    constexpr int K = (DEG + 1) * (DEG + 1);
+
+    float gm[3] = {0.f, 0.f, 0.f};
+    float gsig[6] = {0.f, 0.f, 0.f, 0.f, 0.f, 0.f};  // dL/dSigma as a symmetric matrix
+    float gop = 0.0f;
+    float gshc[K][3];
+#pragma unroll
+    for (int k = 0; k < K; ++k) gshc[k][0] = gshc[k][1] = gshc[k][2] = 0.0f;
+
+    for (int v = 0; v < vt.n_views; ++v) {
+        const size_t vg = (size_t)v * n + g;
+        if (touched[vg] == 0u) continue;
+        const float* g2 = grad2d + vg * kGrad2d;
+        float gmx = g2[0], gmy = g2[1], gA = g2[2], gB = g2[3], gC = g2[4], gO = g2[5];
+        float gcol[3] = {g2[6], g2[7], g2[8]};
+        const ViewGeom& geo = vt.v[v];
+        if (geo.channels == 1) gcol[0] = gcol[1] = gcol[2] = g2[6] * (1.0f / 3.0f);
+        const Cam& cam = cam_all[v];
+        Proj p;
+        project_one(mean, shp, cam, near_z, vt.log2_tw, vt.log2_th, geo.tiles_x, geo.tiles_y, p);
+        if (!p.visible) continue;
+
+        gop += gO;
+        // colour -> SH coefficients and the viewing direction
+        float Y[16];
+        sh_eval(DEG, p.dir[0], p.dir[1], p.dir[2], Y);
+        float col[3] = {0.f, 0.f, 0.f};
+#pragma unroll
+        for (int k = 0; k < K; ++k) {
+            const float* c = sh + ((size_t)k * n + g) * 3;
+            col[0] = fmaf(Y[k], c[0], col[0]);
+            col[1] = fmaf(Y[k], c[1], col[1]);
+            col[2] = fmaf(Y[k], c[2], col[2]);
+        }
+        // a clamped channel passes no gradient
+#pragma unroll
+        for (int ch = 0; ch < 3; ++ch)
+            if (col[ch] + 0.5f < 0.0f) gcol[ch] = 0.0f;
+        float w[16];
+#pragma unroll
+        for (int k = 0; k < 16; ++k) w[k] = 0.0f;
+#pragma unroll
+        for (int k = 0; k < K; ++k) {
+            const float* c = sh + ((size_t)k * n + g) * 3;
+            gshc[k][0] += Y[k] * gcol[0];
+            gshc[k][1] += Y[k] * gcol[1];
+            gshc[k][2] += Y[k] * gcol[2];
+            w[k] = gcol[0] * c[0] + gcol[1] * c[1] + gcol[2] * c[2];
+        }
+        float gd[3] = {0.f, 0.f, 0.f};
+        sh_grad_acc(DEG, p.dir[0], p.dir[1], p.dir[2], w, gd[0], gd[1], gd[2]);
+        if (p.dist > 0.0f) {
+            const float dd = gd[0] * p.dir[0] + gd[1] * p.dir[1] + gd[2] * p.dir[2];
+            const float id = 1.0f / p.dist;
+            for (int e = 0; e < 3; ++e) gm[e] += (gd[e] - p.dir[e] * dd) * id;
+        }
+        // conic -> 2D covariance: dL/dCov = -Q G Q, G = [[gA, gB/2], [gB/2, gC]]
+        const float A = p.ca, B = p.cb, C = p.cc;
+        const float ga = -(A * A * gA + A * B * gB + B * B * gC);
+        const float gc = -(B * B * gA + B * C * gB + C * C * gC);
+        const float gb = -(2.0f * A * B * gA + (A * C + B * B) * gB + 2.0f * B * C * gC);
+        // Cov = T Sigma T^T + 0.3 I:
+        //   dSigma += T^T Gs T with Gs = [[ga, gb/2], [gb/2, gc]]
+        //   dT = 2 Gs T Sigma
+        const float* T = p.T;
+        const float hb = 0.5f * gb;
+        float GT[6];  // Gs T
+        for (int k = 0; k < 3; ++k) {
+            GT[k] = ga * T[k] + hb * T[3 + k];
+            GT[3 + k] = hb * T[k] + gc * T[3 + k];
+        }
+        gsig[0] += T[0] * GT[0] + T[3] * GT[3];
+        gsig[1] += T[0] * GT[1] + T[3] * GT[4];
+        gsig[2] += T[0] * GT[2] + T[3] * GT[5];
+        gsig[3] += T[1] * GT[1] + T[4] * GT[4];
+        gsig[4] += T[1] * GT[2] + T[4] * GT[5];
+        gsig[5] += T[2] * GT[2] + T[5] * GT[5];
+        const float* S = shp.sig;
+        float gT[6];
+        for (int r = 0; r < 2; ++r) {
+            const float* gr = GT + 3 * r;
+            gT[3 * r + 0] = 2.0f * (gr[0] * S[0] + gr[1] * S[1] + gr[2] * S[2]);
+            gT[3 * r + 1] = 2.0f * (gr[0] * S[1] + gr[1] * S[3] + gr[2] * S[4]);
+            gT[3 * r + 2] = 2.0f * (gr[0] * S[2] + gr[1] * S[4] + gr[2] * S[5]);
+        }
+        // T = J W: dJ = dT W^T (only the non-constant entries of J)
+        const float* W = cam.R;
+        const float gJ00 = gT[0] * W[0] + gT[1] * W[1] + gT[2] * W[2];
+        const float gJ02 = gT[0] * W[6] + gT[1] * W[7] + gT[2] * W[8];
+        const float gJ11 = gT[3] * W[3] + gT[4] * W[4] + gT[5] * W[5];
+        const float gJ12 = gT[3] * W[6] + gT[4] * W[7] + gT[5] * W[8];
+        const float z = p.xc[2], iz = 1.0f / z, iz2 = iz * iz;
+        float gxc[3];
+        float gz = gJ00 * (-cam.fx * iz2) + gJ02 * (cam.fx * p.u * iz2) + gJ11 * (-cam.fy * iz2) +
+                   gJ12 * (cam.fy * p.v * iz2);
+        const float gu = gJ02 * (-cam.fx * iz), gv = gJ12 * (-cam.fy * iz);
+        gxc[0] = gmx * cam.fx * iz;
+        gxc[1] = gmy * cam.fy * iz;
+        gz -= (gmx * cam.fx * p.xc[0] + gmy * cam.fy * p.xc[1]) * iz2;
+        if (!p.uc) {
+            gxc[0] += gu * iz;
+            gz -= gu * p.xc[0] * iz2;
+        }
+        if (!p.vc) {
+            gxc[1] += gv * iz;
+            gz -= gv * p.xc[1] * iz2;
+        }
+        gxc[2] = gz;
+        for (int e = 0; e < 3; ++e) gm[e] += W[e] * gxc[0] + W[3 + e] * gxc[1] + W[6 + e] * gxc[2];
+    }
+
+    // Sigma = M M^T, M = Rq diag(s): dM = 2 dSigma M (dSigma symmetric)
+    const float* R = shp.Rq;
+    float M[9];
+    for (int r = 0; r < 3; ++r)
+        for (int c = 0; c < 3; ++c) M[3 * r + c] = R[3 * r + c] * shp.s[c];
+    const float Gs[9] = {gsig[0], gsig[1], gsig[2], gsig[1], gsig[3], gsig[4],
+                         gsig[2], gsig[4], gsig[5]};
+    float gM[9];
+    for (int r = 0; r < 3; ++r)
+        for (int c = 0; c < 3; ++c)
+            gM[3 * r + c] = 2.0f * (Gs[3 * r] * M[c] + Gs[3 * r + 1] * M[3 + c] +
+                                    Gs[3 * r + 2] * M[6 + c]);
+    float gls[3], gR[9];
+    for (int c = 0; c < 3; ++c) {
+        const float gsc = gM[c] * R[c] + gM[3 + c] * R[3 + c] + gM[6 + c] * R[6 + c];
+        gls[c] = gsc * shp.s[c];
+        for (int r = 0; r < 3; ++r) gR[3 * r + c] = gM[3 * r + c] * shp.s[c];
+    }
+    // Rq(qn) -> qn
+    const float w = shp.qn[0], x = shp.qn[1], y = shp.qn[2], z = shp.qn[3];
+    float gq[4];
+    gq[0] = 2.0f * (-z * gR[1] + y * gR[2] + z * gR[3] - x * gR[5] - y * gR[6] + x * gR[7]);
+    gq[1] = 2.0f * (y * gR[1] + z * gR[2] + y * gR[3] - w * gR[5] + z * gR[6] + w * gR[7]) -
+            4.0f * x * (gR[4] + gR[8]);
+    gq[2] = 2.0f * (x * gR[1] + w * gR[2] + x * gR[3] + z * gR[5] - w * gR[6] + z * gR[7]) -
+            4.0f * y * (gR[0] + gR[8]);
+    gq[3] = 2.0f * (-w * gR[1] + x * gR[2] + w * gR[3] + y * gR[5] + x * gR[6] + y * gR[7]) -
+            4.0f * z * (gR[0] + gR[4]);
+    // qn = q / |q|
+    const float dq = gq[0] * w + gq[1] * x + gq[2] * y + gq[3] * z;
+    const float iq = 1.0f / shp.qnorm;
+    float4 gq4 = make_float4((gq[0] - w * dq) * iq, (gq[1] - x * dq) * iq, (gq[2] - y * dq) * iq,
+                             (gq[3] - z * dq) * iq);
+    const float glog = gop * opacity * (1.0f - opacity);
+
+    if (accumulate) {
+        for (int e = 0; e < 3; ++e) {
+            g_means[3 * g + e] += gm[e];
+            g_ls[3 * g + e] += gls[e];
+        }
+        float4 o = reinterpret_cast<float4*>(g_quats)[g];
+        o.x += gq4.x; o.y += gq4.y; o.z += gq4.z; o.w += gq4.w;
+        reinterpret_cast<float4*>(g_quats)[g] = o;
+        g_logit[g] += glog;
+#pragma unroll
+        for (int k = 0; k < K; ++k)
+            for (int ch = 0; ch < 3; ++ch) g_sh[((size_t)k * n + g) * 3 + ch] += gshc[k][ch];
+    } else {
+        for (int e = 0; e < 3; ++e) {
+            g_means[3 * g + e] = gm[e];
+            g_ls[3 * g + e] = gls[e];
+        }
+        reinterpret_cast<float4*>(g_quats)[g] = gq4;
+        g_logit[g] = glog;
+#pragma unroll
+        for (int k = 0; k < K; ++k)
+            for (int ch = 0; ch < 3; ++ch) g_sh[((size_t)k * n + g) * 3 + ch] = gshc[k][ch];
+    }
+}
+
+}  // namespace
+
+gs_status launch_project(const Plan* p, const gs_map* map, const gs_view* views_dev, void* ws,
+                         cudaStream_t st) {
+    if (reinterpret_cast<uintptr_t>(map->quats) % 16) return GS_ERR_INVALID;
+    const int n = map->n;
+    DevCounters* ctr = buf<DevCounters>(p, ws, GS_BUF_COUNTERS);
+    if (cudaMemsetAsync(ctr, 0, sizeof(DevCounters), st) != cudaSuccess) return GS_ERR_CUDA;
+    dim3 grid((n + kProjThreads - 1) / kProjThreads,
+              (p->vt.n_views + kViewsPerThread - 1) / kViewsPerThread);
+    auto* kern = map->sh_degree == 0   ? k_project<0>
+                 : map->sh_degree == 1 ? k_project<1>
+                 : map->sh_degree == 2 ? k_project<2>
+                                       : k_project<3>;
+    kern<<<grid, kProjThreads, 0, st>>>(
+        map->means, map->log_scales, map->quats, map->opacity_logits, map->sh, n, views_dev,
+        p->vt, p->cfg.near_z, buf<float4>(p, ws, GS_BUF_PROJ), buf<uint16_t>(p, ws, GS_BUF_RECT),
+        buf<uint32_t>(p, ws, GS_BUF_TOUCHED), buf<int32_t>(p, ws, GS_BUF_RADIUS),
+        buf<uint32_t>(p, ws, B_DKEY_A), buf<uint32_t>(p, ws, GS_BUF_DEPTH_ORDER), ctr);
+    return launch_status();
+}
+
+gs_status launch_project_bwd(const Plan* p, const gs_map* map, const gs_view* views_dev,
+                             void* ws, const gs_map_grad* grads, int accumulate,
+                             cudaStream_t st) {
+    if (reinterpret_cast<uintptr_t>(grads->quats) % 16) return GS_ERR_INVALID;
+    const int n = map->n;
+    const size_t smem = sizeof(Cam) * p->vt.n_views;
+    auto* kern = map->sh_degree == 0   ? k_project_bwd<0>
+                 : map->sh_degree == 1 ? k_project_bwd<1>
+                 : map->sh_degree == 2 ? k_project_bwd<2>
+                                       : k_project_bwd<3>;
+    kern<<<(n + kProjThreads - 1) / kProjThreads, kProjThreads, smem, st>>>(
+        map->means, map->log_scales, map->quats, map->opacity_logits, map->sh, n, views_dev,
+        p->vt, p->cfg.near_z, buf<uint32_t>(p, ws, GS_BUF_TOUCHED),
+        buf<float>(p, ws, GS_BUF_GRAD2D), grads->means, grads->log_scales, grads->quats,
+        grads->opacity_logits, grads->sh, accumulate);
+    return launch_status();
+}
+
+}  // namespace gs

@@ -1,0 +1,376 @@
+"""Mapping-step driver over the C-ABI: map storage, rasteriser, autograd, graphs.
+
+PyTorch provides device memory, streams and CUDA-graph capture here; every
+arithmetic step of the mapping iteration (paper Sec. III-B: render with the
+3DGS tile rasteriser, Eq. 2 loss, gradient descent with the default 3DGS
+Adam of Sec. IV-A) runs in libgs_gb300.so.
+
+* ``GaussianMap`` keeps every parameter group in ONE contiguous float32
+  buffer (means | log_scales | quats | opacity_logits | sh[K][N][3]), each
+  group starting on a 256-byte boundary, with gradients and Adam moments in
+  buffers of the same layout -- so the fused Adam kernel is one pass and a
+  later cross-GPU all-reduce of the gradient would be one call.
+* ``Rasterizer`` owns a plan and its workspace for one batch of views.
+* ``GSRender`` is the torch.autograd.Function over the rasteriser, with an
+  optional recompute mode that keeps only (final_T, last_idx) between the
+  forward and the backward.
+* ``MappingStep`` is one whole iteration, optionally captured as a CUDA graph.
+"""
+from __future__ import annotations
+
+import numpy as np
+import torch
+
+from . import binding as B
+
+ALIGN_FLOATS = 64  # 256-byte group alignment
+GROUPS = ("means", "log_scales", "quats", "opacity_logits", "sh_dc", "sh_rest")
+
+# Default learning rates of 3DGS (the paper keeps the default optimiser
+# configuration, Sec. IV-A); the position rate is scaled by the scene extent.
+DEFAULT_LR = dict(means=1.6e-4, log_scales=5e-3, quats=1e-3, opacity_logits=0.05,
+                  sh_dc=2.5e-3, sh_rest=2.5e-3 / 20.0)
+
+
+def _align(x):
+    return (x + ALIGN_FLOATS - 1) // ALIGN_FLOATS * ALIGN_FLOATS
+
+
+def param_layout(n: int, degree: int):
+    """Offsets (floats) of each group in the packed buffer, and the total."""
+    K = (degree + 1) ** 2
+    off = {}
+    o = 0
+    off["means"] = o
+    o = _align(o + 3 * n)
+    off["log_scales"] = o
+    o = _align(o + 3 * n)
+    off["quats"] = o
+    o = _align(o + 4 * n)
+    off["opacity_logits"] = o
+    o = _align(o + n)
+    off["sh"] = o
+    off["sh_dc"] = o
+    off["sh_rest"] = o + 3 * n
+    o = _align(o + 3 * K * n)
+    return off, o
+
+
+class GaussianMap:
+    """Gaussian parameters, gradients and Adam state on one GPU."""
+
+    def __init__(self, params, device="cuda", capacity=None):
+        self.n = int(params["means"].shape[0])
+        self.degree = int(params["sh_degree"])
+        self.K = (self.degree + 1) ** 2
+        self.capacity = int(capacity or self.n)
+        self.device = torch.device(device)
+        self.off, self.total = param_layout(self.capacity, self.degree)
+        self.data = torch.zeros(self.total, dtype=torch.float32, device=self.device)
+        self.grad = torch.zeros_like(self.data)
+        self.m = torch.zeros_like(self.data)
+        self.v = torch.zeros_like(self.data)
+        self.step = torch.zeros(1, dtype=torch.int32, device=self.device)
+        self.load(params)
+
+    # views into the packed buffers ------------------------------------------
+    def _views(self, buf):
+        n, c, K = self.n, self.capacity, self.K
+        o = self.off
+        return dict(
+            means=buf[o["means"]:o["means"] + 3 * n].view(n, 3),
+            log_scales=buf[o["log_scales"]:o["log_scales"] + 3 * n].view(n, 3),
+            quats=buf[o["quats"]:o["quats"] + 4 * n].view(n, 4),
+            opacity_logits=buf[o["opacity_logits"]:o["opacity_logits"] + n],
+            sh=buf[o["sh"]:o["sh"] + 3 * K * c].view(K, c, 3)[:, :n],
+        )
+
+    def params(self):
+        return self._views(self.data)
+
+    def grads(self):
+        return self._views(self.grad)
+
+    def load(self, params):
+        assert params["means"].shape[0] == self.n
+        P = self.params()
+        for k in ("means", "log_scales", "quats", "opacity_logits"):
+            P[k].copy_(torch.as_tensor(np.asarray(params[k], np.float32)))
+        sh = torch.as_tensor(np.asarray(params["sh"], np.float32))
+        self.data[self.off["sh"]:self.off["sh"] + 3 * self.K * self.capacity].view(
+            self.K, self.capacity, 3)[:, :self.n].copy_(sh)
+
+    def to_numpy(self):
+        P = self.params()
+        out = {k: P[k].detach().cpu().numpy().copy() for k in P}
+        out["sh_degree"] = self.degree
+        return out
+
+    def gs_map(self) -> B.gs_map:
+        P = self.params()
+        if self.capacity != self.n:
+            raise ValueError("SH planes are strided by capacity; use capacity == n for the C-ABI")
+        return B.gs_map(P["means"].data_ptr(), P["log_scales"].data_ptr(), P["quats"].data_ptr(),
+                        P["opacity_logits"].data_ptr(), P["sh"].data_ptr(), self.n, self.degree)
+
+    def gs_map_grad(self) -> B.gs_map_grad:
+        G = self.grads()
+        return B.gs_map_grad(G["means"].data_ptr(), G["log_scales"].data_ptr(),
+                             G["quats"].data_ptr(), G["opacity_logits"].data_ptr(),
+                             G["sh"].data_ptr())
+
+    def adam_groups(self, lr=None, extent=1.0):
+        """(offsets, rates) of the six Adam groups over the packed buffer."""
+        lr = dict(DEFAULT_LR, **(lr or {}))
+        lr = dict(lr, means=lr["means"] * extent)
+        starts = [self.off[g] for g in GROUPS]
+        offsets = starts + [self.total]
+        offsets[0] = 0
+        return offsets, [lr[g] for g in GROUPS]
+
+    def adam_step(self, lr=None, extent=1.0, beta1=0.9, beta2=0.999, eps=1e-15, stream=None):
+        offs, rates = self.adam_groups(lr, extent)
+        B.gs_adam_step(self.data, self.grad, self.m, self.v, offs, rates, beta1, beta2, eps,
+                       self.step, stream)
+
+
+def make_view(v) -> B.gs_view:
+    R = np.asarray(v["R"], np.float32).reshape(9)
+    t = np.asarray(v["t"], np.float32).reshape(3)
+    return B.gs_view((B.c_float * 9)(*R.tolist()), (B.c_float * 3)(*t.tolist()), float(v["fx"]),
+                     float(v["fy"]), float(v["cx"]), float(v["cy"]), int(v["width"]),
+                     int(v["height"]), int(v.get("channels", 3)), 0)
+
+
+def views_to_device(views, device="cuda"):
+    arr = (B.gs_view * len(views))(*[make_view(v) for v in views])
+    raw = np.frombuffer(bytes(arr), dtype=np.uint8).copy()
+    return arr, torch.from_numpy(raw).to(device)
+
+
+class Rasterizer:
+    """Plan + workspace + output buffers for one batch of views."""
+
+    def __init__(self, views, n_capacity, instance_capacity=None, tile=(16, 16), smem_batch=128,
+                 near_z=0.2, bg=(0.0, 0.0, 0.0), device="cuda"):
+        self.views = list(views)
+        self.device = torch.device(device)
+        self.cfg = B.gs_config(int(tile[0]), int(tile[1]), int(smem_batch), 0, float(near_z),
+                               (B.c_float * 3)(*[float(x) for x in bg]))
+        self.n_capacity = int(n_capacity)
+        if instance_capacity is None:
+            px = sum(v["width"] * v["height"] for v in self.views)
+            instance_capacity = max(1 << 20, 4 * px, 8 * n_capacity)
+        self.instance_capacity = int(instance_capacity)
+        self.host_views, self.views_dev = views_to_device(self.views, self.device)
+        self.plan = B.gs_plan_init(self.cfg, list(self.host_views), self.n_capacity,
+                                   self.instance_capacity)
+        self.ws = torch.empty(B.gs_plan_workspace_bytes(self.plan), dtype=torch.uint8,
+                              device=self.device)
+        self.ws.zero_()
+        tot = B.gs_plan_totals(self.plan)
+        self.total_values, self.total_pixels = tot["total_values"], tot["total_pixels"]
+        self.total_tiles = tot["total_tiles"]
+        self.view_info = [B.gs_plan_view(self.plan, v) for v in range(len(self.views))]
+        self.images = torch.zeros(self.total_values, dtype=torch.float32, device=self.device)
+        self.final_T = torch.zeros(self.total_pixels, dtype=torch.float32, device=self.device)
+        self.last_idx = torch.zeros(self.total_pixels, dtype=torch.int32, device=self.device)
+        self.dL = torch.zeros(self.total_values, dtype=torch.float32, device=self.device)
+        self.loss = torch.zeros(1, dtype=torch.float32, device=self.device)
+
+    # per-view slices --------------------------------------------------------
+    def view_slice(self, buf, v, per_pixel=False):
+        vw, info = self.views[v], self.view_info[v]
+        H, W, C = vw["height"], vw["width"], vw.get("channels", 3)
+        if per_pixel:
+            return buf[info["pixel_offset"]:info["pixel_offset"] + H * W].view(H, W)
+        return buf[info["value_offset"]:info["value_offset"] + C * H * W].view(C, H, W)
+
+    def pack(self, per_view_images):
+        """Concatenate [C][H][W] arrays of every view into one packed tensor."""
+        flat = [torch.as_tensor(np.asarray(x, np.float32)).reshape(-1) for x in per_view_images]
+        return torch.cat(flat).to(self.device)
+
+    def buffer(self, buf_id, dtype=torch.uint8):
+        off, nbytes = B.gs_plan_buffer(self.plan, buf_id)
+        return self.ws[off:off + nbytes].view(dtype)
+
+    def set_poses(self, views):
+        """Copy new poses (same sizes) to the device copy read by the kernels."""
+        arr, dev = views_to_device(views, self.device)
+        self.views_dev.copy_(dev)
+
+    # the C-ABI steps ---------------------------------------------------------
+    def project(self, gmap: B.gs_map, stream=None):
+        B.gs_project(self.plan, gmap, self.views_dev, self.ws, stream)
+
+    def bin_sort(self, n, stream=None):
+        B.gs_bin_sort(self.plan, n, self.ws, stream)
+
+    def render_fwd(self, images=None, final_T=None, last_idx=None, stream=None):
+        B.gs_render_fwd(self.plan, self.ws, self.images if images is None else images,
+                        self.final_T if final_T is None else final_T,
+                        self.last_idx if last_idx is None else last_idx, stream)
+
+    def forward(self, gmap: B.gs_map, stream=None):
+        self.project(gmap, stream)
+        self.bin_sort(gmap.n, stream)
+        self.render_fwd(stream=stream)
+
+    def loss_l1_ssim(self, targets, lam, view_weight=None, images=None, stream=None):
+        w = 1.0 / len(self.views) if view_weight is None else view_weight
+        B.gs_loss_l1_ssim(self.plan, self.images if images is None else images, targets, lam, w,
+                          self.loss, self.dL, self.ws, stream)
+
+    def render_bwd(self, gmap: B.gs_map, grads: B.gs_map_grad, dL=None, final_T=None,
+                   last_idx=None, accumulate=False, stream=None):
+        B.gs_render_bwd(self.plan, gmap, self.views_dev, self.ws,
+                        self.final_T if final_T is None else final_T,
+                        self.last_idx if last_idx is None else last_idx,
+                        self.dL if dL is None else dL, grads, accumulate, stream)
+
+    def counters(self, stream=None) -> B.gs_counters:
+        return B.gs_read_counters(self.plan, self.ws, stream)
+
+
+def fit_instance_capacity(views, gmap: GaussianMap, headroom=1.25, **kw):
+    """A rasteriser whose instance capacity fits this map with headroom (one
+    synchronising probe at set-up, none afterwards)."""
+    probe = Rasterizer(views, gmap.capacity, **kw)
+    probe.project(gmap.gs_map())
+    probe.bin_sort(gmap.n)
+    raw = probe.counters().n_instances_raw
+    if raw > probe.instance_capacity:
+        kw = dict(kw)
+        probe = Rasterizer(views, gmap.capacity, instance_capacity=int(raw * headroom) + 1024, **kw)
+        return probe
+    cap = int(raw * headroom) + 1024
+    if cap < probe.instance_capacity:
+        return Rasterizer(views, gmap.capacity, instance_capacity=cap, **kw)
+    return probe
+
+
+def _map_from_tensors(means, log_scales, quats, opacity_logits, sh, degree):
+    for t in (means, log_scales, quats, opacity_logits, sh):
+        if not (t.is_cuda and t.dtype == torch.float32 and t.is_contiguous()):
+            raise ValueError("GSRender inputs must be contiguous float32 CUDA tensors")
+    return B.gs_map(means.data_ptr(), log_scales.data_ptr(), quats.data_ptr(),
+                    opacity_logits.data_ptr(), sh.data_ptr(), means.shape[0], degree)
+
+
+class GSRender(torch.autograd.Function):
+    """images = GSRender.apply(means, log_scales, quats, opacity_logits, sh, rast, recompute)
+
+    sh is [K][N][3].  The backward calls gs_render_bwd.  With recompute=True
+    only final_T and last_idx are kept from the forward; the projection and
+    the (deterministic) binning are re-run in the backward.
+    """
+
+    @staticmethod
+    def forward(ctx, means, log_scales, quats, opacity_logits, sh, rast: Rasterizer,
+                recompute=False):
+        degree = int(round(sh.shape[0] ** 0.5)) - 1
+        gmap = _map_from_tensors(means, log_scales, quats, opacity_logits, sh, degree)
+        rast.forward(gmap)
+        images = rast.images.clone()
+        final_T = rast.final_T.clone()
+        last_idx = rast.last_idx.clone()
+        ctx.rast, ctx.recompute, ctx.degree = rast, bool(recompute), degree
+        ctx.save_for_backward(means, log_scales, quats, opacity_logits, sh, final_T, last_idx)
+        return images
+
+    @staticmethod
+    def backward(ctx, dimages):
+        means, log_scales, quats, opacity_logits, sh, final_T, last_idx = ctx.saved_tensors
+        rast = ctx.rast
+        gmap = _map_from_tensors(means, log_scales, quats, opacity_logits, sh, ctx.degree)
+        if ctx.recompute:
+            rast.project(gmap)
+            rast.bin_sort(gmap.n)
+        g = [torch.zeros_like(t) for t in (means, log_scales, quats, opacity_logits, sh)]
+        grads = B.gs_map_grad(*[t.data_ptr() for t in g])
+        rast.render_bwd(gmap, grads, dL=dimages.contiguous(), final_T=final_T, last_idx=last_idx)
+        return (*g, None, None)
+
+
+class MappingStep:
+    """One mapping iteration (project, bin, render, loss, backward, Adam) on a
+    batch of views, optionally captured as one CUDA graph."""
+
+    def __init__(self, gmap: GaussianMap, rast: Rasterizer, targets: torch.Tensor, lam: float,
+                 lr=None, extent=1.0):
+        self.gmap, self.rast, self.targets, self.lam = gmap, rast, targets, float(lam)
+        self.lr, self.extent = lr, extent
+        self.graph = None
+        self._m = gmap.gs_map()
+        self._g = gmap.gs_map_grad()
+
+    def run(self, stream=None):
+        r = self.rast
+        r.project(self._m, stream)
+        r.bin_sort(self.gmap.n, stream)
+        r.render_fwd(stream=stream)
+        r.loss_l1_ssim(self.targets, self.lam, stream=stream)
+        r.render_bwd(self._m, self._g, accumulate=False, stream=stream)
+        self.gmap.adam_step(self.lr, self.extent, stream=stream)
+
+    def capture(self, warmup=2):
+        s = torch.cuda.Stream()
+        s.wait_stream(torch.cuda.current_stream())
+        with torch.cuda.stream(s):
+            for _ in range(warmup):
+                self.run()
+        torch.cuda.current_stream().wait_stream(s)
+        self.graph = torch.cuda.CUDAGraph()
+        with torch.cuda.graph(self.graph):
+            self.run()
+        return self.graph
+
+    def __call__(self):
+        if self.graph is not None:
+            self.graph.replay()
+        else:
+            self.run()
+
+
+class PerViewLoop:
+    """The same iteration as MappingStep over V views, but one plan per view:
+    V x (project, bin, render, loss, backward), gradients accumulated, one
+    Adam step -- the baseline the batched form is compared with."""
+
+    def __init__(self, gmap: GaussianMap, views, targets_per_view, lam, lr=None, extent=1.0,
+                 **rast_kw):
+        self.gmap, self.lam, self.lr, self.extent = gmap, float(lam), lr, extent
+        self.rasts = [fit_instance_capacity([v], gmap, **rast_kw) for v in views]
+        self.targets = [r.pack([t]) for r, t in zip(self.rasts, targets_per_view)]
+        self._m = gmap.gs_map()
+        self._g = gmap.gs_map_grad()
+        self.graph = None
+
+    def run(self, stream=None):
+        V = len(self.rasts)
+        for i, (r, t) in enumerate(zip(self.rasts, self.targets)):
+            r.project(self._m, stream)
+            r.bin_sort(self.gmap.n, stream)
+            r.render_fwd(stream=stream)
+            r.loss_l1_ssim(t, self.lam, view_weight=1.0 / V, stream=stream)
+            r.render_bwd(self._m, self._g, accumulate=i > 0, stream=stream)
+        self.gmap.adam_step(self.lr, self.extent, stream=stream)
+
+    def capture(self, warmup=2):
+        s = torch.cuda.Stream()
+        s.wait_stream(torch.cuda.current_stream())
+        with torch.cuda.stream(s):
+            for _ in range(warmup):
+                self.run()
+        torch.cuda.current_stream().wait_stream(s)
+        self.graph = torch.cuda.CUDAGraph()
+        with torch.cuda.graph(self.graph):
+            self.run()
+        return self.graph
+
+    def __call__(self):
+        if self.graph is not None:
+            self.graph.replay()
+        else:
+            self.run()

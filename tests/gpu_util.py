@@ -1,0 +1,76 @@
+"""Helpers shared by the GPU parity tests: read workspace buffers back, build
+the oracle-side guard masks, compare tile lists."""
+import numpy as np
+import torch
+
+import oracle
+from paper_2409_13055_gb300 import binding as B
+from paper_2409_13055_gb300 import mapping
+
+FWD_GUARDS = oracle.GUARD_RECT | oracle.GUARD_NEAR | oracle.GUARD_DET | oracle.GUARD_DEPTH
+
+
+def gpu_projection(rast: mapping.Rasterizer, n: int, v: int = 0):
+    """Per-Gaussian projection outputs of view v from the workspace."""
+    V = len(rast.views)
+    proj = rast.buffer(B.GS_BUF_PROJ, torch.float32)[: V * n * 12].view(V, n, 12)[v]
+    proj = proj.cpu().numpy().astype(np.float64)
+    rect = rast.buffer(B.GS_BUF_RECT, torch.int16)[: V * n * 4].view(V, n, 4)[v]
+    rect = rect.cpu().numpy().astype(np.int64) & 0xFFFF
+    touched = rast.buffer(B.GS_BUF_TOUCHED, torch.int32)[: V * n].view(V, n)[v].cpu().numpy()
+    radius = rast.buffer(B.GS_BUF_RADIUS, torch.int32)[: V * n].view(V, n)[v].cpu().numpy()
+    depth32 = rast.buffer(B.GS_BUF_PROJ, torch.float32)[: V * n * 12].view(V, n, 12)[v, :, 11]
+    return dict(mean2d=proj[:, 0:2] + proj[:, 2:4], conic=proj[:, 4:7], opacity=proj[:, 7],
+                rgb=proj[:, 8:11], depth32=depth32.cpu().numpy(), rect=rect, touched=touched,
+                radius=radius)
+
+
+def gpu_tile_lists(rast: mapping.Rasterizer):
+    """(ranges[T,2], keys[I], values[I]) of the last gs_bin_sort."""
+    c = rast.counters()
+    I = int(c.n_instances)
+    keys = rast.buffer(B.GS_BUF_TILE_KEYS, torch.int32)[:I].cpu().numpy()
+    vals = rast.buffer(B.GS_BUF_TILE_VALUES, torch.int32)[:I].cpu().numpy()
+    ranges = rast.buffer(B.GS_BUF_RANGES, torch.int32)[: 2 * rast.total_tiles].view(-1, 2)
+    return ranges.cpu().numpy(), keys, vals, c
+
+
+def guard_pixel_mask(view, proj, rout, tile=(16, 16)):
+    """Pixels whose value may legitimately differ between an FP32 evaluation and
+    the FP64 oracle: a per-pixel decision inside its guard band, or a pixel of a
+    tile next to the rect of a Gaussian with a guarded rect / depth / cull."""
+    H, W = view["height"], view["width"]
+    tw, th = tile
+    mask = (rout["guard_px"] & (oracle.GPX_ALPHA | oracle.GPX_TRANS | oracle.GPX_POWER)) != 0
+    flagged = np.nonzero(proj["guard"] & FWD_GUARDS)[0]
+    whole_view = False
+    for g in flagged:
+        if proj["tiles_touched"][g] == 0:
+            whole_view = True  # culled on one side only: cannot localise it
+            continue
+        x0, y0, x1, y1 = proj["rect"][g]
+        mask[max(0, (y0 - 1) * th):min(H, (y1 + 1) * th), max(0, (x0 - 1) * tw):min(W, (x1 + 1) * tw)] = True
+    if whole_view:
+        mask[:] = True
+    return mask
+
+
+def grad_pixel_mask(rout):
+    """Pixels whose gradient contributions cross a kink (alpha clamp)."""
+    return (rout["guard_px"] & oracle.GPX_KINK) != 0
+
+
+def rel_l2(a, b):
+    a = np.asarray(a, np.float64).ravel()
+    b = np.asarray(b, np.float64).ravel()
+    nb = np.linalg.norm(b)
+    return float(np.linalg.norm(a - b) / nb) if nb > 0 else float(np.linalg.norm(a))
+
+
+def tile_lists_from_gpu(ranges, vals, tile_range, n):
+    """{tile: [gaussian indices]} for tiles in tile_range (view-local values)."""
+    out = {}
+    for t in tile_range:
+        b, e = ranges[t]
+        out[t] = (vals[b:e] % n).tolist() if e > b else []
+    return out

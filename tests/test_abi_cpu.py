@@ -1,0 +1,112 @@
+"""Host-side checks of the C-ABI that need no GPU: the library builds for
+sm_103a, loads, exports every function include/gs.h declares, and its
+host-only entry points validate their arguments and size workspaces."""
+import ctypes
+import shutil
+
+import pytest
+
+from paper_2409_13055_gb300 import binding as B
+from paper_2409_13055_gb300 import build as gsbuild
+from paper_2409_13055_gb300 import mapping, scenes
+
+pytestmark = pytest.mark.skipif(shutil.which("nvcc") is None and not __import__("os").path.exists(
+    "/usr/local/cuda/bin/nvcc"), reason="nvcc is needed to build the library")
+
+
+@pytest.fixture(scope="module")
+def lib():
+    gsbuild.build()
+    return B.lib()
+
+
+def test_exports_every_declared_function(lib):
+    names = B.header_functions()
+    assert len(names) >= 12
+    for n in names:
+        assert hasattr(lib, n), n
+    assert set(names) == set(B._SIGNATURES), set(names) ^ set(B._SIGNATURES)
+
+
+def test_struct_sizes_match_header():
+    assert ctypes.sizeof(B.gs_view) == 80
+    assert ctypes.sizeof(B.gs_config) == 32
+    assert ctypes.sizeof(B.gs_counters) == 32
+    assert ctypes.sizeof(B.gs_plan) == 8 * B.GS_PLAN_WORDS
+
+
+def _cfg(tw=16, th=16, batch=128, near=0.2):
+    return B.gs_config(tw, th, batch, 0, near, (B.c_float * 3)(0, 0, 0))
+
+
+def _views(*sizes):
+    return [mapping.make_view(scenes.camera(w, h, 500.0, 500.0, channels=c)) for (w, h, c) in sizes]
+
+
+def test_plan_layout_and_offsets(lib):
+    vs = _views((640, 480, 3), (752, 480, 1), (1200, 680, 3))
+    plan = B.gs_plan_init(_cfg(), vs, 1000, 100000)
+    tot = B.gs_plan_totals(plan)
+    assert tot["total_values"] == 640 * 480 * 3 + 752 * 480 + 1200 * 680 * 3
+    assert tot["total_pixels"] == 640 * 480 + 752 * 480 + 1200 * 680
+    assert tot["total_tiles"] == 40 * 30 + 47 * 30 + 75 * 43
+    v2 = B.gs_plan_view(plan, 2)
+    assert v2["value_offset"] == 640 * 480 * 3 + 752 * 480
+    assert v2["pixel_offset"] == 640 * 480 + 752 * 480
+    assert v2["tile_offset"] == 40 * 30 + 47 * 30
+    assert (v2["tiles_x"], v2["tiles_y"]) == (75, 43)
+    ws = B.gs_plan_workspace_bytes(plan)
+    seen = []
+    for b in range(10):
+        off, nbytes = B.gs_plan_buffer(plan, b)
+        assert off % 256 == 0 and off + nbytes <= ws
+        seen.append((off, nbytes))
+
+
+@pytest.mark.parametrize("cfg,views,ncap,icap,err", [
+    (dict(tw=12), [(64, 64, 3)], 10, 100, B.GS_ERR_UNSUPPORTED),
+    (dict(tw=64, th=8), [(64, 64, 3)], 10, 100, B.GS_ERR_UNSUPPORTED),
+    (dict(batch=48), [(64, 64, 3)], 10, 100, B.GS_ERR_UNSUPPORTED),
+    (dict(near=0.0), [(64, 64, 3)], 10, 100, B.GS_ERR_INVALID),
+    (dict(), [(64, 64, 2)], 10, 100, B.GS_ERR_INVALID),
+    (dict(), [(0, 64, 3)], 10, 100, B.GS_ERR_INVALID),
+    (dict(), [(64, 64, 3)], 0, 100, B.GS_ERR_INVALID),
+    (dict(), [(64, 64, 3)], 10, 0, B.GS_ERR_INVALID),
+])
+def test_plan_init_rejects(lib, cfg, views, ncap, icap, err):
+    plan = B.gs_plan()
+    arr = (B.gs_view * len(views))(*_views(*views))
+    st = lib.gs_plan_init(ctypes.byref(plan), ctypes.byref(_cfg(**cfg)), len(views), arr, ncap,
+                          icap)
+    assert st == err
+
+
+def test_calls_reject_bad_arguments_without_launching(lib):
+    plan = B.gs_plan_init(_cfg(), _views((64, 48, 3)), 10, 1000)
+    nullmap = B.gs_map(None, None, None, None, None, 10, 0)
+    assert lib.gs_project(ctypes.byref(plan), ctypes.byref(nullmap), None, None, None) == \
+        B.GS_ERR_INVALID
+    assert lib.gs_bin_sort(ctypes.byref(plan), 0, ctypes.c_void_p(256), None) == B.GS_ERR_INVALID
+    bad = B.gs_plan()  # never initialised
+    assert lib.gs_render_fwd(ctypes.byref(bad), ctypes.c_void_p(256), ctypes.c_void_p(256),
+                             ctypes.c_void_p(256), ctypes.c_void_p(256), None) == B.GS_ERR_INVALID
+    assert lib.gs_loss_l1_ssim(ctypes.byref(plan), ctypes.c_void_p(256), ctypes.c_void_p(256),
+                               1.5, 1.0, ctypes.c_void_p(256), ctypes.c_void_p(256),
+                               ctypes.c_void_p(256), None) == B.GS_ERR_INVALID
+    offs = (B.c_int64 * 2)(0, 5)
+    lrs = (B.c_float * 1)(0.1)
+    p = ctypes.c_void_p(256)
+    assert lib.gs_adam_step(p, p, p, p, 6, 1, offs, lrs, 0.9, 0.999, 1e-15, p, None) == \
+        B.GS_ERR_INVALID  # offsets do not end at n
+    assert lib.gs_adam_step(p, p, p, p, 5, 1, offs, lrs, 1.0, 0.999, 1e-15, p, None) == \
+        B.GS_ERR_INVALID  # beta1 = 1
+    assert B.gs_status_string(B.GS_ERR_CAPACITY).startswith("GS_ERR_CAPACITY")
+
+
+def test_param_layout_alignment():
+    for n, deg in [(1, 0), (3, 3), (1000, 3), (777, 1)]:
+        off, total = mapping.param_layout(n, deg)
+        for k in ("means", "log_scales", "quats", "opacity_logits", "sh"):
+            assert off[k] % 64 == 0
+        assert off["sh_rest"] == off["sh"] + 3 * n
+        assert total >= off["sh"] + 3 * (deg + 1) ** 2 * n and total % 64 == 0
