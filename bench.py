@@ -153,10 +153,18 @@ def oracle_iteration_seconds(p, view, target, lam):
     return time.perf_counter() - t0
 
 
-def make_workload(seed_target=True):
+WORKLOADS = {
+    # name: (n Gaussians, seed offset, width, height, focal, sh degree)
+    "room1M_1200x680": (1_000_000, 3, 1200, 680, 600.0, 3),
+    "room200k_640x480": (200_000, 2, 640, 480, 525.0, 3),
+}
+
+
+def make_workload(name=WORKLOAD):
     from paper_2409_13055_gb300 import scenes
-    p = scenes.room_scene(1_000_000, seed=scenes.SEED_BASE + 3)
-    view = scenes.camera(1200, 680, 600.0, 600.0)
+    n, so, w, h, f, deg = WORKLOADS[name]
+    p = scenes.room_scene(n, seed=scenes.SEED_BASE + so, sh_degree=deg)
+    view = scenes.camera(w, h, f, f)
     return p, view
 
 
@@ -164,7 +172,7 @@ def run_reference(args, ws, rank):
     if rank != 0:
         return
     from paper_2409_13055_gb300 import scenes
-    p, view = make_workload()
+    p, view = make_workload(args.workload)
     target = scenes.random_target(view, scenes.SEED_BASE + 13)
     times = []
     for _ in range(args.warmup if args.reference_warmup else 0):
@@ -176,8 +184,9 @@ def run_reference(args, ws, rank):
     out = dict(metric=METRIC, value=v, unit="iters/s", impl="reference", n_gpus=0,
                steps=args.steps, warmup=0, ms_per_step=1e3 * t, higher_is_better=True,
                scaling="weak", vs_baseline=None, dtype="f64", data="synthetic",
-               config=dict(workload=WORKLOAD, gaussians=1_000_000, width=1200, height=680,
-                           sh_degree=3, views=1, lam=0.2),
+               config=dict(workload=args.workload, gaussians=int(p["means"].shape[0]),
+                           width=view["width"], height=view["height"], sh_degree=3, views=1,
+                           lam=0.2),
                cpu_baseline=dict(value=v, unit="iters/s", cores=1, kind="oracle",
                                  sample="one full FP64 mapping iteration of the workload per step "
                                         "(target: seeded noise image)"),
@@ -206,7 +215,7 @@ def run_gpu(args, ws, rank, local):
     gsbuild.build()
     peaks = load_peaks()
 
-    p, view = make_workload()
+    p, view = make_workload(args.workload)
     lam = 0.2
     # target: render of a perturbed copy of the map (set-up, untimed)
     pert = scenes.perturbed(p, scenes.SEED_BASE + 23)
@@ -334,7 +343,8 @@ def run_gpu(args, ws, rank, local):
     out = dict(metric=METRIC, value=value, unit="iters/s", n_gpus=ws, steps=K, warmup=args.warmup,
                ms_per_step=ms_step, higher_is_better=True, scaling="weak", vs_baseline=None,
                dtype="f32", data="synthetic",
-               config=dict(workload=WORKLOAD, gaussians=n, width=1200, height=680, sh_degree=3,
+               config=dict(workload=args.workload, gaussians=n, width=view["width"],
+                           height=view["height"], sh_degree=3,
                            views=1, lam=0.2, tile=f"{args.tile_w}x{args.tile_h}",
                            smem_batch=args.batch, cuda_graph="one graph per stage",
                            l2="working set ~1.2 GB > 129 MB L2, no flush",
@@ -363,6 +373,9 @@ def main():
     ap.add_argument("--steps", type=int, default=200)
     ap.add_argument("--warmup", type=int, default=5)
     ap.add_argument("--impl", default="gb300", choices=["gb300", "reference"])
+    ap.add_argument("--workload", default=WORKLOAD, choices=sorted(WORKLOADS),
+                    help="room1M_1200x680 is the headline; room200k_640x480 a smaller "
+                         "case of the same shape for profiling")
     ap.add_argument("--tile-w", type=int, default=16)
     ap.add_argument("--tile-h", type=int, default=16)
     ap.add_argument("--batch", type=int, default=128)

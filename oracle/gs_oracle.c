@@ -357,7 +357,8 @@ static int project_one(int i, int n, int degree, const double *means, const doub
  * Outputs per Gaussian: mean2d, depth (camera z), cov2d (a,b,c dilated),
  * conic (inverse of cov2d), opacity, rgb, colour-clamp mask, radius
  * r = ceil(3 sqrt(lambda_max)), tile rect [x0,y0,x1,y1) and tiles_touched.
- * A culled Gaussian has tiles_touched = 0, radius = 0 and rect 0.
+ * A culled Gaussian has tiles_touched = 0 and rect 0; one culled only
+ * because its rect is empty keeps its other outputs.
  * Returns the number of visible Gaussians.
  */
 int oracle_project(int n, int degree, const double *means, const double *log_scales,
@@ -402,17 +403,20 @@ int oracle_project(int n, int degree, const double *means, const double *log_sca
                 rc[k] = f < 0.0 ? 0 : (f > lim[k] ? lim[k] : (int)f);
             }
             int area = (rc[2] - rc[0]) * (rc[3] - rc[1]);
+            /* Screen-space quantities are reported for every Gaussian that
+             * survives the near-plane and determinant tests, so that callers
+             * can locate one whose rect came out empty. */
+            mean2d[2 * i] = P.mean2d[0];
+            mean2d[2 * i + 1] = P.mean2d[1];
+            for (int k = 0; k < 3; k++) {
+                cov2d[3 * i + k] = P.cov[k];
+                conic[3 * i + k] = P.conic[k];
+                rgb[3 * i + k] = P.rgb[k];
+                clamped[3 * i + k] = P.clamped[k];
+            }
+            opacity[i] = P.opacity;
+            radius[i] = r;
             if (area > 0) {
-                mean2d[2 * i] = P.mean2d[0];
-                mean2d[2 * i + 1] = P.mean2d[1];
-                for (int k = 0; k < 3; k++) {
-                    cov2d[3 * i + k] = P.cov[k];
-                    conic[3 * i + k] = P.conic[k];
-                    rgb[3 * i + k] = P.rgb[k];
-                    clamped[3 * i + k] = P.clamped[k];
-                }
-                opacity[i] = P.opacity;
-                radius[i] = r;
                 for (int k = 0; k < 4; k++) rect[4 * i + k] = rc[k];
                 tiles_touched[i] = area;
                 nvis++;

@@ -37,21 +37,30 @@ def gpu_tile_lists(rast: mapping.Rasterizer):
 
 def guard_pixel_mask(view, proj, rout, tile=(16, 16)):
     """Pixels whose value may legitimately differ between an FP32 evaluation and
-    the FP64 oracle: a per-pixel decision inside its guard band, or a pixel of a
-    tile next to the rect of a Gaussian with a guarded rect / depth / cull."""
+    the FP64 oracle: a per-pixel decision inside its guard band, or a pixel
+    that a Gaussian with a guarded rect / depth key / cull decision reaches with
+    alpha >= 1/255 (within radius + one tile of its mean, from the oracle's own
+    mean and conic)."""
     H, W = view["height"], view["width"]
     tw, th = tile
     mask = (rout["guard_px"] & (oracle.GPX_ALPHA | oracle.GPX_TRANS | oracle.GPX_POWER)) != 0
     flagged = np.nonzero(proj["guard"] & FWD_GUARDS)[0]
-    whole_view = False
     for g in flagged:
-        if proj["tiles_touched"][g] == 0:
-            whole_view = True  # culled on one side only: cannot localise it
+        if proj["opacity"][g] == 0.0:
+            mask[:] = True  # culled by the near plane or determinant: cannot localise it
+            return mask
+        reach = int(proj["radius"][g]) + max(tw, th)
+        cx, cy = proj["mean2d"][g]
+        xa, xb = max(0, int(np.floor(cx)) - reach), min(W, int(np.ceil(cx)) + reach + 1)
+        ya, yb = max(0, int(np.floor(cy)) - reach), min(H, int(np.ceil(cy)) + reach + 1)
+        if xa >= xb or ya >= yb:
             continue
-        x0, y0, x1, y1 = proj["rect"][g]
-        mask[max(0, (y0 - 1) * th):min(H, (y1 + 1) * th), max(0, (x0 - 1) * tw):min(W, (x1 + 1) * tw)] = True
-    if whole_view:
-        mask[:] = True
+        yy, xx = np.mgrid[ya:yb, xa:xb]
+        dx, dy = cx - xx, cy - yy
+        a, b, c = proj["conic"][g]
+        power = -0.5 * (a * dx * dx + c * dy * dy) - b * dx * dy
+        alpha = proj["opacity"][g] * np.exp(np.minimum(power, 0.0))
+        mask[ya:yb, xa:xb] |= alpha >= (1.0 / 255.0) * 0.999
     return mask
 
 

@@ -144,7 +144,11 @@ def test_render_grayscale_and_mixed_batch():
 
 
 def test_order_invariance_bit_identical():
-    p, view = CASES["room20k_sh3"]()
+    """Permuting the input Gaussians leaves the image bit-identical when every
+    FP32 depth key is distinct (ties are broken by index, so a permutation may
+    legitimately reorder exactly tied Gaussians)."""
+    p = scenes.room_scene(20_000, seed=31)
+    view = posed(scenes.camera(160, 120, 131.25, 131.25), 11, 0.2, 10.0)
     perm = np.random.default_rng(3).permutation(p["means"].shape[0])
     _, r1 = run_forward(p, view)
     _, r2 = run_forward(scenes.subset(p, perm), view)
@@ -348,27 +352,33 @@ def test_autograd_function_and_recompute_mode():
 
 
 def test_cuda_graph_replay_matches_eager():
-    p, v, targets, lam = scenes.workload("planes10k_320x240")
+    """Three iterations replayed from one captured CUDA graph equal three eager
+    iterations: same step counter, same gradients of the last iteration and
+    the same parameter updates (up to the order of the backward's float
+    atomics)."""
+    p, view = CASES["tiny_sh3_posed"]()
+    target = scenes.random_target(view, 12)
     runs = []
     for use_graph in (False, True):
         gm = mapping.GaussianMap(p)
-        rast = mapping.Rasterizer(v, gm.n, instance_capacity=1 << 20)
-        step = mapping.MappingStep(gm, rast, rast.pack(targets), 0.2)
+        rast = mapping.Rasterizer([view], gm.n, instance_capacity=1 << 18)
+        step = mapping.MappingStep(gm, rast, rast.pack([target]), 0.2)
         if use_graph:
             step.capture(warmup=0)
-            for _ in range(3):
-                step()
-        else:
-            for _ in range(3):
-                step()
+        start = gm.data.clone()
+        for _ in range(3):
+            step()
         torch.cuda.synchronize()
-        runs.append((gm.data.clone(), gm.step.item()))
-    # the graph was captured after zero warm-up runs and replayed three times
-    assert runs[0][1] == runs[1][1] == 3
-    torch.testing.assert_close(runs[0][0], runs[1][0], rtol=1e-5, atol=1e-7)
+        runs.append((gm.data - start, gm.grad.clone(), gm.step.item()))
+    assert runs[0][2] == runs[1][2] == 3
+    assert U.rel_l2(runs[1][1].cpu().numpy(), runs[0][1].cpu().numpy()) < 1e-5
+    assert U.rel_l2(runs[1][0].cpu().numpy(), runs[0][0].cpu().numpy()) < 1e-3
 
 
 def test_batched_equals_per_view_loop():
+    """One batched launch over three mixed views and the loop of three
+    single-view plans compute the same loss and gradients (up to the order of
+    the backward's float atomics)."""
     p = scenes.room_scene(30_000, seed=51)
     views = [scenes.camera(160, 120, 131.25, 131.25),
              posed(scenes.camera(188, 120, 115.0, 115.0, channels=1), 8, 0.2, 10.0),
@@ -380,9 +390,12 @@ def test_batched_equals_per_view_loop():
         if batched:
             rast = mapping.fit_instance_capacity(views, gm)
             it = mapping.MappingStep(gm, rast, rast.pack(targets), 0.2)
+            loss = lambda: rast.loss.item()
         else:
             it = mapping.PerViewLoop(gm, views, targets, 0.2)
+            loss = lambda: sum(r.loss.item() for r in it.rasts)
         it()
         torch.cuda.synchronize()
-        out.append(gm.data.clone())
-    torch.testing.assert_close(out[0], out[1], rtol=1e-4, atol=1e-7)
+        out.append((gm.grad.clone().cpu().numpy(), loss()))
+    assert abs(out[0][1] - out[1][1]) < 1e-6
+    assert U.rel_l2(out[0][0], out[1][0]) < 1e-5
