@@ -202,6 +202,57 @@ def tile_passes(total_tiles):
     return (bits + 7) // 8
 
 
+def run_batched(args, ws):
+    """The 16-keyframe form: one batched iteration over 6 x 640x480 RGB,
+    6 x 752x480 gray and 4 x 1200x680 RGB views of a shared 500k SH-3 map,
+    against the loop of 16 single-view iterations with one Adam step; each
+    captured as one CUDA graph and timed with CUDA events."""
+    import torch
+    from paper_2409_13055_gb300 import mapping, scenes
+
+    p = scenes.room_scene(500_000, seed=scenes.SEED_BASE + 4)
+    views = scenes.views_mixed16()
+    lam = 0.2
+    cfg = dict(tile=(args.tile_w, args.tile_h), smem_batch=args.batch,
+               pixels_per_thread=args.ppt)
+    gt = mapping.GaussianMap(scenes.perturbed(p, scenes.SEED_BASE + 24))
+    r = mapping.fit_instance_capacity(views, gt)
+    r.forward(gt.gs_map())
+    targets = [r.view_slice(r.images, v).cpu().numpy() for v in range(len(views))]
+    del gt, r
+    K = max(10, min(args.steps, 100))
+    result = {}
+    stream = torch.cuda.current_stream()
+    for mode in ("batched", "per_view"):
+        gm = mapping.GaussianMap(p)
+        if mode == "batched":
+            rast = mapping.fit_instance_capacity(views, gm, headroom=1.5, **cfg)
+            it = mapping.MappingStep(gm, rast, rast.pack(targets), lam)
+        else:
+            it = mapping.PerViewLoop(gm, views, targets, lam, **cfg)
+        it.capture(warmup=max(3, args.warmup))
+        for _ in range(3):
+            it()
+        torch.cuda.synchronize()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        barrier(ws)
+        e0.record(stream)
+        for _ in range(K):
+            it()
+        e1.record(stream)
+        torch.cuda.synchronize()
+        ms = reduce_max(e0.elapsed_time(e1), ws) / K
+        result[mode] = dict(iters_per_s=ws * 1e3 / ms, ms_per_iter=ms)
+        del it, gm
+        torch.cuda.empty_cache()
+    result["speedup_batched_over_per_view"] = (result["batched"]["iters_per_s"] /
+                                               result["per_view"]["iters_per_s"])
+    result["config"] = dict(gaussians=500_000, views="6x640x480x3 + 6x752x480x1 + 4x1200x680x3",
+                            steps=K, tile=f"{args.tile_w}x{args.tile_h}", smem_batch=args.batch,
+                            pixels_per_thread=args.ppt, cuda_graph="whole iteration")
+    return result
+
+
 def run_gpu(args, ws, rank, local):
     import torch
     from paper_2409_13055_gb300 import binding as B
@@ -220,14 +271,21 @@ def run_gpu(args, ws, rank, local):
     # target: render of a perturbed copy of the map (set-up, untimed)
     pert = scenes.perturbed(p, scenes.SEED_BASE + 23)
     gt_map = mapping.GaussianMap(pert)
-    rast = mapping.fit_instance_capacity([view], gt_map, tile=(args.tile_w, args.tile_h),
-                                         smem_batch=args.batch)
+    rast = mapping.fit_instance_capacity([view], gt_map)
     rast.forward(gt_map.gs_map())
     target = rast.images.clone()
     del gt_map
     gm = mapping.GaussianMap(p)
+    tuned = None
+    if None in (args.tile_w, args.tile_h, args.batch, args.ppt):
+        from paper_2409_13055_gb300 import autotune
+        tuned = autotune.autotune([view], gm, target, lam, use_cache=False)
+        args.tile_w = args.tile_w or tuned["tile"][0]
+        args.tile_h = args.tile_h or tuned["tile"][1]
+        args.batch = args.batch or tuned["smem_batch"]
+        args.ppt = args.ppt or tuned["pixels_per_thread"]
     rast = mapping.fit_instance_capacity([view], gm, headroom=1.5, tile=(args.tile_w, args.tile_h),
-                                         smem_batch=args.batch)
+                                         smem_batch=args.batch, pixels_per_thread=args.ppt)
     step = mapping.MappingStep(gm, rast, target, lam)
     m, g = gm.gs_map(), gm.gs_map_grad()
     stages = [
@@ -346,13 +404,22 @@ def run_gpu(args, ws, rank, local):
                config=dict(workload=args.workload, gaussians=n, width=view["width"],
                            height=view["height"], sh_degree=3,
                            views=1, lam=0.2, tile=f"{args.tile_w}x{args.tile_h}",
-                           smem_batch=args.batch, cuda_graph="one graph per stage",
+                           smem_batch=args.batch, pixels_per_thread=args.ppt,
+                           autotuned=tuned is not None, cuda_graph="one graph per stage",
                            l2="working set ~1.2 GB > 129 MB L2, no flush",
                            instances=instances, pairs_bwd=pairs_bwd),
                stages_ms=stage_ms, roofline=roof,
                e2e=dict(value=1e3 / e2e_ms * ws, unit="iters/s", h2d_bytes_per_step=int(h2d),
                         d2h_bytes_per_step=4),
                clocks=clocks, gpu_launches=launches_per_step * K)
+
+    if tuned is not None:
+        out["autotune"] = [dict(t, ms=round(t["ms"], 4)) for t in tuned["timings"]]
+    if not args.no_batched:
+        del rast, step, graphs
+        gm = None
+        torch.cuda.empty_cache()
+        out["batched16"] = run_batched(args, ws)
 
     if rank == 0 and not args.no_cpu_baseline:
         from paper_2409_13055_gb300 import scenes as sc
@@ -376,9 +443,12 @@ def main():
     ap.add_argument("--workload", default=WORKLOAD, choices=sorted(WORKLOADS),
                     help="room1M_1200x680 is the headline; room200k_640x480 a smaller "
                          "case of the same shape for profiling")
-    ap.add_argument("--tile-w", type=int, default=16)
-    ap.add_argument("--tile-h", type=int, default=16)
-    ap.add_argument("--batch", type=int, default=128)
+    ap.add_argument("--tile-w", type=int, default=None, help="fix the tile width (else autotuned)")
+    ap.add_argument("--tile-h", type=int, default=None)
+    ap.add_argument("--batch", type=int, default=None, help="Gaussians per shared-memory batch")
+    ap.add_argument("--ppt", type=int, default=None, help="pixels per thread")
+    ap.add_argument("--no-batched", action="store_true",
+                    help="skip the 16-keyframe batched vs per-view measurement")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--reference-warmup", action="store_true")
     args = ap.parse_args()

@@ -93,11 +93,17 @@ typedef struct {
  *     tile_w*tile_h in [64, 256] are accepted);
  *   smem_batch: Gaussians staged per shared-memory batch, 32..256, a
  *     multiple of 32;
+ *   pixels_per_thread: 0 (automatic) or 1, 2, 4, 8 consecutive pixels of a
+ *     tile row handled by one thread; tile_w must be a multiple of it and the
+ *     tile must keep at least one full warp of threads;
  *   near_z: Gaussians whose camera depth is not above near_z are culled
  *     (default reading 0.2 m);
- *   bg: background colour, entering the image as T_final * bg. */
+ *   bg: background colour, entering the image as T_final * bg.
+ * The tile shape changes which pixels a Gaussian can reach (its 3-sigma
+ * rect is counted in whole tiles), hence the image; smem_batch and
+ * pixels_per_thread change only the speed. */
 typedef struct {
-    int32_t tile_w, tile_h, smem_batch, reserved;
+    int32_t tile_w, tile_h, smem_batch, pixels_per_thread;
     float near_z;
     float bg[3];
 } gs_config;
@@ -215,6 +221,7 @@ gs_status gs_render_bwd(const gs_plan *plan, const gs_map *map, const gs_view *v
  * parameter buffer of n_floats split into n_groups contiguous groups:
  * group g covers [group_offsets_host[g], group_offsets_host[g+1]) with
  * learning rate group_lr_host[g] (HOST arrays of n_groups+1 and n_groups).
+ * n_floats must be below 2^31 (GS_ERR_UNSUPPORTED otherwise).
  * *step_dev (device int32) is incremented first, then
  *   m = b1 m + (1-b1) g;  v = b2 v + (1-b2) g^2;
  *   p -= lr (m / (1 - b1^t)) / (sqrt(v / (1 - b2^t)) + eps),  t = *step_dev. */

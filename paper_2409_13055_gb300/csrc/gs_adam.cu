@@ -2,7 +2,9 @@
 //
 // One fused, HBM-bound pass over every parameter group: 16 bytes read
 // (p, g, m, v) and 12 written (p, m, v) per float, float4-vectorised, grid
-// sized to a multiple of the 152 SMs and striding over the buffer.  The step
+// sized to a multiple of the 152 SMs and striding over the buffer; the
+// gradient is read with a streaming hint (used once).  At most 2^31 - 1
+// floats per call.  The step
 // counter lives on the device and is advanced by a one-thread kernel first,
 // so a captured CUDA graph replays correct bias corrections every iteration.
 #include <math.h>
@@ -16,14 +18,14 @@ constexpr int kAdamThreads = 256;
 constexpr int kAdamBlocks = 152 * 8;
 
 struct Groups {
-    long long off[GS_MAX_GROUPS + 1];
+    uint32_t off[GS_MAX_GROUPS + 1];  // element offsets (n < 2^31)
     float lr[GS_MAX_GROUPS];
     int n;
 };
 
 __global__ void k_step_inc(int32_t* step) { *step += 1; }
 
-__device__ __forceinline__ float lr_of(const Groups& g, long long i) {
+__device__ __forceinline__ float lr_of(const Groups& g, uint32_t i) {
     float lr = g.lr[0];
 #pragma unroll
     for (int k = 1; k < GS_MAX_GROUPS; ++k)
@@ -31,11 +33,28 @@ __device__ __forceinline__ float lr_of(const Groups& g, long long i) {
     return lr;
 }
 
+// Learning rates of the four elements e..e+3; one lookup unless a group
+// boundary falls inside the chunk.
+__device__ __forceinline__ float4 lr4_of(const Groups& g, uint32_t e) {
+    const float a = lr_of(g, e), d = lr_of(g, e + 3);
+    if (a == d) return make_float4(a, a, a, a);
+    return make_float4(a, lr_of(g, e + 1), lr_of(g, e + 2), d);
+}
+
 __device__ __forceinline__ void adam1(float& p, float g, float& m, float& v, float lr, float b1,
                                       float b2, float eps, float ibc1, float ibc2) {
     m = fmaf(b1, m, (1.0f - b1) * g);
     v = fmaf(b2, v, (1.0f - b2) * g * g);
     p -= lr * (m * ibc1) / (sqrtf(v * ibc2) + eps);
+}
+
+__device__ __forceinline__ void adam4(float4& p, const float4& g, float4& m, float4& v,
+                                      const float4& lr, float b1, float b2, float eps, float ibc1,
+                                      float ibc2) {
+    adam1(p.x, g.x, m.x, v.x, lr.x, b1, b2, eps, ibc1, ibc2);
+    adam1(p.y, g.y, m.y, v.y, lr.y, b1, b2, eps, ibc1, ibc2);
+    adam1(p.z, g.z, m.z, v.z, lr.z, b1, b2, eps, ibc1, ibc2);
+    adam1(p.w, g.w, m.w, v.w, lr.w, b1, b2, eps, ibc1, ibc2);
 }
 
 __global__ void __launch_bounds__(kAdamThreads)
@@ -60,22 +79,18 @@ k_adam(float* __restrict__ params, const float* __restrict__ grads, float* __res
         float4* M = reinterpret_cast<float4*>(m);
         float4* V = reinterpret_cast<float4*>(v);
         for (long long i = tid; i < n4; i += stride) {
-            float4 p4 = P[i], m4 = M[i], v4 = V[i];
-            const float4 g4 = __ldcs(G + i);
-            const long long e = i << 2;
-            adam1(p4.x, g4.x, m4.x, v4.x, lr_of(groups, e), b1, b2, eps, ibc1, ibc2);
-            adam1(p4.y, g4.y, m4.y, v4.y, lr_of(groups, e + 1), b1, b2, eps, ibc1, ibc2);
-            adam1(p4.z, g4.z, m4.z, v4.z, lr_of(groups, e + 2), b1, b2, eps, ibc1, ibc2);
-            adam1(p4.w, g4.w, m4.w, v4.w, lr_of(groups, e + 3), b1, b2, eps, ibc1, ibc2);
-            P[i] = p4;
-            M[i] = m4;
-            V[i] = v4;
+            float4 p0 = P[i], m0 = M[i], v0 = V[i];
+            const float4 g0 = __ldcs(G + i);
+            adam4(p0, g0, m0, v0, lr4_of(groups, (uint32_t)(i << 2)), b1, b2, eps, ibc1, ibc2);
+            P[i] = p0;
+            M[i] = m0;
+            V[i] = v0;
         }
         done = n4 << 2;
     }
     for (long long i = done + tid; i < n; i += stride) {
         float p = params[i], mm = m[i], vv = v[i];
-        adam1(p, grads[i], mm, vv, lr_of(groups, i), b1, b2, eps, ibc1, ibc2);
+        adam1(p, grads[i], mm, vv, lr_of(groups, (uint32_t)i), b1, b2, eps, ibc1, ibc2);
         params[i] = p;
         m[i] = mm;
         v[i] = vv;
@@ -87,9 +102,10 @@ k_adam(float* __restrict__ params, const float* __restrict__ grads, float* __res
 gs_status launch_adam(float* params, const float* grads, float* m, float* v, int64_t n,
                       int32_t n_groups, const int64_t* offs, const float* lrs, float b1, float b2,
                       float eps, int32_t* step_dev, cudaStream_t st) {
+    if (n >= (int64_t(1) << 31)) return GS_ERR_UNSUPPORTED;
     Groups g;
     g.n = n_groups;
-    for (int k = 0; k <= GS_MAX_GROUPS; ++k) g.off[k] = k <= n_groups ? offs[k] : n;
+    for (int k = 0; k <= GS_MAX_GROUPS; ++k) g.off[k] = (uint32_t)(k <= n_groups ? offs[k] : n);
     for (int k = 0; k < GS_MAX_GROUPS; ++k) g.lr[k] = k < n_groups ? lrs[k] : 0.0f;
     const bool aligned = ((reinterpret_cast<uintptr_t>(params) | reinterpret_cast<uintptr_t>(grads) |
                            reinterpret_cast<uintptr_t>(m) | reinterpret_cast<uintptr_t>(v)) &

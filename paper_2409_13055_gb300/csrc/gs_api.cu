@@ -31,12 +31,17 @@ extern "C" gs_status gs_plan_init(gs_plan* plan, const gs_config* cfg, int32_t n
         return GS_ERR_UNSUPPORTED;
     if (cfg->smem_batch < 32 || cfg->smem_batch > 256 || cfg->smem_batch % 32)
         return GS_ERR_UNSUPPORTED;
+    int ppt = cfg->pixels_per_thread;
+    if (ppt == 0) ppt = (cfg->tile_w * cfg->tile_h >= 128 && cfg->tile_w % 4 == 0) ? 4 : 2;
+    if (ppt != 1 && ppt != 2 && ppt != 4 && ppt != 8) return GS_ERR_UNSUPPORTED;
+    if (cfg->tile_w % ppt || (cfg->tile_w * cfg->tile_h / ppt) % 32) return GS_ERR_UNSUPPORTED;
     if (!(cfg->near_z > 0.0f)) return GS_ERR_INVALID;
     if ((int64_t)n_views * n_capacity > (int64_t(1) << 31)) return GS_ERR_INVALID;
 
     memset(plan, 0, sizeof(*plan));
     Plan* p = reinterpret_cast<Plan*>(plan);
     p->cfg = *cfg;
+    p->cfg.pixels_per_thread = ppt;
     p->n_capacity = n_capacity;
     p->inst_capacity = instance_capacity;
     p->vt.n_views = n_views;

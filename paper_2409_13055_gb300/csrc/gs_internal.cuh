@@ -15,7 +15,7 @@ constexpr uint32_t kPlanMagic = 0x67733330u;  // "gs30"
 constexpr int kRadixBits = 8;
 constexpr int kRadix = 1 << kRadixBits;
 constexpr int kSortThreads = 256;
-constexpr int kSortItems = 16;
+constexpr int kSortItems = 4;
 constexpr int kSortTile = kSortThreads * kSortItems;  // elements per sort block
 constexpr int kScanThreads = 256;
 constexpr int kScanItems = 8;

@@ -17,9 +17,13 @@
 //    would keep only ~6e-5 px at x = 1000;
 //  * the forward and the backward evaluate alpha with the same explicitly
 //    rounded operations, so both take the same skip decisions;
-//  * the backward reduces each Gaussian's nine gradient components over the
-//    warp with xor shuffles (skipping Gaussians no lane touches) and issues
-//    them as nine parallel atomics from lanes 0..8.
+//  * register blocking: each thread owns 1-8 consecutive pixels of a tile
+//    row, so every staged Gaussian is read from shared memory once per
+//    thread, not once per pixel;
+//  * the backward sums each Gaussian's nine gradient components over the
+//    thread's pixels, then over the warp with a recursive-halving
+//    reduce-scatter (16 shuffles, skipped when no lane touches the
+//    Gaussian), and issues them as nine parallel atomics.
 #include "gs_internal.cuh"
 
 namespace gs {
@@ -79,8 +83,15 @@ __device__ __forceinline__ void issue_batch(float4* stage, uint32_t* ids,
 
 // Replace the mean pair of each staged record by its tile-local offset:
 // stage[3j] = {lx, ly, a, b}; stage[3j+1] = {a, b, c, o}; stage[3j+2] =
-// {r, g, b, gray}.
-__device__ __forceinline__ void localise_batch(float4* stage, int cnt, float tx0, float ty0) {
+// {r, g, b, gray}; and record in wmask[j] which warps of the CTA the Gaussian
+// can reach.  Warp w owns tile rows [w*rows, (w+1)*rows).  A warp is left out
+// only if its pixel strip misses the bounding box of the Gaussian's
+// alpha >= 1/255 ellipse, {d : d^T Q d <= 2 ln(255 o)}, whose half-extents
+// are sqrt(2 ln(255 o) (Q^-1)_xx) and sqrt(2 ln(255 o) (Q^-1)_yy); the box is
+// grown by 0.1% + 0.01 px, far beyond FP32 rounding, so every skipped
+// evaluation would have been skipped by the alpha test itself.
+__device__ __forceinline__ void localise_batch(float4* stage, uint32_t* wmask, int cnt, float tx0,
+                                               float ty0, int tile_w, int rows, int nwarps) {
     for (int j = threadIdx.x; j < cnt; j += blockDim.x) {
         float4 m = stage[3 * j];
         const float4 q = stage[3 * j + 1];
@@ -92,6 +103,27 @@ __device__ __forceinline__ void localise_batch(float4* stage, int cnt, float tx0
         stage[3 * j] = m;
         col.w = (col.x + col.y + col.z) * (1.0f / 3.0f);
         stage[3 * j + 2] = col;
+        const uint32_t all = nwarps >= 32 ? 0xffffffffu : ((1u << nwarps) - 1u);
+        uint32_t bits = 0u;
+        const float tau = logf(255.0f * q.w);
+        const float detq = q.x * q.z - q.y * q.y;
+        if (tau > 0.0f) {
+            if (!(detq > 0.0f)) {
+                bits = all;
+            } else {
+                const float ex = sqrtf(2.0f * tau * q.z / detq) * 1.001f + 0.01f;
+                const float ey = sqrtf(2.0f * tau * q.x / detq) * 1.001f + 0.01f;
+                if (!(ex == ex) || !(ey == ey)) {
+                    bits = all;
+                } else if (m.x + ex >= 0.0f && m.x - ex <= (float)(tile_w - 1)) {
+                    for (int w = 0; w < nwarps; ++w) {
+                        const float r0 = (float)(w * rows), r1 = (float)(w * rows + rows - 1);
+                        if (m.y + ey >= r0 && m.y - ey <= r1) bits |= 1u << w;
+                    }
+                }
+            }
+        }
+        wmask[j] = bits;
     }
 }
 
@@ -99,51 +131,80 @@ __device__ __forceinline__ float alpha_of(float o, float power) {
     return fminf(kAlphaMax, __fmul_rn(o, __expf(power)));
 }
 
-template <int CH>
-__device__ __forceinline__ void blend_batch(const float4* stage, int cnt, uint32_t pos0, float lx,
-                                            float ly, float& T, float* C, int32_t& last,
-                                            bool& done) {
-    for (int j = 0; j < cnt; ++j) {
+// Pixels a thread owns: PPT consecutive pixels of one tile row, starting at
+// tile-local (lx0, ly).
+struct PixelRun {
+    int lx0, ly;
+};
+
+__device__ __forceinline__ PixelRun pixel_run(int ppt, int log2_tw, int tile_w) {
+    const int p0 = threadIdx.x * ppt;
+    PixelRun r;
+    r.lx0 = p0 & (tile_w - 1);
+    r.ly = p0 >> log2_tw;
+    return r;
+}
+
+// Front-to-back blending of one staged batch for the PPT pixels of a thread.
+// live: bit k set while pixel k still accumulates.
+template <int CH, int PPT>
+__device__ __forceinline__ void blend_batch(const float4* stage, const uint32_t* wmask, int cnt,
+                                            uint32_t pos0, int lx0, float ly, float* T,
+                                            float (*C)[CH], int32_t* last, unsigned& live) {
+    const uint32_t wbit = 1u << (threadIdx.x >> 5);
+    for (int j = 0; j < cnt && live; ++j) {
+        if (!(wmask[j] & wbit)) continue;
         const float4 g = stage[3 * j];
         const float4 q = stage[3 * j + 1];
-        const float power = gauss_power(g.z, g.w, q.z, g.x - lx, g.y - ly);
-        if (power > 0.0f) continue;
-        const float alpha = alpha_of(q.w, power);
-        if (alpha < kAlphaMin) continue;
-        const float Tn = __fmul_rn(T, __fsub_rn(1.0f, alpha));
-        if (Tn < kTMin) {
-            done = true;
-            break;
-        }
         const float4 col = stage[3 * j + 2];
-        const float wgt = alpha * T;
-        if (CH == 3) {
-            C[0] = fmaf(wgt, col.x, C[0]);
-            C[1] = fmaf(wgt, col.y, C[1]);
-            C[2] = fmaf(wgt, col.z, C[2]);
-        } else {
-            C[0] = fmaf(wgt, col.w, C[0]);
+        const float dy = g.y - ly;
+#pragma unroll
+        for (int k = 0; k < PPT; ++k) {
+            // predicated rather than branched: the same decisions as the
+            // backward, without divergent control flow inside the warp
+            const float power = gauss_power(g.z, g.w, q.z, g.x - (float)(lx0 + k), dy);
+            const float alpha = alpha_of(q.w, power);
+            const float Tn = __fmul_rn(T[k], __fsub_rn(1.0f, alpha));
+            const bool hit = ((live >> k) & 1u) && power <= 0.0f && alpha >= kAlphaMin;
+            const bool stop = hit && Tn < kTMin;
+            const bool add = hit && !stop;
+            const float wgt = add ? alpha * T[k] : 0.0f;
+            if (CH == 3) {
+                C[k][0] = fmaf(wgt, col.x, C[k][0]);
+                C[k][1] = fmaf(wgt, col.y, C[k][1]);
+                C[k][2] = fmaf(wgt, col.z, C[k][2]);
+            } else {
+                C[k][0] = fmaf(wgt, col.w, C[k][0]);
+            }
+            T[k] = add ? Tn : T[k];
+            last[k] = add ? (int32_t)(pos0 + j + 1) : last[k];
+            live = stop ? (live & ~(1u << k)) : live;
         }
-        T = Tn;
-        last = (int32_t)(pos0 + j + 1);
     }
 }
 
-__global__ void k_render_fwd(ViewTable vt, const uint32_t* __restrict__ ranges,
-                             const uint32_t* __restrict__ ivals, const float4* __restrict__ rec,
-                             int batch, float bg0, float bg1, float bg2,
-                             float* __restrict__ images, float* __restrict__ final_T,
-                             int32_t* __restrict__ last_idx) {
-    extern __shared__ float4 smem[];
-    const TileCtx tc = tile_ctx(vt, ranges, blockIdx.x);
-    const int lxi = threadIdx.x & (vt.tile_w - 1);
-    const int lyi = threadIdx.x >> vt.log2_tw;
-    const int px = tc.tx0 + lxi, py = tc.ty0 + lyi;
-    const bool inside = px < tc.width && py < tc.height;
-    const float lx = (float)lxi, ly = (float)lyi;
-    float T = 1.0f, C[3] = {0.f, 0.f, 0.f};
-    int32_t last = 0;
-    bool done = !inside;
+template <int CH, int PPT>
+__device__ void render_fwd_tile(const ViewTable& vt, const TileCtx& tc,
+                                const uint32_t* __restrict__ ivals,
+                                const float4* __restrict__ rec, float4* smem, int batch,
+                                const float* bg, float* __restrict__ images,
+                                float* __restrict__ final_T, int32_t* __restrict__ last_idx) {
+    uint32_t* const mask0 = reinterpret_cast<uint32_t*>(smem + 6 * batch);
+    const int nwarps = blockDim.x >> 5;
+    const int rows = (32 * PPT) >> vt.log2_tw;
+    const PixelRun pr = pixel_run(PPT, vt.log2_tw, vt.tile_w);
+    const int py = tc.ty0 + pr.ly;
+    float T[PPT], C[PPT][CH];
+    int32_t last[PPT];
+    unsigned live = 0u;
+#pragma unroll
+    for (int k = 0; k < PPT; ++k) {
+        T[k] = 1.0f;
+        last[k] = 0;
+#pragma unroll
+        for (int c = 0; c < CH; ++c) C[k][c] = 0.0f;
+        if (tc.tx0 + pr.lx0 + k < tc.width && py < tc.height) live |= 1u << k;
+    }
     const int total = (int)(tc.end - tc.begin);
     const int nb = (total + batch - 1) / batch;
     if (nb > 0) {
@@ -162,181 +223,232 @@ __global__ void k_render_fwd(ViewTable vt, const uint32_t* __restrict__ ranges,
             cp_async_wait_all();
         }
         __syncthreads();
-        localise_batch(cur, cnt, (float)tc.tx0, (float)tc.ty0);
+        uint32_t* cmask = mask0 + (b & 1) * batch;
+        localise_batch(cur, cmask, cnt, (float)tc.tx0, (float)tc.ty0, vt.tile_w, rows, nwarps);
         __syncthreads();
-        if (!done) {
-            if (tc.channels == 3)
-                blend_batch<3>(cur, cnt, (uint32_t)(b * batch), lx, ly, T, C, last, done);
-            else
-                blend_batch<1>(cur, cnt, (uint32_t)(b * batch), lx, ly, T, C, last, done);
-        }
-        if (__syncthreads_count(done) == (int)blockDim.x) {
+        blend_batch<CH, PPT>(cur, cmask, cnt, (uint32_t)(b * batch), pr.lx0, (float)pr.ly, T, C,
+                             last, live);
+        if (__syncthreads_count(live != 0u) == 0) {
             cp_async_wait_all();  // nothing may still be landing in shared memory
             break;
         }
     }
-    if (!inside) return;
-    const int64_t pix = (int64_t)py * tc.width + px;
+    if (py >= tc.height) return;
     const int64_t plane = (int64_t)tc.width * tc.height;
-    if (tc.channels == 3) {
-        images[tc.val_base + pix] = fmaf(T, bg0, C[0]);
-        images[tc.val_base + plane + pix] = fmaf(T, bg1, C[1]);
-        images[tc.val_base + 2 * plane + pix] = fmaf(T, bg2, C[2]);
-    } else {
-        images[tc.val_base + pix] = fmaf(T, (bg0 + bg1 + bg2) * (1.0f / 3.0f), C[0]);
-    }
-    final_T[tc.pix_base + pix] = T;
-    last_idx[tc.pix_base + pix] = last;
-}
-
-__device__ __forceinline__ float warp_sum(float x) {
+    const float bgg = (bg[0] + bg[1] + bg[2]) * (1.0f / 3.0f);
 #pragma unroll
-    for (int o = 16; o > 0; o >>= 1) x += __shfl_xor_sync(0xffffffffu, x, o);
-    return x;
-}
-
-template <int CH>
-__device__ __forceinline__ void adjoint_batch(const float4* stage, const uint32_t* ids, int lo_rel,
-                                              int hi_rel, uint32_t pos0, float lx, float ly,
-                                              int32_t last, const float* g, float& T, float* S,
-                                              float* __restrict__ grad2d) {
-    const int lane = threadIdx.x & 31;
-    for (int j = hi_rel - 1; j >= lo_rel; --j) {
-        const uint32_t pos = pos0 + (uint32_t)j;
-        float v[kGrad2d];
+    for (int k = 0; k < PPT; ++k) {
+        const int px = tc.tx0 + pr.lx0 + k;
+        if (px >= tc.width) continue;
+        const int64_t pix = (int64_t)py * tc.width + px;
+        if (CH == 3) {
 #pragma unroll
-        for (int k = 0; k < kGrad2d; ++k) v[k] = 0.0f;
-        bool contrib = false;
-        if ((int32_t)pos < last) {
-            const float4 gm = stage[3 * j];
-            const float4 q = stage[3 * j + 1];
-            const float dx = gm.x - lx, dy = gm.y - ly;
-            const float power = gauss_power(gm.z, gm.w, q.z, dx, dy);
-            if (power <= 0.0f) {
-                const float G = __expf(power);
-                const float oG = __fmul_rn(q.w, G);
-                const float alpha = fminf(kAlphaMax, oG);
-                if (alpha >= kAlphaMin) {
-                    contrib = true;
-                    const float4 col = stage[3 * j + 2];
-                    const float one_m = __fsub_rn(1.0f, alpha);
-                    const float inv = 1.0f / one_m;
-                    const float Ti = T * inv;
-                    const float w = alpha * Ti;
-                    float dal;
-                    if (CH == 3) {
-                        dal = g[0] * (Ti * col.x - S[0] * inv) + g[1] * (Ti * col.y - S[1] * inv) +
-                              g[2] * (Ti * col.z - S[2] * inv);
-                        S[0] = fmaf(w, col.x, S[0]);
-                        S[1] = fmaf(w, col.y, S[1]);
-                        S[2] = fmaf(w, col.z, S[2]);
-                        v[6] = w * g[0];
-                        v[7] = w * g[1];
-                        v[8] = w * g[2];
-                    } else {
-                        dal = g[0] * (Ti * col.w - S[0] * inv);
-                        S[0] = fmaf(w, col.w, S[0]);
-                        v[6] = w * g[0];
-                    }
-                    T = Ti;
-                    if (oG < kAlphaMax) {
-                        const float dpow = oG * dal;
-                        v[0] = -dpow * (gm.z * dx + gm.w * dy);
-                        v[1] = -dpow * (gm.w * dx + q.z * dy);
-                        v[2] = -0.5f * dpow * dx * dx;
-                        v[3] = -dpow * dx * dy;
-                        v[4] = -0.5f * dpow * dy * dy;
-                        v[5] = G * dal;
-                    }
-                }
-            }
+            for (int c = 0; c < CH; ++c)
+                images[tc.val_base + c * plane + pix] = fmaf(T[k], bg[c], C[k][c]);
+        } else {
+            images[tc.val_base + pix] = fmaf(T[k], bgg, C[k][0]);
         }
-        if (__any_sync(0xffffffffu, contrib)) {
-#pragma unroll
-            for (int k = 0; k < kGrad2d; ++k) v[k] = warp_sum(v[k]);
-            float mine = 0.0f;
-#pragma unroll
-            for (int k = 0; k < kGrad2d; ++k) mine = (lane == k) ? v[k] : mine;
-            const int nval = CH == 3 ? kGrad2d : 7;
-            if (lane < nval) atomicAdd(grad2d + (size_t)ids[j] * kGrad2d + lane, mine);
-        }
+        final_T[tc.pix_base + pix] = T[k];
+        last_idx[tc.pix_base + pix] = last[k];
     }
 }
 
-__global__ void k_render_bwd(ViewTable vt, const uint32_t* __restrict__ ranges,
+template <int PPT>
+__global__ void k_render_fwd(ViewTable vt, const uint32_t* __restrict__ ranges,
                              const uint32_t* __restrict__ ivals, const float4* __restrict__ rec,
                              int batch, float bg0, float bg1, float bg2,
-                             const float* __restrict__ final_T, const int32_t* __restrict__ last_idx,
-                             const float* __restrict__ dL, float* __restrict__ grad2d) {
+                             float* __restrict__ images, float* __restrict__ final_T,
+                             int32_t* __restrict__ last_idx) {
     extern __shared__ float4 smem[];
-    uint32_t* const ids0 = reinterpret_cast<uint32_t*>(smem + 6 * batch);
-    __shared__ int s_maxlast;
     const TileCtx tc = tile_ctx(vt, ranges, blockIdx.x);
-    const int lxi = threadIdx.x & (vt.tile_w - 1);
-    const int lyi = threadIdx.x >> vt.log2_tw;
-    const int px = tc.tx0 + lxi, py = tc.ty0 + lyi;
-    const bool inside = px < tc.width && py < tc.height;
-    const float lx = (float)lxi, ly = (float)lyi;
-    const int64_t pix = (int64_t)py * tc.width + px;
-    const int64_t plane = (int64_t)tc.width * tc.height;
-    int32_t last = 0;
-    float T = 1.0f, g[3] = {0.f, 0.f, 0.f}, S[3] = {0.f, 0.f, 0.f};
-    if (threadIdx.x == 0) s_maxlast = 0;
-    __syncthreads();
-    if (inside) {
-        last = last_idx[tc.pix_base + pix];
-        T = final_T[tc.pix_base + pix];
-        if (tc.channels == 3) {
-            g[0] = dL[tc.val_base + pix];
-            g[1] = dL[tc.val_base + plane + pix];
-            g[2] = dL[tc.val_base + 2 * plane + pix];
-            S[0] = T * bg0;
-            S[1] = T * bg1;
-            S[2] = T * bg2;
-        } else {
-            g[0] = dL[tc.val_base + pix];
-            S[0] = T * ((bg0 + bg1 + bg2) * (1.0f / 3.0f));
+    const float bg[3] = {bg0, bg1, bg2};
+    if (tc.channels == 3)
+        render_fwd_tile<3, PPT>(vt, tc, ivals, rec, smem, batch, bg, images, final_T, last_idx);
+    else
+        render_fwd_tile<1, PPT>(vt, tc, ivals, rec, smem, batch, bg, images, final_T, last_idx);
+}
+
+// Warp reduce-scatter of 16 values by recursive halving: afterwards lane L
+// holds the warp total of value L >> 1 (16 shuffles instead of 5 per value).
+__device__ __forceinline__ float warp_reduce16(float* v) {
+    const int lane = threadIdx.x & 31;
+#pragma unroll
+    for (int h = 8, o = 16; h >= 1; h >>= 1, o >>= 1) {
+        const bool up = (lane & o) != 0;
+#pragma unroll
+        for (int i = 0; i < h; ++i) {
+            const float send = up ? v[i] : v[i + h];
+            const float keep = up ? v[i + h] : v[i];
+            v[i] = keep + __shfl_xor_sync(0xffffffffu, send, o);
         }
-        atomicMax(&s_maxlast, last);
     }
+    return v[0] + __shfl_xor_sync(0xffffffffu, v[0], 1);
+}
+
+template <int CH, int PPT>
+__device__ void render_bwd_tile(const ViewTable& vt, const TileCtx& tc,
+                                const uint32_t* __restrict__ ivals,
+                                const float4* __restrict__ rec, float4* smem, int* s_maxlast,
+                                int batch, const float* bg, const float* __restrict__ final_T,
+                                const int32_t* __restrict__ last_idx,
+                                const float* __restrict__ dL, float* __restrict__ grad2d) {
+    // shared memory: stage[2][3*batch] float4 | ids[2][batch] | masks[2][batch] |
+    //                acc[batch][9] float (the batch's per-Gaussian gradient sums)
+    uint32_t* const ids0 = reinterpret_cast<uint32_t*>(smem + 6 * batch);
+    uint32_t* const mask0 = ids0 + 2 * batch;
+    float* const acc = reinterpret_cast<float*>(mask0 + 2 * batch);
+    const int nwarps = blockDim.x >> 5;
+    const int rows = (32 * PPT) >> vt.log2_tw;
+    const uint32_t wbit = 1u << (threadIdx.x >> 5);
+    const PixelRun pr = pixel_run(PPT, vt.log2_tw, vt.tile_w);
+    const int py = tc.ty0 + pr.ly;
+    const float ly = (float)pr.ly;
+    const int64_t plane = (int64_t)tc.width * tc.height;
+    const float bgg = (bg[0] + bg[1] + bg[2]) * (1.0f / 3.0f);
+    float T[PPT], g[PPT][CH], S[PPT][CH];
+    int32_t last[PPT];
+    int mylast = 0;
+#pragma unroll
+    for (int k = 0; k < PPT; ++k) {
+        const int px = tc.tx0 + pr.lx0 + k;
+        last[k] = 0;
+        T[k] = 1.0f;
+#pragma unroll
+        for (int c = 0; c < CH; ++c) g[k][c] = S[k][c] = 0.0f;
+        if (px < tc.width && py < tc.height) {
+            const int64_t pix = (int64_t)py * tc.width + px;
+            last[k] = last_idx[tc.pix_base + pix];
+            T[k] = final_T[tc.pix_base + pix];
+#pragma unroll
+            for (int c = 0; c < CH; ++c) {
+                g[k][c] = dL[tc.val_base + c * plane + pix];
+                S[k][c] = T[k] * (CH == 3 ? bg[c] : bgg);
+            }
+            mylast = max(mylast, last[k]);
+        }
+    }
+    if (threadIdx.x == 0) *s_maxlast = 0;
+    for (int i = threadIdx.x; i < kGrad2d * batch; i += blockDim.x) acc[i] = 0.0f;
     __syncthreads();
-    const int maxlast = s_maxlast;
+    atomicMax(s_maxlast, mylast);
+    __syncthreads();
+    const int maxlast = *s_maxlast;
     const int nb = (maxlast + batch - 1) / batch;
+    const int lane = threadIdx.x & 31;
+    const int ncomp = CH == 3 ? kGrad2d : 7;
     // batch k covers list positions [max(0, maxlast - (k+1) batch), maxlast - k batch)
-    auto bounds = [&](int k, int& lo, int& hi) {
-        hi = maxlast - k * batch;
-        lo = max(0, hi - batch);
-    };
     if (nb > 0) {
-        int lo, hi;
-        bounds(0, lo, hi);
-        issue_batch(smem, ids0, ivals, rec, tc.begin + lo, hi - lo);
+        const int lo = max(0, maxlast - batch);
+        issue_batch(smem, ids0, ivals, rec, tc.begin + lo, maxlast - lo);
         cp_async_commit();
     }
-    for (int k = 0; k < nb; ++k) {
-        int lo, hi;
-        bounds(k, lo, hi);
-        float4* cur = smem + (k & 1) * 3 * batch;
-        uint32_t* cur_ids = ids0 + (k & 1) * batch;
-        if (k + 1 < nb) {
-            int lo2, hi2;
-            bounds(k + 1, lo2, hi2);
-            issue_batch(smem + ((k + 1) & 1) * 3 * batch, ids0 + ((k + 1) & 1) * batch, ivals, rec,
-                        tc.begin + lo2, hi2 - lo2);
+    for (int kb = 0; kb < nb; ++kb) {
+        const int hi = maxlast - kb * batch, lo = max(0, hi - batch);
+        const int cnt = hi - lo;
+        float4* cur = smem + (kb & 1) * 3 * batch;
+        const uint32_t* cur_ids = ids0 + (kb & 1) * batch;
+        uint32_t* cmask = mask0 + (kb & 1) * batch;
+        if (kb + 1 < nb) {
+            const int hi2 = lo, lo2 = max(0, hi2 - batch);
+            issue_batch(smem + ((kb + 1) & 1) * 3 * batch, ids0 + ((kb + 1) & 1) * batch, ivals,
+                        rec, tc.begin + lo2, hi2 - lo2);
             cp_async_commit();
             cp_async_wait_one();
         } else {
             cp_async_wait_all();
         }
         __syncthreads();
-        localise_batch(cur, hi - lo, (float)tc.tx0, (float)tc.ty0);
+        localise_batch(cur, cmask, cnt, (float)tc.tx0, (float)tc.ty0, vt.tile_w, rows, nwarps);
         __syncthreads();
-        if (tc.channels == 3)
-            adjoint_batch<3>(cur, cur_ids, 0, hi - lo, (uint32_t)lo, lx, ly, last, g, T, S, grad2d);
-        else
-            adjoint_batch<1>(cur, cur_ids, 0, hi - lo, (uint32_t)lo, lx, ly, last, g, T, S, grad2d);
+        for (int j = cnt - 1; j >= 0; --j) {
+            if (!(cmask[j] & wbit)) continue;
+            const int32_t pos = lo + j;
+            const float4 gm = cur[3 * j];
+            const float4 q = cur[3 * j + 1];
+            const float4 col = cur[3 * j + 2];
+            const float dy = gm.y - ly;
+            float v[16];
+#pragma unroll
+            for (int i = 0; i < 16; ++i) v[i] = 0.0f;
+            bool contrib = false;
+#pragma unroll
+            for (int k = 0; k < PPT; ++k) {
+                // predicated: every lane runs the same instructions; a lane
+                // whose pixel is not blended here contributes zeros and
+                // keeps its state
+                const float dx = gm.x - (float)(pr.lx0 + k);
+                const float power = gauss_power(gm.z, gm.w, q.z, dx, dy);
+                const float G = __expf(power);
+                const float oG = __fmul_rn(q.w, G);
+                const float alpha = fminf(kAlphaMax, oG);
+                const bool hit = pos < last[k] && power <= 0.0f && alpha >= kAlphaMin;
+                contrib |= hit;
+                const float inv = __frcp_rn(__fsub_rn(1.0f, alpha));
+                const float Ti = T[k] * inv;
+                const float w = hit ? alpha * Ti : 0.0f;
+                float dal;
+                if (CH == 3) {
+                    dal = g[k][0] * (Ti * col.x - S[k][0] * inv) +
+                          g[k][1] * (Ti * col.y - S[k][1] * inv) +
+                          g[k][2] * (Ti * col.z - S[k][2] * inv);
+                    S[k][0] = fmaf(w, col.x, S[k][0]);
+                    S[k][1] = fmaf(w, col.y, S[k][1]);
+                    S[k][2] = fmaf(w, col.z, S[k][2]);
+                    v[6] = fmaf(w, g[k][0], v[6]);
+                    v[7] = fmaf(w, g[k][1], v[7]);
+                    v[8] = fmaf(w, g[k][2], v[8]);
+                } else {
+                    dal = g[k][0] * (Ti * col.w - S[k][0] * inv);
+                    S[k][0] = fmaf(w, col.w, S[k][0]);
+                    v[6] = fmaf(w, g[k][0], v[6]);
+                }
+                T[k] = hit ? Ti : T[k];
+                // alpha = o G when unclamped; a clamped alpha passes no gradient
+                const bool free_a = hit && oG < kAlphaMax;
+                const float dpow = free_a ? oG * dal : 0.0f;
+                v[0] -= dpow * (gm.z * dx + gm.w * dy);
+                v[1] -= dpow * (gm.w * dx + q.z * dy);
+                v[2] -= 0.5f * dpow * dx * dx;
+                v[3] -= dpow * dx * dy;
+                v[4] -= 0.5f * dpow * dy * dy;
+                v[5] = fmaf(free_a ? G : 0.0f, dal, v[5]);
+            }
+            if (__any_sync(0xffffffffu, contrib)) {
+                const float tot = warp_reduce16(v);
+                const int comp = lane >> 1;
+                if ((lane & 1) == 0 && comp < ncomp) atomicAdd(acc + j * kGrad2d + comp, tot);
+            }
+        }
+        __syncthreads();
+        // flush this batch's sums: one global atomic per (Gaussian, component, tile)
+        for (int i = threadIdx.x; i < kGrad2d * cnt; i += blockDim.x) {
+            const float a = acc[i];
+            if (a != 0.0f) {
+                const int j = i / kGrad2d;
+                atomicAdd(grad2d + (size_t)cur_ids[j] * kGrad2d + (i - j * kGrad2d), a);
+                acc[i] = 0.0f;
+            }
+        }
         __syncthreads();
     }
+}
+
+template <int PPT>
+__global__ void k_render_bwd(ViewTable vt, const uint32_t* __restrict__ ranges,
+                             const uint32_t* __restrict__ ivals, const float4* __restrict__ rec,
+                             int batch, float bg0, float bg1, float bg2,
+                             const float* __restrict__ final_T, const int32_t* __restrict__ last_idx,
+                             const float* __restrict__ dL, float* __restrict__ grad2d) {
+    extern __shared__ float4 smem[];
+    __shared__ int s_maxlast;
+    const TileCtx tc = tile_ctx(vt, ranges, blockIdx.x);
+    const float bg[3] = {bg0, bg1, bg2};
+    if (tc.channels == 3)
+        render_bwd_tile<3, PPT>(vt, tc, ivals, rec, smem, &s_maxlast, batch, bg, final_T,
+                                last_idx, dL, grad2d);
+    else
+        render_bwd_tile<1, PPT>(vt, tc, ivals, rec, smem, &s_maxlast, batch, bg, final_T,
+                                last_idx, dL, grad2d);
 }
 
 }  // namespace
@@ -344,12 +456,19 @@ __global__ void k_render_bwd(ViewTable vt, const uint32_t* __restrict__ ranges,
 gs_status launch_project_bwd(const Plan* p, const gs_map* map, const gs_view* views_dev,
                              void* ws, const gs_map_grad* grads, int accumulate, cudaStream_t st);
 
+template <typename K1, typename K2, typename K4, typename K8>
+static K1 pick(int ppt, K1 a, K2 b, K4 c, K8 d) {
+    return ppt == 1 ? a : ppt == 2 ? b : ppt == 4 ? c : d;
+}
+
 gs_status launch_render_fwd(const Plan* p, const void* ws, float* images, float* final_T,
                             int32_t* last_idx, cudaStream_t st) {
     const int batch = p->cfg.smem_batch;
-    const size_t smem = (size_t)2 * 3 * batch * sizeof(float4);
-    const int threads = p->cfg.tile_w * p->cfg.tile_h;
-    k_render_fwd<<<p->total_tiles, threads, smem, st>>>(
+    const int ppt = p->cfg.pixels_per_thread;
+    const size_t smem = (size_t)2 * 3 * batch * sizeof(float4) + 2 * batch * sizeof(uint32_t);
+    const int threads = p->cfg.tile_w * p->cfg.tile_h / ppt;
+    auto kern = pick(ppt, k_render_fwd<1>, k_render_fwd<2>, k_render_fwd<4>, k_render_fwd<8>);
+    kern<<<p->total_tiles, threads, smem, st>>>(
         p->vt, cbuf<uint32_t>(p, ws, GS_BUF_RANGES),
         cbuf<uint32_t>(p, ws, (p->tile_passes & 1) ? (int)B_IVAL_B : (int)GS_BUF_TILE_VALUES),
         cbuf<float4>(p, ws, GS_BUF_PROJ), batch, p->cfg.bg[0], p->cfg.bg[1], p->cfg.bg[2], images,
@@ -362,12 +481,15 @@ gs_status launch_render_bwd(const Plan* p, const gs_map* map, const gs_view* vie
                             const float* dL, const gs_map_grad* grads, int32_t accumulate,
                             cudaStream_t st) {
     const int batch = p->cfg.smem_batch;
-    const size_t smem = (size_t)2 * 3 * batch * sizeof(float4) + 2 * batch * sizeof(uint32_t);
-    const int threads = p->cfg.tile_w * p->cfg.tile_h;
+    const int ppt = p->cfg.pixels_per_thread;
+    const size_t smem = (size_t)2 * 3 * batch * sizeof(float4) + 4 * batch * sizeof(uint32_t) +
+                        (size_t)kGrad2d * batch * sizeof(float);
+    const int threads = p->cfg.tile_w * p->cfg.tile_h / ppt;
     float* grad2d = buf<float>(p, ws, GS_BUF_GRAD2D);
     const size_t g2bytes = (size_t)p->vt.n_views * map->n * kGrad2d * sizeof(float);
     if (cudaMemsetAsync(grad2d, 0, g2bytes, st) != cudaSuccess) return GS_ERR_CUDA;
-    k_render_bwd<<<p->total_tiles, threads, smem, st>>>(
+    auto kern = pick(ppt, k_render_bwd<1>, k_render_bwd<2>, k_render_bwd<4>, k_render_bwd<8>);
+    kern<<<p->total_tiles, threads, smem, st>>>(
         p->vt, cbuf<uint32_t>(p, ws, GS_BUF_RANGES),
         cbuf<uint32_t>(p, ws, (p->tile_passes & 1) ? (int)B_IVAL_B : (int)GS_BUF_TILE_VALUES),
         cbuf<float4>(p, ws, GS_BUF_PROJ), batch, p->cfg.bg[0], p->cfg.bg[1], p->cfg.bg[2],
