@@ -10,7 +10,7 @@ target rendered from a perturbed copy of the map.  Inputs are resident in HBM
 for `value`; `e2e` adds, per step, the pinned-host -> device copy of the
 step's target image and pose and the device -> host read of the loss.
 
-The timed region replays the iteration as six CUDA graphs (one per stage)
+The timed region replays the iteration as seven CUDA graphs (one per stage)
 with CUDA events between them on the launching stream, so every stage's
 device time comes from the timed region itself.  The working set (map,
 gradients, Adam moments: ~0.95 GB, plus the workspace) is far larger than the
@@ -293,7 +293,8 @@ def run_gpu(args, ws, rank, local):
         ("bin_sort", lambda: rast.bin_sort(gm.n)),
         ("render_fwd", lambda: rast.render_fwd()),
         ("loss_l1_ssim", lambda: rast.loss_l1_ssim(step.targets, lam)),
-        ("render_bwd", lambda: rast.render_bwd(m, g)),
+        ("render_bwd", lambda: rast.render_bwd_pixels()),
+        ("project_bwd", lambda: rast.project_bwd(m, g)),
         ("adam", lambda: gm.adam_step()),
     ]
     # warm-up (eager), then capture one graph per stage
@@ -379,6 +380,7 @@ def run_gpu(args, ws, rank, local):
         bin_sort=n * 4 * 16 + n * 12 + instances * 8 + tile_passes(rast.total_tiles) * instances * 16
         + instances * 4 + rast.total_tiles * 8,
         loss_l1_ssim=rast.total_values * 44,
+        project_bwd=n * 2 * (4 * (11 + 3 * K_sh)) + n * (36 + 4),
         adam=n_floats * 28,
     )
     dominant = max(stage_ms, key=stage_ms.get)

@@ -211,11 +211,26 @@ gs_status gs_loss_l1_ssim(const gs_plan *plan, const float *images, const float 
  * from last_idx, recovering T_i = T_{i+1} / (1 - alpha_i) from final_T,
  * reduces each Gaussian's screen-space gradient over a warp with shuffles and
  * adds it atomically; the projection adjoint then maps it to the parameter
- * gradients, summed over views.  accumulate = 0 overwrites grads, 1 adds. */
+ * gradients, summed over views.  accumulate = 0 overwrites grads, 1 adds.
+ * Equivalent to gs_render_bwd_pixels followed by gs_project_bwd. */
 gs_status gs_render_bwd(const gs_plan *plan, const gs_map *map, const gs_view *views_dev,
                         void *ws, const float *final_T, const int32_t *last_idx,
                         const float *dL_dimages, const gs_map_grad *grads, int32_t accumulate,
                         void *stream);
+
+/* A7 alone: the pixel adjoint of gs_render_bwd, leaving the per-view
+ * screen-space gradients (dmean2d, dconic, dopacity, dcolour) in the
+ * workspace buffer GS_BUF_GRAD2D (zeroed first). */
+gs_status gs_render_bwd_pixels(const gs_plan *plan, void *ws, const float *final_T,
+                               const int32_t *last_idx, const float *dL_dimages, void *stream);
+
+/* A8 alone: the projection adjoint of gs_render_bwd, mapping the
+ * screen-space gradients in GS_BUF_GRAD2D to parameter gradients summed over
+ * the plan's views (accumulate = 0 overwrites grads, 1 adds).  The map and
+ * views must be those of the preceding gs_project. */
+gs_status gs_project_bwd(const gs_plan *plan, const gs_map *map, const gs_view *views_dev,
+                         const void *ws, const gs_map_grad *grads, int32_t accumulate,
+                         void *stream);
 
 /* A9: Adam (paper Sec. IV-A, default 3DGS optimiser) over one contiguous
  * parameter buffer of n_floats split into n_groups contiguous groups:

@@ -73,6 +73,10 @@ _SIGNATURES = {
                                   c_void_p, c_void_p, c_void_p]),
     "gs_render_bwd": (c_int32, [_P(gs_plan), _P(gs_map), c_void_p, c_void_p, c_void_p, c_void_p,
                                 c_void_p, _P(gs_map_grad), c_int32, c_void_p]),
+    "gs_render_bwd_pixels": (c_int32, [_P(gs_plan), c_void_p, c_void_p, c_void_p, c_void_p,
+                                       c_void_p]),
+    "gs_project_bwd": (c_int32, [_P(gs_plan), _P(gs_map), c_void_p, c_void_p, _P(gs_map_grad),
+                                 c_int32, c_void_p]),
     "gs_adam_step": (c_int32, [c_void_p, c_void_p, c_void_p, c_void_p, c_int64, c_int32,
                                _P(c_int64), _P(c_float), c_float, c_float, c_float, c_void_p,
                                c_void_p]),
@@ -193,6 +197,18 @@ def gs_render_bwd(plan, gmap: gs_map, views_dev, ws, final_T, last_idx, dL_dimag
                               _ptr(final_T), _ptr(last_idx), _ptr(dL_dimages),
                               ctypes.byref(grads), 1 if accumulate else 0, _stream(stream)),
           "gs_render_bwd")
+
+
+def gs_render_bwd_pixels(plan, ws, final_T, last_idx, dL_dimages, stream=None):
+    check(lib().gs_render_bwd_pixels(ctypes.byref(plan), _ptr(ws), _ptr(final_T), _ptr(last_idx),
+                                     _ptr(dL_dimages), _stream(stream)), "gs_render_bwd_pixels")
+
+
+def gs_project_bwd(plan, gmap: gs_map, views_dev, ws, grads: gs_map_grad, accumulate=False,
+                   stream=None):
+    check(lib().gs_project_bwd(ctypes.byref(plan), ctypes.byref(gmap), _ptr(views_dev), _ptr(ws),
+                               ctypes.byref(grads), 1 if accumulate else 0, _stream(stream)),
+          "gs_project_bwd")
 
 
 def gs_adam_step(params, grads, m, v, group_offsets, group_lr, beta1, beta2, eps, step_dev,

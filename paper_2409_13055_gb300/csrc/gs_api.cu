@@ -214,6 +214,25 @@ extern "C" gs_status gs_render_bwd(const gs_plan* plan, const gs_map* map,
                              accumulate ? 1 : 0, S(stream));
 }
 
+extern "C" gs_status gs_render_bwd_pixels(const gs_plan* plan, void* ws, const float* final_T,
+                                          const int32_t* last_idx, const float* dL_dimages,
+                                          void* stream) {
+    if (!plan_ok(plan) || !ws || !final_T || !last_idx || !dL_dimages) return GS_ERR_INVALID;
+    return launch_render_bwd_pixels(P(plan), ws, final_T, last_idx, dL_dimages, S(stream));
+}
+
+extern "C" gs_status gs_project_bwd(const gs_plan* plan, const gs_map* map,
+                                    const gs_view* views_dev, const void* ws,
+                                    const gs_map_grad* grads, int32_t accumulate, void* stream) {
+    if (!plan_ok(plan) || !views_dev || !ws || !grads) return GS_ERR_INVALID;
+    if (!map_ok(P(plan), map)) return GS_ERR_INVALID;
+    if (!grads->means || !grads->log_scales || !grads->quats || !grads->opacity_logits ||
+        !grads->sh)
+        return GS_ERR_INVALID;
+    return launch_project_bwd(P(plan), map, views_dev, const_cast<void*>(ws), grads,
+                              accumulate ? 1 : 0, S(stream));
+}
+
 extern "C" gs_status gs_adam_step(float* params, const float* grads, float* m, float* v,
                                   int64_t n_floats, int32_t n_groups,
                                   const int64_t* group_offsets_host, const float* group_lr_host,

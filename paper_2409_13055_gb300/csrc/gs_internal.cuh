@@ -194,6 +194,10 @@ gs_status launch_render_bwd(const Plan* p, const gs_map* map, const gs_view* vie
                             void* ws, const float* final_T, const int32_t* last_idx,
                             const float* dL, const gs_map_grad* grads, int32_t accumulate,
                             cudaStream_t st);
+gs_status launch_render_bwd_pixels(const Plan* p, void* ws, const float* final_T,
+                                   const int32_t* last_idx, const float* dL, cudaStream_t st);
+gs_status launch_project_bwd(const Plan* p, const gs_map* map, const gs_view* views_dev,
+                             void* ws, const gs_map_grad* grads, int accumulate, cudaStream_t st);
 gs_status launch_adam(float* params, const float* grads, float* m, float* v, int64_t n,
                       int32_t n_groups, const int64_t* offs, const float* lrs, float b1,
                       float b2, float eps, int32_t* step_dev, cudaStream_t st);

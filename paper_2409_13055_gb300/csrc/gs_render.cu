@@ -453,9 +453,6 @@ __global__ void k_render_bwd(ViewTable vt, const uint32_t* __restrict__ ranges,
 
 }  // namespace
 
-gs_status launch_project_bwd(const Plan* p, const gs_map* map, const gs_view* views_dev,
-                             void* ws, const gs_map_grad* grads, int accumulate, cudaStream_t st);
-
 template <typename K1, typename K2, typename K4, typename K8>
 static K1 pick(int ppt, K1 a, K2 b, K4 c, K8 d) {
     return ppt == 1 ? a : ppt == 2 ? b : ppt == 4 ? c : d;
@@ -476,25 +473,29 @@ gs_status launch_render_fwd(const Plan* p, const void* ws, float* images, float*
     return launch_status();
 }
 
-gs_status launch_render_bwd(const Plan* p, const gs_map* map, const gs_view* views_dev,
-                            void* ws, const float* final_T, const int32_t* last_idx,
-                            const float* dL, const gs_map_grad* grads, int32_t accumulate,
-                            cudaStream_t st) {
+gs_status launch_render_bwd_pixels(const Plan* p, void* ws, const float* final_T,
+                                   const int32_t* last_idx, const float* dL, cudaStream_t st) {
     const int batch = p->cfg.smem_batch;
     const int ppt = p->cfg.pixels_per_thread;
     const size_t smem = (size_t)2 * 3 * batch * sizeof(float4) + 4 * batch * sizeof(uint32_t) +
                         (size_t)kGrad2d * batch * sizeof(float);
     const int threads = p->cfg.tile_w * p->cfg.tile_h / ppt;
     float* grad2d = buf<float>(p, ws, GS_BUF_GRAD2D);
-    const size_t g2bytes = (size_t)p->vt.n_views * map->n * kGrad2d * sizeof(float);
-    if (cudaMemsetAsync(grad2d, 0, g2bytes, st) != cudaSuccess) return GS_ERR_CUDA;
+    if (cudaMemsetAsync(grad2d, 0, p->len[GS_BUF_GRAD2D], st) != cudaSuccess) return GS_ERR_CUDA;
     auto kern = pick(ppt, k_render_bwd<1>, k_render_bwd<2>, k_render_bwd<4>, k_render_bwd<8>);
     kern<<<p->total_tiles, threads, smem, st>>>(
         p->vt, cbuf<uint32_t>(p, ws, GS_BUF_RANGES),
         cbuf<uint32_t>(p, ws, (p->tile_passes & 1) ? (int)B_IVAL_B : (int)GS_BUF_TILE_VALUES),
         cbuf<float4>(p, ws, GS_BUF_PROJ), batch, p->cfg.bg[0], p->cfg.bg[1], p->cfg.bg[2],
         final_T, last_idx, dL, grad2d);
-    gs_status s = launch_status();
+    return launch_status();
+}
+
+gs_status launch_render_bwd(const Plan* p, const gs_map* map, const gs_view* views_dev,
+                            void* ws, const float* final_T, const int32_t* last_idx,
+                            const float* dL, const gs_map_grad* grads, int32_t accumulate,
+                            cudaStream_t st) {
+    gs_status s = launch_render_bwd_pixels(p, ws, final_T, last_idx, dL, st);
     if (s != GS_OK) return s;
     return launch_project_bwd(p, map, views_dev, ws, grads, accumulate, st);
 }

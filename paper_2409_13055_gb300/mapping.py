@@ -230,6 +230,14 @@ class Rasterizer:
                         self.last_idx if last_idx is None else last_idx,
                         self.dL if dL is None else dL, grads, accumulate, stream)
 
+    def render_bwd_pixels(self, dL=None, final_T=None, last_idx=None, stream=None):
+        B.gs_render_bwd_pixels(self.plan, self.ws, self.final_T if final_T is None else final_T,
+                               self.last_idx if last_idx is None else last_idx,
+                               self.dL if dL is None else dL, stream)
+
+    def project_bwd(self, gmap: B.gs_map, grads: B.gs_map_grad, accumulate=False, stream=None):
+        B.gs_project_bwd(self.plan, gmap, self.views_dev, self.ws, grads, accumulate, stream)
+
     def counters(self, stream=None) -> B.gs_counters:
         return B.gs_read_counters(self.plan, self.ws, stream)
 

@@ -293,6 +293,33 @@ def test_backward_parity(case):
         assert U.rel_l2(a, b) <= GRAD_TOL, (k, U.rel_l2(a, b))
 
 
+def test_split_backward_equals_combined():
+    """gs_render_bwd_pixels followed by gs_project_bwd equals gs_render_bwd
+    (up to the order of the float atomics), and accumulate = 1 adds."""
+    p, view = CASES["tiny_sh3_posed"]()
+    target = scenes.random_target(view, 41)
+    out = []
+    for split in (False, True):
+        gm = mapping.GaussianMap(p)
+        rast = mapping.Rasterizer([view], gm.n, instance_capacity=1 << 18)
+        m, g = gm.gs_map(), gm.gs_map_grad()
+        rast.forward(m)
+        rast.loss_l1_ssim(rast.pack([target]), 0.2)
+        if split:
+            rast.render_bwd_pixels()
+            rast.project_bwd(m, g, accumulate=False)
+        else:
+            rast.render_bwd(m, g)
+        torch.cuda.synchronize()
+        out.append(gm.grad.clone().cpu().numpy())
+        if split:
+            rast.project_bwd(m, g, accumulate=True)
+            torch.cuda.synchronize()
+            twice = gm.grad.clone().cpu().numpy()
+    assert U.rel_l2(out[1], out[0]) < 1e-5
+    assert U.rel_l2(twice, 2.0 * out[1]) < 1e-6
+
+
 def test_adam_parity():
     rng = np.random.default_rng(8)
     n = 100_003  # ragged: not a multiple of the float4 width
