@@ -124,13 +124,23 @@ def dist_setup():
 
 
 def reduce_max(x, ws):
+    """Max of a float over the ranks of the default process group."""
     if ws == 1:
         return x
     import torch
     import torch.distributed as dist
-    t = torch.tensor([x], dtype=torch.float64, device="cuda")
+    dev = "cpu" if dist.get_backend() == "gloo" else "cuda"
+    t = torch.tensor([x], dtype=torch.float64, device=dev)
     dist.all_reduce(t, op=dist.ReduceOp.MAX)
     return float(t.item())
+
+
+def replica_throughput(local_ms, steps, ws):
+    """Whole-job iterations/s of `ws` independent replicas, each timing `steps`
+    iterations in `local_ms`: all ranks' iterations over the slowest rank's
+    time.  Returns (value, max_ms)."""
+    max_ms = reduce_max(local_ms, ws)
+    return ws * steps / (max_ms / 1e3), max_ms
 
 
 def barrier(ws):
@@ -342,9 +352,8 @@ def run_gpu(args, ws, rank, local):
     total_ms = ev[0][0].elapsed_time(ev[K - 1][len(graphs)])
     stage_ms = {name: float(np.mean([ev[k][j].elapsed_time(ev[k][j + 1]) for k in range(K)]))
                 for j, (name, _) in enumerate(graphs)}
-    total_ms = reduce_max(total_ms, ws)
+    value, total_ms = replica_throughput(total_ms, K, ws)
     ms_step = total_ms / K
-    value = ws * K / (total_ms / 1e3)
     status = rast.counters()
     assert status.status == 0, f"device status {status.status}"
 
