@@ -218,6 +218,32 @@ gs_status gs_render_bwd(const gs_plan *plan, const gs_map *map, const gs_view *v
                         const float *dL_dimages, const gs_map_grad *grads, int32_t accumulate,
                         void *stream);
 
+/* gs_loss_l1_ssim without a workspace, for callers that cannot allocate
+ * device memory: code that runs where cudaMalloc is unavailable or forbidden
+ * (inside a fixed, pre-reserved memory budget, a host callback, or a real-time
+ * thread that must not block on the allocator) and that has no workspace of
+ * its own to lend.  The paper has no counterpart to this entry point.
+ *
+ * Same arguments, arithmetic and results as gs_loss_l1_ssim, minus ws: its
+ * scratch (SSIM partial maps, per-block loss partials, a reduction ticket) is
+ * a fixed array compiled into the library, about 12.6 MB, which every GPU
+ * that loads the library holds until the process exits.  Limits: the plan's
+ * images may hold at most 2^20 values in total (sum of C*H*W; e.g. one
+ * 640x480 RGB view) and at most 8192 loss tiles of 32x16; larger plans are
+ * rejected with GS_ERR_CAPACITY before anything is enqueued.  Nothing is
+ * allocated, by this call or any library routine it uses.
+ *
+ * The first call on a device looks up the array's device address
+ * (cudaGetSymbolAddress, with that device current) and caches it; make that
+ * first call before any stream capture.  All calls share the one array and
+ * it keeps the last call's contents (the ticket is cleared at the start of
+ * every call): calls that overlap on the GPU -- on different streams, or from
+ * several threads -- race on the scratch and corrupt each other's results;
+ * order them on one stream. */
+gs_status gs_loss_l1_ssim_noalloc(const gs_plan *plan, const float *images, const float *targets,
+                                  float lambda, float view_weight, float *loss_dev,
+                                  float *dL_dimages, void *stream);
+
 /* A7 alone: the pixel adjoint of gs_render_bwd, leaving the per-view
  * screen-space gradients (dmean2d, dconic, dopacity, dcolour) in the
  * workspace buffer GS_BUF_GRAD2D (zeroed first). */

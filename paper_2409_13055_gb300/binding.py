@@ -73,6 +73,8 @@ _SIGNATURES = {
                                   c_void_p, c_void_p, c_void_p]),
     "gs_render_bwd": (c_int32, [_P(gs_plan), _P(gs_map), c_void_p, c_void_p, c_void_p, c_void_p,
                                 c_void_p, _P(gs_map_grad), c_int32, c_void_p]),
+    "gs_loss_l1_ssim_noalloc": (c_int32, [_P(gs_plan), c_void_p, c_void_p, c_float, c_float,
+                                          c_void_p, c_void_p, c_void_p]),
     "gs_render_bwd_pixels": (c_int32, [_P(gs_plan), c_void_p, c_void_p, c_void_p, c_void_p,
                                        c_void_p]),
     "gs_project_bwd": (c_int32, [_P(gs_plan), _P(gs_map), c_void_p, c_void_p, _P(gs_map_grad),
@@ -197,6 +199,15 @@ def gs_render_bwd(plan, gmap: gs_map, views_dev, ws, final_T, last_idx, dL_dimag
                               _ptr(final_T), _ptr(last_idx), _ptr(dL_dimages),
                               ctypes.byref(grads), 1 if accumulate else 0, _stream(stream)),
           "gs_render_bwd")
+
+
+def gs_loss_l1_ssim_noalloc(plan, images, targets, lam, view_weight, loss_dev, dL_dimages,
+                            stream=None):
+    """gs_loss_l1_ssim with the library's fixed scratch instead of a workspace;
+    returns the raw status so callers can see GS_ERR_CAPACITY."""
+    return lib().gs_loss_l1_ssim_noalloc(ctypes.byref(plan), _ptr(images), _ptr(targets),
+                                         float(lam), float(view_weight), _ptr(loss_dev),
+                                         _ptr(dL_dimages), _stream(stream))
 
 
 def gs_render_bwd_pixels(plan, ws, final_T, last_idx, dL_dimages, stream=None):

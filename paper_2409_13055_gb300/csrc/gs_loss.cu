@@ -18,6 +18,8 @@
 // order by whichever block finishes last (a ticket counter, no waiting).
 #include <math.h>
 
+#include <mutex>
+
 #include "gs_internal.cuh"
 
 namespace gs {
@@ -225,6 +227,18 @@ k_ssim_bwd(ViewTable vt, Win win, const float* __restrict__ img, const float* __
 
 }  // namespace
 
+static Win loss_window() {
+    Win win;
+    double g[kWin], s = 0.0;
+    for (int k = 0; k < kWin; ++k) {
+        const double d = k - kHalo;
+        g[k] = exp(-d * d / (2.0 * 1.5 * 1.5));
+        s += g[k];
+    }
+    for (int k = 0; k < kWin; ++k) win.w[k] = (float)(g[k] / s);
+    return win;
+}
+
 gs_status launch_loss(const Plan* p, const float* images, const float* targets, float lambda,
                       float view_weight, float* loss_dev, float* dL, void* ws, cudaStream_t st) {
     Win win;
@@ -248,3 +262,77 @@ gs_status launch_loss(const Plan* p, const float* images, const float* targets, 
 }
 
 }  // namespace gs
+
+// ---------------------------------------------------------------------------
+// gs_loss_l1_ssim_noalloc: the same loss for callers that cannot allocate
+// device memory, with its scratch in a fixed array compiled into this library.
+// ---------------------------------------------------------------------------
+namespace gs {
+namespace {
+
+constexpr size_t kNoAllocMaxValues = size_t(1) << 20;  // image values (C*H*W over all views)
+constexpr int kNoAllocMaxBlocks = 8192;                // 32x16 loss tiles over all planes
+constexpr size_t kNoAllocPartialsOffset = 256;         // after the counters
+constexpr size_t kNoAllocMapsOffset =
+    kNoAllocPartialsOffset + ((size_t(kNoAllocMaxBlocks + 1) * 2 * sizeof(float) + 255) & ~size_t(255));
+constexpr size_t kNoAllocBytes = kNoAllocMapsOffset + 3 * kNoAllocMaxValues * sizeof(float);
+
+// Scratch of gs_loss_l1_ssim_noalloc: counters (ticket of the loss reduction)
+// | per-block loss partials | the three SSIM partial-derivative maps.  About
+// 12.6 MB, held on every GPU that loads the library until the process exits.
+static __device__ __align__(256) unsigned char g_noalloc_scratch[kNoAllocBytes];
+
+std::mutex g_noalloc_mutex;
+void* g_noalloc_addr[GS_MAX_VIEWS] = {nullptr};  // per device ordinal
+
+// Device address of the scratch array on the current device.  In host code
+// the array's name is only a host-side stand-in, so the address is looked up
+// with cudaGetSymbolAddress once per device (the device must be current).
+gs_status noalloc_scratch(void** out) {
+    int dev = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess) return GS_ERR_CUDA;
+    if (dev < 0 || dev >= GS_MAX_VIEWS) return GS_ERR_UNSUPPORTED;
+    std::lock_guard<std::mutex> lock(g_noalloc_mutex);
+    if (g_noalloc_addr[dev] == nullptr) {
+        void* p = nullptr;
+        if (cudaGetSymbolAddress(&p, g_noalloc_scratch) != cudaSuccess || p == nullptr)
+            return GS_ERR_CUDA;
+        g_noalloc_addr[dev] = p;
+    }
+    *out = g_noalloc_addr[dev];
+    return GS_OK;
+}
+
+}  // namespace
+}  // namespace gs
+
+extern "C" gs_status gs_loss_l1_ssim_noalloc(const gs_plan* plan, const float* images,
+                                             const float* targets, float lambda, float view_weight,
+                                             float* loss_dev, float* dL_dimages, void* stream) {
+    using namespace gs;
+    if (!plan || P(plan)->magic != kPlanMagic || !images || !targets || !loss_dev || !dL_dimages)
+        return GS_ERR_INVALID;
+    if (!(lambda >= 0.0f && lambda <= 1.0f) || !(view_weight > 0.0f)) return GS_ERR_INVALID;
+    const Plan* p = P(plan);
+    // sizes are checked before anything touches the GPU
+    if ((size_t)p->total_values > kNoAllocMaxValues || p->loss_blocks > kNoAllocMaxBlocks)
+        return GS_ERR_CAPACITY;
+    void* scratch = nullptr;
+    gs_status s = noalloc_scratch(&scratch);
+    if (s != GS_OK) return s;
+    cudaStream_t st = S(stream);
+    char* base = static_cast<char*>(scratch);
+    DevCounters* ctr = reinterpret_cast<DevCounters*>(base);
+    float* partials = reinterpret_cast<float*>(base + kNoAllocPartialsOffset);
+    float* maps = reinterpret_cast<float*>(base + kNoAllocMapsOffset);
+    // the array keeps whatever the last call left: the ticket must start at zero
+    if (cudaMemsetAsync(ctr, 0, sizeof(DevCounters), st) != cudaSuccess) return GS_ERR_CUDA;
+    const Win win = loss_window();
+    k_ssim_fwd<<<p->loss_blocks, kLossThreads, 0, st>>>(p->vt, win, images, targets, lambda,
+                                                        view_weight, p->total_values, maps,
+                                                        partials, p->loss_blocks, ctr, loss_dev);
+    k_ssim_bwd<<<p->loss_blocks, kLossThreads, 0, st>>>(p->vt, win, images, targets, lambda,
+                                                        view_weight, p->total_values, maps,
+                                                        dL_dimages);
+    return launch_status();
+}
