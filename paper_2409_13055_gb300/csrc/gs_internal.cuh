@@ -49,6 +49,8 @@ enum PrivBuf {
     B_IVAL_B,
     B_LOSS_MAPS,
     B_LOSS_BLOCKS,
+    B_GCOL,     // [V*n] x 3: colour gradient as it reaches the SH coefficients
+    B_OFFSETS,  // [V*n + 1] instance offsets of the entries in depth order
     B_TOTAL
 };
 

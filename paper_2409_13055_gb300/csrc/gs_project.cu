@@ -317,9 +317,9 @@ k_project_bwd(const float* __restrict__ means, const float* __restrict__ log_sca
               const float* __restrict__ quats, const float* __restrict__ opacity_logits,
               const float* __restrict__ sh, int n, const gs_view* __restrict__ views,
               ViewTable vt, float near_z, const uint32_t* __restrict__ touched,
-              const float* __restrict__ grad2d, float* __restrict__ g_means,
-              float* __restrict__ g_ls, float* __restrict__ g_quats, float* __restrict__ g_logit,
-              float* __restrict__ g_sh, int accumulate) {
+              const float* __restrict__ grad2d, float* __restrict__ gcol_out,
+              float* __restrict__ g_means, float* __restrict__ g_ls, float* __restrict__ g_quats,
+              float* __restrict__ g_logit, int accumulate) {
     extern __shared__ Cam cam_all[];
     for (int v = threadIdx.x; v < vt.n_views; v += blockDim.x) load_cam(views[v], cam_all[v]);
     __syncthreads();
@@ -338,9 +338,6 @@ k_project_bwd(const float* __restrict__ means, const float* __restrict__ log_sca
     float gm[3] = {0.f, 0.f, 0.f};
     float gsig[6] = {0.f, 0.f, 0.f, 0.f, 0.f, 0.f};  // dL/dSigma as a symmetric matrix
     float gop = 0.0f;
-    float gshc[K][3];
-#pragma unroll
-    for (int k = 0; k < K; ++k) gshc[k][0] = gshc[k][1] = gshc[k][2] = 0.0f;
 
     for (int v = 0; v < vt.n_views; ++v) {
         const size_t vg = (size_t)v * n + g;
@@ -353,7 +350,11 @@ k_project_bwd(const float* __restrict__ means, const float* __restrict__ log_sca
         const Cam& cam = cam_all[v];
         Proj p;
         project_one(mean, shp, cam, near_z, vt.log2_tw, vt.log2_th, geo.tiles_x, geo.tiles_y, p);
-        if (!p.visible) continue;
+        float* gc_out = gcol_out + vg * 3;
+        if (!p.visible) {
+            gc_out[0] = gc_out[1] = gc_out[2] = 0.0f;
+            continue;
+        }
 
         gop += gO;
         // colour -> SH coefficients and the viewing direction
@@ -371,15 +372,17 @@ k_project_bwd(const float* __restrict__ means, const float* __restrict__ log_sca
 #pragma unroll
         for (int ch = 0; ch < 3; ++ch)
             if (col[ch] + 0.5f < 0.0f) gcol[ch] = 0.0f;
+        // the SH coefficients' own gradient, Y_k(dir) gcol, is formed by
+        // k_sh_bwd from this masked colour gradient
+        gc_out[0] = gcol[0];
+        gc_out[1] = gcol[1];
+        gc_out[2] = gcol[2];
         float w[16];
 #pragma unroll
         for (int k = 0; k < 16; ++k) w[k] = 0.0f;
 #pragma unroll
         for (int k = 0; k < K; ++k) {
             const float* c = sh + ((size_t)k * n + g) * 3;
-            gshc[k][0] += Y[k] * gcol[0];
-            gshc[k][1] += Y[k] * gcol[1];
-            gshc[k][2] += Y[k] * gcol[2];
             w[k] = gcol[0] * c[0] + gcol[1] * c[1] + gcol[2] * c[2];
         }
         float gd[3] = {0.f, 0.f, 0.f};
@@ -488,9 +491,6 @@ k_project_bwd(const float* __restrict__ means, const float* __restrict__ log_sca
         o.x += gq4.x; o.y += gq4.y; o.z += gq4.z; o.w += gq4.w;
         reinterpret_cast<float4*>(g_quats)[g] = o;
         g_logit[g] += glog;
-#pragma unroll
-        for (int k = 0; k < K; ++k)
-            for (int ch = 0; ch < 3; ++ch) g_sh[((size_t)k * n + g) * 3 + ch] += gshc[k][ch];
     } else {
         for (int e = 0; e < 3; ++e) {
             g_means[3 * g + e] = gm[e];
@@ -498,9 +498,57 @@ k_project_bwd(const float* __restrict__ means, const float* __restrict__ log_sca
         }
         reinterpret_cast<float4*>(g_quats)[g] = gq4;
         g_logit[g] = glog;
+    }
+}
+
+// Gradient of the SH coefficients: sum over views of Y_k(dir_v) gcol_v, with
+// gcol the colour gradient k_project_bwd left (zero on clamped channels, a
+// grayscale view's gradient spread over the three channels).
+template <int DEG>
+__global__ void __launch_bounds__(kProjThreads)
+k_sh_bwd(const float* __restrict__ means, int n, const gs_view* __restrict__ views, ViewTable vt,
+         const uint32_t* __restrict__ touched, const float* __restrict__ gcol_in,
+         float* __restrict__ g_sh, int accumulate) {
+    extern __shared__ Cam cam_all[];
+    for (int v = threadIdx.x; v < vt.n_views; v += blockDim.x) load_cam(views[v], cam_all[v]);
+    __syncthreads();
+    const int g = blockIdx.x * blockDim.x + threadIdx.x;
+    if (g >= n) return;
+    constexpr int K = (DEG + 1) * (DEG + 1);
+    const float mean[3] = {means[3 * g], means[3 * g + 1], means[3 * g + 2]};
+    float acc[K][3];
 #pragma unroll
-        for (int k = 0; k < K; ++k)
-            for (int ch = 0; ch < 3; ++ch) g_sh[((size_t)k * n + g) * 3 + ch] = gshc[k][ch];
+    for (int k = 0; k < K; ++k) acc[k][0] = acc[k][1] = acc[k][2] = 0.0f;
+    for (int v = 0; v < vt.n_views; ++v) {
+        const size_t vg = (size_t)v * n + g;
+        if (touched[vg] == 0u) continue;
+        const float* gc = gcol_in + vg * 3;
+        const float c0 = gc[0], c1 = gc[1], c2 = gc[2];
+        const Cam& cam = cam_all[v];
+        const float d0 = mean[0] - cam.cc[0], d1 = mean[1] - cam.cc[1], d2 = mean[2] - cam.cc[2];
+        const float dist = sqrtf(d0 * d0 + d1 * d1 + d2 * d2);
+        const float id = dist > 0.0f ? 1.0f / dist : 0.0f;
+        float Y[16];
+        sh_eval(DEG, d0 * id, d1 * id, d2 * id, Y);
+#pragma unroll
+        for (int k = 0; k < K; ++k) {
+            acc[k][0] = fmaf(Y[k], c0, acc[k][0]);
+            acc[k][1] = fmaf(Y[k], c1, acc[k][1]);
+            acc[k][2] = fmaf(Y[k], c2, acc[k][2]);
+        }
+    }
+#pragma unroll
+    for (int k = 0; k < K; ++k) {
+        float* o = g_sh + ((size_t)k * n + g) * 3;
+        if (accumulate) {
+            o[0] += acc[k][0];
+            o[1] += acc[k][1];
+            o[2] += acc[k][2];
+        } else {
+            o[0] = acc[k][0];
+            o[1] = acc[k][1];
+            o[2] = acc[k][2];
+        }
     }
 }
 
@@ -532,15 +580,23 @@ gs_status launch_project_bwd(const Plan* p, const gs_map* map, const gs_view* vi
     if (reinterpret_cast<uintptr_t>(grads->quats) % 16) return GS_ERR_INVALID;
     const int n = map->n;
     const size_t smem = sizeof(Cam) * p->vt.n_views;
+    const int blocks = (n + kProjThreads - 1) / kProjThreads;
+    float* gcol = buf<float>(p, ws, B_GCOL);
+    const uint32_t* touched = buf<uint32_t>(p, ws, GS_BUF_TOUCHED);
     auto* kern = map->sh_degree == 0   ? k_project_bwd<0>
                  : map->sh_degree == 1 ? k_project_bwd<1>
                  : map->sh_degree == 2 ? k_project_bwd<2>
                                        : k_project_bwd<3>;
-    kern<<<(n + kProjThreads - 1) / kProjThreads, kProjThreads, smem, st>>>(
+    kern<<<blocks, kProjThreads, smem, st>>>(
         map->means, map->log_scales, map->quats, map->opacity_logits, map->sh, n, views_dev,
-        p->vt, p->cfg.near_z, buf<uint32_t>(p, ws, GS_BUF_TOUCHED),
-        buf<float>(p, ws, GS_BUF_GRAD2D), grads->means, grads->log_scales, grads->quats,
-        grads->opacity_logits, grads->sh, accumulate);
+        p->vt, p->cfg.near_z, touched, buf<float>(p, ws, GS_BUF_GRAD2D), gcol, grads->means,
+        grads->log_scales, grads->quats, grads->opacity_logits, accumulate);
+    auto* kern_sh = map->sh_degree == 0   ? k_sh_bwd<0>
+                    : map->sh_degree == 1 ? k_sh_bwd<1>
+                    : map->sh_degree == 2 ? k_sh_bwd<2>
+                                          : k_sh_bwd<3>;
+    kern_sh<<<blocks, kProjThreads, smem, st>>>(map->means, n, views_dev, p->vt, touched, gcol,
+                                                 grads->sh, accumulate);
     return launch_status();
 }
 
