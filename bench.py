@@ -407,9 +407,9 @@ def run_gpu(args, ws, rank, local):
                     frac=achieved / peak, traffic=None, algorithmic=flops,
                     peak_source="152 SMs x 128 FP32 lanes x 2 x sm_max_mhz (%s)" % peaks["source"])
 
-    # project 1, bin_sort 17 + 3 per tile-id pass, render_fwd 1, loss 2,
+    # project 1, bin_sort 18 + 3 per tile-id pass, render_fwd 1, loss 2,
     # render_bwd 1, project_bwd 2, adam 2
-    launches_per_step = 1 + (17 + 3 * tile_passes(rast.total_tiles)) + 1 + 2 + 1 + 2 + 2
+    launches_per_step = 1 + (18 + 3 * tile_passes(rast.total_tiles)) + 1 + 2 + 1 + 2 + 2
 
     out = dict(metric=METRIC, value=value, unit="iters/s", n_gpus=ws, steps=K, warmup=args.warmup,
                ms_per_step=ms_step, higher_is_better=True, scaling="weak", vs_baseline=None,

@@ -51,6 +51,7 @@ enum PrivBuf {
     B_LOSS_BLOCKS,
     B_GCOL,     // [V*n] x 3: colour gradient as it reaches the SH coefficients
     B_OFFSETS,  // [V*n + 1] instance offsets of the entries in depth order
+    B_TILE_ORDER,  // [total_tiles] render order of the tiles, longest lists first
     B_TOTAL
 };
 

@@ -255,12 +255,13 @@ __device__ void render_fwd_tile(const ViewTable& vt, const TileCtx& tc,
 
 template <int PPT>
 __global__ void k_render_fwd(ViewTable vt, const uint32_t* __restrict__ ranges,
+                             const uint32_t* __restrict__ order,
                              const uint32_t* __restrict__ ivals, const float4* __restrict__ rec,
                              int batch, float bg0, float bg1, float bg2,
                              float* __restrict__ images, float* __restrict__ final_T,
                              int32_t* __restrict__ last_idx) {
     extern __shared__ float4 smem[];
-    const TileCtx tc = tile_ctx(vt, ranges, blockIdx.x);
+    const TileCtx tc = tile_ctx(vt, ranges, (int)order[blockIdx.x]);
     const float bg[3] = {bg0, bg1, bg2};
     if (tc.channels == 3)
         render_fwd_tile<3, PPT>(vt, tc, ivals, rec, smem, batch, bg, images, final_T, last_idx);
@@ -435,13 +436,14 @@ __device__ void render_bwd_tile(const ViewTable& vt, const TileCtx& tc,
 
 template <int PPT>
 __global__ void k_render_bwd(ViewTable vt, const uint32_t* __restrict__ ranges,
+                             const uint32_t* __restrict__ order,
                              const uint32_t* __restrict__ ivals, const float4* __restrict__ rec,
                              int batch, float bg0, float bg1, float bg2,
                              const float* __restrict__ final_T, const int32_t* __restrict__ last_idx,
                              const float* __restrict__ dL, float* __restrict__ grad2d) {
     extern __shared__ float4 smem[];
     __shared__ int s_maxlast;
-    const TileCtx tc = tile_ctx(vt, ranges, blockIdx.x);
+    const TileCtx tc = tile_ctx(vt, ranges, (int)order[blockIdx.x]);
     const float bg[3] = {bg0, bg1, bg2};
     if (tc.channels == 3)
         render_bwd_tile<3, PPT>(vt, tc, ivals, rec, smem, &s_maxlast, batch, bg, final_T,
@@ -466,7 +468,7 @@ gs_status launch_render_fwd(const Plan* p, const void* ws, float* images, float*
     const int threads = p->cfg.tile_w * p->cfg.tile_h / ppt;
     auto kern = pick(ppt, k_render_fwd<1>, k_render_fwd<2>, k_render_fwd<4>, k_render_fwd<8>);
     kern<<<p->total_tiles, threads, smem, st>>>(
-        p->vt, cbuf<uint32_t>(p, ws, GS_BUF_RANGES),
+        p->vt, cbuf<uint32_t>(p, ws, GS_BUF_RANGES), cbuf<uint32_t>(p, ws, B_TILE_ORDER),
         cbuf<uint32_t>(p, ws, (p->tile_passes & 1) ? (int)B_IVAL_B : (int)GS_BUF_TILE_VALUES),
         cbuf<float4>(p, ws, GS_BUF_PROJ), batch, p->cfg.bg[0], p->cfg.bg[1], p->cfg.bg[2], images,
         final_T, last_idx);
@@ -484,7 +486,7 @@ gs_status launch_render_bwd_pixels(const Plan* p, void* ws, const float* final_T
     if (cudaMemsetAsync(grad2d, 0, p->len[GS_BUF_GRAD2D], st) != cudaSuccess) return GS_ERR_CUDA;
     auto kern = pick(ppt, k_render_bwd<1>, k_render_bwd<2>, k_render_bwd<4>, k_render_bwd<8>);
     kern<<<p->total_tiles, threads, smem, st>>>(
-        p->vt, cbuf<uint32_t>(p, ws, GS_BUF_RANGES),
+        p->vt, cbuf<uint32_t>(p, ws, GS_BUF_RANGES), cbuf<uint32_t>(p, ws, B_TILE_ORDER),
         cbuf<uint32_t>(p, ws, (p->tile_passes & 1) ? (int)B_IVAL_B : (int)GS_BUF_TILE_VALUES),
         cbuf<float4>(p, ws, GS_BUF_PROJ), batch, p->cfg.bg[0], p->cfg.bg[1], p->cfg.bg[2],
         final_T, last_idx, dL, grad2d);

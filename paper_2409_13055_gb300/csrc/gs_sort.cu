@@ -299,6 +299,53 @@ __global__ void k_ranges(const uint32_t* __restrict__ keys, const uint32_t* coun
     }
 }
 
+// Heavy-first order of the tiles for the render kernels: tiles bucketed by
+// the bit length of their list length, longest bucket first, so the CTAs of
+// the longest lists start in the first wave instead of forming the tail.
+// One CTA; within a bucket the order is arbitrary (it changes scheduling,
+// never a result).
+constexpr int kOrderThreads = 1024;
+constexpr int kOrderBuckets = 33;
+
+__device__ __forceinline__ int work_bucket(const uint32_t* ranges, int t) {
+    const uint32_t len = ranges[2 * t + 1] - ranges[2 * t];
+    return len == 0u ? kOrderBuckets - 1 : __clz(len);  // 0 = longest
+}
+
+__global__ void __launch_bounds__(kOrderThreads)
+k_tile_order(const uint32_t* __restrict__ ranges, int T, uint32_t* __restrict__ order) {
+    __shared__ uint32_t cnt[kOrderBuckets], base[kOrderBuckets];
+    if (threadIdx.x < kOrderBuckets) cnt[threadIdx.x] = 0u;
+    __syncthreads();
+    const int lane = threadIdx.x & 31;
+    const uint32_t lt = (1u << lane) - 1u;
+    for (int t0 = 0; t0 < T; t0 += kOrderThreads) {
+        const int t = t0 + threadIdx.x;
+        const int b = t < T ? work_bucket(ranges, t) : 1000 + lane;  // unique dummy
+        const uint32_t peers = __match_any_sync(0xffffffffu, b);
+        if (t < T && (__ffs(peers) - 1) == lane) atomicAdd(&cnt[b], __popc(peers));
+    }
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        uint32_t run = 0u;
+        for (int b = 0; b < kOrderBuckets; ++b) {
+            base[b] = run;
+            run += cnt[b];
+        }
+    }
+    __syncthreads();
+    for (int t0 = 0; t0 < T; t0 += kOrderThreads) {
+        const int t = t0 + threadIdx.x;
+        const int b = t < T ? work_bucket(ranges, t) : 1000 + lane;
+        const uint32_t peers = __match_any_sync(0xffffffffu, b);
+        const int leader = __ffs(peers) - 1;
+        uint32_t first = 0u;
+        if (t < T && leader == lane) first = atomicAdd(&base[b], __popc(peers));
+        first = __shfl_sync(0xffffffffu, first, leader);
+        if (t < T) order[first + __popc(peers & lt)] = (uint32_t)t;
+    }
+}
+
 template <int ITEMS>
 gs_status radix_pass_t(const uint32_t* kin, const uint32_t* vin, uint32_t* kout, uint32_t* vout,
                        const uint32_t* count_dev, uint32_t count_host, uint32_t cap, int shift,
@@ -379,6 +426,8 @@ gs_status launch_bin_sort(const Plan* p, int32_t n, void* ws, cudaStream_t st) {
         cudaSuccess)
         return GS_ERR_CUDA;
     k_ranges<<<kGrid, 256, 0, st>>>(sorted_keys, cnt, ranges);
+    k_tile_order<<<1, kOrderThreads, 0, st>>>(ranges, p->total_tiles,
+                                              buf<uint32_t>(p, ws, B_TILE_ORDER));
     return launch_status();
 }
 
