@@ -224,7 +224,8 @@ def run_batched(args, ws):
     views = scenes.views_mixed16()
     lam = 0.2
     cfg = dict(tile=(args.tile_w, args.tile_h), smem_batch=args.batch,
-               pixels_per_thread=args.ppt)
+               pixels_per_thread=args.ppt, smem_batch_bwd=args.batch_bwd,
+               pixels_per_thread_bwd=args.ppt_bwd)
     gt = mapping.GaussianMap(scenes.perturbed(p, scenes.SEED_BASE + 24))
     r = mapping.fit_instance_capacity(views, gt)
     r.forward(gt.gs_map())
@@ -259,7 +260,8 @@ def run_batched(args, ws):
                                                result["per_view"]["iters_per_s"])
     result["config"] = dict(gaussians=500_000, views="6x640x480x3 + 6x752x480x1 + 4x1200x680x3",
                             steps=K, tile=f"{args.tile_w}x{args.tile_h}", smem_batch=args.batch,
-                            pixels_per_thread=args.ppt, cuda_graph="whole iteration")
+                            pixels_per_thread=args.ppt, smem_batch_bwd=args.batch_bwd,
+                            pixels_per_thread_bwd=args.ppt_bwd, cuda_graph="whole iteration")
     return result
 
 
@@ -294,8 +296,14 @@ def run_gpu(args, ws, rank, local):
         args.tile_h = args.tile_h or tuned["tile"][1]
         args.batch = args.batch or tuned["smem_batch"]
         args.ppt = args.ppt or tuned["pixels_per_thread"]
+        args.batch_bwd = args.batch_bwd or tuned["smem_batch_bwd"]
+        args.ppt_bwd = args.ppt_bwd or tuned["pixels_per_thread_bwd"]
+    args.batch_bwd = args.batch_bwd or args.batch
+    args.ppt_bwd = args.ppt_bwd or args.ppt
     rast = mapping.fit_instance_capacity([view], gm, headroom=1.5, tile=(args.tile_w, args.tile_h),
-                                         smem_batch=args.batch, pixels_per_thread=args.ppt)
+                                         smem_batch=args.batch, pixels_per_thread=args.ppt,
+                                         smem_batch_bwd=args.batch_bwd,
+                                         pixels_per_thread_bwd=args.ppt_bwd)
     step = mapping.MappingStep(gm, rast, target, lam)
     m, g = gm.gs_map(), gm.gs_map_grad()
     stages = [
@@ -418,6 +426,7 @@ def run_gpu(args, ws, rank, local):
                            height=view["height"], sh_degree=3,
                            views=1, lam=0.2, tile=f"{args.tile_w}x{args.tile_h}",
                            smem_batch=args.batch, pixels_per_thread=args.ppt,
+                           smem_batch_bwd=args.batch_bwd, pixels_per_thread_bwd=args.ppt_bwd,
                            autotuned=tuned is not None, cuda_graph="one graph per stage",
                            l2="working set ~1.2 GB > 129 MB L2, no flush",
                            instances=instances, pairs_bwd=pairs_bwd),
@@ -427,7 +436,8 @@ def run_gpu(args, ws, rank, local):
                clocks=clocks, gpu_launches=launches_per_step * K)
 
     if tuned is not None:
-        out["autotune"] = [dict(t, ms=round(t["ms"], 4)) for t in tuned["timings"]]
+        out["autotune"] = [dict(t, ms=round(t["ms"], 4), fwd_ms=round(t["fwd_ms"], 4),
+                                bwd_ms=round(t["bwd_ms"], 4)) for t in tuned["timings"]]
     if not args.no_batched:
         del rast, step, graphs
         gm = None
@@ -460,6 +470,8 @@ def main():
     ap.add_argument("--tile-h", type=int, default=None)
     ap.add_argument("--batch", type=int, default=None, help="Gaussians per shared-memory batch")
     ap.add_argument("--ppt", type=int, default=None, help="pixels per thread")
+    ap.add_argument("--batch-bwd", type=int, default=None, help="backward smem batch")
+    ap.add_argument("--ppt-bwd", type=int, default=None, help="backward pixels per thread")
     ap.add_argument("--no-batched", action="store_true",
                     help="skip the 16-keyframe batched vs per-view measurement")
     ap.add_argument("--no-cpu-baseline", action="store_true")

@@ -96,14 +96,17 @@ typedef struct {
  *   pixels_per_thread: 0 (automatic) or 1, 2, 4, 8 consecutive pixels of a
  *     tile row handled by one thread; tile_w must be a multiple of it and the
  *     tile must keep at least one full warp of threads;
+ *   smem_batch_bwd, pixels_per_thread_bwd: the same two choices for the
+ *     backward (gs_render_bwd*); 0 = as for the forward;
  *   near_z: Gaussians whose camera depth is not above near_z are culled
  *     (default reading 0.2 m);
  *   bg: background colour, entering the image as T_final * bg.
  * The tile shape changes which pixels a Gaussian can reach (its 3-sigma
- * rect is counted in whole tiles), hence the image; smem_batch and
- * pixels_per_thread change only the speed. */
+ * rect is counted in whole tiles), hence the image; the batch sizes and
+ * pixels per thread change only the speed. */
 typedef struct {
     int32_t tile_w, tile_h, smem_batch, pixels_per_thread;
+    int32_t smem_batch_bwd, pixels_per_thread_bwd;
     float near_z;
     float bg[3];
 } gs_config;

@@ -44,7 +44,8 @@ class gs_map_grad(ctypes.Structure):
 
 class gs_config(ctypes.Structure):
     _fields_ = [("tile_w", c_int32), ("tile_h", c_int32), ("smem_batch", c_int32),
-                ("pixels_per_thread", c_int32), ("near_z", c_float), ("bg", c_float * 3)]
+                ("pixels_per_thread", c_int32), ("smem_batch_bwd", c_int32),
+                ("pixels_per_thread_bwd", c_int32), ("near_z", c_float), ("bg", c_float * 3)]
 
 
 class gs_plan(ctypes.Structure):

@@ -29,12 +29,18 @@ extern "C" gs_status gs_plan_init(gs_plan* plan, const gs_config* cfg, int32_t n
     const int l2w = ilog2_exact(cfg->tile_w), l2h = ilog2_exact(cfg->tile_h);
     if (l2w < 0 || l2h < 0 || cfg->tile_w * cfg->tile_h < 64 || cfg->tile_w * cfg->tile_h > 256)
         return GS_ERR_UNSUPPORTED;
-    if (cfg->smem_batch < 32 || cfg->smem_batch > 256 || cfg->smem_batch % 32)
-        return GS_ERR_UNSUPPORTED;
+    auto batch_ok = [](int b) { return b >= 32 && b <= 256 && b % 32 == 0; };
+    auto ppt_ok = [&](int q) {
+        return (q == 1 || q == 2 || q == 4 || q == 8) && cfg->tile_w % q == 0 &&
+               (cfg->tile_w * cfg->tile_h / q) % 32 == 0;
+    };
+    if (!batch_ok(cfg->smem_batch)) return GS_ERR_UNSUPPORTED;
     int ppt = cfg->pixels_per_thread;
-    if (ppt == 0) ppt = (cfg->tile_w * cfg->tile_h >= 128 && cfg->tile_w % 4 == 0) ? 4 : 2;
-    if (ppt != 1 && ppt != 2 && ppt != 4 && ppt != 8) return GS_ERR_UNSUPPORTED;
-    if (cfg->tile_w % ppt || (cfg->tile_w * cfg->tile_h / ppt) % 32) return GS_ERR_UNSUPPORTED;
+    if (ppt == 0) ppt = 1;
+    if (!ppt_ok(ppt)) return GS_ERR_UNSUPPORTED;
+    const int batch_bwd = cfg->smem_batch_bwd ? cfg->smem_batch_bwd : cfg->smem_batch;
+    const int ppt_bwd = cfg->pixels_per_thread_bwd ? cfg->pixels_per_thread_bwd : ppt;
+    if (!batch_ok(batch_bwd) || !ppt_ok(ppt_bwd)) return GS_ERR_UNSUPPORTED;
     if (!(cfg->near_z > 0.0f)) return GS_ERR_INVALID;
     if ((int64_t)n_views * n_capacity > (int64_t(1) << 31)) return GS_ERR_INVALID;
 
@@ -42,6 +48,8 @@ extern "C" gs_status gs_plan_init(gs_plan* plan, const gs_config* cfg, int32_t n
     Plan* p = reinterpret_cast<Plan*>(plan);
     p->cfg = *cfg;
     p->cfg.pixels_per_thread = ppt;
+    p->cfg.smem_batch_bwd = batch_bwd;
+    p->cfg.pixels_per_thread_bwd = ppt_bwd;
     p->n_capacity = n_capacity;
     p->inst_capacity = instance_capacity;
     p->vt.n_views = n_views;

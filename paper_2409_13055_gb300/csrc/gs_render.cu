@@ -477,8 +477,8 @@ gs_status launch_render_fwd(const Plan* p, const void* ws, float* images, float*
 
 gs_status launch_render_bwd_pixels(const Plan* p, void* ws, const float* final_T,
                                    const int32_t* last_idx, const float* dL, cudaStream_t st) {
-    const int batch = p->cfg.smem_batch;
-    const int ppt = p->cfg.pixels_per_thread;
+    const int batch = p->cfg.smem_batch_bwd;
+    const int ppt = p->cfg.pixels_per_thread_bwd;
     const size_t smem = (size_t)2 * 3 * batch * sizeof(float4) + 4 * batch * sizeof(uint32_t) +
                         (size_t)kGrad2d * batch * sizeof(float);
     const int threads = p->cfg.tile_w * p->cfg.tile_h / ppt;

@@ -30,13 +30,13 @@ def test_exports_every_declared_function(lib):
 
 def test_struct_sizes_match_header():
     assert ctypes.sizeof(B.gs_view) == 80
-    assert ctypes.sizeof(B.gs_config) == 32
+    assert ctypes.sizeof(B.gs_config) == 40
     assert ctypes.sizeof(B.gs_counters) == 32
     assert ctypes.sizeof(B.gs_plan) == 8 * B.GS_PLAN_WORDS
 
 
-def _cfg(tw=16, th=16, batch=128, near=0.2, ppt=0):
-    return B.gs_config(tw, th, batch, ppt, near, (B.c_float * 3)(0, 0, 0))
+def _cfg(tw=16, th=16, batch=128, near=0.2, ppt=0, batch_bwd=0, ppt_bwd=0):
+    return B.gs_config(tw, th, batch, ppt, batch_bwd, ppt_bwd, near, (B.c_float * 3)(0, 0, 0))
 
 
 def _views(*sizes):
@@ -70,6 +70,8 @@ def test_plan_layout_and_offsets(lib):
     (dict(near=0.0), [(64, 64, 3)], 10, 100, B.GS_ERR_INVALID),
     (dict(ppt=3), [(64, 64, 3)], 10, 100, B.GS_ERR_UNSUPPORTED),
     (dict(tw=8, th=8, ppt=4), [(64, 64, 3)], 10, 100, B.GS_ERR_UNSUPPORTED),
+    (dict(ppt_bwd=3), [(64, 64, 3)], 10, 100, B.GS_ERR_UNSUPPORTED),
+    (dict(batch_bwd=40), [(64, 64, 3)], 10, 100, B.GS_ERR_UNSUPPORTED),
     (dict(), [(64, 64, 2)], 10, 100, B.GS_ERR_INVALID),
     (dict(), [(0, 64, 3)], 10, 100, B.GS_ERR_INVALID),
     (dict(), [(64, 64, 3)], 0, 100, B.GS_ERR_INVALID),

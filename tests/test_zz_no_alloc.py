@@ -23,7 +23,7 @@ def lib():
 
 
 def _plan(views):
-    cfg = B.gs_config(16, 16, 128, 0, 0.2, (B.c_float * 3)(0, 0, 0))
+    cfg = B.gs_config(16, 16, 128, 0, 0, 0, 0.2, (B.c_float * 3)(0, 0, 0))
     return B.gs_plan_init(cfg, [mapping.make_view(v) for v in views], 16, 1024)
 
 
