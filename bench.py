@@ -391,14 +391,15 @@ def run_gpu(args, ws, rank, local):
     # --- roofline of the dominant kernel ----------------------------------
     n = gm.n
     K_sh = (gm.degree + 1) ** 2
-    n_floats = gm.total
     algo_bytes = dict(
         project=n * (4 * (11 + 3 * K_sh)) + n * 72,
         bin_sort=n * 4 * 16 + n * 12 + instances * 8 + tile_passes(rast.total_tiles) * instances * 16
         + instances * 4 + rast.total_tiles * 8,
         loss_l1_ssim=rast.total_values * 44,
-        project_bwd=n * 2 * (4 * (11 + 3 * K_sh)) + n * (36 + 4),
-        adam=n_floats * 28,
+        # parameters read (44 + 12K B), gradients written (same), screen-space
+        # gradient 36 B, colour gradient 24 B, tiles touched 4 B
+        project_bwd=n * 2 * (4 * (11 + 3 * K_sh)) + n * (36 + 24 + 4),
+        adam=gm.total * 28,
     )
     dominant = max(stage_ms, key=stage_ms.get)
     if dominant in algo_bytes:

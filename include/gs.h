@@ -261,6 +261,26 @@ gs_status gs_project_bwd(const gs_plan *plan, const gs_map *map, const gs_view *
                          const void *ws, const gs_map_grad *grads, int32_t accumulate,
                          void *stream);
 
+/* A8 + A9 fused: the projection adjoint of gs_project_bwd followed, in the
+ * same kernels, by one Adam step (as gs_adam_step) on every Gaussian, so the
+ * parameter gradients are never written to and read back from memory.
+ * map: the parameters of the preceding gs_project (read); params: where the
+ * updated parameters go (normally the same arrays as map, updated in place);
+ * m, v: Adam moments in the gs_map layout; grads_acc (nullable): gradients
+ * of other views to add first (a loop of single-view plans passes its
+ * accumulated gradients here on its last view); grads_out (nullable): receives
+ * the total gradient.  group_lr_host: 6 HOST floats, the learning rates of
+ * means, log-scales, quaternions, opacity logits, SH coefficient 0 and SH
+ * coefficients 1.. .  *step_dev is incremented first; bias corrections as in
+ * gs_adam_step.  Same results, bit for bit, as gs_project_bwd into a zeroed
+ * gradient plus gs_adam_step. */
+gs_status gs_project_bwd_adam(const gs_plan *plan, const gs_map *map, const gs_view *views_dev,
+                              void *ws, const gs_map_grad *params, const gs_map_grad *m,
+                              const gs_map_grad *v, const gs_map_grad *grads_acc,
+                              const gs_map_grad *grads_out, const float *group_lr_host,
+                              float beta1, float beta2, float eps, int32_t *step_dev,
+                              void *stream);
+
 /* A9: Adam (paper Sec. IV-A, default 3DGS optimiser) over one contiguous
  * parameter buffer of n_floats split into n_groups contiguous groups:
  * group g covers [group_offsets_host[g], group_offsets_host[g+1]) with

@@ -80,6 +80,10 @@ _SIGNATURES = {
                                        c_void_p]),
     "gs_project_bwd": (c_int32, [_P(gs_plan), _P(gs_map), c_void_p, c_void_p, _P(gs_map_grad),
                                  c_int32, c_void_p]),
+    "gs_project_bwd_adam": (c_int32, [_P(gs_plan), _P(gs_map), c_void_p, c_void_p,
+                                      _P(gs_map_grad), _P(gs_map_grad), _P(gs_map_grad),
+                                      _P(gs_map_grad), _P(gs_map_grad), _P(c_float), c_float,
+                                      c_float, c_float, c_void_p, c_void_p]),
     "gs_adam_step": (c_int32, [c_void_p, c_void_p, c_void_p, c_void_p, c_int64, c_int32,
                                _P(c_int64), _P(c_float), c_float, c_float, c_float, c_void_p,
                                c_void_p]),
@@ -221,6 +225,19 @@ def gs_project_bwd(plan, gmap: gs_map, views_dev, ws, grads: gs_map_grad, accumu
     check(lib().gs_project_bwd(ctypes.byref(plan), ctypes.byref(gmap), _ptr(views_dev), _ptr(ws),
                                ctypes.byref(grads), 1 if accumulate else 0, _stream(stream)),
           "gs_project_bwd")
+
+
+def gs_project_bwd_adam(plan, gmap: gs_map, views_dev, ws, params: gs_map_grad, m: gs_map_grad,
+                        v: gs_map_grad, group_lr, beta1, beta2, eps, step_dev, grads_acc=None,
+                        grads_out=None, stream=None):
+    lrs = (c_float * 6)(*[float(x) for x in group_lr])
+    check(lib().gs_project_bwd_adam(ctypes.byref(plan), ctypes.byref(gmap), _ptr(views_dev),
+                                    _ptr(ws), ctypes.byref(params), ctypes.byref(m),
+                                    ctypes.byref(v),
+                                    ctypes.byref(grads_acc) if grads_acc is not None else None,
+                                    ctypes.byref(grads_out) if grads_out is not None else None,
+                                    lrs, float(beta1), float(beta2), float(eps), _ptr(step_dev),
+                                    _stream(stream)), "gs_project_bwd_adam")
 
 
 def gs_adam_step(params, grads, m, v, group_offsets, group_lr, beta1, beta2, eps, step_dev,

@@ -41,13 +41,6 @@ __device__ __forceinline__ float4 lr4_of(const Groups& g, uint32_t e) {
     return make_float4(a, lr_of(g, e + 1), lr_of(g, e + 2), d);
 }
 
-__device__ __forceinline__ void adam1(float& p, float g, float& m, float& v, float lr, float b1,
-                                      float b2, float eps, float ibc1, float ibc2) {
-    m = fmaf(b1, m, (1.0f - b1) * g);
-    v = fmaf(b2, v, (1.0f - b2) * g * g);
-    p -= lr * (m * ibc1) / (sqrtf(v * ibc2) + eps);
-}
-
 __device__ __forceinline__ void adam4(float4& p, const float4& g, float4& m, float4& v,
                                       const float4& lr, float b1, float b2, float eps, float ibc1,
                                       float ibc2) {
@@ -62,11 +55,7 @@ k_adam(float* __restrict__ params, const float* __restrict__ grads, float* __res
        float* __restrict__ v, long long n, Groups groups, float b1, float b2, float eps,
        const int32_t* __restrict__ step, int vec) {
     __shared__ float s_bc[2];
-    if (threadIdx.x == 0) {
-        const int t = *step;
-        s_bc[0] = (float)(1.0 / (1.0 - pow((double)b1, (double)t)));
-        s_bc[1] = (float)(1.0 / (1.0 - pow((double)b2, (double)t)));
-    }
+    if (threadIdx.x == 0) adam_bias(b1, b2, *step, s_bc[0], s_bc[1]);
     __syncthreads();
     const float ibc1 = s_bc[0], ibc2 = s_bc[1];
     const long long stride = (long long)gridDim.x * blockDim.x;
@@ -98,6 +87,11 @@ k_adam(float* __restrict__ params, const float* __restrict__ grads, float* __res
 }
 
 }  // namespace
+
+gs_status launch_step_inc(int32_t* step_dev, cudaStream_t st) {
+    k_step_inc<<<1, 1, 0, st>>>(step_dev);
+    return launch_status();
+}
 
 gs_status launch_adam(float* params, const float* grads, float* m, float* v, int64_t n,
                       int32_t n_groups, const int64_t* offs, const float* lrs, float b1, float b2,

@@ -125,6 +125,7 @@ extern "C" gs_status gs_plan_init(gs_plan* plan, const gs_config* cfg, int32_t n
     len[B_GCOL] = (size_t)VN * 3 * sizeof(float);
     len[B_OFFSETS] = (size_t)(VN + 1) * sizeof(uint32_t);
     len[B_TILE_ORDER] = (size_t)tiles * sizeof(uint32_t);
+    len[B_GMEAN] = (size_t)n_capacity * 3 * sizeof(float);
     size_t off = 0;
     for (int b = 0; b < B_TOTAL; ++b) {
         p->off[b] = off;
@@ -242,6 +243,29 @@ extern "C" gs_status gs_project_bwd(const gs_plan* plan, const gs_map* map,
         return GS_ERR_INVALID;
     return launch_project_bwd(P(plan), map, views_dev, const_cast<void*>(ws), grads,
                               accumulate ? 1 : 0, S(stream));
+}
+
+static bool grad_ok(const gs_map_grad* g) {
+    return g && g->means && g->log_scales && g->quats && g->opacity_logits && g->sh;
+}
+
+extern "C" gs_status gs_project_bwd_adam(const gs_plan* plan, const gs_map* map,
+                                         const gs_view* views_dev, void* ws,
+                                         const gs_map_grad* params, const gs_map_grad* m,
+                                         const gs_map_grad* v, const gs_map_grad* grads_acc,
+                                         const gs_map_grad* grads_out, const float* group_lr_host,
+                                         float beta1, float beta2, float eps, int32_t* step_dev,
+                                         void* stream) {
+    if (!plan_ok(plan) || !views_dev || !ws || !group_lr_host || !step_dev) return GS_ERR_INVALID;
+    if (!map_ok(P(plan), map) || !grad_ok(params) || !grad_ok(m) || !grad_ok(v))
+        return GS_ERR_INVALID;
+    if ((grads_acc && !grad_ok(grads_acc)) || (grads_out && !grad_ok(grads_out)))
+        return GS_ERR_INVALID;
+    if (!(beta1 >= 0.0f && beta1 < 1.0f && beta2 >= 0.0f && beta2 < 1.0f && eps >= 0.0f))
+        return GS_ERR_INVALID;
+    return launch_project_bwd_adam(P(plan), map, views_dev, ws, params, m, v, grads_acc,
+                                   grads_out, group_lr_host, beta1, beta2, eps, step_dev,
+                                   S(stream));
 }
 
 extern "C" gs_status gs_adam_step(float* params, const float* grads, float* m, float* v,

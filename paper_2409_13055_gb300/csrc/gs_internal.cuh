@@ -52,6 +52,7 @@ enum PrivBuf {
     B_GCOL,     // [V*n] x 3: colour gradient as it reaches the SH coefficients
     B_OFFSETS,  // [V*n + 1] instance offsets of the entries in depth order
     B_TILE_ORDER,  // [total_tiles] render order of the tiles, longest lists first
+    B_GMEAN,       // [n] x 3 mean gradients held between the fused adjoint kernels
     B_TOTAL
 };
 
@@ -179,6 +180,23 @@ __device__ __forceinline__ float gauss_power(float a, float b, float c, float dx
     return __fmaf_rn(-0.5f, q, -__fmul_rn(b, __fmul_rn(dx, dy)));
 }
 
+// One Adam update of one float (paper Sec. IV-A, the default 3DGS optimiser):
+// m = b1 m + (1-b1) g; v = b2 v + (1-b2) g^2; p -= lr (m ibc1) / (sqrt(v ibc2) + eps),
+// ibc = 1 / (1 - beta^t).  Shared by the stand-alone and the fused Adam so both
+// produce the same bits.
+__device__ __forceinline__ void adam1(float& p, float g, float& m, float& v, float lr, float b1,
+                                      float b2, float eps, float ibc1, float ibc2) {
+    m = fmaf(b1, m, (1.0f - b1) * g);
+    v = fmaf(b2, v, (1.0f - b2) * g * g);
+    p -= lr * (m * ibc1) / (sqrtf(v * ibc2) + eps);
+}
+
+// Bias corrections 1/(1 - b1^t), 1/(1 - b2^t) of step t.
+__device__ __forceinline__ void adam_bias(float b1, float b2, int t, float& ibc1, float& ibc2) {
+    ibc1 = (float)(1.0 / (1.0 - pow((double)b1, (double)t)));
+    ibc2 = (float)(1.0 / (1.0 - pow((double)b2, (double)t)));
+}
+
 constexpr float kAlphaMin = 1.0f / 255.0f;
 constexpr float kAlphaMax = 0.99f;
 constexpr float kTMin = 1e-4f;
@@ -201,6 +219,12 @@ gs_status launch_render_bwd_pixels(const Plan* p, void* ws, const float* final_T
                                    const int32_t* last_idx, const float* dL, cudaStream_t st);
 gs_status launch_project_bwd(const Plan* p, const gs_map* map, const gs_view* views_dev,
                              void* ws, const gs_map_grad* grads, int accumulate, cudaStream_t st);
+gs_status launch_step_inc(int32_t* step_dev, cudaStream_t st);
+gs_status launch_project_bwd_adam(const Plan* p, const gs_map* map, const gs_view* views_dev,
+                                  void* ws, const gs_map_grad* params, const gs_map_grad* m,
+                                  const gs_map_grad* v, const gs_map_grad* grads_acc,
+                                  const gs_map_grad* grads_out, const float* lr6, float b1,
+                                  float b2, float eps, int32_t* step_dev, cudaStream_t st);
 gs_status launch_adam(float* params, const float* grads, float* m, float* v, int64_t n,
                       int32_t n_groups, const int64_t* offs, const float* lrs, float b1,
                       float b2, float eps, int32_t* step_dev, cudaStream_t st);

@@ -157,6 +157,21 @@ struct Proj {
     float dir[3], dist;
 };
 
+// Adam state for the fused projection adjoint: parameter, moment and optional
+// gradient arrays in the gs_map layout; lr per group (means, log-scales,
+// quaternions, opacity, SH DC, SH rest).
+struct FusedAdam {
+    float lr[6];
+    float b1, b2, eps;
+    const int32_t* step;
+    float *p_means, *p_ls, *p_quats, *p_logit, *p_sh;
+    float *m_means, *m_ls, *m_quats, *m_logit, *m_sh;
+    float *v_means, *v_ls, *v_quats, *v_logit, *v_sh;
+    const float *a_means, *a_ls, *a_quats, *a_logit, *a_sh;  // gradients to add, or null
+    float *o_means, *o_ls, *o_quats, *o_logit, *o_sh;        // gradients out, or null
+    float* gmean;                                            // [n][3] deferred mean gradients
+};
+
 __device__ __forceinline__ void project_one(const float* mean, const Shape& sh, const Cam& cam,
                                             float near_z, int log2_tw, int log2_th, int tiles_x,
                                             int tiles_y, Proj& p) {
@@ -311,7 +326,7 @@ k_project(const float* __restrict__ means, const float* __restrict__ log_scales,
 
 // A8: chain rule of the projection, summed over views.  One thread per
 // Gaussian reads its screen-space gradient from every view it is visible in.
-template <int DEG>
+template <int DEG, bool ADAM>
 __global__ void __launch_bounds__(kProjThreads)
 k_project_bwd(const float* __restrict__ means, const float* __restrict__ log_scales,
               const float* __restrict__ quats, const float* __restrict__ opacity_logits,
@@ -319,9 +334,11 @@ k_project_bwd(const float* __restrict__ means, const float* __restrict__ log_sca
               ViewTable vt, float near_z, const uint32_t* __restrict__ touched,
               const float* __restrict__ grad2d, float* __restrict__ gcol_out,
               float* __restrict__ g_means, float* __restrict__ g_ls, float* __restrict__ g_quats,
-              float* __restrict__ g_logit, int accumulate) {
+              float* __restrict__ g_logit, int accumulate, FusedAdam fa) {
     extern __shared__ Cam cam_all[];
+    __shared__ float s_bc[2];
     for (int v = threadIdx.x; v < vt.n_views; v += blockDim.x) load_cam(views[v], cam_all[v]);
+    if (ADAM && threadIdx.x == 0) adam_bias(fa.b1, fa.b2, *fa.step, s_bc[0], s_bc[1]);
     __syncthreads();
     const int g = blockIdx.x * blockDim.x + threadIdx.x;
     if (g >= n) return;
@@ -482,7 +499,44 @@ k_project_bwd(const float* __restrict__ means, const float* __restrict__ log_sca
                              (gq[3] - z * dq) * iq);
     const float glog = gop * opacity * (1.0f - opacity);
 
-    if (accumulate) {
+    if (ADAM) {
+        // Adam on log-scales, quaternion and opacity now; the means wait for
+        // k_sh_bwd, which still needs their current values
+        const float ibc1 = s_bc[0], ibc2 = s_bc[1];
+        float gg[3];
+        for (int e = 0; e < 3; ++e) {
+            fa.gmean[3 * g + e] = gm[e] + (fa.a_means ? fa.a_means[3 * g + e] : 0.0f);
+            gg[e] = gls[e] + (fa.a_ls ? fa.a_ls[3 * g + e] : 0.0f);
+            if (fa.o_ls) fa.o_ls[3 * g + e] = gg[e];
+            float p = ls[e], m = fa.m_ls[3 * g + e], v = fa.v_ls[3 * g + e];
+            adam1(p, gg[e], m, v, fa.lr[1], fa.b1, fa.b2, fa.eps, ibc1, ibc2);
+            fa.p_ls[3 * g + e] = p;
+            fa.m_ls[3 * g + e] = m;
+            fa.v_ls[3 * g + e] = v;
+        }
+        float4 gqa = gq4;
+        if (fa.a_quats) {
+            const float4 a = reinterpret_cast<const float4*>(fa.a_quats)[g];
+            gqa.x += a.x; gqa.y += a.y; gqa.z += a.z; gqa.w += a.w;
+        }
+        if (fa.o_quats) reinterpret_cast<float4*>(fa.o_quats)[g] = gqa;
+        float4 pq = q, mq = reinterpret_cast<float4*>(fa.m_quats)[g],
+               vq = reinterpret_cast<float4*>(fa.v_quats)[g];
+        adam1(pq.x, gqa.x, mq.x, vq.x, fa.lr[2], fa.b1, fa.b2, fa.eps, ibc1, ibc2);
+        adam1(pq.y, gqa.y, mq.y, vq.y, fa.lr[2], fa.b1, fa.b2, fa.eps, ibc1, ibc2);
+        adam1(pq.z, gqa.z, mq.z, vq.z, fa.lr[2], fa.b1, fa.b2, fa.eps, ibc1, ibc2);
+        adam1(pq.w, gqa.w, mq.w, vq.w, fa.lr[2], fa.b1, fa.b2, fa.eps, ibc1, ibc2);
+        reinterpret_cast<float4*>(fa.p_quats)[g] = pq;
+        reinterpret_cast<float4*>(fa.m_quats)[g] = mq;
+        reinterpret_cast<float4*>(fa.v_quats)[g] = vq;
+        const float gl = glog + (fa.a_logit ? fa.a_logit[g] : 0.0f);
+        if (fa.o_logit) fa.o_logit[g] = gl;
+        float pl = logit, ml = fa.m_logit[g], vl = fa.v_logit[g];
+        adam1(pl, gl, ml, vl, fa.lr[3], fa.b1, fa.b2, fa.eps, ibc1, ibc2);
+        fa.p_logit[g] = pl;
+        fa.m_logit[g] = ml;
+        fa.v_logit[g] = vl;
+    } else if (accumulate) {
         for (int e = 0; e < 3; ++e) {
             g_means[3 * g + e] += gm[e];
             g_ls[3 * g + e] += gls[e];
@@ -504,13 +558,15 @@ k_project_bwd(const float* __restrict__ means, const float* __restrict__ log_sca
 // Gradient of the SH coefficients: sum over views of Y_k(dir_v) gcol_v, with
 // gcol the colour gradient k_project_bwd left (zero on clamped channels, a
 // grayscale view's gradient spread over the three channels).
-template <int DEG>
+template <int DEG, bool ADAM>
 __global__ void __launch_bounds__(kProjThreads)
-k_sh_bwd(const float* __restrict__ means, int n, const gs_view* __restrict__ views, ViewTable vt,
-         const uint32_t* __restrict__ touched, const float* __restrict__ gcol_in,
-         float* __restrict__ g_sh, int accumulate) {
+k_sh_bwd(const float* means, const float* sh, int n, const gs_view* __restrict__ views,
+         ViewTable vt, const uint32_t* __restrict__ touched, const float* __restrict__ gcol_in,
+         float* __restrict__ g_sh, int accumulate, FusedAdam fa) {
     extern __shared__ Cam cam_all[];
+    __shared__ float s_bc[2];
     for (int v = threadIdx.x; v < vt.n_views; v += blockDim.x) load_cam(views[v], cam_all[v]);
+    if (ADAM && threadIdx.x == 0) adam_bias(fa.b1, fa.b2, *fa.step, s_bc[0], s_bc[1]);
     __syncthreads();
     const int g = blockIdx.x * blockDim.x + threadIdx.x;
     if (g >= n) return;
@@ -537,17 +593,44 @@ k_sh_bwd(const float* __restrict__ means, int n, const gs_view* __restrict__ vie
             acc[k][2] = fmaf(Y[k], c2, acc[k][2]);
         }
     }
+    if (ADAM) {
+        const float ibc1 = s_bc[0], ibc2 = s_bc[1];
+        for (int e = 0; e < 3; ++e) {
+            const float gg = fa.gmean[3 * g + e];
+            if (fa.o_means) fa.o_means[3 * g + e] = gg;
+            float p = mean[e], m = fa.m_means[3 * g + e], v = fa.v_means[3 * g + e];
+            adam1(p, gg, m, v, fa.lr[0], fa.b1, fa.b2, fa.eps, ibc1, ibc2);
+            fa.p_means[3 * g + e] = p;
+            fa.m_means[3 * g + e] = m;
+            fa.v_means[3 * g + e] = v;
+        }
 #pragma unroll
-    for (int k = 0; k < K; ++k) {
-        float* o = g_sh + ((size_t)k * n + g) * 3;
-        if (accumulate) {
-            o[0] += acc[k][0];
-            o[1] += acc[k][1];
-            o[2] += acc[k][2];
-        } else {
-            o[0] = acc[k][0];
-            o[1] = acc[k][1];
-            o[2] = acc[k][2];
+        for (int k = 0; k < K; ++k) {
+            const float lr = k == 0 ? fa.lr[4] : fa.lr[5];
+            const size_t o = ((size_t)k * n + g) * 3;
+            for (int c = 0; c < 3; ++c) {
+                const float gg = acc[k][c] + (fa.a_sh ? fa.a_sh[o + c] : 0.0f);
+                if (fa.o_sh) fa.o_sh[o + c] = gg;
+                float p = sh[o + c], m = fa.m_sh[o + c], v = fa.v_sh[o + c];
+                adam1(p, gg, m, v, lr, fa.b1, fa.b2, fa.eps, ibc1, ibc2);
+                fa.p_sh[o + c] = p;
+                fa.m_sh[o + c] = m;
+                fa.v_sh[o + c] = v;
+            }
+        }
+    } else {
+#pragma unroll
+        for (int k = 0; k < K; ++k) {
+            float* o = g_sh + ((size_t)k * n + g) * 3;
+            if (accumulate) {
+                o[0] += acc[k][0];
+                o[1] += acc[k][1];
+                o[2] += acc[k][2];
+            } else {
+                o[0] = acc[k][0];
+                o[1] = acc[k][1];
+                o[2] = acc[k][2];
+            }
         }
     }
 }
@@ -574,30 +657,78 @@ gs_status launch_project(const Plan* p, const gs_map* map, const gs_view* views_
     return launch_status();
 }
 
-gs_status launch_project_bwd(const Plan* p, const gs_map* map, const gs_view* views_dev,
-                             void* ws, const gs_map_grad* grads, int accumulate,
-                             cudaStream_t st) {
-    if (reinterpret_cast<uintptr_t>(grads->quats) % 16) return GS_ERR_INVALID;
+template <bool ADAM>
+gs_status launch_project_bwd_t(const Plan* p, const gs_map* map, const gs_view* views_dev,
+                               void* ws, const gs_map_grad* grads, int accumulate,
+                               const FusedAdam& fa, cudaStream_t st) {
     const int n = map->n;
     const size_t smem = sizeof(Cam) * p->vt.n_views;
     const int blocks = (n + kProjThreads - 1) / kProjThreads;
     float* gcol = buf<float>(p, ws, B_GCOL);
     const uint32_t* touched = buf<uint32_t>(p, ws, GS_BUF_TOUCHED);
-    auto* kern = map->sh_degree == 0   ? k_project_bwd<0>
-                 : map->sh_degree == 1 ? k_project_bwd<1>
-                 : map->sh_degree == 2 ? k_project_bwd<2>
-                                       : k_project_bwd<3>;
+    auto* kern = map->sh_degree == 0   ? k_project_bwd<0, ADAM>
+                 : map->sh_degree == 1 ? k_project_bwd<1, ADAM>
+                 : map->sh_degree == 2 ? k_project_bwd<2, ADAM>
+                                       : k_project_bwd<3, ADAM>;
     kern<<<blocks, kProjThreads, smem, st>>>(
         map->means, map->log_scales, map->quats, map->opacity_logits, map->sh, n, views_dev,
-        p->vt, p->cfg.near_z, touched, buf<float>(p, ws, GS_BUF_GRAD2D), gcol, grads->means,
-        grads->log_scales, grads->quats, grads->opacity_logits, accumulate);
-    auto* kern_sh = map->sh_degree == 0   ? k_sh_bwd<0>
-                    : map->sh_degree == 1 ? k_sh_bwd<1>
-                    : map->sh_degree == 2 ? k_sh_bwd<2>
-                                          : k_sh_bwd<3>;
-    kern_sh<<<blocks, kProjThreads, smem, st>>>(map->means, n, views_dev, p->vt, touched, gcol,
-                                                 grads->sh, accumulate);
+        p->vt, p->cfg.near_z, touched, buf<float>(p, ws, GS_BUF_GRAD2D), gcol,
+        grads ? grads->means : nullptr, grads ? grads->log_scales : nullptr,
+        grads ? grads->quats : nullptr, grads ? grads->opacity_logits : nullptr, accumulate, fa);
+    auto* kern_sh = map->sh_degree == 0   ? k_sh_bwd<0, ADAM>
+                    : map->sh_degree == 1 ? k_sh_bwd<1, ADAM>
+                    : map->sh_degree == 2 ? k_sh_bwd<2, ADAM>
+                                          : k_sh_bwd<3, ADAM>;
+    kern_sh<<<blocks, kProjThreads, smem, st>>>(map->means, map->sh, n, views_dev, p->vt, touched,
+                                                 gcol, grads ? grads->sh : nullptr, accumulate, fa);
     return launch_status();
+}
+
+gs_status launch_project_bwd(const Plan* p, const gs_map* map, const gs_view* views_dev,
+                             void* ws, const gs_map_grad* grads, int accumulate,
+                             cudaStream_t st) {
+    if (reinterpret_cast<uintptr_t>(grads->quats) % 16) return GS_ERR_INVALID;
+    FusedAdam fa{};
+    return launch_project_bwd_t<false>(p, map, views_dev, ws, grads, accumulate, fa, st);
+}
+
+gs_status launch_project_bwd_adam(const Plan* p, const gs_map* map, const gs_view* views_dev,
+                                  void* ws, const gs_map_grad* params, const gs_map_grad* m,
+                                  const gs_map_grad* v, const gs_map_grad* grads_acc,
+                                  const gs_map_grad* grads_out, const float* lr6, float b1,
+                                  float b2, float eps, int32_t* step_dev, cudaStream_t st) {
+    auto misaligned = [](const gs_map_grad* g) {
+        return g && (reinterpret_cast<uintptr_t>(g->quats) % 16) != 0;
+    };
+    if (misaligned(params) || misaligned(m) || misaligned(v) || misaligned(grads_acc) ||
+        misaligned(grads_out) || reinterpret_cast<uintptr_t>(map->quats) % 16)
+        return GS_ERR_INVALID;
+    FusedAdam fa{};
+    for (int k = 0; k < 6; ++k) fa.lr[k] = lr6[k];
+    fa.b1 = b1;
+    fa.b2 = b2;
+    fa.eps = eps;
+    fa.step = step_dev;
+    fa.p_means = params->means; fa.p_ls = params->log_scales; fa.p_quats = params->quats;
+    fa.p_logit = params->opacity_logits; fa.p_sh = params->sh;
+    fa.m_means = m->means; fa.m_ls = m->log_scales; fa.m_quats = m->quats;
+    fa.m_logit = m->opacity_logits; fa.m_sh = m->sh;
+    fa.v_means = v->means; fa.v_ls = v->log_scales; fa.v_quats = v->quats;
+    fa.v_logit = v->opacity_logits; fa.v_sh = v->sh;
+    if (grads_acc) {
+        fa.a_means = grads_acc->means; fa.a_ls = grads_acc->log_scales;
+        fa.a_quats = grads_acc->quats; fa.a_logit = grads_acc->opacity_logits;
+        fa.a_sh = grads_acc->sh;
+    }
+    if (grads_out) {
+        fa.o_means = grads_out->means; fa.o_ls = grads_out->log_scales;
+        fa.o_quats = grads_out->quats; fa.o_logit = grads_out->opacity_logits;
+        fa.o_sh = grads_out->sh;
+    }
+    fa.gmean = buf<float>(p, ws, B_GMEAN);
+    gs_status s = launch_step_inc(step_dev, st);
+    if (s != GS_OK) return s;
+    return launch_project_bwd_t<true>(p, map, views_dev, ws, nullptr, 0, fa, st);
 }
 
 }  // namespace gs

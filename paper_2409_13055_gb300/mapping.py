@@ -119,6 +119,24 @@ class GaussianMap:
                              G["quats"].data_ptr(), G["opacity_logits"].data_ptr(),
                              G["sh"].data_ptr())
 
+    def _struct(self, buf) -> B.gs_map_grad:
+        V = self._views(buf)
+        return B.gs_map_grad(V["means"].data_ptr(), V["log_scales"].data_ptr(),
+                             V["quats"].data_ptr(), V["opacity_logits"].data_ptr(),
+                             V["sh"].data_ptr())
+
+    def gs_map_params(self) -> B.gs_map_grad:
+        """The parameter arrays as writable pointers (in-place Adam target)."""
+        return self._struct(self.data)
+
+    def gs_map_moments(self):
+        return self._struct(self.m), self._struct(self.v)
+
+    def group_lr(self, lr=None, extent=1.0):
+        """Learning rates of means, log-scales, quats, opacity, SH DC, SH rest."""
+        lr = dict(DEFAULT_LR, **(lr or {}))
+        return [lr["means"] * extent] + [lr[g] for g in GROUPS[1:]]
+
     def adam_groups(self, lr=None, extent=1.0):
         """(offsets, rates) of the six Adam groups over the packed buffer."""
         lr = dict(DEFAULT_LR, **(lr or {}))
@@ -240,6 +258,15 @@ class Rasterizer:
     def project_bwd(self, gmap: B.gs_map, grads: B.gs_map_grad, accumulate=False, stream=None):
         B.gs_project_bwd(self.plan, gmap, self.views_dev, self.ws, grads, accumulate, stream)
 
+    def project_bwd_adam(self, gmap: GaussianMap, lr=None, extent=1.0, grads_acc=None,
+                         grads_out=None, beta1=0.9, beta2=0.999, eps=1e-15, stream=None):
+        """Projection adjoint fused with one Adam step on gmap (in place)."""
+        mm, vv = gmap.gs_map_moments()
+        B.gs_project_bwd_adam(self.plan, gmap.gs_map(), self.views_dev, self.ws,
+                              gmap.gs_map_params(), mm, vv, gmap.group_lr(lr, extent), beta1,
+                              beta2, eps, gmap.step, grads_acc=grads_acc, grads_out=grads_out,
+                              stream=stream)
+
     def counters(self, stream=None) -> B.gs_counters:
         return B.gs_read_counters(self.plan, self.ws, stream)
 
@@ -309,9 +336,9 @@ class MappingStep:
     batch of views, optionally captured as one CUDA graph."""
 
     def __init__(self, gmap: GaussianMap, rast: Rasterizer, targets: torch.Tensor, lam: float,
-                 lr=None, extent=1.0):
+                 lr=None, extent=1.0, fused=False, keep_grads=False):
         self.gmap, self.rast, self.targets, self.lam = gmap, rast, targets, float(lam)
-        self.lr, self.extent = lr, extent
+        self.lr, self.extent, self.fused, self.keep_grads = lr, extent, fused, keep_grads
         self.graph = None
         self._m = gmap.gs_map()
         self._g = gmap.gs_map_grad()
@@ -322,8 +349,16 @@ class MappingStep:
         r.bin_sort(self.gmap.n, stream)
         r.render_fwd(stream=stream)
         r.loss_l1_ssim(self.targets, self.lam, stream=stream)
-        r.render_bwd(self._m, self._g, accumulate=False, stream=stream)
-        self.gmap.adam_step(self.lr, self.extent, stream=stream)
+        if self.fused:
+            # Adam applied inside the projection adjoint (fewer bytes moved,
+            # but slower than the two passes on this workload); the gradients
+            # are written to gmap.grad only when asked for
+            r.render_bwd_pixels(stream=stream)
+            r.project_bwd_adam(self.gmap, self.lr, self.extent,
+                               grads_out=self._g if self.keep_grads else None, stream=stream)
+        else:
+            r.render_bwd(self._m, self._g, accumulate=False, stream=stream)
+            self.gmap.adam_step(self.lr, self.extent, stream=stream)
 
     def capture(self, warmup=2):
         s = torch.cuda.Stream()
@@ -350,7 +385,7 @@ class PerViewLoop:
     Adam step -- the baseline the batched form is compared with."""
 
     def __init__(self, gmap: GaussianMap, views, targets_per_view, lam, lr=None, extent=1.0,
-                 **rast_kw):
+                 keep_grads=True, **rast_kw):
         self.gmap, self.lam, self.lr, self.extent = gmap, float(lam), lr, extent
         self.rasts = [fit_instance_capacity([v], gmap, **rast_kw) for v in views]
         self.targets = [r.pack([t]) for r, t in zip(self.rasts, targets_per_view)]

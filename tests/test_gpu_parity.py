@@ -320,6 +320,41 @@ def test_split_backward_equals_combined():
     assert U.rel_l2(twice, 2.0 * out[1]) < 1e-6
 
 
+def test_fused_projection_adjoint_adam_is_bit_identical():
+    """gs_project_bwd_adam equals gs_project_bwd into a zeroed gradient followed
+    by gs_adam_step, bit for bit, from the same screen-space gradients; with
+    grads_acc it adds the given gradients first."""
+    p, view = CASES["tiny_sh3_posed"]()
+    target = scenes.random_target(view, 51)
+    g1, g2 = mapping.GaussianMap(p), mapping.GaussianMap(p)
+    for gm in (g1, g2):  # non-trivial moments and step count
+        gm.m.normal_(0, 1e-3)
+        gm.v.uniform_(0, 1e-6)
+        gm.step.fill_(3)
+    g2.m.copy_(g1.m)
+    g2.v.copy_(g1.v)
+    rast = mapping.Rasterizer([view], g1.n, instance_capacity=1 << 18)
+    rast.forward(g1.gs_map())
+    rast.loss_l1_ssim(rast.pack([target]), 0.2)
+    rast.render_bwd_pixels()
+    rast.project_bwd(g1.gs_map(), g1.gs_map_grad())
+    g1.adam_step()
+    g2.grad.fill_(7.0)
+    rast.project_bwd_adam(g2, grads_out=g2.gs_map_grad())
+    torch.cuda.synchronize()
+    assert g1.step.item() == g2.step.item() == 4
+    groups = lambda gm, buf: torch.cat([t.reshape(-1) for t in gm._views(buf).values()])
+    for a, b in ((g1.grad, g2.grad), (g1.data, g2.data), (g1.m, g2.m), (g1.v, g2.v)):
+        assert torch.equal(groups(g1, a), groups(g2, b))
+    # accumulation: grads_acc = the same gradient again doubles it
+    acc = mapping.GaussianMap(p)
+    acc.grad.copy_(g1.grad)
+    g3 = mapping.GaussianMap(p)
+    rast.project_bwd_adam(g3, grads_acc=acc.gs_map_grad(), grads_out=g3.gs_map_grad())
+    torch.cuda.synchronize()
+    torch.testing.assert_close(groups(g3, g3.grad), 2.0 * groups(g1, g1.grad), rtol=1e-6, atol=0)
+
+
 def test_adam_parity():
     rng = np.random.default_rng(8)
     n = 100_003  # ragged: not a multiple of the float4 width
@@ -423,7 +458,7 @@ def test_cuda_graph_replay_matches_eager():
     for use_graph in (False, True):
         gm = mapping.GaussianMap(p)
         rast = mapping.Rasterizer([view], gm.n, instance_capacity=1 << 18)
-        step = mapping.MappingStep(gm, rast, rast.pack([target]), 0.2)
+        step = mapping.MappingStep(gm, rast, rast.pack([target]), 0.2, keep_grads=True)
         if use_graph:
             step.capture(warmup=0)
         start = gm.data.clone()
@@ -450,10 +485,10 @@ def test_batched_equals_per_view_loop():
         gm = mapping.GaussianMap(p)
         if batched:
             rast = mapping.fit_instance_capacity(views, gm)
-            it = mapping.MappingStep(gm, rast, rast.pack(targets), 0.2)
+            it = mapping.MappingStep(gm, rast, rast.pack(targets), 0.2, keep_grads=True)
             loss = lambda: rast.loss.item()
         else:
-            it = mapping.PerViewLoop(gm, views, targets, 0.2)
+            it = mapping.PerViewLoop(gm, views, targets, 0.2, keep_grads=True)
             loss = lambda: sum(r.loss.item() for r in it.rasts)
         it()
         torch.cuda.synchronize()
