@@ -26,7 +26,7 @@ from . import mapping
 
 TILES = ((8, 8), (16, 16), (32, 8))
 BATCHES = (32, 64, 128)
-PPTS = (1, 2)
+PPTS = (1, 2, 4, 8)
 
 
 def cache_path():

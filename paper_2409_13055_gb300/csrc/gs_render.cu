@@ -67,13 +67,47 @@ __device__ __forceinline__ TileCtx tile_ctx(const ViewTable& vt, const uint32_t*
     return c;
 }
 
+// The threads that render one tile: the whole CTA (one tile per CTA), or a
+// single warp (one tile per warp, several tiles per CTA), whose barriers,
+// votes and reductions then stay inside the warp.  Warp teams lift the limit
+// of 32 resident CTAs per SM when a tile needs only 32 threads.
+template <bool WARP>
+struct Team {
+    int tid, size;
+    __device__ __forceinline__ Team() {
+        tid = WARP ? (int)(threadIdx.x & 31) : (int)threadIdx.x;
+        size = WARP ? 32 : (int)blockDim.x;
+    }
+    __device__ __forceinline__ void sync() const {
+        if (WARP) __syncwarp(); else __syncthreads();
+    }
+    // predicate vote that is also a barrier (shared memory ordered across it)
+    __device__ __forceinline__ bool any(bool p) const {
+        if (WARP) {
+            __syncwarp();
+            return __any_sync(0xffffffffu, p);
+        }
+        return __syncthreads_or(p) != 0;
+    }
+    // max over the team; scratch: one shared int (CTA teams only)
+    __device__ __forceinline__ int max(int v, int* scratch) const {
+        if (WARP) return (int)__reduce_max_sync(0xffffffffu, (unsigned)v);
+        if (threadIdx.x == 0) *scratch = 0;
+        __syncthreads();
+        atomicMax(scratch, v);
+        __syncthreads();
+        return *scratch;
+    }
+};
+
 // Gather records [first, first+cnt) of the tile list into stage (3 float4
 // each) and their (view*n + index) ids into ids.
-__device__ __forceinline__ void issue_batch(float4* stage, uint32_t* ids,
+template <class TM>
+__device__ __forceinline__ void issue_batch(const TM& tm, float4* stage, uint32_t* ids,
                                             const uint32_t* __restrict__ ivals,
                                             const float4* __restrict__ rec, uint32_t first,
                                             int cnt) {
-    for (int c = threadIdx.x; c < 3 * cnt; c += blockDim.x) {
+    for (int c = tm.tid; c < 3 * cnt; c += tm.size) {
         const int j = c / 3, part = c - 3 * j;
         const uint32_t vg = __ldg(ivals + first + j);
         cp_async16(stage + 3 * j + part, rec + (size_t)vg * 3 + part);
@@ -90,9 +124,11 @@ __device__ __forceinline__ void issue_batch(float4* stage, uint32_t* ids,
 // are sqrt(2 ln(255 o) (Q^-1)_xx) and sqrt(2 ln(255 o) (Q^-1)_yy); the box is
 // grown by 0.1% + 0.01 px, far beyond FP32 rounding, so every skipped
 // evaluation would have been skipped by the alpha test itself.
-__device__ __forceinline__ void localise_batch(float4* stage, uint32_t* wmask, int cnt, float tx0,
-                                               float ty0, int tile_w, int rows, int nwarps) {
-    for (int j = threadIdx.x; j < cnt; j += blockDim.x) {
+template <class TM>
+__device__ __forceinline__ void localise_batch(const TM& tm, float4* stage, uint32_t* wmask,
+                                               int cnt, float tx0, float ty0, int tile_w, int rows,
+                                               int nwarps) {
+    for (int j = tm.tid; j < cnt; j += tm.size) {
         float4 m = stage[3 * j];
         const float4 q = stage[3 * j + 1];
         float4 col = stage[3 * j + 2];
@@ -137,8 +173,8 @@ struct PixelRun {
     int lx0, ly;
 };
 
-__device__ __forceinline__ PixelRun pixel_run(int ppt, int log2_tw, int tile_w) {
-    const int p0 = threadIdx.x * ppt;
+__device__ __forceinline__ PixelRun pixel_run(int tid, int ppt, int log2_tw, int tile_w) {
+    const int p0 = tid * ppt;
     PixelRun r;
     r.lx0 = p0 & (tile_w - 1);
     r.ly = p0 >> log2_tw;
@@ -148,10 +184,10 @@ __device__ __forceinline__ PixelRun pixel_run(int ppt, int log2_tw, int tile_w) 
 // Front-to-back blending of one staged batch for the PPT pixels of a thread.
 // live: bit k set while pixel k still accumulates.
 template <int CH, int PPT>
-__device__ __forceinline__ void blend_batch(const float4* stage, const uint32_t* wmask, int cnt,
-                                            uint32_t pos0, int lx0, float ly, float* T,
+__device__ __forceinline__ void blend_batch(int tid, const float4* stage, const uint32_t* wmask,
+                                            int cnt, uint32_t pos0, int lx0, float ly, float* T,
                                             float (*C)[CH], int32_t* last, unsigned& live) {
-    const uint32_t wbit = 1u << (threadIdx.x >> 5);
+    const uint32_t wbit = 1u << (tid >> 5);
     for (int j = 0; j < cnt && live; ++j) {
         if (!(wmask[j] & wbit)) continue;
         const float4 g = stage[3 * j];
@@ -183,16 +219,16 @@ __device__ __forceinline__ void blend_batch(const float4* stage, const uint32_t*
     }
 }
 
-template <int CH, int PPT>
-__device__ void render_fwd_tile(const ViewTable& vt, const TileCtx& tc,
+template <int CH, int PPT, class TM>
+__device__ void render_fwd_tile(const TM& tm, const ViewTable& vt, const TileCtx& tc,
                                 const uint32_t* __restrict__ ivals,
                                 const float4* __restrict__ rec, float4* smem, int batch,
                                 const float* bg, float* __restrict__ images,
                                 float* __restrict__ final_T, int32_t* __restrict__ last_idx) {
     uint32_t* const mask0 = reinterpret_cast<uint32_t*>(smem + 6 * batch);
-    const int nwarps = blockDim.x >> 5;
+    const int nwarps = tm.size >> 5;
     const int rows = (32 * PPT) >> vt.log2_tw;
-    const PixelRun pr = pixel_run(PPT, vt.log2_tw, vt.tile_w);
+    const PixelRun pr = pixel_run(tm.tid, PPT, vt.log2_tw, vt.tile_w);
     const int py = tc.ty0 + pr.ly;
     float T[PPT], C[PPT][CH];
     int32_t last[PPT];
@@ -208,27 +244,27 @@ __device__ void render_fwd_tile(const ViewTable& vt, const TileCtx& tc,
     const int total = (int)(tc.end - tc.begin);
     const int nb = (total + batch - 1) / batch;
     if (nb > 0) {
-        issue_batch(smem, nullptr, ivals, rec, tc.begin, min(batch, total));
+        issue_batch(tm, smem, nullptr, ivals, rec, tc.begin, min(batch, total));
         cp_async_commit();
     }
     for (int b = 0; b < nb; ++b) {
         const int cnt = min(batch, total - b * batch);
         float4* cur = smem + (b & 1) * 3 * batch;
         if (b + 1 < nb) {
-            issue_batch(smem + ((b + 1) & 1) * 3 * batch, nullptr, ivals, rec,
+            issue_batch(tm, smem + ((b + 1) & 1) * 3 * batch, nullptr, ivals, rec,
                         tc.begin + (b + 1) * batch, min(batch, total - (b + 1) * batch));
             cp_async_commit();
             cp_async_wait_one();
         } else {
             cp_async_wait_all();
         }
-        __syncthreads();
+        tm.sync();
         uint32_t* cmask = mask0 + (b & 1) * batch;
-        localise_batch(cur, cmask, cnt, (float)tc.tx0, (float)tc.ty0, vt.tile_w, rows, nwarps);
-        __syncthreads();
-        blend_batch<CH, PPT>(cur, cmask, cnt, (uint32_t)(b * batch), pr.lx0, (float)pr.ly, T, C,
-                             last, live);
-        if (__syncthreads_count(live != 0u) == 0) {
+        localise_batch(tm, cur, cmask, cnt, (float)tc.tx0, (float)tc.ty0, vt.tile_w, rows, nwarps);
+        tm.sync();
+        blend_batch<CH, PPT>(tm.tid, cur, cmask, cnt, (uint32_t)(b * batch), pr.lx0,
+                             (float)pr.ly, T, C, last, live);
+        if (!tm.any(live != 0u)) {
             cp_async_wait_all();  // nothing may still be landing in shared memory
             break;
         }
@@ -263,10 +299,37 @@ __global__ void k_render_fwd(ViewTable vt, const uint32_t* __restrict__ ranges,
     extern __shared__ float4 smem[];
     const TileCtx tc = tile_ctx(vt, ranges, (int)order[blockIdx.x]);
     const float bg[3] = {bg0, bg1, bg2};
+    const Team<false> tm;
     if (tc.channels == 3)
-        render_fwd_tile<3, PPT>(vt, tc, ivals, rec, smem, batch, bg, images, final_T, last_idx);
+        render_fwd_tile<3, PPT>(tm, vt, tc, ivals, rec, smem, batch, bg, images, final_T, last_idx);
     else
-        render_fwd_tile<1, PPT>(vt, tc, ivals, rec, smem, batch, bg, images, final_T, last_idx);
+        render_fwd_tile<1, PPT>(tm, vt, tc, ivals, rec, smem, batch, bg, images, final_T, last_idx);
+}
+
+// One tile per warp, blockDim.x / 32 tiles per CTA, each warp with its own
+// slice of shared memory (team_f4 float4 per warp).
+constexpr int kMaxWarpTeams = 4;
+constexpr size_t kSmemDefault = 48 * 1024;  // dynamic shared memory without opt-in
+
+template <int PPT>
+__global__ void k_render_fwd_w(ViewTable vt, const uint32_t* __restrict__ ranges,
+                               const uint32_t* __restrict__ order,
+                               const uint32_t* __restrict__ ivals, const float4* __restrict__ rec,
+                               int batch, int team_f4, int total_tiles, float bg0, float bg1,
+                               float bg2, float* __restrict__ images, float* __restrict__ final_T,
+                               int32_t* __restrict__ last_idx) {
+    extern __shared__ float4 smem[];
+    const int w = threadIdx.x >> 5;
+    const int slot = blockIdx.x * (blockDim.x >> 5) + w;
+    if (slot >= total_tiles) return;
+    const TileCtx tc = tile_ctx(vt, ranges, (int)order[slot]);
+    const float bg[3] = {bg0, bg1, bg2};
+    const Team<true> tm;
+    float4* mine = smem + (size_t)w * team_f4;
+    if (tc.channels == 3)
+        render_fwd_tile<3, PPT>(tm, vt, tc, ivals, rec, mine, batch, bg, images, final_T, last_idx);
+    else
+        render_fwd_tile<1, PPT>(tm, vt, tc, ivals, rec, mine, batch, bg, images, final_T, last_idx);
 }
 
 // Warp reduce-scatter of 16 values by recursive halving: afterwards lane L
@@ -286,8 +349,8 @@ __device__ __forceinline__ float warp_reduce16(float* v) {
     return v[0] + __shfl_xor_sync(0xffffffffu, v[0], 1);
 }
 
-template <int CH, int PPT>
-__device__ void render_bwd_tile(const ViewTable& vt, const TileCtx& tc,
+template <int CH, int PPT, class TM>
+__device__ void render_bwd_tile(const TM& tm, const ViewTable& vt, const TileCtx& tc,
                                 const uint32_t* __restrict__ ivals,
                                 const float4* __restrict__ rec, float4* smem, int* s_maxlast,
                                 int batch, const float* bg, const float* __restrict__ final_T,
@@ -298,10 +361,10 @@ __device__ void render_bwd_tile(const ViewTable& vt, const TileCtx& tc,
     uint32_t* const ids0 = reinterpret_cast<uint32_t*>(smem + 6 * batch);
     uint32_t* const mask0 = ids0 + 2 * batch;
     float* const acc = reinterpret_cast<float*>(mask0 + 2 * batch);
-    const int nwarps = blockDim.x >> 5;
+    const int nwarps = tm.size >> 5;
     const int rows = (32 * PPT) >> vt.log2_tw;
-    const uint32_t wbit = 1u << (threadIdx.x >> 5);
-    const PixelRun pr = pixel_run(PPT, vt.log2_tw, vt.tile_w);
+    const uint32_t wbit = 1u << (tm.tid >> 5);
+    const PixelRun pr = pixel_run(tm.tid, PPT, vt.log2_tw, vt.tile_w);
     const int py = tc.ty0 + pr.ly;
     const float ly = (float)pr.ly;
     const int64_t plane = (int64_t)tc.width * tc.height;
@@ -328,19 +391,15 @@ __device__ void render_bwd_tile(const ViewTable& vt, const TileCtx& tc,
             mylast = max(mylast, last[k]);
         }
     }
-    if (threadIdx.x == 0) *s_maxlast = 0;
-    for (int i = threadIdx.x; i < kGrad2d * batch; i += blockDim.x) acc[i] = 0.0f;
-    __syncthreads();
-    atomicMax(s_maxlast, mylast);
-    __syncthreads();
-    const int maxlast = *s_maxlast;
+    for (int i = tm.tid; i < kGrad2d * batch; i += tm.size) acc[i] = 0.0f;
+    const int maxlast = tm.max(mylast, s_maxlast);
     const int nb = (maxlast + batch - 1) / batch;
     const int lane = threadIdx.x & 31;
     const int ncomp = CH == 3 ? kGrad2d : 7;
     // batch k covers list positions [max(0, maxlast - (k+1) batch), maxlast - k batch)
     if (nb > 0) {
         const int lo = max(0, maxlast - batch);
-        issue_batch(smem, ids0, ivals, rec, tc.begin + lo, maxlast - lo);
+        issue_batch(tm, smem, ids0, ivals, rec, tc.begin + lo, maxlast - lo);
         cp_async_commit();
     }
     for (int kb = 0; kb < nb; ++kb) {
@@ -351,16 +410,16 @@ __device__ void render_bwd_tile(const ViewTable& vt, const TileCtx& tc,
         uint32_t* cmask = mask0 + (kb & 1) * batch;
         if (kb + 1 < nb) {
             const int hi2 = lo, lo2 = max(0, hi2 - batch);
-            issue_batch(smem + ((kb + 1) & 1) * 3 * batch, ids0 + ((kb + 1) & 1) * batch, ivals,
-                        rec, tc.begin + lo2, hi2 - lo2);
+            issue_batch(tm, smem + ((kb + 1) & 1) * 3 * batch, ids0 + ((kb + 1) & 1) * batch,
+                        ivals, rec, tc.begin + lo2, hi2 - lo2);
             cp_async_commit();
             cp_async_wait_one();
         } else {
             cp_async_wait_all();
         }
-        __syncthreads();
-        localise_batch(cur, cmask, cnt, (float)tc.tx0, (float)tc.ty0, vt.tile_w, rows, nwarps);
-        __syncthreads();
+        tm.sync();
+        localise_batch(tm, cur, cmask, cnt, (float)tc.tx0, (float)tc.ty0, vt.tile_w, rows, nwarps);
+        tm.sync();
         for (int j = cnt - 1; j >= 0; --j) {
             if (!(cmask[j] & wbit)) continue;
             const int32_t pos = lo + j;
@@ -420,9 +479,9 @@ __device__ void render_bwd_tile(const ViewTable& vt, const TileCtx& tc,
                 if ((lane & 1) == 0 && comp < ncomp) atomicAdd(acc + j * kGrad2d + comp, tot);
             }
         }
-        __syncthreads();
+        tm.sync();
         // flush this batch's sums: one global atomic per (Gaussian, component, tile)
-        for (int i = threadIdx.x; i < kGrad2d * cnt; i += blockDim.x) {
+        for (int i = tm.tid; i < kGrad2d * cnt; i += tm.size) {
             const float a = acc[i];
             if (a != 0.0f) {
                 const int j = i / kGrad2d;
@@ -430,7 +489,7 @@ __device__ void render_bwd_tile(const ViewTable& vt, const TileCtx& tc,
                 acc[i] = 0.0f;
             }
         }
-        __syncthreads();
+        tm.sync();
     }
 }
 
@@ -445,11 +504,36 @@ __global__ void k_render_bwd(ViewTable vt, const uint32_t* __restrict__ ranges,
     __shared__ int s_maxlast;
     const TileCtx tc = tile_ctx(vt, ranges, (int)order[blockIdx.x]);
     const float bg[3] = {bg0, bg1, bg2};
+    const Team<false> tm;
     if (tc.channels == 3)
-        render_bwd_tile<3, PPT>(vt, tc, ivals, rec, smem, &s_maxlast, batch, bg, final_T,
+        render_bwd_tile<3, PPT>(tm, vt, tc, ivals, rec, smem, &s_maxlast, batch, bg, final_T,
                                 last_idx, dL, grad2d);
     else
-        render_bwd_tile<1, PPT>(vt, tc, ivals, rec, smem, &s_maxlast, batch, bg, final_T,
+        render_bwd_tile<1, PPT>(tm, vt, tc, ivals, rec, smem, &s_maxlast, batch, bg, final_T,
+                                last_idx, dL, grad2d);
+}
+
+template <int PPT>
+__global__ void k_render_bwd_w(ViewTable vt, const uint32_t* __restrict__ ranges,
+                               const uint32_t* __restrict__ order,
+                               const uint32_t* __restrict__ ivals, const float4* __restrict__ rec,
+                               int batch, int team_f4, int total_tiles, float bg0, float bg1,
+                               float bg2, const float* __restrict__ final_T,
+                               const int32_t* __restrict__ last_idx, const float* __restrict__ dL,
+                               float* __restrict__ grad2d) {
+    extern __shared__ float4 smem[];
+    const int w = threadIdx.x >> 5;
+    const int slot = blockIdx.x * (blockDim.x >> 5) + w;
+    if (slot >= total_tiles) return;
+    const TileCtx tc = tile_ctx(vt, ranges, (int)order[slot]);
+    const float bg[3] = {bg0, bg1, bg2};
+    const Team<true> tm;
+    float4* mine = smem + (size_t)w * team_f4;
+    if (tc.channels == 3)
+        render_bwd_tile<3, PPT>(tm, vt, tc, ivals, rec, mine, nullptr, batch, bg, final_T,
+                                last_idx, dL, grad2d);
+    else
+        render_bwd_tile<1, PPT>(tm, vt, tc, ivals, rec, mine, nullptr, batch, bg, final_T,
                                 last_idx, dL, grad2d);
 }
 
@@ -460,17 +544,45 @@ static K1 pick(int ppt, K1 a, K2 b, K4 c, K8 d) {
     return ppt == 1 ? a : ppt == 2 ? b : ppt == 4 ? c : d;
 }
 
+// Shared memory of one tile team, in float4 units: the double-buffered
+// stage (6 float4 per Gaussian slot) and the 32-bit arrays (2 per slot in the
+// forward: masks; 4 plus the nine gradient sums in the backward).
+static int team_f4(int batch, bool bwd) {
+    const size_t words = bwd ? (size_t)(4 + kGrad2d) * batch : (size_t)2 * batch;
+    return 6 * batch + (int)((words * 4 + 15) / 16);
+}
+
+// Warp teams per CTA: as many as fit the default dynamic shared memory, at
+// most kMaxWarpTeams (the largest batch still fits one).
+static int warp_teams(int tf4) {
+    const int t = (int)(kSmemDefault / ((size_t)tf4 * sizeof(float4)));
+    return t < 1 ? 1 : (t > kMaxWarpTeams ? kMaxWarpTeams : t);
+}
+
 gs_status launch_render_fwd(const Plan* p, const void* ws, float* images, float* final_T,
                             int32_t* last_idx, cudaStream_t st) {
     const int batch = p->cfg.smem_batch;
     const int ppt = p->cfg.pixels_per_thread;
-    const size_t smem = (size_t)2 * 3 * batch * sizeof(float4) + 2 * batch * sizeof(uint32_t);
     const int threads = p->cfg.tile_w * p->cfg.tile_h / ppt;
+    const int tf4 = team_f4(batch, false);
+    const uint32_t* ranges = cbuf<uint32_t>(p, ws, GS_BUF_RANGES);
+    const uint32_t* order = cbuf<uint32_t>(p, ws, B_TILE_ORDER);
+    const uint32_t* vals =
+        cbuf<uint32_t>(p, ws, (p->tile_passes & 1) ? (int)B_IVAL_B : (int)GS_BUF_TILE_VALUES);
+    const float4* rec = cbuf<float4>(p, ws, GS_BUF_PROJ);
+    if (threads == 32) {
+        auto kern = pick(ppt, k_render_fwd_w<1>, k_render_fwd_w<2>, k_render_fwd_w<4>,
+                         k_render_fwd_w<8>);
+        const int teams = warp_teams(tf4);
+        const int blocks = (p->total_tiles + teams - 1) / teams;
+        kern<<<blocks, 32 * teams, (size_t)teams * tf4 * sizeof(float4), st>>>(
+            p->vt, ranges, order, vals, rec, batch, tf4, p->total_tiles, p->cfg.bg[0],
+            p->cfg.bg[1], p->cfg.bg[2], images, final_T, last_idx);
+        return launch_status();
+    }
     auto kern = pick(ppt, k_render_fwd<1>, k_render_fwd<2>, k_render_fwd<4>, k_render_fwd<8>);
-    kern<<<p->total_tiles, threads, smem, st>>>(
-        p->vt, cbuf<uint32_t>(p, ws, GS_BUF_RANGES), cbuf<uint32_t>(p, ws, B_TILE_ORDER),
-        cbuf<uint32_t>(p, ws, (p->tile_passes & 1) ? (int)B_IVAL_B : (int)GS_BUF_TILE_VALUES),
-        cbuf<float4>(p, ws, GS_BUF_PROJ), batch, p->cfg.bg[0], p->cfg.bg[1], p->cfg.bg[2], images,
+    kern<<<p->total_tiles, threads, (size_t)tf4 * sizeof(float4), st>>>(
+        p->vt, ranges, order, vals, rec, batch, p->cfg.bg[0], p->cfg.bg[1], p->cfg.bg[2], images,
         final_T, last_idx);
     return launch_status();
 }
@@ -479,16 +591,28 @@ gs_status launch_render_bwd_pixels(const Plan* p, void* ws, const float* final_T
                                    const int32_t* last_idx, const float* dL, cudaStream_t st) {
     const int batch = p->cfg.smem_batch_bwd;
     const int ppt = p->cfg.pixels_per_thread_bwd;
-    const size_t smem = (size_t)2 * 3 * batch * sizeof(float4) + 4 * batch * sizeof(uint32_t) +
-                        (size_t)kGrad2d * batch * sizeof(float);
     const int threads = p->cfg.tile_w * p->cfg.tile_h / ppt;
+    const int tf4 = team_f4(batch, true);
     float* grad2d = buf<float>(p, ws, GS_BUF_GRAD2D);
     if (cudaMemsetAsync(grad2d, 0, p->len[GS_BUF_GRAD2D], st) != cudaSuccess) return GS_ERR_CUDA;
+    const uint32_t* ranges = cbuf<uint32_t>(p, ws, GS_BUF_RANGES);
+    const uint32_t* order = cbuf<uint32_t>(p, ws, B_TILE_ORDER);
+    const uint32_t* vals =
+        cbuf<uint32_t>(p, ws, (p->tile_passes & 1) ? (int)B_IVAL_B : (int)GS_BUF_TILE_VALUES);
+    const float4* rec = cbuf<float4>(p, ws, GS_BUF_PROJ);
+    if (threads == 32) {
+        auto kern = pick(ppt, k_render_bwd_w<1>, k_render_bwd_w<2>, k_render_bwd_w<4>,
+                         k_render_bwd_w<8>);
+        const int teams = warp_teams(tf4);
+        const int blocks = (p->total_tiles + teams - 1) / teams;
+        kern<<<blocks, 32 * teams, (size_t)teams * tf4 * sizeof(float4), st>>>(
+            p->vt, ranges, order, vals, rec, batch, tf4, p->total_tiles, p->cfg.bg[0],
+            p->cfg.bg[1], p->cfg.bg[2], final_T, last_idx, dL, grad2d);
+        return launch_status();
+    }
     auto kern = pick(ppt, k_render_bwd<1>, k_render_bwd<2>, k_render_bwd<4>, k_render_bwd<8>);
-    kern<<<p->total_tiles, threads, smem, st>>>(
-        p->vt, cbuf<uint32_t>(p, ws, GS_BUF_RANGES), cbuf<uint32_t>(p, ws, B_TILE_ORDER),
-        cbuf<uint32_t>(p, ws, (p->tile_passes & 1) ? (int)B_IVAL_B : (int)GS_BUF_TILE_VALUES),
-        cbuf<float4>(p, ws, GS_BUF_PROJ), batch, p->cfg.bg[0], p->cfg.bg[1], p->cfg.bg[2],
+    kern<<<p->total_tiles, threads, (size_t)tf4 * sizeof(float4), st>>>(
+        p->vt, ranges, order, vals, rec, batch, p->cfg.bg[0], p->cfg.bg[1], p->cfg.bg[2],
         final_T, last_idx, dL, grad2d);
     return launch_status();
 }

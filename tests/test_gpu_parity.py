@@ -152,21 +152,25 @@ def test_pixels_per_thread_do_not_change_results(tile, ppts):
         assert U.rel_l2(out[3].cpu().numpy(), ref[3].cpu().numpy()) < 1e-5
 
 
-def test_render_grayscale_and_mixed_batch():
+@pytest.mark.parametrize("tile,ppt", [((16, 16), 1), ((8, 8), 2)])
+def test_render_grayscale_and_mixed_batch(tile, ppt):
     """One launch over three views of different sizes and channel counts equals
-    the oracle view by view."""
+    the oracle view by view, with one tile per CTA and with one tile per warp
+    (8x8 tiles at two pixels per thread, where one CTA holds tiles of
+    different views)."""
     p = scenes.room_scene(20_000, seed=41)
     views = [scenes.camera(160, 120, 131.25, 131.25),
              dict(scenes.camera(188, 120, 115.0, 115.0, channels=1)),
              posed(scenes.camera(300, 170, 150.0, 150.0), 7, 0.2, 10.0)]
     gm = mapping.GaussianMap(p)
-    rast = mapping.Rasterizer(views, gm.n, instance_capacity=1 << 21, bg=(0.2, 0.4, 0.6))
+    rast = mapping.Rasterizer(views, gm.n, instance_capacity=1 << 21, bg=(0.2, 0.4, 0.6),
+                              tile=tile, pixels_per_thread=ppt)
     rast.forward(gm.gs_map())
     torch.cuda.synchronize()
     for v, view in enumerate(views):
         img = rast.view_slice(rast.images, v).cpu().numpy()
-        proj, st, lst, o = oracle.forward_view(p, view, bg=(0.2, 0.4, 0.6))
-        ok = ~U.guard_pixel_mask(view, proj, o)
+        proj, st, lst, o = oracle.forward_view(p, view, tile[0], tile[1], bg=(0.2, 0.4, 0.6))
+        ok = ~U.guard_pixel_mask(view, proj, o, tile)
         assert np.abs(img - o["image"])[:, ok].max() <= IMG_TOL
 
 
