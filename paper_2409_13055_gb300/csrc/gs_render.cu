@@ -5,8 +5,10 @@
 // adjoint walking each list back to front.
 //
 // GB300 design:
-//  * one CTA per 2D tile of one view, one thread per pixel; all views of a
-//    batch share the launch (the CTA looks its view up from the tile id);
+//  * one CTA per 2D tile of one view, or one warp per tile (several tiles
+//    per CTA) when a tile needs 32 threads; all views of a batch share the
+//    launch (each tile looks its view up from the tile id); tiles are taken
+//    heavy-first, by the length of their lists;
 //  * each CTA streams its tile's Gaussians through shared memory in batches
 //    of `smem_batch` records gathered with cp.async, double-buffered so the
 //    gather of batch k+1 (L2-resident records, random order) overlaps the
@@ -20,10 +22,12 @@
 //  * register blocking: each thread owns 1-8 consecutive pixels of a tile
 //    row, so every staged Gaussian is read from shared memory once per
 //    thread, not once per pixel;
-//  * the backward sums each Gaussian's nine gradient components over the
-//    thread's pixels, then over the warp with a recursive-halving
-//    reduce-scatter (16 shuffles, skipped when no lane touches the
-//    Gaussian), and issues them as nine parallel atomics.
+//  * the backward sums, per Gaussian, the moments of dL/dpower and the
+//    colour weights (nine values, from which the screen-space gradient is
+//    linear) over the thread's pixels, then over the warp with a split
+//    reduce-scatter (12 shuffles, skipped when no lane touches the
+//    Gaussian), into shared memory; once per batch they become the gradient
+//    and leave as nine parallel atomics per Gaussian.
 #include "gs_internal.cuh"
 
 namespace gs {
@@ -88,6 +92,11 @@ struct Team {
             return __any_sync(0xffffffffu, p);
         }
         return __syncthreads_or(p) != 0;
+    }
+    // shared-memory accumulation: plain in a warp team, whose lanes write
+    // distinct addresses; atomic when several warps share the sums
+    __device__ __forceinline__ void add(float* a, float v) const {
+        if (WARP) *a += v; else atomicAdd(a, v);
     }
     // max over the team; scratch: one shared int (CTA teams only)
     __device__ __forceinline__ int max(int v, int* scratch) const {
@@ -332,23 +341,70 @@ __global__ void k_render_fwd_w(ViewTable vt, const uint32_t* __restrict__ ranges
         render_fwd_tile<1, PPT>(tm, vt, tc, ivals, rec, mine, batch, bg, images, final_T, last_idx);
 }
 
-// Warp reduce-scatter of 16 values by recursive halving: afterwards lane L
-// holds the warp total of value L >> 1 (16 shuffles instead of 5 per value).
-__device__ __forceinline__ float warp_reduce16(float* v) {
-    const int lane = threadIdx.x & 31;
+// Warp reduce-scatter of N values (N = 9 or 7).  At the levels with lane
+// offsets 16, 8, 4, 2 a lane holding S partial sums keeps the first
+// ceil(S/2) (offset bit clear) or the rest (bit set, padded with a zero) and
+// sends the other part to its partner; once one sum is left the remaining
+// levels add it across lanes.  N = 9 takes 12 shuffles (a 16-wide
+// reduce-scatter takes 16).  Returns the warp total of the component that
+// reduce_component(lane) names.
+template <int N, int O = 16>
+__device__ __forceinline__ float warp_reduce_split(float* v) {
+    constexpr int K = (N + 1) / 2;
+    if (N == 1) {
+        v[0] += __shfl_xor_sync(0xffffffffu, v[0], O);
+    } else {
+        const bool up = (threadIdx.x & O) != 0;
 #pragma unroll
-    for (int h = 8, o = 16; h >= 1; h >>= 1, o >>= 1) {
-        const bool up = (lane & o) != 0;
-#pragma unroll
-        for (int i = 0; i < h; ++i) {
-            const float send = up ? v[i] : v[i + h];
-            const float keep = up ? v[i + h] : v[i];
-            v[i] = keep + __shfl_xor_sync(0xffffffffu, send, o);
+        for (int i = 0; i < K; ++i) {
+            const float lo = v[i];
+            const float hi = i + K < N ? v[i + K] : 0.0f;
+            v[i] = (up ? hi : lo) + __shfl_xor_sync(0xffffffffu, up ? lo : hi, O);
         }
     }
-    return v[0] + __shfl_xor_sync(0xffffffffu, v[0], 1);
+    if constexpr (O > 1) return warp_reduce_split<(N == 1 ? 1 : K), O / 2>(v);
+    return v[0];
 }
 
+// The component whose total warp_reduce_split<N> leaves in this lane, or -1
+// when the lane holds padding or a copy that another lane reports.
+template <int N>
+__device__ __forceinline__ int reduce_component(int lane) {
+    int sizes[5];
+    for (int L = 0, s = N; L < 5; ++L, s = (s + 1) / 2) sizes[L] = s;
+    int idx = 0;
+    for (int L = 4; L >= 0; --L) {
+        const int S = sizes[L], O = 16 >> L;
+        if (S == 1) {
+            if (lane & O) return -1;
+            continue;
+        }
+        if (lane & O) idx += (S + 1) / 2;
+        if (idx >= S) return -1;
+    }
+    return idx;
+}
+
+// Reciprocal by the hardware approximation (PTX rcp.approx.ftz.f32, within
+// about one ulp); the argument 1 - alpha lies in [0.01, 1].
+__device__ __forceinline__ float rcp_approx(float x) {
+    float y;
+    asm("rcp.approx.ftz.f32 %0, %1;" : "=f"(y) : "f"(x));
+    return y;
+}
+
+// Back-to-front adjoint of one tile (Eq. 1 differentiated; the transmittance
+// before each Gaussian is recovered by dividing by 1 - alpha).  Per pixel the
+// colour accumulated behind the current Gaussian enters only through its dot
+// product with dL/dC, so one scalar gS = dL/dC . S is carried instead of S.
+// Per Gaussian the lanes sum the moments of dL/dpower,
+//   A0 = sum dp, A1 = sum dp dx, A2 = sum dp dy, A3 = sum dp dx^2,
+//   A4 = sum dp dx dy, A5 = sum dp dy^2   (dx, dy = mean - pixel),
+// and the colour weights; with power = -(a dx^2 + c dy^2)/2 - b dx dy the
+// screen-space gradient is linear in them:
+//   dL/dmean = -(a A1 + b A2, b A1 + c A2), dL/d(a, b, c) = (-A3/2, -A4, -A5/2),
+//   dL/do = A0 / o   (dp = o G dL/dalpha wherever alpha = o G is unclamped),
+// which is applied once per Gaussian and batch, before the global atomics.
 template <int CH, int PPT, class TM>
 __device__ void render_bwd_tile(const TM& tm, const ViewTable& vt, const TileCtx& tc,
                                 const uint32_t* __restrict__ ivals,
@@ -357,7 +413,8 @@ __device__ void render_bwd_tile(const TM& tm, const ViewTable& vt, const TileCtx
                                 const int32_t* __restrict__ last_idx,
                                 const float* __restrict__ dL, float* __restrict__ grad2d) {
     // shared memory: stage[2][3*batch] float4 | ids[2][batch] | masks[2][batch] |
-    //                acc[batch][9] float (the batch's per-Gaussian gradient sums)
+    //                acc[batch][9] float (the batch's per-Gaussian sums)
+    constexpr int NC = CH == 3 ? kGrad2d : 7;  // moments + colour components
     uint32_t* const ids0 = reinterpret_cast<uint32_t*>(smem + 6 * batch);
     uint32_t* const mask0 = ids0 + 2 * batch;
     float* const acc = reinterpret_cast<float*>(mask0 + 2 * batch);
@@ -369,7 +426,7 @@ __device__ void render_bwd_tile(const TM& tm, const ViewTable& vt, const TileCtx
     const float ly = (float)pr.ly;
     const int64_t plane = (int64_t)tc.width * tc.height;
     const float bgg = (bg[0] + bg[1] + bg[2]) * (1.0f / 3.0f);
-    float T[PPT], g[PPT][CH], S[PPT][CH];
+    float T[PPT], g[PPT][CH], gS[PPT];
     int32_t last[PPT];
     int mylast = 0;
 #pragma unroll
@@ -377,25 +434,27 @@ __device__ void render_bwd_tile(const TM& tm, const ViewTable& vt, const TileCtx
         const int px = tc.tx0 + pr.lx0 + k;
         last[k] = 0;
         T[k] = 1.0f;
+        gS[k] = 0.0f;
 #pragma unroll
-        for (int c = 0; c < CH; ++c) g[k][c] = S[k][c] = 0.0f;
+        for (int c = 0; c < CH; ++c) g[k][c] = 0.0f;
         if (px < tc.width && py < tc.height) {
             const int64_t pix = (int64_t)py * tc.width + px;
             last[k] = last_idx[tc.pix_base + pix];
             T[k] = final_T[tc.pix_base + pix];
+            float gb = 0.0f;
 #pragma unroll
             for (int c = 0; c < CH; ++c) {
                 g[k][c] = dL[tc.val_base + c * plane + pix];
-                S[k][c] = T[k] * (CH == 3 ? bg[c] : bgg);
+                gb = fmaf(g[k][c], CH == 3 ? bg[c] : bgg, gb);
             }
+            gS[k] = T[k] * gb;  // the background seen through T_final
             mylast = max(mylast, last[k]);
         }
     }
     for (int i = tm.tid; i < kGrad2d * batch; i += tm.size) acc[i] = 0.0f;
     const int maxlast = tm.max(mylast, s_maxlast);
     const int nb = (maxlast + batch - 1) / batch;
-    const int lane = threadIdx.x & 31;
-    const int ncomp = CH == 3 ? kGrad2d : 7;
+    const int comp = reduce_component<NC>(threadIdx.x & 31);
     // batch k covers list positions [max(0, maxlast - (k+1) batch), maxlast - k batch)
     if (nb > 0) {
         const int lo = max(0, maxlast - batch);
@@ -427,9 +486,9 @@ __device__ void render_bwd_tile(const TM& tm, const ViewTable& vt, const TileCtx
             const float4 q = cur[3 * j + 1];
             const float4 col = cur[3 * j + 2];
             const float dy = gm.y - ly;
-            float v[16];
+            float P0 = 0.0f, P1 = 0.0f, P3 = 0.0f, cw[CH];
 #pragma unroll
-            for (int i = 0; i < 16; ++i) v[i] = 0.0f;
+            for (int c = 0; c < CH; ++c) cw[c] = 0.0f;
             bool contrib = false;
 #pragma unroll
             for (int k = 0; k < PPT; ++k) {
@@ -443,41 +502,57 @@ __device__ void render_bwd_tile(const TM& tm, const ViewTable& vt, const TileCtx
                 const float alpha = fminf(kAlphaMax, oG);
                 const bool hit = pos < last[k] && power <= 0.0f && alpha >= kAlphaMin;
                 contrib |= hit;
-                const float inv = __frcp_rn(__fsub_rn(1.0f, alpha));
+                const float inv = rcp_approx(1.0f - alpha);
                 const float Ti = T[k] * inv;
                 const float w = hit ? alpha * Ti : 0.0f;
-                float dal;
-                if (CH == 3) {
-                    dal = g[k][0] * (Ti * col.x - S[k][0] * inv) +
-                          g[k][1] * (Ti * col.y - S[k][1] * inv) +
-                          g[k][2] * (Ti * col.z - S[k][2] * inv);
-                    S[k][0] = fmaf(w, col.x, S[k][0]);
-                    S[k][1] = fmaf(w, col.y, S[k][1]);
-                    S[k][2] = fmaf(w, col.z, S[k][2]);
-                    v[6] = fmaf(w, g[k][0], v[6]);
-                    v[7] = fmaf(w, g[k][1], v[7]);
-                    v[8] = fmaf(w, g[k][2], v[8]);
-                } else {
-                    dal = g[k][0] * (Ti * col.w - S[k][0] * inv);
-                    S[k][0] = fmaf(w, col.w, S[k][0]);
-                    v[6] = fmaf(w, g[k][0], v[6]);
-                }
+                float gc;
+                if (CH == 3)
+                    gc = fmaf(g[k][2], col.z, fmaf(g[k][1], col.y, g[k][0] * col.x));
+                else
+                    gc = g[k][0] * col.w;
+                const float dal = fmaf(Ti, gc, -inv * gS[k]);
+                gS[k] = fmaf(w, gc, gS[k]);
+#pragma unroll
+                for (int c = 0; c < CH; ++c) cw[c] = fmaf(w, g[k][c], cw[c]);
                 T[k] = hit ? Ti : T[k];
                 // alpha = o G when unclamped; a clamped alpha passes no gradient
-                const bool free_a = hit && oG < kAlphaMax;
-                const float dpow = free_a ? oG * dal : 0.0f;
-                v[0] -= dpow * (gm.z * dx + gm.w * dy);
-                v[1] -= dpow * (gm.w * dx + q.z * dy);
-                v[2] -= 0.5f * dpow * dx * dx;
-                v[3] -= dpow * dx * dy;
-                v[4] -= 0.5f * dpow * dy * dy;
-                v[5] = fmaf(free_a ? G : 0.0f, dal, v[5]);
+                const float dp = (hit && oG < kAlphaMax) ? oG * dal : 0.0f;
+                const float t = dp * dx;
+                P0 += dp;
+                P1 += t;
+                P3 = fmaf(t, dx, P3);
             }
             if (__any_sync(0xffffffffu, contrib)) {
-                const float tot = warp_reduce16(v);
-                const int comp = lane >> 1;
-                if ((lane & 1) == 0 && comp < ncomp) atomicAdd(acc + j * kGrad2d + comp, tot);
+                // the pixels of a run share dy: A2 = dy A0, A4 = dy A1, A5 = dy A2
+                float v[NC];
+                v[0] = P0;
+                v[1] = P1;
+                v[2] = dy * P0;
+                v[3] = P3;
+                v[4] = dy * P1;
+                v[5] = dy * v[2];
+#pragma unroll
+                for (int c = 0; c < CH; ++c) v[6 + c] = cw[c];
+                const float tot = warp_reduce_split<NC>(v);
+                if (comp >= 0) tm.add(acc + j * kGrad2d + comp, tot);
             }
+        }
+        tm.sync();
+        // moments -> screen-space gradient (see above), one Gaussian per thread
+        for (int j = tm.tid; j < cnt; j += tm.size) {
+            float* a = acc + j * kGrad2d;
+            const float A0 = a[0], A1 = a[1], A2 = a[2];
+            if (A0 == 0.0f && A1 == 0.0f && A2 == 0.0f && a[3] == 0.0f && a[4] == 0.0f &&
+                a[5] == 0.0f)
+                continue;
+            const float ca = cur[3 * j].z, cb = cur[3 * j].w;
+            const float4 q = cur[3 * j + 1];
+            a[0] = -fmaf(ca, A1, cb * A2);
+            a[1] = -fmaf(cb, A1, q.z * A2);
+            a[2] = -0.5f * a[3];
+            a[3] = -a[4];
+            a[4] = -0.5f * a[5];
+            a[5] = A0 != 0.0f ? A0 / q.w : 0.0f;
         }
         tm.sync();
         // flush this batch's sums: one global atomic per (Gaussian, component, tile)
