@@ -192,8 +192,9 @@ gs_status gs_bin_sort(const gs_plan *plan, int32_t n, void *ws, void *stream);
  * - b dx dy, skipped when > 0; alpha = min(0.99, o e^power), skipped when
  * < 1/255; the Gaussian that would take T below 1e-4 stops the pixel and is
  * not added.  Writes images (packed planar), final_T and last_idx (one past
- * the list position of the last blended Gaussian, 0 if none). */
-gs_status gs_render_fwd(const gs_plan *plan, const void *ws, float *images, float *final_T,
+ * the list position of the last blended Gaussian, 0 if none).  Of ws it
+ * writes only the tile-queue counter of its persistent launch. */
+gs_status gs_render_fwd(const gs_plan *plan, void *ws, float *images, float *final_T,
                         int32_t *last_idx, void *stream);
 
 /* A6: photometric loss, Eq. 2 read as

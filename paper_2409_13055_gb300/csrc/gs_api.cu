@@ -126,6 +126,7 @@ extern "C" gs_status gs_plan_init(gs_plan* plan, const gs_config* cfg, int32_t n
     len[B_OFFSETS] = (size_t)(VN + 1) * sizeof(uint32_t);
     len[B_TILE_ORDER] = (size_t)tiles * sizeof(uint32_t);
     len[B_GMEAN] = (size_t)n_capacity * 3 * sizeof(float);
+    len[B_TILE_QUEUE] = 2 * sizeof(uint32_t);
     size_t off = 0;
     for (int b = 0; b < B_TOTAL; ++b) {
         p->off[b] = off;
@@ -196,7 +197,7 @@ extern "C" gs_status gs_bin_sort(const gs_plan* plan, int32_t n, void* ws, void*
     return launch_bin_sort(P(plan), n, ws, S(stream));
 }
 
-extern "C" gs_status gs_render_fwd(const gs_plan* plan, const void* ws, float* images,
+extern "C" gs_status gs_render_fwd(const gs_plan* plan, void* ws, float* images,
                                    float* final_T, int32_t* last_idx, void* stream) {
     if (!plan_ok(plan) || !ws || !images || !final_T || !last_idx) return GS_ERR_INVALID;
     return launch_render_fwd(P(plan), ws, images, final_T, last_idx, S(stream));

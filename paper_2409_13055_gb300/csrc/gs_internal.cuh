@@ -53,6 +53,7 @@ enum PrivBuf {
     B_OFFSETS,  // [V*n + 1] instance offsets of the entries in depth order
     B_TILE_ORDER,  // [total_tiles] render order of the tiles, longest lists first
     B_GMEAN,       // [n] x 3 mean gradients held between the fused adjoint kernels
+    B_TILE_QUEUE,  // [2] u32 next-tile counters of the forward and backward render
     B_TOTAL
 };
 
@@ -207,7 +208,7 @@ constexpr float kTMin = 1e-4f;
 gs_status launch_project(const Plan* p, const gs_map* map, const gs_view* views_dev, void* ws,
                          cudaStream_t st);
 gs_status launch_bin_sort(const Plan* p, int32_t n, void* ws, cudaStream_t st);
-gs_status launch_render_fwd(const Plan* p, const void* ws, float* images, float* final_T,
+gs_status launch_render_fwd(const Plan* p, void* ws, float* images, float* final_T,
                             int32_t* last_idx, cudaStream_t st);
 gs_status launch_loss(const Plan* p, const float* images, const float* targets, float lambda,
                       float view_weight, float* loss_dev, float* dL, void* ws, cudaStream_t st);

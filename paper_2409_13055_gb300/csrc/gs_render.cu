@@ -28,6 +28,8 @@
 //    reduce-scatter (12 shuffles, skipped when no lane touches the
 //    Gaussian), into shared memory; once per batch they become the gradient
 //    and leave as nine parallel atomics per Gaussian.
+#include <mutex>
+
 #include "gs_internal.cuh"
 
 namespace gs {
@@ -92,6 +94,19 @@ struct Team {
             return __any_sync(0xffffffffu, p);
         }
         return __syncthreads_or(p) != 0;
+    }
+    // the next tile slot from the launch's queue counter (q), taken by one
+    // thread; scratch: one shared int (CTA teams only)
+    __device__ __forceinline__ int next(uint32_t* q, int* scratch) const {
+        if (WARP) {
+            int s = 0;
+            if (tid == 0) s = (int)atomicAdd(q, 1u);
+            return __shfl_sync(0xffffffffu, s, 0);
+        }
+        __syncthreads();  // every thread has read the previous slot
+        if (threadIdx.x == 0) *scratch = (int)atomicAdd(q, 1u);
+        __syncthreads();
+        return *scratch;
     }
     // shared-memory accumulation: plain in a warp team, whose lanes write
     // distinct addresses; atomic when several warps share the sums
@@ -298,48 +313,38 @@ __device__ void render_fwd_tile(const TM& tm, const ViewTable& vt, const TileCtx
     }
 }
 
-template <int PPT>
+// Persistent render kernels: each team (the CTA, or one warp of it) takes
+// the next slot of the heavy-first tile order from a queue counter until the
+// order is exhausted, so a team that drew a short list moves on at once
+// (longest-first list scheduling).  A warp team owns team_f4 float4 of the
+// CTA's dynamic shared memory.
+template <int PPT, bool WARP>
 __global__ void k_render_fwd(ViewTable vt, const uint32_t* __restrict__ ranges,
                              const uint32_t* __restrict__ order,
                              const uint32_t* __restrict__ ivals, const float4* __restrict__ rec,
-                             int batch, float bg0, float bg1, float bg2,
-                             float* __restrict__ images, float* __restrict__ final_T,
-                             int32_t* __restrict__ last_idx) {
+                             int batch, int team_f4, int total_tiles, uint32_t* queue, float bg0,
+                             float bg1, float bg2, float* __restrict__ images,
+                             float* __restrict__ final_T, int32_t* __restrict__ last_idx) {
     extern __shared__ float4 smem[];
-    const TileCtx tc = tile_ctx(vt, ranges, (int)order[blockIdx.x]);
+    __shared__ int s_slot;
+    const Team<WARP> tm;
+    float4* mine = smem + (WARP ? (size_t)(threadIdx.x >> 5) * team_f4 : 0);
     const float bg[3] = {bg0, bg1, bg2};
-    const Team<false> tm;
-    if (tc.channels == 3)
-        render_fwd_tile<3, PPT>(tm, vt, tc, ivals, rec, smem, batch, bg, images, final_T, last_idx);
-    else
-        render_fwd_tile<1, PPT>(tm, vt, tc, ivals, rec, smem, batch, bg, images, final_T, last_idx);
+    for (;;) {
+        const int slot = tm.next(queue, &s_slot);
+        if (slot >= total_tiles) break;
+        const TileCtx tc = tile_ctx(vt, ranges, (int)order[slot]);
+        if (tc.channels == 3)
+            render_fwd_tile<3, PPT>(tm, vt, tc, ivals, rec, mine, batch, bg, images, final_T,
+                                    last_idx);
+        else
+            render_fwd_tile<1, PPT>(tm, vt, tc, ivals, rec, mine, batch, bg, images, final_T,
+                                    last_idx);
+    }
 }
 
-// One tile per warp, blockDim.x / 32 tiles per CTA, each warp with its own
-// slice of shared memory (team_f4 float4 per warp).
 constexpr int kMaxWarpTeams = 4;
 constexpr size_t kSmemDefault = 48 * 1024;  // dynamic shared memory without opt-in
-
-template <int PPT>
-__global__ void k_render_fwd_w(ViewTable vt, const uint32_t* __restrict__ ranges,
-                               const uint32_t* __restrict__ order,
-                               const uint32_t* __restrict__ ivals, const float4* __restrict__ rec,
-                               int batch, int team_f4, int total_tiles, float bg0, float bg1,
-                               float bg2, float* __restrict__ images, float* __restrict__ final_T,
-                               int32_t* __restrict__ last_idx) {
-    extern __shared__ float4 smem[];
-    const int w = threadIdx.x >> 5;
-    const int slot = blockIdx.x * (blockDim.x >> 5) + w;
-    if (slot >= total_tiles) return;
-    const TileCtx tc = tile_ctx(vt, ranges, (int)order[slot]);
-    const float bg[3] = {bg0, bg1, bg2};
-    const Team<true> tm;
-    float4* mine = smem + (size_t)w * team_f4;
-    if (tc.channels == 3)
-        render_fwd_tile<3, PPT>(tm, vt, tc, ivals, rec, mine, batch, bg, images, final_T, last_idx);
-    else
-        render_fwd_tile<1, PPT>(tm, vt, tc, ivals, rec, mine, batch, bg, images, final_T, last_idx);
-}
 
 // Warp reduce-scatter of N values (N = 9 or 7).  At the levels with lane
 // offsets 16, 8, 4, 2 a lane holding S partial sums keeps the first
@@ -568,54 +573,36 @@ __device__ void render_bwd_tile(const TM& tm, const ViewTable& vt, const TileCtx
     }
 }
 
-template <int PPT>
+template <int PPT, bool WARP>
 __global__ void k_render_bwd(ViewTable vt, const uint32_t* __restrict__ ranges,
                              const uint32_t* __restrict__ order,
                              const uint32_t* __restrict__ ivals, const float4* __restrict__ rec,
-                             int batch, float bg0, float bg1, float bg2,
-                             const float* __restrict__ final_T, const int32_t* __restrict__ last_idx,
-                             const float* __restrict__ dL, float* __restrict__ grad2d) {
+                             int batch, int team_f4, int total_tiles, uint32_t* queue, float bg0,
+                             float bg1, float bg2, const float* __restrict__ final_T,
+                             const int32_t* __restrict__ last_idx, const float* __restrict__ dL,
+                             float* __restrict__ grad2d) {
     extern __shared__ float4 smem[];
-    __shared__ int s_maxlast;
-    const TileCtx tc = tile_ctx(vt, ranges, (int)order[blockIdx.x]);
+    __shared__ int s_slot, s_maxlast;
+    const Team<WARP> tm;
+    float4* mine = smem + (WARP ? (size_t)(threadIdx.x >> 5) * team_f4 : 0);
     const float bg[3] = {bg0, bg1, bg2};
-    const Team<false> tm;
-    if (tc.channels == 3)
-        render_bwd_tile<3, PPT>(tm, vt, tc, ivals, rec, smem, &s_maxlast, batch, bg, final_T,
-                                last_idx, dL, grad2d);
-    else
-        render_bwd_tile<1, PPT>(tm, vt, tc, ivals, rec, smem, &s_maxlast, batch, bg, final_T,
-                                last_idx, dL, grad2d);
-}
-
-template <int PPT>
-__global__ void k_render_bwd_w(ViewTable vt, const uint32_t* __restrict__ ranges,
-                               const uint32_t* __restrict__ order,
-                               const uint32_t* __restrict__ ivals, const float4* __restrict__ rec,
-                               int batch, int team_f4, int total_tiles, float bg0, float bg1,
-                               float bg2, const float* __restrict__ final_T,
-                               const int32_t* __restrict__ last_idx, const float* __restrict__ dL,
-                               float* __restrict__ grad2d) {
-    extern __shared__ float4 smem[];
-    const int w = threadIdx.x >> 5;
-    const int slot = blockIdx.x * (blockDim.x >> 5) + w;
-    if (slot >= total_tiles) return;
-    const TileCtx tc = tile_ctx(vt, ranges, (int)order[slot]);
-    const float bg[3] = {bg0, bg1, bg2};
-    const Team<true> tm;
-    float4* mine = smem + (size_t)w * team_f4;
-    if (tc.channels == 3)
-        render_bwd_tile<3, PPT>(tm, vt, tc, ivals, rec, mine, nullptr, batch, bg, final_T,
-                                last_idx, dL, grad2d);
-    else
-        render_bwd_tile<1, PPT>(tm, vt, tc, ivals, rec, mine, nullptr, batch, bg, final_T,
-                                last_idx, dL, grad2d);
+    for (;;) {
+        const int slot = tm.next(queue, &s_slot);
+        if (slot >= total_tiles) break;
+        const TileCtx tc = tile_ctx(vt, ranges, (int)order[slot]);
+        if (tc.channels == 3)
+            render_bwd_tile<3, PPT>(tm, vt, tc, ivals, rec, mine, &s_maxlast, batch, bg, final_T,
+                                    last_idx, dL, grad2d);
+        else
+            render_bwd_tile<1, PPT>(tm, vt, tc, ivals, rec, mine, &s_maxlast, batch, bg, final_T,
+                                    last_idx, dL, grad2d);
+    }
 }
 
 }  // namespace
 
-template <typename K1, typename K2, typename K4, typename K8>
-static K1 pick(int ppt, K1 a, K2 b, K4 c, K8 d) {
+template <typename K>
+static K pick(int ppt, K a, K b, K c, K d) {
     return ppt == 1 ? a : ppt == 2 ? b : ppt == 4 ? c : d;
 }
 
@@ -634,31 +621,85 @@ static int warp_teams(int tf4) {
     return t < 1 ? 1 : (t > kMaxWarpTeams ? kMaxWarpTeams : t);
 }
 
-gs_status launch_render_fwd(const Plan* p, const void* ws, float* images, float* final_T,
+// CTAs of a persistent launch: the resident CTAs of the whole GPU, no more
+// than there are teams' worth of tiles.  The occupancy query runs once per
+// (kernel, shape, device) and is cached.
+static int persistent_blocks(const void* kern, int threads, size_t smem, int tiles_per_block,
+                             int total_tiles) {
+    struct Entry {
+        const void* k;
+        int threads, dev;
+        size_t smem;
+        int blocks;
+    };
+    static Entry cache[64];
+    static int used = 0;
+    static std::mutex mu;
+    int dev = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess) return -1;
+    int resident = 0;
+    {
+        std::lock_guard<std::mutex> lock(mu);
+        for (int i = 0; i < used; ++i)
+            if (cache[i].k == kern && cache[i].threads == threads && cache[i].smem == smem &&
+                cache[i].dev == dev)
+                resident = cache[i].blocks;
+        if (resident == 0) {
+            int per_sm = 0, sms = 0;
+            if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, threads, smem) !=
+                    cudaSuccess ||
+                cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess)
+                return -1;
+            resident = per_sm * sms;
+            if (resident < 1) return -1;
+            if (used < 64) cache[used++] = Entry{kern, threads, dev, smem, resident};
+        }
+    }
+    const int want = (total_tiles + tiles_per_block - 1) / tiles_per_block;
+    return want < resident ? (want < 1 ? 1 : want) : resident;
+}
+
+// The launch shape of a render kernel: one warp per tile when a tile needs
+// 32 threads, else one CTA per tile.
+struct RenderShape {
+    bool warp;
+    int threads, tf4, teams;
+    size_t smem;
+};
+
+static RenderShape render_shape(const Plan* p, int batch, int ppt, bool bwd) {
+    RenderShape s;
+    const int tile_threads = p->cfg.tile_w * p->cfg.tile_h / ppt;
+    s.warp = tile_threads == 32;
+    s.tf4 = team_f4(batch, bwd);
+    s.teams = s.warp ? warp_teams(s.tf4) : 1;
+    s.threads = s.warp ? 32 * s.teams : tile_threads;
+    s.smem = (size_t)s.teams * s.tf4 * sizeof(float4);
+    return s;
+}
+
+gs_status launch_render_fwd(const Plan* p, void* ws, float* images, float* final_T,
                             int32_t* last_idx, cudaStream_t st) {
     const int batch = p->cfg.smem_batch;
     const int ppt = p->cfg.pixels_per_thread;
-    const int threads = p->cfg.tile_w * p->cfg.tile_h / ppt;
-    const int tf4 = team_f4(batch, false);
+    const RenderShape s = render_shape(p, batch, ppt, false);
     const uint32_t* ranges = cbuf<uint32_t>(p, ws, GS_BUF_RANGES);
     const uint32_t* order = cbuf<uint32_t>(p, ws, B_TILE_ORDER);
     const uint32_t* vals =
         cbuf<uint32_t>(p, ws, (p->tile_passes & 1) ? (int)B_IVAL_B : (int)GS_BUF_TILE_VALUES);
     const float4* rec = cbuf<float4>(p, ws, GS_BUF_PROJ);
-    if (threads == 32) {
-        auto kern = pick(ppt, k_render_fwd_w<1>, k_render_fwd_w<2>, k_render_fwd_w<4>,
-                         k_render_fwd_w<8>);
-        const int teams = warp_teams(tf4);
-        const int blocks = (p->total_tiles + teams - 1) / teams;
-        kern<<<blocks, 32 * teams, (size_t)teams * tf4 * sizeof(float4), st>>>(
-            p->vt, ranges, order, vals, rec, batch, tf4, p->total_tiles, p->cfg.bg[0],
-            p->cfg.bg[1], p->cfg.bg[2], images, final_T, last_idx);
-        return launch_status();
-    }
-    auto kern = pick(ppt, k_render_fwd<1>, k_render_fwd<2>, k_render_fwd<4>, k_render_fwd<8>);
-    kern<<<p->total_tiles, threads, (size_t)tf4 * sizeof(float4), st>>>(
-        p->vt, ranges, order, vals, rec, batch, p->cfg.bg[0], p->cfg.bg[1], p->cfg.bg[2], images,
-        final_T, last_idx);
+    uint32_t* queue = buf<uint32_t>(p, ws, B_TILE_QUEUE);
+    auto kern = s.warp ? pick(ppt, k_render_fwd<1, true>, k_render_fwd<2, true>,
+                              k_render_fwd<4, true>, k_render_fwd<8, true>)
+                       : pick(ppt, k_render_fwd<1, false>, k_render_fwd<2, false>,
+                              k_render_fwd<4, false>, k_render_fwd<8, false>);
+    const int blocks = persistent_blocks((const void*)kern, s.threads, s.smem, s.teams,
+                                         p->total_tiles);
+    if (blocks < 0) return GS_ERR_CUDA;
+    if (cudaMemsetAsync(queue, 0, sizeof(uint32_t), st) != cudaSuccess) return GS_ERR_CUDA;
+    kern<<<blocks, s.threads, s.smem, st>>>(p->vt, ranges, order, vals, rec, batch, s.tf4,
+                                            p->total_tiles, queue, p->cfg.bg[0], p->cfg.bg[1],
+                                            p->cfg.bg[2], images, final_T, last_idx);
     return launch_status();
 }
 
@@ -666,29 +707,26 @@ gs_status launch_render_bwd_pixels(const Plan* p, void* ws, const float* final_T
                                    const int32_t* last_idx, const float* dL, cudaStream_t st) {
     const int batch = p->cfg.smem_batch_bwd;
     const int ppt = p->cfg.pixels_per_thread_bwd;
-    const int threads = p->cfg.tile_w * p->cfg.tile_h / ppt;
-    const int tf4 = team_f4(batch, true);
+    const RenderShape s = render_shape(p, batch, ppt, true);
     float* grad2d = buf<float>(p, ws, GS_BUF_GRAD2D);
-    if (cudaMemsetAsync(grad2d, 0, p->len[GS_BUF_GRAD2D], st) != cudaSuccess) return GS_ERR_CUDA;
     const uint32_t* ranges = cbuf<uint32_t>(p, ws, GS_BUF_RANGES);
     const uint32_t* order = cbuf<uint32_t>(p, ws, B_TILE_ORDER);
     const uint32_t* vals =
         cbuf<uint32_t>(p, ws, (p->tile_passes & 1) ? (int)B_IVAL_B : (int)GS_BUF_TILE_VALUES);
     const float4* rec = cbuf<float4>(p, ws, GS_BUF_PROJ);
-    if (threads == 32) {
-        auto kern = pick(ppt, k_render_bwd_w<1>, k_render_bwd_w<2>, k_render_bwd_w<4>,
-                         k_render_bwd_w<8>);
-        const int teams = warp_teams(tf4);
-        const int blocks = (p->total_tiles + teams - 1) / teams;
-        kern<<<blocks, 32 * teams, (size_t)teams * tf4 * sizeof(float4), st>>>(
-            p->vt, ranges, order, vals, rec, batch, tf4, p->total_tiles, p->cfg.bg[0],
-            p->cfg.bg[1], p->cfg.bg[2], final_T, last_idx, dL, grad2d);
-        return launch_status();
-    }
-    auto kern = pick(ppt, k_render_bwd<1>, k_render_bwd<2>, k_render_bwd<4>, k_render_bwd<8>);
-    kern<<<p->total_tiles, threads, (size_t)tf4 * sizeof(float4), st>>>(
-        p->vt, ranges, order, vals, rec, batch, p->cfg.bg[0], p->cfg.bg[1], p->cfg.bg[2],
-        final_T, last_idx, dL, grad2d);
+    uint32_t* queue = buf<uint32_t>(p, ws, B_TILE_QUEUE) + 1;
+    auto kern = s.warp ? pick(ppt, k_render_bwd<1, true>, k_render_bwd<2, true>,
+                              k_render_bwd<4, true>, k_render_bwd<8, true>)
+                       : pick(ppt, k_render_bwd<1, false>, k_render_bwd<2, false>,
+                              k_render_bwd<4, false>, k_render_bwd<8, false>);
+    const int blocks = persistent_blocks((const void*)kern, s.threads, s.smem, s.teams,
+                                         p->total_tiles);
+    if (blocks < 0) return GS_ERR_CUDA;
+    if (cudaMemsetAsync(grad2d, 0, p->len[GS_BUF_GRAD2D], st) != cudaSuccess) return GS_ERR_CUDA;
+    if (cudaMemsetAsync(queue, 0, sizeof(uint32_t), st) != cudaSuccess) return GS_ERR_CUDA;
+    kern<<<blocks, s.threads, s.smem, st>>>(p->vt, ranges, order, vals, rec, batch, s.tf4,
+                                            p->total_tiles, queue, p->cfg.bg[0], p->cfg.bg[1],
+                                            p->cfg.bg[2], final_T, last_idx, dL, grad2d);
     return launch_status();
 }
 
