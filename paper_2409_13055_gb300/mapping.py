@@ -100,6 +100,41 @@ class GaussianMap:
         self.data[self.off["sh"]:self.off["sh"] + 3 * self.K * self.capacity].view(
             self.K, self.capacity, 3)[:, :self.n].copy_(sh)
 
+    def append(self, params):
+        """Insert Gaussians after the current ones (streaming insertion): the
+        packed buffers are laid out again for the new size and the old values
+        copied over, the new Gaussians' Adam moments start at zero and the
+        step counter is kept, as when new entries join a running Adam.  Every
+        device pointer of the map changes, so rasterisers may be reused but
+        captured graphs must be captured again."""
+        k = int(params["means"].shape[0])
+        if int(params["sh_degree"]) != self.degree:
+            raise ValueError("SH degree differs from the map's")
+        n0, cap0, off0 = self.n, self.capacity, self.off
+        n1 = n0 + k
+        off1, total1 = param_layout(n1, self.degree)
+        widths = dict(means=3, log_scales=3, quats=4, opacity_logits=1)
+
+        def relayout(old, copy):
+            new = torch.zeros(total1, dtype=torch.float32, device=self.device)
+            if copy:
+                for g, w in widths.items():
+                    new[off1[g]:off1[g] + w * n0].copy_(old[off0[g]:off0[g] + w * n0])
+                new[off1["sh"]:off1["sh"] + 3 * self.K * n1].view(self.K, n1, 3)[:, :n0].copy_(
+                    old[off0["sh"]:off0["sh"] + 3 * self.K * cap0].view(self.K, cap0, 3)[:, :n0])
+            return new
+
+        self.data = relayout(self.data, True)
+        self.m = relayout(self.m, True)
+        self.v = relayout(self.v, True)
+        self.grad = relayout(self.grad, False)
+        self.n = self.capacity = n1
+        self.off, self.total = off1, total1
+        P = self.params()
+        for g in widths:
+            P[g][n0:].copy_(torch.as_tensor(np.asarray(params[g], np.float32)).reshape(P[g][n0:].shape))
+        P["sh"][:, n0:].copy_(torch.as_tensor(np.asarray(params["sh"], np.float32)))
+
     def to_numpy(self):
         P = self.params()
         out = {k: P[k].detach().cpu().numpy().copy() for k in P}
@@ -336,9 +371,13 @@ class MappingStep:
     batch of views, optionally captured as one CUDA graph."""
 
     def __init__(self, gmap: GaussianMap, rast: Rasterizer, targets: torch.Tensor, lam: float,
-                 lr=None, extent=1.0, fused=False, keep_grads=False):
+                 lr=None, extent=1.0, fused=False, keep_grads=False, recompute=False):
         self.gmap, self.rast, self.targets, self.lam = gmap, rast, targets, float(lam)
         self.lr, self.extent, self.fused, self.keep_grads = lr, extent, fused, keep_grads
+        # recompute: the checkpointed backward -- projection and binning are
+        # run again (bit-identically) between the loss and the adjoint, as
+        # when the forward's intermediates were not kept
+        self.recompute = bool(recompute)
         self.graph = None
         self._m = gmap.gs_map()
         self._g = gmap.gs_map_grad()
@@ -349,6 +388,9 @@ class MappingStep:
         r.bin_sort(self.gmap.n, stream)
         r.render_fwd(stream=stream)
         r.loss_l1_ssim(self.targets, self.lam, stream=stream)
+        if self.recompute:
+            r.project(self._m, stream)
+            r.bin_sort(self.gmap.n, stream)
         if self.fused:
             # Adam applied inside the projection adjoint (fewer bytes moved,
             # but slower than the two passes on this workload); the gradients

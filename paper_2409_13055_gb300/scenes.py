@@ -230,3 +230,147 @@ def workload(name):
         v = views_mixed16()
         return p, v, None, 0.2
     raise KeyError(name)
+
+
+# --------------------------------------------------------------------------
+# Streaming keyframes (drone-like loop through the room).
+# --------------------------------------------------------------------------
+EUROC_W, EUROC_H, EUROC_F = 752, 480, 460.0
+
+
+def drone_loop(n_kf, seed=SEED_BASE + 5, length=5.0, width=EUROC_W, height=EUROC_H, f=EUROC_F,
+               centre=(0.0, -0.2, 1.6), jitter_m=0.02, jitter_deg=4.0):
+    """n_kf grayscale keyframes evenly spaced on a closed horizontal loop of the
+    given length (a circle in x-z with a +-0.1 m vertical wave), the camera
+    looking along the direction of travel, pitched 10 degrees down, with
+    seeded position and orientation jitter.  Returns camera dicts."""
+    rng = np.random.default_rng(seed)
+    r = length / (2 * np.pi)
+    views = []
+    for k in range(n_kf):
+        th = 2 * np.pi * k / n_kf
+        c = np.array([centre[0] + r * np.cos(th), centre[1] + 0.1 * np.sin(3 * th),
+                      centre[2] + r * np.sin(th)]) + rng.normal(0, jitter_m, 3)
+        fwd = np.array([-np.sin(th), 0.0, np.cos(th)])  # tangent of the loop
+        yaw = np.arctan2(fwd[0], fwd[2])
+        R_cw = (_rotation_from_axis_angle([0, 1, 0], yaw) @
+                _rotation_from_axis_angle([1, 0, 0], np.deg2rad(-10.0)) @
+                _rotation_from_axis_angle(rng.normal(size=3), np.deg2rad(rng.uniform(0, jitter_deg))))
+        R = R_cw.T
+        t = -R @ c
+        views.append(camera(width, height, f, f, R=R.astype(np.float32), t=t.astype(np.float32),
+                            channels=1))
+    return views
+
+
+def room_textures(seed=SEED_BASE + 5, n_boxes=20):
+    """The room's faces (as in room_scene with the same seed) with a seeded
+    grayscale texture per face: base + amp * sin(2 pi a/p) sin(2 pi b/p) over
+    the face's metric coordinates (a, b)."""
+    rng = np.random.default_rng(seed)
+    faces = _room_faces(rng, n_boxes)
+    tex = [(rng.uniform(0.25, 0.75), rng.uniform(0.1, 0.2), rng.uniform(0.12, 0.45))
+           for _ in faces]
+    return faces, tex
+
+
+def ray_cast(view, faces, tex, device="cpu"):
+    """Depth (camera z) and grayscale image of the textured room seen from a
+    view, by intersecting each pixel's ray (through the integer pixel
+    coordinate) with every axis-aligned face; nearest hit wins.  Torch on the
+    given device; returns float32 numpy arrays [H][W]."""
+    import torch
+    H, W = view["height"], view["width"]
+    dt = torch.float64
+    R = torch.as_tensor(np.asarray(view["R"], np.float64), dtype=dt, device=device)
+    t = torch.as_tensor(np.asarray(view["t"], np.float64), dtype=dt, device=device)
+    c = -R.T @ t
+    ys, xs = torch.meshgrid(torch.arange(H, dtype=dt, device=device),
+                            torch.arange(W, dtype=dt, device=device), indexing="ij")
+    d_cam = torch.stack([(xs - view["cx"]) / view["fx"], (ys - view["cy"]) / view["fy"],
+                         torch.ones_like(xs)], dim=-1)
+    d = d_cam @ R  # rows: R^T d_cam
+    best = torch.full((H, W), float("inf"), dtype=dt, device=device)
+    gray = torch.zeros((H, W), dtype=dt, device=device)
+    for (O, U, Vv), (base, amp, per) in zip(faces, tex):
+        O, U, Vv = (np.asarray(a, np.float64) for a in (O, U, Vv))
+        n_ax = int(np.argmax(np.abs(np.cross(U, Vv))))  # the face's normal axis
+        u_ax, v_ax = int(np.argmax(np.abs(U))), int(np.argmax(np.abs(Vv)))
+        du = d[..., n_ax]
+        s = (O[n_ax] - float(c[n_ax])) / torch.where(du == 0, torch.full_like(du, 1e-30), du)
+        a = (c[u_ax] + s * d[..., u_ax] - O[u_ax]) / U[u_ax]
+        b = (c[v_ax] + s * d[..., v_ax] - O[v_ax]) / Vv[v_ax]
+        hit = (s > 1e-6) & (a >= 0) & (a <= 1) & (b >= 0) & (b <= 1) & (s < best)
+        val = base + amp * torch.sin(2 * np.pi * a * abs(U[u_ax]) / per) * \
+            torch.sin(2 * np.pi * b * abs(Vv[v_ax]) / per)
+        best = torch.where(hit, s, best)
+        gray = torch.where(hit, val, gray)
+    depth = best  # ray parameter along d with d_cam.z = 1, i.e. camera z
+    return depth.float().cpu().numpy(), gray.float().cpu().numpy()
+
+
+def dso_points(view, depth, gray, n_points, seed, block=4, idepth_sigma=0.01, sh_degree=3,
+               opacity=0.1):
+    """A semi-dense DSO-like point set turned into new Gaussians: per block x
+    block pixel block the pixel of largest central-difference gradient, the
+    n_points strongest of those, depth from the ray cast with inverse-depth
+    noise N(0, idepth_sigma), back-projected; isotropic scale of one block's
+    footprint, identity rotation, the given opacity, SH DC from the pixel's
+    gray value (the rest zero)."""
+    rng = np.random.default_rng(seed)
+    H, W = gray.shape
+    gx = np.zeros_like(gray)
+    gy = np.zeros_like(gray)
+    gx[:, 1:-1] = 0.5 * (gray[:, 2:] - gray[:, :-2])
+    gy[1:-1, :] = 0.5 * (gray[2:, :] - gray[:-2, :])
+    mag = np.hypot(gx, gy)
+    mag[~np.isfinite(depth)] = -1.0
+    Hb, Wb = H // block, W // block
+    blocks = mag[:Hb * block, :Wb * block].reshape(Hb, block, Wb, block).transpose(0, 2, 1, 3)
+    blocks = blocks.reshape(Hb, Wb, block * block)
+    arg = blocks.argmax(axis=2)
+    val = np.take_along_axis(blocks, arg[..., None], axis=2)[..., 0]
+    by, bx = np.meshgrid(np.arange(Hb), np.arange(Wb), indexing="ij")
+    py = by * block + arg // block
+    px = bx * block + arg % block
+    order = np.argsort(-val, axis=None, kind="stable")[:n_points]
+    py, px = py.reshape(-1)[order], px.reshape(-1)[order]
+    keep = val.reshape(-1)[order] > 0
+    py, px = py[keep], px[keep]
+    z = depth[py, px].astype(np.float64)
+    iz = 1.0 / z + rng.normal(0.0, idepth_sigma, z.shape)
+    z = 1.0 / np.clip(iz, 1e-3, None)
+    xc = np.stack([(px - view["cx"]) / view["fx"] * z, (py - view["cy"]) / view["fy"] * z, z], 1)
+    R = np.asarray(view["R"], np.float64)
+    t = np.asarray(view["t"], np.float64)
+    xw = (xc - t) @ R  # R^T (x_c - t)
+    n = xw.shape[0]
+    K = (sh_degree + 1) ** 2
+    sh = np.zeros((K, n, 3))
+    sh[0] = ((gray[py, px] - 0.5) * 2.0 * np.sqrt(np.pi))[:, None]  # DC of a gray colour
+    q = np.zeros((n, 4))
+    q[:, 0] = 1.0
+    return dict(
+        means=np.ascontiguousarray(xw, np.float32),
+        log_scales=np.ascontiguousarray(
+            np.repeat(np.log(z * 0.5 * block / view["fx"])[:, None], 3, 1), np.float32),
+        quats=np.ascontiguousarray(q, np.float32),
+        opacity_logits=np.full(n, np.log(opacity / (1 - opacity)), np.float32),
+        sh=np.ascontiguousarray(sh, np.float32),
+        sh_degree=int(sh_degree),
+    )
+
+
+def streaming_keyframes(n_kf, points_per_kf, seed=SEED_BASE + 5, width=EUROC_W, height=EUROC_H,
+                        f=EUROC_F, device="cpu", sh_degree=3):
+    """Yields (view, target [1][H][W], new Gaussians) for each keyframe of the
+    streaming workload: ray-cast textured room as the keyframe image, its
+    DSO-like points as the Gaussians inserted with it."""
+    scale = width / EUROC_W
+    views = drone_loop(n_kf, seed, width=width, height=height, f=f)
+    faces, tex = room_textures(seed)
+    for k, v in enumerate(views):
+        depth, gray = ray_cast(v, faces, tex, device)
+        new = dso_points(v, depth, gray, points_per_kf, seed + 1000 + k,
+                         block=max(2, int(round(4 * scale))), sh_degree=sh_degree)
+        yield v, gray[None].astype(np.float32), new

@@ -1,0 +1,106 @@
+"""Streaming mapping: keyframes arrive one at a time, each inserting new
+Gaussians, and the map is optimised over a sliding window of the latest
+keyframes (paper Sec. III-B: the mapping thread receives keyframes and the
+photometric-SLAM point cloud, initialises Gaussians from it and optimises them
+over a window of keyframes).
+
+Per keyframe:
+  1. its new Gaussians are appended to the map (``GaussianMap.append``: Adam
+     moments zero, step counter kept);
+  2. the window's views, targets and rasteriser are set up (one rasteriser per
+     window size, planned for the map's capacity and re-planned with headroom
+     when the map or the instance count outgrows it);
+  3. ``iters`` batched mapping iterations run over the whole window, each one
+     ``MappingStep`` (project, bin, render, loss, backward, Adam), with the
+     checkpointed backward by default, captured as one CUDA graph and replayed.
+
+Every arithmetic step runs in libgs_gb300.so; this module only moves memory
+and decides when to re-plan.
+"""
+from __future__ import annotations
+
+import numpy as np
+import torch
+
+from . import mapping
+
+
+class StreamingMapper:
+    """Sliding-window mapper over a growing map."""
+
+    def __init__(self, degree=3, window=8, iters=30, lam=0.2, lr=None, extent=1.0,
+                 recompute=True, capacity=1 << 20, instance_headroom=1.25, graphs=True,
+                 device="cuda", **rast_kw):
+        self.degree, self.window, self.iters, self.lam = int(degree), int(window), int(iters), lam
+        self.lr, self.extent, self.recompute = lr, extent, bool(recompute)
+        self.capacity, self.headroom, self.graphs = int(capacity), float(instance_headroom), graphs
+        self.device = torch.device(device)
+        self.rast_kw = rast_kw
+        self.gmap = None
+        self.frames = []        # (view, target) of the window, oldest first
+        self._rasts = {}        # window size -> Rasterizer
+        self.step = None
+        self.keyframes = 0
+        self.iterations = 0
+        self.replans = 0
+
+    # -- set-up ---------------------------------------------------------------
+    def _rasterizer(self, views):
+        V = len(views)
+        r = self._rasts.get(V)
+        n = self.gmap.n
+        if r is None or r.n_capacity < n:
+            while self.capacity < n:
+                self.capacity *= 2
+            r = mapping.Rasterizer(views, self.capacity, instance_capacity=None, **self.rast_kw)
+            self._rasts[V] = r
+            self.replans += 1
+        r.set_poses(views)
+        # instance capacity: one synchronising probe per keyframe
+        r.project(self.gmap.gs_map())
+        r.bin_sort(n)
+        raw = int(r.counters().n_instances_raw)
+        if raw > r.instance_capacity:
+            r = mapping.Rasterizer(views, self.capacity,
+                                   instance_capacity=int(raw * self.headroom) + 4096,
+                                   **self.rast_kw)
+            r.set_poses(views)
+            self._rasts[V] = r
+            self.replans += 1
+        return r
+
+    def insert_keyframe(self, view, target, new_gaussians):
+        """Append the keyframe's Gaussians, slide the window and prepare the
+        window's mapping iteration (not yet run)."""
+        if self.gmap is None:
+            self.gmap = mapping.GaussianMap(new_gaussians, self.device)
+        else:
+            self.gmap.append(new_gaussians)
+        self.frames.append((view, np.asarray(target, np.float32)))
+        if len(self.frames) > self.window:
+            self.frames.pop(0)
+        views = [f[0] for f in self.frames]
+        rast = self._rasterizer(views)
+        targets = rast.pack([f[1] for f in self.frames])
+        self.step = mapping.MappingStep(self.gmap, rast, targets, self.lam, self.lr, self.extent,
+                                        recompute=self.recompute)
+        self._eager_done = False
+        self.keyframes += 1
+
+    def iterate(self, k=1):
+        """k mapping iterations over the current window: the first eagerly,
+        the rest as replays of a graph captured after it."""
+        for _ in range(k):
+            if self.graphs and self.step.graph is None and self._eager_done:
+                self.step.capture(warmup=0)
+            self.step()
+            self._eager_done = True
+            self.iterations += 1
+
+    def add_keyframe(self, view, target, new_gaussians):
+        self.insert_keyframe(view, target, new_gaussians)
+        self.iterate(self.iters)
+
+    def status(self):
+        """Device status of the current rasteriser (synchronises)."""
+        return self.step.rast.counters()
