@@ -125,7 +125,7 @@ extern "C" gs_status gs_plan_init(gs_plan* plan, const gs_config* cfg, int32_t n
     len[B_GCOL] = (size_t)VN * 3 * sizeof(float);
     len[B_OFFSETS] = (size_t)(VN + 1) * sizeof(uint32_t);
     len[B_TILE_ORDER] = (size_t)tiles * sizeof(uint32_t);
-    len[B_GMEAN] = (size_t)n_capacity * 3 * sizeof(float);
+    len[B_GPARAM] = (size_t)n_capacity * 11 * sizeof(float);
     len[B_TILE_QUEUE] = 2 * sizeof(uint32_t);
     size_t off = 0;
     for (int b = 0; b < B_TOTAL; ++b) {

@@ -52,7 +52,8 @@ enum PrivBuf {
     B_GCOL,     // [V*n] x 3: colour gradient as it reaches the SH coefficients
     B_OFFSETS,  // [V*n + 1] instance offsets of the entries in depth order
     B_TILE_ORDER,  // [total_tiles] render order of the tiles, longest lists first
-    B_GMEAN,       // [n] x 3 mean gradients held between the fused adjoint kernels
+    B_GPARAM,      // [n] x 11: this pass's quaternion, mean, log-scale, opacity gradients
+                   // held between the two fused adjoint kernels
     B_TILE_QUEUE,  // [2] u32 next-tile counters of the forward and backward render
     B_TOTAL
 };

@@ -159,7 +159,8 @@ struct Proj {
 
 // Adam state for the fused projection adjoint: parameter, moment and optional
 // gradient arrays in the gs_map layout; lr per group (means, log-scales,
-// quaternions, opacity, SH DC, SH rest).
+// quaternions, opacity, SH DC, SH rest); the per-Gaussian gradients that
+// k_project_bwd left in workspace scratch (s_*).
 struct FusedAdam {
     float lr[6];
     float b1, b2, eps;
@@ -169,8 +170,43 @@ struct FusedAdam {
     float *v_means, *v_ls, *v_quats, *v_logit, *v_sh;
     const float *a_means, *a_ls, *a_quats, *a_logit, *a_sh;  // gradients to add, or null
     float *o_means, *o_ls, *o_quats, *o_logit, *o_sh;        // gradients out, or null
-    float* gmean;                                            // [n][3] deferred mean gradients
+    const float *s_means, *s_ls, *s_quats, *s_logit;         // this pass's gradients
 };
+
+// Adam on one warp-wide run of cnt <= 128 consecutive floats of a parameter
+// array: lane l takes floats l, l+32, l+64, l+96, every access a coalesced
+// row, all loads issued before any store.  g: this pass's gradient (shared
+// or global memory), add: gradient to add or null, out: total gradient out
+// or null.
+__device__ __forceinline__ void adam_run(float* __restrict__ p, float* __restrict__ m,
+                                         float* __restrict__ v, const float* __restrict__ g,
+                                         const float* __restrict__ add, float* __restrict__ out,
+                                         int cnt, float lr, const FusedAdam& fa, float ibc1,
+                                         float ibc2) {
+    const int lane = threadIdx.x & 31;
+    float gg[4], pp[4], mm[4], vv[4];
+#pragma unroll
+    for (int r = 0; r < 4; ++r) {
+        const int i = lane + 32 * r;
+        if (i < cnt) {
+            gg[r] = g[i] + (add ? add[i] : 0.0f);
+            pp[r] = p[i];
+            mm[r] = m[i];
+            vv[r] = v[i];
+        }
+    }
+#pragma unroll
+    for (int r = 0; r < 4; ++r) {
+        const int i = lane + 32 * r;
+        if (i < cnt) {
+            adam1(pp[r], gg[r], mm[r], vv[r], lr, fa.b1, fa.b2, fa.eps, ibc1, ibc2);
+            p[i] = pp[r];
+            m[i] = mm[r];
+            v[i] = vv[r];
+            if (out) out[i] = gg[r];
+        }
+    }
+}
 
 __device__ __forceinline__ void project_one(const float* mean, const Shape& sh, const Cam& cam,
                                             float near_z, int log2_tw, int log2_th, int tiles_x,
@@ -326,7 +362,7 @@ k_project(const float* __restrict__ means, const float* __restrict__ log_scales,
 
 // A8: chain rule of the projection, summed over views.  One thread per
 // Gaussian reads its screen-space gradient from every view it is visible in.
-template <int DEG, bool ADAM>
+template <int DEG>
 __global__ void __launch_bounds__(kProjThreads)
 k_project_bwd(const float* __restrict__ means, const float* __restrict__ log_scales,
               const float* __restrict__ quats, const float* __restrict__ opacity_logits,
@@ -334,11 +370,9 @@ k_project_bwd(const float* __restrict__ means, const float* __restrict__ log_sca
               ViewTable vt, float near_z, const uint32_t* __restrict__ touched,
               const float* __restrict__ grad2d, float* __restrict__ gcol_out,
               float* __restrict__ g_means, float* __restrict__ g_ls, float* __restrict__ g_quats,
-              float* __restrict__ g_logit, int accumulate, FusedAdam fa) {
+              float* __restrict__ g_logit, int accumulate) {
     extern __shared__ Cam cam_all[];
-    __shared__ float s_bc[2];
     for (int v = threadIdx.x; v < vt.n_views; v += blockDim.x) load_cam(views[v], cam_all[v]);
-    if (ADAM && threadIdx.x == 0) adam_bias(fa.b1, fa.b2, *fa.step, s_bc[0], s_bc[1]);
     __syncthreads();
     const int g = blockIdx.x * blockDim.x + threadIdx.x;
     if (g >= n) return;
@@ -499,44 +533,7 @@ k_project_bwd(const float* __restrict__ means, const float* __restrict__ log_sca
                              (gq[3] - z * dq) * iq);
     const float glog = gop * opacity * (1.0f - opacity);
 
-    if (ADAM) {
-        // Adam on log-scales, quaternion and opacity now; the means wait for
-        // k_sh_bwd, which still needs their current values
-        const float ibc1 = s_bc[0], ibc2 = s_bc[1];
-        float gg[3];
-        for (int e = 0; e < 3; ++e) {
-            fa.gmean[3 * g + e] = gm[e] + (fa.a_means ? fa.a_means[3 * g + e] : 0.0f);
-            gg[e] = gls[e] + (fa.a_ls ? fa.a_ls[3 * g + e] : 0.0f);
-            if (fa.o_ls) fa.o_ls[3 * g + e] = gg[e];
-            float p = ls[e], m = fa.m_ls[3 * g + e], v = fa.v_ls[3 * g + e];
-            adam1(p, gg[e], m, v, fa.lr[1], fa.b1, fa.b2, fa.eps, ibc1, ibc2);
-            fa.p_ls[3 * g + e] = p;
-            fa.m_ls[3 * g + e] = m;
-            fa.v_ls[3 * g + e] = v;
-        }
-        float4 gqa = gq4;
-        if (fa.a_quats) {
-            const float4 a = reinterpret_cast<const float4*>(fa.a_quats)[g];
-            gqa.x += a.x; gqa.y += a.y; gqa.z += a.z; gqa.w += a.w;
-        }
-        if (fa.o_quats) reinterpret_cast<float4*>(fa.o_quats)[g] = gqa;
-        float4 pq = q, mq = reinterpret_cast<float4*>(fa.m_quats)[g],
-               vq = reinterpret_cast<float4*>(fa.v_quats)[g];
-        adam1(pq.x, gqa.x, mq.x, vq.x, fa.lr[2], fa.b1, fa.b2, fa.eps, ibc1, ibc2);
-        adam1(pq.y, gqa.y, mq.y, vq.y, fa.lr[2], fa.b1, fa.b2, fa.eps, ibc1, ibc2);
-        adam1(pq.z, gqa.z, mq.z, vq.z, fa.lr[2], fa.b1, fa.b2, fa.eps, ibc1, ibc2);
-        adam1(pq.w, gqa.w, mq.w, vq.w, fa.lr[2], fa.b1, fa.b2, fa.eps, ibc1, ibc2);
-        reinterpret_cast<float4*>(fa.p_quats)[g] = pq;
-        reinterpret_cast<float4*>(fa.m_quats)[g] = mq;
-        reinterpret_cast<float4*>(fa.v_quats)[g] = vq;
-        const float gl = glog + (fa.a_logit ? fa.a_logit[g] : 0.0f);
-        if (fa.o_logit) fa.o_logit[g] = gl;
-        float pl = logit, ml = fa.m_logit[g], vl = fa.v_logit[g];
-        adam1(pl, gl, ml, vl, fa.lr[3], fa.b1, fa.b2, fa.eps, ibc1, ibc2);
-        fa.p_logit[g] = pl;
-        fa.m_logit[g] = ml;
-        fa.v_logit[g] = vl;
-    } else if (accumulate) {
+    if (accumulate) {
         for (int e = 0; e < 3; ++e) {
             g_means[3 * g + e] += gm[e];
             g_ls[3 * g + e] += gls[e];
@@ -558,9 +555,20 @@ k_project_bwd(const float* __restrict__ means, const float* __restrict__ log_sca
 // Gradient of the SH coefficients: sum over views of Y_k(dir_v) gcol_v, with
 // gcol the colour gradient k_project_bwd left (zero on clamped channels, a
 // grayscale view's gradient spread over the three channels).
+//
+// With ADAM the whole Adam step of the warp's 32 Gaussians follows in the
+// same kernel, on every parameter group.  A thread's own coefficients lie
+// N*3 floats apart in the [K][N][3] SH planes, so each warp passes its SH
+// gradients through shared memory ([k][lane*3 + c], conflict-free) and then
+// updates runs of consecutive floats: the means, log-scales, quaternions and
+// opacities of its 32 Gaussians (96, 96, 128 and 32 floats) and, per
+// coefficient k, 96 floats of SH; see adam_run.  Launched with
+// kShAdamThreads threads so the staging fits the default shared memory.
+constexpr int kShAdamThreads = 128;
+
 template <int DEG, bool ADAM>
 __global__ void __launch_bounds__(kProjThreads)
-k_sh_bwd(const float* means, const float* sh, int n, const gs_view* __restrict__ views,
+k_sh_bwd(const float* means, int n, const gs_view* __restrict__ views,
          ViewTable vt, const uint32_t* __restrict__ touched, const float* __restrict__ gcol_in,
          float* __restrict__ g_sh, int accumulate, FusedAdam fa) {
     extern __shared__ Cam cam_all[];
@@ -569,13 +577,19 @@ k_sh_bwd(const float* means, const float* sh, int n, const gs_view* __restrict__
     if (ADAM && threadIdx.x == 0) adam_bias(fa.b1, fa.b2, *fa.step, s_bc[0], s_bc[1]);
     __syncthreads();
     const int g = blockIdx.x * blockDim.x + threadIdx.x;
-    if (g >= n) return;
+    if (!ADAM && g >= n) return;
+    const bool valid = g < n;  // (ADAM keeps every lane for the warp-wide update)
     constexpr int K = (DEG + 1) * (DEG + 1);
-    const float mean[3] = {means[3 * g], means[3 * g + 1], means[3 * g + 2]};
+    float mean[3] = {0.f, 0.f, 0.f};
+    if (valid) {
+        mean[0] = means[3 * g];
+        mean[1] = means[3 * g + 1];
+        mean[2] = means[3 * g + 2];
+    }
     float acc[K][3];
 #pragma unroll
     for (int k = 0; k < K; ++k) acc[k][0] = acc[k][1] = acc[k][2] = 0.0f;
-    for (int v = 0; v < vt.n_views; ++v) {
+    for (int v = 0; valid && v < vt.n_views; ++v) {
         const size_t vg = (size_t)v * n + g;
         if (touched[vg] == 0u) continue;
         const float* gc = gcol_in + vg * 3;
@@ -595,28 +609,36 @@ k_sh_bwd(const float* means, const float* sh, int n, const gs_view* __restrict__
     }
     if (ADAM) {
         const float ibc1 = s_bc[0], ibc2 = s_bc[1];
-        for (int e = 0; e < 3; ++e) {
-            const float gg = fa.gmean[3 * g + e];
-            if (fa.o_means) fa.o_means[3 * g + e] = gg;
-            float p = mean[e], m = fa.m_means[3 * g + e], v = fa.v_means[3 * g + e];
-            adam1(p, gg, m, v, fa.lr[0], fa.b1, fa.b2, fa.eps, ibc1, ibc2);
-            fa.p_means[3 * g + e] = p;
-            fa.m_means[3 * g + e] = m;
-            fa.v_means[3 * g + e] = v;
-        }
+        float* stage = reinterpret_cast<float*>(cam_all + vt.n_views) +
+                       (size_t)(threadIdx.x >> 5) * (K * 96);
+        const int lane = threadIdx.x & 31;
 #pragma unroll
         for (int k = 0; k < K; ++k) {
-            const float lr = k == 0 ? fa.lr[4] : fa.lr[5];
-            const size_t o = ((size_t)k * n + g) * 3;
-            for (int c = 0; c < 3; ++c) {
-                const float gg = acc[k][c] + (fa.a_sh ? fa.a_sh[o + c] : 0.0f);
-                if (fa.o_sh) fa.o_sh[o + c] = gg;
-                float p = sh[o + c], m = fa.m_sh[o + c], v = fa.v_sh[o + c];
-                adam1(p, gg, m, v, lr, fa.b1, fa.b2, fa.eps, ibc1, ibc2);
-                fa.p_sh[o + c] = p;
-                fa.m_sh[o + c] = m;
-                fa.v_sh[o + c] = v;
-            }
+            stage[k * 96 + lane * 3 + 0] = acc[k][0];
+            stage[k * 96 + lane * 3 + 1] = acc[k][1];
+            stage[k * 96 + lane * 3 + 2] = acc[k][2];
+        }
+        __syncwarp();
+        const int g0 = blockIdx.x * blockDim.x + (threadIdx.x & ~31);
+        if (g0 >= n) return;  // the whole warp: nothing of it is in the map
+        const int nw = n - g0 < 32 ? n - g0 : 32;
+        auto opt = [](const float* a, size_t o) { return a ? a + o : nullptr; };
+        auto opto = [](float* a, size_t o) { return a ? a + o : nullptr; };
+        const size_t o3 = (size_t)g0 * 3, o4 = (size_t)g0 * 4, o1 = (size_t)g0;
+        adam_run(fa.p_means + o3, fa.m_means + o3, fa.v_means + o3, fa.s_means + o3,
+                 opt(fa.a_means, o3), opto(fa.o_means, o3), 3 * nw, fa.lr[0], fa, ibc1, ibc2);
+        adam_run(fa.p_ls + o3, fa.m_ls + o3, fa.v_ls + o3, fa.s_ls + o3, opt(fa.a_ls, o3),
+                 opto(fa.o_ls, o3), 3 * nw, fa.lr[1], fa, ibc1, ibc2);
+        adam_run(fa.p_quats + o4, fa.m_quats + o4, fa.v_quats + o4, fa.s_quats + o4,
+                 opt(fa.a_quats, o4), opto(fa.o_quats, o4), 4 * nw, fa.lr[2], fa, ibc1, ibc2);
+        adam_run(fa.p_logit + o1, fa.m_logit + o1, fa.v_logit + o1, fa.s_logit + o1,
+                 opt(fa.a_logit, o1), opto(fa.o_logit, o1), nw, fa.lr[3], fa, ibc1, ibc2);
+#pragma unroll 2
+        for (int k = 0; k < K; ++k) {
+            const size_t base = ((size_t)k * n + g0) * 3;
+            adam_run(fa.p_sh + base, fa.m_sh + base, fa.v_sh + base, stage + k * 96,
+                     opt(fa.a_sh, base), opto(fa.o_sh, base), 3 * nw,
+                     k == 0 ? fa.lr[4] : fa.lr[5], fa, ibc1, ibc2);
         }
     } else {
 #pragma unroll
@@ -657,30 +679,22 @@ gs_status launch_project(const Plan* p, const gs_map* map, const gs_view* views_
     return launch_status();
 }
 
-template <bool ADAM>
-gs_status launch_project_bwd_t(const Plan* p, const gs_map* map, const gs_view* views_dev,
-                               void* ws, const gs_map_grad* grads, int accumulate,
-                               const FusedAdam& fa, cudaStream_t st) {
+static gs_status launch_project_adjoint(const Plan* p, const gs_map* map,
+                                        const gs_view* views_dev, void* ws,
+                                        const gs_map_grad* grads, int accumulate,
+                                        cudaStream_t st) {
     const int n = map->n;
     const size_t smem = sizeof(Cam) * p->vt.n_views;
     const int blocks = (n + kProjThreads - 1) / kProjThreads;
-    float* gcol = buf<float>(p, ws, B_GCOL);
-    const uint32_t* touched = buf<uint32_t>(p, ws, GS_BUF_TOUCHED);
-    auto* kern = map->sh_degree == 0   ? k_project_bwd<0, ADAM>
-                 : map->sh_degree == 1 ? k_project_bwd<1, ADAM>
-                 : map->sh_degree == 2 ? k_project_bwd<2, ADAM>
-                                       : k_project_bwd<3, ADAM>;
+    auto* kern = map->sh_degree == 0   ? k_project_bwd<0>
+                 : map->sh_degree == 1 ? k_project_bwd<1>
+                 : map->sh_degree == 2 ? k_project_bwd<2>
+                                       : k_project_bwd<3>;
     kern<<<blocks, kProjThreads, smem, st>>>(
         map->means, map->log_scales, map->quats, map->opacity_logits, map->sh, n, views_dev,
-        p->vt, p->cfg.near_z, touched, buf<float>(p, ws, GS_BUF_GRAD2D), gcol,
-        grads ? grads->means : nullptr, grads ? grads->log_scales : nullptr,
-        grads ? grads->quats : nullptr, grads ? grads->opacity_logits : nullptr, accumulate, fa);
-    auto* kern_sh = map->sh_degree == 0   ? k_sh_bwd<0, ADAM>
-                    : map->sh_degree == 1 ? k_sh_bwd<1, ADAM>
-                    : map->sh_degree == 2 ? k_sh_bwd<2, ADAM>
-                                          : k_sh_bwd<3, ADAM>;
-    kern_sh<<<blocks, kProjThreads, smem, st>>>(map->means, map->sh, n, views_dev, p->vt, touched,
-                                                 gcol, grads ? grads->sh : nullptr, accumulate, fa);
+        p->vt, p->cfg.near_z, buf<uint32_t>(p, ws, GS_BUF_TOUCHED),
+        buf<float>(p, ws, GS_BUF_GRAD2D), buf<float>(p, ws, B_GCOL), grads->means,
+        grads->log_scales, grads->quats, grads->opacity_logits, accumulate);
     return launch_status();
 }
 
@@ -688,8 +702,18 @@ gs_status launch_project_bwd(const Plan* p, const gs_map* map, const gs_view* vi
                              void* ws, const gs_map_grad* grads, int accumulate,
                              cudaStream_t st) {
     if (reinterpret_cast<uintptr_t>(grads->quats) % 16) return GS_ERR_INVALID;
+    gs_status s = launch_project_adjoint(p, map, views_dev, ws, grads, accumulate, st);
+    if (s != GS_OK) return s;
+    const int n = map->n;
+    auto* kern_sh = map->sh_degree == 0   ? k_sh_bwd<0, false>
+                    : map->sh_degree == 1 ? k_sh_bwd<1, false>
+                    : map->sh_degree == 2 ? k_sh_bwd<2, false>
+                                          : k_sh_bwd<3, false>;
     FusedAdam fa{};
-    return launch_project_bwd_t<false>(p, map, views_dev, ws, grads, accumulate, fa, st);
+    kern_sh<<<(n + kProjThreads - 1) / kProjThreads, kProjThreads, sizeof(Cam) * p->vt.n_views,
+              st>>>(map->means, n, views_dev, p->vt, buf<uint32_t>(p, ws, GS_BUF_TOUCHED),
+                    buf<float>(p, ws, B_GCOL), grads->sh, accumulate, fa);
+    return launch_status();
 }
 
 gs_status launch_project_bwd_adam(const Plan* p, const gs_map* map, const gs_view* views_dev,
@@ -725,10 +749,33 @@ gs_status launch_project_bwd_adam(const Plan* p, const gs_map* map, const gs_vie
         fa.o_quats = grads_out->quats; fa.o_logit = grads_out->opacity_logits;
         fa.o_sh = grads_out->sh;
     }
-    fa.gmean = buf<float>(p, ws, B_GMEAN);
+    // this pass's per-Gaussian gradients: quaternions first (16-byte rows)
+    const int n = map->n;
+    float* scratch = buf<float>(p, ws, B_GPARAM);
+    gs_map_grad sg{};
+    sg.quats = scratch;
+    sg.means = scratch + 4 * (size_t)n;
+    sg.log_scales = scratch + 7 * (size_t)n;
+    sg.opacity_logits = scratch + 10 * (size_t)n;
+    fa.s_quats = sg.quats;
+    fa.s_means = sg.means;
+    fa.s_ls = sg.log_scales;
+    fa.s_logit = sg.opacity_logits;
     gs_status s = launch_step_inc(step_dev, st);
     if (s != GS_OK) return s;
-    return launch_project_bwd_t<true>(p, map, views_dev, ws, nullptr, 0, fa, st);
+    s = launch_project_adjoint(p, map, views_dev, ws, &sg, 0, st);
+    if (s != GS_OK) return s;
+    const int K = (map->sh_degree + 1) * (map->sh_degree + 1);
+    const size_t smem =
+        sizeof(Cam) * p->vt.n_views + (size_t)(kShAdamThreads / 32) * K * 96 * sizeof(float);
+    auto* kern_sh = map->sh_degree == 0   ? k_sh_bwd<0, true>
+                    : map->sh_degree == 1 ? k_sh_bwd<1, true>
+                    : map->sh_degree == 2 ? k_sh_bwd<2, true>
+                                          : k_sh_bwd<3, true>;
+    kern_sh<<<(n + kShAdamThreads - 1) / kShAdamThreads, kShAdamThreads, smem, st>>>(
+        map->means, n, views_dev, p->vt, buf<uint32_t>(p, ws, GS_BUF_TOUCHED),
+        buf<float>(p, ws, B_GCOL), nullptr, 0, fa);
+    return launch_status();
 }
 
 }  // namespace gs
