@@ -41,8 +41,23 @@ sys.path.insert(0, ROOT)
 METRIC = ("mapping iters/s (fwd+bwd+Adam) @1M Gaussians 1200×680; batched vs per-view; "
           "%roofline")
 WORKLOAD = "room1M_1200x680"
-PAIR_FLOPS_FWD = 26.0  # FP32 operations per evaluated (pixel, Gaussian) pair, forward
-PAIR_FLOPS_BWD = 64.0  # and per pair of the adjoint
+# FP32 operations per (pixel, Gaussian) pair of the algorithm as written (an
+# FMA counts 2): forward 26 (offset 1, power 9, exp 2, alpha 2, transmittance
+# 2, weight 1, blend 6, the three skip/stop tests 3); adjoint 64 (recompute 12,
+# transmittance and colour-behind recursion 20, gradient terms 23, sum over the
+# tile's pixels 9), the count of the adjoint as written, kept fixed across
+# implementations so the fractions stay comparable.
+PAIR_FLOPS_FWD = 26.0
+PAIR_FLOPS_BWD = 64.0
+
+# DRAM bytes (read + write) of one k_render_bwd launch on the 1M 1200x680
+# workload, from one single-pass ncu capture per launch shape (tile, backward
+# batch, backward pixels per thread) of the kernel as committed; other shapes
+# report null.  Summarised with its command in
+# profiles/launches_room1M_1200x680.md.
+RENDER_BWD_TRAFFIC = {
+    ("room1M_1200x680", "8x8", 32, 2): 93.78e6 + 1.32e6,
+}
 
 
 def load_peaks():
@@ -472,8 +487,12 @@ def run_gpu(args, ws, rank, local):
         flops = (pairs_bwd * PAIR_FLOPS_BWD) if dominant == "render_bwd" else (pairs_bwd * PAIR_FLOPS_FWD)
         peak = fp32_peak_tflops(peaks["sm_max_mhz"])
         achieved = flops / (stage_ms[dominant] * 1e-3) / 1e12
+        traffic = None
+        if dominant == "render_bwd":
+            traffic = RENDER_BWD_TRAFFIC.get((args.workload, f"{args.tile_w}x{args.tile_h}",
+                                              args.batch_bwd, args.ppt_bwd))
         roof = dict(bound="alu", kernel=dominant, achieved=achieved, peak=peak, unit="TFLOP/s",
-                    frac=achieved / peak, traffic=None, algorithmic=flops,
+                    frac=achieved / peak, traffic=traffic, algorithmic=flops,
                     peak_source="152 SMs x 128 FP32 lanes x 2 x sm_max_mhz (%s)" % peaks["source"])
 
     # project 1, bin_sort 18 + 3 per tile-id pass, render_fwd 1, loss 2,

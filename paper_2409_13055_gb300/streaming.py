@@ -38,7 +38,7 @@ class StreamingMapper:
         self.rast_kw = rast_kw
         self.gmap = None
         self.frames = []        # (view, target) of the window, oldest first
-        self._rasts = {}        # window size -> Rasterizer
+        self._rasts = {}        # window size -> its Rasterizer (the current one only)
         self.step = None
         self.keyframes = 0
         self.iterations = 0
@@ -53,7 +53,10 @@ class StreamingMapper:
             while self.capacity < n:
                 self.capacity *= 2
             r = mapping.Rasterizer(views, self.capacity, instance_capacity=None, **self.rast_kw)
-            self._rasts[V] = r
+            # one rasteriser at a time: a smaller window does not come back
+            # once the window is full, and each plan's workspace grows with
+            # views x capacity
+            self._rasts = {V: r}
             self.replans += 1
         r.set_poses(views)
         # instance capacity: one synchronising probe per keyframe
