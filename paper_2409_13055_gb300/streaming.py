@@ -7,9 +7,9 @@ over a window of keyframes).
 Per keyframe:
   1. its new Gaussians are appended to the map (``GaussianMap.append``: Adam
      moments zero, step counter kept);
-  2. the window's views, targets and rasteriser are set up (one rasteriser per
-     window size, planned for the map's capacity and re-planned with headroom
-     when the map or the instance count outgrows it);
+  2. the window's views, targets and rasteriser are set up (one rasteriser,
+     planned for the window size and the map's capacity and re-planned with
+     headroom when either changes or the instance count outgrows it);
   3. ``iters`` batched mapping iterations run over the whole window, each one
      ``MappingStep`` (project, bin, render, loss, backward, Adam), with the
      checkpointed backward by default, captured as one CUDA graph and replayed.
