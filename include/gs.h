@@ -167,7 +167,7 @@ enum {
 };
 gs_status gs_plan_buffer(const gs_plan *plan, int32_t id, size_t *offset, size_t *bytes);
 
-/* A1: projection (paper Sec. II "projecting Gaussians onto the camera plane";
+/* A1: projection (paper Sec. II: each Gaussian mapped onto the image plane;
  * Sec. III-B original 3DGS rasteriser).  For every (view, Gaussian): camera
  * transform, cull at near_z or on non-finite input, 3D covariance from the
  * normalised quaternion and exp(log_scales), EWA 2D covariance with the
@@ -187,7 +187,7 @@ gs_status gs_project(const gs_plan *plan, const gs_map *map, const gs_view *view
  * synchronisation); overflow sets GS_DEV_CAPACITY. */
 gs_status gs_bin_sort(const gs_plan *plan, int32_t n, void *ws, void *stream);
 
-/* A5: forward compositing (paper Sec. II "blending them front-to-back").
+/* A5: forward compositing (paper Sec. II: blending in depth order, front first).
  * Per pixel, front to back over its tile's list: power = -(a dx^2 + c dy^2)/2
  * - b dx dy, skipped when > 0; alpha = min(0.99, o e^power), skipped when
  * < 1/255; the Gaussian that would take T below 1e-4 stops the pixel and is

@@ -352,8 +352,8 @@ static int project_one(int i, int n, int degree, const double *means, const doub
 }
 
 /*
- * Projection of every Gaussian into one view (paper Sec. II: "projecting
- * Gaussians onto the camera plane"; Sec. III-B: original 3DGS rasteriser).
+ * Projection of every Gaussian into one view (paper Sec. II: the Gaussians
+ * are mapped onto the image plane; Sec. III-B: original 3DGS rasteriser).
  * Outputs per Gaussian: mean2d, depth (camera z), cov2d (a,b,c dilated),
  * conic (inverse of cov2d), opacity, rgb, colour-clamp mask, radius
  * r = ceil(3 sqrt(lambda_max)), tile rect [x0,y0,x1,y1) and tiles_touched.
