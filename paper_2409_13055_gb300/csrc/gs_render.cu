@@ -206,29 +206,39 @@ __device__ __forceinline__ PixelRun pixel_run(int tid, int ppt, int log2_tw, int
 }
 
 // Front-to-back blending of one staged batch for the PPT pixels of a thread.
-// live: bit k set while pixel k still accumulates.
+// live: bit k set while pixel k still accumulates.  The loop is warp-uniform
+// (a lane whose pixels are done runs predicated) so the warp can vote: a
+// Gaussian that no pixel of the warp blends costs only its alpha evaluation,
+// and the warp leaves the batch once none of its pixels is live.
 template <int CH, int PPT>
 __device__ __forceinline__ void blend_batch(int tid, const float4* stage, const uint32_t* wmask,
                                             int cnt, uint32_t pos0, int lx0, float ly, float* T,
                                             float (*C)[CH], int32_t* last, unsigned& live) {
     const uint32_t wbit = 1u << (tid >> 5);
-    for (int j = 0; j < cnt && live; ++j) {
+    if (!__any_sync(0xffffffffu, live != 0u)) return;
+    for (int j = 0; j < cnt; ++j) {
         if (!(wmask[j] & wbit)) continue;
         const float4 g = stage[3 * j];
         const float4 q = stage[3 * j + 1];
-        const float4 col = stage[3 * j + 2];
         const float dy = g.y - ly;
+        float al[PPT];
+        unsigned hits = 0u;
 #pragma unroll
         for (int k = 0; k < PPT; ++k) {
-            // predicated rather than branched: the same decisions as the
-            // backward, without divergent control flow inside the warp
+            // the same decisions as the backward, from the same rounded ops
             const float power = gauss_power(g.z, g.w, q.z, g.x - (float)(lx0 + k), dy);
-            const float alpha = alpha_of(q.w, power);
-            const float Tn = __fmul_rn(T[k], __fsub_rn(1.0f, alpha));
-            const bool hit = ((live >> k) & 1u) && power <= 0.0f && alpha >= kAlphaMin;
+            al[k] = alpha_of(q.w, power);
+            if (((live >> k) & 1u) && power <= 0.0f && al[k] >= kAlphaMin) hits |= 1u << k;
+        }
+        if (!__any_sync(0xffffffffu, hits != 0u)) continue;
+        const float4 col = stage[3 * j + 2];
+#pragma unroll
+        for (int k = 0; k < PPT; ++k) {
+            const bool hit = (hits >> k) & 1u;
+            const float Tn = __fmul_rn(T[k], __fsub_rn(1.0f, al[k]));
             const bool stop = hit && Tn < kTMin;
             const bool add = hit && !stop;
-            const float wgt = add ? alpha * T[k] : 0.0f;
+            const float wgt = add ? al[k] * T[k] : 0.0f;
             if (CH == 3) {
                 C[k][0] = fmaf(wgt, col.x, C[k][0]);
                 C[k][1] = fmaf(wgt, col.y, C[k][1]);
@@ -240,6 +250,7 @@ __device__ __forceinline__ void blend_batch(int tid, const float4* stage, const 
             last[k] = add ? (int32_t)(pos0 + j + 1) : last[k];
             live = stop ? (live & ~(1u << k)) : live;
         }
+        if (!__any_sync(0xffffffffu, live != 0u)) return;
     }
 }
 
@@ -491,22 +502,30 @@ __device__ void render_bwd_tile(const TM& tm, const ViewTable& vt, const TileCtx
             const float4 q = cur[3 * j + 1];
             const float4 col = cur[3 * j + 2];
             const float dy = gm.y - ly;
-            float P0 = 0.0f, P1 = 0.0f, P3 = 0.0f, cw[CH];
-#pragma unroll
-            for (int c = 0; c < CH; ++c) cw[c] = 0.0f;
+            // phase 1: alpha and the blend decision of every pixel of the
+            // lane; a Gaussian that no pixel of the warp blends is done here
+            float dxk[PPT], oGk[PPT], alk[PPT];
+            bool hk[PPT];
             bool contrib = false;
 #pragma unroll
             for (int k = 0; k < PPT; ++k) {
-                // predicated: every lane runs the same instructions; a lane
-                // whose pixel is not blended here contributes zeros and
-                // keeps its state
-                const float dx = gm.x - (float)(pr.lx0 + k);
-                const float power = gauss_power(gm.z, gm.w, q.z, dx, dy);
-                const float G = __expf(power);
-                const float oG = __fmul_rn(q.w, G);
-                const float alpha = fminf(kAlphaMax, oG);
-                const bool hit = pos < last[k] && power <= 0.0f && alpha >= kAlphaMin;
-                contrib |= hit;
+                dxk[k] = gm.x - (float)(pr.lx0 + k);
+                const float power = gauss_power(gm.z, gm.w, q.z, dxk[k], dy);
+                oGk[k] = __fmul_rn(q.w, __expf(power));
+                alk[k] = fminf(kAlphaMax, oGk[k]);
+                hk[k] = pos < last[k] && power <= 0.0f && alk[k] >= kAlphaMin;
+                contrib |= hk[k];
+            }
+            if (!__any_sync(0xffffffffu, contrib)) continue;
+            // phase 2, predicated: a lane whose pixel is not blended here
+            // contributes zeros and keeps its state
+            float P0 = 0.0f, P1 = 0.0f, P3 = 0.0f, cw[CH];
+#pragma unroll
+            for (int c = 0; c < CH; ++c) cw[c] = 0.0f;
+#pragma unroll
+            for (int k = 0; k < PPT; ++k) {
+                const float alpha = alk[k], oG = oGk[k], dx = dxk[k];
+                const bool hit = hk[k];
                 const float inv = rcp_approx(1.0f - alpha);
                 const float Ti = T[k] * inv;
                 const float w = hit ? alpha * Ti : 0.0f;
@@ -527,7 +546,7 @@ __device__ void render_bwd_tile(const TM& tm, const ViewTable& vt, const TileCtx
                 P1 += t;
                 P3 = fmaf(t, dx, P3);
             }
-            if (__any_sync(0xffffffffu, contrib)) {
+            {
                 // the pixels of a run share dy: A2 = dy A0, A4 = dy A1, A5 = dy A2
                 float v[NC];
                 v[0] = P0;
