@@ -177,17 +177,20 @@ def render_brute(proj, view, tile_w=16, tile_h=16, bg=(0.0, 0.0, 0.0), use_rect=
 
 def render_bwd(proj, tile_start, tile_list, view, dL_dimg, tile_w=16, tile_h=16,
                bg=(0.0, 0.0, 0.0)):
-    """Adjoint of `render`: screen-space gradients per Gaussian."""
+    """Adjoint of `render`: screen-space gradients per Gaussian, and the
+    homodirectional mean gradient dmean2d_abs (per-pixel contributions summed
+    by absolute value per component; the AbsGS density-control statistic)."""
     W, H, C = int(view["width"]), int(view["height"]), int(view.get("channels", 3))
     n = proj["mean2d"].shape[0]
     g = dict(dmean2d=np.zeros((n, 2)), dconic=np.zeros((n, 3)), dopacity=np.zeros(n),
-             drgb=np.zeros((n, 3)))
+             drgb=np.zeros((n, 3)), dmean2d_abs=np.zeros((n, 2)))
     _L().oracle_render_bwd(
         _i(n), _p(_d(proj["mean2d"])), _p(_d(proj["conic"])), _p(_d(proj["opacity"])),
         _p(_d(proj["rgb"])), _p(np.ascontiguousarray(tile_start, np.int64)),
         _p(np.ascontiguousarray(tile_list, np.int32)), _i(W), _i(H), _i(tile_w), _i(tile_h),
         _i(C), _p(_d(bg)), _p(_d(np.asarray(dL_dimg).reshape(C, H, W))),
-        _p(g["dmean2d"]), _p(g["dconic"]), _p(g["dopacity"]), _p(g["drgb"]))
+        _p(g["dmean2d"]), _p(g["dconic"]), _p(g["dopacity"]), _p(g["drgb"]),
+        _p(g["dmean2d_abs"]))
     return g
 
 
@@ -256,8 +259,10 @@ PARAM_GROUPS = ("means", "log_scales", "quats", "opacity_logits", "sh")
 
 
 def iteration(params, views, targets, lam, tile_w=16, tile_h=16, bg=(0.0, 0.0, 0.0),
-              near_z=NEAR_Z):
-    """Loss (mean over views) and parameter gradients (sum of per-view adjoints)."""
+              near_z=NEAR_Z, stats=None):
+    """Loss (mean over views) and parameter gradients (sum of per-view adjoints).
+    With stats = (accum, denom) the density-control statistic of this
+    iteration is added to them (densify_stats)."""
     grads = zero_grads(params)
     total = 0.0
     renders = []
@@ -268,5 +273,105 @@ def iteration(params, views, targets, lam, tile_w=16, tile_h=16, bg=(0.0, 0.0, 0
         total += L / V
         g2d = render_bwd(proj, start, lst, view, dimg / V, tile_w, tile_h, bg)
         project_bwd(params, view, g2d, grads, tile_w, tile_h, near_z)
+        if stats is not None:
+            densify_stats(stats[0], stats[1], view, proj["tiles_touched"], g2d["dmean2d_abs"])
         renders.append(out)
     return total, grads, renders
+
+
+# --------------------------------------------------------------------------
+# Adaptive density control (paper Sec. III-B): every so many iterations,
+# Gaussians with a high homodirectional view-space position gradient (the
+# AbsGS criterion) are cloned when small and split when large, and Gaussians
+# of low opacity are pruned; splitting and cloning use the original 3DGS
+# parameters.  Readings: the statistic is the gradient with respect to the
+# projected mean in normalised device coordinates (x_ndc = 2 x_px / W - 1,
+# so d/dx_ndc = W/2 d/dx_px), its per-pixel contributions summed by absolute
+# value per component, the Euclidean norm of that pair added once per
+# (iteration, view) in which the Gaussian touches a tile, and averaged over
+# those counts.
+# --------------------------------------------------------------------------
+DENSIFY_DEFAULTS = dict(grad_threshold=0.0004, percent_dense=0.01, min_opacity=0.005,
+                        split_shrink=1.6)
+
+# categories of densify_categories
+PRUNE, KEEP, CLONE, SPLIT = 0, 1, 2, 3
+
+
+def densify_stats(accum, denom, view, touched, dmean2d_abs):
+    """Add one view's homodirectional statistic: for every Gaussian touching a
+    tile, accum += |(W/2 sum|dL/dx|, H/2 sum|dL/dy|)|, denom += 1 (in place)."""
+    vis = np.asarray(touched) > 0
+    hx = np.asarray(dmean2d_abs, np.float64)[:, 0] * (0.5 * view["width"])
+    hy = np.asarray(dmean2d_abs, np.float64)[:, 1] * (0.5 * view["height"])
+    accum[vis] += np.hypot(hx, hy)[vis]
+    denom[vis] += 1.0
+
+
+def densify_categories(params, accum, denom, extent, cfg=None):
+    """Per Gaussian: PRUNE if its opacity is below min_opacity (first); else
+    CLONE if its mean statistic reaches grad_threshold and its largest scale
+    is at most percent_dense * extent; SPLIT if the statistic reaches the
+    threshold and the Gaussian is larger; KEEP otherwise."""
+    c = dict(DENSIFY_DEFAULTS, **(cfg or {}))
+    ol = np.asarray(params["opacity_logits"], np.float64)
+    opacity = 1.0 / (1.0 + np.exp(-ol))
+    smax = np.exp(np.max(np.asarray(params["log_scales"], np.float64), axis=1))
+    accum = np.asarray(accum, np.float64)
+    denom = np.asarray(denom, np.float64)
+    stat = np.where(denom > 0, accum / np.where(denom > 0, denom, 1.0), 0.0)
+    high = (denom > 0) & (stat >= c["grad_threshold"])
+    small = smax <= c["percent_dense"] * extent
+    cat = np.full(ol.shape[0], KEEP, np.int32)
+    cat[high & small] = CLONE
+    cat[high & ~small] = SPLIT
+    cat[opacity < c["min_opacity"]] = PRUNE
+    return cat
+
+
+def densify_apply(params, moments, cat, samples, cfg=None):
+    """The map after density control, in this order: the kept Gaussians (KEEP
+    and the originals of CLONE) by index, then the clones by index, then two
+    children per SPLIT Gaussian by index.  A clone copies its original. A
+    child c of Gaussian i has mean mu_i + R(q_i / |q_i|) (s_i * samples[i, c])
+    (samples: standard normal draws, passed in), log-scales reduced by
+    log(split_shrink), and the rotation, opacity and SH of its parent.
+    moments: dict name -> (m, v) per group in the params layout; kept
+    Gaussians keep theirs, new ones start at zero."""
+    from scipy.spatial.transform import Rotation
+    c = dict(DENSIFY_DEFAULTS, **(cfg or {}))
+    cat = np.asarray(cat)
+    keep = (cat == KEEP) | (cat == CLONE)
+    clone = cat == CLONE
+    split = np.flatnonzero(cat == SPLIT)
+    mu = np.asarray(params["means"], np.float64)
+    ls = np.asarray(params["log_scales"], np.float64)
+    q = np.asarray(params["quats"], np.float64)
+    samples = np.asarray(samples, np.float64).reshape(-1, 2, 3)
+    out = {}
+    for k in ("means", "log_scales", "quats", "opacity_logits"):
+        a = np.asarray(params[k], np.float64)
+        out[k] = np.concatenate([a[keep], a[clone], np.repeat(a[split], 2, axis=0)])
+    sh = np.asarray(params["sh"], np.float64)
+    out["sh"] = np.concatenate([sh[:, keep], sh[:, clone], np.repeat(sh[:, split], 2, axis=1)],
+                               axis=1)
+    if split.size:
+        Rm = Rotation.from_quat(q[split], scalar_first=True).as_matrix()  # normalises
+        s = np.exp(ls[split])
+        child = mu[split][:, None, :] + np.einsum("nij,ncj->nci", Rm, s[:, None, :] *
+                                                  samples[split])
+        base = keep.sum() + clone.sum()
+        out["means"][base:] = child.reshape(-1, 3)
+        out["log_scales"][base:] -= np.log(c["split_shrink"])
+    out["sh_degree"] = params["sh_degree"]
+    new_moments = {}
+    n_new = clone.sum() + 2 * split.size
+    for k, (m, v) in (moments or {}).items():
+        m, v = np.asarray(m, np.float64), np.asarray(v, np.float64)
+        if k == "sh":
+            z = np.zeros((m.shape[0], n_new, m.shape[2]))
+            new_moments[k] = (np.concatenate([m[:, keep], z], 1), np.concatenate([v[:, keep], z], 1))
+        else:
+            z = np.zeros((n_new,) + m.shape[1:])
+            new_moments[k] = (np.concatenate([m[keep], z]), np.concatenate([v[keep], z]))
+    return out, new_moments

@@ -682,7 +682,7 @@ void oracle_render_bwd(int n, const double *mean2d, const double *conic, const d
                        const double *rgb, const int64_t *tile_start, const int32_t *list, int W,
                        int H, int tile_w, int tile_h, int channels, const double *bg,
                        const double *dL_dimg, double *dmean2d, double *dconic, double *dopacity,
-                       double *drgb) {
+                       double *drgb, double *dmean2d_abs) {
     (void)n;
     const int tiles_x = (W + tile_w - 1) / tile_w;
     int64_t maxlen = 0;
@@ -723,8 +723,18 @@ void oracle_render_bwd(int n, const double *mean2d, const double *conic, const d
                 double dpow = o * cs[k].G * dal;
                 double a = conic[3 * gi], b = conic[3 * gi + 1], cc = conic[3 * gi + 2];
                 double dx = cs[k].dx, dy = cs[k].dy;
-                dmean2d[2 * gi] += dpow * (-(a * dx + b * dy));
-                dmean2d[2 * gi + 1] += dpow * (-(b * dx + cc * dy));
+                const double gx = dpow * (-(a * dx + b * dy));
+                const double gy = dpow * (-(b * dx + cc * dy));
+                dmean2d[2 * gi] += gx;
+                dmean2d[2 * gi + 1] += gy;
+                /* Homodirectional view-space gradient (AbsGS, the density
+                 * control of paper Sec. III-B): the per-pixel contributions
+                 * summed by absolute value, component by component, so that
+                 * contributions of opposite sign do not cancel. */
+                if (dmean2d_abs) {
+                    dmean2d_abs[2 * gi] += fabs(gx);
+                    dmean2d_abs[2 * gi + 1] += fabs(gy);
+                }
                 dconic[3 * gi] += dpow * (-0.5 * dx * dx);
                 dconic[3 * gi + 1] += dpow * (-dx * dy);
                 dconic[3 * gi + 2] += dpow * (-0.5 * dy * dy);
