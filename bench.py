@@ -333,6 +333,54 @@ def run_streaming(args, ws):
                             pixels_per_thread_bwd=args.ppt_bwd))
 
 
+def run_density(args, ws, p, view, target):
+    """Adaptive density control on the headline workload: K whole-iteration
+    graph replays that also accumulate the AbsGS statistic (pixel adjoint
+    with the homodirectional sums + gs_densify_stats), then one density
+    control step (count, one host read of the new size, apply) timed on the
+    host clock around a synchronised region."""
+    import time
+
+    import torch
+    from paper_2409_13055_gb300 import mapping
+
+    gm = mapping.GaussianMap(p)
+    rast = mapping.fit_instance_capacity([view], gm, headroom=1.5, tile=(args.tile_w, args.tile_h),
+                                         smem_batch=args.batch, pixels_per_thread=args.ppt,
+                                         smem_batch_bwd=args.batch_bwd,
+                                         pixels_per_thread_bwd=args.ppt_bwd, density_stats=True)
+    accum = torch.zeros(gm.n, device="cuda")
+    denom = torch.zeros(gm.n, device="cuda")
+    step = mapping.MappingStep(gm, rast, target, 0.2, stats=(accum, denom))
+    step.capture(warmup=max(3, args.warmup))
+    K = max(10, min(args.steps, 100))
+    stream = torch.cuda.current_stream()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    barrier(ws)
+    torch.cuda.synchronize()
+    e0.record(stream)
+    for _ in range(K):
+        step()
+    e1.record(stream)
+    torch.cuda.synchronize()
+    it_ms = reduce_max(e0.elapsed_time(e1), ws) / K
+    samples = torch.randn(gm.n, 2, 3, device="cuda",
+                          generator=torch.Generator(device="cuda").manual_seed(2409_13055))
+    n0 = gm.n
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    kept, cloned, split = gm.densify(accum, denom, samples, extent=1.0)
+    torch.cuda.synchronize()
+    dens_ms = (time.perf_counter() - t0) * 1e3
+    return dict(iters_per_s_with_stats=ws * 1e3 / it_ms, ms_per_iter_with_stats=it_ms,
+                densify_ms=dens_ms, gaussians_before=n0, gaussians_after=gm.n, kept=kept,
+                cloned=cloned, split=split, pruned=n0 - kept - split,
+                config=dict(statistic_iterations=K + max(3, args.warmup) + 1,
+                            grad_threshold=0.0004, percent_dense=0.01, min_opacity=0.005,
+                            extent=1.0, cuda_graph="whole iteration",
+                            densify="count + one host read + apply, host clock"))
+
+
 def run_gpu(args, ws, rank, local):
     import torch
     from paper_2409_13055_gb300 import binding as B
@@ -529,6 +577,9 @@ def run_gpu(args, ws, rank, local):
     if args.streaming_kfs > 0:
         torch.cuda.empty_cache()
         out["streaming"] = run_streaming(args, ws)
+    if not args.no_density:
+        torch.cuda.empty_cache()
+        out["density_control"] = run_density(args, ws, p, view, target)
 
     if rank == 0 and not args.no_cpu_baseline:
         from paper_2409_13055_gb300 import scenes as sc
@@ -565,6 +616,8 @@ def main():
                          "1M: 0.44 vs 0.56 ms), or inside the projection adjoint")
     ap.add_argument("--streaming-kfs", type=int, default=100,
                     help="keyframes of the streaming measurement (0 skips it)")
+    ap.add_argument("--no-density", action="store_true",
+                    help="skip the adaptive density control measurement")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--reference-warmup", action="store_true")
     args = ap.parse_args()

@@ -100,7 +100,10 @@ typedef struct {
  *     backward (gs_render_bwd*); 0 = as for the forward;
  *   near_z: Gaussians whose camera depth is not above near_z are culled
  *     (default reading 0.2 m);
- *   bg: background colour, entering the image as T_final * bg.
+ *   bg: background colour, entering the image as T_final * bg;
+ *   density_stats: nonzero makes the pixel adjoint also sum, per (view,
+ *     Gaussian), the per-pixel contributions to dL/dmean2d by absolute value
+ *     (GS_BUF_ABSGRAD), the statistic of the density control below.
  * The tile shape changes which pixels a Gaussian can reach (its 3-sigma
  * rect is counted in whole tiles), hence the image; the batch sizes and
  * pixels per thread change only the speed. */
@@ -109,6 +112,7 @@ typedef struct {
     int32_t smem_batch_bwd, pixels_per_thread_bwd;
     float near_z;
     float bg[3];
+    int32_t density_stats;
 } gs_config;
 
 /* A plan: the sizes, tile grids and workspace layout of one batch of views.
@@ -163,6 +167,8 @@ enum {
     GS_BUF_RANGES = 8,      /* [total_tiles] x 2 uint32: [begin, end) of each tile */
     GS_BUF_GRAD2D = 9,      /* [V*n] x 9 floats: dmean2d (2), dconic (3), dopacity,
                                dcolour (3) accumulated by gs_render_bwd */
+    GS_BUF_ABSGRAD = 10,    /* [V*n] x 2 floats: sum over pixels of |dL_p/dmean2d| per
+                               component (only with density_stats) */
     GS_BUF_COUNT = 16
 };
 gs_status gs_plan_buffer(const gs_plan *plan, int32_t id, size_t *offset, size_t *bytes);
@@ -294,6 +300,65 @@ gs_status gs_adam_step(float *params, const float *grads, float *m, float *v, in
                        int32_t n_groups, const int64_t *group_offsets_host,
                        const float *group_lr_host, float beta1, float beta2, float eps,
                        int32_t *step_dev, void *stream);
+
+/* ---------------------------------------------------------------------------
+ * Adaptive density control (paper Sec. III-B): periodically, Gaussians with a
+ * high homodirectional view-space position gradient (the AbsGS criterion) are
+ * cloned when small and split in two when large, with the original 3DGS
+ * parameters, and Gaussians of low opacity are pruned.
+ *
+ * Readings: the statistic of a Gaussian is the mean, over the (iteration,
+ * view) pairs in which it touches a tile, of |(W/2 h_x, H/2 h_y)|, where
+ * (h_x, h_y) sums over pixels the absolute per-pixel contributions to
+ * dL/dmean2d (pixel units; W/2, H/2 convert to normalised device
+ * coordinates).  Category, in this order: PRUNE if sigmoid(opacity_logit) <
+ * min_opacity; CLONE if statistic >= grad_threshold and the largest scale
+ * exp(max log_scale) <= percent_dense * extent; SPLIT if statistic >=
+ * grad_threshold otherwise; else KEEP.  Output order: kept Gaussians (KEEP
+ * and the originals of CLONE) by index, clones by index, then two children
+ * per SPLIT by index; child c of Gaussian i: mean + R(q/|q|) (s * xi_ic)
+ * with xi = samples[i][c][0..2] (standard normal draws, supplied by the
+ * caller), log-scales - log(split_shrink), rotation, opacity and SH copied.
+ * Adam moments: kept Gaussians keep theirs, new ones start at zero.
+ * ------------------------------------------------------------------------- */
+typedef struct {
+    float grad_threshold; /* 3DGS-style NDC gradient threshold (0.0004) */
+    float percent_dense;  /* clone/split boundary as a fraction of extent (0.01) */
+    float min_opacity;    /* prune below (0.005) */
+    float split_shrink;   /* children scales divided by this (1.6) */
+    float extent;         /* scene extent */
+    int32_t reserved[3];
+} gs_densify_config;
+
+/* Adds this iteration's statistic: for each (view, Gaussian) of the plan with
+ * tiles touched > 0, accum[i] += |(W/2 h_x, H/2 h_y)| and denom[i] += 1
+ * (device float arrays of n).  Needs a plan with density_stats and a
+ * preceding gs_render_bwd / gs_render_bwd_pixels. */
+gs_status gs_densify_stats(const gs_plan *plan, int32_t n, const void *ws, float *accum,
+                           float *denom, void *stream);
+
+/* Bytes of device scratch gs_densify_count / gs_densify_apply need for n
+ * Gaussians. */
+size_t gs_densify_scratch_bytes(int32_t n);
+
+/* Categorises every Gaussian of map and writes counts_dev[0..3] (device int32)
+ * = (kept, cloned, split, 0); the new map holds kept + cloned + 2 split
+ * Gaussians.  The per-block counts stay in scratch for gs_densify_apply. */
+gs_status gs_densify_count(const gs_map *map, const float *accum, const float *denom,
+                           const gs_densify_config *cfg, void *scratch, int32_t *counts_dev,
+                           void *stream);
+
+/* Writes the new map (dst: n_out Gaussians, SH planes [K][n_out][3]) and its
+ * moments (dst_m, dst_v; src_m/src_v the moments of map) from the same
+ * inputs given to gs_densify_count and its scratch.  samples: device floats
+ * [map->n][2][3].  n_out must equal kept + cloned + 2 split (checked on the
+ * device: GS_DEV_CAPACITY is not used; a mismatch writes nothing past
+ * n_out and sets counts_dev[3] = 1 if counts_dev is given). counts_dev: [4]. */
+gs_status gs_densify_apply(const gs_map *map, const gs_map_grad *src_m, const gs_map_grad *src_v,
+                           const float *accum, const float *denom, const float *samples,
+                           const gs_densify_config *cfg, const void *scratch, int32_t n_out,
+                           gs_map_grad *dst, gs_map_grad *dst_m, gs_map_grad *dst_v,
+                           int32_t *counts_dev, void *stream);
 
 /* Copies the device counters of the workspace to *out (host) and waits for
  * `stream`. */

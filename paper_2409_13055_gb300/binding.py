@@ -22,7 +22,7 @@ GS_OK, GS_ERR_INVALID, GS_ERR_CUDA, GS_ERR_CAPACITY, GS_ERR_UNSUPPORTED, GS_ERR_
 GS_DEV_CAPACITY, GS_DEV_NONFINITE = 1, 2
 GS_MAX_VIEWS, GS_MAX_GROUPS, GS_PLAN_WORDS = 64, 8, 1536
 (GS_BUF_COUNTERS, GS_BUF_PROJ, GS_BUF_RECT, GS_BUF_TOUCHED, GS_BUF_RADIUS, GS_BUF_DEPTH_ORDER,
- GS_BUF_TILE_KEYS, GS_BUF_TILE_VALUES, GS_BUF_RANGES, GS_BUF_GRAD2D) = range(10)
+ GS_BUF_TILE_KEYS, GS_BUF_TILE_VALUES, GS_BUF_RANGES, GS_BUF_GRAD2D, GS_BUF_ABSGRAD) = range(11)
 
 
 class gs_view(ctypes.Structure):
@@ -45,7 +45,14 @@ class gs_map_grad(ctypes.Structure):
 class gs_config(ctypes.Structure):
     _fields_ = [("tile_w", c_int32), ("tile_h", c_int32), ("smem_batch", c_int32),
                 ("pixels_per_thread", c_int32), ("smem_batch_bwd", c_int32),
-                ("pixels_per_thread_bwd", c_int32), ("near_z", c_float), ("bg", c_float * 3)]
+                ("pixels_per_thread_bwd", c_int32), ("near_z", c_float), ("bg", c_float * 3),
+                ("density_stats", c_int32)]
+
+
+class gs_densify_config(ctypes.Structure):
+    _fields_ = [("grad_threshold", c_float), ("percent_dense", c_float),
+                ("min_opacity", c_float), ("split_shrink", c_float), ("extent", c_float),
+                ("reserved", c_int32 * 3)]
 
 
 class gs_plan(ctypes.Structure):
@@ -87,6 +94,15 @@ _SIGNATURES = {
     "gs_adam_step": (c_int32, [c_void_p, c_void_p, c_void_p, c_void_p, c_int64, c_int32,
                                _P(c_int64), _P(c_float), c_float, c_float, c_float, c_void_p,
                                c_void_p]),
+    "gs_densify_stats": (c_int32, [_P(gs_plan), c_int32, c_void_p, c_void_p, c_void_p,
+                                   c_void_p]),
+    "gs_densify_scratch_bytes": (c_size_t, [c_int32]),
+    "gs_densify_count": (c_int32, [_P(gs_map), c_void_p, c_void_p, _P(gs_densify_config),
+                                   c_void_p, c_void_p, c_void_p]),
+    "gs_densify_apply": (c_int32, [_P(gs_map), _P(gs_map_grad), _P(gs_map_grad), c_void_p,
+                                   c_void_p, c_void_p, _P(gs_densify_config), c_void_p, c_int32,
+                                   _P(gs_map_grad), _P(gs_map_grad), _P(gs_map_grad), c_void_p,
+                                   c_void_p]),
     "gs_read_counters": (c_int32, [_P(gs_plan), c_void_p, _P(gs_counters), c_void_p]),
     "gs_status_string": (ctypes.c_char_p, [c_int32]),
 }
@@ -248,6 +264,30 @@ def gs_adam_step(params, grads, m, v, group_offsets, group_lr, beta1, beta2, eps
     check(lib().gs_adam_step(_ptr(params), _ptr(grads), _ptr(m), _ptr(v), int(params.numel()), ng,
                              offs, lrs, float(beta1), float(beta2), float(eps), _ptr(step_dev),
                              _stream(stream)), "gs_adam_step")
+
+
+def gs_densify_stats(plan, n, ws, accum, denom, stream=None):
+    check(lib().gs_densify_stats(ctypes.byref(plan), int(n), _ptr(ws), _ptr(accum), _ptr(denom),
+                                 _stream(stream)), "gs_densify_stats")
+
+
+def gs_densify_scratch_bytes(n) -> int:
+    return int(lib().gs_densify_scratch_bytes(int(n)))
+
+
+def gs_densify_count(gmap, accum, denom, cfg, scratch, counts_dev, stream=None):
+    check(lib().gs_densify_count(ctypes.byref(gmap), _ptr(accum), _ptr(denom), ctypes.byref(cfg),
+                                 _ptr(scratch), _ptr(counts_dev), _stream(stream)),
+          "gs_densify_count")
+
+
+def gs_densify_apply(gmap, src_m, src_v, accum, denom, samples, cfg, scratch, n_out, dst, dst_m,
+                     dst_v, counts_dev, stream=None):
+    check(lib().gs_densify_apply(ctypes.byref(gmap), ctypes.byref(src_m), ctypes.byref(src_v),
+                                 _ptr(accum), _ptr(denom), _ptr(samples), ctypes.byref(cfg),
+                                 _ptr(scratch), int(n_out), ctypes.byref(dst), ctypes.byref(dst_m),
+                                 ctypes.byref(dst_v), _ptr(counts_dev), _stream(stream)),
+          "gs_densify_apply")
 
 
 def gs_read_counters(plan, ws, stream=None) -> gs_counters:

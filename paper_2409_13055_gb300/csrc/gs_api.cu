@@ -109,6 +109,7 @@ extern "C" gs_status gs_plan_init(gs_plan* plan, const gs_config* cfg, int32_t n
     len[GS_BUF_TILE_VALUES] = (size_t)instance_capacity * sizeof(uint32_t);
     len[GS_BUF_RANGES] = (size_t)tiles * 2 * sizeof(uint32_t);
     len[GS_BUF_GRAD2D] = (size_t)VN * kGrad2d * sizeof(float);
+    len[GS_BUF_ABSGRAD] = cfg->density_stats ? (size_t)VN * 2 * sizeof(float) : 0;
     len[B_DKEY_A] = (size_t)VN * sizeof(uint32_t);
     len[B_DKEY_B] = (size_t)VN * sizeof(uint32_t);
     len[B_DVAL_B] = (size_t)VN * sizeof(uint32_t);
@@ -168,7 +169,7 @@ extern "C" gs_status gs_plan_buffer(const gs_plan* plan, int32_t id, size_t* off
                                     size_t* bytes) {
     if (!plan_ok(plan) || id < 0 || id >= GS_BUF_COUNT) return GS_ERR_INVALID;
     const Plan* p = P(plan);
-    if (id > GS_BUF_GRAD2D) return GS_ERR_INVALID;
+    if (id > GS_BUF_ABSGRAD) return GS_ERR_INVALID;
     size_t o = p->off[id], l = p->len[id];
     // The sorted instance arrays end in the A or B buffer depending on the
     // number of tile-id passes; report where the result is.

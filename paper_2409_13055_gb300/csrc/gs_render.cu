@@ -421,16 +421,20 @@ __device__ __forceinline__ float rcp_approx(float x) {
 //   dL/dmean = -(a A1 + b A2, b A1 + c A2), dL/d(a, b, c) = (-A3/2, -A4, -A5/2),
 //   dL/do = A0 / o   (dp = o G dL/dalpha wherever alpha = o G is unclamped),
 // which is applied once per Gaussian and batch, before the global atomics.
-template <int CH, int PPT, class TM>
+template <int CH, int PPT, class TM, bool ABS>
 __device__ void render_bwd_tile(const TM& tm, const ViewTable& vt, const TileCtx& tc,
                                 const uint32_t* __restrict__ ivals,
                                 const float4* __restrict__ rec, float4* smem, int* s_maxlast,
                                 int batch, const float* bg, const float* __restrict__ final_T,
                                 const int32_t* __restrict__ last_idx,
-                                const float* __restrict__ dL, float* __restrict__ grad2d) {
+                                const float* __restrict__ dL, float* __restrict__ grad2d,
+                                float* __restrict__ absgrad) {
     // shared memory: stage[2][3*batch] float4 | ids[2][batch] | masks[2][batch] |
-    //                acc[batch][9] float (the batch's per-Gaussian sums)
-    constexpr int NC = CH == 3 ? kGrad2d : 7;  // moments + colour components
+    //                acc[batch][KA] float (the batch's per-Gaussian sums: 9, and
+    //                with ABS the two homodirectional sums in slots 9, 10)
+    constexpr int NC0 = CH == 3 ? kGrad2d : 7;  // moments + colour components
+    constexpr int NC = NC0 + (ABS ? 2 : 0);      // values reduced per Gaussian
+    constexpr int KA = kGrad2d + (ABS ? 2 : 0);  // shared slots per Gaussian
     uint32_t* const ids0 = reinterpret_cast<uint32_t*>(smem + 6 * batch);
     uint32_t* const mask0 = ids0 + 2 * batch;
     float* const acc = reinterpret_cast<float*>(mask0 + 2 * batch);
@@ -467,10 +471,12 @@ __device__ void render_bwd_tile(const TM& tm, const ViewTable& vt, const TileCtx
             mylast = max(mylast, last[k]);
         }
     }
-    for (int i = tm.tid; i < kGrad2d * batch; i += tm.size) acc[i] = 0.0f;
+    for (int i = tm.tid; i < KA * batch; i += tm.size) acc[i] = 0.0f;
     const int maxlast = tm.max(mylast, s_maxlast);
     const int nb = (maxlast + batch - 1) / batch;
-    const int comp = reduce_component<NC>(threadIdx.x & 31);
+    const int comp_r = reduce_component<NC>(threadIdx.x & 31);
+    // the shared slot of the reduced value this lane holds
+    const int comp = comp_r < NC0 ? comp_r : (comp_r < 0 ? -1 : kGrad2d + comp_r - NC0);
     // batch k covers list positions [max(0, maxlast - (k+1) batch), maxlast - k batch)
     if (nb > 0) {
         const int lo = max(0, maxlast - batch);
@@ -519,7 +525,7 @@ __device__ void render_bwd_tile(const TM& tm, const ViewTable& vt, const TileCtx
             if (!__any_sync(0xffffffffu, contrib)) continue;
             // phase 2, predicated: a lane whose pixel is not blended here
             // contributes zeros and keeps its state
-            float P0 = 0.0f, P1 = 0.0f, P3 = 0.0f, cw[CH];
+            float P0 = 0.0f, P1 = 0.0f, P3 = 0.0f, cw[CH], Hx = 0.0f, Hy = 0.0f;
 #pragma unroll
             for (int c = 0; c < CH; ++c) cw[c] = 0.0f;
 #pragma unroll
@@ -545,6 +551,11 @@ __device__ void render_bwd_tile(const TM& tm, const ViewTable& vt, const TileCtx
                 P0 += dp;
                 P1 += t;
                 P3 = fmaf(t, dx, P3);
+                if (ABS) {
+                    // this pixel's own contribution to dL/dmean2d, by magnitude
+                    Hx += fabsf(dp * fmaf(gm.z, dx, gm.w * dy));
+                    Hy += fabsf(dp * fmaf(gm.w, dx, q.z * dy));
+                }
             }
             {
                 // the pixels of a run share dy: A2 = dy A0, A4 = dy A1, A5 = dy A2
@@ -557,14 +568,18 @@ __device__ void render_bwd_tile(const TM& tm, const ViewTable& vt, const TileCtx
                 v[5] = dy * v[2];
 #pragma unroll
                 for (int c = 0; c < CH; ++c) v[6 + c] = cw[c];
+                if (ABS) {
+                    v[NC0] = Hx;
+                    v[NC0 + 1] = Hy;
+                }
                 const float tot = warp_reduce_split<NC>(v);
-                if (comp >= 0) tm.add(acc + j * kGrad2d + comp, tot);
+                if (comp >= 0) tm.add(acc + j * KA + comp, tot);
             }
         }
         tm.sync();
         // moments -> screen-space gradient (see above), one Gaussian per thread
         for (int j = tm.tid; j < cnt; j += tm.size) {
-            float* a = acc + j * kGrad2d;
+            float* a = acc + j * KA;
             const float A0 = a[0], A1 = a[1], A2 = a[2];
             if (A0 == 0.0f && A1 == 0.0f && A2 == 0.0f && a[3] == 0.0f && a[4] == 0.0f &&
                 a[5] == 0.0f)
@@ -580,11 +595,14 @@ __device__ void render_bwd_tile(const TM& tm, const ViewTable& vt, const TileCtx
         }
         tm.sync();
         // flush this batch's sums: one global atomic per (Gaussian, component, tile)
-        for (int i = tm.tid; i < kGrad2d * cnt; i += tm.size) {
+        for (int i = tm.tid; i < KA * cnt; i += tm.size) {
             const float a = acc[i];
             if (a != 0.0f) {
-                const int j = i / kGrad2d;
-                atomicAdd(grad2d + (size_t)cur_ids[j] * kGrad2d + (i - j * kGrad2d), a);
+                const int j = i / KA, c = i - j * KA;
+                if (c < kGrad2d)
+                    atomicAdd(grad2d + (size_t)cur_ids[j] * kGrad2d + c, a);
+                else
+                    atomicAdd(absgrad + (size_t)cur_ids[j] * 2 + (c - kGrad2d), a);
                 acc[i] = 0.0f;
             }
         }
@@ -592,14 +610,14 @@ __device__ void render_bwd_tile(const TM& tm, const ViewTable& vt, const TileCtx
     }
 }
 
-template <int PPT, bool WARP>
+template <int PPT, bool WARP, bool ABS>
 __global__ void k_render_bwd(ViewTable vt, const uint32_t* __restrict__ ranges,
                              const uint32_t* __restrict__ order,
                              const uint32_t* __restrict__ ivals, const float4* __restrict__ rec,
                              int batch, int team_f4, int total_tiles, uint32_t* queue, float bg0,
                              float bg1, float bg2, const float* __restrict__ final_T,
                              const int32_t* __restrict__ last_idx, const float* __restrict__ dL,
-                             float* __restrict__ grad2d) {
+                             float* __restrict__ grad2d, float* __restrict__ absgrad) {
     extern __shared__ float4 smem[];
     __shared__ int s_slot, s_maxlast;
     const Team<WARP> tm;
@@ -610,11 +628,13 @@ __global__ void k_render_bwd(ViewTable vt, const uint32_t* __restrict__ ranges,
         if (slot >= total_tiles) break;
         const TileCtx tc = tile_ctx(vt, ranges, (int)order[slot]);
         if (tc.channels == 3)
-            render_bwd_tile<3, PPT>(tm, vt, tc, ivals, rec, mine, &s_maxlast, batch, bg, final_T,
-                                    last_idx, dL, grad2d);
+            render_bwd_tile<3, PPT, Team<WARP>, ABS>(tm, vt, tc, ivals, rec, mine, &s_maxlast,
+                                                     batch, bg, final_T, last_idx, dL, grad2d,
+                                                     absgrad);
         else
-            render_bwd_tile<1, PPT>(tm, vt, tc, ivals, rec, mine, &s_maxlast, batch, bg, final_T,
-                                    last_idx, dL, grad2d);
+            render_bwd_tile<1, PPT, Team<WARP>, ABS>(tm, vt, tc, ivals, rec, mine, &s_maxlast,
+                                                     batch, bg, final_T, last_idx, dL, grad2d,
+                                                     absgrad);
     }
 }
 
@@ -628,8 +648,9 @@ static K pick(int ppt, K a, K b, K c, K d) {
 // Shared memory of one tile team, in float4 units: the double-buffered
 // stage (6 float4 per Gaussian slot) and the 32-bit arrays (2 per slot in the
 // forward: masks; 4 plus the nine gradient sums in the backward).
-static int team_f4(int batch, bool bwd) {
-    const size_t words = bwd ? (size_t)(4 + kGrad2d) * batch : (size_t)2 * batch;
+static int team_f4(int batch, bool bwd, bool abs_stats = false) {
+    const size_t words =
+        bwd ? (size_t)(4 + kGrad2d + (abs_stats ? 2 : 0)) * batch : (size_t)2 * batch;
     return 6 * batch + (int)((words * 4 + 15) / 16);
 }
 
@@ -690,7 +711,7 @@ static RenderShape render_shape(const Plan* p, int batch, int ppt, bool bwd) {
     RenderShape s;
     const int tile_threads = p->cfg.tile_w * p->cfg.tile_h / ppt;
     s.warp = tile_threads == 32;
-    s.tf4 = team_f4(batch, bwd);
+    s.tf4 = team_f4(batch, bwd, bwd && p->cfg.density_stats != 0);
     s.teams = s.warp ? warp_teams(s.tf4) : 1;
     s.threads = s.warp ? 32 * s.teams : tile_threads;
     s.smem = (size_t)s.teams * s.tf4 * sizeof(float4);
@@ -734,18 +755,30 @@ gs_status launch_render_bwd_pixels(const Plan* p, void* ws, const float* final_T
         cbuf<uint32_t>(p, ws, (p->tile_passes & 1) ? (int)B_IVAL_B : (int)GS_BUF_TILE_VALUES);
     const float4* rec = cbuf<float4>(p, ws, GS_BUF_PROJ);
     uint32_t* queue = buf<uint32_t>(p, ws, B_TILE_QUEUE) + 1;
-    auto kern = s.warp ? pick(ppt, k_render_bwd<1, true>, k_render_bwd<2, true>,
-                              k_render_bwd<4, true>, k_render_bwd<8, true>)
-                       : pick(ppt, k_render_bwd<1, false>, k_render_bwd<2, false>,
-                              k_render_bwd<4, false>, k_render_bwd<8, false>);
+    const bool abs_stats = p->cfg.density_stats != 0;
+    float* absgrad = abs_stats ? buf<float>(p, ws, GS_BUF_ABSGRAD) : nullptr;
+    auto kern =
+        abs_stats
+            ? (s.warp ? pick(ppt, k_render_bwd<1, true, true>, k_render_bwd<2, true, true>,
+                             k_render_bwd<4, true, true>, k_render_bwd<8, true, true>)
+                      : pick(ppt, k_render_bwd<1, false, true>, k_render_bwd<2, false, true>,
+                             k_render_bwd<4, false, true>, k_render_bwd<8, false, true>))
+            : (s.warp ? pick(ppt, k_render_bwd<1, true, false>, k_render_bwd<2, true, false>,
+                             k_render_bwd<4, true, false>, k_render_bwd<8, true, false>)
+                      : pick(ppt, k_render_bwd<1, false, false>, k_render_bwd<2, false, false>,
+                             k_render_bwd<4, false, false>, k_render_bwd<8, false, false>));
     const int blocks = persistent_blocks((const void*)kern, s.threads, s.smem, s.teams,
                                          p->total_tiles);
     if (blocks < 0) return GS_ERR_CUDA;
     if (cudaMemsetAsync(grad2d, 0, p->len[GS_BUF_GRAD2D], st) != cudaSuccess) return GS_ERR_CUDA;
     if (cudaMemsetAsync(queue, 0, sizeof(uint32_t), st) != cudaSuccess) return GS_ERR_CUDA;
+    if (abs_stats &&
+        cudaMemsetAsync(absgrad, 0, p->len[GS_BUF_ABSGRAD], st) != cudaSuccess)
+        return GS_ERR_CUDA;
     kern<<<blocks, s.threads, s.smem, st>>>(p->vt, ranges, order, vals, rec, batch, s.tf4,
                                             p->total_tiles, queue, p->cfg.bg[0], p->cfg.bg[1],
-                                            p->cfg.bg[2], final_T, last_idx, dL, grad2d);
+                                            p->cfg.bg[2], final_T, last_idx, dL, grad2d,
+                                            absgrad);
     return launch_status();
 }
 

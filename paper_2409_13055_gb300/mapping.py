@@ -74,9 +74,12 @@ class GaussianMap:
         self.load(params)
 
     # views into the packed buffers ------------------------------------------
-    def _views(self, buf):
+    def _views(self, buf, layout=None):
         n, c, K = self.n, self.capacity, self.K
         o = self.off
+        if layout is not None:  # (n, offsets) of a buffer laid out for another size
+            n, o = layout
+            c = n
         return dict(
             means=buf[o["means"]:o["means"] + 3 * n].view(n, 3),
             log_scales=buf[o["log_scales"]:o["log_scales"] + 3 * n].view(n, 3),
@@ -135,6 +138,41 @@ class GaussianMap:
             P[g][n0:].copy_(torch.as_tensor(np.asarray(params[g], np.float32)).reshape(P[g][n0:].shape))
         P["sh"][:, n0:].copy_(torch.as_tensor(np.asarray(params["sh"], np.float32)))
 
+    def densify(self, accum, denom, samples, extent=1.0, grad_threshold=0.0004,
+                percent_dense=0.01, min_opacity=0.005, split_shrink=1.6, stream=None):
+        """Adaptive density control (paper Sec. III-B; rules in gs.h): prune
+        low-opacity Gaussians, clone small and split large ones whose mean
+        statistic accum/denom reaches grad_threshold.  samples: device float
+        tensor [n][2][3] of standard normal draws for the split offsets.  One
+        host synchronisation reads the new size; the buffers are laid out
+        again for it (pointers change), moments of new Gaussians are zero and
+        the step counter is kept.  Returns (kept, cloned, split)."""
+        cfg = B.gs_densify_config(float(grad_threshold), float(percent_dense), float(min_opacity),
+                                  float(split_shrink), float(extent))
+        scratch = torch.empty(max(1, B.gs_densify_scratch_bytes(self.n)), dtype=torch.uint8,
+                              device=self.device)
+        counts = torch.zeros(4, dtype=torch.int32, device=self.device)
+        src = self.gs_map()
+        B.gs_densify_count(src, accum, denom, cfg, scratch, counts, stream)
+        kept, cloned, split, _ = (int(x) for x in counts.cpu().tolist())
+        n_out = kept + cloned + 2 * split
+        if n_out == 0:
+            raise ValueError("density control would remove every Gaussian")
+        off1, total1 = param_layout(n_out, self.degree)
+        lay = (n_out, off1)
+        bufs = [torch.zeros(total1, dtype=torch.float32, device=self.device) for _ in range(4)]
+        data1, m1, v1, grad1 = bufs
+        sm, sv = self.gs_map_moments()
+        B.gs_densify_apply(src, sm, sv, accum, denom, samples, cfg, scratch, n_out,
+                           self._struct(data1, lay), self._struct(m1, lay), self._struct(v1, lay),
+                           counts, stream)
+        if int(counts[3].item()) != 0:
+            raise RuntimeError("gs_densify_apply: output size mismatch")
+        self.data, self.m, self.v, self.grad = data1, m1, v1, grad1
+        self.n = self.capacity = n_out
+        self.off, self.total = off1, total1
+        return kept, cloned, split
+
     def to_numpy(self):
         P = self.params()
         out = {k: P[k].detach().cpu().numpy().copy() for k in P}
@@ -154,8 +192,8 @@ class GaussianMap:
                              G["quats"].data_ptr(), G["opacity_logits"].data_ptr(),
                              G["sh"].data_ptr())
 
-    def _struct(self, buf) -> B.gs_map_grad:
-        V = self._views(buf)
+    def _struct(self, buf, layout=None) -> B.gs_map_grad:
+        V = self._views(buf, layout)
         return B.gs_map_grad(V["means"].data_ptr(), V["log_scales"].data_ptr(),
                              V["quats"].data_ptr(), V["opacity_logits"].data_ptr(),
                              V["sh"].data_ptr())
@@ -206,13 +244,13 @@ class Rasterizer:
 
     def __init__(self, views, n_capacity, instance_capacity=None, tile=(16, 16), smem_batch=128,
                  near_z=0.2, bg=(0.0, 0.0, 0.0), pixels_per_thread=0, smem_batch_bwd=0,
-                 pixels_per_thread_bwd=0, device="cuda"):
+                 pixels_per_thread_bwd=0, density_stats=False, device="cuda"):
         self.views = list(views)
         self.device = torch.device(device)
         self.cfg = B.gs_config(int(tile[0]), int(tile[1]), int(smem_batch),
                                int(pixels_per_thread), int(smem_batch_bwd),
                                int(pixels_per_thread_bwd), float(near_z),
-                               (B.c_float * 3)(*[float(x) for x in bg]))
+                               (B.c_float * 3)(*[float(x) for x in bg]), int(bool(density_stats)))
         self.n_capacity = int(n_capacity)
         if instance_capacity is None:
             px = sum(v["width"] * v["height"] for v in self.views)
@@ -302,6 +340,11 @@ class Rasterizer:
                               beta2, eps, gmap.step, grads_acc=grads_acc, grads_out=grads_out,
                               stream=stream)
 
+    def densify_stats(self, n, accum, denom, stream=None):
+        """Adds the last backward's density-control statistic (plan built
+        with density_stats) to accum / denom."""
+        B.gs_densify_stats(self.plan, n, self.ws, accum, denom, stream)
+
     def counters(self, stream=None) -> B.gs_counters:
         return B.gs_read_counters(self.plan, self.ws, stream)
 
@@ -371,9 +414,13 @@ class MappingStep:
     batch of views, optionally captured as one CUDA graph."""
 
     def __init__(self, gmap: GaussianMap, rast: Rasterizer, targets: torch.Tensor, lam: float,
-                 lr=None, extent=1.0, fused=False, keep_grads=False, recompute=False):
+                 lr=None, extent=1.0, fused=False, keep_grads=False, recompute=False,
+                 stats=None):
         self.gmap, self.rast, self.targets, self.lam = gmap, rast, targets, float(lam)
         self.lr, self.extent, self.fused, self.keep_grads = lr, extent, fused, keep_grads
+        # stats = (accum, denom): the density-control statistic of every
+        # iteration is added to them (the rasteriser needs density_stats)
+        self.stats = stats
         # recompute: the checkpointed backward -- projection and binning are
         # run again (bit-identically) between the loss and the adjoint, as
         # when the forward's intermediates were not kept
@@ -401,6 +448,8 @@ class MappingStep:
         else:
             r.render_bwd(self._m, self._g, accumulate=False, stream=stream)
             self.gmap.adam_step(self.lr, self.extent, stream=stream)
+        if self.stats is not None:
+            r.densify_stats(self.gmap.n, self.stats[0], self.stats[1], stream)
 
     def capture(self, warmup=2):
         s = torch.cuda.Stream()

@@ -30,7 +30,8 @@ def test_exports_every_declared_function(lib):
 
 def test_struct_sizes_match_header():
     assert ctypes.sizeof(B.gs_view) == 80
-    assert ctypes.sizeof(B.gs_config) == 40
+    assert ctypes.sizeof(B.gs_config) == 44
+    assert ctypes.sizeof(B.gs_densify_config) == 32
     assert ctypes.sizeof(B.gs_counters) == 32
     assert ctypes.sizeof(B.gs_plan) == 8 * B.GS_PLAN_WORDS
 
@@ -105,6 +106,30 @@ def test_calls_reject_bad_arguments_without_launching(lib):
     assert lib.gs_adam_step(p, p, p, p, 5, 1, offs, lrs, 1.0, 0.999, 1e-15, p, None) == \
         B.GS_ERR_INVALID  # beta1 = 1
     assert B.gs_status_string(B.GS_ERR_CAPACITY).startswith("GS_ERR_CAPACITY")
+
+
+def test_density_control_rejects_bad_arguments_without_launching(lib):
+    p = ctypes.c_void_p(256)
+    plan = B.gs_plan_init(_cfg(), _views((64, 48, 3)), 10, 1000)  # no density_stats
+    assert lib.gs_densify_stats(ctypes.byref(plan), 10, p, p, p, None) == B.GS_ERR_INVALID
+    assert lib.gs_densify_scratch_bytes(0) == 0
+    assert lib.gs_densify_scratch_bytes(257) == 6 * 2 * 4 + 256
+    good = B.gs_densify_config(0.0004, 0.01, 0.005, 1.6, 1.0)
+    badcfg = B.gs_densify_config(0.0004, 0.01, 0.005, 0.0, 1.0)  # split_shrink 0
+    m = B.gs_map(p, p, p, p, p, 10, 3)
+    empty = B.gs_map(p, p, p, p, p, 0, 3)
+    assert lib.gs_densify_count(ctypes.byref(m), p, p, ctypes.byref(badcfg), p, p, None) == \
+        B.GS_ERR_INVALID
+    assert lib.gs_densify_count(ctypes.byref(empty), p, p, ctypes.byref(good), p, p, None) == \
+        B.GS_ERR_INVALID
+    g = B.gs_map_grad(p, p, p, p, p)
+    nullg = B.gs_map_grad(None, p, p, p, p)
+    assert lib.gs_densify_apply(ctypes.byref(m), ctypes.byref(g), ctypes.byref(g), p, p, p,
+                                ctypes.byref(good), p, 10, ctypes.byref(nullg), ctypes.byref(g),
+                                ctypes.byref(g), p, None) == B.GS_ERR_INVALID
+    assert lib.gs_densify_apply(ctypes.byref(m), ctypes.byref(g), ctypes.byref(g), p, p, p,
+                                ctypes.byref(good), p, -1, ctypes.byref(g), ctypes.byref(g),
+                                ctypes.byref(g), p, None) == B.GS_ERR_INVALID
 
 
 def test_param_layout_alignment():
