@@ -375,3 +375,30 @@ def densify_apply(params, moments, cat, samples, cfg=None):
             z = np.zeros((n_new,) + m.shape[1:])
             new_moments[k] = (np.concatenate([m[keep], z]), np.concatenate([v[keep], z]))
     return out, new_moments
+
+
+# --------------------------------------------------------------------------
+# Gaussian-pyramid targets (paper Sec. III-B: the keyframe image is smoothed
+# and down-sampled repeatedly; training starts on the coarsest level and moves
+# to finer ones).  Readings: the 5-tap binomial kernel [1, 4, 6, 4, 1] / 16
+# applied along each axis, borders mirrored without repeating the edge pixel
+# (d c b | a b c d | c b a), then every second pixel kept starting at 0, so
+# level L+1 has ceil(W/2) x ceil(H/2) pixels and its pixel i sits on pixel
+# 2i of level L (intrinsics fx/2, fy/2, cx/2, cy/2).
+# --------------------------------------------------------------------------
+PYR_KERNEL = np.array([1.0, 4.0, 6.0, 4.0, 1.0]) / 16.0
+
+
+def pyr_down(img):
+    """One pyramid level of a [C][H][W] image (float64)."""
+    from scipy.ndimage import convolve1d
+    a = np.asarray(img, np.float64)
+    a = convolve1d(a, PYR_KERNEL, axis=-1, mode="mirror")
+    a = convolve1d(a, PYR_KERNEL, axis=-2, mode="mirror")
+    return a[..., ::2, ::2]
+
+
+def pyr_view(view):
+    """The camera of the next pyramid level."""
+    return dict(view, width=(view["width"] + 1) // 2, height=(view["height"] + 1) // 2,
+                fx=view["fx"] / 2, fy=view["fy"] / 2, cx=view["cx"] / 2, cy=view["cy"] / 2)
