@@ -381,6 +381,50 @@ def run_density(args, ws, p, view, target):
                             densify="count + one host read + apply, host clock"))
 
 
+def run_pyramid(args, ws, p, view, target):
+    """Gaussian-pyramid training (paper Sec. III-B) on the headline workload:
+    the time to build a 3-level target pyramid, and the mapping iteration at
+    each level (whole-iteration graph, CUDA events)."""
+    import torch
+    from paper_2409_13055_gb300 import mapping, pyramid
+
+    stream = torch.cuda.current_stream()
+    img = target.reshape(3, view["height"], view["width"])
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    for _ in range(3):
+        pyramid.pyramid(img, 3)
+    e0.record(stream)
+    for _ in range(10):
+        levels = pyramid.pyramid(img, 3)
+    e1.record(stream)
+    torch.cuda.synchronize()
+    build_ms = e0.elapsed_time(e1) / 10
+    out = dict(pyramid_build_ms=build_ms, levels=[])
+    K = max(10, min(args.steps, 100))
+    for level in range(3):
+        v = pyramid.level_view(view, level)
+        gm = mapping.GaussianMap(p)
+        rast = mapping.fit_instance_capacity([v], gm, headroom=1.5, tile=(args.tile_w, args.tile_h),
+                                             smem_batch=args.batch, pixels_per_thread=args.ppt,
+                                             smem_batch_bwd=args.batch_bwd,
+                                             pixels_per_thread_bwd=args.ppt_bwd)
+        step = mapping.MappingStep(gm, rast, levels[level].reshape(-1).contiguous(), 0.2)
+        step.capture(warmup=max(3, args.warmup))
+        barrier(ws)
+        torch.cuda.synchronize()
+        e0.record(stream)
+        for _ in range(K):
+            step()
+        e1.record(stream)
+        torch.cuda.synchronize()
+        ms = reduce_max(e0.elapsed_time(e1), ws) / K
+        out["levels"].append(dict(level=level, width=v["width"], height=v["height"],
+                                  iters_per_s=ws * 1e3 / ms, ms_per_iter=ms))
+        del step, rast, gm
+        torch.cuda.empty_cache()
+    return out
+
+
 def run_gpu(args, ws, rank, local):
     import torch
     from paper_2409_13055_gb300 import binding as B
@@ -580,6 +624,9 @@ def run_gpu(args, ws, rank, local):
     if not args.no_density:
         torch.cuda.empty_cache()
         out["density_control"] = run_density(args, ws, p, view, target)
+    if not args.no_pyramid:
+        torch.cuda.empty_cache()
+        out["pyramid"] = run_pyramid(args, ws, p, view, target)
 
     if rank == 0 and not args.no_cpu_baseline:
         from paper_2409_13055_gb300 import scenes as sc
@@ -616,6 +663,8 @@ def main():
                          "1M: 0.44 vs 0.56 ms), or inside the projection adjoint")
     ap.add_argument("--streaming-kfs", type=int, default=100,
                     help="keyframes of the streaming measurement (0 skips it)")
+    ap.add_argument("--no-pyramid", action="store_true",
+                    help="skip the Gaussian-pyramid level measurement")
     ap.add_argument("--no-density", action="store_true",
                     help="skip the adaptive density control measurement")
     ap.add_argument("--no-cpu-baseline", action="store_true")

@@ -360,6 +360,16 @@ gs_status gs_densify_apply(const gs_map *map, const gs_map_grad *src_m, const gs
                            gs_map_grad *dst, gs_map_grad *dst_m, gs_map_grad *dst_v,
                            int32_t *counts_dev, void *stream);
 
+/* One level of the Gaussian pyramid of a target (paper Sec. III-B: training
+ * starts on smoothed, down-sampled keyframe images and moves to finer
+ * levels).  src: [channels][height][width]; dst: [channels][ceil(height/2)]
+ * [ceil(width/2)].  Reading: the 5-tap binomial [1, 4, 6, 4, 1]/16 along each
+ * axis, mirrored borders without repeating the edge pixel, every second
+ * pixel kept from 0; a view of the next level has half its focal lengths
+ * and principal point. */
+gs_status gs_pyr_down(const float *src, int32_t channels, int32_t height, int32_t width,
+                      float *dst, void *stream);
+
 /* Copies the device counters of the workspace to *out (host) and waits for
  * `stream`. */
 gs_status gs_read_counters(const gs_plan *plan, const void *ws, gs_counters *out, void *stream);

@@ -103,6 +103,7 @@ _SIGNATURES = {
                                    c_void_p, c_void_p, _P(gs_densify_config), c_void_p, c_int32,
                                    _P(gs_map_grad), _P(gs_map_grad), _P(gs_map_grad), c_void_p,
                                    c_void_p]),
+    "gs_pyr_down": (c_int32, [c_void_p, c_int32, c_int32, c_int32, c_void_p, c_void_p]),
     "gs_read_counters": (c_int32, [_P(gs_plan), c_void_p, _P(gs_counters), c_void_p]),
     "gs_status_string": (ctypes.c_char_p, [c_int32]),
 }
@@ -288,6 +289,11 @@ def gs_densify_apply(gmap, src_m, src_v, accum, denom, samples, cfg, scratch, n_
                                  _ptr(scratch), int(n_out), ctypes.byref(dst), ctypes.byref(dst_m),
                                  ctypes.byref(dst_v), _ptr(counts_dev), _stream(stream)),
           "gs_densify_apply")
+
+
+def gs_pyr_down(src, channels, height, width, dst, stream=None):
+    check(lib().gs_pyr_down(_ptr(src), int(channels), int(height), int(width), _ptr(dst),
+                            _stream(stream)), "gs_pyr_down")
 
 
 def gs_read_counters(plan, ws, stream=None) -> gs_counters:

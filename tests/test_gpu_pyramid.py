@@ -1,0 +1,70 @@
+"""GPU parity of the Gaussian-pyramid targets (paper Sec. III-B: progressive
+training from smoothed, down-sampled keyframe images to full resolution).
+
+Bars: a pyramid level within 1e-6 max-abs of the FP64 oracle's (values in
+[0, 1]; one FP32 rounding per tap); a mapping iteration at a coarse level
+matching the oracle's iteration on the oracle's own pyramid target and
+level camera (loss 1e-5 relative, gradients 1e-3 relative L2 per group with
+the FP32 floor of the whole-iteration bar).
+"""
+import numpy as np
+import pytest
+import torch
+
+import oracle
+from paper_2409_13055_gb300 import binding as B
+from paper_2409_13055_gb300 import pyramid, scenes
+
+pytestmark = pytest.mark.gpu
+
+GROUPS = ("means", "log_scales", "quats", "opacity_logits", "sh")
+
+
+@pytest.fixture(scope="module", autouse=True)
+def _lib():
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    from paper_2409_13055_gb300 import build
+    build.build()
+    B.lib()
+
+
+@pytest.mark.parametrize("shape", [(3, 480, 752), (1, 121, 187), (3, 2, 3), (1, 1, 1),
+                                   (3, 7, 1)])
+def test_pyramid_levels_match_oracle(shape):
+    rng = np.random.default_rng(sum(shape))
+    img = rng.uniform(size=shape).astype(np.float32)
+    got = pyramid.pyramid(torch.tensor(img, device="cuda"), 4)
+    want = img.astype(np.float64)
+    for level in range(1, 4):
+        want = oracle.pyr_down(want)
+        g = got[level].cpu().numpy()
+        assert g.shape == want.shape
+        assert np.max(np.abs(g - want)) <= 1e-6, (level, np.max(np.abs(g - want)))
+
+
+def test_coarse_to_fine_iterations_match_oracle():
+    from paper_2409_13055_gb300.streaming import StreamingMapper
+    kfs = list(scenes.streaming_keyframes(2, 400, width=188, height=120, f=115.0))
+    mapper = StreamingMapper(window=2, iters=2, lam=0.2, capacity=1024, pyramid_levels=2)
+    assert [pyramid.level_for(i, 2, 2) for i in range(2)] == [1, 0]
+    window = []
+    for view, tgt, new in kfs:
+        mapper.insert_keyframe(view, tgt, new)
+        window = (window + [(view, tgt)])[-2:]
+        for level in (1, 0):
+            before = mapper.gmap.to_numpy()
+            mapper.iterate(1)
+            torch.cuda.synchronize()
+            assert mapper.last_step is mapper.steps[level]
+            loss = mapper.last_step.rast.loss.item()
+            grads = {g: t.cpu().numpy() for g, t in mapper.gmap.grads().items()}
+            views = [w[0] if level == 0 else oracle.pyr_view(w[0]) for w in window]
+            targets = [w[1].astype(np.float64) if level == 0 else oracle.pyr_down(w[1])
+                       for w in window]
+            L, og, _ = oracle.iteration(before, views, targets, 0.2)
+            assert abs(loss - L) <= 1e-5 * abs(L), (level, loss, L)
+            floor = 1e-6 * np.sqrt(sum(np.sum(np.square(og[g])) for g in GROUPS))
+            for g in GROUPS:
+                err = np.linalg.norm(grads[g].astype(np.float64) - og[g])
+                assert err <= 1e-3 * np.linalg.norm(og[g]) + floor, (level, g, err)
