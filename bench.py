@@ -193,6 +193,20 @@ def make_workload(name=WORKLOAD):
     return p, view
 
 
+def z_ordered(p):
+    """The same map stored along a Z-order curve of the means (the GPU path's
+    storage order: a view's visible Gaussians form long runs, so warps of the
+    per-Gaussian kernels cull together).  The set of Gaussians is unchanged."""
+    import torch
+    from paper_2409_13055_gb300 import mapping
+    perm = mapping.morton_order(torch.as_tensor(p["means"], dtype=torch.float64)).numpy()
+    out = {k: (v[perm] if isinstance(v, np.ndarray) and k != "sh" else v) for k, v in p.items()}
+    out["sh"] = np.ascontiguousarray(p["sh"][:, perm])
+    for k in ("means", "log_scales", "quats", "opacity_logits"):
+        out[k] = np.ascontiguousarray(out[k])
+    return out
+
+
 def run_reference(args, ws, rank):
     if rank != 0:
         return
@@ -236,6 +250,8 @@ def run_batched(args, ws):
     from paper_2409_13055_gb300 import mapping, scenes
 
     p = scenes.room_scene(500_000, seed=scenes.SEED_BASE + 4)
+    if args.map_order == "zorder":
+        p = z_ordered(p)
     views = scenes.views_mixed16()
     lam = 0.2
     cfg = dict(tile=(args.tile_w, args.tile_h), smem_batch=args.batch,
@@ -439,6 +455,8 @@ def run_gpu(args, ws, rank, local):
     peaks = load_peaks()
 
     p, view = make_workload(args.workload)
+    if args.map_order == "zorder":
+        p = z_ordered(p)
     lam = 0.2
     # target: render of a perturbed copy of the map (set-up, untimed)
     pert = scenes.perturbed(p, scenes.SEED_BASE + 23)
@@ -475,6 +493,11 @@ def run_gpu(args, ws, rank, local):
     ]
     if args.adam == "fused":
         stages.append(("project_bwd_adam", lambda: rast.project_bwd_adam(gm)))
+    elif args.adam == "sparse":
+        vis = torch.zeros(gm.n, dtype=torch.uint8, device="cuda")
+        stages += [("project_bwd", lambda: rast.project_bwd(m, g)),
+                   ("adam_sparse", lambda: (rast.visibility(gm.n, vis),
+                                            gm.adam_step(visible=vis)))]
     else:
         stages += [("project_bwd", lambda: rast.project_bwd(m, g)),
                    ("adam", lambda: gm.adam_step())]
@@ -591,7 +614,7 @@ def run_gpu(args, ws, rank, local):
     # render_bwd 1, then project_bwd 2 + adam 2, or step counter + the two
     # fused adjoint kernels
     launches_per_step = 1 + (18 + 3 * tile_passes(rast.total_tiles)) + 1 + 2 + 1 + \
-        (3 if args.adam == "fused" else 4)
+        {"fused": 3, "separate": 4, "sparse": 5}[args.adam]
 
     out = dict(metric=METRIC, value=value, unit="iters/s", n_gpus=ws, steps=K, warmup=args.warmup,
                ms_per_step=ms_step, higher_is_better=True, scaling="weak", vs_baseline=None,
@@ -602,7 +625,7 @@ def run_gpu(args, ws, rank, local):
                            smem_batch=args.batch, pixels_per_thread=args.ppt,
                            smem_batch_bwd=args.batch_bwd, pixels_per_thread_bwd=args.ppt_bwd,
                            autotuned=tuned is not None, cuda_graph="one graph per stage",
-                           adam=args.adam,
+                           adam=args.adam, map_order=args.map_order,
                            l2="working set ~1.2 GB > 129 MB L2, no flush",
                            instances=instances, pairs_bwd=pairs_bwd),
                stages_ms=stage_ms, roofline=roof,
@@ -658,9 +681,12 @@ def main():
     ap.add_argument("--ppt-bwd", type=int, default=None, help="backward pixels per thread")
     ap.add_argument("--no-batched", action="store_true",
                     help="skip the 16-keyframe batched vs per-view measurement")
-    ap.add_argument("--adam", default="separate", choices=["fused", "separate"],
+    ap.add_argument("--adam", default="separate", choices=["fused", "separate", "sparse"],
                     help="Adam as its own pass over the gradient buffer (measured faster at "
-                         "1M: 0.44 vs 0.56 ms), or inside the projection adjoint")
+                         "1M: 0.44 vs 0.56 ms), inside the projection adjoint, or the "
+                         "visibility-masked variant (changes the optimiser: not the headline)")
+    ap.add_argument("--map-order", default="zorder", choices=["zorder", "generated"],
+                    help="storage order of the map's Gaussians (the same set either way)")
     ap.add_argument("--streaming-kfs", type=int, default=100,
                     help="keyframes of the streaming measurement (0 skips it)")
     ap.add_argument("--no-pyramid", action="store_true",

@@ -301,6 +301,30 @@ gs_status gs_adam_step(float *params, const float *grads, float *m, float *v, in
                        const float *group_lr_host, float beta1, float beta2, float eps,
                        int32_t *step_dev, void *stream);
 
+/* Visibility of the last gs_project: vis[i] = 1 (device uint8 [n]) if
+ * Gaussian i touches a tile in any view of the plan, else 0. */
+gs_status gs_visibility(const gs_plan *plan, int32_t n, const void *ws, uint8_t *vis,
+                        void *stream);
+
+/* A9 variant, visibility-masked ("sparse") Adam -- no counterpart in the
+ * paper, whose optimiser is the dense 3DGS Adam: the floats of Gaussians
+ * with vis[i] == 0 are neither read nor written (their moments do not decay
+ * and their parameters do not move); visible ones get exactly the dense
+ * update with the shared step t.  Float j of group k (offsets as in
+ * gs_adam_step) belongs to Gaussian ((j - off_k) mod (stride_k n_gauss)) /
+ * stride_k, with group_stride_host[k] the floats per Gaussian per plane (3
+ * for means, log-scales and each SH plane, 4 for quaternions, 1 for
+ * opacities; only 1, 3 and 4 are accepted, GS_ERR_UNSUPPORTED otherwise); a
+ * group holds whole planes of stride_k n_gauss floats (at most 64 planes in
+ * all), and floats after its last whole plane (padding) are skipped.  The
+ * four buffers must be 16-byte aligned (GS_ERR_INVALID otherwise). */
+gs_status gs_adam_step_sparse(float *params, const float *grads, float *m, float *v,
+                              int64_t n_floats, int32_t n_groups,
+                              const int64_t *group_offsets_host, const float *group_lr_host,
+                              const int32_t *group_stride_host, int32_t n_gauss,
+                              const uint8_t *vis, float beta1, float beta2, float eps,
+                              int32_t *step_dev, void *stream);
+
 /* ---------------------------------------------------------------------------
  * Adaptive density control (paper Sec. III-B): periodically, Gaussians with a
  * high homodirectional view-space position gradient (the AbsGS criterion) are

@@ -242,6 +242,17 @@ def adam(p, g, m, v, lr, step, b1=0.9, b2=0.999, eps=1e-15):
                      _f(b2), _f(eps), _i(step))
 
 
+def adam_masked(p, g, m, v, lr, step, mask, b1=0.9, b2=0.999, eps=1e-15):
+    """The visibility-masked variant of the Adam step (no counterpart in the
+    paper, whose optimiser is dense): `adam` on the elements where mask is
+    true, the others left untouched (in place)."""
+    idx = np.flatnonzero(np.asarray(mask).reshape(-1))
+    pp, mm, vv = (np.ascontiguousarray(a.reshape(-1)[idx]) for a in (p, m, v))
+    adam(pp, np.asarray(g, np.float64).reshape(-1)[idx], mm, vv, lr, step, b1, b2, eps)
+    for a, b in ((p, pp), (m, mm), (v, vv)):
+        a.reshape(-1)[idx] = b
+
+
 # --------------------------------------------------------------------------
 # Composition: a whole view, a whole mapping iteration.
 # --------------------------------------------------------------------------

@@ -94,6 +94,10 @@ _SIGNATURES = {
     "gs_adam_step": (c_int32, [c_void_p, c_void_p, c_void_p, c_void_p, c_int64, c_int32,
                                _P(c_int64), _P(c_float), c_float, c_float, c_float, c_void_p,
                                c_void_p]),
+    "gs_visibility": (c_int32, [_P(gs_plan), c_int32, c_void_p, c_void_p, c_void_p]),
+    "gs_adam_step_sparse": (c_int32, [c_void_p, c_void_p, c_void_p, c_void_p, c_int64, c_int32,
+                                      _P(c_int64), _P(c_float), _P(c_int32), c_int32, c_void_p,
+                                      c_float, c_float, c_float, c_void_p, c_void_p]),
     "gs_densify_stats": (c_int32, [_P(gs_plan), c_int32, c_void_p, c_void_p, c_void_p,
                                    c_void_p]),
     "gs_densify_scratch_bytes": (c_size_t, [c_int32]),
@@ -265,6 +269,23 @@ def gs_adam_step(params, grads, m, v, group_offsets, group_lr, beta1, beta2, eps
     check(lib().gs_adam_step(_ptr(params), _ptr(grads), _ptr(m), _ptr(v), int(params.numel()), ng,
                              offs, lrs, float(beta1), float(beta2), float(eps), _ptr(step_dev),
                              _stream(stream)), "gs_adam_step")
+
+
+def gs_visibility(plan, n, ws, vis, stream=None):
+    check(lib().gs_visibility(ctypes.byref(plan), int(n), _ptr(ws), _ptr(vis), _stream(stream)),
+          "gs_visibility")
+
+
+def gs_adam_step_sparse(params, grads, m, v, group_offsets, group_lr, group_strides, n_gauss, vis,
+                        beta1, beta2, eps, step_dev, stream=None):
+    ng = len(group_lr)
+    offs = (c_int64 * (ng + 1))(*[int(x) for x in group_offsets])
+    lrs = (c_float * ng)(*[float(x) for x in group_lr])
+    strides = (c_int32 * ng)(*[int(x) for x in group_strides])
+    check(lib().gs_adam_step_sparse(_ptr(params), _ptr(grads), _ptr(m), _ptr(v),
+                                    int(params.numel()), ng, offs, lrs, strides, int(n_gauss),
+                                    _ptr(vis), float(beta1), float(beta2), float(eps),
+                                    _ptr(step_dev), _stream(stream)), "gs_adam_step_sparse")
 
 
 def gs_densify_stats(plan, n, ws, accum, denom, stream=None):

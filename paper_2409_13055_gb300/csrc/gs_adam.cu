@@ -86,7 +86,159 @@ k_adam(float* __restrict__ params, const float* __restrict__ grads, float* __res
     }
 }
 
+// Visibility-masked variant: float j of a plane of s floats per Gaussian
+// (means, log-scales and each SH plane: 3; quaternions: 4; opacities: 1)
+// belongs to Gaussian j / s; floats of an invisible Gaussian are neither read
+// nor written.  Grid: blockIdx.y = plane (planes listed on the host, each a
+// contiguous run of s * n floats), each thread four consecutive floats of
+// its plane, the owners found with divisions by the constants 1, 3 or 4.
+// Memory traffic falls only where visible Gaussians are contiguous in index:
+// a 32-byte sector is read whenever one of its floats is visible.
+constexpr int kMaxPlanes = 64;
+struct Planes {
+    uint32_t start[kMaxPlanes];  // first float of the plane in the buffer
+    uint8_t stride[kMaxPlanes];  // 1, 3 or 4 floats per Gaussian
+    float lr[kMaxPlanes];
+    int count;
+};
+
+template <int S>
+__device__ __forceinline__ void sparse_scalar(float* __restrict__ params,
+                                              const float* __restrict__ grads,
+                                              float* __restrict__ m, float* __restrict__ v,
+                                              uint32_t base, uint32_t j,
+                                              const uint8_t* __restrict__ vis, float lr, float b1,
+                                              float b2, float eps, float ibc1, float ibc2) {
+    if (!vis[j / S]) return;
+    const uint32_t i = base + j;
+    float p = params[i], mm = m[i], vv = v[i];
+    adam1(p, grads[i], mm, vv, lr, b1, b2, eps, ibc1, ibc2);
+    params[i] = p;
+    m[i] = mm;
+    v[i] = vv;
+}
+
+// Aligned body of a plane in float4s: a float4 none of whose floats is
+// visible is skipped without touching memory; otherwise the four floats are
+// loaded as one vector and the visible ones updated (the others written back
+// unchanged).
+template <int S>
+__device__ __forceinline__ void sparse_body(float* __restrict__ params,
+                                            const float* __restrict__ grads,
+                                            float* __restrict__ m, float* __restrict__ v,
+                                            uint32_t base, uint32_t head, uint32_t n4,
+                                            const uint8_t* __restrict__ vis, float lr, float b1,
+                                            float b2, float eps, float ibc1, float ibc2) {
+    for (uint32_t f = blockIdx.x * blockDim.x + threadIdx.x; f < n4;
+         f += gridDim.x * blockDim.x) {
+        const uint32_t j = head + 4u * f;
+        const bool o0 = vis[j / S], o1 = vis[(j + 1) / S], o2 = vis[(j + 2) / S],
+                   o3 = vis[(j + 3) / S];
+        if (!(o0 | o1 | o2 | o3)) continue;
+        const uint32_t q = (base + j) >> 2;
+        float4 p = reinterpret_cast<float4*>(params)[q];
+        float4 mm = reinterpret_cast<float4*>(m)[q];
+        float4 vv = reinterpret_cast<float4*>(v)[q];
+        const float4 g = __ldcs(reinterpret_cast<const float4*>(grads) + q);
+        if (o0) adam1(p.x, g.x, mm.x, vv.x, lr, b1, b2, eps, ibc1, ibc2);
+        if (o1) adam1(p.y, g.y, mm.y, vv.y, lr, b1, b2, eps, ibc1, ibc2);
+        if (o2) adam1(p.z, g.z, mm.z, vv.z, lr, b1, b2, eps, ibc1, ibc2);
+        if (o3) adam1(p.w, g.w, mm.w, vv.w, lr, b1, b2, eps, ibc1, ibc2);
+        reinterpret_cast<float4*>(params)[q] = p;
+        reinterpret_cast<float4*>(m)[q] = mm;
+        reinterpret_cast<float4*>(v)[q] = vv;
+    }
+}
+
+// One plane per blockIdx.y: an unaligned head (< 4 floats up to the first
+// 16-byte boundary of the buffer), the float4 body, a tail (< 4 floats).
+// The buffers' base addresses are 16-byte aligned (checked on the host).
+template <int S>
+__device__ __forceinline__ void sparse_plane(float* params, const float* grads, float* m,
+                                             float* v, uint32_t base, uint32_t len,
+                                             const uint8_t* vis, float lr, float b1, float b2,
+                                             float eps, float ibc1, float ibc2) {
+    uint32_t head = (4u - (base & 3u)) & 3u;
+    if (head > len) head = len;
+    const uint32_t n4 = (len - head) >> 2, body_end = head + 4u * n4;
+    if (blockIdx.x == 0 && threadIdx.x < 8) {
+        const uint32_t t = threadIdx.x;
+        const uint32_t j = t < 4 ? t : body_end + (t - 4);
+        if ((t < 4 && j < head) || (t >= 4 && j < len))
+            sparse_scalar<S>(params, grads, m, v, base, j, vis, lr, b1, b2, eps, ibc1, ibc2);
+    }
+    sparse_body<S>(params, grads, m, v, base, head, n4, vis, lr, b1, b2, eps, ibc1, ibc2);
+}
+
+__global__ void __launch_bounds__(kAdamThreads)
+k_adam_sparse(float* __restrict__ params, const float* __restrict__ grads, float* __restrict__ m,
+              float* __restrict__ v, Planes planes, uint32_t n_gauss,
+              const uint8_t* __restrict__ vis, float b1, float b2, float eps,
+              const int32_t* __restrict__ step) {
+    __shared__ float s_bc[2];
+    if (threadIdx.x == 0) adam_bias(b1, b2, *step, s_bc[0], s_bc[1]);
+    __syncthreads();
+    const int pl = blockIdx.y;
+    const uint32_t S = planes.stride[pl], len = S * n_gauss, base = planes.start[pl];
+    const float lr = planes.lr[pl];
+    if (S == 3)
+        sparse_plane<3>(params, grads, m, v, base, len, vis, lr, b1, b2, eps, s_bc[0], s_bc[1]);
+    else if (S == 4)
+        sparse_plane<4>(params, grads, m, v, base, len, vis, lr, b1, b2, eps, s_bc[0], s_bc[1]);
+    else
+        sparse_plane<1>(params, grads, m, v, base, len, vis, lr, b1, b2, eps, s_bc[0], s_bc[1]);
+}
+
+__global__ void k_visibility(int n, int n_views, const uint32_t* __restrict__ touched,
+                             uint8_t* __restrict__ vis) {
+    const int g = blockIdx.x * blockDim.x + threadIdx.x;
+    if (g >= n) return;
+    uint8_t any = 0;
+    for (int v = 0; v < n_views; ++v) any |= touched[(size_t)v * n + g] != 0u;
+    vis[g] = any;
+}
+
 }  // namespace
+
+gs_status launch_visibility(int n, int n_views, const uint32_t* touched, uint8_t* vis,
+                            cudaStream_t st) {
+    k_visibility<<<(n + 255) / 256, 256, 0, st>>>(n, n_views, touched, vis);
+    return launch_status();
+}
+
+gs_status launch_adam_sparse(float* params, const float* grads, float* m, float* v, int64_t n,
+                             int32_t n_groups, const int64_t* offs, const float* lrs,
+                             const int32_t* strides, int32_t n_gauss, const uint8_t* vis,
+                             float b1, float b2, float eps, int32_t* step_dev, cudaStream_t st) {
+    if (n >= (int64_t(1) << 31)) return GS_ERR_UNSUPPORTED;
+    Planes pl{};
+    for (int k = 0; k < n_groups; ++k) {
+        const int s = strides[k];
+        if (s != 1 && s != 3 && s != 4) return GS_ERR_UNSUPPORTED;
+        const int64_t plane = (int64_t)s * n_gauss;
+        for (int64_t o = offs[k]; o + plane <= offs[k + 1]; o += plane) {
+            if (pl.count == kMaxPlanes) return GS_ERR_UNSUPPORTED;
+            pl.start[pl.count] = (uint32_t)o;
+            pl.stride[pl.count] = (uint8_t)s;
+            pl.lr[pl.count] = lrs[k];
+            ++pl.count;
+        }
+    }
+    if (pl.count == 0) return GS_ERR_INVALID;
+    if (((reinterpret_cast<uintptr_t>(params) | reinterpret_cast<uintptr_t>(grads) |
+          reinterpret_cast<uintptr_t>(m) | reinterpret_cast<uintptr_t>(v)) & 15) != 0)
+        return GS_ERR_INVALID;
+    // a float4 per thread; enough CTAs along x to cover the largest plane
+    // (4 n_gauss floats) with a few loop trips
+    int bx = (int)((4LL * n_gauss + 4LL * kAdamThreads - 1) / (4LL * kAdamThreads));
+    if (bx > 152 * 4) bx = 152 * 4;
+    if (bx < 1) bx = 1;
+    k_step_inc<<<1, 1, 0, st>>>(step_dev);
+    k_adam_sparse<<<dim3(bx, pl.count), kAdamThreads, 0, st>>>(params, grads, m, v, pl,
+                                                               (uint32_t)n_gauss, vis, b1, b2,
+                                                               eps, step_dev);
+    return launch_status();
+}
 
 gs_status launch_step_inc(int32_t* step_dev, cudaStream_t st) {
     k_step_inc<<<1, 1, 0, st>>>(step_dev);

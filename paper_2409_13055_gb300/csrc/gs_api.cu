@@ -288,6 +288,39 @@ extern "C" gs_status gs_adam_step(float* params, const float* grads, float* m, f
                        group_lr_host, beta1, beta2, eps, step_dev, S(stream));
 }
 
+extern "C" gs_status gs_visibility(const gs_plan* plan, int32_t n, const void* ws,
+                                   uint8_t* vis, void* stream) {
+    if (!plan_ok(plan) || !ws || !vis || n < 1 || n > P(plan)->n_capacity) return GS_ERR_INVALID;
+    return launch_visibility(n, P(plan)->vt.n_views, cbuf<uint32_t>(P(plan), ws, GS_BUF_TOUCHED),
+                             vis, S(stream));
+}
+
+extern "C" gs_status gs_adam_step_sparse(float* params, const float* grads, float* m, float* v,
+                                         int64_t n_floats, int32_t n_groups,
+                                         const int64_t* group_offsets_host,
+                                         const float* group_lr_host,
+                                         const int32_t* group_stride_host, int32_t n_gauss,
+                                         const uint8_t* vis, float beta1, float beta2, float eps,
+                                         int32_t* step_dev, void* stream) {
+    if (!params || !grads || !m || !v || !step_dev || !group_offsets_host || !group_lr_host ||
+        !group_stride_host || !vis || n_gauss < 1)
+        return GS_ERR_INVALID;
+    if (n_floats < 1 || n_groups < 1 || n_groups > GS_MAX_GROUPS) return GS_ERR_INVALID;
+    if (group_offsets_host[0] != 0 || group_offsets_host[n_groups] != n_floats)
+        return GS_ERR_INVALID;
+    for (int g = 0; g < n_groups; ++g) {
+        if (group_offsets_host[g + 1] < group_offsets_host[g]) return GS_ERR_INVALID;
+        if (group_stride_host[g] < 1 ||
+            (int64_t)group_stride_host[g] * n_gauss >= (int64_t(1) << 31))
+            return GS_ERR_INVALID;
+    }
+    if (!(beta1 >= 0.0f && beta1 < 1.0f && beta2 >= 0.0f && beta2 < 1.0f && eps >= 0.0f))
+        return GS_ERR_INVALID;
+    return launch_adam_sparse(params, grads, m, v, n_floats, n_groups, group_offsets_host,
+                              group_lr_host, group_stride_host, n_gauss, vis, beta1, beta2, eps,
+                              step_dev, S(stream));
+}
+
 extern "C" gs_status gs_read_counters(const gs_plan* plan, const void* ws, gs_counters* out,
                                       void* stream) {
     if (!plan_ok(plan) || !ws || !out) return GS_ERR_INVALID;

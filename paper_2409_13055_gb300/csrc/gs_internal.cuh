@@ -227,6 +227,12 @@ gs_status launch_project_bwd_adam(const Plan* p, const gs_map* map, const gs_vie
                                   const gs_map_grad* v, const gs_map_grad* grads_acc,
                                   const gs_map_grad* grads_out, const float* lr6, float b1,
                                   float b2, float eps, int32_t* step_dev, cudaStream_t st);
+gs_status launch_visibility(int n, int n_views, const uint32_t* touched, uint8_t* vis,
+                            cudaStream_t st);
+gs_status launch_adam_sparse(float* params, const float* grads, float* m, float* v, int64_t n,
+                             int32_t n_groups, const int64_t* offs, const float* lrs,
+                             const int32_t* strides, int32_t n_gauss, const uint8_t* vis,
+                             float b1, float b2, float eps, int32_t* step_dev, cudaStream_t st);
 gs_status launch_adam(float* params, const float* grads, float* m, float* v, int64_t n,
                       int32_t n_groups, const int64_t* offs, const float* lrs, float b1,
                       float b2, float eps, int32_t* step_dev, cudaStream_t st);

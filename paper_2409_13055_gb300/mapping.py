@@ -25,6 +25,7 @@ from . import binding as B
 
 ALIGN_FLOATS = 64  # 256-byte group alignment
 GROUPS = ("means", "log_scales", "quats", "opacity_logits", "sh_dc", "sh_rest")
+GROUP_STRIDES = (3, 3, 4, 1, 3, 3)  # floats per Gaussian per plane of each group
 
 # Default learning rates of 3DGS (the paper keeps the default optimiser
 # configuration, Sec. IV-A); the position rate is scaled by the scene extent.
@@ -173,6 +174,19 @@ class GaussianMap:
         self.off, self.total = off1, total1
         return kept, cloned, split
 
+    def permute(self, perm: torch.Tensor):
+        """Reorders the Gaussians (parameters, gradients and moments) so that
+        new index i holds old Gaussian perm[i]; renders are unchanged except
+        for the order of exactly tied depths."""
+        perm = perm.to(self.device, torch.int64)
+        for buf in (self.data, self.grad, self.m, self.v):
+            V = self._views(buf)
+            for k, t in V.items():
+                if k == "sh":
+                    t.copy_(t[:, perm].clone())
+                else:
+                    t.copy_(t[perm].clone())
+
     def to_numpy(self):
         P = self.params()
         out = {k: P[k].detach().cpu().numpy().copy() for k in P}
@@ -219,10 +233,32 @@ class GaussianMap:
         offsets[0] = 0
         return offsets, [lr[g] for g in GROUPS]
 
-    def adam_step(self, lr=None, extent=1.0, beta1=0.9, beta2=0.999, eps=1e-15, stream=None):
+    def adam_step(self, lr=None, extent=1.0, beta1=0.9, beta2=0.999, eps=1e-15, stream=None,
+                  visible=None):
+        """One Adam step; with visible (device uint8 [n], e.g. from
+        Rasterizer.visibility) the visibility-masked variant."""
         offs, rates = self.adam_groups(lr, extent)
-        B.gs_adam_step(self.data, self.grad, self.m, self.v, offs, rates, beta1, beta2, eps,
-                       self.step, stream)
+        if visible is None:
+            B.gs_adam_step(self.data, self.grad, self.m, self.v, offs, rates, beta1, beta2, eps,
+                           self.step, stream)
+        else:
+            B.gs_adam_step_sparse(self.data, self.grad, self.m, self.v, offs, rates,
+                                  GROUP_STRIDES, self.n, visible, beta1, beta2, eps, self.step,
+                                  stream)
+
+
+def morton_order(means: torch.Tensor, bits: int = 10) -> torch.Tensor:
+    """Permutation sorting 3D points along a Z-order curve over their
+    bounding box (bits per axis): neighbours in space become neighbours in
+    index, so a view's visible Gaussians form long runs in memory."""
+    lo = means.min(0).values
+    span = (means.max(0).values - lo).clamp_min(1e-12)
+    q = ((means - lo) / span * ((1 << bits) - 1)).round().to(torch.int64)
+    code = torch.zeros(means.shape[0], dtype=torch.int64, device=means.device)
+    for b in range(bits):
+        for a in range(3):
+            code |= ((q[:, a] >> b) & 1) << (3 * b + a)
+    return torch.argsort(code, stable=True)
 
 
 def make_view(v) -> B.gs_view:
@@ -340,6 +376,10 @@ class Rasterizer:
                               beta2, eps, gmap.step, grads_acc=grads_acc, grads_out=grads_out,
                               stream=stream)
 
+    def visibility(self, n, vis, stream=None):
+        """vis[i] = 1 where Gaussian i touched a tile in the last projection."""
+        B.gs_visibility(self.plan, n, self.ws, vis, stream)
+
     def densify_stats(self, n, accum, denom, stream=None):
         """Adds the last backward's density-control statistic (plan built
         with density_stats) to accum / denom."""
@@ -415,9 +455,13 @@ class MappingStep:
 
     def __init__(self, gmap: GaussianMap, rast: Rasterizer, targets: torch.Tensor, lam: float,
                  lr=None, extent=1.0, fused=False, keep_grads=False, recompute=False,
-                 stats=None):
+                 stats=None, sparse_adam=False):
         self.gmap, self.rast, self.targets, self.lam = gmap, rast, targets, float(lam)
         self.lr, self.extent, self.fused, self.keep_grads = lr, extent, fused, keep_grads
+        # sparse_adam: the visibility-masked Adam variant (Gaussians that touch
+        # no tile of any view in this iteration keep parameters and moments)
+        self.visible = (torch.zeros(gmap.n, dtype=torch.uint8, device=gmap.device)
+                        if sparse_adam else None)
         # stats = (accum, denom): the density-control statistic of every
         # iteration is added to them (the rasteriser needs density_stats)
         self.stats = stats
@@ -447,7 +491,9 @@ class MappingStep:
                                grads_out=self._g if self.keep_grads else None, stream=stream)
         else:
             r.render_bwd(self._m, self._g, accumulate=False, stream=stream)
-            self.gmap.adam_step(self.lr, self.extent, stream=stream)
+            if self.visible is not None:
+                r.visibility(self.gmap.n, self.visible, stream)
+            self.gmap.adam_step(self.lr, self.extent, stream=stream, visible=self.visible)
         if self.stats is not None:
             r.densify_stats(self.gmap.n, self.stats[0], self.stats[1], stream)
 

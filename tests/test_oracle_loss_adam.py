@@ -150,3 +150,22 @@ def test_iteration_gradient_central_differences(degree, lam, channels):
             assert abs(fd - gflat[j]) <= 1e-6 + 1e-5 * abs(fd), (key, j, fd, gflat[j])
             checked += 1
     assert checked > 0.9 * total
+
+
+def test_masked_adam_equals_dense_on_its_elements_and_leaves_the_rest():
+    """All-true mask = the dense step bit for bit; false entries unchanged."""
+    rng = np.random.default_rng(12)
+    n = 50
+    p0, g, m0, v0 = rng.normal(size=n), rng.normal(size=n), rng.normal(size=n), rng.uniform(size=n)
+    a = [x.copy() for x in (p0, m0, v0)]
+    b = [x.copy() for x in (p0, m0, v0)]
+    oracle.adam(a[0], g, a[1], a[2], 1e-3, 3)
+    oracle.adam_masked(b[0], g, b[1], b[2], 1e-3, 3, np.ones(n, bool))
+    for x, y in zip(a, b):
+        np.testing.assert_array_equal(x, y)
+    mask = rng.uniform(size=n) < 0.4
+    c = [x.copy() for x in (p0, m0, v0)]
+    oracle.adam_masked(c[0], g, c[1], c[2], 1e-3, 3, mask)
+    for x, y, z in zip(c, a, (p0, m0, v0)):
+        np.testing.assert_array_equal(x[mask], y[mask])
+        np.testing.assert_array_equal(x[~mask], z[~mask])
