@@ -481,7 +481,8 @@ def run_gpu(args, ws, rank, local):
     rast = mapping.fit_instance_capacity([view], gm, headroom=1.5, tile=(args.tile_w, args.tile_h),
                                          smem_batch=args.batch, pixels_per_thread=args.ppt,
                                          smem_batch_bwd=args.batch_bwd,
-                                         pixels_per_thread_bwd=args.ppt_bwd)
+                                         pixels_per_thread_bwd=args.ppt_bwd,
+                                         deterministic=args.deterministic)
     step = mapping.MappingStep(gm, rast, target, lam)
     m, g = gm.gs_map(), gm.gs_map_grad()
     stages = [
@@ -626,6 +627,7 @@ def run_gpu(args, ws, rank, local):
                            smem_batch_bwd=args.batch_bwd, pixels_per_thread_bwd=args.ppt_bwd,
                            autotuned=tuned is not None, cuda_graph="one graph per stage",
                            adam=args.adam, map_order=args.map_order,
+                           deterministic=bool(args.deterministic),
                            l2="working set ~1.2 GB > 129 MB L2, no flush",
                            instances=instances, pairs_bwd=pairs_bwd),
                stages_ms=stage_ms, roofline=roof,
@@ -685,6 +687,9 @@ def main():
                     help="Adam as its own pass over the gradient buffer (measured faster at "
                          "1M: 0.44 vs 0.56 ms), inside the projection adjoint, or the "
                          "visibility-masked variant (changes the optimiser: not the headline)")
+    ap.add_argument("--deterministic", action="store_true",
+                    help="bit-reproducible pixel adjoint (partial sums per (Gaussian, tile) "
+                         "reduced in a fixed order instead of float atomics)")
     ap.add_argument("--map-order", default="zorder", choices=["zorder", "generated"],
                     help="storage order of the map's Gaussians (the same set either way)")
     ap.add_argument("--streaming-kfs", type=int, default=100,

@@ -103,7 +103,13 @@ typedef struct {
  *   bg: background colour, entering the image as T_final * bg;
  *   density_stats: nonzero makes the pixel adjoint also sum, per (view,
  *     Gaussian), the per-pixel contributions to dL/dmean2d by absolute value
- *     (GS_BUF_ABSGRAD), the statistic of the density control below.
+ *     (GS_BUF_ABSGRAD), the statistic of the density control below;
+ *   deterministic: nonzero makes the pixel adjoint bit-reproducible (no
+ *     paper counterpart): each (Gaussian, tile) pair's partial sums are
+ *     stored in its own slot, indexed by the pair's emission position, and
+ *     summed per Gaussian in emission order by a second kernel, instead of
+ *     float atomics; needs one warp per tile in the backward (tile_w *
+ *     tile_h / pixels_per_thread_bwd == 32, GS_ERR_UNSUPPORTED otherwise).
  * The tile shape changes which pixels a Gaussian can reach (its 3-sigma
  * rect is counted in whole tiles), hence the image; the batch sizes and
  * pixels per thread change only the speed. */
@@ -113,6 +119,7 @@ typedef struct {
     float near_z;
     float bg[3];
     int32_t density_stats;
+    int32_t deterministic;
 } gs_config;
 
 /* A plan: the sizes, tile grids and workspace layout of one batch of views.

@@ -41,6 +41,7 @@ extern "C" gs_status gs_plan_init(gs_plan* plan, const gs_config* cfg, int32_t n
     const int batch_bwd = cfg->smem_batch_bwd ? cfg->smem_batch_bwd : cfg->smem_batch;
     const int ppt_bwd = cfg->pixels_per_thread_bwd ? cfg->pixels_per_thread_bwd : ppt;
     if (!batch_ok(batch_bwd) || !ppt_ok(ppt_bwd)) return GS_ERR_UNSUPPORTED;
+    if (cfg->deterministic && cfg->tile_w * cfg->tile_h / ppt_bwd != 32) return GS_ERR_UNSUPPORTED;
     if (!(cfg->near_z > 0.0f)) return GS_ERR_INVALID;
     if ((int64_t)n_views * n_capacity > (int64_t(1) << 31)) return GS_ERR_INVALID;
 
@@ -128,6 +129,8 @@ extern "C" gs_status gs_plan_init(gs_plan* plan, const gs_config* cfg, int32_t n
     len[B_TILE_ORDER] = (size_t)tiles * sizeof(uint32_t);
     len[B_GPARAM] = (size_t)n_capacity * 11 * sizeof(float);
     len[B_TILE_QUEUE] = 2 * sizeof(uint32_t);
+    len[B_GID_OF] = cfg->deterministic ? (size_t)instance_capacity * sizeof(uint32_t) : 0;
+    len[B_PARTIAL] = cfg->deterministic ? (size_t)instance_capacity * 11 * sizeof(float) : 0;
     size_t off = 0;
     for (int b = 0; b < B_TOTAL; ++b) {
         p->off[b] = off;

@@ -55,6 +55,10 @@ enum PrivBuf {
     B_GPARAM,      // [n] x 11: this pass's quaternion, mean, log-scale, opacity gradients
                    // held between the two fused adjoint kernels
     B_TILE_QUEUE,  // [2] u32 next-tile counters of the forward and backward render
+    B_GID_OF,      // [instance_capacity] u32 (view*n + index) of each emitted instance
+                   // (deterministic plans: the sort then carries emission positions)
+    B_PARTIAL,     // [instance_capacity] x 11 floats: per-(Gaussian, tile) partial sums
+                   // of the pixel adjoint (deterministic plans)
     B_TOTAL
 };
 
@@ -80,7 +84,8 @@ struct DevCounters {
     unsigned long long n_raw;      // before clamping
     float loss;
     uint32_t loss_blocks_done;     // last-block-done ticket of the loss reduction
-    uint32_t pad[2];
+    uint32_t vn;                   // (view, Gaussian) pairs of the last gs_bin_sort
+    uint32_t pad;
 };
 
 inline const Plan* P(const gs_plan* p) { return reinterpret_cast<const Plan*>(p); }

@@ -125,17 +125,21 @@ struct Team {
 };
 
 // Gather records [first, first+cnt) of the tile list into stage (3 float4
-// each) and their (view*n + index) ids into ids.
+// each) and the list values into ids: the (view*n + index) id, or, in a
+// deterministic plan (gid_of given), the emission position, whose id is
+// gid_of[position].
 template <class TM>
 __device__ __forceinline__ void issue_batch(const TM& tm, float4* stage, uint32_t* ids,
                                             const uint32_t* __restrict__ ivals,
+                                            const uint32_t* __restrict__ gid_of,
                                             const float4* __restrict__ rec, uint32_t first,
                                             int cnt) {
     for (int c = tm.tid; c < 3 * cnt; c += tm.size) {
         const int j = c / 3, part = c - 3 * j;
-        const uint32_t vg = __ldg(ivals + first + j);
+        const uint32_t x = __ldg(ivals + first + j);
+        const uint32_t vg = gid_of ? __ldg(gid_of + x) : x;
         cp_async16(stage + 3 * j + part, rec + (size_t)vg * 3 + part);
-        if (part == 0 && ids) ids[j] = vg;
+        if (part == 0 && ids) ids[j] = x;
     }
 }
 
@@ -257,6 +261,7 @@ __device__ __forceinline__ void blend_batch(int tid, const float4* stage, const 
 template <int CH, int PPT, class TM>
 __device__ void render_fwd_tile(const TM& tm, const ViewTable& vt, const TileCtx& tc,
                                 const uint32_t* __restrict__ ivals,
+                                const uint32_t* __restrict__ gid_of,
                                 const float4* __restrict__ rec, float4* smem, int batch,
                                 const float* bg, float* __restrict__ images,
                                 float* __restrict__ final_T, int32_t* __restrict__ last_idx) {
@@ -279,14 +284,14 @@ __device__ void render_fwd_tile(const TM& tm, const ViewTable& vt, const TileCtx
     const int total = (int)(tc.end - tc.begin);
     const int nb = (total + batch - 1) / batch;
     if (nb > 0) {
-        issue_batch(tm, smem, nullptr, ivals, rec, tc.begin, min(batch, total));
+        issue_batch(tm, smem, nullptr, ivals, gid_of, rec, tc.begin, min(batch, total));
         cp_async_commit();
     }
     for (int b = 0; b < nb; ++b) {
         const int cnt = min(batch, total - b * batch);
         float4* cur = smem + (b & 1) * 3 * batch;
         if (b + 1 < nb) {
-            issue_batch(tm, smem + ((b + 1) & 1) * 3 * batch, nullptr, ivals, rec,
+            issue_batch(tm, smem + ((b + 1) & 1) * 3 * batch, nullptr, ivals, gid_of, rec,
                         tc.begin + (b + 1) * batch, min(batch, total - (b + 1) * batch));
             cp_async_commit();
             cp_async_wait_one();
@@ -332,7 +337,8 @@ __device__ void render_fwd_tile(const TM& tm, const ViewTable& vt, const TileCtx
 template <int PPT, bool WARP>
 __global__ void k_render_fwd(ViewTable vt, const uint32_t* __restrict__ ranges,
                              const uint32_t* __restrict__ order,
-                             const uint32_t* __restrict__ ivals, const float4* __restrict__ rec,
+                             const uint32_t* __restrict__ ivals,
+                             const uint32_t* __restrict__ gid_of, const float4* __restrict__ rec,
                              int batch, int team_f4, int total_tiles, uint32_t* queue, float bg0,
                              float bg1, float bg2, float* __restrict__ images,
                              float* __restrict__ final_T, int32_t* __restrict__ last_idx) {
@@ -346,11 +352,11 @@ __global__ void k_render_fwd(ViewTable vt, const uint32_t* __restrict__ ranges,
         if (slot >= total_tiles) break;
         const TileCtx tc = tile_ctx(vt, ranges, (int)order[slot]);
         if (tc.channels == 3)
-            render_fwd_tile<3, PPT>(tm, vt, tc, ivals, rec, mine, batch, bg, images, final_T,
-                                    last_idx);
+            render_fwd_tile<3, PPT>(tm, vt, tc, ivals, gid_of, rec, mine, batch, bg, images,
+                                    final_T, last_idx);
         else
-            render_fwd_tile<1, PPT>(tm, vt, tc, ivals, rec, mine, batch, bg, images, final_T,
-                                    last_idx);
+            render_fwd_tile<1, PPT>(tm, vt, tc, ivals, gid_of, rec, mine, batch, bg, images,
+                                    final_T, last_idx);
     }
 }
 
@@ -424,11 +430,12 @@ __device__ __forceinline__ float rcp_approx(float x) {
 template <int CH, int PPT, class TM, bool ABS>
 __device__ void render_bwd_tile(const TM& tm, const ViewTable& vt, const TileCtx& tc,
                                 const uint32_t* __restrict__ ivals,
+                                const uint32_t* __restrict__ gid_of,
                                 const float4* __restrict__ rec, float4* smem, int* s_maxlast,
                                 int batch, const float* bg, const float* __restrict__ final_T,
                                 const int32_t* __restrict__ last_idx,
                                 const float* __restrict__ dL, float* __restrict__ grad2d,
-                                float* __restrict__ absgrad) {
+                                float* __restrict__ absgrad, float* __restrict__ partial) {
     // shared memory: stage[2][3*batch] float4 | ids[2][batch] | masks[2][batch] |
     //                acc[batch][KA] float (the batch's per-Gaussian sums: 9, and
     //                with ABS the two homodirectional sums in slots 9, 10)
@@ -480,7 +487,7 @@ __device__ void render_bwd_tile(const TM& tm, const ViewTable& vt, const TileCtx
     // batch k covers list positions [max(0, maxlast - (k+1) batch), maxlast - k batch)
     if (nb > 0) {
         const int lo = max(0, maxlast - batch);
-        issue_batch(tm, smem, ids0, ivals, rec, tc.begin + lo, maxlast - lo);
+        issue_batch(tm, smem, ids0, ivals, gid_of, rec, tc.begin + lo, maxlast - lo);
         cp_async_commit();
     }
     for (int kb = 0; kb < nb; ++kb) {
@@ -492,7 +499,7 @@ __device__ void render_bwd_tile(const TM& tm, const ViewTable& vt, const TileCtx
         if (kb + 1 < nb) {
             const int hi2 = lo, lo2 = max(0, hi2 - batch);
             issue_batch(tm, smem + ((kb + 1) & 1) * 3 * batch, ids0 + ((kb + 1) & 1) * batch,
-                        ivals, rec, tc.begin + lo2, hi2 - lo2);
+                        ivals, gid_of, rec, tc.begin + lo2, hi2 - lo2);
             cp_async_commit();
             cp_async_wait_one();
         } else {
@@ -595,15 +602,25 @@ __device__ void render_bwd_tile(const TM& tm, const ViewTable& vt, const TileCtx
         }
         tm.sync();
         // flush this batch's sums: one global atomic per (Gaussian, component, tile)
-        for (int i = tm.tid; i < KA * cnt; i += tm.size) {
-            const float a = acc[i];
-            if (a != 0.0f) {
+        if (partial) {
+            // deterministic plan: every staged pair's sums go to its own slot
+            // (cur_ids hold emission positions), zeros included
+            for (int i = tm.tid; i < KA * cnt; i += tm.size) {
                 const int j = i / KA, c = i - j * KA;
-                if (c < kGrad2d)
-                    atomicAdd(grad2d + (size_t)cur_ids[j] * kGrad2d + c, a);
-                else
-                    atomicAdd(absgrad + (size_t)cur_ids[j] * 2 + (c - kGrad2d), a);
+                partial[(size_t)cur_ids[j] * 11 + c] = acc[i];
                 acc[i] = 0.0f;
+            }
+        } else {
+            for (int i = tm.tid; i < KA * cnt; i += tm.size) {
+                const float a = acc[i];
+                if (a != 0.0f) {
+                    const int j = i / KA, c = i - j * KA;
+                    if (c < kGrad2d)
+                        atomicAdd(grad2d + (size_t)cur_ids[j] * kGrad2d + c, a);
+                    else
+                        atomicAdd(absgrad + (size_t)cur_ids[j] * 2 + (c - kGrad2d), a);
+                    acc[i] = 0.0f;
+                }
             }
         }
         tm.sync();
@@ -613,11 +630,13 @@ __device__ void render_bwd_tile(const TM& tm, const ViewTable& vt, const TileCtx
 template <int PPT, bool WARP, bool ABS>
 __global__ void k_render_bwd(ViewTable vt, const uint32_t* __restrict__ ranges,
                              const uint32_t* __restrict__ order,
-                             const uint32_t* __restrict__ ivals, const float4* __restrict__ rec,
+                             const uint32_t* __restrict__ ivals,
+                             const uint32_t* __restrict__ gid_of, const float4* __restrict__ rec,
                              int batch, int team_f4, int total_tiles, uint32_t* queue, float bg0,
                              float bg1, float bg2, const float* __restrict__ final_T,
                              const int32_t* __restrict__ last_idx, const float* __restrict__ dL,
-                             float* __restrict__ grad2d, float* __restrict__ absgrad) {
+                             float* __restrict__ grad2d, float* __restrict__ absgrad,
+                             float* __restrict__ partial) {
     extern __shared__ float4 smem[];
     __shared__ int s_slot, s_maxlast;
     const Team<WARP> tm;
@@ -628,13 +647,42 @@ __global__ void k_render_bwd(ViewTable vt, const uint32_t* __restrict__ ranges,
         if (slot >= total_tiles) break;
         const TileCtx tc = tile_ctx(vt, ranges, (int)order[slot]);
         if (tc.channels == 3)
-            render_bwd_tile<3, PPT, Team<WARP>, ABS>(tm, vt, tc, ivals, rec, mine, &s_maxlast,
-                                                     batch, bg, final_T, last_idx, dL, grad2d,
-                                                     absgrad);
+            render_bwd_tile<3, PPT, Team<WARP>, ABS>(tm, vt, tc, ivals, gid_of, rec, mine,
+                                                     &s_maxlast, batch, bg, final_T, last_idx, dL,
+                                                     grad2d, absgrad, partial);
         else
-            render_bwd_tile<1, PPT, Team<WARP>, ABS>(tm, vt, tc, ivals, rec, mine, &s_maxlast,
-                                                     batch, bg, final_T, last_idx, dL, grad2d,
-                                                     absgrad);
+            render_bwd_tile<1, PPT, Team<WARP>, ABS>(tm, vt, tc, ivals, gid_of, rec, mine,
+                                                     &s_maxlast, batch, bg, final_T, last_idx, dL,
+                                                     grad2d, absgrad, partial);
+    }
+}
+
+// Deterministic plans: the screen-space gradient of each (view, Gaussian) is
+// the sum of its (Gaussian, tile) partial sums in emission order -- the
+// pairs of one (view, Gaussian) were emitted at consecutive positions
+// [offs[k], offs[k+1]) of its depth-order rank k -- so every run adds the
+// same numbers in the same order.
+__global__ void k_partial_reduce(const uint32_t* __restrict__ depth_order,
+                                 const uint32_t* __restrict__ offs,
+                                 const DevCounters* __restrict__ ctr,
+                                 const float* __restrict__ partial, int abs_stats,
+                                 float* __restrict__ grad2d, float* __restrict__ absgrad) {
+    const uint32_t k = blockIdx.x * blockDim.x + threadIdx.x;
+    if (k >= ctr->vn) return;
+    const uint32_t cnt = ctr->n_instances;
+    const uint32_t vg = depth_order[k];
+    const uint32_t a = min(offs[k], cnt), b = min(offs[k + 1], cnt);
+    float s[11];
+#pragma unroll
+    for (int c = 0; c < 11; ++c) s[c] = 0.0f;
+    for (uint32_t e = a; e < b; ++e)
+#pragma unroll
+        for (int c = 0; c < 11; ++c) s[c] += partial[(size_t)e * 11 + c];
+#pragma unroll
+    for (int c = 0; c < kGrad2d; ++c) grad2d[(size_t)vg * kGrad2d + c] = s[c];
+    if (abs_stats) {
+        absgrad[2 * (size_t)vg] = s[kGrad2d];
+        absgrad[2 * (size_t)vg + 1] = s[kGrad2d + 1];
     }
 }
 
@@ -728,6 +776,7 @@ gs_status launch_render_fwd(const Plan* p, void* ws, float* images, float* final
     const uint32_t* vals =
         cbuf<uint32_t>(p, ws, (p->tile_passes & 1) ? (int)B_IVAL_B : (int)GS_BUF_TILE_VALUES);
     const float4* rec = cbuf<float4>(p, ws, GS_BUF_PROJ);
+    const uint32_t* gid_of = p->cfg.deterministic ? cbuf<uint32_t>(p, ws, B_GID_OF) : nullptr;
     uint32_t* queue = buf<uint32_t>(p, ws, B_TILE_QUEUE);
     auto kern = s.warp ? pick(ppt, k_render_fwd<1, true>, k_render_fwd<2, true>,
                               k_render_fwd<4, true>, k_render_fwd<8, true>)
@@ -737,9 +786,10 @@ gs_status launch_render_fwd(const Plan* p, void* ws, float* images, float* final
                                          p->total_tiles);
     if (blocks < 0) return GS_ERR_CUDA;
     if (cudaMemsetAsync(queue, 0, sizeof(uint32_t), st) != cudaSuccess) return GS_ERR_CUDA;
-    kern<<<blocks, s.threads, s.smem, st>>>(p->vt, ranges, order, vals, rec, batch, s.tf4,
-                                            p->total_tiles, queue, p->cfg.bg[0], p->cfg.bg[1],
-                                            p->cfg.bg[2], images, final_T, last_idx);
+    kern<<<blocks, s.threads, s.smem, st>>>(p->vt, ranges, order, vals, gid_of, rec, batch,
+                                            s.tf4, p->total_tiles, queue, p->cfg.bg[0],
+                                            p->cfg.bg[1], p->cfg.bg[2], images, final_T,
+                                            last_idx);
     return launch_status();
 }
 
@@ -757,6 +807,9 @@ gs_status launch_render_bwd_pixels(const Plan* p, void* ws, const float* final_T
     uint32_t* queue = buf<uint32_t>(p, ws, B_TILE_QUEUE) + 1;
     const bool abs_stats = p->cfg.density_stats != 0;
     float* absgrad = abs_stats ? buf<float>(p, ws, GS_BUF_ABSGRAD) : nullptr;
+    const bool det = p->cfg.deterministic != 0;
+    const uint32_t* gid_of = det ? cbuf<uint32_t>(p, ws, B_GID_OF) : nullptr;
+    float* partial = det ? buf<float>(p, ws, B_PARTIAL) : nullptr;
     auto kern =
         abs_stats
             ? (s.warp ? pick(ppt, k_render_bwd<1, true, true>, k_render_bwd<2, true, true>,
@@ -775,10 +828,21 @@ gs_status launch_render_bwd_pixels(const Plan* p, void* ws, const float* final_T
     if (abs_stats &&
         cudaMemsetAsync(absgrad, 0, p->len[GS_BUF_ABSGRAD], st) != cudaSuccess)
         return GS_ERR_CUDA;
-    kern<<<blocks, s.threads, s.smem, st>>>(p->vt, ranges, order, vals, rec, batch, s.tf4,
-                                            p->total_tiles, queue, p->cfg.bg[0], p->cfg.bg[1],
-                                            p->cfg.bg[2], final_T, last_idx, dL, grad2d,
-                                            absgrad);
+    if (det && cudaMemsetAsync(partial, 0, p->len[B_PARTIAL], st) != cudaSuccess)
+        return GS_ERR_CUDA;
+    kern<<<blocks, s.threads, s.smem, st>>>(p->vt, ranges, order, vals, gid_of, rec, batch,
+                                            s.tf4, p->total_tiles, queue, p->cfg.bg[0],
+                                            p->cfg.bg[1], p->cfg.bg[2], final_T, last_idx, dL,
+                                            grad2d, absgrad, partial);
+    if (det) {
+        // grid over the plan's capacity; the pair count of the last binning
+        // is read on the device
+        const uint32_t VNcap = (uint32_t)p->vt.n_views * (uint32_t)p->n_capacity;
+        k_partial_reduce<<<(VNcap + 255) / 256, 256, 0, st>>>(
+            cbuf<uint32_t>(p, ws, GS_BUF_DEPTH_ORDER), cbuf<uint32_t>(p, ws, B_OFFSETS),
+            cbuf<DevCounters>(p, ws, GS_BUF_COUNTERS), partial, abs_stats ? 1 : 0, grad2d,
+            absgrad);
+    }
     return launch_status();
 }
 

@@ -211,7 +211,8 @@ k_scan_reduce(const uint32_t* __restrict__ order, const uint32_t* __restrict__ t
 
 // Exclusive scan of the block sums (one block), total instance count.
 __global__ void __launch_bounds__(kSortThreads)
-k_scan_blocks(uint32_t* __restrict__ block_sums, int nb, uint32_t cap, DevCounters* ctr) {
+k_scan_blocks(uint32_t* __restrict__ block_sums, int nb, uint32_t cap, uint32_t vn,
+              DevCounters* ctr) {
     __shared__ uint32_t wt[33];
     unsigned long long carry = 0;
     for (int base = 0; base < nb; base += kSortThreads * 4) {
@@ -233,6 +234,7 @@ k_scan_blocks(uint32_t* __restrict__ block_sums, int nb, uint32_t cap, DevCounte
     }
     if (threadIdx.x == 0) {
         ctr->n_raw = carry;
+        ctr->vn = vn;
         ctr->n_instances = (uint32_t)min(carry, (unsigned long long)cap);
         if (carry > cap) atomicOr(&ctr->status, (uint32_t)GS_DEV_CAPACITY);
     }
@@ -274,7 +276,8 @@ constexpr int kEmitEntries = 256;
 __global__ void __launch_bounds__(kEmitEntries)
 k_emit(const uint32_t* __restrict__ order, const uint32_t* __restrict__ off,
        const uint2* __restrict__ rects, uint32_t count, int n, ViewTable vt, uint32_t cap,
-       uint32_t* __restrict__ ikeys, uint32_t* __restrict__ ivals) {
+       uint32_t* __restrict__ ikeys, uint32_t* __restrict__ ivals,
+       uint32_t* __restrict__ gid_of) {
     __shared__ uint32_t s_off[kEmitEntries + 1];
     __shared__ uint32_t s_vg[kEmitEntries];
     __shared__ uint2 s_rect[kEmitEntries];
@@ -306,7 +309,13 @@ k_emit(const uint32_t* __restrict__ order, const uint32_t* __restrict__ off,
         const uint32_t dy = k / w, dx = k - dy * w;
         const ViewGeom& geo = vt.v[s_view[lo]];
         ikeys[pos] = (uint32_t)geo.tile_offset + (y0 + dy) * (uint32_t)geo.tiles_x + x0 + dx;
-        ivals[pos] = s_vg[lo];
+        if (gid_of) {
+            // deterministic plans: the sort carries the emission position
+            ivals[pos] = pos;
+            gid_of[pos] = s_vg[lo];
+        } else {
+            ivals[pos] = s_vg[lo];
+        }
     }
 }
 
@@ -421,7 +430,7 @@ gs_status launch_bin_sort(const Plan* p, int32_t n, void* ws, cudaStream_t st) {
     uint32_t* bsums = buf<uint32_t>(p, ws, B_SCAN_BLOCKS);
     const uint32_t* touched = buf<uint32_t>(p, ws, GS_BUF_TOUCHED);
     k_scan_reduce<<<snb, kScanThreads, 0, st>>>(va, touched, VN, bsums);
-    k_scan_blocks<<<1, kSortThreads, 0, st>>>(bsums, snb, icap, ctr);
+    k_scan_blocks<<<1, kSortThreads, 0, st>>>(bsums, snb, icap, VN, ctr);
     uint32_t* ika = buf<uint32_t>(p, ws, GS_BUF_TILE_KEYS);
     uint32_t* iva = buf<uint32_t>(p, ws, GS_BUF_TILE_VALUES);
     uint32_t* ikb = buf<uint32_t>(p, ws, B_IKEY_B);
@@ -429,7 +438,8 @@ gs_status launch_bin_sort(const Plan* p, int32_t n, void* ws, cudaStream_t st) {
     uint32_t* offs = buf<uint32_t>(p, ws, B_OFFSETS);
     k_scan_offsets<<<snb, kScanThreads, 0, st>>>(va, touched, bsums, VN, offs);
     k_emit<<<(VN + kEmitEntries - 1) / kEmitEntries, kEmitEntries, 0, st>>>(
-        va, offs, buf<uint2>(p, ws, GS_BUF_RECT), VN, n, p->vt, icap, ika, iva);
+        va, offs, buf<uint2>(p, ws, GS_BUF_RECT), VN, n, p->vt, icap, ika, iva,
+        p->cfg.deterministic ? buf<uint32_t>(p, ws, B_GID_OF) : nullptr);
     gs_status s = launch_status();
     if (s != GS_OK) return s;
 

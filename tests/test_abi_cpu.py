@@ -30,7 +30,7 @@ def test_exports_every_declared_function(lib):
 
 def test_struct_sizes_match_header():
     assert ctypes.sizeof(B.gs_view) == 80
-    assert ctypes.sizeof(B.gs_config) == 44
+    assert ctypes.sizeof(B.gs_config) == 48
     assert ctypes.sizeof(B.gs_densify_config) == 32
     assert ctypes.sizeof(B.gs_counters) == 32
     assert ctypes.sizeof(B.gs_plan) == 8 * B.GS_PLAN_WORDS
@@ -106,6 +106,17 @@ def test_calls_reject_bad_arguments_without_launching(lib):
     assert lib.gs_adam_step(p, p, p, p, 5, 1, offs, lrs, 1.0, 0.999, 1e-15, p, None) == \
         B.GS_ERR_INVALID  # beta1 = 1
     assert B.gs_status_string(B.GS_ERR_CAPACITY).startswith("GS_ERR_CAPACITY")
+
+
+def test_deterministic_plans_need_one_warp_per_tile(lib):
+    views = _views((64, 48, 3))
+    ok = B.gs_config(8, 8, 64, 1, 32, 2, 0.2, (B.c_float * 3)(0, 0, 0), 0, 1)
+    bad = B.gs_config(16, 16, 64, 1, 64, 1, 0.2, (B.c_float * 3)(0, 0, 0), 0, 1)
+    plan = B.gs_plan()
+    arr = (B.gs_view * 1)(*views)
+    assert lib.gs_plan_init(ctypes.byref(plan), ctypes.byref(ok), 1, arr, 10, 1000) == B.GS_OK
+    assert lib.gs_plan_init(ctypes.byref(plan), ctypes.byref(bad), 1, arr, 10, 1000) == \
+        B.GS_ERR_UNSUPPORTED
 
 
 def test_density_control_rejects_bad_arguments_without_launching(lib):
