@@ -401,6 +401,25 @@ gs_status gs_densify_apply(const gs_map *map, const gs_map_grad *src_m, const gs
 gs_status gs_pyr_down(const float *src, int32_t channels, int32_t height, int32_t width,
                       float *dst, void *stream);
 
+/* ---------------------------------------------------------------------------
+ * Point-cloud densification (paper Sec. III-A): tracked pixels are chosen
+ * DSO-style (per block the pixel of largest gradient above a threshold,
+ * repeated with lower thresholds on larger blocks), and points in flat,
+ * untracked regions are added at the mean depth of the vertices of their
+ * triangle in the Delaunay triangulation of the tracked pixels.
+ * ------------------------------------------------------------------------- */
+
+/* Delaunay triangulation of n distinct points with integer coordinates in
+ * [0, 2^20) (HOST arrays: xy_host[n][2]; tri_host[tri_capacity][3] receives
+ * counter-clockwise vertex indices).  Exact predicates; on co-circular
+ * points one of the valid triangulations.  Synchronous host code (no GPU
+ * work).  *n_tri is set to the triangle count (2n - h - 2 for h points on
+ * the hull boundary; 0 if all points are collinear or n < 3);
+ * GS_ERR_CAPACITY if it exceeds tri_capacity (the first tri_capacity are
+ * written), GS_ERR_INVALID for duplicate or out-of-range points. */
+gs_status gs_delaunay(const int32_t *xy_host, int32_t n, int32_t *tri_host, int32_t tri_capacity,
+                      int32_t *n_tri);
+
 /* Copies the device counters of the workspace to *out (host) and waits for
  * `stream`. */
 gs_status gs_read_counters(const gs_plan *plan, const void *ws, gs_counters *out, void *stream);

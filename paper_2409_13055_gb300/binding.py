@@ -108,6 +108,7 @@ _SIGNATURES = {
                                    _P(gs_map_grad), _P(gs_map_grad), _P(gs_map_grad), c_void_p,
                                    c_void_p]),
     "gs_pyr_down": (c_int32, [c_void_p, c_int32, c_int32, c_int32, c_void_p, c_void_p]),
+    "gs_delaunay": (c_int32, [c_void_p, c_int32, c_void_p, c_int32, _P(c_int32)]),
     "gs_read_counters": (c_int32, [_P(gs_plan), c_void_p, _P(gs_counters), c_void_p]),
     "gs_status_string": (ctypes.c_char_p, [c_int32]),
 }
@@ -315,6 +316,20 @@ def gs_densify_apply(gmap, src_m, src_v, accum, denom, samples, cfg, scratch, n_
 def gs_pyr_down(src, channels, height, width, dst, stream=None):
     check(lib().gs_pyr_down(_ptr(src), int(channels), int(height), int(width), _ptr(dst),
                             _stream(stream)), "gs_pyr_down")
+
+
+def gs_delaunay(xy):
+    """Triangles [T][3] (int32, counter-clockwise) of the Delaunay triangulation
+    of the integer points xy [n][2] (host numpy)."""
+    import numpy as np
+    xy = np.ascontiguousarray(xy, dtype=np.int32)
+    n = xy.shape[0]
+    cap = max(1, 2 * n)
+    tri = np.zeros((cap, 3), np.int32)
+    cnt = c_int32(0)
+    check(lib().gs_delaunay(xy.ctypes.data, n, tri.ctypes.data, cap, ctypes.byref(cnt)),
+          "gs_delaunay")
+    return tri[: cnt.value].copy()
 
 
 def gs_read_counters(plan, ws, stream=None) -> gs_counters:
