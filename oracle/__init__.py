@@ -413,3 +413,65 @@ def pyr_view(view):
     """The camera of the next pyramid level."""
     return dict(view, width=(view["width"] + 1) // 2, height=(view["height"] + 1) // 2,
                 fx=view["fx"] / 2, fy=view["fy"] / 2, cx=view["cx"] / 2, cy=view["cy"] / 2)
+
+
+# --------------------------------------------------------------------------
+# Point-cloud densification (paper Sec. III-A).  Pixel selection: per block
+# the pixel of largest image gradient, if above the pass threshold, repeated
+# on larger blocks with lower thresholds where nothing was selected yet.
+# Readings: central-difference gradient (zero on the one-pixel border),
+# compared as the squared magnitude; pass k uses blocks of block * 2^k pixels
+# (partial blocks at the right and bottom edges included) and the squared
+# threshold thr_sq[k]; ties go to the first pixel in raster order; a pass-k
+# block is skipped if any of its pixels was selected in an earlier pass.
+# Interpolation: on the pixels of a grid of step `grid` whose squared
+# gradient is below flat_sq and that were not selected, the depth is the mean
+# of the vertex depths of the first (lowest-index) triangle containing the
+# pixel (closed triangles), none outside the triangulation.
+# --------------------------------------------------------------------------
+def grad_sq(gray):
+    g = np.asarray(gray, np.float64)
+    gx = np.zeros_like(g)
+    gy = np.zeros_like(g)
+    gx[1:-1, 1:-1] = 0.5 * (g[1:-1, 2:] - g[1:-1, :-2])
+    gy[1:-1, 1:-1] = 0.5 * (g[2:, 1:-1] - g[:-2, 1:-1])
+    return gx * gx + gy * gy
+
+
+def select_pixels(gray, block, thr_sq):
+    """int32 [H][W]: 0, or k + 1 for a pixel selected in pass k."""
+    g2 = grad_sq(gray)
+    H, W = g2.shape
+    sel = np.zeros((H, W), np.int32)
+    for k, t in enumerate(thr_sq):
+        s = block << k
+        for y0 in range(0, H, s):
+            for x0 in range(0, W, s):
+                if np.any(sel[y0:y0 + s, x0:x0 + s]):
+                    continue
+                reg = g2[y0:y0 + s, x0:x0 + s]
+                i = int(np.argmax(reg))  # first maximum in raster order
+                if reg.flat[i] >= t:
+                    sel[y0 + i // reg.shape[1], x0 + i % reg.shape[1]] = k + 1
+    return sel
+
+
+def interp_depth(tri, xy, depth, gray, selected, grid, flat_sq):
+    """float64 [ceil(H/grid)][ceil(W/grid)] depths (0 where no point)."""
+    g2 = grad_sq(gray)
+    H, W = g2.shape
+    out = np.zeros(((H + grid - 1) // grid, (W + grid - 1) // grid))
+    P = np.asarray(xy, np.int64)
+    T = np.asarray(tri, np.int64)
+    for gy in range(out.shape[0]):
+        for gx in range(out.shape[1]):
+            x, y = gx * grid, gy * grid
+            if selected[y, x] or not g2[y, x] < flat_sq:
+                continue
+            for t, (a, b, c) in enumerate(T):
+                e = [(P[v][0] - P[u][0]) * (y - P[u][1]) - (P[v][1] - P[u][1]) * (x - P[u][0])
+                     for u, v in ((a, b), (b, c), (c, a))]
+                if min(e) >= 0:
+                    out[gy, gx] = (depth[a] + depth[b] + depth[c]) / 3.0
+                    break
+    return out
