@@ -441,6 +441,41 @@ def run_pyramid(args, ws, p, view, target):
     return out
 
 
+def run_pointcloud(args, ws):
+    """Point-cloud densification of a keyframe (paper Sec. III-A) at the
+    EuRoC-like 752x480: GPU selection, host Delaunay of the selected pixels,
+    GPU mean-depth interpolation and the new Gaussians, on 10 ray-cast
+    keyframes of the drone loop (host clock, synchronised; the ray cast is
+    input generation and not timed)."""
+    import time
+
+    import torch
+    from paper_2409_13055_gb300 import pointcloud, scenes
+
+    views = scenes.drone_loop(10)
+    faces, tex = scenes.room_textures()
+    frames = [scenes.ray_cast(v, faces, tex, device="cuda") for v in views]
+    rows = []
+    for it, (v, (depth, gray)) in enumerate(zip(views, frames)):
+        D = torch.tensor(depth, device="cuda")
+        G = torch.tensor(gray, device="cuda")
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        px, py, z = pointcloud.keyframe_points(G, lambda x, y: D[y, x])
+        new = pointcloud.gaussians_from_points(v, px, py, z, G)
+        torch.cuda.synchronize()
+        ms = (time.perf_counter() - t0) * 1e3
+        n_sel = int(torch.count_nonzero(pointcloud.select_pixels(G)[1]).item())
+        if it > 0:  # the first keyframe warms up
+            rows.append((ms, n_sel, int(px.numel()) - n_sel, new["means"].shape[0]))
+    a = np.array(rows, float)
+    return dict(ms_per_keyframe=float(a[:, 0].mean()), selected_per_keyframe=float(a[:, 1].mean()),
+                interpolated_per_keyframe=float(a[:, 2].mean()),
+                config=dict(image="752x480x1", block=4, passes=3,
+                            thresholds_sq=list(pointcloud.DEFAULT_THRESHOLDS_SQ), grid=4,
+                            keyframes=len(rows), clock="host, synchronised"))
+
+
 def run_gpu(args, ws, rank, local):
     import torch
     from paper_2409_13055_gb300 import binding as B
@@ -652,6 +687,8 @@ def run_gpu(args, ws, rank, local):
     if not args.no_pyramid:
         torch.cuda.empty_cache()
         out["pyramid"] = run_pyramid(args, ws, p, view, target)
+    if not args.no_pointcloud:
+        out["pointcloud"] = run_pointcloud(args, ws)
 
     if rank == 0 and not args.no_cpu_baseline:
         from paper_2409_13055_gb300 import scenes as sc
@@ -694,6 +731,8 @@ def main():
                     help="storage order of the map's Gaussians (the same set either way)")
     ap.add_argument("--streaming-kfs", type=int, default=100,
                     help="keyframes of the streaming measurement (0 skips it)")
+    ap.add_argument("--no-pointcloud", action="store_true",
+                    help="skip the keyframe point-cloud densification measurement")
     ap.add_argument("--no-pyramid", action="store_true",
                     help="skip the Gaussian-pyramid level measurement")
     ap.add_argument("--no-density", action="store_true",

@@ -420,6 +420,29 @@ gs_status gs_pyr_down(const float *src, int32_t channels, int32_t height, int32_
 gs_status gs_delaunay(const int32_t *xy_host, int32_t n, int32_t *tri_host, int32_t tri_capacity,
                       int32_t *n_tri);
 
+/* DSO-style selection on a [height][width] gray image: grad_sq receives the
+ * squared central-difference gradient (zero on the one-pixel border) and
+ * selected the pass (k + 1) in which each pixel was chosen, else 0.  Pass k
+ * (k < passes <= 8) divides the image into blocks of block * 2^k pixels
+ * (partial blocks at the right and bottom edges included); a block without
+ * an earlier selection takes its first pixel (raster order) of largest
+ * squared gradient if that reaches threshold_sq_host[k] (HOST array). */
+gs_status gs_select_pixels(const float *gray, int32_t height, int32_t width, int32_t block,
+                           int32_t passes, const float *threshold_sq_host, float *grad_sq,
+                           int32_t *selected, void *stream);
+
+/* Mean-depth interpolation on the grid pixels (gx * grid, gy * grid): a
+ * pixel not selected and with grad_sq < flat_sq that lies in a triangle of
+ * tri[n_tri][3] (counter-clockwise indices into xy[][2] pixel coordinates;
+ * closed triangles, the lowest index wins on shared edges) gets the mean of
+ * the three vertex depths in out[ceil(height/grid)][ceil(width/grid)],
+ * every other grid pixel 0.  owner: int32 scratch of the same size.  All
+ * device arrays. */
+gs_status gs_interp_depth(const int32_t *tri, int32_t n_tri, const int32_t *xy,
+                          const float *depth, const float *grad_sq, const int32_t *selected,
+                          int32_t height, int32_t width, int32_t grid, float flat_sq,
+                          int32_t *owner, float *out, void *stream);
+
 /* Copies the device counters of the workspace to *out (host) and waits for
  * `stream`. */
 gs_status gs_read_counters(const gs_plan *plan, const void *ws, gs_counters *out, void *stream);

@@ -109,6 +109,11 @@ _SIGNATURES = {
                                    c_void_p]),
     "gs_pyr_down": (c_int32, [c_void_p, c_int32, c_int32, c_int32, c_void_p, c_void_p]),
     "gs_delaunay": (c_int32, [c_void_p, c_int32, c_void_p, c_int32, _P(c_int32)]),
+    "gs_select_pixels": (c_int32, [c_void_p, c_int32, c_int32, c_int32, c_int32, _P(c_float),
+                                   c_void_p, c_void_p, c_void_p]),
+    "gs_interp_depth": (c_int32, [c_void_p, c_int32, c_void_p, c_void_p, c_void_p, c_void_p,
+                                  c_int32, c_int32, c_int32, c_float, c_void_p, c_void_p,
+                                  c_void_p]),
     "gs_read_counters": (c_int32, [_P(gs_plan), c_void_p, _P(gs_counters), c_void_p]),
     "gs_status_string": (ctypes.c_char_p, [c_int32]),
 }
@@ -330,6 +335,21 @@ def gs_delaunay(xy):
     check(lib().gs_delaunay(xy.ctypes.data, n, tri.ctypes.data, cap, ctypes.byref(cnt)),
           "gs_delaunay")
     return tri[: cnt.value].copy()
+
+
+def gs_select_pixels(gray, block, thresholds_sq, grad_sq, selected, stream=None):
+    H, W = gray.shape
+    thr = (c_float * len(thresholds_sq))(*[float(t) for t in thresholds_sq])
+    check(lib().gs_select_pixels(_ptr(gray), H, W, int(block), len(thresholds_sq), thr,
+                                 _ptr(grad_sq), _ptr(selected), _stream(stream)),
+          "gs_select_pixels")
+
+
+def gs_interp_depth(tri, xy, depth, grad_sq, selected, grid, flat_sq, owner, out, stream=None):
+    H, W = grad_sq.shape
+    check(lib().gs_interp_depth(_ptr(tri), int(tri.shape[0]), _ptr(xy), _ptr(depth),
+                                _ptr(grad_sq), _ptr(selected), H, W, int(grid), float(flat_sq),
+                                _ptr(owner), _ptr(out), _stream(stream)), "gs_interp_depth")
 
 
 def gs_read_counters(plan, ws, stream=None) -> gs_counters:
