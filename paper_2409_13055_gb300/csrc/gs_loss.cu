@@ -29,6 +29,7 @@ constexpr int kTX = 32, kTY = 16, kHalo = 5, kWin = 11;
 constexpr int kRows = kTY + 2 * kHalo;  // 26
 constexpr int kCols = kTX + 2 * kHalo;  // 42
 constexpr int kLossThreads = 256;       // 32 x 8
+constexpr int kSeg = 4;                 // outputs per thread in the horizontal passes
 
 struct Win {
     float w[kWin];
@@ -92,38 +93,59 @@ k_ssim_fwd(ViewTable vt, Win win, const float* __restrict__ img, const float* __
         sy[r][c] = b;
     }
     __syncthreads();
-    for (int i = threadIdx.x; i < kRows * kTX; i += blockDim.x) {
-        const int r = i / kTX, c = i - r * kTX;
-        float mx = 0.f, my = 0.f, xx = 0.f, yy = 0.f, xy = 0.f;
+    // horizontal pass, register-blocked: a thread takes kSeg consecutive
+    // outputs of one row, reading their kSeg + 10 inputs once
+    for (int i = threadIdx.x; i < kRows * (kTX / kSeg); i += blockDim.x) {
+        const int r = i / (kTX / kSeg), c0 = (i - r * (kTX / kSeg)) * kSeg;
+        float a[kSeg + kWin - 1], b[kSeg + kWin - 1];
 #pragma unroll
-        for (int k = 0; k < kWin; ++k) {
-            const float a = sx[r][c + k], b = sy[r][c + k], w = win.w[k];
-            mx = fmaf(w, a, mx);
-            my = fmaf(w, b, my);
-            xx = fmaf(w, a * a, xx);
-            yy = fmaf(w, b * b, yy);
-            xy = fmaf(w, a * b, xy);
+        for (int k = 0; k < kSeg + kWin - 1; ++k) {
+            a[k] = sx[r][c0 + k];
+            b[k] = sy[r][c0 + k];
         }
-        h[0][r][c] = mx;
-        h[1][r][c] = my;
-        h[2][r][c] = xx;
-        h[3][r][c] = yy;
-        h[4][r][c] = xy;
+#pragma unroll
+        for (int o = 0; o < kSeg; ++o) {
+            float mx = 0.f, my = 0.f, xx = 0.f, yy = 0.f, xy = 0.f;
+#pragma unroll
+            for (int k = 0; k < kWin; ++k) {
+                const float u = a[o + k], v = b[o + k], w = win.w[k];
+                mx = fmaf(w, u, mx);
+                my = fmaf(w, v, my);
+                xx = fmaf(w, u * u, xx);
+                yy = fmaf(w, v * v, yy);
+                xy = fmaf(w, u * v, xy);
+            }
+            h[0][r][c0 + o] = mx;
+            h[1][r][c0 + o] = my;
+            h[2][r][c0 + o] = xx;
+            h[3][r][c0 + o] = yy;
+            h[4][r][c0 + o] = xy;
+        }
     }
     __syncthreads();
     const float C1 = 0.01f * 0.01f, C2 = 0.03f * 0.03f;
     const int tx = threadIdx.x & 31, ty = threadIdx.x >> 5;
     float l1 = 0.0f, ss = 0.0f;
-    for (int rr = ty; rr < kTY; rr += kLossThreads / 32) {
+    // vertical pass, register-blocked: a thread takes two consecutive rows
+    // of one column, reading their 12 rows of horizontal sums once
+    static_assert(kTY == 2 * (kLossThreads / 32), "two output rows per thread");
+    const int r0 = 2 * ty;
+    float m2[2][5] = {{0.f, 0.f, 0.f, 0.f, 0.f}, {0.f, 0.f, 0.f, 0.f, 0.f}};
+#pragma unroll
+    for (int k = 0; k < kWin + 1; ++k) {
+#pragma unroll
+        for (int q = 0; q < 5; ++q) {
+            const float hv = h[q][r0 + k][tx];
+            if (k < kWin) m2[0][q] = fmaf(win.w[k], hv, m2[0][q]);
+            if (k >= 1) m2[1][q] = fmaf(win.w[k - 1], hv, m2[1][q]);
+        }
+    }
+#pragma unroll
+    for (int o = 0; o < 2; ++o) {
+        const int rr = r0 + o;
         const int x = bp.x0 + tx, y = bp.y0 + rr;
         if (x >= bp.width || y >= bp.height) continue;
-        float m[5] = {0.f, 0.f, 0.f, 0.f, 0.f};
-#pragma unroll
-        for (int k = 0; k < kWin; ++k) {
-            const float w = win.w[k];
-#pragma unroll
-            for (int q = 0; q < 5; ++q) m[q] = fmaf(w, h[q][rr + k][tx], m[q]);
-        }
+        const float* m = m2[o];
         const float mx = m[0], my = m[1];
         const float vx = m[2] - mx * mx, vy = m[3] - my * my, cxy = m[4] - mx * my;
         const float A = 2.0f * mx * my + C1, B = 2.0f * cxy + C2;
@@ -187,35 +209,50 @@ k_ssim_bwd(ViewTable vt, Win win, const float* __restrict__ img, const float* __
         sm[2][r][c] = d;
     }
     __syncthreads();
-    for (int i = threadIdx.x; i < kRows * kTX; i += blockDim.x) {
-        const int r = i / kTX, c = i - r * kTX;
-        float a = 0.f, b = 0.f, d = 0.f;
+    for (int i = threadIdx.x; i < kRows * (kTX / kSeg); i += blockDim.x) {
+        const int r = i / (kTX / kSeg), c0 = (i - r * (kTX / kSeg)) * kSeg;
+        float u[3][kSeg + kWin - 1];
 #pragma unroll
-        for (int k = 0; k < kWin; ++k) {
-            const float w = win.w[k];
-            a = fmaf(w, sm[0][r][c + k], a);
-            b = fmaf(w, sm[1][r][c + k], b);
-            d = fmaf(w, sm[2][r][c + k], d);
+        for (int k = 0; k < kSeg + kWin - 1; ++k) {
+            u[0][k] = sm[0][r][c0 + k];
+            u[1][k] = sm[1][r][c0 + k];
+            u[2][k] = sm[2][r][c0 + k];
         }
-        h[0][r][c] = a;
-        h[1][r][c] = b;
-        h[2][r][c] = d;
+#pragma unroll
+        for (int o = 0; o < kSeg; ++o) {
+            float a = 0.f, b = 0.f, d = 0.f;
+#pragma unroll
+            for (int k = 0; k < kWin; ++k) {
+                const float w = win.w[k];
+                a = fmaf(w, u[0][o + k], a);
+                b = fmaf(w, u[1][o + k], b);
+                d = fmaf(w, u[2][o + k], d);
+            }
+            h[0][r][c0 + o] = a;
+            h[1][r][c0 + o] = b;
+            h[2][r][c0 + o] = d;
+        }
     }
     __syncthreads();
     const ViewGeom& g = vt.v[bp.view];
     const float scale = inv_views / ((float)g.channels * (float)g.width * (float)g.height);
     const int tx = threadIdx.x & 31, ty = threadIdx.x >> 5;
-    for (int rr = ty; rr < kTY; rr += kLossThreads / 32) {
-        const int x = bp.x0 + tx, y = bp.y0 + rr;
-        if (x >= bp.width || y >= bp.height) continue;
-        float a = 0.f, b = 0.f, d = 0.f;
+    const int r0 = 2 * ty;
+    float u2[2][3] = {{0.f, 0.f, 0.f}, {0.f, 0.f, 0.f}};
 #pragma unroll
-        for (int k = 0; k < kWin; ++k) {
-            const float w = win.w[k];
-            a = fmaf(w, h[0][rr + k][tx], a);
-            b = fmaf(w, h[1][rr + k][tx], b);
-            d = fmaf(w, h[2][rr + k][tx], d);
+    for (int k = 0; k < kWin + 1; ++k) {
+#pragma unroll
+        for (int q = 0; q < 3; ++q) {
+            const float hv = h[q][r0 + k][tx];
+            if (k < kWin) u2[0][q] = fmaf(win.w[k], hv, u2[0][q]);
+            if (k >= 1) u2[1][q] = fmaf(win.w[k - 1], hv, u2[1][q]);
         }
+    }
+#pragma unroll
+    for (int o = 0; o < 2; ++o) {
+        const int x = bp.x0 + tx, y = bp.y0 + r0 + o;
+        if (x >= bp.width || y >= bp.height) continue;
+        const float a = u2[o][0], b = u2[o][1], d = u2[o][2];
         const int64_t idx = bp.plane + (int64_t)y * bp.width + x;
         const float xv = img[idx], yv = tgt[idx];
         const float diff = xv - yv;
