@@ -127,7 +127,6 @@ extern "C" gs_status gs_plan_init(gs_plan* plan, const gs_config* cfg, int32_t n
     len[B_GCOL] = (size_t)VN * 3 * sizeof(float);
     len[B_OFFSETS] = (size_t)(VN + 1) * sizeof(uint32_t);
     len[B_TILE_ORDER] = (size_t)tiles * sizeof(uint32_t);
-    len[B_GPARAM] = (size_t)n_capacity * 11 * sizeof(float);
     len[B_TILE_QUEUE] = 2 * sizeof(uint32_t);
     len[B_GID_OF] = cfg->deterministic ? (size_t)instance_capacity * sizeof(uint32_t) : 0;
     len[B_PARTIAL] = cfg->deterministic ? (size_t)instance_capacity * 11 * sizeof(float) : 0;

@@ -52,8 +52,6 @@ enum PrivBuf {
     B_GCOL,     // [V*n] x 3: colour gradient as it reaches the SH coefficients
     B_OFFSETS,  // [V*n + 1] instance offsets of the entries in depth order
     B_TILE_ORDER,  // [total_tiles] render order of the tiles, longest lists first
-    B_GPARAM,      // [n] x 11: this pass's quaternion, mean, log-scale, opacity gradients
-                   // held between the two fused adjoint kernels
     B_TILE_QUEUE,  // [2] u32 next-tile counters of the forward and backward render
     B_GID_OF,      // [instance_capacity] u32 (view*n + index) of each emitted instance
                    // (deterministic plans: the sort then carries emission positions)

@@ -38,27 +38,36 @@ constexpr float kY3c = 0.4570457994644658f;
 constexpr float kY3d = 0.3731763325901154f;
 constexpr float kY3e = 1.445305721320277f;
 
+// Every product and sum is an explicitly rounded intrinsic, so no FMA
+// contraction is left to the compiler: the basis comes out bit-identical in
+// every kernel that evaluates it (the fused and the two-pass adjoints form
+// the SH gradient from it independently).
 __device__ __forceinline__ void sh_eval(int degree, float x, float y, float z, float* Y) {
     Y[0] = kY0;
     if (degree < 1) return;
-    Y[1] = -kY1 * y;
-    Y[2] = kY1 * z;
-    Y[3] = -kY1 * x;
+    Y[1] = __fmul_rn(-kY1, y);
+    Y[2] = __fmul_rn(kY1, z);
+    Y[3] = __fmul_rn(-kY1, x);
     if (degree < 2) return;
-    const float xx = x * x, yy = y * y, zz = z * z;
-    Y[4] = kY2a * x * y;
-    Y[5] = -kY2a * y * z;
-    Y[6] = kY2b * (2.0f * zz - xx - yy);
-    Y[7] = -kY2a * x * z;
-    Y[8] = kY2c * (xx - yy);
+    const float xx = __fmul_rn(x, x), yy = __fmul_rn(y, y), zz = __fmul_rn(z, z);
+    const float xmy = __fsub_rn(xx, yy);                       // x^2 - y^2
+    const float t2 = __fsub_rn(__fsub_rn(__fmul_rn(2.0f, zz), xx), yy);  // 2z^2 - x^2 - y^2
+    Y[4] = __fmul_rn(__fmul_rn(kY2a, x), y);
+    Y[5] = __fmul_rn(__fmul_rn(-kY2a, y), z);
+    Y[6] = __fmul_rn(kY2b, t2);
+    Y[7] = __fmul_rn(__fmul_rn(-kY2a, x), z);
+    Y[8] = __fmul_rn(kY2c, xmy);
     if (degree < 3) return;
-    Y[9] = -kY3a * y * (3.0f * xx - yy);
-    Y[10] = kY3b * x * y * z;
-    Y[11] = -kY3c * y * (4.0f * zz - xx - yy);
-    Y[12] = kY3d * z * (2.0f * zz - 3.0f * xx - 3.0f * yy);
-    Y[13] = -kY3c * x * (4.0f * zz - xx - yy);
-    Y[14] = kY3e * z * (xx - yy);
-    Y[15] = -kY3a * x * (xx - 3.0f * yy);
+    const float t4 = __fsub_rn(__fsub_rn(__fmul_rn(4.0f, zz), xx), yy);  // 4z^2 - x^2 - y^2
+    Y[9] = __fmul_rn(__fmul_rn(-kY3a, y), __fsub_rn(__fmul_rn(3.0f, xx), yy));
+    Y[10] = __fmul_rn(__fmul_rn(__fmul_rn(kY3b, x), y), z);
+    Y[11] = __fmul_rn(__fmul_rn(-kY3c, y), t4);
+    Y[12] = __fmul_rn(__fmul_rn(kY3d, z),
+                      __fsub_rn(__fsub_rn(__fmul_rn(2.0f, zz), __fmul_rn(3.0f, xx)),
+                                __fmul_rn(3.0f, yy)));
+    Y[13] = __fmul_rn(__fmul_rn(-kY3c, x), t4);
+    Y[14] = __fmul_rn(__fmul_rn(kY3e, z), xmy);
+    Y[15] = __fmul_rn(__fmul_rn(-kY3a, x), __fsub_rn(xx, __fmul_rn(3.0f, yy)));
 }
 
 // d/d(x,y,z) of the polynomials above, accumulated as g += w * grad Y_k.
@@ -159,8 +168,7 @@ struct Proj {
 
 // Adam state for the fused projection adjoint: parameter, moment and optional
 // gradient arrays in the gs_map layout; lr per group (means, log-scales,
-// quaternions, opacity, SH DC, SH rest); the per-Gaussian gradients that
-// k_project_bwd left in workspace scratch (s_*).
+// quaternions, opacity, SH DC, SH rest).
 struct FusedAdam {
     float lr[6];
     float b1, b2, eps;
@@ -170,43 +178,7 @@ struct FusedAdam {
     float *v_means, *v_ls, *v_quats, *v_logit, *v_sh;
     const float *a_means, *a_ls, *a_quats, *a_logit, *a_sh;  // gradients to add, or null
     float *o_means, *o_ls, *o_quats, *o_logit, *o_sh;        // gradients out, or null
-    const float *s_means, *s_ls, *s_quats, *s_logit;         // this pass's gradients
 };
-
-// Adam on one warp-wide run of cnt <= 128 consecutive floats of a parameter
-// array: lane l takes floats l, l+32, l+64, l+96, every access a coalesced
-// row, all loads issued before any store.  g: this pass's gradient (shared
-// or global memory), add: gradient to add or null, out: total gradient out
-// or null.
-__device__ __forceinline__ void adam_run(float* __restrict__ p, float* __restrict__ m,
-                                         float* __restrict__ v, const float* __restrict__ g,
-                                         const float* __restrict__ add, float* __restrict__ out,
-                                         int cnt, float lr, const FusedAdam& fa, float ibc1,
-                                         float ibc2) {
-    const int lane = threadIdx.x & 31;
-    float gg[4], pp[4], mm[4], vv[4];
-#pragma unroll
-    for (int r = 0; r < 4; ++r) {
-        const int i = lane + 32 * r;
-        if (i < cnt) {
-            gg[r] = g[i] + (add ? add[i] : 0.0f);
-            pp[r] = p[i];
-            mm[r] = m[i];
-            vv[r] = v[i];
-        }
-    }
-#pragma unroll
-    for (int r = 0; r < 4; ++r) {
-        const int i = lane + 32 * r;
-        if (i < cnt) {
-            adam1(pp[r], gg[r], mm[r], vv[r], lr, fa.b1, fa.b2, fa.eps, ibc1, ibc2);
-            p[i] = pp[r];
-            m[i] = mm[r];
-            v[i] = vv[r];
-            if (out) out[i] = gg[r];
-        }
-    }
-}
 
 __device__ __forceinline__ void project_one(const float* mean, const Shape& sh, const Cam& cam,
                                             float near_z, int log2_tw, int log2_th, int tiles_x,
@@ -360,22 +332,21 @@ k_project(const float* __restrict__ means, const float* __restrict__ log_scales,
     }
 }
 
-// A8: chain rule of the projection, summed over views.  One thread per
-// Gaussian reads its screen-space gradient from every view it is visible in.
-template <int DEG>
-__global__ void __launch_bounds__(kProjThreads)
-k_project_bwd(const float* __restrict__ means, const float* __restrict__ log_scales,
-              const float* __restrict__ quats, const float* __restrict__ opacity_logits,
-              const float* __restrict__ sh, int n, const gs_view* __restrict__ views,
-              ViewTable vt, float near_z, const uint32_t* __restrict__ touched,
-              const float* __restrict__ grad2d, float* __restrict__ gcol_out,
-              float* __restrict__ g_means, float* __restrict__ g_ls, float* __restrict__ g_quats,
-              float* __restrict__ g_logit, int accumulate) {
-    extern __shared__ Cam cam_all[];
-    for (int v = threadIdx.x; v < vt.n_views; v += blockDim.x) load_cam(views[v], cam_all[v]);
-    __syncthreads();
-    const int g = blockIdx.x * blockDim.x + threadIdx.x;
-    if (g >= n) return;
+// A8: chain rule of the projection for Gaussian g, summed over the views it
+// is visible in: screen-space gradient -> gradients of the mean, log-scales,
+// quaternion and opacity logit.  The colour gradient that reaches the SH
+// coefficients (zero on clamped channels, a grayscale view's gradient spread
+// over the three channels) goes to gcol_out per (view, Gaussian), or, FUSED,
+// is folded at once into this Gaussian's SH gradient: sh_acc[k * sh_stride +
+// c] += Y_k(dir) gcol[c], view by view in view order (the sum k_sh_bwd forms).
+template <int DEG, bool FUSED>
+__device__ __forceinline__ void adjoint_one(
+    int g, const float* __restrict__ means, const float* __restrict__ log_scales,
+    const float* __restrict__ quats, const float* __restrict__ opacity_logits,
+    const float* __restrict__ sh, int n, const Cam* cam_all, const ViewTable& vt, float near_z,
+    const uint32_t* __restrict__ touched, const float* __restrict__ grad2d,
+    float* __restrict__ gcol_out, float* sh_acc, int sh_stride, float gm_out[3],
+    float gls[3], float4& gq4, float& glog) {
     const float mean[3] = {means[3 * g], means[3 * g + 1], means[3 * g + 2]};
     const float ls[3] = {log_scales[3 * g], log_scales[3 * g + 1], log_scales[3 * g + 2]};
     const float4 q = reinterpret_cast<const float4*>(quats)[g];
@@ -401,9 +372,11 @@ k_project_bwd(const float* __restrict__ means, const float* __restrict__ log_sca
         const Cam& cam = cam_all[v];
         Proj p;
         project_one(mean, shp, cam, near_z, vt.log2_tw, vt.log2_th, geo.tiles_x, geo.tiles_y, p);
-        float* gc_out = gcol_out + vg * 3;
         if (!p.visible) {
-            gc_out[0] = gc_out[1] = gc_out[2] = 0.0f;
+            if (!FUSED) {
+                float* gc_out = gcol_out + vg * 3;
+                gc_out[0] = gc_out[1] = gc_out[2] = 0.0f;
+            }
             continue;
         }
 
@@ -423,11 +396,22 @@ k_project_bwd(const float* __restrict__ means, const float* __restrict__ log_sca
 #pragma unroll
         for (int ch = 0; ch < 3; ++ch)
             if (col[ch] + 0.5f < 0.0f) gcol[ch] = 0.0f;
-        // the SH coefficients' own gradient, Y_k(dir) gcol, is formed by
-        // k_sh_bwd from this masked colour gradient
-        gc_out[0] = gcol[0];
-        gc_out[1] = gcol[1];
-        gc_out[2] = gcol[2];
+        // the SH coefficients' own gradient, Y_k(dir) gcol, from this masked
+        // colour gradient
+        if (FUSED) {
+#pragma unroll
+            for (int k = 0; k < K; ++k) {
+                float* a = sh_acc + k * sh_stride;
+                a[0] = fmaf(Y[k], gcol[0], a[0]);
+                a[1] = fmaf(Y[k], gcol[1], a[1]);
+                a[2] = fmaf(Y[k], gcol[2], a[2]);
+            }
+        } else {
+            float* gc_out = gcol_out + vg * 3;
+            gc_out[0] = gcol[0];
+            gc_out[1] = gcol[1];
+            gc_out[2] = gcol[2];
+        }
         float w[16];
 #pragma unroll
         for (int k = 0; k < 16; ++k) w[k] = 0.0f;
@@ -510,7 +494,7 @@ k_project_bwd(const float* __restrict__ means, const float* __restrict__ log_sca
         for (int c = 0; c < 3; ++c)
             gM[3 * r + c] = 2.0f * (Gs[3 * r] * M[c] + Gs[3 * r + 1] * M[3 + c] +
                                     Gs[3 * r + 2] * M[6 + c]);
-    float gls[3], gR[9];
+    float gR[9];
     for (int c = 0; c < 3; ++c) {
         const float gsc = gM[c] * R[c] + gM[3 + c] * R[3 + c] + gM[6 + c] * R[6 + c];
         gls[c] = gsc * shp.s[c];
@@ -529,10 +513,32 @@ k_project_bwd(const float* __restrict__ means, const float* __restrict__ log_sca
     // qn = q / |q|
     const float dq = gq[0] * w + gq[1] * x + gq[2] * y + gq[3] * z;
     const float iq = 1.0f / shp.qnorm;
-    float4 gq4 = make_float4((gq[0] - w * dq) * iq, (gq[1] - x * dq) * iq, (gq[2] - y * dq) * iq,
-                             (gq[3] - z * dq) * iq);
-    const float glog = gop * opacity * (1.0f - opacity);
+    gq4 = make_float4((gq[0] - w * dq) * iq, (gq[1] - x * dq) * iq, (gq[2] - y * dq) * iq,
+                      (gq[3] - z * dq) * iq);
+    glog = gop * opacity * (1.0f - opacity);
+#pragma unroll
+    for (int e = 0; e < 3; ++e) gm_out[e] = gm[e];
+}
 
+
+template <int DEG>
+__global__ void __launch_bounds__(kProjThreads)
+k_project_bwd(const float* __restrict__ means, const float* __restrict__ log_scales,
+              const float* __restrict__ quats, const float* __restrict__ opacity_logits,
+              const float* __restrict__ sh, int n, const gs_view* __restrict__ views,
+              ViewTable vt, float near_z, const uint32_t* __restrict__ touched,
+              const float* __restrict__ grad2d, float* __restrict__ gcol_out,
+              float* __restrict__ g_means, float* __restrict__ g_ls, float* __restrict__ g_quats,
+              float* __restrict__ g_logit, int accumulate) {
+    extern __shared__ Cam cam_all[];
+    for (int v = threadIdx.x; v < vt.n_views; v += blockDim.x) load_cam(views[v], cam_all[v]);
+    __syncthreads();
+    const int g = blockIdx.x * blockDim.x + threadIdx.x;
+    if (g >= n) return;
+    float gm[3], gls[3], glog;
+    float4 gq4;
+    adjoint_one<DEG, false>(g, means, log_scales, quats, opacity_logits, sh, n, cam_all, vt,
+                            near_z, touched, grad2d, gcol_out, nullptr, 0, gm, gls, gq4, glog);
     if (accumulate) {
         for (int e = 0; e < 3; ++e) {
             g_means[3 * g + e] += gm[e];
@@ -555,41 +561,22 @@ k_project_bwd(const float* __restrict__ means, const float* __restrict__ log_sca
 // Gradient of the SH coefficients: sum over views of Y_k(dir_v) gcol_v, with
 // gcol the colour gradient k_project_bwd left (zero on clamped channels, a
 // grayscale view's gradient spread over the three channels).
-//
-// With ADAM the whole Adam step of the warp's 32 Gaussians follows in the
-// same kernel, on every parameter group.  A thread's own coefficients lie
-// N*3 floats apart in the [K][N][3] SH planes, so each warp passes its SH
-// gradients through shared memory ([k][lane*3 + c], conflict-free) and then
-// updates runs of consecutive floats: the means, log-scales, quaternions and
-// opacities of its 32 Gaussians (96, 96, 128 and 32 floats) and, per
-// coefficient k, 96 floats of SH; see adam_run.  Launched with
-// kShAdamThreads threads so the staging fits the default shared memory.
-constexpr int kShAdamThreads = 128;
-
-template <int DEG, bool ADAM>
+template <int DEG>
 __global__ void __launch_bounds__(kProjThreads)
-k_sh_bwd(const float* means, int n, const gs_view* __restrict__ views,
-         ViewTable vt, const uint32_t* __restrict__ touched, const float* __restrict__ gcol_in,
-         float* __restrict__ g_sh, int accumulate, FusedAdam fa) {
+k_sh_bwd(const float* means, int n, const gs_view* __restrict__ views, ViewTable vt,
+         const uint32_t* __restrict__ touched, const float* __restrict__ gcol_in,
+         float* __restrict__ g_sh, int accumulate) {
     extern __shared__ Cam cam_all[];
-    __shared__ float s_bc[2];
     for (int v = threadIdx.x; v < vt.n_views; v += blockDim.x) load_cam(views[v], cam_all[v]);
-    if (ADAM && threadIdx.x == 0) adam_bias(fa.b1, fa.b2, *fa.step, s_bc[0], s_bc[1]);
     __syncthreads();
     const int g = blockIdx.x * blockDim.x + threadIdx.x;
-    if (!ADAM && g >= n) return;
-    const bool valid = g < n;  // (ADAM keeps every lane for the warp-wide update)
+    if (g >= n) return;
     constexpr int K = (DEG + 1) * (DEG + 1);
-    float mean[3] = {0.f, 0.f, 0.f};
-    if (valid) {
-        mean[0] = means[3 * g];
-        mean[1] = means[3 * g + 1];
-        mean[2] = means[3 * g + 2];
-    }
+    const float mean[3] = {means[3 * g], means[3 * g + 1], means[3 * g + 2]};
     float acc[K][3];
 #pragma unroll
     for (int k = 0; k < K; ++k) acc[k][0] = acc[k][1] = acc[k][2] = 0.0f;
-    for (int v = 0; valid && v < vt.n_views; ++v) {
+    for (int v = 0; v < vt.n_views; ++v) {
         const size_t vg = (size_t)v * n + g;
         if (touched[vg] == 0u) continue;
         const float* gc = gcol_in + vg * 3;
@@ -607,54 +594,199 @@ k_sh_bwd(const float* means, int n, const gs_view* __restrict__ views,
             acc[k][2] = fmaf(Y[k], c2, acc[k][2]);
         }
     }
-    if (ADAM) {
-        const float ibc1 = s_bc[0], ibc2 = s_bc[1];
-        float* stage = reinterpret_cast<float*>(cam_all + vt.n_views) +
-                       (size_t)(threadIdx.x >> 5) * (K * 96);
-        const int lane = threadIdx.x & 31;
 #pragma unroll
-        for (int k = 0; k < K; ++k) {
-            stage[k * 96 + lane * 3 + 0] = acc[k][0];
-            stage[k * 96 + lane * 3 + 1] = acc[k][1];
-            stage[k * 96 + lane * 3 + 2] = acc[k][2];
-        }
-        __syncwarp();
-        const int g0 = blockIdx.x * blockDim.x + (threadIdx.x & ~31);
-        if (g0 >= n) return;  // the whole warp: nothing of it is in the map
-        const int nw = n - g0 < 32 ? n - g0 : 32;
-        auto opt = [](const float* a, size_t o) { return a ? a + o : nullptr; };
-        auto opto = [](float* a, size_t o) { return a ? a + o : nullptr; };
-        const size_t o3 = (size_t)g0 * 3, o4 = (size_t)g0 * 4, o1 = (size_t)g0;
-        adam_run(fa.p_means + o3, fa.m_means + o3, fa.v_means + o3, fa.s_means + o3,
-                 opt(fa.a_means, o3), opto(fa.o_means, o3), 3 * nw, fa.lr[0], fa, ibc1, ibc2);
-        adam_run(fa.p_ls + o3, fa.m_ls + o3, fa.v_ls + o3, fa.s_ls + o3, opt(fa.a_ls, o3),
-                 opto(fa.o_ls, o3), 3 * nw, fa.lr[1], fa, ibc1, ibc2);
-        adam_run(fa.p_quats + o4, fa.m_quats + o4, fa.v_quats + o4, fa.s_quats + o4,
-                 opt(fa.a_quats, o4), opto(fa.o_quats, o4), 4 * nw, fa.lr[2], fa, ibc1, ibc2);
-        adam_run(fa.p_logit + o1, fa.m_logit + o1, fa.v_logit + o1, fa.s_logit + o1,
-                 opt(fa.a_logit, o1), opto(fa.o_logit, o1), nw, fa.lr[3], fa, ibc1, ibc2);
-#pragma unroll 2
-        for (int k = 0; k < K; ++k) {
-            const size_t base = ((size_t)k * n + g0) * 3;
-            adam_run(fa.p_sh + base, fa.m_sh + base, fa.v_sh + base, stage + k * 96,
-                     opt(fa.a_sh, base), opto(fa.o_sh, base), 3 * nw,
-                     k == 0 ? fa.lr[4] : fa.lr[5], fa, ibc1, ibc2);
-        }
-    } else {
-#pragma unroll
-        for (int k = 0; k < K; ++k) {
-            float* o = g_sh + ((size_t)k * n + g) * 3;
-            if (accumulate) {
-                o[0] += acc[k][0];
-                o[1] += acc[k][1];
-                o[2] += acc[k][2];
-            } else {
-                o[0] = acc[k][0];
-                o[1] = acc[k][1];
-                o[2] = acc[k][2];
-            }
+    for (int k = 0; k < K; ++k) {
+        float* o = g_sh + ((size_t)k * n + g) * 3;
+        if (accumulate) {
+            o[0] += acc[k][0];
+            o[1] += acc[k][1];
+            o[2] += acc[k][2];
+        } else {
+            o[0] = acc[k][0];
+            o[1] = acc[k][1];
+            o[2] = acc[k][2];
         }
     }
+}
+
+// A8 + A9 in one pass over a chunk of kFuseThreads consecutive Gaussians.
+//
+// Phase 1 (a thread per Gaussian): the projection adjoint (adjoint_one) with
+// the gradients staged in shared memory in the order of the parameter
+// arrays: means [3c], log-scales [3c], quaternions [4c], logits [c], then one
+// [3c] run per SH coefficient plane (the [K][N][3] layout), c = kFuseThreads.
+// Phase 2 (a thread per float): Adam over those runs, each a contiguous
+// range of a parameter array and of its two moments; every run is a multiple
+// of kFuseThreads floats, so a warp always works inside one run and each of
+// its loads and stores is one 128-byte line.  Up to six runs per thread are
+// loaded before any is updated, for enough bytes in flight.  The gradients
+// never go to global memory unless asked for (grads_out).
+constexpr int kFuseThreads = 128;
+constexpr int kFuseMinBlocks = 4;
+constexpr int kShPlanes = 4;  // SH planes per Adam batch (3 runs each)
+static_assert((11 + 3 * 16) * kFuseThreads * sizeof(float) + sizeof(Cam) * GS_MAX_VIEWS <=
+                  48 * 1024,
+              "the fused stage fits the default dynamic shared memory");
+
+// Adam on NP planes x NR runs of kFuseThreads floats of one parameter array:
+// run j of plane q starts at float off + q * plane_stride + j * kFuseThreads
+// and holds the floats below `total` of its plane; its gradient is at
+// g + (q * NR + j) * kFuseThreads in shared memory (plus add, if given).
+// lr_first applies to plane 0, lr_rest to the others.  All NP * NR loads of
+// a thread are issued before any update.
+struct AdamRuns {
+    float b1, b2, eps, ibc1, ibc2;
+    int t;
+    template <int NP, int NR>
+    __device__ __forceinline__ void run(float* __restrict__ p, float* __restrict__ m,
+                                        float* __restrict__ v, const float* __restrict__ add,
+                                        float* __restrict__ out, size_t off, size_t plane_stride,
+                                        int total, const float* g, float lr_first,
+                                        float lr_rest) const {
+        constexpr int U = NP * NR;
+        float pp[U], mm[U], vv[U], gg[U];
+#pragma unroll
+        for (int q = 0; q < NP; ++q)
+#pragma unroll
+            for (int j = 0; j < NR; ++j) {
+                const int u = q * NR + j;
+                const size_t i = off + q * plane_stride + (size_t)j * kFuseThreads + t;
+                if (j * kFuseThreads + t < total) {
+                    gg[u] = g[u * kFuseThreads + t];
+                    if (add) gg[u] += add[i];
+                    pp[u] = p[i];
+                    mm[u] = m[i];
+                    vv[u] = v[i];
+                }
+            }
+#pragma unroll
+        for (int q = 0; q < NP; ++q)
+#pragma unroll
+            for (int j = 0; j < NR; ++j) {
+                const int u = q * NR + j;
+                const size_t i = off + q * plane_stride + (size_t)j * kFuseThreads + t;
+                if (j * kFuseThreads + t < total) {
+                    adam1(pp[u], gg[u], mm[u], vv[u], q == 0 ? lr_first : lr_rest, b1, b2, eps,
+                          ibc1, ibc2);
+                    p[i] = pp[u];
+                    m[i] = mm[u];
+                    v[i] = vv[u];
+                    if (out) out[i] = gg[u];
+                }
+            }
+    }
+};
+
+// Run r (of 11 + 3K) of the chunk of Gaussians [g0, g0 + cnt): its group
+// (0 means, 1 log-scales, 2 quaternions, 3 logits, 4 SH), the offset of its
+// first float in that group's array and the number of its floats in use.
+template <int K>
+__device__ __forceinline__ void run_of(int r, int g0, int cnt, int n, int& grp, size_t& off,
+                                       int& len) {
+    constexpr int C = kFuseThreads;
+    if (r < 6) {
+        grp = r / 3; off = (size_t)3 * g0 + (size_t)(r % 3) * C; len = 3 * cnt - (r % 3) * C;
+    } else if (r < 10) {
+        grp = 2; off = (size_t)4 * g0 + (size_t)(r - 6) * C; len = 4 * cnt - (r - 6) * C;
+    } else if (r < 11) {
+        grp = 3; off = (size_t)g0; len = cnt;
+    } else {
+        const int k = (r - 11) / 3, j = (r - 11) % 3;
+        grp = 4; off = ((size_t)k * n + g0) * 3 + (size_t)j * C; len = 3 * cnt - j * C;
+    }
+}
+
+// Parameter (a = 0), first moment (1) or second moment (2) array of group grp.
+__device__ __forceinline__ const float* state_array(const FusedAdam& fa, int a, int grp) {
+    auto pick = [grp](const float* g0, const float* g1, const float* g2, const float* g3,
+                      const float* g4) {
+        return grp == 0 ? g0 : grp == 1 ? g1 : grp == 2 ? g2 : grp == 3 ? g3 : g4;
+    };
+    return a == 0   ? pick(fa.p_means, fa.p_ls, fa.p_quats, fa.p_logit, fa.p_sh)
+           : a == 1 ? pick(fa.m_means, fa.m_ls, fa.m_quats, fa.m_logit, fa.m_sh)
+                    : pick(fa.v_means, fa.v_ls, fa.v_quats, fa.v_logit, fa.v_sh);
+}
+
+template <int DEG>
+__global__ void __launch_bounds__(kFuseThreads, kFuseMinBlocks)
+k_adjoint_adam(const float* __restrict__ means, const float* __restrict__ log_scales,
+               const float* __restrict__ quats, const float* __restrict__ opacity_logits,
+               const float* __restrict__ sh, int n, const gs_view* __restrict__ views,
+               ViewTable vt, float near_z, const uint32_t* __restrict__ touched,
+               const float* __restrict__ grad2d, FusedAdam fa) {
+    constexpr int K = (DEG + 1) * (DEG + 1);
+    constexpr int C = kFuseThreads;
+    constexpr int kRuns = 11 + 3 * K;  // runs of C floats per chunk
+    extern __shared__ float4 fuse_smem[];
+    float* stage = reinterpret_cast<float*>(fuse_smem);  // kRuns * C floats
+    Cam* cam_all = reinterpret_cast<Cam*>(stage + kRuns * C);
+    __shared__ float s_bc[2];
+    for (int v = threadIdx.x; v < vt.n_views; v += blockDim.x) load_cam(views[v], cam_all[v]);
+    if (threadIdx.x == 0) adam_bias(fa.b1, fa.b2, *fa.step, s_bc[0], s_bc[1]);
+    const int t = threadIdx.x;
+    const int g0 = blockIdx.x * C;
+    const int cnt = min(C, n - g0);
+    // Ask L2 for the chunk's parameters and moments now, so that their DRAM
+    // reads overlap the adjoint below: each of the kRuns runs of the three
+    // arrays is C floats = 4 lines of 128 bytes; a thread takes every C-th
+    // line, only lines that phase 2 will load.
+    {
+        constexpr int kLines = kRuns * 3 * (C / 32);
+        for (int L = t; L < kLines; L += C) {
+            const int r = L / (3 * (C / 32)), a = (L / (C / 32)) % 3, line = L % (C / 32);
+            int grp, len;
+            size_t off;
+            run_of<K>(r, g0, cnt, n, grp, off, len);
+            if (line * 32 < len)
+                asm volatile("prefetch.global.L2 [%0];" ::"l"(state_array(fa, a, grp) + off +
+                                                              line * 32));
+        }
+    }
+    float* sh_acc = stage + 11 * C + 3 * t;
+#pragma unroll
+    for (int k = 0; k < 3 * K; ++k) sh_acc[(k / 3) * 3 * C + k % 3] = 0.0f;
+    __syncthreads();
+    if (t < cnt) {
+        float gm[3], gls[3], glog;
+        float4 gq4;
+        adjoint_one<DEG, true>(g0 + t, means, log_scales, quats, opacity_logits, sh, n, cam_all,
+                               vt, near_z, touched, grad2d, nullptr, sh_acc, 3 * C, gm, gls, gq4,
+                               glog);
+#pragma unroll
+        for (int e = 0; e < 3; ++e) {
+            stage[3 * t + e] = gm[e];
+            stage[3 * C + 3 * t + e] = gls[e];
+        }
+        stage[6 * C + 4 * t + 0] = gq4.x;
+        stage[6 * C + 4 * t + 1] = gq4.y;
+        stage[6 * C + 4 * t + 2] = gq4.z;
+        stage[6 * C + 4 * t + 3] = gq4.w;
+        stage[10 * C + t] = glog;
+    }
+    __syncthreads();
+    const AdamRuns ar{fa.b1, fa.b2, fa.eps, s_bc[0], s_bc[1], t};
+    const size_t o3 = (size_t)3 * g0, o4 = (size_t)4 * g0;
+    ar.run<1, 3>(fa.p_means, fa.m_means, fa.v_means, fa.a_means, fa.o_means, o3, 0, 3 * cnt,
+                 stage, fa.lr[0], fa.lr[0]);
+    ar.run<1, 3>(fa.p_ls, fa.m_ls, fa.v_ls, fa.a_ls, fa.o_ls, o3, 0, 3 * cnt, stage + 3 * C,
+                 fa.lr[1], fa.lr[1]);
+    ar.run<1, 4>(fa.p_quats, fa.m_quats, fa.v_quats, fa.a_quats, fa.o_quats, o4, 0, 4 * cnt,
+                 stage + 6 * C, fa.lr[2], fa.lr[2]);
+    ar.run<1, 1>(fa.p_logit, fa.m_logit, fa.v_logit, fa.a_logit, fa.o_logit, (size_t)g0, 0, cnt,
+                 stage + 10 * C, fa.lr[3], fa.lr[3]);
+    // SH: kShPlanes coefficient planes at a time; plane 0 takes the DC rate
+    const size_t ps = (size_t)3 * n;
+    int k = 0;
+    for (; k + kShPlanes <= K; k += kShPlanes)
+        ar.run<kShPlanes, 3>(fa.p_sh, fa.m_sh, fa.v_sh, fa.a_sh, fa.o_sh, k * ps + o3, ps,
+                             3 * cnt, stage + (11 + 3 * k) * C, k == 0 ? fa.lr[4] : fa.lr[5],
+                             fa.lr[5]);
+    for (; k + 2 <= K; k += 2)
+        ar.run<2, 3>(fa.p_sh, fa.m_sh, fa.v_sh, fa.a_sh, fa.o_sh, k * ps + o3, ps, 3 * cnt,
+                     stage + (11 + 3 * k) * C, k == 0 ? fa.lr[4] : fa.lr[5], fa.lr[5]);
+    if (k < K)
+        ar.run<1, 3>(fa.p_sh, fa.m_sh, fa.v_sh, fa.a_sh, fa.o_sh, k * ps + o3, ps, 3 * cnt,
+                     stage + (11 + 3 * k) * C, k == 0 ? fa.lr[4] : fa.lr[5], fa.lr[5]);
 }
 
 }  // namespace
@@ -705,14 +837,13 @@ gs_status launch_project_bwd(const Plan* p, const gs_map* map, const gs_view* vi
     gs_status s = launch_project_adjoint(p, map, views_dev, ws, grads, accumulate, st);
     if (s != GS_OK) return s;
     const int n = map->n;
-    auto* kern_sh = map->sh_degree == 0   ? k_sh_bwd<0, false>
-                    : map->sh_degree == 1 ? k_sh_bwd<1, false>
-                    : map->sh_degree == 2 ? k_sh_bwd<2, false>
-                                          : k_sh_bwd<3, false>;
-    FusedAdam fa{};
+    auto* kern_sh = map->sh_degree == 0   ? k_sh_bwd<0>
+                    : map->sh_degree == 1 ? k_sh_bwd<1>
+                    : map->sh_degree == 2 ? k_sh_bwd<2>
+                                          : k_sh_bwd<3>;
     kern_sh<<<(n + kProjThreads - 1) / kProjThreads, kProjThreads, sizeof(Cam) * p->vt.n_views,
               st>>>(map->means, n, views_dev, p->vt, buf<uint32_t>(p, ws, GS_BUF_TOUCHED),
-                    buf<float>(p, ws, B_GCOL), grads->sh, accumulate, fa);
+                    buf<float>(p, ws, B_GCOL), grads->sh, accumulate);
     return launch_status();
 }
 
@@ -749,32 +880,20 @@ gs_status launch_project_bwd_adam(const Plan* p, const gs_map* map, const gs_vie
         fa.o_quats = grads_out->quats; fa.o_logit = grads_out->opacity_logits;
         fa.o_sh = grads_out->sh;
     }
-    // this pass's per-Gaussian gradients: quaternions first (16-byte rows)
-    const int n = map->n;
-    float* scratch = buf<float>(p, ws, B_GPARAM);
-    gs_map_grad sg{};
-    sg.quats = scratch;
-    sg.means = scratch + 4 * (size_t)n;
-    sg.log_scales = scratch + 7 * (size_t)n;
-    sg.opacity_logits = scratch + 10 * (size_t)n;
-    fa.s_quats = sg.quats;
-    fa.s_means = sg.means;
-    fa.s_ls = sg.log_scales;
-    fa.s_logit = sg.opacity_logits;
     gs_status s = launch_step_inc(step_dev, st);
     if (s != GS_OK) return s;
-    s = launch_project_adjoint(p, map, views_dev, ws, &sg, 0, st);
-    if (s != GS_OK) return s;
+    const int n = map->n;
     const int K = (map->sh_degree + 1) * (map->sh_degree + 1);
     const size_t smem =
-        sizeof(Cam) * p->vt.n_views + (size_t)(kShAdamThreads / 32) * K * 96 * sizeof(float);
-    auto* kern_sh = map->sh_degree == 0   ? k_sh_bwd<0, true>
-                    : map->sh_degree == 1 ? k_sh_bwd<1, true>
-                    : map->sh_degree == 2 ? k_sh_bwd<2, true>
-                                          : k_sh_bwd<3, true>;
-    kern_sh<<<(n + kShAdamThreads - 1) / kShAdamThreads, kShAdamThreads, smem, st>>>(
-        map->means, n, views_dev, p->vt, buf<uint32_t>(p, ws, GS_BUF_TOUCHED),
-        buf<float>(p, ws, B_GCOL), nullptr, 0, fa);
+        (size_t)(11 + 3 * K) * kFuseThreads * sizeof(float) + sizeof(Cam) * p->vt.n_views;
+    auto* kern = map->sh_degree == 0   ? k_adjoint_adam<0>
+                 : map->sh_degree == 1 ? k_adjoint_adam<1>
+                 : map->sh_degree == 2 ? k_adjoint_adam<2>
+                                       : k_adjoint_adam<3>;
+    kern<<<(n + kFuseThreads - 1) / kFuseThreads, kFuseThreads, smem, st>>>(
+        map->means, map->log_scales, map->quats, map->opacity_logits, map->sh, n, views_dev,
+        p->vt, p->cfg.near_z, buf<uint32_t>(p, ws, GS_BUF_TOUCHED),
+        buf<float>(p, ws, GS_BUF_GRAD2D), fa);
     return launch_status();
 }
 

@@ -324,12 +324,26 @@ def test_split_backward_equals_combined():
     assert U.rel_l2(twice, 2.0 * out[1]) < 1e-6
 
 
-def test_fused_projection_adjoint_adam_is_bit_identical():
+FUSED_CASES = {
+    # 600 Gaussians: four full chunks of the fused kernel and a ragged one
+    "tiny_sh3_posed": lambda: (CASES["tiny_sh3_posed"]()[0], [CASES["tiny_sh3_posed"]()[1]]),
+    # SH degree 0, 10k Gaussians
+    "planes10k": lambda: (CASES["planes10k"]()[0], [CASES["planes10k"]()[1]]),
+    # three views of different sizes, one grayscale: gradients summed over views
+    "room20k_three_views": lambda: (scenes.room_scene(20_000, seed=41), [
+        scenes.camera(160, 120, 131.25, 131.25),
+        dict(scenes.camera(188, 120, 115.0, 115.0, channels=1)),
+        posed(scenes.camera(300, 170, 150.0, 150.0), 7, 0.2, 10.0)]),
+}
+
+
+@pytest.mark.parametrize("case", list(FUSED_CASES))
+def test_fused_projection_adjoint_adam_is_bit_identical(case):
     """gs_project_bwd_adam equals gs_project_bwd into a zeroed gradient followed
     by gs_adam_step, bit for bit, from the same screen-space gradients; with
     grads_acc it adds the given gradients first."""
-    p, view = CASES["tiny_sh3_posed"]()
-    target = scenes.random_target(view, 51)
+    p, views = FUSED_CASES[case]()
+    targets = [scenes.random_target(v, 51 + i) for i, v in enumerate(views)]
     g1, g2 = mapping.GaussianMap(p), mapping.GaussianMap(p)
     for gm in (g1, g2):  # non-trivial moments and step count
         gm.m.normal_(0, 1e-3)
@@ -337,9 +351,9 @@ def test_fused_projection_adjoint_adam_is_bit_identical():
         gm.step.fill_(3)
     g2.m.copy_(g1.m)
     g2.v.copy_(g1.v)
-    rast = mapping.Rasterizer([view], g1.n, instance_capacity=1 << 18)
+    rast = mapping.Rasterizer(views, g1.n, instance_capacity=1 << 21)
     rast.forward(g1.gs_map())
-    rast.loss_l1_ssim(rast.pack([target]), 0.2)
+    rast.loss_l1_ssim(rast.pack(targets), 0.2)
     rast.render_bwd_pixels()
     rast.project_bwd(g1.gs_map(), g1.gs_map_grad())
     g1.adam_step()
@@ -348,6 +362,7 @@ def test_fused_projection_adjoint_adam_is_bit_identical():
     torch.cuda.synchronize()
     assert g1.step.item() == g2.step.item() == 4
     groups = lambda gm, buf: torch.cat([t.reshape(-1) for t in gm._views(buf).values()])
+    assert groups(g1, g1.grad).abs().sum() > 0
     for a, b in ((g1.grad, g2.grad), (g1.data, g2.data), (g1.m, g2.m), (g1.v, g2.v)):
         assert torch.equal(groups(g1, a), groups(g2, b))
     # accumulation: grads_acc = the same gradient again doubles it
