@@ -320,7 +320,8 @@ constexpr size_t kNoAllocBytes = kNoAllocMapsOffset + 3 * kNoAllocMaxValues * si
 static __device__ __align__(256) unsigned char g_noalloc_scratch[kNoAllocBytes];
 
 std::mutex g_noalloc_mutex;
-void* g_noalloc_addr[GS_MAX_VIEWS] = {nullptr};  // per device ordinal
+constexpr int kNoAllocMaxDevices = 64;
+void* g_noalloc_addr[kNoAllocMaxDevices] = {nullptr};  // per device ordinal
 
 // Device address of the scratch array on the current device.  In host code
 // the array's name is only a host-side stand-in, so the address is looked up
@@ -328,7 +329,7 @@ void* g_noalloc_addr[GS_MAX_VIEWS] = {nullptr};  // per device ordinal
 gs_status noalloc_scratch(void** out) {
     int dev = 0;
     if (cudaGetDevice(&dev) != cudaSuccess) return GS_ERR_CUDA;
-    if (dev < 0 || dev >= GS_MAX_VIEWS) return GS_ERR_UNSUPPORTED;
+    if (dev < 0 || dev >= kNoAllocMaxDevices) return GS_ERR_UNSUPPORTED;
     std::lock_guard<std::mutex> lock(g_noalloc_mutex);
     if (g_noalloc_addr[dev] == nullptr) {
         void* p = nullptr;
