@@ -37,6 +37,9 @@ GUARD_RECT, GUARD_NEAR, GUARD_DET, GUARD_KINK, GUARD_DEPTH = 1, 2, 4, 8, 16
 GPX_ALPHA, GPX_TRANS, GPX_POWER, GPX_KINK = 1, 2, 4, 16
 
 NEAR_Z = 0.2
+# Tile rects cut to the tiles that can receive alpha >= 1/255 (reading C4'),
+# the default of the GPU path too; tight=False gives the plain 3-sigma squares.
+TIGHT_RECT = True
 
 
 def build(force: bool = False) -> str:
@@ -107,8 +110,10 @@ def ssim_window() -> np.ndarray:
     return out
 
 
-def project(params, view, tile_w=16, tile_h=16, near_z=NEAR_Z):
-    """Projection of all Gaussians into one view (Sec. II / Sec. III-B)."""
+def project(params, view, tile_w=16, tile_h=16, near_z=NEAR_Z, tight=TIGHT_RECT):
+    """Projection of all Gaussians into one view (Sec. II / Sec. III-B).
+    tight: tile rects cut to the tiles that can receive alpha >= 1/255
+    (reading C4' in gs_oracle.c); the rendered image is the same."""
     n = params["means"].shape[0]
     deg = int(params["sh_degree"])
     means, ls, q = _d(params["means"]), _d(params["log_scales"]), _d(params["quats"])
@@ -123,7 +128,7 @@ def project(params, view, tile_w=16, tile_h=16, near_z=NEAR_Z):
         _i(view["width"]), _i(view["height"]), _i(tile_w), _i(tile_h), _f(near_z),
         _p(out["mean2d"]), _p(out["depth"]), _p(out["cov2d"]), _p(out["conic"]),
         _p(out["opacity"]), _p(out["rgb"]), _p(out["clamped"]), _p(out["radius"]),
-        _p(out["rect"]), _p(out["tiles_touched"]), _p(out["guard"]))
+        _p(out["rect"]), _p(out["tiles_touched"]), _p(out["guard"]), _i(1 if tight else 0))
     out["n_visible"] = nvis
     return out
 
@@ -201,7 +206,8 @@ def zero_grads(params):
                 opacity_logits=np.zeros(n), sh=np.zeros((K, n, 3)))
 
 
-def project_bwd(params, view, g2d, grads=None, tile_w=16, tile_h=16, near_z=NEAR_Z):
+def project_bwd(params, view, g2d, grads=None, tile_w=16, tile_h=16, near_z=NEAR_Z,
+                tight=TIGHT_RECT):
     """Adjoint of `project`: parameter gradients, accumulated into `grads`."""
     if grads is None:
         grads = zero_grads(params)
@@ -213,7 +219,7 @@ def project_bwd(params, view, g2d, grads=None, tile_w=16, tile_h=16, near_z=NEAR
         _i(view["width"]), _i(view["height"]), _i(tile_w), _i(tile_h), _f(near_z),
         _p(_d(g2d["dmean2d"])), _p(_d(g2d["dconic"])), _p(_d(g2d["dopacity"])),
         _p(_d(g2d["drgb"])), _p(grads["means"]), _p(grads["log_scales"]), _p(grads["quats"]),
-        _p(grads["opacity_logits"]), _p(grads["sh"]))
+        _p(grads["opacity_logits"]), _p(grads["sh"]), _i(1 if tight else 0))
     return grads
 
 
@@ -256,9 +262,10 @@ def adam_masked(p, g, m, v, lr, step, mask, b1=0.9, b2=0.999, eps=1e-15):
 # --------------------------------------------------------------------------
 # Composition: a whole view, a whole mapping iteration.
 # --------------------------------------------------------------------------
-def forward_view(params, view, tile_w=16, tile_h=16, bg=(0.0, 0.0, 0.0), near_z=NEAR_Z):
+def forward_view(params, view, tile_w=16, tile_h=16, bg=(0.0, 0.0, 0.0), near_z=NEAR_Z,
+                 tight=TIGHT_RECT):
     """project -> bin -> render for one view; returns (proj, tile_start, list, render_out)."""
-    proj = project(params, view, tile_w, tile_h, near_z)
+    proj = project(params, view, tile_w, tile_h, near_z, tight)
     tx, ty = tile_grid(view["width"], view["height"], tile_w, tile_h)
     start, lst = bin_tiles(proj["depth"].astype(np.float32), proj["rect"],
                            proj["tiles_touched"], tx, ty)
@@ -270,7 +277,7 @@ PARAM_GROUPS = ("means", "log_scales", "quats", "opacity_logits", "sh")
 
 
 def iteration(params, views, targets, lam, tile_w=16, tile_h=16, bg=(0.0, 0.0, 0.0),
-              near_z=NEAR_Z, stats=None):
+              near_z=NEAR_Z, stats=None, tight=TIGHT_RECT):
     """Loss (mean over views) and parameter gradients (sum of per-view adjoints).
     With stats = (accum, denom) the density-control statistic of this
     iteration is added to them (densify_stats)."""
@@ -279,11 +286,11 @@ def iteration(params, views, targets, lam, tile_w=16, tile_h=16, bg=(0.0, 0.0, 0
     renders = []
     V = len(views)
     for view, tgt in zip(views, targets):
-        proj, start, lst, out = forward_view(params, view, tile_w, tile_h, bg, near_z)
+        proj, start, lst, out = forward_view(params, view, tile_w, tile_h, bg, near_z, tight)
         L, dimg = loss_l1_ssim(out["image"], tgt, lam)
         total += L / V
         g2d = render_bwd(proj, start, lst, view, dimg / V, tile_w, tile_h, bg)
-        project_bwd(params, view, g2d, grads, tile_w, tile_h, near_z)
+        project_bwd(params, view, g2d, grads, tile_w, tile_h, near_z, tight)
         if stats is not None:
             densify_stats(stats[0], stats[1], view, proj["tiles_touched"], g2d["dmean2d_abs"])
         renders.append(out)

@@ -74,6 +74,66 @@ static int near_int(double v, double margin) {
     return fabs(v - r) < margin;
 }
 
+/*
+ * Tile rect of one projected Gaussian, [x0,y0,x1,y1) clamped to the grid, and
+ * its radius r; returns the area (0: the Gaussian draws into no tile).
+ *
+ * Square rect (reading C4): [floor((mu-r)/t), floor((mu+r+t-1)/t)) with
+ * r = ceil(3 sqrt(lambda_max)) of the dilated 2D covariance.
+ *
+ * tight = 1 (reading C4'): the square rect intersected with the tiles that
+ * meet the axis-aligned box of the ellipse outside which alpha < 1/255.
+ * alpha = min(0.99, o exp(-q/2)) with q = d^T cov^-1 d, so alpha >= 1/255
+ * needs q <= t_a = 2 ln(255 o), and the ellipse q <= t_a has half-widths
+ * sqrt(t_a cov_xx), sqrt(t_a cov_yy).  A tile left out has no pixel that
+ * the renderer would blend: the rect shrinks, the image does not.  The level
+ * is widened to t = 1.01 t_a + 0.01 so that no FP32 evaluation of alpha near
+ * the ellipse can reach 1/255 in a dropped tile; with o < 0.999/255 no pixel
+ * reaches it at all and the rect is empty.  Pixel x of tile k satisfies
+ * k t <= x <= k t + t - 1, so tiles [ceil((mu - h - t + 1)/t), floor((mu + h)/t)]
+ * meet [mu - h, mu + h].
+ */
+#define OR_TIGHT_MIN_OPACITY (0.999 / 255.0)
+#define OR_G_TIGHT 1e-4 /* tight rect edges in tile units, relative to 1 + h / t */
+
+static int tile_rect(const double mean2d[2], const double cov[3], double det, double opacity,
+                     int tile_w, int tile_h, int tiles_x, int tiles_y, int tight, int rc[4],
+                     int *r_out, int *guard) {
+    double mid = 0.5 * (cov[0] + cov[2]);
+    double lam = mid + sqrt(fmax(0.0, mid * mid - det));
+    double ext = OR_SIGMAS * sqrt(lam);
+    int r = (int)ceil(ext);
+    *r_out = r;
+    if (near_int(ext, OR_G_RADIUS * fmax(1.0, ext))) *guard |= OR_GUARD_RECT;
+    double ex[4] = {(mean2d[0] - r) / tile_w, (mean2d[1] - r) / tile_h,
+                    (mean2d[0] + r + tile_w - 1) / tile_w, (mean2d[1] + r + tile_h - 1) / tile_h};
+    int lim[4] = {tiles_x, tiles_y, tiles_x, tiles_y};
+    for (int k = 0; k < 4; k++) {
+        double f = floor(ex[k]);
+        if (near_int(ex[k], OR_G_TILE) && f >= -1.0 && f <= lim[k]) *guard |= OR_GUARD_RECT;
+        rc[k] = f < 0.0 ? 0 : (f > lim[k] ? lim[k] : (int)f);
+    }
+    if (tight) {
+        if (fabs(opacity - OR_TIGHT_MIN_OPACITY) < 1e-6 * OR_TIGHT_MIN_OPACITY)
+            *guard |= OR_GUARD_RECT;
+        if (!(opacity >= OR_TIGHT_MIN_OPACITY)) return 0;
+        double t = 1.01 * (2.0 * log(255.0 * opacity)) + 0.01;
+        double h[2] = {sqrt(t * cov[0]), sqrt(t * cov[2])};
+        double tl[2] = {tile_w, tile_h};
+        for (int a = 0; a < 2; a++) {
+            double lo = (mean2d[a] - h[a] - tl[a] + 1.0) / tl[a];
+            double hi = (mean2d[a] + h[a]) / tl[a];
+            double margin = OR_G_TIGHT * (1.0 + h[a] / tl[a]);
+            if (near_int(lo, margin) || near_int(hi, margin)) *guard |= OR_GUARD_RECT;
+            double klo = ceil(lo), khi = floor(hi) + 1.0;
+            if (klo > rc[a]) rc[a] = klo > lim[a] ? lim[a] : (int)klo;
+            if (khi < rc[a + 2]) rc[a + 2] = khi < 0.0 ? 0 : (int)khi;
+        }
+    }
+    int w = rc[2] - rc[0], hgt = rc[3] - rc[1];
+    return (w > 0 && hgt > 0) ? w * hgt : 0;
+}
+
 /* ------------------------------------------------------------------------ */
 /* Real spherical harmonics, degrees 0..3.                                  */
 /* Reading of the colour model: the paper renders plain RGB (Sec. III-B,   */
@@ -366,7 +426,7 @@ int oracle_project(int n, int degree, const double *means, const double *log_sca
                    const double *cam, int W, int H, int tile_w, int tile_h, double near_z,
                    double *mean2d, double *depth, double *cov2d, double *conic, double *opacity,
                    double *rgb, int *clamped, int *radius, int *rect, int *tiles_touched,
-                   int *guard) {
+                   int *guard, int tight) {
     const int tiles_x = (W + tile_w - 1) / tile_w, tiles_y = (H + tile_h - 1) / tile_h;
     int nvis = 0;
     for (int i = 0; i < n; i++) {
@@ -385,24 +445,9 @@ int oracle_project(int n, int degree, const double *means, const double *log_sca
         rect[4 * i] = rect[4 * i + 1] = rect[4 * i + 2] = rect[4 * i + 3] = 0;
         tiles_touched[i] = 0;
         if (ok) {
-            /* 3-sigma extent along the major axis of the dilated 2D cov. */
-            double mid = 0.5 * (P.cov[0] + P.cov[2]);
-            double lam = mid + sqrt(fmax(0.0, mid * mid - P.det));
-            double ext = OR_SIGMAS * sqrt(lam);
-            int r = (int)ceil(ext);
-            if (near_int(ext, OR_G_RADIUS * fmax(1.0, ext))) g |= OR_GUARD_RECT;
-            /* Tile rect [floor((mu-r)/t), floor((mu+r+t-1)/t)) clamped to the grid. */
-            double ex[4] = {(P.mean2d[0] - r) / tile_w, (P.mean2d[1] - r) / tile_h,
-                            (P.mean2d[0] + r + tile_w - 1) / tile_w,
-                            (P.mean2d[1] + r + tile_h - 1) / tile_h};
-            int lim[4] = {tiles_x, tiles_y, tiles_x, tiles_y};
-            int rc[4];
-            for (int k = 0; k < 4; k++) {
-                double f = floor(ex[k]);
-                if (near_int(ex[k], OR_G_TILE) && f >= -1.0 && f <= lim[k]) g |= OR_GUARD_RECT;
-                rc[k] = f < 0.0 ? 0 : (f > lim[k] ? lim[k] : (int)f);
-            }
-            int area = (rc[2] - rc[0]) * (rc[3] - rc[1]);
+            int rc[4], r;
+            int area = tile_rect(P.mean2d, P.cov, P.det, P.opacity, tile_w, tile_h, tiles_x,
+                                 tiles_y, tight, rc, &r, &g);
             /* Screen-space quantities are reported for every Gaussian that
              * survives the near-plane and determinant tests, so that callers
              * can locate one whose rect came out empty. */
@@ -755,7 +800,7 @@ void oracle_project_bwd(int n, int degree, const double *means, const double *lo
                         const double *cam, int W, int H, int tile_w, int tile_h, double near_z,
                         const double *dmean2d, const double *dconic, const double *dopacity,
                         const double *drgb, double *gmeans, double *glog_scales, double *gquats,
-                        double *gopacity_logits, double *gsh) {
+                        double *gopacity_logits, double *gsh, int tight) {
     const double *R = cam;
     const double fx = cam[12], fy = cam[13];
     const int tiles_x = (W + tile_w - 1) / tile_w, tiles_y = (H + tile_h - 1) / tile_h;
@@ -767,19 +812,10 @@ void oracle_project_bwd(int n, int degree, const double *means, const double *lo
                          near_z, &P, &gd))
             continue;
         /* Same visibility test as oracle_project: non-empty rect. */
-        double mid = 0.5 * (P.cov[0] + P.cov[2]);
-        double lam = mid + sqrt(fmax(0.0, mid * mid - P.det));
-        int r = (int)ceil(OR_SIGMAS * sqrt(lam));
-        double ex[4] = {(P.mean2d[0] - r) / tile_w, (P.mean2d[1] - r) / tile_h,
-                        (P.mean2d[0] + r + tile_w - 1) / tile_w,
-                        (P.mean2d[1] + r + tile_h - 1) / tile_h};
-        int lim[4] = {tiles_x, tiles_y, tiles_x, tiles_y};
-        int rc[4];
-        for (int k = 0; k < 4; k++) {
-            double f = floor(ex[k]);
-            rc[k] = f < 0.0 ? 0 : (f > lim[k] ? lim[k] : (int)f);
-        }
-        if ((rc[2] - rc[0]) * (rc[3] - rc[1]) <= 0) continue;
+        int rc[4], r, gr = 0;
+        if (tile_rect(P.mean2d, P.cov, P.det, P.opacity, tile_w, tile_h, tiles_x, tiles_y, tight,
+                      rc, &r, &gr) == 0)
+            continue;
 
         const double z = P.xc[2];
         double gxc[3] = {0.0, 0.0, 0.0};

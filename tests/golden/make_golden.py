@@ -29,9 +29,10 @@ def golden_case():
     return p, view, target
 
 
-def compute():
+def compute(tight=False):
+    """The record is of the plain 3-sigma square tile rects (tight=False)."""
     p, view, target = golden_case()
-    L, g, renders = oracle.iteration(p, [view], [target], 0.2, bg=(0.1, 0.2, 0.3))
+    L, g, renders = oracle.iteration(p, [view], [target], 0.2, bg=(0.1, 0.2, 0.3), tight=tight)
     img = renders[0]["image"]
     rng = np.random.default_rng(80)
     pix = [(int(c), int(y), int(x)) for c, y, x in

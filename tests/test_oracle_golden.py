@@ -24,3 +24,21 @@ def test_oracle_matches_frozen_record():
         assert abs(got["grad_norms"][k] - v) <= 1e-10 * max(1.0, abs(v))
     np.testing.assert_allclose(got["grad_means_first"], want["grad_means_first"], rtol=1e-10,
                                atol=1e-15)
+
+
+def test_tight_rects_change_no_result():
+    """Cutting the tile rects to the tiles that can receive alpha >= 1/255
+    (reading C4') drops only (Gaussian, tile) pairs that every pixel skips:
+    loss, image, transmittance and gradients equal the frozen square-rect
+    record; only the list positions (last_idx) move."""
+    with open(os.path.join(HERE, "golden", "oracle_small.json")) as f:
+        want = json.load(f)
+    got = compute(tight=True)
+    assert abs(got["loss"] - want["loss"]) < 1e-12
+    assert abs(got["image_sum"] - want["image_sum"]) < 1e-10
+    assert abs(got["final_T_sum"] - want["final_T_sum"]) < 1e-10
+    assert got["last_idx_sum"] <= want["last_idx_sum"]
+    np.testing.assert_allclose([p[3] for p in got["pixels"]], [p[3] for p in want["pixels"]],
+                               atol=1e-13)
+    for k, v in want["grad_norms"].items():
+        assert abs(got["grad_norms"][k] - v) <= 1e-10 * max(1.0, abs(v))

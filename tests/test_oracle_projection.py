@@ -76,7 +76,7 @@ def test_mean_projection_is_pinhole():
 def test_isotropic_on_axis_closed_form(z, log_s, f):
     W, H = 320, 240
     view = scenes.camera(W, H, f, f)
-    pr = oracle.project(one_gaussian([0, 0, z], [log_s] * 3, logit=0.3), view)
+    pr = oracle.project(one_gaussian([0, 0, z], [log_s] * 3, logit=0.3), view, tight=False)
     s = math.exp(log_s)
     var = (f * s / z) ** 2 + 0.3
     np.testing.assert_allclose(pr["cov2d"][0], [var, 0.0, var], rtol=1e-13, atol=1e-15)
@@ -244,3 +244,75 @@ def test_project_bwd_matches_central_differences(degree, offscreen):
             checked += 1
     assert checked > 0.9 * sum(p[k].size for k in ("means", "log_scales", "quats",
                                                          "opacity_logits", "sh"))
+
+
+# ----------------------------------------------------------------------------
+# Tight rects (reading C4'): the square rect cut to the box of the ellipse
+# outside which alpha = o exp(-q/2) < 1/255, widened to q <= 1.01 t + 0.01.
+# ----------------------------------------------------------------------------
+@pytest.mark.parametrize("z,log_s,f,logit", [(2.0, -4.0, 300.0, 0.3), (1.0, -3.0, 525.0, -2.0),
+                                             (3.7, -4.5, 600.0, -4.5), (1.5, -3.5, 400.0, 3.0)])
+def test_tight_rect_isotropic_closed_form(z, log_s, f, logit):
+    W, H = 320, 240
+    view = scenes.camera(W, H, f, f)
+    pr = oracle.project(one_gaussian([0, 0, z], [log_s] * 3, logit=logit), view, tight=True)
+    var = (f * math.exp(log_s) / z) ** 2 + 0.3
+    o = 1 / (1 + math.exp(-logit))
+    r = math.ceil(3 * math.sqrt(var))
+    sq = [max(0, math.floor((W / 2 - r) / 16)), max(0, math.floor((H / 2 - r) / 16)),
+          min(20, math.floor((W / 2 + r + 15) / 16)), min(15, math.floor((H / 2 + r + 15) / 16))]
+    h = math.sqrt((1.01 * 2 * math.log(255 * o) + 0.01) * var)
+    box = [math.ceil((W / 2 - h - 15) / 16), math.ceil((H / 2 - h - 15) / 16),
+           math.floor((W / 2 + h) / 16) + 1, math.floor((H / 2 + h) / 16) + 1]
+    want = [max(sq[0], box[0]), max(sq[1], box[1]), min(sq[2], box[2]), min(sq[3], box[3])]
+    assert list(pr["rect"][0]) == want
+    assert pr["tiles_touched"][0] == (want[2] - want[0]) * (want[3] - want[1])
+
+
+def test_tight_rect_empty_below_alpha_threshold():
+    """o < 0.999/255: alpha < 1/255 at every pixel, so no tile at all."""
+    view = scenes.camera(320, 240, 300.0, 300.0)
+    logit = math.log((0.99 / 255) / (1 - 0.99 / 255))
+    pr = oracle.project(one_gaussian([0, 0, 2.0], [-3.0] * 3, logit=logit), view, tight=True)
+    assert pr["tiles_touched"][0] == 0
+    assert oracle.project(one_gaussian([0, 0, 2.0], [-3.0] * 3, logit=logit), view,
+                          tight=False)["tiles_touched"][0] > 0
+
+
+@pytest.mark.parametrize("tile", [(16, 16), (8, 8)])
+def test_tight_rect_drops_only_tiles_without_alpha(tile):
+    """Brute force over pixels: every tile of the square rect left out of the
+    tight rect has alpha < 1/255 at all its pixels (alpha evaluated from the
+    projected mean, conic and opacity as the renderer does), and the tight
+    rect lies inside the square one."""
+    tw, th = tile
+    W, H = 160, 120
+    rng = np.random.default_rng(5)
+    R, t = scenes.random_pose(rng, 0.3, 20.0)
+    view = scenes.camera(W, H, 150.0, 150.0, R=R, t=t)
+    n = 300
+    q = rng.normal(size=(n, 4))
+    p = dict(means=rng.uniform(-0.6, 0.6, (n, 3)) + np.array([0, 0, 2.0]),
+             log_scales=rng.normal(-3.5, 0.8, (n, 3)), quats=q / np.linalg.norm(q, axis=1)[:, None],
+             opacity_logits=rng.normal(-1.0, 2.0, n), sh=np.zeros((1, n, 3)), sh_degree=0)
+    sq = oracle.project(p, view, tw, th, tight=False)
+    ti = oracle.project(p, view, tw, th, tight=True)
+    ys, xs = np.mgrid[0:H, 0:W]
+    dropped = 0
+    for i in np.flatnonzero(sq["tiles_touched"] > 0):
+        a, b, c = sq["conic"][i]
+        dx, dy = xs - sq["mean2d"][i, 0], ys - sq["mean2d"][i, 1]
+        alpha = np.minimum(0.99, sq["opacity"][i] * np.exp(-0.5 * (a * dx * dx + c * dy * dy)
+                                                           - b * dx * dy))
+        s0, t0 = sq["rect"][i], ti["rect"][i]
+        if ti["tiles_touched"][i] > 0:
+            assert s0[0] <= t0[0] and s0[1] <= t0[1] and t0[2] <= s0[2] and t0[3] <= s0[3]
+        for ty in range(s0[1], s0[3]):
+            for tx in range(s0[0], s0[2]):
+                inside = (ti["tiles_touched"][i] > 0 and t0[0] <= tx < t0[2]
+                          and t0[1] <= ty < t0[3])
+                if not inside:
+                    dropped += 1
+                    blk = alpha[ty * th:(ty + 1) * th, tx * tw:(tx + 1) * tw]
+                    assert blk.max() < 1 / 255, (i, tx, ty, blk.max())
+    assert dropped > 50  # the cut is not vacuous on this scene
