@@ -51,9 +51,9 @@ PAIR_FLOPS_FWD = 26.0
 PAIR_FLOPS_BWD = 64.0
 
 # DRAM bytes (read + write) of one k_render_bwd launch on the 1M 1200x680
-# workload stored in Z-order, from one single-pass ncu capture per launch
-# shape (tile, backward batch, backward pixels per thread) of the kernel as
-# committed; other shapes and modes report null.  Summarised with its command in
+# workload stored in Z-order with square tile rects, from one single-pass ncu
+# capture per launch shape (tile, backward batch, backward pixels per thread)
+# of the kernel as committed; other shapes and modes report null.  Summarised with its command in
 # profiles/launches_room1M_1200x680.md.
 RENDER_BWD_TRAFFIC = {
     ("room1M_1200x680", "8x8", 32, 2): 60.67e6 + 0.83e6,
@@ -505,7 +505,8 @@ def run_gpu(args, ws, rank, local):
     tuned = None
     if None in (args.tile_w, args.tile_h, args.batch, args.ppt):
         from paper_2409_13055_gb300 import autotune
-        tuned = autotune.autotune([view], gm, target, lam, use_cache=False)
+        tuned = autotune.autotune([view], gm, target, lam, use_cache=False,
+                                  tight_rect=not args.square_rects)
         args.tile_w = args.tile_w or tuned["tile"][0]
         args.tile_h = args.tile_h or tuned["tile"][1]
         args.batch = args.batch or tuned["smem_batch"]
@@ -518,7 +519,8 @@ def run_gpu(args, ws, rank, local):
                                          smem_batch=args.batch, pixels_per_thread=args.ppt,
                                          smem_batch_bwd=args.batch_bwd,
                                          pixels_per_thread_bwd=args.ppt_bwd,
-                                         deterministic=args.deterministic)
+                                         deterministic=args.deterministic,
+                                         tight_rect=not args.square_rects)
     step = mapping.MappingStep(gm, rast, target, lam)
     m, g = gm.gs_map(), gm.gs_map_grad()
     stages = [
@@ -640,7 +642,8 @@ def run_gpu(args, ws, rank, local):
         peak = fp32_peak_tflops(peaks["sm_max_mhz"])
         achieved = flops / (stage_ms[dominant] * 1e-3) / 1e12
         traffic = None
-        if dominant == "render_bwd" and args.map_order == "zorder" and not args.deterministic:
+        if (dominant == "render_bwd" and args.map_order == "zorder" and not args.deterministic
+                and args.square_rects):
             traffic = RENDER_BWD_TRAFFIC.get((args.workload, f"{args.tile_w}x{args.tile_h}",
                                               args.batch_bwd, args.ppt_bwd))
         roof = dict(bound="alu", kernel=dominant, achieved=achieved, peak=peak, unit="TFLOP/s",
@@ -664,6 +667,7 @@ def run_gpu(args, ws, rank, local):
                            autotuned=tuned is not None, cuda_graph="one graph per stage",
                            adam=args.adam, map_order=args.map_order,
                            deterministic=bool(args.deterministic),
+                           tile_rects="square" if args.square_rects else "tight",
                            l2="working set ~1.2 GB > 129 MB L2, no flush",
                            instances=instances, pairs_bwd=pairs_bwd),
                stages_ms=stage_ms, roofline=roof,
@@ -725,6 +729,9 @@ def main():
                     help="Adam as its own pass over the gradient buffer (measured faster at "
                          "1M: 0.44 vs 0.56 ms), inside the projection adjoint, or the "
                          "visibility-masked variant (changes the optimiser: not the headline)")
+    ap.add_argument("--square-rects", action="store_true",
+                    help="plain 3-sigma square tile rects instead of the opacity-aware tight "
+                         "ones (same images and gradients, more (Gaussian, tile) instances)")
     ap.add_argument("--deterministic", action="store_true",
                     help="bit-reproducible pixel adjoint (partial sums per (Gaussian, tile) "
                          "reduced in a fixed order instead of float atomics)")

@@ -109,10 +109,17 @@ typedef struct {
  *     stored in its own slot, indexed by the pair's emission position, and
  *     summed per Gaussian in emission order by a second kernel, instead of
  *     float atomics; needs one warp per tile in the backward (tile_w *
- *     tile_h / pixels_per_thread_bwd == 32, GS_ERR_UNSUPPORTED otherwise).
+ *     tile_h / pixels_per_thread_bwd == 32, GS_ERR_UNSUPPORTED otherwise);
+ *   tight_rect: nonzero (recommended) cuts each Gaussian's 3-sigma square
+ *     tile rect to the tiles that meet the axis-aligned box of the ellipse
+ *     outside which alpha = o exp(power) < 1/255, with the level widened by
+ *     1% + 0.01 against FP32 rounding; a Gaussian with o < 0.999/255 gets no
+ *     tile.  Only (Gaussian, tile) pairs that every pixel would skip are
+ *     dropped: images and gradients are unchanged, the instance lists (and
+ *     so last_idx) shorter.
  * The tile shape changes which pixels a Gaussian can reach (its 3-sigma
- * rect is counted in whole tiles), hence the image; the batch sizes and
- * pixels per thread change only the speed. */
+ * rect is counted in whole tiles), hence the image; the batch sizes, pixels
+ * per thread and tight_rect change only the speed. */
 typedef struct {
     int32_t tile_w, tile_h, smem_batch, pixels_per_thread;
     int32_t smem_batch_bwd, pixels_per_thread_bwd;
@@ -120,6 +127,7 @@ typedef struct {
     float bg[3];
     int32_t density_stats;
     int32_t deterministic;
+    int32_t tight_rect;
 } gs_config;
 
 /* A plan: the sizes, tile grids and workspace layout of one batch of views.

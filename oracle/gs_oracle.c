@@ -94,7 +94,7 @@ static int near_int(double v, double margin) {
  * meet [mu - h, mu + h].
  */
 #define OR_TIGHT_MIN_OPACITY (0.999 / 255.0)
-#define OR_G_TIGHT 1e-4 /* tight rect edges in tile units, relative to 1 + h / t */
+#define OR_G_TIGHT 1e-5 /* tight rect edges in tile units, relative to 1 + h / t */
 
 static int tile_rect(const double mean2d[2], const double cov[3], double det, double opacity,
                      int tile_w, int tile_h, int tiles_x, int tiles_y, int tight, int rc[4],

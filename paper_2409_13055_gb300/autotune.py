@@ -35,18 +35,19 @@ def cache_path():
                                        "autotune.json"))
 
 
-def cache_key(views, n):
+def cache_key(views, n, tight_rect=True):
     name = torch.cuda.get_device_name()
     sizes = ",".join(f"{v['width']}x{v['height']}x{v.get('channels', 3)}" for v in views)
-    return f"{name}|{sizes}|n2^{max(0, int(math.log2(max(1, n))))}"
+    rects = "tight" if tight_rect else "square"
+    return f"{name}|{sizes}|n2^{max(0, int(math.log2(max(1, n))))}|{rects}"
 
 
-def _time_config(views, gmap, targets_packed, lam, tile, batch, ppt, iters):
+def _time_config(views, gmap, targets_packed, lam, tile, batch, ppt, iters, tight_rect=True):
     """Mean (total, forward, backward) milliseconds of project + bin + forward +
     loss + pixel adjoint + projection adjoint with one launch shape."""
     rast = mapping.fit_instance_capacity(views, gmap, tile=tile, smem_batch=batch,
                                          pixels_per_thread=ppt, smem_batch_bwd=batch,
-                                         pixels_per_thread_bwd=ppt)
+                                         pixels_per_thread_bwd=ppt, tight_rect=tight_rect)
     m, g = gmap.gs_map(), gmap.gs_map_grad()
     ev = [torch.cuda.Event(enable_timing=True) for _ in range(5)]
 
@@ -80,10 +81,10 @@ def _time_config(views, gmap, targets_packed, lam, tile, batch, ppt, iters):
 
 
 def autotune(views, gmap: mapping.GaussianMap, targets_packed, lam, iters=5, use_cache=True,
-             verbose=False):
+             verbose=False, tight_rect=True):
     """Returns dict(tile=(w, h), smem_batch, pixels_per_thread, smem_batch_bwd,
     pixels_per_thread_bwd, ms, timings=[...])."""
-    key = cache_key(views, gmap.n)
+    key = cache_key(views, gmap.n, tight_rect)
     path = cache_path()
     cache = {}
     fields = ("smem_batch", "pixels_per_thread", "smem_batch_bwd", "pixels_per_thread_bwd")
@@ -100,7 +101,7 @@ def autotune(views, gmap: mapping.GaussianMap, targets_packed, lam, iters=5, use
     timings = []
 
     def run(tile, batch, ppt):
-        t = _time_config(views, gmap, targets_packed, lam, tile, batch, ppt, iters)
+        t = _time_config(views, gmap, targets_packed, lam, tile, batch, ppt, iters, tight_rect)
         timings.append(dict(tile=tile, smem_batch=batch, pixels_per_thread=ppt, ms=t[0],
                             fwd_ms=t[1], bwd_ms=t[2]))
         if verbose:

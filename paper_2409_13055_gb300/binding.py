@@ -46,7 +46,8 @@ class gs_config(ctypes.Structure):
     _fields_ = [("tile_w", c_int32), ("tile_h", c_int32), ("smem_batch", c_int32),
                 ("pixels_per_thread", c_int32), ("smem_batch_bwd", c_int32),
                 ("pixels_per_thread_bwd", c_int32), ("near_z", c_float), ("bg", c_float * 3),
-                ("density_stats", c_int32), ("deterministic", c_int32)]
+                ("density_stats", c_int32), ("deterministic", c_int32),
+                ("tight_rect", c_int32)]
 
 
 class gs_densify_config(ctypes.Structure):

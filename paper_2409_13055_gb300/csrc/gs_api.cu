@@ -58,6 +58,7 @@ extern "C" gs_status gs_plan_init(gs_plan* plan, const gs_config* cfg, int32_t n
     p->vt.tile_h = cfg->tile_h;
     p->vt.log2_tw = l2w;
     p->vt.log2_th = l2h;
+    p->vt.tight_rect = cfg->tight_rect != 0;
     int64_t tiles = 0, pixels = 0, values = 0;
     for (int v = 0; v < n_views; ++v) {
         const gs_view& vw = views_host[v];

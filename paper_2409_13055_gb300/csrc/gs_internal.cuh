@@ -35,6 +35,7 @@ struct ViewGeom {
 struct ViewTable {
     int32_t n_views;
     int32_t tile_w, tile_h, log2_tw, log2_th;
+    int32_t tight_rect;  // gs_config.tight_rect
     ViewGeom v[GS_MAX_VIEWS];
 };
 

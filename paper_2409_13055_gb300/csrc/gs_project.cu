@@ -180,9 +180,13 @@ struct FusedAdam {
     float *o_means, *o_ls, *o_quats, *o_logit, *o_sh;        // gradients out, or null
 };
 
+// Opacity below which no pixel can reach alpha >= 1/255 (alpha <= opacity),
+// with a 0.1% margin: such a Gaussian gets no tile under tight rects.
+constexpr float kTightMinOpacity = 0.999f / 255.0f;
+
 __device__ __forceinline__ void project_one(const float* mean, const Shape& sh, const Cam& cam,
                                             float near_z, int log2_tw, int log2_th, int tiles_x,
-                                            int tiles_y, Proj& p) {
+                                            int tiles_y, float opacity, int tight, Proj& p) {
     p.visible = false;
     float xh, xl, yh, yl, zh, zl;
     dot3_plus(cam.R[0], cam.R[1], cam.R[2], mean[0], mean[1], mean[2], cam.t[0], xh, xl);
@@ -255,6 +259,33 @@ __device__ __forceinline__ void project_one(const float* mean, const Shape& sh, 
     p.rect[1] = min(max(y0, 0), tiles_y);
     p.rect[2] = min(max(x1, 0), tiles_x);
     p.rect[3] = min(max(y1, 0), tiles_y);
+    if (tight) {
+        // Cut to the tiles meeting the box of the ellipse q <= 1.01 t + 0.01,
+        // t = 2 ln(255 o): outside it o exp(-q/2) < 1/255 with a margin no
+        // FP32 evaluation of alpha can cross.  Tile k holds pixels
+        // k T .. k T + T - 1, so tiles [ceil((mu - h - T + 1) / T),
+        // floor((mu + h) / T)] meet [mu - h, mu + h].
+        if (!(opacity >= kTightMinOpacity)) return;
+        const float t = __fmaf_rn(1.01f, 2.0f * logf(255.0f * opacity), 0.01f);
+        const float hx = sqrtf(t * p.a), hy = sqrtf(t * p.c);
+        two_sum(p.mxh, -(hx + tw1), sh_, e2);
+        fast_two_sum(sh_, __fadd_rn(e2, p.mxl), sh_, sl);
+        const int lx = -df_floor_div(-sh_, -sl, itw);  // ceil
+        two_sum(p.myh, -(hy + th1), sh_, e2);
+        fast_two_sum(sh_, __fadd_rn(e2, p.myl), sh_, sl);
+        const int ly = -df_floor_div(-sh_, -sl, ith);
+        two_sum(p.mxh, hx, sh_, e2);
+        fast_two_sum(sh_, __fadd_rn(e2, p.mxl), sh_, sl);
+        const int ux = df_floor_div(sh_, sl, itw) + 1;
+        two_sum(p.myh, hy, sh_, e2);
+        fast_two_sum(sh_, __fadd_rn(e2, p.myl), sh_, sl);
+        const int uy = df_floor_div(sh_, sl, ith) + 1;
+        p.rect[0] = max(p.rect[0], min(lx, tiles_x));
+        p.rect[1] = max(p.rect[1], min(ly, tiles_y));
+        p.rect[2] = min(p.rect[2], max(ux, 0));
+        p.rect[3] = min(p.rect[3], max(uy, 0));
+        if (p.rect[2] <= p.rect[0] || p.rect[3] <= p.rect[1]) return;
+    }
     if ((p.rect[2] - p.rect[0]) * (p.rect[3] - p.rect[1]) <= 0) return;
     float d0 = mean[0] - cam.cc[0], d1 = mean[1] - cam.cc[1], d2 = mean[2] - cam.cc[2];
     p.dist = sqrtf(d0 * d0 + d1 * d1 + d2 * d2);
@@ -296,7 +327,7 @@ k_project(const float* __restrict__ means, const float* __restrict__ log_scales,
         const ViewGeom& geo = vt.v[v];
         Proj p;
         project_one(mean, shp, cams[j], near_z, vt.log2_tw, vt.log2_th, geo.tiles_x,
-                    geo.tiles_y, p);
+                    geo.tiles_y, opacity, vt.tight_rect, p);
         const bool vis = finite && p.visible;
         dval[vg] = (uint32_t)vg;
         if (!vis) {
@@ -371,7 +402,8 @@ __device__ __forceinline__ void adjoint_one(
         if (geo.channels == 1) gcol[0] = gcol[1] = gcol[2] = g2[6] * (1.0f / 3.0f);
         const Cam& cam = cam_all[v];
         Proj p;
-        project_one(mean, shp, cam, near_z, vt.log2_tw, vt.log2_th, geo.tiles_x, geo.tiles_y, p);
+        project_one(mean, shp, cam, near_z, vt.log2_tw, vt.log2_th, geo.tiles_x, geo.tiles_y,
+                    opacity, vt.tight_rect, p);
         if (!p.visible) {
             if (!FUSED) {
                 float* gc_out = gcol_out + vg * 3;

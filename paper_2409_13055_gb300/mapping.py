@@ -281,14 +281,14 @@ class Rasterizer:
     def __init__(self, views, n_capacity, instance_capacity=None, tile=(16, 16), smem_batch=128,
                  near_z=0.2, bg=(0.0, 0.0, 0.0), pixels_per_thread=0, smem_batch_bwd=0,
                  pixels_per_thread_bwd=0, density_stats=False, deterministic=False,
-                 device="cuda"):
+                 tight_rect=True, device="cuda"):
         self.views = list(views)
         self.device = torch.device(device)
         self.cfg = B.gs_config(int(tile[0]), int(tile[1]), int(smem_batch),
                                int(pixels_per_thread), int(smem_batch_bwd),
                                int(pixels_per_thread_bwd), float(near_z),
                                (B.c_float * 3)(*[float(x) for x in bg]), int(bool(density_stats)),
-                               int(bool(deterministic)))
+                               int(bool(deterministic)), int(bool(tight_rect)))
         self.n_capacity = int(n_capacity)
         if instance_capacity is None:
             px = sum(v["width"] * v["height"] for v in self.views)

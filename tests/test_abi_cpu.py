@@ -30,7 +30,7 @@ def test_exports_every_declared_function(lib):
 
 def test_struct_sizes_match_header():
     assert ctypes.sizeof(B.gs_view) == 80
-    assert ctypes.sizeof(B.gs_config) == 48
+    assert ctypes.sizeof(B.gs_config) == 52
     assert ctypes.sizeof(B.gs_densify_config) == 32
     assert ctypes.sizeof(B.gs_counters) == 32
     assert ctypes.sizeof(B.gs_plan) == 8 * B.GS_PLAN_WORDS

@@ -107,6 +107,39 @@ def test_binning_bit_exact(case):
 
 
 @pytest.mark.parametrize("case", list(CASES))
+def test_tight_rects_same_render_fewer_instances(case):
+    """Square against tight tile rects on the GPU: the tight lists are
+    shorter, while the image, the final transmittance and the loss are bit-
+    identical and the parameter gradients equal up to the order of float
+    atomics; the square rects match the oracle's square rects."""
+    p, view = CASES[case]()
+    target = scenes.random_target(view, 3)
+    out = {}
+    for tight in (False, True):
+        gm = mapping.GaussianMap(p)
+        rast = mapping.Rasterizer([view], gm.n, instance_capacity=1 << 21, tight_rect=tight,
+                                  bg=(0.1, 0.2, 0.3))
+        rast.forward(gm.gs_map())
+        rast.loss_l1_ssim(rast.pack([target]), 0.2)
+        rast.render_bwd(gm.gs_map(), gm.gs_map_grad())
+        torch.cuda.synchronize()
+        c = rast.counters()
+        assert c.status == 0
+        out[tight] = dict(img=rast.images.clone(), T=rast.final_T.clone(),
+                          grad=gm.grad.clone().cpu().numpy(), n=int(c.n_instances),
+                          proj=U.gpu_projection(rast, gm.n), loss=rast.loss.item())
+    sq, ti = out[False], out[True]
+    assert ti["n"] < sq["n"]
+    assert torch.equal(sq["img"], ti["img"]) and torch.equal(sq["T"], ti["T"])
+    assert sq["loss"] == ti["loss"]
+    assert U.rel_l2(ti["grad"], sq["grad"]) < 1e-5
+    o = oracle.project(p, view, tight=False)
+    ok = ((o["guard"] & U.FWD_GUARDS) == 0) & (o["tiles_touched"] > 0)
+    np.testing.assert_array_equal(sq["proj"]["rect"][ok], o["rect"][ok])
+    np.testing.assert_array_equal(sq["proj"]["touched"][ok], o["tiles_touched"][ok])
+
+
+@pytest.mark.parametrize("case", list(CASES))
 @pytest.mark.parametrize("tile", [(16, 16), (8, 8), (32, 8)])
 def test_render_parity(case, tile):
     p, view = CASES[case]()
