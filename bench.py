@@ -651,10 +651,11 @@ def run_gpu(args, ws, rank, local):
                     peak_source="152 SMs x 128 FP32 lanes x 2 x sm_max_mhz (%s)" % peaks["source"])
 
     # project 1, bin_sort 18 + 3 per tile-id pass, render_fwd 1, loss 2,
-    # render_bwd 1, then project_bwd 2 + adam 2, or step counter + the fused
-    # adjoint kernel
+    # render_bwd 1, then the projection adjoint (one kernel for one view) +
+    # step counter + adam (+ the visibility kernel for sparse), or step
+    # counter + the fused adjoint kernel
     launches_per_step = 1 + (18 + 3 * tile_passes(rast.total_tiles)) + 1 + 2 + 1 + \
-        {"fused": 2, "separate": 4, "sparse": 5}[args.adam]
+        {"fused": 2, "separate": 3, "sparse": 4}[args.adam]
 
     out = dict(metric=METRIC, value=value, unit="iters/s", n_gpus=ws, steps=K, warmup=args.warmup,
                ms_per_step=ms_step, higher_is_better=True, scaling="weak", vs_baseline=None,

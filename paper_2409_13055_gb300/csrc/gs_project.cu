@@ -367,17 +367,24 @@ k_project(const float* __restrict__ means, const float* __restrict__ log_scales,
 // is visible in: screen-space gradient -> gradients of the mean, log-scales,
 // quaternion and opacity logit.  The colour gradient that reaches the SH
 // coefficients (zero on clamped channels, a grayscale view's gradient spread
-// over the three channels) goes to gcol_out per (view, Gaussian), or, FUSED,
-// is folded at once into this Gaussian's SH gradient: sh_acc[k * sh_stride +
-// c] += Y_k(dir) gcol[c], view by view in view order (the sum k_sh_bwd forms).
-template <int DEG, bool FUSED>
+// over the three channels) goes, by MODE:
+//   kShViaGcol  to gcol_out per (view, Gaussian), for k_sh_bwd;
+//   kShStaged   into this Gaussian's SH gradient at once, sh_acc[k * sh_stride
+//               + c] += Y_k(dir) gcol[c] view by view in view order (the sum
+//               k_sh_bwd forms), sh_acc in shared memory;
+//   kShDirect   (one view only) straight to the SH gradient array, sh_acc =
+//               its row of this Gaussian, sh_stride = 3 n: Y_k(dir) gcol[c],
+//               rounded as k_sh_bwd rounds it, written or (accumulate) added.
+constexpr int kShViaGcol = 0, kShStaged = 1, kShDirect = 2;
+
+template <int DEG, int MODE>
 __device__ __forceinline__ void adjoint_one(
     int g, const float* __restrict__ means, const float* __restrict__ log_scales,
     const float* __restrict__ quats, const float* __restrict__ opacity_logits,
     const float* __restrict__ sh, int n, const Cam* cam_all, const ViewTable& vt, float near_z,
     const uint32_t* __restrict__ touched, const float* __restrict__ grad2d,
-    float* __restrict__ gcol_out, float* sh_acc, int sh_stride, float gm_out[3],
-    float gls[3], float4& gq4, float& glog) {
+    float* __restrict__ gcol_out, float* sh_acc, size_t sh_stride, int accumulate,
+    float gm_out[3], float gls[3], float4& gq4, float& glog) {
     const float mean[3] = {means[3 * g], means[3 * g + 1], means[3 * g + 2]};
     const float ls[3] = {log_scales[3 * g], log_scales[3 * g + 1], log_scales[3 * g + 2]};
     const float4 q = reinterpret_cast<const float4*>(quats)[g];
@@ -391,6 +398,7 @@ __device__ __forceinline__ void adjoint_one(
     float gm[3] = {0.f, 0.f, 0.f};
     float gsig[6] = {0.f, 0.f, 0.f, 0.f, 0.f, 0.f};  // dL/dSigma as a symmetric matrix
     float gop = 0.0f;
+    bool sh_written = false;
 
     for (int v = 0; v < vt.n_views; ++v) {
         const size_t vg = (size_t)v * n + g;
@@ -405,7 +413,7 @@ __device__ __forceinline__ void adjoint_one(
         project_one(mean, shp, cam, near_z, vt.log2_tw, vt.log2_th, geo.tiles_x, geo.tiles_y,
                     opacity, vt.tight_rect, p);
         if (!p.visible) {
-            if (!FUSED) {
+            if (MODE == kShViaGcol) {
                 float* gc_out = gcol_out + vg * 3;
                 gc_out[0] = gc_out[1] = gc_out[2] = 0.0f;
             }
@@ -430,7 +438,7 @@ __device__ __forceinline__ void adjoint_one(
             if (col[ch] + 0.5f < 0.0f) gcol[ch] = 0.0f;
         // the SH coefficients' own gradient, Y_k(dir) gcol, from this masked
         // colour gradient
-        if (FUSED) {
+        if (MODE == kShStaged) {
 #pragma unroll
             for (int k = 0; k < K; ++k) {
                 float* a = sh_acc + k * sh_stride;
@@ -438,6 +446,17 @@ __device__ __forceinline__ void adjoint_one(
                 a[1] = fmaf(Y[k], gcol[1], a[1]);
                 a[2] = fmaf(Y[k], gcol[2], a[2]);
             }
+        } else if (MODE == kShDirect) {
+#pragma unroll
+            for (int k = 0; k < K; ++k) {
+                float* a = sh_acc + k * sh_stride;
+#pragma unroll
+                for (int c = 0; c < 3; ++c) {
+                    const float y = __fmul_rn(Y[k], gcol[c]);
+                    a[c] = accumulate ? __fadd_rn(a[c], y) : y;
+                }
+            }
+            sh_written = true;
         } else {
             float* gc_out = gcol_out + vg * 3;
             gc_out[0] = gcol[0];
@@ -550,18 +569,26 @@ __device__ __forceinline__ void adjoint_one(
     glog = gop * opacity * (1.0f - opacity);
 #pragma unroll
     for (int e = 0; e < 3; ++e) gm_out[e] = gm[e];
+    if (MODE == kShDirect && !sh_written && !accumulate) {
+        // not visible in the view: a zero SH gradient
+#pragma unroll
+        for (int k = 0; k < K; ++k)
+            sh_acc[k * sh_stride] = sh_acc[k * sh_stride + 1] = sh_acc[k * sh_stride + 2] = 0.0f;
+    }
 }
 
 
-template <int DEG>
-__global__ void __launch_bounds__(kProjThreads)
+// DIRECT (single-view plans): the SH gradient is written here and k_sh_bwd
+// is not launched.
+template <int DEG, bool DIRECT>
+__global__ void __launch_bounds__(kProjThreads, 2)
 k_project_bwd(const float* __restrict__ means, const float* __restrict__ log_scales,
               const float* __restrict__ quats, const float* __restrict__ opacity_logits,
               const float* __restrict__ sh, int n, const gs_view* __restrict__ views,
               ViewTable vt, float near_z, const uint32_t* __restrict__ touched,
               const float* __restrict__ grad2d, float* __restrict__ gcol_out,
               float* __restrict__ g_means, float* __restrict__ g_ls, float* __restrict__ g_quats,
-              float* __restrict__ g_logit, int accumulate) {
+              float* __restrict__ g_logit, float* __restrict__ g_sh, int accumulate) {
     extern __shared__ Cam cam_all[];
     for (int v = threadIdx.x; v < vt.n_views; v += blockDim.x) load_cam(views[v], cam_all[v]);
     __syncthreads();
@@ -569,8 +596,10 @@ k_project_bwd(const float* __restrict__ means, const float* __restrict__ log_sca
     if (g >= n) return;
     float gm[3], gls[3], glog;
     float4 gq4;
-    adjoint_one<DEG, false>(g, means, log_scales, quats, opacity_logits, sh, n, cam_all, vt,
-                            near_z, touched, grad2d, gcol_out, nullptr, 0, gm, gls, gq4, glog);
+    adjoint_one<DEG, DIRECT ? kShDirect : kShViaGcol>(
+        g, means, log_scales, quats, opacity_logits, sh, n, cam_all, vt, near_z, touched, grad2d,
+        gcol_out, DIRECT ? g_sh + (size_t)g * 3 : nullptr, (size_t)3 * n, accumulate, gm, gls,
+        gq4, glog);
     if (accumulate) {
         for (int e = 0; e < 3; ++e) {
             g_means[3 * g + e] += gm[e];
@@ -781,9 +810,9 @@ k_adjoint_adam(const float* __restrict__ means, const float* __restrict__ log_sc
     if (t < cnt) {
         float gm[3], gls[3], glog;
         float4 gq4;
-        adjoint_one<DEG, true>(g0 + t, means, log_scales, quats, opacity_logits, sh, n, cam_all,
-                               vt, near_z, touched, grad2d, nullptr, sh_acc, 3 * C, gm, gls, gq4,
-                               glog);
+        adjoint_one<DEG, kShStaged>(g0 + t, means, log_scales, quats, opacity_logits, sh, n,
+                                    cam_all, vt, near_z, touched, grad2d, nullptr, sh_acc, 3 * C,
+                                    0, gm, gls, gq4, glog);
 #pragma unroll
         for (int e = 0; e < 3; ++e) {
             stage[3 * t + e] = gm[e];
@@ -850,15 +879,20 @@ static gs_status launch_project_adjoint(const Plan* p, const gs_map* map,
     const int n = map->n;
     const size_t smem = sizeof(Cam) * p->vt.n_views;
     const int blocks = (n + kProjThreads - 1) / kProjThreads;
-    auto* kern = map->sh_degree == 0   ? k_project_bwd<0>
-                 : map->sh_degree == 1 ? k_project_bwd<1>
-                 : map->sh_degree == 2 ? k_project_bwd<2>
-                                       : k_project_bwd<3>;
+    const bool direct = p->vt.n_views == 1;
+    auto* kern = direct ? (map->sh_degree == 0   ? k_project_bwd<0, true>
+                           : map->sh_degree == 1 ? k_project_bwd<1, true>
+                           : map->sh_degree == 2 ? k_project_bwd<2, true>
+                                                 : k_project_bwd<3, true>)
+                        : (map->sh_degree == 0   ? k_project_bwd<0, false>
+                           : map->sh_degree == 1 ? k_project_bwd<1, false>
+                           : map->sh_degree == 2 ? k_project_bwd<2, false>
+                                                 : k_project_bwd<3, false>);
     kern<<<blocks, kProjThreads, smem, st>>>(
         map->means, map->log_scales, map->quats, map->opacity_logits, map->sh, n, views_dev,
         p->vt, p->cfg.near_z, buf<uint32_t>(p, ws, GS_BUF_TOUCHED),
         buf<float>(p, ws, GS_BUF_GRAD2D), buf<float>(p, ws, B_GCOL), grads->means,
-        grads->log_scales, grads->quats, grads->opacity_logits, accumulate);
+        grads->log_scales, grads->quats, grads->opacity_logits, grads->sh, accumulate);
     return launch_status();
 }
 
@@ -867,7 +901,7 @@ gs_status launch_project_bwd(const Plan* p, const gs_map* map, const gs_view* vi
                              cudaStream_t st) {
     if (reinterpret_cast<uintptr_t>(grads->quats) % 16) return GS_ERR_INVALID;
     gs_status s = launch_project_adjoint(p, map, views_dev, ws, grads, accumulate, st);
-    if (s != GS_OK) return s;
+    if (s != GS_OK || p->vt.n_views == 1) return s;  // one view: SH gradient already written
     const int n = map->n;
     auto* kern_sh = map->sh_degree == 0   ? k_sh_bwd<0>
                     : map->sh_degree == 1 ? k_sh_bwd<1>
