@@ -476,10 +476,20 @@ class MappingStep:
         self._g = gmap.gs_map_grad()
 
     def run(self, stream=None):
+        self.run_front(stream)
+        self.run_back(stream)
+
+    def run_front(self, stream=None):
+        """Projection, binning and forward render (reads the views, not the
+        targets)."""
         r = self.rast
         r.project(self._m, stream)
         r.bin_sort(self.gmap.n, stream)
         r.render_fwd(stream=stream)
+
+    def run_back(self, stream=None):
+        """Loss, backward and optimiser step (reads the targets)."""
+        r = self.rast
         r.loss_l1_ssim(self.targets, self.lam, stream=stream)
         if self.recompute:
             r.project(self._m, stream)
@@ -516,6 +526,79 @@ class MappingStep:
             self.graph.replay()
         else:
             self.run()
+
+
+class HostPipeline:
+    """Mapping iterations fed from pinned host memory: each call to `submit`
+    copies one iteration's targets and camera poses host -> device, runs the
+    iteration (two CUDA graphs) and copies its loss device -> host.
+
+    The copies overlap the compute: the inputs of iteration i go to staging
+    buffers on a copy stream while iteration i-1 still runs (they wait only
+    until iteration i-1 has taken its own inputs out of the staging buffers),
+    the poses are moved into place before the forward half and the targets
+    before the backward half, and the host reads the loss of iteration i-1
+    while iteration i runs.  `submit` returns the previous iteration's loss
+    (None for the first); `drain` waits for and returns the last one."""
+
+    def __init__(self, step: MappingStep, warmup=2):
+        self.step = step
+        self.rast = step.rast
+        self.copy_stream = torch.cuda.Stream()
+        self.stage_targets = torch.empty_like(step.targets)
+        self.stage_views = torch.empty_like(self.rast.views_dev)
+        self.host_loss = [torch.empty(1, dtype=torch.float32).pin_memory() for _ in range(2)]
+        self.ev_views = torch.cuda.Event()
+        self.ev_targets = torch.cuda.Event()
+        self.ev_free = torch.cuda.Event()
+        self.ev_loss = [torch.cuda.Event(), torch.cuda.Event()]
+        self.i = 0
+        # two graphs: the forward half reads the poses, the backward half the targets
+        s = torch.cuda.Stream()
+        s.wait_stream(torch.cuda.current_stream())
+        with torch.cuda.stream(s):
+            for _ in range(warmup):
+                step.run()
+        torch.cuda.current_stream().wait_stream(s)
+        self.g_front, self.g_back = torch.cuda.CUDAGraph(), torch.cuda.CUDAGraph()
+        with torch.cuda.graph(self.g_front):
+            step.run_front()
+        with torch.cuda.graph(self.g_back):
+            step.run_back()
+        self.ev_free.record(torch.cuda.current_stream())
+
+    def submit(self, host_targets: torch.Tensor, host_views: torch.Tensor):
+        main = torch.cuda.current_stream()
+        cs = self.copy_stream
+        with torch.cuda.stream(cs):
+            cs.wait_event(self.ev_free)
+            self.stage_views.copy_(host_views, non_blocking=True)
+            self.ev_views.record(cs)
+            self.stage_targets.copy_(host_targets, non_blocking=True)
+            self.ev_targets.record(cs)
+        main.wait_event(self.ev_views)
+        self.rast.views_dev.copy_(self.stage_views, non_blocking=True)
+        self.g_front.replay()
+        main.wait_event(self.ev_targets)
+        self.step.targets.copy_(self.stage_targets, non_blocking=True)
+        self.ev_free.record(main)
+        self.g_back.replay()
+        k = self.i & 1
+        self.host_loss[k].copy_(self.rast.loss, non_blocking=True)
+        self.ev_loss[k].record(main)
+        self.i += 1
+        if self.i < 2:
+            return None
+        prev = (self.i - 2) & 1
+        self.ev_loss[prev].synchronize()
+        return float(self.host_loss[prev].item())
+
+    def drain(self):
+        if self.i == 0:
+            return None
+        last = (self.i - 1) & 1
+        self.ev_loss[last].synchronize()
+        return float(self.host_loss[last].item())
 
 
 class PerViewLoop:

@@ -499,6 +499,48 @@ def test_autograd_function_and_recompute_mode():
         assert U.rel_l2(gk.cpu().numpy(), og[name]) < 5e-4, name
 
 
+def test_host_pipeline_matches_direct_steps():
+    """HostPipeline (inputs copied from pinned host memory on a copy stream,
+    loss read back one iteration late) gives the losses and updates of
+    eager iterations on device-resident inputs, with a different target and
+    pose each iteration."""
+    p, view = CASES["tiny_sh3_posed"]()
+    views = [posed(view, 30 + i, 0.05, 3.0) for i in range(4)]
+    targets = [scenes.random_target(view, 40 + i) for i in range(4)]
+    # direct: eager iterations, inputs written on the device
+    gm = mapping.GaussianMap(p)
+    rast = mapping.Rasterizer([views[0]], gm.n, instance_capacity=1 << 18)
+    step = mapping.MappingStep(gm, rast, rast.pack([targets[0]]), 0.2)
+    start = gm.data.clone()
+    want = []
+    for v, t in zip(views, targets):
+        rast.views_dev.copy_(mapping.views_to_device([v], rast.device)[1])
+        step.targets.copy_(rast.pack([t]))
+        step.run()
+        want.append(rast.loss.item())
+    want_delta = (gm.data - start).cpu().numpy()
+    # pipelined, from pinned host buffers
+    gm2 = mapping.GaussianMap(p)
+    rast2 = mapping.Rasterizer([views[0]], gm2.n, instance_capacity=1 << 18)
+    step2 = mapping.MappingStep(gm2, rast2, rast2.pack([targets[0]]), 0.2)
+    snapshot = (gm2.data.clone(), gm2.m.clone(), gm2.v.clone(), gm2.step.clone())
+    pipe = mapping.HostPipeline(step2, warmup=1)
+    for buf, val in zip((gm2.data, gm2.m, gm2.v, gm2.step), snapshot):
+        buf.copy_(val)  # undo the capture's warm-up iteration
+    got = []
+    for v, t in zip(views, targets):
+        hv = mapping.views_to_device([v], "cpu")[1].pin_memory()
+        ht = torch.as_tensor(np.ascontiguousarray(t, np.float32)).reshape(-1).pin_memory()
+        prev = pipe.submit(ht, hv)
+        if prev is not None:
+            got.append(prev)
+    got.append(pipe.drain())
+    torch.cuda.synchronize()
+    assert len(got) == 4
+    np.testing.assert_allclose(got, want, rtol=1e-5, atol=0)
+    assert U.rel_l2((gm2.data - snapshot[0]).cpu().numpy(), want_delta) < 1e-3
+
+
 def test_cuda_graph_replay_matches_eager():
     """Three iterations replayed from one captured CUDA graph equal three eager
     iterations: same step counter, same gradients of the last iteration and
