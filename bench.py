@@ -51,13 +51,14 @@ PAIR_FLOPS_FWD = 26.0
 PAIR_FLOPS_BWD = 64.0
 
 # DRAM bytes (read + write) of one k_render_bwd launch on the 1M 1200x680
-# workload stored in Z-order with square tile rects, from one single-pass ncu
-# capture per launch shape (tile, backward batch, backward pixels per thread)
+# workload stored in Z-order, from one single-pass ncu capture per launch
+# shape (tile, backward batch, backward pixels per thread) and tile-rect mode
 # of the kernel as committed; other shapes and modes report null.  Summarised with its command in
 # profiles/launches_room1M_1200x680.md.
 RENDER_BWD_TRAFFIC = {
-    ("room1M_1200x680", "8x8", 32, 2): 60.67e6 + 0.83e6,
-    ("room1M_1200x680", "8x8", 64, 2): 60.67e6 + 0.82e6,
+    ("room1M_1200x680", "8x8", 32, 2, "square"): 60.67e6 + 0.83e6,
+    ("room1M_1200x680", "8x8", 64, 2, "square"): 60.67e6 + 0.82e6,
+    ("room1M_1200x680", "8x8", 64, 2, "tight"): 55.92e6 + 0.01e6,
 }
 
 
@@ -644,10 +645,10 @@ def run_gpu(args, ws, rank, local):
         peak = fp32_peak_tflops(peaks["sm_max_mhz"])
         achieved = flops / (stage_ms[dominant] * 1e-3) / 1e12
         traffic = None
-        if (dominant == "render_bwd" and args.map_order == "zorder" and not args.deterministic
-                and args.square_rects):
+        if dominant == "render_bwd" and args.map_order == "zorder" and not args.deterministic:
             traffic = RENDER_BWD_TRAFFIC.get((args.workload, f"{args.tile_w}x{args.tile_h}",
-                                              args.batch_bwd, args.ppt_bwd))
+                                              args.batch_bwd, args.ppt_bwd,
+                                              "square" if args.square_rects else "tight"))
         roof = dict(bound="alu", kernel=dominant, achieved=achieved, peak=peak, unit="TFLOP/s",
                     frac=achieved / peak, traffic=traffic, algorithmic=flops,
                     peak_source="152 SMs x 128 FP32 lanes x 2 x sm_max_mhz (%s)" % peaks["source"])

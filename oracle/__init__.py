@@ -37,7 +37,7 @@ GUARD_RECT, GUARD_NEAR, GUARD_DET, GUARD_KINK, GUARD_DEPTH = 1, 2, 4, 8, 16
 GPX_ALPHA, GPX_TRANS, GPX_POWER, GPX_KINK = 1, 2, 4, 16
 
 NEAR_Z = 0.2
-# Tile rects cut to the tiles that can receive alpha >= 1/255 (reading C4'),
+# Tile rects cut to the tiles that can receive alpha >= 1/255 (reading C19),
 # the default of the GPU path too; tight=False gives the plain 3-sigma squares.
 TIGHT_RECT = True
 
@@ -113,7 +113,7 @@ def ssim_window() -> np.ndarray:
 def project(params, view, tile_w=16, tile_h=16, near_z=NEAR_Z, tight=TIGHT_RECT):
     """Projection of all Gaussians into one view (Sec. II / Sec. III-B).
     tight: tile rects cut to the tiles that can receive alpha >= 1/255
-    (reading C4' in gs_oracle.c); the rendered image is the same."""
+    (reading C19 in gs_oracle.c); the rendered image is the same."""
     n = params["means"].shape[0]
     deg = int(params["sh_degree"])
     means, ls, q = _d(params["means"]), _d(params["log_scales"]), _d(params["quats"])

@@ -81,7 +81,7 @@ static int near_int(double v, double margin) {
  * Square rect (reading C4): [floor((mu-r)/t), floor((mu+r+t-1)/t)) with
  * r = ceil(3 sqrt(lambda_max)) of the dilated 2D covariance.
  *
- * tight = 1 (reading C4'): the square rect intersected with the tiles that
+ * tight = 1 (reading C19): the square rect intersected with the tiles that
  * meet the axis-aligned box of the ellipse outside which alpha < 1/255.
  * alpha = min(0.99, o exp(-q/2)) with q = d^T cov^-1 d, so alpha >= 1/255
  * needs q <= t_a = 2 ln(255 o), and the ellipse q <= t_a has half-widths

@@ -28,7 +28,7 @@ def test_oracle_matches_frozen_record():
 
 def test_tight_rects_change_no_result():
     """Cutting the tile rects to the tiles that can receive alpha >= 1/255
-    (reading C4') drops only (Gaussian, tile) pairs that every pixel skips:
+    (reading C19) drops only (Gaussian, tile) pairs that every pixel skips:
     loss, image, transmittance and gradients equal the frozen square-rect
     record; only the list positions (last_idx) move."""
     with open(os.path.join(HERE, "golden", "oracle_small.json")) as f:

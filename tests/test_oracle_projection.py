@@ -247,7 +247,7 @@ def test_project_bwd_matches_central_differences(degree, offscreen):
 
 
 # ----------------------------------------------------------------------------
-# Tight rects (reading C4'): the square rect cut to the box of the ellipse
+# Tight rects (reading C19): the square rect cut to the box of the ellipse
 # outside which alpha = o exp(-q/2) < 1/255, widened to q <= 1.01 t + 0.01.
 # ----------------------------------------------------------------------------
 @pytest.mark.parametrize("z,log_s,f,logit", [(2.0, -4.0, 300.0, 0.3), (1.0, -3.0, 525.0, -2.0),
