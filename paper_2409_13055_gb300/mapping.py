@@ -531,15 +531,15 @@ class MappingStep:
 class HostPipeline:
     """Mapping iterations fed from pinned host memory: each call to `submit`
     copies one iteration's targets and camera poses host -> device, runs the
-    iteration (two CUDA graphs) and copies its loss device -> host.
+    iteration (one CUDA graph) and copies its loss device -> host.
 
     The copies overlap the compute: the inputs of iteration i go to staging
     buffers on a copy stream while iteration i-1 still runs (they wait only
     until iteration i-1 has taken its own inputs out of the staging buffers),
-    the poses are moved into place before the forward half and the targets
-    before the backward half, and the host reads the loss of iteration i-1
-    while iteration i runs.  `submit` returns the previous iteration's loss
-    (None for the first); `drain` waits for and returns the last one."""
+    are moved into place by two device copies ahead of the graph, and the
+    host reads the loss of iteration i-1 while iteration i runs.  `submit`
+    returns the previous iteration's loss (None for the first); `drain` waits
+    for and returns the last one."""
 
     def __init__(self, step: MappingStep, warmup=2):
         self.step = step
@@ -548,23 +548,19 @@ class HostPipeline:
         self.stage_targets = torch.empty_like(step.targets)
         self.stage_views = torch.empty_like(self.rast.views_dev)
         self.host_loss = [torch.empty(1, dtype=torch.float32).pin_memory() for _ in range(2)]
-        self.ev_views = torch.cuda.Event()
-        self.ev_targets = torch.cuda.Event()
+        self.ev_inputs = torch.cuda.Event()
         self.ev_free = torch.cuda.Event()
         self.ev_loss = [torch.cuda.Event(), torch.cuda.Event()]
         self.i = 0
-        # two graphs: the forward half reads the poses, the backward half the targets
         s = torch.cuda.Stream()
         s.wait_stream(torch.cuda.current_stream())
         with torch.cuda.stream(s):
             for _ in range(warmup):
                 step.run()
         torch.cuda.current_stream().wait_stream(s)
-        self.g_front, self.g_back = torch.cuda.CUDAGraph(), torch.cuda.CUDAGraph()
-        with torch.cuda.graph(self.g_front):
-            step.run_front()
-        with torch.cuda.graph(self.g_back):
-            step.run_back()
+        self.graph = torch.cuda.CUDAGraph()
+        with torch.cuda.graph(self.graph):
+            step.run()
         self.ev_free.record(torch.cuda.current_stream())
 
     def submit(self, host_targets: torch.Tensor, host_views: torch.Tensor):
@@ -573,16 +569,13 @@ class HostPipeline:
         with torch.cuda.stream(cs):
             cs.wait_event(self.ev_free)
             self.stage_views.copy_(host_views, non_blocking=True)
-            self.ev_views.record(cs)
             self.stage_targets.copy_(host_targets, non_blocking=True)
-            self.ev_targets.record(cs)
-        main.wait_event(self.ev_views)
+            self.ev_inputs.record(cs)
+        main.wait_event(self.ev_inputs)
         self.rast.views_dev.copy_(self.stage_views, non_blocking=True)
-        self.g_front.replay()
-        main.wait_event(self.ev_targets)
         self.step.targets.copy_(self.stage_targets, non_blocking=True)
         self.ev_free.record(main)
-        self.g_back.replay()
+        self.graph.replay()
         k = self.i & 1
         self.host_loss[k].copy_(self.rast.loss, non_blocking=True)
         self.ev_loss[k].record(main)
