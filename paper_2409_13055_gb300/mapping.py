@@ -533,23 +533,26 @@ class HostPipeline:
     copies one iteration's targets and camera poses host -> device, runs the
     iteration (one CUDA graph) and copies its loss device -> host.
 
-    The copies overlap the compute: the inputs of iteration i go to staging
-    buffers on a copy stream while iteration i-1 still runs (they wait only
-    until iteration i-1 has taken its own inputs out of the staging buffers),
-    are moved into place by two device copies ahead of the graph, and the
-    host reads the loss of iteration i-1 while iteration i runs.  `submit`
+    No copy sits on the compute stream: inputs and the loss alternate
+    between two sets of device buffers, each set with its own captured graph.
+    The uploads of iteration i (on an upload stream) run while iteration i-1
+    computes from the other set; the loss of iteration i is read back on a
+    download stream once its graph ends, while iteration i+1 runs; a set is
+    refilled only after the loss read of its previous iteration.  `submit`
     returns the previous iteration's loss (None for the first); `drain` waits
     for and returns the last one."""
 
     def __init__(self, step: MappingStep, warmup=2):
         self.step = step
         self.rast = step.rast
-        self.copy_stream = torch.cuda.Stream()
-        self.stage_targets = torch.empty_like(step.targets)
-        self.stage_views = torch.empty_like(self.rast.views_dev)
+        self.up = torch.cuda.Stream()
+        self.down = torch.cuda.Stream()
+        self.targets = [step.targets, torch.empty_like(step.targets)]
+        self.views = [self.rast.views_dev, self.rast.views_dev.clone()]
+        self.loss = [self.rast.loss, torch.zeros_like(self.rast.loss)]
         self.host_loss = [torch.empty(1, dtype=torch.float32).pin_memory() for _ in range(2)]
-        self.ev_inputs = torch.cuda.Event()
-        self.ev_free = torch.cuda.Event()
+        self.ev_in = [torch.cuda.Event(), torch.cuda.Event()]
+        self.ev_done = [torch.cuda.Event(), torch.cuda.Event()]
         self.ev_loss = [torch.cuda.Event(), torch.cuda.Event()]
         self.i = 0
         s = torch.cuda.Stream()
@@ -558,27 +561,39 @@ class HostPipeline:
             for _ in range(warmup):
                 step.run()
         torch.cuda.current_stream().wait_stream(s)
-        self.graph = torch.cuda.CUDAGraph()
-        with torch.cuda.graph(self.graph):
-            step.run()
-        self.ev_free.record(torch.cuda.current_stream())
+        # one graph per buffer set: the buffers' addresses are baked in
+        self.graphs = []
+        for b in range(2):
+            self._use(b)
+            g = torch.cuda.CUDAGraph()
+            with torch.cuda.graph(g):
+                step.run()
+            self.graphs.append(g)
+        self._use(0)
+        main = torch.cuda.current_stream()
+        for e in self.ev_loss:
+            e.record(main)
+
+    def _use(self, b):
+        self.step.targets = self.targets[b]
+        self.rast.views_dev = self.views[b]
+        self.rast.loss = self.loss[b]
 
     def submit(self, host_targets: torch.Tensor, host_views: torch.Tensor):
         main = torch.cuda.current_stream()
-        cs = self.copy_stream
-        with torch.cuda.stream(cs):
-            cs.wait_event(self.ev_free)
-            self.stage_views.copy_(host_views, non_blocking=True)
-            self.stage_targets.copy_(host_targets, non_blocking=True)
-            self.ev_inputs.record(cs)
-        main.wait_event(self.ev_inputs)
-        self.rast.views_dev.copy_(self.stage_views, non_blocking=True)
-        self.step.targets.copy_(self.stage_targets, non_blocking=True)
-        self.ev_free.record(main)
-        self.graph.replay()
-        k = self.i & 1
-        self.host_loss[k].copy_(self.rast.loss, non_blocking=True)
-        self.ev_loss[k].record(main)
+        b = self.i & 1
+        with torch.cuda.stream(self.up):
+            self.up.wait_event(self.ev_loss[b])  # set b's last iteration is read out
+            self.views[b].copy_(host_views, non_blocking=True)
+            self.targets[b].copy_(host_targets, non_blocking=True)
+            self.ev_in[b].record(self.up)
+        main.wait_event(self.ev_in[b])
+        self.graphs[b].replay()
+        self.ev_done[b].record(main)
+        with torch.cuda.stream(self.down):
+            self.down.wait_event(self.ev_done[b])
+            self.host_loss[b].copy_(self.loss[b], non_blocking=True)
+            self.ev_loss[b].record(self.down)
         self.i += 1
         if self.i < 2:
             return None
@@ -591,6 +606,7 @@ class HostPipeline:
             return None
         last = (self.i - 1) & 1
         self.ev_loss[last].synchronize()
+        torch.cuda.current_stream().wait_stream(self.down)
         return float(self.host_loss[last].item())
 
 
