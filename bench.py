@@ -196,17 +196,8 @@ def make_workload(name=WORKLOAD):
 
 
 def z_ordered(p):
-    """The same map stored along a Z-order curve of the means (the GPU path's
-    storage order: a view's visible Gaussians form long runs, so warps of the
-    per-Gaussian kernels cull together).  The set of Gaussians is unchanged."""
-    import torch
-    from paper_2409_13055_gb300 import mapping
-    perm = mapping.morton_order(torch.as_tensor(p["means"], dtype=torch.float64)).numpy()
-    out = {k: (v[perm] if isinstance(v, np.ndarray) and k != "sh" else v) for k, v in p.items()}
-    out["sh"] = np.ascontiguousarray(p["sh"][:, perm])
-    for k in ("means", "log_scales", "quats", "opacity_logits"):
-        out[k] = np.ascontiguousarray(out[k])
-    return out
+    from paper_2409_13055_gb300 import scenes
+    return scenes.z_ordered(p)
 
 
 def run_reference(args, ws, rank):

@@ -33,7 +33,8 @@ _lock = threading.Lock()
 _lib = None
 
 # Guard bits (mirrors of the #defines in gs_oracle.c, which is the authority).
-GUARD_RECT, GUARD_NEAR, GUARD_DET, GUARD_KINK, GUARD_DEPTH = 1, 2, 4, 8, 16
+GUARD_RECT, GUARD_NEAR, GUARD_DET, GUARD_KINK, GUARD_DEPTH, GUARD_TIGHT, GUARD_RADIUS = (
+    1, 2, 4, 8, 16, 32, 64)
 GPX_ALPHA, GPX_TRANS, GPX_POWER, GPX_KINK = 1, 2, 4, 16
 
 NEAR_Z = 0.2

@@ -62,6 +62,12 @@
 #define OR_GUARD_DET 4
 #define OR_GUARD_KINK 8 /* colour clamp or Jacobian clamp close to switching */
 #define OR_GUARD_DEPTH 16 /* FP32 depth key ambiguous (depth next to a rounding midpoint) */
+/* a tight-rect edge (reading C19) or its opacity cut close to switching: the
+ * tile it adds or drops has alpha < 1/255 at every pixel, so the lists may
+ * differ there but no pixel value can */
+#define OR_GUARD_TIGHT 32
+/* 3 sqrt(lambda_max) close to an integer: the radius may differ by one */
+#define OR_GUARD_RADIUS 64
 
 /* Guard bits reported per pixel by oracle_render. */
 #define OR_GPX_ALPHA 1
@@ -96,26 +102,28 @@ static int near_int(double v, double margin) {
 #define OR_TIGHT_MIN_OPACITY (0.999 / 255.0)
 #define OR_G_TIGHT 1e-5 /* tight rect edges in tile units, relative to 1 + h / t */
 
-static int tile_rect(const double mean2d[2], const double cov[3], double det, double opacity,
-                     int tile_w, int tile_h, int tiles_x, int tiles_y, int tight, int rc[4],
-                     int *r_out, int *guard) {
-    double mid = 0.5 * (cov[0] + cov[2]);
-    double lam = mid + sqrt(fmax(0.0, mid * mid - det));
-    double ext = OR_SIGMAS * sqrt(lam);
-    int r = (int)ceil(ext);
-    *r_out = r;
-    if (near_int(ext, OR_G_RADIUS * fmax(1.0, ext))) *guard |= OR_GUARD_RECT;
-    double ex[4] = {(mean2d[0] - r) / tile_w, (mean2d[1] - r) / tile_h,
-                    (mean2d[0] + r + tile_w - 1) / tile_w, (mean2d[1] + r + tile_h - 1) / tile_h};
+/* Square rect of radius r: rc = [floor((mu-r)/t), floor((mu+r+t-1)/t)) clamped
+ * to the grid; ex[k] the unfloored edge values. */
+static void square_rect(const double mean2d[2], int r, int tile_w, int tile_h, int tiles_x,
+                        int tiles_y, int rc[4], double ex[4]) {
+    ex[0] = (mean2d[0] - r) / tile_w;
+    ex[1] = (mean2d[1] - r) / tile_h;
+    ex[2] = (mean2d[0] + r + tile_w - 1) / tile_w;
+    ex[3] = (mean2d[1] + r + tile_h - 1) / tile_h;
     int lim[4] = {tiles_x, tiles_y, tiles_x, tiles_y};
     for (int k = 0; k < 4; k++) {
         double f = floor(ex[k]);
-        if (near_int(ex[k], OR_G_TILE) && f >= -1.0 && f <= lim[k]) *guard |= OR_GUARD_RECT;
         rc[k] = f < 0.0 ? 0 : (f > lim[k] ? lim[k] : (int)f);
     }
+}
+
+/* The tight cut (reading C19) applied to rc in place; returns the area. */
+static int cut_rect(const double mean2d[2], const double cov[3], double opacity, int tile_w,
+                    int tile_h, int tiles_x, int tiles_y, int tight, int rc[4], int *guard) {
     if (tight) {
+        int lim[2] = {tiles_x, tiles_y};
         if (fabs(opacity - OR_TIGHT_MIN_OPACITY) < 1e-6 * OR_TIGHT_MIN_OPACITY)
-            *guard |= OR_GUARD_RECT;
+            *guard |= OR_GUARD_TIGHT;
         if (!(opacity >= OR_TIGHT_MIN_OPACITY)) return 0;
         double t = 1.01 * (2.0 * log(255.0 * opacity)) + 0.01;
         double h[2] = {sqrt(t * cov[0]), sqrt(t * cov[2])};
@@ -124,7 +132,7 @@ static int tile_rect(const double mean2d[2], const double cov[3], double det, do
             double lo = (mean2d[a] - h[a] - tl[a] + 1.0) / tl[a];
             double hi = (mean2d[a] + h[a]) / tl[a];
             double margin = OR_G_TIGHT * (1.0 + h[a] / tl[a]);
-            if (near_int(lo, margin) || near_int(hi, margin)) *guard |= OR_GUARD_RECT;
+            if (near_int(lo, margin) || near_int(hi, margin)) *guard |= OR_GUARD_TIGHT;
             double klo = ceil(lo), khi = floor(hi) + 1.0;
             if (klo > rc[a]) rc[a] = klo > lim[a] ? lim[a] : (int)klo;
             if (khi < rc[a + 2]) rc[a + 2] = khi < 0.0 ? 0 : (int)khi;
@@ -132,6 +140,52 @@ static int tile_rect(const double mean2d[2], const double cov[3], double det, do
     }
     int w = rc[2] - rc[0], hgt = rc[3] - rc[1];
     return (w > 0 && hgt > 0) ? w * hgt : 0;
+}
+
+static int same_rect(const int a[4], int area_a, const int b[4], int area_b) {
+    if (area_a == 0 || area_b == 0) return area_a == area_b;
+    return a[0] == b[0] && a[1] == b[1] && a[2] == b[2] && a[3] == b[3];
+}
+
+/* Guards: OR_GUARD_RADIUS when 3 sqrt(lambda_max) is close to an integer
+ * (the radius itself may differ in FP32); OR_GUARD_RECT only when that, or
+ * a square edge close to a tile boundary, could change the final rect
+ * (checked by computing the rect with the other choice). */
+static int tile_rect(const double mean2d[2], const double cov[3], double det, double opacity,
+                     int tile_w, int tile_h, int tiles_x, int tiles_y, int tight, int rc[4],
+                     int *r_out, int *guard) {
+    double mid = 0.5 * (cov[0] + cov[2]);
+    double lam = mid + sqrt(fmax(0.0, mid * mid - det));
+    double ext = OR_SIGMAS * sqrt(lam);
+    int r = (int)ceil(ext);
+    *r_out = r;
+    double ex[4];
+    int sq[4];
+    square_rect(mean2d, r, tile_w, tile_h, tiles_x, tiles_y, sq, ex);
+    for (int k = 0; k < 4; k++) rc[k] = sq[k];
+    int area = cut_rect(mean2d, cov, opacity, tile_w, tile_h, tiles_x, tiles_y, tight, rc, guard);
+    int alt[4], scratch = 0;
+    double ex2[4];
+    if (near_int(ext, OR_G_RADIUS * fmax(1.0, ext))) {
+        *guard |= OR_GUARD_RADIUS;
+        int k0 = (int)floor(ext + 0.5);
+        square_rect(mean2d, r == k0 ? k0 + 1 : k0, tile_w, tile_h, tiles_x, tiles_y, alt, ex2);
+        int a2 = cut_rect(mean2d, cov, opacity, tile_w, tile_h, tiles_x, tiles_y, tight, alt,
+                          &scratch);
+        if (!same_rect(rc, area, alt, a2)) *guard |= OR_GUARD_RECT;
+    }
+    int lim[4] = {tiles_x, tiles_y, tiles_x, tiles_y};
+    for (int k = 0; k < 4; k++) {
+        if (!near_int(ex[k], OR_G_TILE)) continue;
+        double m = floor(ex[k] + 0.5), f = floor(ex[k]);
+        double g = f == m ? m - 1.0 : m; /* the other floor */
+        for (int j = 0; j < 4; j++) alt[j] = sq[j];
+        alt[k] = g < 0.0 ? 0 : (g > lim[k] ? lim[k] : (int)g);
+        int a2 = cut_rect(mean2d, cov, opacity, tile_w, tile_h, tiles_x, tiles_y, tight, alt,
+                          &scratch);
+        if (!same_rect(rc, area, alt, a2)) *guard |= OR_GUARD_RECT;
+    }
+    return area;
 }
 
 /* ------------------------------------------------------------------------ */

@@ -211,6 +211,21 @@ def views_mixed16(seed=SEED_BASE + 4):
     return views
 
 
+def z_ordered(p):
+    """The same map stored along a Z-order curve of the means (the storage
+    order the benchmark uses: a view's visible Gaussians form long runs, so
+    warps of the per-Gaussian kernels cull together).  The set of Gaussians
+    is unchanged."""
+    import torch
+    from .mapping import morton_order
+    perm = morton_order(torch.as_tensor(p["means"], dtype=torch.float64)).numpy()
+    out = {k: (v[perm] if isinstance(v, np.ndarray) and k != "sh" else v) for k, v in p.items()}
+    out["sh"] = np.ascontiguousarray(p["sh"][:, perm])
+    for k in ("means", "log_scales", "quats", "opacity_logits"):
+        out[k] = np.ascontiguousarray(out[k])
+    return out
+
+
 def workload(name):
     """(params, views, targets, lambda) of a named workload."""
     if name == "planes10k_320x240":

@@ -7,7 +7,12 @@ import oracle
 from paper_2409_13055_gb300 import binding as B
 from paper_2409_13055_gb300 import mapping
 
-FWD_GUARDS = oracle.GUARD_RECT | oracle.GUARD_NEAR | oracle.GUARD_DET | oracle.GUARD_DEPTH
+# decisions that can change a tile list or a radius (all of them) or a pixel
+# value (all but the tight-rect edges, which only move tiles where alpha <
+# 1/255, and a radius change that leaves the rect as it is)
+FWD_GUARDS = (oracle.GUARD_RECT | oracle.GUARD_NEAR | oracle.GUARD_DET | oracle.GUARD_DEPTH |
+              oracle.GUARD_TIGHT | oracle.GUARD_RADIUS)
+PIXEL_GUARDS = oracle.GUARD_RECT | oracle.GUARD_NEAR | oracle.GUARD_DET | oracle.GUARD_DEPTH
 
 
 def gpu_projection(rast: mapping.Rasterizer, n: int, v: int = 0):
@@ -35,33 +40,65 @@ def gpu_tile_lists(rast: mapping.Rasterizer):
     return ranges.cpu().numpy(), keys, vals, c
 
 
-def guard_pixel_mask(view, proj, rout, tile=(16, 16)):
+def guard_pixel_mask(view, proj, rout, tile=(16, 16), params=None,
+                     pixel_bits=oracle.GPX_ALPHA | oracle.GPX_TRANS | oracle.GPX_POWER):
     """Pixels whose value may legitimately differ between an FP32 evaluation and
     the FP64 oracle: a per-pixel decision inside its guard band, or a pixel
     that a Gaussian with a guarded rect / depth key / cull decision reaches with
     alpha >= 1/255 (within radius + one tile of its mean, from the oracle's own
-    mean and conic)."""
+    mean and conic).  A Gaussian the oracle culls at the near plane has no
+    projection to localise it with: with `params` it is projected again with
+    the near plane halved, else every pixel is masked."""
     H, W = view["height"], view["width"]
     tw, th = tile
-    mask = (rout["guard_px"] & (oracle.GPX_ALPHA | oracle.GPX_TRANS | oracle.GPX_POWER)) != 0
-    flagged = np.nonzero(proj["guard"] & FWD_GUARDS)[0]
+    mask = (rout["guard_px"] & pixel_bits) != 0
+    flagged = np.nonzero(proj["guard"] & PIXEL_GUARDS)[0]
     for g in flagged:
-        if proj["opacity"][g] == 0.0:
-            mask[:] = True  # culled by the near plane or determinant: cannot localise it
-            return mask
-        reach = int(proj["radius"][g]) + max(tw, th)
-        cx, cy = proj["mean2d"][g]
+        radius, (cx, cy) = proj["radius"][g], proj["mean2d"][g]
+        (a, b, c), op = proj["conic"][g], proj["opacity"][g]
+        if op == 0.0:
+            if not proj["guard"][g] & (oracle.GUARD_NEAR | oracle.GUARD_DET):
+                continue  # culled on both sides: its other guards do not matter
+            if params is None:
+                mask[:] = True  # culled by the near plane or determinant
+                return mask
+            one = {k: (v[g:g + 1] if k not in ("sh", "sh_degree") else v) for k, v in params.items()}
+            one["sh"] = params["sh"][:, g:g + 1]
+            pg = oracle.project(one, view, tw, th, near_z=0.5 * oracle.NEAR_Z, tight=False)
+            if pg["opacity"][0] == 0.0:
+                mask[:] = True  # culled for another reason: cannot localise it
+                return mask
+            radius, (cx, cy) = pg["radius"][0], pg["mean2d"][0]
+            (a, b, c), op = pg["conic"][0], pg["opacity"][0]
+        reach = int(radius) + max(tw, th)
         xa, xb = max(0, int(np.floor(cx)) - reach), min(W, int(np.ceil(cx)) + reach + 1)
         ya, yb = max(0, int(np.floor(cy)) - reach), min(H, int(np.ceil(cy)) + reach + 1)
         if xa >= xb or ya >= yb:
             continue
         yy, xx = np.mgrid[ya:yb, xa:xb]
         dx, dy = cx - xx, cy - yy
-        a, b, c = proj["conic"][g]
         power = -0.5 * (a * dx * dx + c * dy * dy) - b * dx * dy
-        alpha = proj["opacity"][g] * np.exp(np.minimum(power, 0.0))
+        alpha = op * np.exp(np.minimum(power, 0.0))
         mask[ya:yb, xa:xb] |= alpha >= (1.0 / 255.0) * 0.999
     return mask
+
+
+def gaussians_clear_of(mask, proj, window=5):
+    """Gaussians whose every pixel with alpha >= 1/255 (bounded by the square
+    of its radius around its mean) lies at least `window` pixels away from a
+    masked pixel: their gradients cannot feel a guard-band decision (the
+    SSIM window spreads a pixel's value over `window` pixels each way).
+    Culled Gaussians count as clear."""
+    H, W = mask.shape
+    sat = np.zeros((H + 1, W + 1), np.int64)
+    sat[1:, 1:] = np.cumsum(np.cumsum(mask.astype(np.int64), 0), 1)
+    r = proj["radius"].astype(np.int64) + window + 1
+    cx = np.round(proj["mean2d"][:, 0]).astype(np.int64)
+    cy = np.round(proj["mean2d"][:, 1]).astype(np.int64)
+    xa, xb = np.clip(cx - r, 0, W), np.clip(cx + r + 1, 0, W)
+    ya, yb = np.clip(cy - r, 0, H), np.clip(cy + r + 1, 0, H)
+    hits = sat[yb, xb] - sat[ya, xb] - sat[yb, xa] + sat[ya, xa]
+    return (proj["tiles_touched"] == 0) | (hits == 0)
 
 
 def grad_pixel_mask(rout):
