@@ -295,7 +295,7 @@ __device__ __forceinline__ void project_one(const float* mean, const Shape& sh, 
 }
 
 template <int DEG>
-__global__ void __launch_bounds__(kProjThreads)
+__global__ void __launch_bounds__(kProjThreads, 4)
 k_project(const float* __restrict__ means, const float* __restrict__ log_scales,
           const float* __restrict__ quats, const float* __restrict__ opacity_logits,
           const float* __restrict__ sh, int n, const gs_view* __restrict__ views,
