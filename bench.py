@@ -531,8 +531,12 @@ def run_gpu(args, ws, rank, local):
                    ("adam_sparse", lambda: (rast.visibility(gm.n, vis),
                                             gm.adam_step(visible=vis)))]
     else:
-        stages += [("project_bwd", lambda: rast.project_bwd(m, g)),
-                   ("adam", lambda: gm.adam_step())]
+        # as MappingStep runs it: the gradient of groups of 32 Gaussians that
+        # touch no tile is neither written nor read (same update)
+        gvis = torch.zeros((gm.n + B.GS_GRAD_GROUP - 1) // B.GS_GRAD_GROUP, dtype=torch.uint8,
+                           device="cuda")
+        stages += [("project_bwd", lambda: rast.project_bwd_groups(m, g, gvis)),
+                   ("adam", lambda: gm.adam_step(group_vis=gvis))]
     # warm-up (eager), then capture one graph per stage
     for _ in range(max(args.warmup, 3)):
         for _, f in stages:

@@ -316,6 +316,30 @@ gs_status gs_adam_step(float *params, const float *grads, float *m, float *v, in
                        const float *group_lr_host, float beta1, float beta2, float eps,
                        int32_t *step_dev, void *stream);
 
+/* A8 + A9 without the known zeros (no paper counterpart; the same results
+ * as gs_project_bwd with accumulate = 0 followed by gs_adam_step).  The
+ * Gaussians form groups of GS_GRAD_GROUP consecutive indices; a group none
+ * of whose Gaussians touches a tile in any view of the last gs_project has
+ * an all-zero gradient.
+ * gs_project_bwd_groups: the projection adjoint, writing the gradients of the
+ * other groups only (those of the zero groups are left as they were) and
+ * group_vis[k] = 1 or 0 (device uint8 [ceil(n / GS_GRAD_GROUP)]) for
+ * written or not.
+ * gs_adam_step_groups: gs_adam_step with the groups, strides and planes of
+ * gs_adam_step_sparse, reading the gradient only where group_vis is 1 and
+ * taking it as zero elsewhere; the floats after a group's last whole plane
+ * (padding, zero) are left as they are, as gs_adam_step leaves them. */
+#define GS_GRAD_GROUP 32
+gs_status gs_project_bwd_groups(const gs_plan *plan, const gs_map *map, const gs_view *views_dev,
+                                const void *ws, const gs_map_grad *grads, uint8_t *group_vis,
+                                void *stream);
+gs_status gs_adam_step_groups(float *params, const float *grads, float *m, float *v,
+                              int64_t n_floats, int32_t n_groups,
+                              const int64_t *group_offsets_host, const float *group_lr_host,
+                              const int32_t *group_stride_host, int32_t n_gauss,
+                              const uint8_t *group_vis, float beta1, float beta2, float eps,
+                              int32_t *step_dev, void *stream);
+
 /* Visibility of the last gs_project: vis[i] = 1 (device uint8 [n]) if
  * Gaussian i touches a tile in any view of the plan, else 0. */
 gs_status gs_visibility(const gs_plan *plan, int32_t n, const void *ws, uint8_t *vis,

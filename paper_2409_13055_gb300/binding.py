@@ -99,6 +99,11 @@ _SIGNATURES = {
     "gs_adam_step_sparse": (c_int32, [c_void_p, c_void_p, c_void_p, c_void_p, c_int64, c_int32,
                                       _P(c_int64), _P(c_float), _P(c_int32), c_int32, c_void_p,
                                       c_float, c_float, c_float, c_void_p, c_void_p]),
+    "gs_project_bwd_groups": (c_int32, [_P(gs_plan), _P(gs_map), c_void_p, c_void_p,
+                                        _P(gs_map_grad), c_void_p, c_void_p]),
+    "gs_adam_step_groups": (c_int32, [c_void_p, c_void_p, c_void_p, c_void_p, c_int64, c_int32,
+                                      _P(c_int64), _P(c_float), _P(c_int32), c_int32, c_void_p,
+                                      c_float, c_float, c_float, c_void_p, c_void_p]),
     "gs_densify_stats": (c_int32, [_P(gs_plan), c_int32, c_void_p, c_void_p, c_void_p,
                                    c_void_p]),
     "gs_densify_scratch_bytes": (c_size_t, [c_int32]),
@@ -293,6 +298,27 @@ def gs_adam_step_sparse(params, grads, m, v, group_offsets, group_lr, group_stri
                                     int(params.numel()), ng, offs, lrs, strides, int(n_gauss),
                                     _ptr(vis), float(beta1), float(beta2), float(eps),
                                     _ptr(step_dev), _stream(stream)), "gs_adam_step_sparse")
+
+
+GS_GRAD_GROUP = 32
+
+
+def gs_project_bwd_groups(plan, gmap, views_dev, ws, grads, group_vis, stream=None):
+    check(lib().gs_project_bwd_groups(ctypes.byref(plan), ctypes.byref(gmap), _ptr(views_dev),
+                                      _ptr(ws), ctypes.byref(grads), _ptr(group_vis),
+                                      _stream(stream)), "gs_project_bwd_groups")
+
+
+def gs_adam_step_groups(params, grads, m, v, group_offsets, group_lr, group_strides, n_gauss,
+                        group_vis, beta1, beta2, eps, step_dev, stream=None):
+    ng = len(group_lr)
+    offs = (c_int64 * (ng + 1))(*[int(x) for x in group_offsets])
+    lrs = (c_float * ng)(*[float(x) for x in group_lr])
+    strides = (c_int32 * ng)(*[int(x) for x in group_strides])
+    check(lib().gs_adam_step_groups(_ptr(params), _ptr(grads), _ptr(m), _ptr(v),
+                                    int(params.numel()), ng, offs, lrs, strides, int(n_gauss),
+                                    _ptr(group_vis), float(beta1), float(beta2), float(eps),
+                                    _ptr(step_dev), _stream(stream)), "gs_adam_step_groups")
 
 
 def gs_densify_stats(plan, n, ws, accum, denom, stream=None):

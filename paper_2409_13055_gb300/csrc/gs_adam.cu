@@ -189,6 +189,68 @@ k_adam_sparse(float* __restrict__ params, const float* __restrict__ grads, float
         sparse_plane<1>(params, grads, m, v, base, len, vis, lr, b1, b2, eps, s_bc[0], s_bc[1]);
 }
 
+// Dense Adam with the gradient of whole groups of 32 consecutive Gaussians
+// taken as zero and not read where group_vis[group] == 0 (groups that touch
+// no tile, whose gradient the projection adjoint left unwritten): the update
+// of k_adam, bit for bit, without the loads of known zeros.  Float j of a
+// plane of S floats per Gaussian belongs to Gaussian j / S; a grid-stride
+// loop over every plane, a float4 per thread and trip (VEC) or a float.
+template <bool VEC>
+__global__ void __launch_bounds__(kAdamThreads)
+k_adam_groups(float* __restrict__ params, const float* __restrict__ grads, float* __restrict__ m,
+              float* __restrict__ v, Planes planes, uint32_t n_gauss,
+              const uint8_t* __restrict__ gvis, float b1, float b2, float eps,
+              const int32_t* __restrict__ step) {
+    __shared__ float s_bc[2];
+    if (threadIdx.x == 0) adam_bias(b1, b2, *step, s_bc[0], s_bc[1]);
+    __syncthreads();
+    const float ibc1 = s_bc[0], ibc2 = s_bc[1];
+    const uint32_t t0 = blockIdx.x * blockDim.x + threadIdx.x, stride = gridDim.x * blockDim.x;
+    for (int pl = 0; pl < planes.count; ++pl) {
+        const uint32_t S = planes.stride[pl], len = S * n_gauss, base = planes.start[pl];
+        const float lr = planes.lr[pl];
+        auto scalar = [&](uint32_t j) {
+            const uint32_t i = base + j;
+            float p = params[i], mm = m[i], vv = v[i];
+            const float g = gvis[(j / S) >> 5] ? grads[i] : 0.0f;
+            adam1(p, g, mm, vv, lr, b1, b2, eps, ibc1, ibc2);
+            params[i] = p;
+            m[i] = mm;
+            v[i] = vv;
+        };
+        if (VEC) {
+            const uint32_t n4 = len >> 2;
+            for (uint32_t f = t0; f < n4; f += stride) {
+                const uint32_t j = 4u * f, q = (base + j) >> 2;
+                float4 p = reinterpret_cast<float4*>(params)[q];
+                float4 mm = reinterpret_cast<float4*>(m)[q];
+                float4 vv = reinterpret_cast<float4*>(v)[q];
+                const bool v0 = gvis[(j / S) >> 5] != 0, v3 = gvis[((j + 3) / S) >> 5] != 0;
+                float4 g = make_float4(0.0f, 0.0f, 0.0f, 0.0f);
+                if (v0 && v3) {
+                    g = __ldcs(reinterpret_cast<const float4*>(grads) + q);
+                } else if (v0 || v3) {  // the four floats straddle two groups
+                    const float* gp = grads + base + j;
+                    g.x = gvis[(j / S) >> 5] ? gp[0] : 0.0f;
+                    g.y = gvis[((j + 1) / S) >> 5] ? gp[1] : 0.0f;
+                    g.z = gvis[((j + 2) / S) >> 5] ? gp[2] : 0.0f;
+                    g.w = gvis[((j + 3) / S) >> 5] ? gp[3] : 0.0f;
+                }
+                adam1(p.x, g.x, mm.x, vv.x, lr, b1, b2, eps, ibc1, ibc2);
+                adam1(p.y, g.y, mm.y, vv.y, lr, b1, b2, eps, ibc1, ibc2);
+                adam1(p.z, g.z, mm.z, vv.z, lr, b1, b2, eps, ibc1, ibc2);
+                adam1(p.w, g.w, mm.w, vv.w, lr, b1, b2, eps, ibc1, ibc2);
+                reinterpret_cast<float4*>(params)[q] = p;
+                reinterpret_cast<float4*>(m)[q] = mm;
+                reinterpret_cast<float4*>(v)[q] = vv;
+            }
+            if (t0 < (len & 3u)) scalar(4u * n4 + t0);  // the last len % 4 floats
+        } else {
+            for (uint32_t j = t0; j < len; j += stride) scalar(j);
+        }
+    }
+}
+
 __global__ void k_visibility(int n, int n_views, const uint32_t* __restrict__ touched,
                              uint8_t* __restrict__ vis) {
     const int g = blockIdx.x * blockDim.x + threadIdx.x;
@@ -237,6 +299,35 @@ gs_status launch_adam_sparse(float* params, const float* grads, float* m, float*
     k_adam_sparse<<<dim3(bx, pl.count), kAdamThreads, 0, st>>>(params, grads, m, v, pl,
                                                                (uint32_t)n_gauss, vis, b1, b2,
                                                                eps, step_dev);
+    return launch_status();
+}
+
+gs_status launch_adam_groups(float* params, const float* grads, float* m, float* v, int64_t n,
+                             int32_t n_groups, const int64_t* offs, const float* lrs,
+                             const int32_t* strides, int32_t n_gauss, const uint8_t* group_vis,
+                             float b1, float b2, float eps, int32_t* step_dev, cudaStream_t st) {
+    if (n >= (int64_t(1) << 31)) return GS_ERR_UNSUPPORTED;
+    Planes pl{};
+    bool vec = ((reinterpret_cast<uintptr_t>(params) | reinterpret_cast<uintptr_t>(grads) |
+                 reinterpret_cast<uintptr_t>(m) | reinterpret_cast<uintptr_t>(v)) & 15) == 0;
+    for (int k = 0; k < n_groups; ++k) {
+        const int s = strides[k];
+        if (s != 1 && s != 3 && s != 4) return GS_ERR_UNSUPPORTED;
+        const int64_t plane = (int64_t)s * n_gauss;
+        for (int64_t o = offs[k]; o + plane <= offs[k + 1]; o += plane) {
+            if (pl.count == kMaxPlanes) return GS_ERR_UNSUPPORTED;
+            pl.start[pl.count] = (uint32_t)o;
+            pl.stride[pl.count] = (uint8_t)s;
+            pl.lr[pl.count] = lrs[k];
+            if (o & 3) vec = false;
+            ++pl.count;
+        }
+    }
+    if (pl.count == 0) return GS_ERR_INVALID;
+    k_step_inc<<<1, 1, 0, st>>>(step_dev);
+    auto* kern = vec ? k_adam_groups<true> : k_adam_groups<false>;
+    kern<<<kAdamBlocks, kAdamThreads, 0, st>>>(params, grads, m, v, pl, (uint32_t)n_gauss,
+                                               group_vis, b1, b2, eps, step_dev);
     return launch_status();
 }
 

@@ -250,6 +250,45 @@ extern "C" gs_status gs_project_bwd(const gs_plan* plan, const gs_map* map,
                               accumulate ? 1 : 0, S(stream));
 }
 
+extern "C" gs_status gs_project_bwd_groups(const gs_plan* plan, const gs_map* map,
+                                           const gs_view* views_dev, const void* ws,
+                                           const gs_map_grad* grads, uint8_t* group_vis,
+                                           void* stream) {
+    if (!plan_ok(plan) || !views_dev || !ws || !grads || !group_vis) return GS_ERR_INVALID;
+    if (!map_ok(P(plan), map)) return GS_ERR_INVALID;
+    if (!grads->means || !grads->log_scales || !grads->quats || !grads->opacity_logits ||
+        !grads->sh)
+        return GS_ERR_INVALID;
+    return launch_project_bwd(P(plan), map, views_dev, const_cast<void*>(ws), grads, 0,
+                              S(stream), group_vis);
+}
+
+extern "C" gs_status gs_adam_step_groups(float* params, const float* grads, float* m, float* v,
+                                         int64_t n_floats, int32_t n_groups,
+                                         const int64_t* group_offsets_host,
+                                         const float* group_lr_host,
+                                         const int32_t* group_stride_host, int32_t n_gauss,
+                                         const uint8_t* group_vis, float beta1, float beta2,
+                                         float eps, int32_t* step_dev, void* stream) {
+    if (!params || !grads || !m || !v || !step_dev || !group_offsets_host || !group_lr_host ||
+        !group_stride_host || !group_vis || n_gauss < 1)
+        return GS_ERR_INVALID;
+    if (n_floats < 1 || n_groups < 1 || n_groups > GS_MAX_GROUPS) return GS_ERR_INVALID;
+    if (group_offsets_host[0] != 0 || group_offsets_host[n_groups] != n_floats)
+        return GS_ERR_INVALID;
+    for (int g = 0; g < n_groups; ++g) {
+        if (group_offsets_host[g + 1] < group_offsets_host[g]) return GS_ERR_INVALID;
+        if (group_stride_host[g] < 1 ||
+            (int64_t)group_stride_host[g] * n_gauss >= (int64_t(1) << 31))
+            return GS_ERR_INVALID;
+    }
+    if (!(beta1 >= 0.0f && beta1 < 1.0f && beta2 >= 0.0f && beta2 < 1.0f && eps >= 0.0f))
+        return GS_ERR_INVALID;
+    return launch_adam_groups(params, grads, m, v, n_floats, n_groups, group_offsets_host,
+                              group_lr_host, group_stride_host, n_gauss, group_vis, beta1, beta2,
+                              eps, step_dev, S(stream));
+}
+
 static bool grad_ok(const gs_map_grad* g) {
     return g && g->means && g->log_scales && g->quats && g->opacity_logits && g->sh;
 }

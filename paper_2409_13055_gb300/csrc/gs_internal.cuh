@@ -224,7 +224,12 @@ gs_status launch_render_bwd(const Plan* p, const gs_map* map, const gs_view* vie
 gs_status launch_render_bwd_pixels(const Plan* p, void* ws, const float* final_T,
                                    const int32_t* last_idx, const float* dL, cudaStream_t st);
 gs_status launch_project_bwd(const Plan* p, const gs_map* map, const gs_view* views_dev,
-                             void* ws, const gs_map_grad* grads, int accumulate, cudaStream_t st);
+                             void* ws, const gs_map_grad* grads, int accumulate, cudaStream_t st,
+                             uint8_t* group_vis = nullptr);
+gs_status launch_adam_groups(float* params, const float* grads, float* m, float* v, int64_t n,
+                             int32_t n_groups, const int64_t* offs, const float* lrs,
+                             const int32_t* strides, int32_t n_gauss, const uint8_t* group_vis,
+                             float b1, float b2, float eps, int32_t* step_dev, cudaStream_t st);
 gs_status launch_step_inc(int32_t* step_dev, cudaStream_t st);
 gs_status launch_project_bwd_adam(const Plan* p, const gs_map* map, const gs_view* views_dev,
                                   void* ws, const gs_map_grad* params, const gs_map_grad* m,

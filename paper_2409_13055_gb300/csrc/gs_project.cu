@@ -363,6 +363,20 @@ k_project(const float* __restrict__ means, const float* __restrict__ log_scales,
     }
 }
 
+// Whether any Gaussian of this warp's group of 32 touches a tile in any view
+// (a warp-wide vote; every lane of the warp must call it).  Lane 0 records the
+// answer in group_vis[g / 32] when given.
+__device__ __forceinline__ bool group_touched(int g, int n, int n_views,
+                                              const uint32_t* __restrict__ touched,
+                                              uint8_t* __restrict__ group_vis) {
+    bool mine = false;
+    if (g < n)
+        for (int v = 0; v < n_views; ++v) mine |= touched[(size_t)v * n + g] != 0u;
+    const bool any = __any_sync(0xffffffffu, mine);
+    if (group_vis && (threadIdx.x & 31) == 0 && g < n) group_vis[g >> 5] = any ? 1 : 0;
+    return any;
+}
+
 // A8: chain rule of the projection for Gaussian g, summed over the views it
 // is visible in: screen-space gradient -> gradients of the mean, log-scales,
 // quaternion and opacity logit.  The colour gradient that reaches the SH
@@ -579,7 +593,9 @@ __device__ __forceinline__ void adjoint_one(
 
 
 // DIRECT (single-view plans): the SH gradient is written here and k_sh_bwd
-// is not launched.
+// is not launched.  With group_vis, a warp's 32 Gaussians form a group: a
+// group none of whose Gaussians touches a tile in any view (all-zero
+// gradient) writes nothing, and group_vis[group] records which groups wrote.
 template <int DEG, bool DIRECT>
 __global__ void __launch_bounds__(kProjThreads, 2)
 k_project_bwd(const float* __restrict__ means, const float* __restrict__ log_scales,
@@ -588,11 +604,13 @@ k_project_bwd(const float* __restrict__ means, const float* __restrict__ log_sca
               ViewTable vt, float near_z, const uint32_t* __restrict__ touched,
               const float* __restrict__ grad2d, float* __restrict__ gcol_out,
               float* __restrict__ g_means, float* __restrict__ g_ls, float* __restrict__ g_quats,
-              float* __restrict__ g_logit, float* __restrict__ g_sh, int accumulate) {
+              float* __restrict__ g_logit, float* __restrict__ g_sh, int accumulate,
+              uint8_t* __restrict__ group_vis) {
     extern __shared__ Cam cam_all[];
     for (int v = threadIdx.x; v < vt.n_views; v += blockDim.x) load_cam(views[v], cam_all[v]);
     __syncthreads();
     const int g = blockIdx.x * blockDim.x + threadIdx.x;
+    if (group_vis && !group_touched(g, n, vt.n_views, touched, group_vis)) return;
     if (g >= n) return;
     float gm[3], gls[3], glog;
     float4 gq4;
@@ -626,11 +644,12 @@ template <int DEG>
 __global__ void __launch_bounds__(kProjThreads)
 k_sh_bwd(const float* means, int n, const gs_view* __restrict__ views, ViewTable vt,
          const uint32_t* __restrict__ touched, const float* __restrict__ gcol_in,
-         float* __restrict__ g_sh, int accumulate) {
+         float* __restrict__ g_sh, int accumulate, int groups) {
     extern __shared__ Cam cam_all[];
     for (int v = threadIdx.x; v < vt.n_views; v += blockDim.x) load_cam(views[v], cam_all[v]);
     __syncthreads();
     const int g = blockIdx.x * blockDim.x + threadIdx.x;
+    if (groups && !group_touched(g, n, vt.n_views, touched, nullptr)) return;
     if (g >= n) return;
     constexpr int K = (DEG + 1) * (DEG + 1);
     const float mean[3] = {means[3 * g], means[3 * g + 1], means[3 * g + 2]};
@@ -875,7 +894,7 @@ gs_status launch_project(const Plan* p, const gs_map* map, const gs_view* views_
 static gs_status launch_project_adjoint(const Plan* p, const gs_map* map,
                                         const gs_view* views_dev, void* ws,
                                         const gs_map_grad* grads, int accumulate,
-                                        cudaStream_t st) {
+                                        uint8_t* group_vis, cudaStream_t st) {
     const int n = map->n;
     const size_t smem = sizeof(Cam) * p->vt.n_views;
     const int blocks = (n + kProjThreads - 1) / kProjThreads;
@@ -892,15 +911,15 @@ static gs_status launch_project_adjoint(const Plan* p, const gs_map* map,
         map->means, map->log_scales, map->quats, map->opacity_logits, map->sh, n, views_dev,
         p->vt, p->cfg.near_z, buf<uint32_t>(p, ws, GS_BUF_TOUCHED),
         buf<float>(p, ws, GS_BUF_GRAD2D), buf<float>(p, ws, B_GCOL), grads->means,
-        grads->log_scales, grads->quats, grads->opacity_logits, grads->sh, accumulate);
+        grads->log_scales, grads->quats, grads->opacity_logits, grads->sh, accumulate, group_vis);
     return launch_status();
 }
 
 gs_status launch_project_bwd(const Plan* p, const gs_map* map, const gs_view* views_dev,
                              void* ws, const gs_map_grad* grads, int accumulate,
-                             cudaStream_t st) {
+                             cudaStream_t st, uint8_t* group_vis) {
     if (reinterpret_cast<uintptr_t>(grads->quats) % 16) return GS_ERR_INVALID;
-    gs_status s = launch_project_adjoint(p, map, views_dev, ws, grads, accumulate, st);
+    gs_status s = launch_project_adjoint(p, map, views_dev, ws, grads, accumulate, group_vis, st);
     if (s != GS_OK || p->vt.n_views == 1) return s;  // one view: SH gradient already written
     const int n = map->n;
     auto* kern_sh = map->sh_degree == 0   ? k_sh_bwd<0>
@@ -909,7 +928,7 @@ gs_status launch_project_bwd(const Plan* p, const gs_map* map, const gs_view* vi
                                           : k_sh_bwd<3>;
     kern_sh<<<(n + kProjThreads - 1) / kProjThreads, kProjThreads, sizeof(Cam) * p->vt.n_views,
               st>>>(map->means, n, views_dev, p->vt, buf<uint32_t>(p, ws, GS_BUF_TOUCHED),
-                    buf<float>(p, ws, B_GCOL), grads->sh, accumulate);
+                    buf<float>(p, ws, B_GCOL), grads->sh, accumulate, group_vis ? 1 : 0);
     return launch_status();
 }
 

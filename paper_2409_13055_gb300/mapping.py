@@ -234,11 +234,19 @@ class GaussianMap:
         return offsets, [lr[g] for g in GROUPS]
 
     def adam_step(self, lr=None, extent=1.0, beta1=0.9, beta2=0.999, eps=1e-15, stream=None,
-                  visible=None):
+                  visible=None, group_vis=None):
         """One Adam step; with visible (device uint8 [n], e.g. from
-        Rasterizer.visibility) the visibility-masked variant."""
+        Rasterizer.visibility) the visibility-masked variant; with group_vis
+        (from Rasterizer.project_bwd_groups) the same dense step, the
+        gradient of the zero groups not read."""
         offs, rates = self.adam_groups(lr, extent)
-        if visible is None:
+        if (visible is not None or group_vis is not None) and self.capacity != self.n:
+            raise ValueError("the masked and grouped steps need a map without spare capacity")
+        if group_vis is not None:
+            B.gs_adam_step_groups(self.data, self.grad, self.m, self.v, offs, rates,
+                                  GROUP_STRIDES, self.n, group_vis, beta1, beta2, eps, self.step,
+                                  stream)
+        elif visible is None:
             B.gs_adam_step(self.data, self.grad, self.m, self.v, offs, rates, beta1, beta2, eps,
                            self.step, stream)
         else:
@@ -369,6 +377,12 @@ class Rasterizer:
     def project_bwd(self, gmap: B.gs_map, grads: B.gs_map_grad, accumulate=False, stream=None):
         B.gs_project_bwd(self.plan, gmap, self.views_dev, self.ws, grads, accumulate, stream)
 
+    def project_bwd_groups(self, gmap: B.gs_map, grads: B.gs_map_grad, group_vis, stream=None):
+        """The projection adjoint writing only groups of GS_GRAD_GROUP
+        Gaussians that touch a tile (group_vis records which)."""
+        B.gs_project_bwd_groups(self.plan, gmap, self.views_dev, self.ws, grads, group_vis,
+                                stream)
+
     def project_bwd_adam(self, gmap: GaussianMap, lr=None, extent=1.0, grads_acc=None,
                          grads_out=None, beta1=0.9, beta2=0.999, eps=1e-15, stream=None):
         """Projection adjoint fused with one Adam step on gmap (in place)."""
@@ -471,6 +485,13 @@ class MappingStep:
         # run again (bit-identically) between the loss and the adjoint, as
         # when the forward's intermediates were not kept
         self.recompute = bool(recompute)
+        # without keep_grads the gradient of groups of GS_GRAD_GROUP Gaussians
+        # that touch no tile (all zero) is neither written nor read
+        self.groups = (not keep_grads and not fused and self.visible is None
+                       and gmap.capacity == gmap.n)
+        if self.groups:
+            ng = (gmap.n + B.GS_GRAD_GROUP - 1) // B.GS_GRAD_GROUP
+            self.group_vis = torch.zeros(ng, dtype=torch.uint8, device=gmap.device)
         self.graph = None
         self._m = gmap.gs_map()
         self._g = gmap.gs_map_grad()
@@ -502,10 +523,16 @@ class MappingStep:
             r.project_bwd_adam(self.gmap, self.lr, self.extent,
                                grads_out=self._g if self.keep_grads else None, stream=stream)
         else:
-            r.render_bwd(self._m, self._g, accumulate=False, stream=stream)
-            if self.visible is not None:
-                r.visibility(self.gmap.n, self.visible, stream)
-            self.gmap.adam_step(self.lr, self.extent, stream=stream, visible=self.visible)
+            if self.groups:
+                r.render_bwd_pixels(stream=stream)
+                r.project_bwd_groups(self._m, self._g, self.group_vis, stream)
+                self.gmap.adam_step(self.lr, self.extent, stream=stream,
+                                    group_vis=self.group_vis)
+            else:
+                r.render_bwd(self._m, self._g, accumulate=False, stream=stream)
+                if self.visible is not None:
+                    r.visibility(self.gmap.n, self.visible, stream)
+                self.gmap.adam_step(self.lr, self.extent, stream=stream, visible=self.visible)
         if self.stats is not None:
             r.densify_stats(self.gmap.n, self.stats[0], self.stats[1], stream)
 

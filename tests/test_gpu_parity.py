@@ -499,6 +499,34 @@ def test_autograd_function_and_recompute_mode():
         assert U.rel_l2(gk.cpu().numpy(), og[name]) < 5e-4, name
 
 
+def test_grouped_adjoint_and_adam_are_bit_identical():
+    """Without keep_grads, MappingStep neither writes nor reads the gradient
+    of groups of 32 Gaussians that touch no tile: the parameters and moments
+    after three iterations equal the dense path's bit for bit (deterministic
+    adjoint, so both see the same gradients), with both kinds of group
+    present (the map in Z-order, so a view's invisible Gaussians cluster)."""
+    p, view = CASES["room20k_sh3"]()
+    p = scenes.z_ordered(p)
+    target = scenes.random_target(view, 77)
+    out = []
+    for keep in (True, False):
+        gm = mapping.GaussianMap(p)
+        rast = mapping.Rasterizer([view], gm.n, instance_capacity=1 << 20, tile=(8, 8),
+                                  pixels_per_thread_bwd=2, deterministic=True)
+        step = mapping.MappingStep(gm, rast, rast.pack([target]), 0.2, keep_grads=keep)
+        assert step.groups == (not keep)
+        for _ in range(3):
+            step.run()
+        torch.cuda.synchronize()
+        out.append((gm.data.clone(), gm.m.clone(), gm.v.clone(), gm.step.item()))
+        if not keep:
+            gv = step.group_vis.cpu().numpy()
+            assert gv.min() == 0 and gv.max() == 1, np.bincount(gv)
+    assert out[0][3] == out[1][3] == 3
+    for a, b in zip(out[0][:3], out[1][:3]):
+        assert torch.equal(a, b)
+
+
 def test_host_pipeline_matches_direct_steps():
     """HostPipeline (inputs copied from pinned host memory on a copy stream,
     loss read back one iteration late) gives the losses and updates of
