@@ -193,8 +193,59 @@ k_adam_sparse(float* __restrict__ params, const float* __restrict__ grads, float
 // taken as zero and not read where group_vis[group] == 0 (groups that touch
 // no tile, whose gradient the projection adjoint left unwritten): the update
 // of k_adam, bit for bit, without the loads of known zeros.  Float j of a
-// plane of S floats per Gaussian belongs to Gaussian j / S; a grid-stride
-// loop over every plane, a float4 per thread and trip (VEC) or a float.
+// plane of S floats per Gaussian belongs to Gaussian j / S (S a compile-time
+// 1, 3 or 4, so the division is a multiply); a grid-stride loop over the
+// plane, a float4 per thread and trip (VEC) or a float.
+template <int S, bool VEC>
+__device__ __forceinline__ void groups_plane(float* __restrict__ params,
+                                             const float* __restrict__ grads,
+                                             float* __restrict__ m, float* __restrict__ v,
+                                             uint32_t base, uint32_t len,
+                                             const uint8_t* __restrict__ gvis, float lr,
+                                             float b1, float b2, float eps, float ibc1,
+                                             float ibc2, uint32_t t0, uint32_t stride) {
+    auto scalar = [&](uint32_t j) {
+        const uint32_t i = base + j;
+        float p = params[i], mm = m[i], vv = v[i];
+        const float g = gvis[(j / S) >> 5] ? grads[i] : 0.0f;
+        adam1(p, g, mm, vv, lr, b1, b2, eps, ibc1, ibc2);
+        params[i] = p;
+        m[i] = mm;
+        v[i] = vv;
+    };
+    if (VEC) {
+        const uint32_t n4 = len >> 2;
+        for (uint32_t f = t0; f < n4; f += stride) {
+            const uint32_t j = 4u * f, q = (base + j) >> 2;
+            float4 p = reinterpret_cast<float4*>(params)[q];
+            float4 mm = reinterpret_cast<float4*>(m)[q];
+            float4 vv = reinterpret_cast<float4*>(v)[q];
+            const uint32_t ga = (j / S) >> 5, gb = ((j + 3) / S) >> 5;
+            const bool va = gvis[ga] != 0, vb = ga == gb ? va : gvis[gb] != 0;
+            float4 g = make_float4(0.0f, 0.0f, 0.0f, 0.0f);
+            if (va && vb) {
+                g = __ldcs(reinterpret_cast<const float4*>(grads) + q);
+            } else if (va || vb) {  // the four floats straddle two groups
+                const float* gp = grads + base + j;
+                g.x = ((j / S) >> 5) == ga ? (va ? gp[0] : 0.0f) : (vb ? gp[0] : 0.0f);
+                g.y = (((j + 1) / S) >> 5) == ga ? (va ? gp[1] : 0.0f) : (vb ? gp[1] : 0.0f);
+                g.z = (((j + 2) / S) >> 5) == ga ? (va ? gp[2] : 0.0f) : (vb ? gp[2] : 0.0f);
+                g.w = vb ? gp[3] : 0.0f;
+            }
+            adam1(p.x, g.x, mm.x, vv.x, lr, b1, b2, eps, ibc1, ibc2);
+            adam1(p.y, g.y, mm.y, vv.y, lr, b1, b2, eps, ibc1, ibc2);
+            adam1(p.z, g.z, mm.z, vv.z, lr, b1, b2, eps, ibc1, ibc2);
+            adam1(p.w, g.w, mm.w, vv.w, lr, b1, b2, eps, ibc1, ibc2);
+            reinterpret_cast<float4*>(params)[q] = p;
+            reinterpret_cast<float4*>(m)[q] = mm;
+            reinterpret_cast<float4*>(v)[q] = vv;
+        }
+        if (t0 < (len & 3u)) scalar(4u * n4 + t0);  // the last len % 4 floats
+    } else {
+        for (uint32_t j = t0; j < len; j += stride) scalar(j);
+    }
+}
+
 template <bool VEC>
 __global__ void __launch_bounds__(kAdamThreads)
 k_adam_groups(float* __restrict__ params, const float* __restrict__ grads, float* __restrict__ m,
@@ -207,47 +258,17 @@ k_adam_groups(float* __restrict__ params, const float* __restrict__ grads, float
     const float ibc1 = s_bc[0], ibc2 = s_bc[1];
     const uint32_t t0 = blockIdx.x * blockDim.x + threadIdx.x, stride = gridDim.x * blockDim.x;
     for (int pl = 0; pl < planes.count; ++pl) {
-        const uint32_t S = planes.stride[pl], len = S * n_gauss, base = planes.start[pl];
+        const uint32_t S = planes.stride[pl], base = planes.start[pl];
         const float lr = planes.lr[pl];
-        auto scalar = [&](uint32_t j) {
-            const uint32_t i = base + j;
-            float p = params[i], mm = m[i], vv = v[i];
-            const float g = gvis[(j / S) >> 5] ? grads[i] : 0.0f;
-            adam1(p, g, mm, vv, lr, b1, b2, eps, ibc1, ibc2);
-            params[i] = p;
-            m[i] = mm;
-            v[i] = vv;
-        };
-        if (VEC) {
-            const uint32_t n4 = len >> 2;
-            for (uint32_t f = t0; f < n4; f += stride) {
-                const uint32_t j = 4u * f, q = (base + j) >> 2;
-                float4 p = reinterpret_cast<float4*>(params)[q];
-                float4 mm = reinterpret_cast<float4*>(m)[q];
-                float4 vv = reinterpret_cast<float4*>(v)[q];
-                const bool v0 = gvis[(j / S) >> 5] != 0, v3 = gvis[((j + 3) / S) >> 5] != 0;
-                float4 g = make_float4(0.0f, 0.0f, 0.0f, 0.0f);
-                if (v0 && v3) {
-                    g = __ldcs(reinterpret_cast<const float4*>(grads) + q);
-                } else if (v0 || v3) {  // the four floats straddle two groups
-                    const float* gp = grads + base + j;
-                    g.x = gvis[(j / S) >> 5] ? gp[0] : 0.0f;
-                    g.y = gvis[((j + 1) / S) >> 5] ? gp[1] : 0.0f;
-                    g.z = gvis[((j + 2) / S) >> 5] ? gp[2] : 0.0f;
-                    g.w = gvis[((j + 3) / S) >> 5] ? gp[3] : 0.0f;
-                }
-                adam1(p.x, g.x, mm.x, vv.x, lr, b1, b2, eps, ibc1, ibc2);
-                adam1(p.y, g.y, mm.y, vv.y, lr, b1, b2, eps, ibc1, ibc2);
-                adam1(p.z, g.z, mm.z, vv.z, lr, b1, b2, eps, ibc1, ibc2);
-                adam1(p.w, g.w, mm.w, vv.w, lr, b1, b2, eps, ibc1, ibc2);
-                reinterpret_cast<float4*>(params)[q] = p;
-                reinterpret_cast<float4*>(m)[q] = mm;
-                reinterpret_cast<float4*>(v)[q] = vv;
-            }
-            if (t0 < (len & 3u)) scalar(4u * n4 + t0);  // the last len % 4 floats
-        } else {
-            for (uint32_t j = t0; j < len; j += stride) scalar(j);
-        }
+        if (S == 3)
+            groups_plane<3, VEC>(params, grads, m, v, base, 3u * n_gauss, gvis, lr, b1, b2, eps,
+                                 ibc1, ibc2, t0, stride);
+        else if (S == 4)
+            groups_plane<4, VEC>(params, grads, m, v, base, 4u * n_gauss, gvis, lr, b1, b2, eps,
+                                 ibc1, ibc2, t0, stride);
+        else
+            groups_plane<1, VEC>(params, grads, m, v, base, n_gauss, gvis, lr, b1, b2, eps, ibc1,
+                                 ibc2, t0, stride);
     }
 }
 
