@@ -64,6 +64,7 @@ def _L():
             lib = ctypes.CDLL(_LIB_PATH)
             lib.oracle_project.restype = ctypes.c_int
             lib.oracle_bin.restype = ctypes.c_int64
+            lib.oracle_bin_spans.restype = ctypes.c_int64
             lib.oracle_loss_l1_ssim.restype = ctypes.c_double
             _lib = lib
     return _lib
@@ -134,8 +135,10 @@ def project(params, view, tile_w=16, tile_h=16, near_z=NEAR_Z, tight=TIGHT_RECT)
     return out
 
 
-def bin_tiles(depth_key, rect, tiles_touched, tiles_x, tiles_y):
-    """Per-tile Gaussian lists in (FP32 depth, index) order (Sec. II depth sorting)."""
+def bin_tiles(depth_key, rect, tiles_touched, tiles_x, tiles_y, spans_of=None, tile=(16, 16)):
+    """Per-tile Gaussian lists in (FP32 depth, index) order (Sec. II depth sorting).
+    Every tile of each rect, or, with spans_of = a projection made with
+    tight=True, each rect's row spans (reading C19)."""
     n = len(tiles_touched)
     dk = np.ascontiguousarray(depth_key, dtype=np.float32)
     rect = np.ascontiguousarray(rect, dtype=np.int32)
@@ -143,8 +146,14 @@ def bin_tiles(depth_key, rect, tiles_touched, tiles_x, tiles_y):
     total = int(tt.astype(np.int64).sum())
     start = np.zeros(tiles_x * tiles_y + 1, np.int64)
     lst = np.zeros(max(total, 1), np.int32)
-    got = _L().oracle_bin(_i(n), _p(dk), _p(rect), _p(tt), _i(tiles_x), _i(tiles_y),
-                          _p(start), _p(lst), ctypes.c_int64(lst.size))
+    if spans_of is None:
+        got = _L().oracle_bin(_i(n), _p(dk), _p(rect), _p(tt), _i(tiles_x), _i(tiles_y),
+                              _p(start), _p(lst), ctypes.c_int64(lst.size))
+    else:
+        got = _L().oracle_bin_spans(
+            _i(n), _p(dk), _p(rect), _p(tt), _p(_d(spans_of["mean2d"])),
+            _p(_d(spans_of["cov2d"])), _p(_d(spans_of["opacity"])), _i(tile[0]), _i(tile[1]),
+            _i(tiles_x), _i(tiles_y), _p(start), _p(lst), ctypes.c_int64(lst.size))
     assert got == total
     return start, lst[:total]
 
@@ -269,7 +278,8 @@ def forward_view(params, view, tile_w=16, tile_h=16, bg=(0.0, 0.0, 0.0), near_z=
     proj = project(params, view, tile_w, tile_h, near_z, tight)
     tx, ty = tile_grid(view["width"], view["height"], tile_w, tile_h)
     start, lst = bin_tiles(proj["depth"].astype(np.float32), proj["rect"],
-                           proj["tiles_touched"], tx, ty)
+                           proj["tiles_touched"], tx, ty, proj if tight else None,
+                           (tile_w, tile_h))
     out = render(proj, start, lst, view, tile_w, tile_h, bg)
     return proj, start, lst, out
 

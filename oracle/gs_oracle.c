@@ -117,7 +117,56 @@ static void square_rect(const double mean2d[2], int r, int tile_w, int tile_h, i
     }
 }
 
-/* The tight cut (reading C19) applied to rc in place; returns the area. */
+/* Tiles of tile row ty that meet the widened ellipse d^T cov^-1 d <= t
+ * (reading C19, per row): the band of pixel rows ty*th .. ty*th+th-1 cuts
+ * the ellipse in a convex set whose x-extent is [xmin, xmax]; tiles
+ * [ceil((mu_x + xmin - tw + 1)/tw), floor((mu_x + xmax)/tw)] meet it, clipped
+ * to [rx0, rx1).  For fixed dy the ellipse spans x = (b/c) dy +- sqrt(det
+ * (t c - dy^2))/c; over the band, x is largest at dy* = b sqrt(t/a) (x =
+ * sqrt(t a)) when dy* lies in the band, else at a band end (the upper edge
+ * is concave in dy); symmetrically for the smallest x at -dy*.  Returns the
+ * number of tiles; decisions within the tight margin are flagged. */
+static int row_span(const double mean2d[2], const double cov[3], double t, int ty, int tile_w,
+                    int tile_h, int rx0, int rx1, int *x0, int *x1, int *guard) {
+    const double a = cov[0], b = cov[1], c = cov[2], det = a * c - b * b;
+    const double Y = sqrt(t * c), X = sqrt(t * a);
+    double lo = ty * (double)tile_h - mean2d[1], hi = lo + tile_h - 1.0;
+    const double my = 1e-5 * (1.0 + Y);
+    if (fabs(lo - Y) < my || fabs(hi + Y) < my) *guard |= OR_GUARD_TIGHT;
+    if (lo > Y || hi < -Y) return 0;
+    if (lo < -Y) lo = -Y;
+    if (hi > Y) hi = Y;
+    const double ds = b * sqrt(t / a);
+    double xmax, xmin;
+    if (lo <= ds && ds <= hi) {
+        xmax = X;
+    } else {
+        const double e0 = (b / c) * lo + sqrt(fmax(0.0, det * (t * c - lo * lo))) / c;
+        const double e1 = (b / c) * hi + sqrt(fmax(0.0, det * (t * c - hi * hi))) / c;
+        xmax = e0 > e1 ? e0 : e1;
+    }
+    if (lo <= -ds && -ds <= hi) {
+        xmin = -X;
+    } else {
+        const double e0 = (b / c) * lo - sqrt(fmax(0.0, det * (t * c - lo * lo))) / c;
+        const double e1 = (b / c) * hi - sqrt(fmax(0.0, det * (t * c - hi * hi))) / c;
+        xmin = e0 < e1 ? e0 : e1;
+    }
+    const double el = (mean2d[0] + xmin - tile_w + 1.0) / tile_w, eh = (mean2d[0] + xmax) / tile_w;
+    const double m = OR_G_TIGHT * (1.0 + X / tile_w);
+    if (near_int(el, m) || near_int(eh, m)) *guard |= OR_GUARD_TIGHT;
+    double klo = ceil(el), khi = floor(eh) + 1.0;
+    int k0 = klo < rx0 ? rx0 : (klo > rx1 ? rx1 : (int)klo);
+    int k1 = khi > rx1 ? rx1 : (khi < rx0 ? rx0 : (int)khi);
+    *x0 = k0;
+    *x1 = k1;
+    return k1 > k0 ? k1 - k0 : 0;
+}
+
+static double tight_level(double opacity) { return 1.01 * (2.0 * log(255.0 * opacity)) + 0.01; }
+
+/* The tight cut (reading C19) applied to rc in place; returns the number of
+ * tiles (the box of the widened ellipse, then its row spans). */
 static int cut_rect(const double mean2d[2], const double cov[3], double opacity, int tile_w,
                     int tile_h, int tiles_x, int tiles_y, int tight, int rc[4], int *guard) {
     if (tight) {
@@ -125,7 +174,7 @@ static int cut_rect(const double mean2d[2], const double cov[3], double opacity,
         if (fabs(opacity - OR_TIGHT_MIN_OPACITY) < 1e-6 * OR_TIGHT_MIN_OPACITY)
             *guard |= OR_GUARD_TIGHT;
         if (!(opacity >= OR_TIGHT_MIN_OPACITY)) return 0;
-        double t = 1.01 * (2.0 * log(255.0 * opacity)) + 0.01;
+        double t = tight_level(opacity);
         double h[2] = {sqrt(t * cov[0]), sqrt(t * cov[2])};
         double tl[2] = {tile_w, tile_h};
         for (int a = 0; a < 2; a++) {
@@ -137,6 +186,11 @@ static int cut_rect(const double mean2d[2], const double cov[3], double opacity,
             if (klo > rc[a]) rc[a] = klo > lim[a] ? lim[a] : (int)klo;
             if (khi < rc[a + 2]) rc[a + 2] = khi < 0.0 ? 0 : (int)khi;
         }
+        if (rc[2] <= rc[0] || rc[3] <= rc[1]) return 0;
+        int total = 0, x0, x1;
+        for (int ty = rc[1]; ty < rc[3]; ty++)
+            total += row_span(mean2d, cov, t, ty, tile_w, tile_h, rc[0], rc[2], &x0, &x1, guard);
+        return total;
     }
     int w = rc[2] - rc[0], hgt = rc[3] - rc[1];
     return (w > 0 && hgt > 0) ? w * hgt : 0;
@@ -576,6 +630,50 @@ int64_t oracle_bin(int n, const float *depth_key, const int *rect, const int *ti
     for (int64_t t = 0; t < T; t++) {
         tile_start[t] = p;
         while (p < total && buf[p].tile == t) {
+            list[p] = buf[p].idx;
+            p++;
+        }
+    }
+    tile_start[T] = total;
+    free(buf);
+    return total;
+}
+
+/* The same with tight rects (reading C19): each Gaussian's tiles are the row
+ * spans of its rect (row_span), from its projected mean, 2D covariance and
+ * opacity. */
+int64_t oracle_bin_spans(int n, const float *depth_key, const int *rect, const int *tiles_touched,
+                         const double *mean2d, const double *cov2d, const double *opacity,
+                         int tile_w, int tile_h, int tiles_x, int tiles_y, int64_t *tile_start,
+                         int32_t *list, int64_t list_cap) {
+    int64_t total = 0;
+    for (int i = 0; i < n; i++) total += tiles_touched[i];
+    if (total > list_cap) return -1;
+    inst_t *buf = (inst_t *)malloc(sizeof(inst_t) * (size_t)(total > 0 ? total : 1));
+    int64_t k = 0;
+    for (int i = 0; i < n; i++) {
+        if (tiles_touched[i] <= 0) continue;
+        const double t = tight_level(opacity[i]);
+        for (int ty = rect[4 * i + 1]; ty < rect[4 * i + 3]; ty++) {
+            int x0, x1, g = 0;
+            row_span(mean2d + 2 * i, cov2d + 3 * i, t, ty, tile_w, tile_h, rect[4 * i + 0],
+                     rect[4 * i + 2], &x0, &x1, &g);
+            for (int tx = x0; tx < x1; tx++) {
+                if (k == total) { free(buf); return -2; } /* spans disagree with the count */
+                buf[k].tile = (int64_t)ty * tiles_x + tx;
+                buf[k].depth = depth_key[i];
+                buf[k].idx = i;
+                k++;
+            }
+        }
+    }
+    if (k != total) { free(buf); return -2; }
+    qsort(buf, (size_t)total, sizeof(inst_t), inst_cmp);
+    int64_t T = (int64_t)tiles_x * tiles_y;
+    int64_t p = 0;
+    for (int64_t tt = 0; tt < T; tt++) {
+        tile_start[tt] = p;
+        while (p < total && buf[p].tile == tt) {
             list[p] = buf[p].idx;
             p++;
         }

@@ -266,7 +266,16 @@ def test_tight_rect_isotropic_closed_form(z, log_s, f, logit):
            math.floor((W / 2 + h) / 16) + 1, math.floor((H / 2 + h) / 16) + 1]
     want = [max(sq[0], box[0]), max(sq[1], box[1]), min(sq[2], box[2]), min(sq[3], box[3])]
     assert list(pr["rect"][0]) == want
-    assert pr["tiles_touched"][0] == (want[2] - want[0]) * (want[3] - want[1])
+    # the tiles of the box whose pixel square comes within h of the centre
+    # (a circle here: distance from the centre to the tile's pixel rectangle)
+    cx, cy = W / 2, H / 2
+    n = 0
+    for ty in range(want[1], want[3]):
+        for tx in range(want[0], want[2]):
+            ddx = max(tx * 16 - cx, 0.0, cx - (tx * 16 + 15))
+            ddy = max(ty * 16 - cy, 0.0, cy - (ty * 16 + 15))
+            n += ddx * ddx + ddy * ddy <= h * h
+    assert pr["tiles_touched"][0] == n
 
 
 def test_tight_rect_empty_below_alpha_threshold():
@@ -279,12 +288,29 @@ def test_tight_rect_empty_below_alpha_threshold():
                           tight=False)["tiles_touched"][0] > 0
 
 
+def _min_q_over_rect(a, b, c, x0, x1, y0, y1):
+    """min of q = a x^2 + 2 b x y + c y^2 over the rectangle [x0,x1] x [y0,y1]
+    (coordinates relative to the centre; a, c > 0, ac > b^2)."""
+    if x0 <= 0 <= x1 and y0 <= 0 <= y1:
+        return 0.0
+    best = np.inf
+    for x in (x0, x1):  # vertical edges: minimise over y in [y0, y1]
+        y = min(max(-b * x / c, y0), y1)
+        best = min(best, a * x * x + 2 * b * x * y + c * y * y)
+    for y in (y0, y1):
+        x = min(max(-b * y / a, x0), x1)
+        best = min(best, a * x * x + 2 * b * x * y + c * y * y)
+    return best
+
+
 @pytest.mark.parametrize("tile", [(16, 16), (8, 8)])
-def test_tight_rect_drops_only_tiles_without_alpha(tile):
-    """Brute force over pixels: every tile of the square rect left out of the
-    tight rect has alpha < 1/255 at all its pixels (alpha evaluated from the
-    projected mean, conic and opacity as the renderer does), and the tight
-    rect lies inside the square one."""
+def test_tight_tiles_are_exactly_those_meeting_the_ellipse(tile):
+    """Brute force over pixels and tiles: each Gaussian's tight tiles (its
+    row spans, read back from the tight binning) are exactly the tiles of
+    its square rect whose pixel rectangle meets the widened ellipse
+    q <= 1.01 * 2 ln(255 o) + 0.01 (q in the conic), which holds every
+    pixel with alpha >= 1/255; every other tile of the square rect has alpha
+    < 1/255 at all its pixels."""
     tw, th = tile
     W, H = 160, 120
     rng = np.random.default_rng(5)
@@ -297,22 +323,36 @@ def test_tight_rect_drops_only_tiles_without_alpha(tile):
              opacity_logits=rng.normal(-1.0, 2.0, n), sh=np.zeros((1, n, 3)), sh_degree=0)
     sq = oracle.project(p, view, tw, th, tight=False)
     ti = oracle.project(p, view, tw, th, tight=True)
+    tx_n, ty_n = oracle.tile_grid(W, H, tw, th)
+    start, lst = oracle.bin_tiles(ti["depth"].astype(np.float32), ti["rect"], ti["tiles_touched"],
+                                  tx_n, ty_n, ti, tile)
+    tiles_of = [set() for _ in range(n)]
+    for tile_id in range(tx_n * ty_n):
+        for g in lst[start[tile_id]:start[tile_id + 1]]:
+            tiles_of[g].add(tile_id)
     ys, xs = np.mgrid[0:H, 0:W]
-    dropped = 0
+    dropped = kept = 0
     for i in np.flatnonzero(sq["tiles_touched"] > 0):
         a, b, c = sq["conic"][i]
-        dx, dy = xs - sq["mean2d"][i, 0], ys - sq["mean2d"][i, 1]
-        alpha = np.minimum(0.99, sq["opacity"][i] * np.exp(-0.5 * (a * dx * dx + c * dy * dy)
-                                                           - b * dx * dy))
-        s0, t0 = sq["rect"][i], ti["rect"][i]
-        if ti["tiles_touched"][i] > 0:
-            assert s0[0] <= t0[0] and s0[1] <= t0[1] and t0[2] <= s0[2] and t0[3] <= s0[3]
+        mx, my = sq["mean2d"][i]
+        o = sq["opacity"][i]
+        dx, dy = xs - mx, ys - my
+        alpha = np.minimum(0.99, o * np.exp(-0.5 * (a * dx * dx + c * dy * dy) - b * dx * dy))
+        lvl = 1.01 * 2 * np.log(255 * o) + 0.01 if 255 * o >= 0.999 else -1.0
+        s0 = sq["rect"][i]
+        assert len(tiles_of[i]) == ti["tiles_touched"][i]
         for ty in range(s0[1], s0[3]):
             for tx in range(s0[0], s0[2]):
-                inside = (ti["tiles_touched"][i] > 0 and t0[0] <= tx < t0[2]
-                          and t0[1] <= ty < t0[3])
+                inside = ty * tx_n + tx in tiles_of[i]
+                qmin = _min_q_over_rect(a, b, c, tx * tw - mx, tx * tw + tw - 1 - mx,
+                                        ty * th - my, ty * th + th - 1 - my)
+                meets = lvl >= 0 and qmin <= lvl
+                if ti["guard"][i] & oracle.GUARD_TIGHT == 0 and abs(qmin - lvl) > 1e-9 * (1 + lvl):
+                    assert inside == meets, (i, tx, ty, qmin, lvl)
                 if not inside:
                     dropped += 1
                     blk = alpha[ty * th:(ty + 1) * th, tx * tw:(tx + 1) * tw]
                     assert blk.max() < 1 / 255, (i, tx, ty, blk.max())
-    assert dropped > 50  # the cut is not vacuous on this scene
+                else:
+                    kept += 1
+    assert dropped > 50 and kept > 50  # the cut is not vacuous on this scene
