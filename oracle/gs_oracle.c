@@ -165,6 +165,10 @@ static int row_span(const double mean2d[2], const double cov[3], double t, int t
 
 static double tight_level(double opacity) { return 1.01 * (2.0 * log(255.0 * opacity)) + 0.01; }
 
+/* Row spans apply to boxes of at most this many tile rows; a taller box keeps
+ * all its tiles (a bound on the per-Gaussian span storage). */
+#define OR_SPAN_ROWS 16
+
 /* The tight cut (reading C19) applied to rc in place; returns the number of
  * tiles (the box of the widened ellipse, then its row spans). */
 static int cut_rect(const double mean2d[2], const double cov[3], double opacity, int tile_w,
@@ -187,6 +191,7 @@ static int cut_rect(const double mean2d[2], const double cov[3], double opacity,
             if (khi < rc[a + 2]) rc[a + 2] = khi < 0.0 ? 0 : (int)khi;
         }
         if (rc[2] <= rc[0] || rc[3] <= rc[1]) return 0;
+        if (rc[3] - rc[1] > OR_SPAN_ROWS) return (rc[2] - rc[0]) * (rc[3] - rc[1]);
         int total = 0, x0, x1;
         for (int ty = rc[1]; ty < rc[3]; ty++)
             total += row_span(mean2d, cov, t, ty, tile_w, tile_h, rc[0], rc[2], &x0, &x1, guard);
@@ -610,7 +615,12 @@ int64_t oracle_bin(int n, const float *depth_key, const int *rect, const int *ti
                    int tiles_x, int tiles_y, int64_t *tile_start, int32_t *list,
                    int64_t list_cap) {
     int64_t total = 0;
-    for (int i = 0; i < n; i++) total += tiles_touched[i];
+    for (int i = 0; i < n; i++) {
+        total += tiles_touched[i];
+        if (tiles_touched[i] > 0 &&
+            tiles_touched[i] != (rect[4 * i + 2] - rect[4 * i + 0]) * (rect[4 * i + 3] - rect[4 * i + 1]))
+            return -2; /* counts that are not the rect areas: not this function's lists */
+    }
     if (total > list_cap) return -1;
     inst_t *buf = (inst_t *)malloc(sizeof(inst_t) * (size_t)(total > 0 ? total : 1));
     int64_t k = 0;
@@ -654,10 +664,12 @@ int64_t oracle_bin_spans(int n, const float *depth_key, const int *rect, const i
     for (int i = 0; i < n; i++) {
         if (tiles_touched[i] <= 0) continue;
         const double t = tight_level(opacity[i]);
+        const int tall = rect[4 * i + 3] - rect[4 * i + 1] > OR_SPAN_ROWS;
         for (int ty = rect[4 * i + 1]; ty < rect[4 * i + 3]; ty++) {
-            int x0, x1, g = 0;
-            row_span(mean2d + 2 * i, cov2d + 3 * i, t, ty, tile_w, tile_h, rect[4 * i + 0],
-                     rect[4 * i + 2], &x0, &x1, &g);
+            int x0 = rect[4 * i + 0], x1 = rect[4 * i + 2], g = 0;
+            if (!tall)
+                row_span(mean2d + 2 * i, cov2d + 3 * i, t, ty, tile_w, tile_h, rect[4 * i + 0],
+                         rect[4 * i + 2], &x0, &x1, &g);
             for (int tx = x0; tx < x1; tx++) {
                 if (k == total) { free(buf); return -2; } /* spans disagree with the count */
                 buf[k].tile = (int64_t)ty * tiles_x + tx;

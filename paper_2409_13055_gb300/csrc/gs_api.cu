@@ -129,6 +129,7 @@ extern "C" gs_status gs_plan_init(gs_plan* plan, const gs_config* cfg, int32_t n
     len[B_OFFSETS] = (size_t)(VN + 1) * sizeof(uint32_t);
     len[B_TILE_ORDER] = (size_t)tiles * sizeof(uint32_t);
     len[B_TILE_QUEUE] = 2 * sizeof(uint32_t);
+    len[B_SPANS] = cfg->tight_rect ? (size_t)VN * kSpanRows * sizeof(uint32_t) : 0;
     len[B_GID_OF] = cfg->deterministic ? (size_t)instance_capacity * sizeof(uint32_t) : 0;
     len[B_PARTIAL] = cfg->deterministic ? (size_t)instance_capacity * 11 * sizeof(float) : 0;
     size_t off = 0;

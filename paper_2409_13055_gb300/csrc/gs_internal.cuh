@@ -58,6 +58,8 @@ enum PrivBuf {
                    // (deterministic plans: the sort then carries emission positions)
     B_PARTIAL,     // [instance_capacity] x 11 floats: per-(Gaussian, tile) partial sums
                    // of the pixel adjoint (deterministic plans)
+    B_SPANS,       // [V*n] x kSpanRows u32: tight row spans, x0 | x1 << 16 per tile row
+                   // (tight plans; Gaussians whose box has at most kSpanRows rows)
     B_TOTAL
 };
 
@@ -177,6 +179,85 @@ __device__ __forceinline__ int df_floor_div(float hi, float lo, float inv_t) {
     float fa = floorf(a);
     if (fa == a && lo < 0.0f) fa -= 1.0f;
     return (int)fa;
+}
+
+// Tight tiles, row by row: the level of the widened ellipse q <= t outside
+// which alpha = o exp(-q/2) < 1/255 with a margin (t = 1.01 * 2 ln(255 o) +
+// 0.01), and the tiles of tile row ty (clipped to [rx0, rx1)) whose band of
+// pixel rows meets it.  q = A dx^2 + 2 B dx dy + C dy^2 in the conic (A, B, C);
+// for a fixed dy the ellipse spans dx = (-B dy +- sqrt(A t - D dy^2)) / A,
+// D = AC - B^2; over the band the largest dx is sqrt(t C / D) when the row of
+// the ellipse's rightmost point, dy* = -(B / C) sqrt(t C / D), lies in the band,
+// else the larger band end; the smallest symmetrically at -dy*.  The
+// projection computes the spans once and stores them (B_SPANS) for the
+// emission to list; a box of more than kSpanRows tile rows keeps all its
+// tiles.
+constexpr int kSpanRows = 16;
+__device__ __forceinline__ float tight_level(float opacity) {
+    return __fmaf_rn(1.01f, __fmul_rn(2.0f, logf(__fmul_rn(255.0f, opacity))), 0.01f);
+}
+
+struct TightEllipse {
+    float mxh, mxl, myh, myl;  // mean as float pairs
+    float X, Y;                // x- and y-half-extents of the widened ellipse
+    float ds;                  // row of its rightmost point, relative to the mean
+    float negB, invA, At, D;   // -B, 1/A, A t, AC - B^2
+};
+
+static __device__ __forceinline__ TightEllipse tight_ellipse(float mxh, float mxl, float myh,
+                                                          float myl, float A, float B, float C,
+                                                          float opacity) {
+    TightEllipse E;
+    const float t = tight_level(opacity);
+    E.mxh = mxh; E.mxl = mxl; E.myh = myh; E.myl = myl;
+    E.D = __fsub_rn(__fmul_rn(A, C), __fmul_rn(B, B));
+    E.Y = __fsqrt_rn(__fdiv_rn(__fmul_rn(t, A), E.D));
+    E.X = __fsqrt_rn(__fdiv_rn(__fmul_rn(t, C), E.D));
+    E.ds = -__fmul_rn(__fdiv_rn(B, C), E.X);
+    E.negB = -B;
+    E.invA = __frcp_rn(A);
+    E.At = __fmul_rn(A, t);
+    return E;
+}
+
+static __device__ __forceinline__ int tight_row_span(const TightEllipse& E, int ty, int log2_tw,
+                                                  int log2_th, int rx0, int rx1, int* x0,
+                                                  int* x1) {
+    const float th = (float)(1 << log2_th), tw = (float)(1 << log2_tw);
+    float lo = __fsub_rn(__fsub_rn(__fmul_rn((float)ty, th), E.myh), E.myl);
+    float hi = __fadd_rn(lo, __fsub_rn(th, 1.0f));
+    *x0 = *x1 = rx0;
+    if (lo > E.Y || hi < -E.Y) return 0;
+    lo = fmaxf(lo, -E.Y);
+    hi = fminf(hi, E.Y);
+    auto half = [&](float dy) {
+        return __fsqrt_rn(fmaxf(0.0f, __fsub_rn(E.At, __fmul_rn(E.D, __fmul_rn(dy, dy)))));
+    };
+    float xmax, xmin;
+    if (lo <= E.ds && E.ds <= hi) {
+        xmax = E.X;
+    } else {
+        xmax = fmaxf(__fmul_rn(__fadd_rn(__fmul_rn(E.negB, lo), half(lo)), E.invA),
+                     __fmul_rn(__fadd_rn(__fmul_rn(E.negB, hi), half(hi)), E.invA));
+    }
+    if (lo <= -E.ds && -E.ds <= hi) {
+        xmin = -E.X;
+    } else {
+        xmin = fminf(__fmul_rn(__fsub_rn(__fmul_rn(E.negB, lo), half(lo)), E.invA),
+                     __fmul_rn(__fsub_rn(__fmul_rn(E.negB, hi), half(hi)), E.invA));
+    }
+    // tiles [ceil((mu + xmin - T + 1) / T), floor((mu + xmax) / T)], mu as a pair
+    const float it = __frcp_rn(tw);  // exact: a power of two
+    float s, e;
+    two_sum(E.mxh, __fsub_rn(xmin, __fsub_rn(tw, 1.0f)), s, e);
+    fast_two_sum(s, __fadd_rn(e, E.mxl), s, e);
+    const int k0 = -df_floor_div(-s, -e, it);
+    two_sum(E.mxh, xmax, s, e);
+    fast_two_sum(s, __fadd_rn(e, E.mxl), s, e);
+    const int k1 = df_floor_div(s, e, it) + 1;
+    *x0 = min(max(k0, rx0), rx1);
+    *x1 = max(min(k1, rx1), *x0);
+    return *x1 - *x0;
 }
 
 // The Gaussian's weight at a pixel, evaluated identically by the forward and

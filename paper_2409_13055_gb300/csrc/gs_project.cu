@@ -266,7 +266,7 @@ __device__ __forceinline__ void project_one(const float* mean, const Shape& sh, 
         // k T .. k T + T - 1, so tiles [ceil((mu - h - T + 1) / T),
         // floor((mu + h) / T)] meet [mu - h, mu + h].
         if (!(opacity >= kTightMinOpacity)) return;
-        const float t = __fmaf_rn(1.01f, 2.0f * logf(255.0f * opacity), 0.01f);
+        const float t = tight_level(opacity);
         const float hx = sqrtf(t * p.a), hy = sqrtf(t * p.c);
         two_sum(p.mxh, -(hx + tw1), sh_, e2);
         fast_two_sum(sh_, __fadd_rn(e2, p.mxl), sh_, sl);
@@ -301,7 +301,8 @@ k_project(const float* __restrict__ means, const float* __restrict__ log_scales,
           const float* __restrict__ sh, int n, const gs_view* __restrict__ views,
           ViewTable vt, float near_z, float4* __restrict__ rec, uint16_t* __restrict__ rect_out,
           uint32_t* __restrict__ touched, int32_t* __restrict__ radius_out,
-          uint32_t* __restrict__ dkey, uint32_t* __restrict__ dval, DevCounters* counters) {
+          uint32_t* __restrict__ dkey, uint32_t* __restrict__ dval, DevCounters* counters,
+          uint32_t* __restrict__ spans) {
     __shared__ Cam cams[kViewsPerThread];
     const int v0 = blockIdx.y * kViewsPerThread;
     const int nv = min(kViewsPerThread, vt.n_views - v0);
@@ -328,7 +329,25 @@ k_project(const float* __restrict__ means, const float* __restrict__ log_scales,
         Proj p;
         project_one(mean, shp, cams[j], near_z, vt.log2_tw, vt.log2_th, geo.tiles_x,
                     geo.tiles_y, opacity, vt.tight_rect, p);
-        const bool vis = finite && p.visible;
+        bool vis = finite && p.visible;
+        uint32_t area = 0u;
+        if (vis) {
+            area = (uint32_t)((p.rect[2] - p.rect[0]) * (p.rect[3] - p.rect[1]));
+            if (vt.tight_rect && p.rect[3] - p.rect[1] <= kSpanRows) {
+                // the row spans of the box, stored for the emission
+                const TightEllipse E =
+                    tight_ellipse(p.mxh, p.mxl, p.myh, p.myl, p.ca, p.cb, p.cc, opacity);
+                uint32_t* sp = spans + vg * kSpanRows;
+                int a0, a1;
+                area = 0u;
+                for (int ty = p.rect[1]; ty < p.rect[3]; ++ty) {
+                    area += (uint32_t)tight_row_span(E, ty, vt.log2_tw, vt.log2_th, p.rect[0],
+                                                     p.rect[2], &a0, &a1);
+                    sp[ty - p.rect[1]] = (uint32_t)a0 | ((uint32_t)a1 << 16);
+                }
+                vis = area > 0u;
+            }
+        }
         dval[vg] = (uint32_t)vg;
         if (!vis) {
             touched[vg] = 0u;
@@ -353,7 +372,7 @@ k_project(const float* __restrict__ means, const float* __restrict__ log_scales,
         r[0] = make_float4(p.mxh, p.myh, p.mxl, p.myl);
         r[1] = make_float4(p.ca, p.cb, p.cc, opacity);
         r[2] = make_float4(col[0], col[1], col[2], p.xc[2]);
-        touched[vg] = (uint32_t)((p.rect[2] - p.rect[0]) * (p.rect[3] - p.rect[1]));
+        touched[vg] = area;
         dkey[vg] = __float_as_uint(p.xc[2]);
         radius_out[vg] = p.radius;
         uint2 rc;
@@ -887,7 +906,8 @@ gs_status launch_project(const Plan* p, const gs_map* map, const gs_view* views_
         map->means, map->log_scales, map->quats, map->opacity_logits, map->sh, n, views_dev,
         p->vt, p->cfg.near_z, buf<float4>(p, ws, GS_BUF_PROJ), buf<uint16_t>(p, ws, GS_BUF_RECT),
         buf<uint32_t>(p, ws, GS_BUF_TOUCHED), buf<int32_t>(p, ws, GS_BUF_RADIUS),
-        buf<uint32_t>(p, ws, B_DKEY_A), buf<uint32_t>(p, ws, GS_BUF_DEPTH_ORDER), ctr);
+        buf<uint32_t>(p, ws, B_DKEY_A), buf<uint32_t>(p, ws, GS_BUF_DEPTH_ORDER), ctr,
+        buf<uint32_t>(p, ws, B_SPANS));
     return launch_status();
 }
 

@@ -277,10 +277,12 @@ __global__ void __launch_bounds__(kEmitEntries)
 k_emit(const uint32_t* __restrict__ order, const uint32_t* __restrict__ off,
        const uint2* __restrict__ rects, uint32_t count, int n, ViewTable vt, uint32_t cap,
        uint32_t* __restrict__ ikeys, uint32_t* __restrict__ ivals,
-       uint32_t* __restrict__ gid_of) {
+       uint32_t* __restrict__ gid_of, const uint32_t* __restrict__ spans) {
     __shared__ uint32_t s_off[kEmitEntries + 1];
     __shared__ uint32_t s_vg[kEmitEntries];
     __shared__ uint2 s_rect[kEmitEntries];
+    // tight rects: the entry's row spans (boxes of at most kSpanRows rows)
+    __shared__ uint32_t s_span[kEmitEntries][kSpanRows];
     __shared__ uint16_t s_view[kEmitEntries];
     const uint32_t e0 = blockIdx.x * (uint32_t)kEmitEntries;
     if (e0 >= count) return;
@@ -292,6 +294,12 @@ k_emit(const uint32_t* __restrict__ order, const uint32_t* __restrict__ off,
         s_vg[e] = vg;
         s_rect[e] = rects[vg];
         s_view[e] = (uint16_t)(vg / (uint32_t)n);
+        if (vt.tight_rect && s_off[e] != off[e0 + e + 1]) {
+            const uint2 rc = s_rect[e];
+            const int rows = (int)(rc.y >> 16) - (int)(rc.x >> 16);
+            if (rows <= kSpanRows)
+                for (int r = 0; r < rows; ++r) s_span[e][r] = spans[(size_t)vg * kSpanRows + r];
+        }
     }
     if (e == 0) s_off[ne] = off[e0 + ne];
     __syncthreads();
@@ -304,11 +312,27 @@ k_emit(const uint32_t* __restrict__ order, const uint32_t* __restrict__ off,
             if (s_off[mid] <= pos) lo = mid; else hi = mid;
         }
         const uint2 rc = s_rect[lo];
-        const uint32_t x0 = rc.x & 0xFFFF, y0 = rc.x >> 16, x1 = rc.y & 0xFFFF;
+        const uint32_t x0 = rc.x & 0xFFFF, y0 = rc.x >> 16, x1 = rc.y & 0xFFFF, y1 = rc.y >> 16;
         const uint32_t w = x1 - x0, k = pos - s_off[lo];
-        const uint32_t dy = k / w, dx = k - dy * w;
+        uint32_t tx, ty;
+        if (vt.tight_rect && y1 - y0 <= (uint32_t)kSpanRows) {
+            // the k-th tile of the row spans the projection stored and counted
+            uint32_t kk = k, r = 0;
+            for (; r + 1 < y1 - y0; ++r) {
+                const uint32_t sp = s_span[lo][r], wr = (sp >> 16) - (sp & 0xFFFF);
+                if (kk < wr) break;
+                kk -= wr;
+            }
+            ty = y0 + r;
+            // (a count that disagreed would land past the row; stay inside the rect)
+            tx = min((s_span[lo][r] & 0xFFFF) + kk, x1 - 1u);
+        } else {
+            const uint32_t dy = k / w;
+            ty = y0 + dy;
+            tx = x0 + (k - dy * w);
+        }
         const ViewGeom& geo = vt.v[s_view[lo]];
-        ikeys[pos] = (uint32_t)geo.tile_offset + (y0 + dy) * (uint32_t)geo.tiles_x + x0 + dx;
+        ikeys[pos] = (uint32_t)geo.tile_offset + ty * (uint32_t)geo.tiles_x + tx;
         if (gid_of) {
             // deterministic plans: the sort carries the emission position
             ivals[pos] = pos;
@@ -439,7 +463,8 @@ gs_status launch_bin_sort(const Plan* p, int32_t n, void* ws, cudaStream_t st) {
     k_scan_offsets<<<snb, kScanThreads, 0, st>>>(va, touched, bsums, VN, offs);
     k_emit<<<(VN + kEmitEntries - 1) / kEmitEntries, kEmitEntries, 0, st>>>(
         va, offs, buf<uint2>(p, ws, GS_BUF_RECT), VN, n, p->vt, icap, ika, iva,
-        p->cfg.deterministic ? buf<uint32_t>(p, ws, B_GID_OF) : nullptr);
+        p->cfg.deterministic ? buf<uint32_t>(p, ws, B_GID_OF) : nullptr,
+        buf<uint32_t>(p, ws, B_SPANS));
     gs_status s = launch_status();
     if (s != GS_OK) return s;
 

@@ -89,20 +89,25 @@ def test_binning_bit_exact(case):
     ranges, keys, vals, c = U.gpu_tile_lists(rast)
     assert c.status == 0 and c.n_instances == c.n_instances_raw
     tx, ty = oracle.tile_grid(view["width"], view["height"], 16, 16)
-    # 1. the integer part alone: the oracle's (tile, depth, index) order over
-    #    the GPU's own FP32 keys and rects must be reproduced exactly
-    start, lst = oracle.bin_tiles(g["depth32"], g["rect"], g["touched"], tx, ty)
-    assert len(lst) == len(vals)
+    # 1. the integer part alone: the GPU's own (tile, Gaussian) pairs, each
+    #    Gaussian with as many as it counted, inside its rect, and in the
+    #    (tile, FP32 depth key, index) order
+    np.testing.assert_array_equal(np.bincount(vals, minlength=gm.n), g["touched"])
+    r = g["rect"][vals]
+    kx, ky = keys % tx, keys // tx
+    assert np.all((kx >= r[:, 0]) & (kx < r[:, 2]) & (ky >= r[:, 1]) & (ky < r[:, 3]))
+    order = np.lexsort((vals, g["depth32"][vals], keys))
+    np.testing.assert_array_equal(order, np.arange(len(vals)))
+    start = np.concatenate([[0], np.cumsum(np.bincount(keys, minlength=tx * ty))])
     np.testing.assert_array_equal(ranges[:, 0], start[:-1])
     np.testing.assert_array_equal(ranges[:, 1], start[1:])
-    np.testing.assert_array_equal(vals, lst)
-    np.testing.assert_array_equal(keys, np.repeat(np.arange(tx * ty), np.diff(start)))
+    assert len(np.unique(keys.astype(np.int64) * gm.n + vals)) == len(vals)  # no pair twice
     # 2. end to end: lists from the oracle's own projection, where no
     #    Gaussian of the scene sits in a guard band
     o = oracle.project(p, view)
     if not np.any(o["guard"] & U.FWD_GUARDS):
         ostart, olst = oracle.bin_tiles(o["depth"].astype(np.float32), o["rect"],
-                                        o["tiles_touched"], tx, ty)
+                                        o["tiles_touched"], tx, ty, o, (16, 16))
         np.testing.assert_array_equal(vals, olst)
 
 

