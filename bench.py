@@ -58,7 +58,7 @@ PAIR_FLOPS_BWD = 64.0
 RENDER_BWD_TRAFFIC = {
     ("room1M_1200x680", "8x8", 32, 2, "square"): 60.67e6 + 0.83e6,
     ("room1M_1200x680", "8x8", 64, 2, "square"): 60.67e6 + 0.82e6,
-    ("room1M_1200x680", "8x8", 64, 2, "tight"): 55.92e6 + 0.01e6,
+    ("room1M_1200x680", "8x8", 64, 2, "tight"): 54.41e6 + 0.06e6,
 }
 
 
