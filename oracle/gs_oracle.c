@@ -168,6 +168,11 @@ static double tight_level(double opacity) { return 1.01 * (2.0 * log(255.0 * opa
 /* Row spans apply to boxes of at most this many tile rows; a taller box keeps
  * all its tiles (a bound on the per-Gaussian span storage). */
 #define OR_SPAN_ROWS 16
+/* ... and to boxes of at least two rows and two columns (a one-row or
+ * one-column box is the ellipse's own bounding box: every tile meets it). */
+static int spans_apply(const int rc[4]) {
+    return rc[3] - rc[1] >= 2 && rc[3] - rc[1] <= OR_SPAN_ROWS && rc[2] - rc[0] >= 2;
+}
 
 /* The tight cut (reading C19) applied to rc in place; returns the number of
  * tiles (the box of the widened ellipse, then its row spans). */
@@ -191,7 +196,7 @@ static int cut_rect(const double mean2d[2], const double cov[3], double opacity,
             if (khi < rc[a + 2]) rc[a + 2] = khi < 0.0 ? 0 : (int)khi;
         }
         if (rc[2] <= rc[0] || rc[3] <= rc[1]) return 0;
-        if (rc[3] - rc[1] > OR_SPAN_ROWS) return (rc[2] - rc[0]) * (rc[3] - rc[1]);
+        if (!spans_apply(rc)) return (rc[2] - rc[0]) * (rc[3] - rc[1]);
         int total = 0, x0, x1;
         for (int ty = rc[1]; ty < rc[3]; ty++)
             total += row_span(mean2d, cov, t, ty, tile_w, tile_h, rc[0], rc[2], &x0, &x1, guard);
@@ -664,7 +669,7 @@ int64_t oracle_bin_spans(int n, const float *depth_key, const int *rect, const i
     for (int i = 0; i < n; i++) {
         if (tiles_touched[i] <= 0) continue;
         const double t = tight_level(opacity[i]);
-        const int tall = rect[4 * i + 3] - rect[4 * i + 1] > OR_SPAN_ROWS;
+        const int tall = !spans_apply(rect + 4 * i);
         for (int ty = rect[4 * i + 1]; ty < rect[4 * i + 3]; ty++) {
             int x0 = rect[4 * i + 0], x1 = rect[4 * i + 2], g = 0;
             if (!tall)

@@ -193,6 +193,13 @@ __device__ __forceinline__ int df_floor_div(float hi, float lo, float inv_t) {
 // emission to list; a box of more than kSpanRows tile rows keeps all its
 // tiles.
 constexpr int kSpanRows = 16;
+
+// Whether a tight box is cut row by row: at least two rows and two columns
+// (a one-row or one-column box is the ellipse's own bounding box, every one
+// of its tiles meets it) and at most kSpanRows rows.
+__device__ __forceinline__ bool tight_spans_apply(int x0, int y0, int x1, int y1) {
+    return y1 - y0 >= 2 && y1 - y0 <= kSpanRows && x1 - x0 >= 2;
+}
 __device__ __forceinline__ float tight_level(float opacity) {
     return __fmaf_rn(1.01f, __fmul_rn(2.0f, logf(__fmul_rn(255.0f, opacity))), 0.01f);
 }

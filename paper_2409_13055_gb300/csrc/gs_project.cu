@@ -333,7 +333,7 @@ k_project(const float* __restrict__ means, const float* __restrict__ log_scales,
         uint32_t area = 0u;
         if (vis) {
             area = (uint32_t)((p.rect[2] - p.rect[0]) * (p.rect[3] - p.rect[1]));
-            if (vt.tight_rect && p.rect[3] - p.rect[1] <= kSpanRows) {
+            if (vt.tight_rect && tight_spans_apply(p.rect[0], p.rect[1], p.rect[2], p.rect[3])) {
                 // the row spans of the box, stored for the emission
                 const TightEllipse E =
                     tight_ellipse(p.mxh, p.mxl, p.myh, p.myl, p.ca, p.cb, p.cc, opacity);

@@ -297,7 +297,7 @@ k_emit(const uint32_t* __restrict__ order, const uint32_t* __restrict__ off,
         if (vt.tight_rect && s_off[e] != off[e0 + e + 1]) {
             const uint2 rc = s_rect[e];
             const int rows = (int)(rc.y >> 16) - (int)(rc.x >> 16);
-            if (rows <= kSpanRows)
+            if (tight_spans_apply(rc.x & 0xFFFF, rc.x >> 16, rc.y & 0xFFFF, rc.y >> 16))
                 for (int r = 0; r < rows; ++r) s_span[e][r] = spans[(size_t)vg * kSpanRows + r];
         }
     }
@@ -315,7 +315,7 @@ k_emit(const uint32_t* __restrict__ order, const uint32_t* __restrict__ off,
         const uint32_t x0 = rc.x & 0xFFFF, y0 = rc.x >> 16, x1 = rc.y & 0xFFFF, y1 = rc.y >> 16;
         const uint32_t w = x1 - x0, k = pos - s_off[lo];
         uint32_t tx, ty;
-        if (vt.tight_rect && y1 - y0 <= (uint32_t)kSpanRows) {
+        if (vt.tight_rect && tight_spans_apply(x0, y0, x1, y1)) {
             // the k-th tile of the row spans the projection stored and counted
             uint32_t kk = k, r = 0;
             for (; r + 1 < y1 - y0; ++r) {

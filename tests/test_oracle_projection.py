@@ -347,7 +347,8 @@ def test_tight_tiles_are_exactly_those_meeting_the_ellipse(tile):
                 qmin = _min_q_over_rect(a, b, c, tx * tw - mx, tx * tw + tw - 1 - mx,
                                         ty * th - my, ty * th + th - 1 - my)
                 t0 = ti["rect"][i]
-                if t0[3] - t0[1] > 16:  # a box of more than 16 tile rows keeps its tiles
+                rows, cols = t0[3] - t0[1], t0[2] - t0[0]
+                if rows > 16 or rows < 2 or cols < 2:  # such a box keeps its tiles
                     meets = (ti["tiles_touched"][i] > 0 and t0[0] <= tx < t0[2]
                              and t0[1] <= ty < t0[3])
                 else:
