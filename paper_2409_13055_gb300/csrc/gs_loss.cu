@@ -81,16 +81,30 @@ k_ssim_fwd(ViewTable vt, Win win, const float* __restrict__ img, const float* __
     __shared__ float red[32];
     __shared__ bool is_last;
     const BlockPos bp = block_pos(vt, blockIdx.x);
-    for (int i = threadIdx.x; i < kRows * kCols; i += blockDim.x) {
-        const int r = i / kCols, c = i - r * kCols;
-        const int y = bp.y0 - kHalo + r, x = bp.x0 - kHalo + c;
-        float a = 0.0f, b = 0.0f;
-        if (x >= 0 && x < bp.width && y >= 0 && y < bp.height) {
-            a = img[bp.plane + (int64_t)y * bp.width + x];
-            b = tgt[bp.plane + (int64_t)y * bp.width + x];
+    // the tile and its halo: every load of a thread issued before any store
+    constexpr int kLoads = (kRows * kCols + kLossThreads - 1) / kLossThreads;
+    {
+        float a[kLoads], b[kLoads];
+#pragma unroll
+        for (int it = 0; it < kLoads; ++it) {
+            const int i = threadIdx.x + it * kLossThreads;
+            const int r = i / kCols, c = i - r * kCols;
+            const int y = bp.y0 - kHalo + r, x = bp.x0 - kHalo + c;
+            a[it] = b[it] = 0.0f;
+            if (i < kRows * kCols && x >= 0 && x < bp.width && y >= 0 && y < bp.height) {
+                a[it] = img[bp.plane + (int64_t)y * bp.width + x];
+                b[it] = tgt[bp.plane + (int64_t)y * bp.width + x];
+            }
         }
-        sx[r][c] = a;
-        sy[r][c] = b;
+#pragma unroll
+        for (int it = 0; it < kLoads; ++it) {
+            const int i = threadIdx.x + it * kLossThreads;
+            if (i < kRows * kCols) {
+                const int r = i / kCols, c = i - r * kCols;
+                sx[r][c] = a[it];
+                sy[r][c] = b[it];
+            }
+        }
     }
     __syncthreads();
     // horizontal pass, register-blocked: a thread takes kSeg consecutive
@@ -194,19 +208,32 @@ k_ssim_bwd(ViewTable vt, Win win, const float* __restrict__ img, const float* __
     __shared__ float sm[3][kRows][kCols + 1];
     __shared__ float h[3][kRows][kTX + 1];
     const BlockPos bp = block_pos(vt, blockIdx.x);
-    for (int i = threadIdx.x; i < kRows * kCols; i += blockDim.x) {
-        const int r = i / kCols, c = i - r * kCols;
-        const int y = bp.y0 - kHalo + r, x = bp.x0 - kHalo + c;
-        float a = 0.f, b = 0.f, d = 0.f;
-        if (x >= 0 && x < bp.width && y >= 0 && y < bp.height) {
-            const int64_t idx = bp.plane + (int64_t)y * bp.width + x;
-            a = maps[idx];
-            b = maps[total_values + idx];
-            d = maps[2 * total_values + idx];
+    constexpr int kLoads = (kRows * kCols + kLossThreads - 1) / kLossThreads;
+    {
+        float a[kLoads], b[kLoads], d[kLoads];
+#pragma unroll
+        for (int it = 0; it < kLoads; ++it) {
+            const int i = threadIdx.x + it * kLossThreads;
+            const int r = i / kCols, c = i - r * kCols;
+            const int y = bp.y0 - kHalo + r, x = bp.x0 - kHalo + c;
+            a[it] = b[it] = d[it] = 0.0f;
+            if (i < kRows * kCols && x >= 0 && x < bp.width && y >= 0 && y < bp.height) {
+                const int64_t idx = bp.plane + (int64_t)y * bp.width + x;
+                a[it] = maps[idx];
+                b[it] = maps[total_values + idx];
+                d[it] = maps[2 * total_values + idx];
+            }
         }
-        sm[0][r][c] = a;
-        sm[1][r][c] = b;
-        sm[2][r][c] = d;
+#pragma unroll
+        for (int it = 0; it < kLoads; ++it) {
+            const int i = threadIdx.x + it * kLossThreads;
+            if (i < kRows * kCols) {
+                const int r = i / kCols, c = i - r * kCols;
+                sm[0][r][c] = a[it];
+                sm[1][r][c] = b[it];
+                sm[2][r][c] = d[it];
+            }
+        }
     }
     __syncthreads();
     for (int i = threadIdx.x; i < kRows * (kTX / kSeg); i += blockDim.x) {
