@@ -113,10 +113,12 @@ typedef struct {
  *   tight_rect: nonzero (recommended) cuts each Gaussian's 3-sigma square
  *     tile rect to the tiles that meet the axis-aligned box of the ellipse
  *     outside which alpha = o exp(power) < 1/255, with the level widened by
- *     1% + 0.01 against FP32 rounding; a Gaussian with o < 0.999/255 gets no
- *     tile.  Only (Gaussian, tile) pairs that every pixel would skip are
- *     dropped: images and gradients are unchanged, the instance lists (and
- *     so last_idx) shorter.
+ *     1% + 0.01 against FP32 rounding (a Gaussian with o < 0.999/255 gets no
+ *     tile), and, in boxes of 2 to 16 tile rows and at least 2 columns, each
+ *     row to the tiles whose pixel band meets that ellipse (GS_BUF_RECT keeps
+ *     the box; GS_BUF_TOUCHED counts the tiles).  Only (Gaussian, tile) pairs
+ *     that every pixel would skip are dropped: images and gradients are
+ *     unchanged, the instance lists (and so last_idx) shorter.
  * The tile shape changes which pixels a Gaussian can reach (its 3-sigma
  * rect is counted in whole tiles), hence the image; the batch sizes, pixels
  * per thread and tight_rect change only the speed. */
@@ -174,7 +176,8 @@ enum {
     GS_BUF_PROJ = 1,     /* [V*n] x 12 floats: mean hi (2), mean lo (2),
                             conic a,b,c, opacity, r, g, b, depth */
     GS_BUF_RECT = 2,     /* [V*n] x 4 uint16: tile rect x0, y0, x1, y1 (x1, y1 exclusive) */
-    GS_BUF_TOUCHED = 3,  /* [V*n] uint32: tiles touched (0 = culled) */
+    GS_BUF_TOUCHED = 3,  /* [V*n] uint32: tiles touched (0 = culled); with tight rects the
+                            tiles of the row spans, at most the rect area */
     GS_BUF_RADIUS = 4,   /* [V*n] int32: ceil(3 sqrt(lambda_max)) */
     GS_BUF_DEPTH_ORDER = 5, /* [V*n] uint32: view*n + index sorted by (depth, view, index) */
     GS_BUF_TILE_KEYS = 6,   /* [instance_capacity] uint32: sorted global tile ids */
