@@ -62,6 +62,32 @@ RENDER_BWD_TRAFFIC = {
 }
 
 
+def iteration_roofline(n, sh_degree, n_views, n_values, n_pixels, instances, pairs, tiles,
+                       passes, n_floats, ms, peaks):
+    """Per-iteration roofline: the sum over the stages of max(algorithmic
+    bytes / HBM peak, algorithmic FLOPs / FP32 peak), with the quantities the
+    iteration itself produced (instances, counted pairs), against the
+    measured iteration time."""
+    K = (sh_degree + 1) ** 2
+    pb = 4 * (11 + 3 * K)  # parameter bytes per Gaussian
+    bw = peaks["hbm_gbs"] * 1e9
+    fl = fp32_peak_tflops(peaks["sm_max_mhz"]) * 1e12
+    vn = n_views * n
+    stages = dict(
+        project=((n_views + 3) // 4 * n * pb + vn * 72) / bw,
+        bin_sort=(vn * (4 * 16 + 12) + instances * (8 + 16 * passes + 4) + tiles * 8) / bw,
+        render_fwd=max(pairs * PAIR_FLOPS_FWD / fl, (instances * 48 + n_pixels * 20) / bw),
+        loss_l1_ssim=n_values * 44 / bw,
+        render_bwd=max(pairs * PAIR_FLOPS_BWD / fl, (instances * 48 + n_pixels * 16) / bw),
+        project_bwd=(vn * (36 + 24 + 4) + 2 * n * pb) / bw,
+        adam=n_floats * 28 / bw,
+    )
+    t = sum(stages.values()) * 1e3
+    return dict(ms_roof=t, ms=ms, frac=t / ms,
+                stages_ms_roof={k: v * 1e3 for k, v in stages.items()},
+                basis="sum over stages of max(bytes / measured HBM copy, FLOPs / FP32 peak)")
+
+
 def load_peaks():
     path = os.path.join(ROOT, "MEASURED_PEAKS.json")
     try:
@@ -278,6 +304,13 @@ def run_batched(args, ws):
         torch.cuda.synchronize()
         ms = reduce_max(e0.elapsed_time(e1), ws) / K
         result[mode] = dict(iters_per_s=ws * 1e3 / ms, ms_per_iter=ms)
+        if mode == "batched":
+            inst = int(rast.counters().n_instances)
+            pairs = int(rast.last_idx.to(torch.int64).sum().item())
+            px = sum(v["width"] * v["height"] for v in views)
+            result[mode]["iteration_roofline"] = iteration_roofline(
+                gm.n, gm.degree, len(views), rast.total_values, px, inst, pairs,
+                rast.total_tiles, tile_passes(rast.total_tiles), gm.total, ms, load_peaks())
         del it, gm
         torch.cuda.empty_cache()
     result["speedup_batched_over_per_view"] = (result["batched"]["iters_per_s"] /
@@ -697,6 +730,10 @@ def run_gpu(args, ws, rank, local):
                            l2="working set ~1.2 GB > 129 MB L2, no flush",
                            instances=instances, pairs_bwd=pairs_bwd),
                stages_ms=stage_ms, roofline=roof,
+               iteration_roofline=iteration_roofline(
+                   n, gm.degree, 1, rast.total_values, view["width"] * view["height"], instances,
+                   pairs_bwd, rast.total_tiles, tile_passes(rast.total_tiles), gm.total, ms_step,
+                   peaks),
                e2e=dict(value=1e3 / e2e_ms * ws, unit="iters/s", h2d_bytes_per_step=int(h2d),
                         d2h_bytes_per_step=4),
                clocks=clocks, gpu_launches=launches_per_step * K)
