@@ -179,7 +179,9 @@ enum {
     GS_BUF_TOUCHED = 3,  /* [V*n] uint32: tiles touched (0 = culled); with tight rects the
                             tiles of the row spans, at most the rect area */
     GS_BUF_RADIUS = 4,   /* [V*n] int32: ceil(3 sqrt(lambda_max)) */
-    GS_BUF_DEPTH_ORDER = 5, /* [V*n] uint32: view*n + index sorted by (depth, view, index) */
+    GS_BUF_DEPTH_ORDER = 5, /* [V*n] uint32: view*n + index of the pairs with a tile,
+                               sorted by (depth, view, index), in the first entries
+                               (as many as such pairs); the rest unspecified */
     GS_BUF_TILE_KEYS = 6,   /* [instance_capacity] uint32: sorted global tile ids */
     GS_BUF_TILE_VALUES = 7, /* [instance_capacity] uint32: view*n + index per instance */
     GS_BUF_RANGES = 8,      /* [total_tiles] x 2 uint32: [begin, end) of each tile */
@@ -204,8 +206,9 @@ gs_status gs_project(const gs_plan *plan, const gs_map *map, const gs_view *view
                      void *stream);
 
 /* A2-A4: binning.  Deterministic (tile, depth, index) order: a stable LSD
- * radix sort whose depth digits run once per (view, Gaussian) before the
- * instances are emitted, followed by stable passes over the tile-id digits
+ * radix sort whose depth digits run once per (view, Gaussian) with a tile
+ * (the first pass drops the culled pairs) before the instances are emitted,
+ * followed by stable passes over the tile-id digits
  * of the instances; then per-tile [begin, end) ranges.  n = map->n of the
  * preceding gs_project.  The instance count stays on the device (no host
  * synchronisation); overflow sets GS_DEV_CAPACITY. */

@@ -115,6 +115,7 @@ extern "C" gs_status gs_plan_init(gs_plan* plan, const gs_config* cfg, int32_t n
     len[B_DKEY_A] = (size_t)VN * sizeof(uint32_t);
     len[B_DKEY_B] = (size_t)VN * sizeof(uint32_t);
     len[B_DVAL_B] = (size_t)VN * sizeof(uint32_t);
+    len[B_DKEY_C] = (size_t)VN * sizeof(uint32_t);
     len[B_SCAN_BLOCKS] = (size_t)(p->scan_blocks + 1) * sizeof(uint32_t) * 2;
     {
         int mb = p->depth_sort_blocks > p->inst_sort_blocks ? p->depth_sort_blocks

@@ -41,9 +41,11 @@ struct ViewTable {
 
 // Workspace buffers (ids >= GS_BUF_COUNT are private).
 enum PrivBuf {
-    B_DKEY_A = GS_BUF_COUNT,
+    B_DKEY_A = GS_BUF_COUNT,  // [V*n] FP32 depth keys of the projection (0xFFFFFFFF: culled);
+                              // the sort reads them and never overwrites them
     B_DKEY_B,
     B_DVAL_B,
+    B_DKEY_C,
     B_SCAN_BLOCKS,
     B_HIST,
     B_IKEY_B,
@@ -85,8 +87,8 @@ struct DevCounters {
     unsigned long long n_raw;      // before clamping
     float loss;
     uint32_t loss_blocks_done;     // last-block-done ticket of the loss reduction
-    uint32_t vn;                   // (view, Gaussian) pairs of the last gs_bin_sort
-    uint32_t pad;
+    uint32_t vn;                   // depth-order entries (visible pairs) of the last gs_bin_sort
+    uint32_t n_sorted;             // visible pairs kept by the first depth pass
 };
 
 inline const Plan* P(const gs_plan* p) { return reinterpret_cast<const Plan*>(p); }

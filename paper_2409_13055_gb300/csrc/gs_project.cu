@@ -301,7 +301,7 @@ k_project(const float* __restrict__ means, const float* __restrict__ log_scales,
           const float* __restrict__ sh, int n, const gs_view* __restrict__ views,
           ViewTable vt, float near_z, float4* __restrict__ rec, uint16_t* __restrict__ rect_out,
           uint32_t* __restrict__ touched, int32_t* __restrict__ radius_out,
-          uint32_t* __restrict__ dkey, uint32_t* __restrict__ dval, DevCounters* counters,
+          uint32_t* __restrict__ dkey, DevCounters* counters,
           uint32_t* __restrict__ spans) {
     __shared__ Cam cams[kViewsPerThread];
     const int v0 = blockIdx.y * kViewsPerThread;
@@ -348,7 +348,6 @@ k_project(const float* __restrict__ means, const float* __restrict__ log_scales,
                 vis = area > 0u;
             }
         }
-        dval[vg] = (uint32_t)vg;
         if (!vis) {
             touched[vg] = 0u;
             dkey[vg] = 0xFFFFFFFFu;
@@ -906,7 +905,7 @@ gs_status launch_project(const Plan* p, const gs_map* map, const gs_view* views_
         map->means, map->log_scales, map->quats, map->opacity_logits, map->sh, n, views_dev,
         p->vt, p->cfg.near_z, buf<float4>(p, ws, GS_BUF_PROJ), buf<uint16_t>(p, ws, GS_BUF_RECT),
         buf<uint32_t>(p, ws, GS_BUF_TOUCHED), buf<int32_t>(p, ws, GS_BUF_RADIUS),
-        buf<uint32_t>(p, ws, B_DKEY_A), buf<uint32_t>(p, ws, GS_BUF_DEPTH_ORDER), ctr,
+        buf<uint32_t>(p, ws, B_DKEY_A), ctr,
         buf<uint32_t>(p, ws, B_SPANS));
     return launch_status();
 }

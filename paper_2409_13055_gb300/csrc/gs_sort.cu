@@ -10,8 +10,11 @@
 // the tile passes already in (depth, view, index) order and stability keeps
 // it.  Per pass: a per-block digit histogram, a per-digit scan over blocks and
 // a stable block-local ranking with warp match + per-warp counters, scattered
-// to the digit's global offset.  No kernel waits on another block, so nothing
-// can spin; the instance count never leaves the device.
+// to the digit's global offset.  The first depth pass drops the (view,
+// Gaussian) pairs the projection culled (key 0xFFFFFFFF, no tile): the later
+// passes, the scan and the emission run over the visible pairs only, whose
+// count stays on the device like the instance count.  No kernel waits on
+// another block, so nothing can spin.
 #include "gs_internal.cuh"
 
 namespace gs {
@@ -19,6 +22,7 @@ namespace {
 
 constexpr int kWarps = kSortThreads / 32;
 constexpr int kGrid = 152 * 8;  // grid-stride kernels
+constexpr uint32_t kCulledKey = 0xFFFFFFFFu;  // depth key of a culled pair (never a depth)
 
 __device__ __forceinline__ uint32_t active_count(const uint32_t* count_dev, uint32_t count_host) {
     return count_dev ? *count_dev : count_host;
@@ -59,7 +63,7 @@ __device__ __forceinline__ uint32_t block_exclusive_scan(uint32_t x, uint32_t* w
 template <int ITEMS>
 __global__ void __launch_bounds__(kSortThreads)
 k_radix_hist(const uint32_t* __restrict__ keys, const uint32_t* count_dev, uint32_t count_host,
-             uint32_t cap, int shift, int nb, uint32_t* __restrict__ hist) {
+             uint32_t cap, int shift, int nb, int drop, uint32_t* __restrict__ hist) {
     constexpr int TILE = kSortThreads * ITEMS;
     __shared__ uint32_t h[kRadix];
     const uint32_t count = min(active_count(count_dev, count_host), cap);
@@ -68,8 +72,10 @@ k_radix_hist(const uint32_t* __restrict__ keys, const uint32_t* count_dev, uint3
     h[threadIdx.x] = 0u;
     __syncthreads();
     const uint32_t end = min(start + (uint32_t)TILE, count);
-    for (uint32_t i = start + threadIdx.x; i < end; i += kSortThreads)
-        atomicAdd(&h[(keys[i] >> shift) & (kRadix - 1)], 1u);
+    for (uint32_t i = start + threadIdx.x; i < end; i += kSortThreads) {
+        const uint32_t k = keys[i];
+        if (!(drop && k == kCulledKey)) atomicAdd(&h[(k >> shift) & (kRadix - 1)], 1u);
+    }
     __syncthreads();
     hist[(size_t)threadIdx.x * nb + blockIdx.x] = h[threadIdx.x];
 }
@@ -110,13 +116,16 @@ k_radix_scan(uint32_t* __restrict__ hist, const uint32_t* count_dev, uint32_t co
 // of its digit comes from per-warp match_any ranking; the block is first
 // reordered by digit in shared memory, so the global writes of each digit's
 // run are consecutive addresses (coalesced) instead of one scattered word per
-// key.
+// key.  With drop, culled keys are neither ranked nor written, and block 0
+// stores the number of keys the pass keeps in *kept_out.  Without vals_in
+// the value of key i is i.
 template <int ITEMS>
 __global__ void __launch_bounds__(kSortThreads)
 k_radix_scatter(const uint32_t* __restrict__ keys_in, const uint32_t* __restrict__ vals_in,
                 uint32_t* __restrict__ keys_out, uint32_t* __restrict__ vals_out,
                 const uint32_t* count_dev, uint32_t count_host, uint32_t cap, int shift, int nb,
-                const uint32_t* __restrict__ hist, const uint32_t* __restrict__ totals) {
+                const uint32_t* __restrict__ hist, const uint32_t* __restrict__ totals, int drop,
+                uint32_t* __restrict__ kept_out) {
     constexpr int TILE = kSortThreads * ITEMS;
     constexpr int kWarpItems = TILE / kWarps;  // consecutive keys per warp
     __shared__ uint32_t base[kRadix];          // global start of the digit's run of this block
@@ -127,12 +136,12 @@ k_radix_scatter(const uint32_t* __restrict__ keys_in, const uint32_t* __restrict
     const uint32_t count = min(active_count(count_dev, count_host), cap);
     const uint32_t start = blockIdx.x * (uint32_t)TILE;
     if (start >= count) return;
-    const int n_here = (int)min((uint32_t)TILE, count - start);
     const int tid = threadIdx.x, lane = tid & 31, w = tid >> 5;
     {
         uint32_t tot;
         uint32_t ex = block_exclusive_scan(totals[tid], wt, tot);
         base[tid] = ex + hist[(size_t)tid * nb + blockIdx.x];
+        if (kept_out && blockIdx.x == 0 && tid == 0) *kept_out = tot;  // keys of all digits
     }
 #pragma unroll
     for (int k = 0; k < kWarps; ++k) wcnt[k][tid] = 0u;
@@ -144,9 +153,10 @@ k_radix_scatter(const uint32_t* __restrict__ keys_in, const uint32_t* __restrict
 #pragma unroll
     for (int r = 0; r < ITEMS; ++r) {
         const uint32_t i = wstart + (uint32_t)r * 32u + lane;
-        const bool ok = i < count;
-        key[r] = ok ? keys_in[i] : 0u;
-        val[r] = ok ? vals_in[i] : 0u;
+        const bool in = i < count;
+        key[r] = in ? keys_in[i] : 0u;
+        val[r] = in ? (vals_in ? vals_in[i] : i) : 0u;
+        const bool ok = in && !(drop && key[r] == kCulledKey);
         const uint32_t d = ok ? ((key[r] >> shift) & (kRadix - 1)) : 0x10000u;
         const uint32_t peers = __match_any_sync(0xffffffffu, d);
         uint32_t rk = 0u;
@@ -164,15 +174,13 @@ k_radix_scatter(const uint32_t* __restrict__ keys_in, const uint32_t* __restrict
         wcnt[k][tid] = digit_count;
         digit_count += c;
     }
-    {
-        uint32_t tot;
-        local[tid] = block_exclusive_scan(digit_count, wt, tot);
-    }
+    uint32_t n_kept;  // keys of this block that are written (all of them without drop)
+    local[tid] = block_exclusive_scan(digit_count, wt, n_kept);
     __syncthreads();
 #pragma unroll
     for (int r = 0; r < ITEMS; ++r) {
         const uint32_t i = wstart + (uint32_t)r * 32u + lane;
-        if (i < count) {
+        if (i < count && !(drop && key[r] == kCulledKey)) {
             const uint32_t d = (key[r] >> shift) & (kRadix - 1);
             const uint32_t s = local[d] + wcnt[w][d] + rank[r];
             skey[s] = key[r];
@@ -183,7 +191,7 @@ k_radix_scatter(const uint32_t* __restrict__ keys_in, const uint32_t* __restrict
 #pragma unroll
     for (int r = 0; r < ITEMS; ++r) {
         const int s = r * kSortThreads + tid;
-        if (s < n_here) {
+        if ((uint32_t)s < n_kept) {
             const uint32_t k = skey[s];
             const uint32_t d = (k >> shift) & (kRadix - 1);
             const uint32_t pos = base[d] + ((uint32_t)s - local[d]);
@@ -193,11 +201,13 @@ k_radix_scatter(const uint32_t* __restrict__ keys_in, const uint32_t* __restrict
     }
 }
 
-// Sum of tiles touched over each scan block, in depth order.
+// Sum of tiles touched over each scan block, in depth order (the first
+// *count_dev entries of order: the visible pairs).
 __global__ void __launch_bounds__(kScanThreads)
 k_scan_reduce(const uint32_t* __restrict__ order, const uint32_t* __restrict__ touched,
-              uint32_t count, uint32_t* __restrict__ block_sums) {
+              const uint32_t* count_dev, uint32_t* __restrict__ block_sums) {
     __shared__ uint32_t wt[33];
+    const uint32_t count = *count_dev;
     const uint32_t start = blockIdx.x * (uint32_t)kScanTile;
     uint32_t s = 0;
     for (int k = 0; k < kScanItems; ++k) {
@@ -209,10 +219,11 @@ k_scan_reduce(const uint32_t* __restrict__ order, const uint32_t* __restrict__ t
     if (threadIdx.x == 0) block_sums[blockIdx.x] = tot;
 }
 
-// Exclusive scan of the block sums (one block), total instance count.
+// Exclusive scan of the block sums (one block), total instance count; vn =
+// the number of depth-order entries (visible pairs) for later readers.
 __global__ void __launch_bounds__(kSortThreads)
-k_scan_blocks(uint32_t* __restrict__ block_sums, int nb, uint32_t cap, uint32_t vn,
-              DevCounters* ctr) {
+k_scan_blocks(uint32_t* __restrict__ block_sums, int nb, uint32_t cap,
+              const uint32_t* vn, DevCounters* ctr) {
     __shared__ uint32_t wt[33];
     unsigned long long carry = 0;
     for (int base = 0; base < nb; base += kSortThreads * 4) {
@@ -234,18 +245,21 @@ k_scan_blocks(uint32_t* __restrict__ block_sums, int nb, uint32_t cap, uint32_t 
     }
     if (threadIdx.x == 0) {
         ctr->n_raw = carry;
-        ctr->vn = vn;
+        ctr->vn = *vn;
         ctr->n_instances = (uint32_t)min(carry, (unsigned long long)cap);
         if (carry > cap) atomicOr(&ctr->status, (uint32_t)GS_DEV_CAPACITY);
     }
 }
 
-// Global exclusive offsets of the instances of every (view, Gaussian) entry
-// in depth order: off[i] for i < count, off[count] = total.
+// Global exclusive offsets of the instances of every visible (view,
+// Gaussian) entry in depth order: off[i] for i < count, off[count] = total
+// (count = *count_dev).
 __global__ void __launch_bounds__(kScanThreads)
 k_scan_offsets(const uint32_t* __restrict__ order, const uint32_t* __restrict__ touched,
-               const uint32_t* __restrict__ block_off, uint32_t count, uint32_t* __restrict__ off) {
+               const uint32_t* __restrict__ block_off, const uint32_t* count_dev,
+               uint32_t* __restrict__ off) {
     __shared__ uint32_t wt[33];
+    const uint32_t count = *count_dev;
     const uint32_t start = blockIdx.x * (uint32_t)kScanTile;
     uint32_t t[kScanItems], s = 0;
     for (int k = 0; k < kScanItems; ++k) {
@@ -275,7 +289,8 @@ constexpr int kEmitEntries = 256;
 
 __global__ void __launch_bounds__(kEmitEntries)
 k_emit(const uint32_t* __restrict__ order, const uint32_t* __restrict__ off,
-       const uint2* __restrict__ rects, uint32_t count, int n, ViewTable vt, uint32_t cap,
+       const uint2* __restrict__ rects, const uint32_t* count_dev, int n, ViewTable vt,
+       uint32_t cap,
        uint32_t* __restrict__ ikeys, uint32_t* __restrict__ ivals,
        uint32_t* __restrict__ gid_of, const uint32_t* __restrict__ spans) {
     __shared__ uint32_t s_off[kEmitEntries + 1];
@@ -284,6 +299,7 @@ k_emit(const uint32_t* __restrict__ order, const uint32_t* __restrict__ off,
     // tight rects: the entry's row spans (boxes of at most kSpanRows rows)
     __shared__ uint32_t s_span[kEmitEntries][kSpanRows];
     __shared__ uint16_t s_view[kEmitEntries];
+    const uint32_t count = *count_dev;
     const uint32_t e0 = blockIdx.x * (uint32_t)kEmitEntries;
     if (e0 >= count) return;
     const uint32_t ne = min((uint32_t)kEmitEntries, count - e0);
@@ -404,26 +420,30 @@ k_tile_order(const uint32_t* __restrict__ ranges, int T, uint32_t* __restrict__ 
 template <int ITEMS>
 gs_status radix_pass_t(const uint32_t* kin, const uint32_t* vin, uint32_t* kout, uint32_t* vout,
                        const uint32_t* count_dev, uint32_t count_host, uint32_t cap, int shift,
-                       uint32_t* hist, uint32_t* totals, cudaStream_t st) {
+                       uint32_t* hist, uint32_t* totals, uint32_t* kept_out, cudaStream_t st) {
     const int nb = (int)((cap + kSortThreads * ITEMS - 1) / (kSortThreads * ITEMS));
+    const int drop = kept_out != nullptr;
     k_radix_hist<ITEMS><<<nb, kSortThreads, 0, st>>>(kin, count_dev, count_host, cap, shift, nb,
-                                                      hist);
+                                                      drop, hist);
     k_radix_scan<ITEMS><<<kRadix, kSortThreads, 0, st>>>(hist, count_dev, count_host, cap, nb,
                                                           totals);
     k_radix_scatter<ITEMS><<<nb, kSortThreads, 0, st>>>(kin, vin, kout, vout, count_dev,
-                                                         count_host, cap, shift, nb, hist, totals);
+                                                         count_host, cap, shift, nb, hist, totals,
+                                                         drop, kept_out);
     return launch_status();
 }
 
 // One stable pass on 8 bits at `shift` over up to `cap` keys (the real count
 // comes from count_dev when given), in blocks of 1024 keys: measured faster
 // than blocks of 2048 or 4096 for both the 1M depth keys and the 5M instances
-// (with the digit-reordered, coalesced writes too).
+// (with the digit-reordered, coalesced writes too).  With kept_out the pass
+// drops the culled keys and stores how many it kept there.
 gs_status radix_pass(const uint32_t* kin, const uint32_t* vin, uint32_t* kout, uint32_t* vout,
                      const uint32_t* count_dev, uint32_t count_host, uint32_t cap, int shift,
-                     uint32_t* hist, uint32_t* totals, cudaStream_t st) {
+                     uint32_t* hist, uint32_t* totals, cudaStream_t st,
+                     uint32_t* kept_out = nullptr) {
     return radix_pass_t<kSortItems>(kin, vin, kout, vout, count_dev, count_host, cap, shift,
-                                    hist, totals, st);
+                                    hist, totals, kept_out, st);
 }
 
 }  // namespace
@@ -437,32 +457,42 @@ gs_status launch_bin_sort(const Plan* p, int32_t n, void* ws, cudaStream_t st) {
                                                     : p->inst_sort_blocks);
     DevCounters* ctr = buf<DevCounters>(p, ws, GS_BUF_COUNTERS);
 
-    // 1. depth digits over the (view, Gaussian) pairs: 4 passes, A->B->A->B->A
-    uint32_t* ka = buf<uint32_t>(p, ws, B_DKEY_A);
-    uint32_t* va = buf<uint32_t>(p, ws, GS_BUF_DEPTH_ORDER);
+    // 1. depth digits over the (view, Gaussian) pairs: 4 passes, the
+    //    projection's keys (values = positions) -> B -> C -> B -> C; the first
+    //    keeps only the visible pairs, whose count (n_sorted) the later passes
+    //    read on the device.  The projection's keys are left intact, so a
+    //    second binning of the same projection sorts the same pairs.
+    const uint32_t* kp = buf<uint32_t>(p, ws, B_DKEY_A);
     uint32_t* kb = buf<uint32_t>(p, ws, B_DKEY_B);
     uint32_t* vb = buf<uint32_t>(p, ws, B_DVAL_B);
-    for (int pass = 0; pass < 4; ++pass) {
-        const bool even = (pass & 1) == 0;
-        gs_status s = radix_pass(even ? ka : kb, even ? va : vb, even ? kb : ka, even ? vb : va,
-                                 nullptr, VN, VN, pass * kRadixBits, hist, totals, st);
+    uint32_t* kc = buf<uint32_t>(p, ws, B_DKEY_C);
+    uint32_t* va = buf<uint32_t>(p, ws, GS_BUF_DEPTH_ORDER);
+    uint32_t* n_sorted = &ctr->n_sorted;
+    gs_status s0 = radix_pass(kp, nullptr, kb, vb, nullptr, VN, VN, 0, hist, totals, st,
+                              n_sorted);
+    if (s0 != GS_OK) return s0;
+    for (int pass = 1; pass < 4; ++pass) {
+        const bool odd = (pass & 1) != 0;
+        gs_status s = radix_pass(odd ? kb : kc, odd ? vb : va, odd ? kc : kb, odd ? va : vb,
+                                 n_sorted, VN, VN, pass * kRadixBits, hist, totals, st);
         if (s != GS_OK) return s;
     }
 
-    // 2. scan of tiles touched in depth order, then emission
+    // 2. scan of tiles touched in depth order, then emission (grids over all
+    //    pairs; blocks past the visible count do nothing)
     const int snb = (int)((VN + kScanTile - 1) / kScanTile);
     uint32_t* bsums = buf<uint32_t>(p, ws, B_SCAN_BLOCKS);
     const uint32_t* touched = buf<uint32_t>(p, ws, GS_BUF_TOUCHED);
-    k_scan_reduce<<<snb, kScanThreads, 0, st>>>(va, touched, VN, bsums);
-    k_scan_blocks<<<1, kSortThreads, 0, st>>>(bsums, snb, icap, VN, ctr);
+    k_scan_reduce<<<snb, kScanThreads, 0, st>>>(va, touched, n_sorted, bsums);
+    k_scan_blocks<<<1, kSortThreads, 0, st>>>(bsums, snb, icap, n_sorted, ctr);
     uint32_t* ika = buf<uint32_t>(p, ws, GS_BUF_TILE_KEYS);
     uint32_t* iva = buf<uint32_t>(p, ws, GS_BUF_TILE_VALUES);
     uint32_t* ikb = buf<uint32_t>(p, ws, B_IKEY_B);
     uint32_t* ivb = buf<uint32_t>(p, ws, B_IVAL_B);
     uint32_t* offs = buf<uint32_t>(p, ws, B_OFFSETS);
-    k_scan_offsets<<<snb, kScanThreads, 0, st>>>(va, touched, bsums, VN, offs);
+    k_scan_offsets<<<snb, kScanThreads, 0, st>>>(va, touched, bsums, n_sorted, offs);
     k_emit<<<(VN + kEmitEntries - 1) / kEmitEntries, kEmitEntries, 0, st>>>(
-        va, offs, buf<uint2>(p, ws, GS_BUF_RECT), VN, n, p->vt, icap, ika, iva,
+        va, offs, buf<uint2>(p, ws, GS_BUF_RECT), n_sorted, n, p->vt, icap, ika, iva,
         p->cfg.deterministic ? buf<uint32_t>(p, ws, B_GID_OF) : nullptr,
         buf<uint32_t>(p, ws, B_SPANS));
     gs_status s = launch_status();

@@ -111,6 +111,26 @@ def test_binning_bit_exact(case):
         np.testing.assert_array_equal(vals, olst)
 
 
+def test_depth_order_holds_the_visible_pairs_and_binning_repeats():
+    """The first depth pass drops the culled pairs: the depth order lists
+    exactly the Gaussians with a tile, by (FP32 depth key, index), and a
+    second binning of the same projection yields the same tile lists."""
+    p, view = CASES["room20k_sh3"]()
+    gm, rast = run_forward(p, view)
+    g = U.gpu_projection(rast, gm.n)
+    vis = np.nonzero(g["touched"] > 0)[0]
+    assert 0 < len(vis) < gm.n
+    order = rast.buffer(B.GS_BUF_DEPTH_ORDER, torch.int32)[: len(vis)].cpu().numpy()
+    np.testing.assert_array_equal(order, vis[np.lexsort((vis, g["depth32"][vis]))])
+    first = U.gpu_tile_lists(rast)
+    rast.bin_sort(gm.n)
+    torch.cuda.synchronize()
+    second = U.gpu_tile_lists(rast)
+    assert second[3].status == 0
+    for a, b in zip(first[:3], second[:3]):
+        np.testing.assert_array_equal(a, b)
+
+
 @pytest.mark.parametrize("case", list(CASES))
 def test_tight_rects_same_render_fewer_instances(case):
     """Square against tight tile rects on the GPU: the tight lists are
@@ -474,10 +494,15 @@ def test_recompute_is_bit_identical():
     rast.project(gm.gs_map())
     rast.bin_sort(gm.n)
     torch.cuda.synchronize()
+    # the depth order is defined on its first entries, one per visible pair
+    n_vis = int((rast.buffer(B.GS_BUF_TOUCHED, torch.int32) != 0).sum().item())
+    assert 0 < n_vis < gm.n
     for b, s in zip(bufs, snap):
         cur = rast.buffer(b)
         if b in (B.GS_BUF_TILE_KEYS, B.GS_BUF_TILE_VALUES):
             assert torch.equal(cur[: 4 * I], s[: 4 * I])
+        elif b == B.GS_BUF_DEPTH_ORDER:
+            assert torch.equal(cur[: 4 * n_vis], s[: 4 * n_vis])
         else:
             assert torch.equal(cur, s), b
 
