@@ -7,6 +7,8 @@
 #include <cuda_runtime.h>
 #include <stdint.h>
 
+#include <utility>
+
 #include "../../include/gs.h"
 
 namespace gs {
@@ -107,6 +109,35 @@ inline cudaStream_t S(void* s) { return reinterpret_cast<cudaStream_t>(s); }
 inline gs_status launch_status() {
     cudaError_t e = cudaGetLastError();
     return e == cudaSuccess ? GS_OK : GS_ERR_CUDA;
+}
+
+// Programmatic dependent launch: the kernel may be scheduled while the kernel
+// before it on the stream is still draining, so that chains of short kernels
+// do not pay a full launch gap at every boundary.  Every kernel launched this
+// way calls grid_dep_begin() before its first access to memory (the wait
+// returns once the preceding grid has completed and its writes are visible),
+// which also keeps the order transitive along the chain.
+template <typename... KArgs, typename... Args>
+inline void launch_pdl(void (*kernel)(KArgs...), dim3 grid, dim3 block, size_t smem,
+                       cudaStream_t st, Args&&... args) {
+    cudaLaunchConfig_t cfg = {};
+    cfg.gridDim = grid;
+    cfg.blockDim = block;
+    cfg.dynamicSmemBytes = smem;
+    cfg.stream = st;
+    cudaLaunchAttribute attr[1];
+    attr[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+    attr[0].val.programmaticStreamSerializationAllowed = 1;
+    cfg.attrs = attr;
+    cfg.numAttrs = 1;
+    (void)cudaLaunchKernelEx(&cfg, kernel, std::forward<Args>(args)...);  // checked by launch_status
+}
+
+// Start of a kernel launched by launch_pdl: wait for the preceding grid.  The
+// next kernel of the chain is released when this grid's CTAs exit.  A plain
+// launch makes the instruction a no-op.
+__device__ __forceinline__ void grid_dep_begin() {
+    asm volatile("griddepcontrol.wait;" ::: "memory");
 }
 
 // ---------------------------------------------------------------------------

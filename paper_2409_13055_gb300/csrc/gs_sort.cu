@@ -64,6 +64,7 @@ template <int ITEMS>
 __global__ void __launch_bounds__(kSortThreads)
 k_radix_hist(const uint32_t* __restrict__ keys, const uint32_t* count_dev, uint32_t count_host,
              uint32_t cap, int shift, int nb, int drop, uint32_t* __restrict__ hist) {
+    grid_dep_begin();
     constexpr int TILE = kSortThreads * ITEMS;
     __shared__ uint32_t h[kRadix];
     const uint32_t count = min(active_count(count_dev, count_host), cap);
@@ -86,6 +87,7 @@ template <int ITEMS>
 __global__ void __launch_bounds__(kSortThreads)
 k_radix_scan(uint32_t* __restrict__ hist, const uint32_t* count_dev, uint32_t count_host,
              uint32_t cap, int nb, uint32_t* __restrict__ totals) {
+    grid_dep_begin();
     constexpr int TILE = kSortThreads * ITEMS;
     __shared__ uint32_t wt[33];
     const uint32_t count = min(active_count(count_dev, count_host), cap);
@@ -126,6 +128,7 @@ k_radix_scatter(const uint32_t* __restrict__ keys_in, const uint32_t* __restrict
                 const uint32_t* count_dev, uint32_t count_host, uint32_t cap, int shift, int nb,
                 const uint32_t* __restrict__ hist, const uint32_t* __restrict__ totals, int drop,
                 uint32_t* __restrict__ kept_out) {
+    grid_dep_begin();
     constexpr int TILE = kSortThreads * ITEMS;
     constexpr int kWarpItems = TILE / kWarps;  // consecutive keys per warp
     __shared__ uint32_t base[kRadix];          // global start of the digit's run of this block
@@ -206,6 +209,7 @@ k_radix_scatter(const uint32_t* __restrict__ keys_in, const uint32_t* __restrict
 __global__ void __launch_bounds__(kScanThreads)
 k_scan_reduce(const uint32_t* __restrict__ order, const uint32_t* __restrict__ touched,
               const uint32_t* count_dev, uint32_t* __restrict__ block_sums) {
+    grid_dep_begin();
     __shared__ uint32_t wt[33];
     const uint32_t count = *count_dev;
     const uint32_t start = blockIdx.x * (uint32_t)kScanTile;
@@ -224,6 +228,7 @@ k_scan_reduce(const uint32_t* __restrict__ order, const uint32_t* __restrict__ t
 __global__ void __launch_bounds__(kSortThreads)
 k_scan_blocks(uint32_t* __restrict__ block_sums, int nb, uint32_t cap,
               const uint32_t* vn, DevCounters* ctr) {
+    grid_dep_begin();
     __shared__ uint32_t wt[33];
     unsigned long long carry = 0;
     for (int base = 0; base < nb; base += kSortThreads * 4) {
@@ -258,6 +263,7 @@ __global__ void __launch_bounds__(kScanThreads)
 k_scan_offsets(const uint32_t* __restrict__ order, const uint32_t* __restrict__ touched,
                const uint32_t* __restrict__ block_off, const uint32_t* count_dev,
                uint32_t* __restrict__ off) {
+    grid_dep_begin();
     __shared__ uint32_t wt[33];
     const uint32_t count = *count_dev;
     const uint32_t start = blockIdx.x * (uint32_t)kScanTile;
@@ -293,6 +299,7 @@ k_emit(const uint32_t* __restrict__ order, const uint32_t* __restrict__ off,
        uint32_t cap,
        uint32_t* __restrict__ ikeys, uint32_t* __restrict__ ivals,
        uint32_t* __restrict__ gid_of, const uint32_t* __restrict__ spans) {
+    grid_dep_begin();
     __shared__ uint32_t s_off[kEmitEntries + 1];
     __shared__ uint32_t s_vg[kEmitEntries];
     __shared__ uint2 s_rect[kEmitEntries];
@@ -361,6 +368,7 @@ k_emit(const uint32_t* __restrict__ order, const uint32_t* __restrict__ off,
 
 __global__ void k_ranges(const uint32_t* __restrict__ keys, const uint32_t* count_dev,
                          uint32_t* __restrict__ ranges) {
+    grid_dep_begin();
     const uint32_t count = *count_dev;
     for (uint32_t i = blockIdx.x * blockDim.x + threadIdx.x; i < count;
          i += gridDim.x * blockDim.x) {
@@ -385,6 +393,7 @@ __device__ __forceinline__ int work_bucket(const uint32_t* ranges, int t) {
 
 __global__ void __launch_bounds__(kOrderThreads)
 k_tile_order(const uint32_t* __restrict__ ranges, int T, uint32_t* __restrict__ order) {
+    grid_dep_begin();
     __shared__ uint32_t cnt[kOrderBuckets], base[kOrderBuckets];
     if (threadIdx.x < kOrderBuckets) cnt[threadIdx.x] = 0u;
     __syncthreads();
@@ -423,13 +432,12 @@ gs_status radix_pass_t(const uint32_t* kin, const uint32_t* vin, uint32_t* kout,
                        uint32_t* hist, uint32_t* totals, uint32_t* kept_out, cudaStream_t st) {
     const int nb = (int)((cap + kSortThreads * ITEMS - 1) / (kSortThreads * ITEMS));
     const int drop = kept_out != nullptr;
-    k_radix_hist<ITEMS><<<nb, kSortThreads, 0, st>>>(kin, count_dev, count_host, cap, shift, nb,
-                                                      drop, hist);
-    k_radix_scan<ITEMS><<<kRadix, kSortThreads, 0, st>>>(hist, count_dev, count_host, cap, nb,
-                                                          totals);
-    k_radix_scatter<ITEMS><<<nb, kSortThreads, 0, st>>>(kin, vin, kout, vout, count_dev,
-                                                         count_host, cap, shift, nb, hist, totals,
-                                                         drop, kept_out);
+    launch_pdl(k_radix_hist<ITEMS>, nb, kSortThreads, 0, st, kin, count_dev, count_host, cap,
+               shift, nb, drop, hist);
+    launch_pdl(k_radix_scan<ITEMS>, kRadix, kSortThreads, 0, st, hist, count_dev, count_host,
+               cap, nb, totals);
+    launch_pdl(k_radix_scatter<ITEMS>, nb, kSortThreads, 0, st, kin, vin, kout, vout, count_dev,
+               count_host, cap, shift, nb, hist, totals, drop, kept_out);
     return launch_status();
 }
 
@@ -456,6 +464,12 @@ gs_status launch_bin_sort(const Plan* p, int32_t n, void* ws, cudaStream_t st) {
                                                     ? p->depth_sort_blocks
                                                     : p->inst_sort_blocks);
     DevCounters* ctr = buf<DevCounters>(p, ws, GS_BUF_COUNTERS);
+    // the per-tile ranges are cleared first, so that every kernel of the
+    // binning follows another kernel (programmatic launches, see launch_pdl)
+    uint32_t* ranges = buf<uint32_t>(p, ws, GS_BUF_RANGES);
+    if (cudaMemsetAsync(ranges, 0, (size_t)p->total_tiles * 2 * sizeof(uint32_t), st) !=
+        cudaSuccess)
+        return GS_ERR_CUDA;
 
     // 1. depth digits over the (view, Gaussian) pairs: 4 passes, the
     //    projection's keys (values = positions) -> B -> C -> B -> C; the first
@@ -483,18 +497,18 @@ gs_status launch_bin_sort(const Plan* p, int32_t n, void* ws, cudaStream_t st) {
     const int snb = (int)((VN + kScanTile - 1) / kScanTile);
     uint32_t* bsums = buf<uint32_t>(p, ws, B_SCAN_BLOCKS);
     const uint32_t* touched = buf<uint32_t>(p, ws, GS_BUF_TOUCHED);
-    k_scan_reduce<<<snb, kScanThreads, 0, st>>>(va, touched, n_sorted, bsums);
-    k_scan_blocks<<<1, kSortThreads, 0, st>>>(bsums, snb, icap, n_sorted, ctr);
+    launch_pdl(k_scan_reduce, snb, kScanThreads, 0, st, va, touched, n_sorted, bsums);
+    launch_pdl(k_scan_blocks, 1, kSortThreads, 0, st, bsums, snb, icap, n_sorted, ctr);
     uint32_t* ika = buf<uint32_t>(p, ws, GS_BUF_TILE_KEYS);
     uint32_t* iva = buf<uint32_t>(p, ws, GS_BUF_TILE_VALUES);
     uint32_t* ikb = buf<uint32_t>(p, ws, B_IKEY_B);
     uint32_t* ivb = buf<uint32_t>(p, ws, B_IVAL_B);
     uint32_t* offs = buf<uint32_t>(p, ws, B_OFFSETS);
-    k_scan_offsets<<<snb, kScanThreads, 0, st>>>(va, touched, bsums, n_sorted, offs);
-    k_emit<<<(VN + kEmitEntries - 1) / kEmitEntries, kEmitEntries, 0, st>>>(
-        va, offs, buf<uint2>(p, ws, GS_BUF_RECT), n_sorted, n, p->vt, icap, ika, iva,
-        p->cfg.deterministic ? buf<uint32_t>(p, ws, B_GID_OF) : nullptr,
-        buf<uint32_t>(p, ws, B_SPANS));
+    launch_pdl(k_scan_offsets, snb, kScanThreads, 0, st, va, touched, bsums, n_sorted, offs);
+    launch_pdl(k_emit, (VN + kEmitEntries - 1) / kEmitEntries, kEmitEntries, 0, st, va, offs,
+               buf<uint2>(p, ws, GS_BUF_RECT), n_sorted, n, p->vt, icap, ika, iva,
+               p->cfg.deterministic ? buf<uint32_t>(p, ws, B_GID_OF) : nullptr,
+               buf<uint32_t>(p, ws, B_SPANS));
     gs_status s = launch_status();
     if (s != GS_OK) return s;
 
@@ -508,14 +522,10 @@ gs_status launch_bin_sort(const Plan* p, int32_t n, void* ws, cudaStream_t st) {
     }
     const uint32_t* sorted_keys = (p->tile_passes & 1) ? ikb : ika;
 
-    // 4. per-tile ranges
-    uint32_t* ranges = buf<uint32_t>(p, ws, GS_BUF_RANGES);
-    if (cudaMemsetAsync(ranges, 0, (size_t)p->total_tiles * 2 * sizeof(uint32_t), st) !=
-        cudaSuccess)
-        return GS_ERR_CUDA;
-    k_ranges<<<kGrid, 256, 0, st>>>(sorted_keys, cnt, ranges);
-    k_tile_order<<<1, kOrderThreads, 0, st>>>(ranges, p->total_tiles,
-                                              buf<uint32_t>(p, ws, B_TILE_ORDER));
+    // 4. per-tile ranges (cleared above)
+    launch_pdl(k_ranges, kGrid, 256, 0, st, sorted_keys, cnt, ranges);
+    launch_pdl(k_tile_order, 1, kOrderThreads, 0, st, ranges, p->total_tiles,
+               buf<uint32_t>(p, ws, B_TILE_ORDER));
     return launch_status();
 }
 
