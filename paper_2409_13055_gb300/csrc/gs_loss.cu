@@ -291,6 +291,8 @@ k_ssim_bwd(ViewTable vt, Win win, const float* __restrict__ img, const float* __
 
 }  // namespace
 
+// The 11-tap window: Gaussian of sigma 1.5 sampled at -5..5, normalised to
+// unit sum (in double, then rounded once).
 static Win loss_window() {
     Win win;
     double g[kWin], s = 0.0;
@@ -305,14 +307,7 @@ static Win loss_window() {
 
 gs_status launch_loss(const Plan* p, const float* images, const float* targets, float lambda,
                       float view_weight, float* loss_dev, float* dL, void* ws, cudaStream_t st) {
-    Win win;
-    double g[kWin], s = 0.0;
-    for (int k = 0; k < kWin; ++k) {
-        const double d = k - kHalo;
-        g[k] = exp(-d * d / (2.0 * 1.5 * 1.5));
-        s += g[k];
-    }
-    for (int k = 0; k < kWin; ++k) win.w[k] = (float)(g[k] / s);
+    const Win win = loss_window();
     float* maps = buf<float>(p, ws, B_LOSS_MAPS);
     float* partials = buf<float>(p, ws, B_LOSS_BLOCKS);
     DevCounters* ctr = buf<DevCounters>(p, ws, GS_BUF_COUNTERS);
