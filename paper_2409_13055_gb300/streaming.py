@@ -121,6 +121,8 @@ class StreamingMapper:
             self.iterations += 1
 
     def add_keyframe(self, view, target, new_gaussians):
+        """One keyframe of the mapping thread: insert it (window, new
+        Gaussians, replan if needed), then run this mapper's iterations."""
         self.insert_keyframe(view, target, new_gaussians)
         self.iterate(self.iters)
 
