@@ -529,7 +529,8 @@ def test_autograd_function_and_recompute_mode():
         assert U.rel_l2(gk.cpu().numpy(), og[name]) < 5e-4, name
 
 
-def test_grouped_adjoint_and_adam_are_bit_identical():
+@pytest.mark.parametrize("sh_degree", [3, 1])
+def test_grouped_adjoint_and_adam_are_bit_identical(sh_degree):
     """Without keep_grads, MappingStep neither writes nor reads the gradient
     of groups of 32 Gaussians that touch no tile: the parameters and moments
     after three iterations equal the dense path's bit for bit (deterministic
@@ -537,6 +538,9 @@ def test_grouped_adjoint_and_adam_are_bit_identical():
     present (the map in Z-order, so a view's invisible Gaussians cluster)."""
     p, view = CASES["room20k_sh3"]()
     p = scenes.z_ordered(p)
+    if sh_degree != 3:
+        K = (sh_degree + 1) ** 2
+        p = dict(p, sh=np.ascontiguousarray(p["sh"][:K]), sh_degree=sh_degree)  # [K, n, 3]
     target = scenes.random_target(view, 77)
     out = []
     for keep in (True, False):
