@@ -232,6 +232,34 @@ def test_render_grayscale_and_mixed_batch(tile, ppt):
         assert np.abs(img - o["image"])[:, ok].max() <= IMG_TOL
 
 
+def test_maximum_view_count_batch():
+    """GS_MAX_VIEWS views of two ragged sizes and both channel counts in one
+    plan: sampled views equal the oracle's render, and the batch loss is the
+    mean of the oracle's per-view losses of the rendered images."""
+    p = scenes.room_scene(5_000, seed=51)
+    views = []
+    for i in range(B.GS_MAX_VIEWS):
+        w, h = (40, 30) if i % 2 == 0 else (26, 18)
+        views.append(posed(scenes.camera(w, h, 30.0, 30.0, channels=1 if i % 3 == 0 else 3),
+                           100 + i, 0.1, 5.0))
+    gm = mapping.GaussianMap(p)
+    rast = mapping.Rasterizer(views, gm.n, instance_capacity=1 << 20, bg=(0.1, 0.2, 0.3))
+    rast.forward(gm.gs_map())
+    targets = [scenes.random_target(v, 200 + i) for i, v in enumerate(views)]
+    rast.loss_l1_ssim(rast.pack(targets), 0.2)
+    torch.cuda.synchronize()
+    assert rast.counters().status == 0
+    imgs = [rast.view_slice(rast.images, v).cpu().numpy() for v in range(len(views))]
+    for v in (0, 1, 3, 32, 62, 63):
+        proj, st, lst, o = oracle.forward_view(p, views[v], 16, 16, bg=(0.1, 0.2, 0.3))
+        ok = ~U.guard_pixel_mask(views[v], proj, o, (16, 16))
+        assert ok.mean() > 0.5
+        assert np.abs(imgs[v] - o["image"])[:, ok].max() <= IMG_TOL, v
+    L = np.mean([oracle.loss_l1_ssim(im.astype(np.float64), t.astype(np.float64), 0.2,
+                                     want_grad=False)[0] for im, t in zip(imgs, targets)])
+    assert abs(rast.loss.item() - L) <= 1e-5 * abs(L)
+
+
 def test_order_invariance_bit_identical():
     """Permuting the input Gaussians leaves the image bit-identical.  Ties of
     the FP32 depth key are broken by index, so the permutation keeps tied
