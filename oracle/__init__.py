@@ -159,18 +159,24 @@ def bin_tiles(depth_key, rect, tiles_touched, tiles_x, tiles_y, spans_of=None, t
 
 
 def render(proj, tile_start, tile_list, view, tile_w=16, tile_h=16, bg=(0.0, 0.0, 0.0)):
-    """Front-to-back compositing of one view from tile lists (Sec. II, Sec. III-B)."""
+    """Front-to-back compositing of one view from tile lists (Sec. II, Sec. III-B).
+    guard_px: per pixel, the guard bits (GPX_*) of the decisions taken there
+    whose FP64 margin FP32 may not resolve; guard_g: per Gaussian, the same
+    bits of its own decisions at any pixel (its alpha next to 1/255 or to
+    the 0.99 clamp, its power next to 0, T(1 - alpha) next to 1e-4 where it
+    is the Gaussian that would end the pixel)."""
     W, H, C = int(view["width"]), int(view["height"]), int(view.get("channels", 3))
     n = proj["mean2d"].shape[0]
     out = dict(image=np.zeros((C, H, W)), final_T=np.zeros((H, W)),
                last_idx=np.zeros((H, W), np.int32), n_eval=np.zeros((H, W), np.int32),
-               n_included=np.zeros((H, W), np.int32), guard_px=np.zeros((H, W), np.int32))
+               n_included=np.zeros((H, W), np.int32), guard_px=np.zeros((H, W), np.int32),
+               guard_g=np.zeros(n, np.int32))
     _L().oracle_render(
         _i(n), _p(_d(proj["mean2d"])), _p(_d(proj["conic"])), _p(_d(proj["opacity"])),
         _p(_d(proj["rgb"])), _p(np.ascontiguousarray(tile_start, np.int64)),
         _p(np.ascontiguousarray(tile_list, np.int32)), _i(W), _i(H), _i(tile_w), _i(tile_h),
         _i(C), _p(_d(bg)), _p(out["image"]), _p(out["final_T"]), _p(out["last_idx"]),
-        _p(out["n_eval"]), _p(out["n_included"]), _p(out["guard_px"]))
+        _p(out["n_eval"]), _p(out["n_included"]), _p(out["guard_px"]), _p(out["guard_g"]))
     return out
 
 

@@ -97,7 +97,10 @@ static int near_int(double v, double margin) {
  * the ellipse can reach 1/255 in a dropped tile; with o < 0.999/255 no pixel
  * reaches it at all and the rect is empty.  Pixel x of tile k satisfies
  * k t <= x <= k t + t - 1, so tiles [ceil((mu - h - t + 1)/t), floor((mu + h)/t)]
- * meet [mu - h, mu + h].
+ * meet [mu - h, mu + h].  Within that box, every tile row keeps only the
+ * tiles whose pixel rectangle meets the widened ellipse (row_span below):
+ * the kept tiles are exactly the tiles of the square rect that meet the
+ * ellipse, a purely geometric set, whatever the box's shape.
  */
 #define OR_TIGHT_MIN_OPACITY (0.999 / 255.0)
 #define OR_G_TIGHT 1e-5 /* tight rect edges in tile units, relative to 1 + h / t */
@@ -165,15 +168,6 @@ static int row_span(const double mean2d[2], const double cov[3], double t, int t
 
 static double tight_level(double opacity) { return 1.01 * (2.0 * log(255.0 * opacity)) + 0.01; }
 
-/* Row spans apply to boxes of at most this many tile rows; a taller box keeps
- * all its tiles (a bound on the per-Gaussian span storage). */
-#define OR_SPAN_ROWS 16
-/* ... and to boxes of at least two rows and two columns (a one-row or
- * one-column box is the ellipse's own bounding box: every tile meets it). */
-static int spans_apply(const int rc[4]) {
-    return rc[3] - rc[1] >= 2 && rc[3] - rc[1] <= OR_SPAN_ROWS && rc[2] - rc[0] >= 2;
-}
-
 /* The tight cut (reading C19) applied to rc in place; returns the number of
  * tiles (the box of the widened ellipse, then its row spans). */
 static int cut_rect(const double mean2d[2], const double cov[3], double opacity, int tile_w,
@@ -196,7 +190,6 @@ static int cut_rect(const double mean2d[2], const double cov[3], double opacity,
             if (khi < rc[a + 2]) rc[a + 2] = khi < 0.0 ? 0 : (int)khi;
         }
         if (rc[2] <= rc[0] || rc[3] <= rc[1]) return 0;
-        if (!spans_apply(rc)) return (rc[2] - rc[0]) * (rc[3] - rc[1]);
         int total = 0, x0, x1;
         for (int ty = rc[1]; ty < rc[3]; ty++)
             total += row_span(mean2d, cov, t, ty, tile_w, tile_h, rc[0], rc[2], &x0, &x1, guard);
@@ -669,12 +662,10 @@ int64_t oracle_bin_spans(int n, const float *depth_key, const int *rect, const i
     for (int i = 0; i < n; i++) {
         if (tiles_touched[i] <= 0) continue;
         const double t = tight_level(opacity[i]);
-        const int tall = !spans_apply(rect + 4 * i);
         for (int ty = rect[4 * i + 1]; ty < rect[4 * i + 3]; ty++) {
             int x0 = rect[4 * i + 0], x1 = rect[4 * i + 2], g = 0;
-            if (!tall)
-                row_span(mean2d + 2 * i, cov2d + 3 * i, t, ty, tile_w, tile_h, rect[4 * i + 0],
-                         rect[4 * i + 2], &x0, &x1, &g);
+            row_span(mean2d + 2 * i, cov2d + 3 * i, t, ty, tile_w, tile_h, rect[4 * i + 0],
+                     rect[4 * i + 2], &x0, &x1, &g);
             for (int tx = x0; tx < x1; tx++) {
                 if (k == total) { free(buf); return -2; } /* spans disagree with the count */
                 buf[k].tile = (int64_t)ty * tiles_x + tx;
@@ -722,11 +713,15 @@ typedef struct {
  * alpha T rgb and multiply T by (1 - alpha).
  * Fills cs[] with the included Gaussians and returns their count; *last is
  * one past the list position of the last included one (0 if none), *neval
- * the number of entries examined, *gpx the guard bits of the pixel.
+ * the number of entries examined, *gpx the guard bits of the pixel.  When
+ * gguard is given, each guard bit is also set on the Gaussian whose own
+ * decision it is (gguard[index]), so that the Gaussians whose inclusion at
+ * some pixel FP32 may decide the other way can be named.
  */
 static int composite_pixel(const int32_t *ids, int64_t len, double px, double py,
                            const double *mean2d, const double *conic, const double *opacity,
-                           contrib_t *cs, double *T_out, int *last, int *neval, int *gpx) {
+                           contrib_t *cs, double *T_out, int *last, int *neval, int *gpx,
+                           int32_t *gguard) {
     double T = 1.0;
     int nc = 0;
     *last = 0;
@@ -737,16 +732,23 @@ static int composite_pixel(const int32_t *ids, int64_t len, double px, double py
         double dx = mean2d[2 * g] - px, dy = mean2d[2 * g + 1] - py;
         double a = conic[3 * g], b = conic[3 * g + 1], c = conic[3 * g + 2];
         double power = -0.5 * (a * dx * dx + c * dy * dy) - b * dx * dy;
-        if (fabs(power) < OR_G_POWER) *gpx |= OR_GPX_POWER;
-        if (power > 0.0) continue;
+        int gb = 0;
+        if (fabs(power) < OR_G_POWER) gb |= OR_GPX_POWER;
+        if (power > 0.0) {
+            *gpx |= gb;
+            if (gguard) gguard[g] |= gb;
+            continue;
+        }
         double G = exp(power);
         double oG = opacity[g] * G;
-        if (fabs(oG * 255.0 - 1.0) < OR_G_ALPHA) *gpx |= OR_GPX_ALPHA;
-        if (fabs(oG / OR_ALPHA_MAX - 1.0) < OR_G_CLAMP) *gpx |= OR_GPX_KINK;
+        if (fabs(oG * 255.0 - 1.0) < OR_G_ALPHA) gb |= OR_GPX_ALPHA;
+        if (fabs(oG / OR_ALPHA_MAX - 1.0) < OR_G_CLAMP) gb |= OR_GPX_KINK;
         double alpha = oG < OR_ALPHA_MAX ? oG : OR_ALPHA_MAX;
-        if (alpha < OR_ALPHA_MIN) continue;
         double Tn = T * (1.0 - alpha);
-        if (fabs(Tn / OR_T_MIN - 1.0) < OR_G_TRANS) *gpx |= OR_GPX_TRANS;
+        if (alpha >= OR_ALPHA_MIN && fabs(Tn / OR_T_MIN - 1.0) < OR_G_TRANS) gb |= OR_GPX_TRANS;
+        *gpx |= gb;
+        if (gguard) gguard[g] |= gb;
+        if (alpha < OR_ALPHA_MIN) continue;
         if (Tn < OR_T_MIN) { j++; break; }
         cs[nc].idx = g;
         cs[nc].alpha = alpha;
@@ -770,14 +772,17 @@ static int composite_pixel(const int32_t *ids, int64_t len, double px, double py
  * three composited channels (reading for grayscale views: compositing is
  * linear, so this equals compositing the per-Gaussian mean colour).  The
  * background bg[3] enters as T_final * bg.  Outputs image[channels][H][W], final_T[H][W],
- * last_idx[H][W], n_eval[H][W], n_included[H][W] and guard_px[H][W].
+ * last_idx[H][W], n_eval[H][W], n_included[H][W] and guard_px[H][W]; and, if
+ * guard_g is given, guard_g[n]: the OR over pixels of the guard bits of each
+ * Gaussian's own decisions (zeroed first).
  */
 void oracle_render(int n, const double *mean2d, const double *conic, const double *opacity,
                    const double *rgb, const int64_t *tile_start,
                    const int32_t *list, int W, int H, int tile_w, int tile_h, int channels,
                    const double *bg, double *image, double *final_T, int32_t *last_idx,
-                   int32_t *n_eval, int32_t *n_included, int32_t *guard_px) {
-    (void)n;
+                   int32_t *n_eval, int32_t *n_included, int32_t *guard_px, int32_t *guard_g) {
+    if (guard_g)
+        for (int i = 0; i < n; i++) guard_g[i] = 0;
     const int tiles_x = (W + tile_w - 1) / tile_w;
     int64_t maxlen = 0;
     int64_t T_tiles = (int64_t)tiles_x * ((H + tile_h - 1) / tile_h);
@@ -792,7 +797,7 @@ void oracle_render(int n, const double *mean2d, const double *conic, const doubl
             double T;
             int last, ne, gp;
             int nc = composite_pixel(ids, len, px, py, mean2d, conic, opacity, cs, &T, &last,
-                                     &ne, &gp);
+                                     &ne, &gp, guard_g);
             double C[3] = {0.0, 0.0, 0.0};
             for (int k = 0; k < nc; k++)
                 for (int ch = 0; ch < 3; ch++) C[ch] += cs[k].alpha * cs[k].T * rgb[3 * cs[k].idx + ch];
@@ -859,7 +864,7 @@ void oracle_render_brute(int n, const double *mean2d, const double *conic, const
             double T;
             int last, ne, gp;
             int nc = composite_pixel(ids, len, px, py, mean2d, conic, opacity, cs, &T, &last,
-                                     &ne, &gp);
+                                     &ne, &gp, NULL);
             double C[3] = {0.0, 0.0, 0.0};
             for (int k = 0; k < nc; k++)
                 for (int ch = 0; ch < 3; ch++) C[ch] += cs[k].alpha * cs[k].T * rgb[3 * cs[k].idx + ch];
@@ -912,7 +917,7 @@ void oracle_render_bwd(int n, const double *mean2d, const double *conic, const d
             double T;
             int last, ne, gp;
             int nc = composite_pixel(ids, len, px, py, mean2d, conic, opacity, cs, &T, &last,
-                                     &ne, &gp);
+                                     &ne, &gp, NULL);
             size_t p = (size_t)py * W + px;
             double g[3];
             if (channels == 3) {

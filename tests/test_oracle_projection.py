@@ -303,23 +303,29 @@ def _min_q_over_rect(a, b, c, x0, x1, y0, y1):
     return best
 
 
-@pytest.mark.parametrize("tile", [(16, 16), (8, 8)])
-def test_tight_tiles_are_exactly_those_meeting_the_ellipse(tile):
+@pytest.mark.parametrize("tile,large", [((16, 16), False), ((8, 8), False), ((8, 8), True)])
+def test_tight_tiles_are_exactly_those_meeting_the_ellipse(tile, large):
     """Brute force over pixels and tiles: each Gaussian's tight tiles (its
     row spans, read back from the tight binning) are exactly the tiles of
     its square rect whose pixel rectangle meets the widened ellipse
     q <= 1.01 * 2 ln(255 o) + 0.01 (q in the conic), which holds every
     pixel with alpha >= 1/255; every other tile of the square rect has alpha
-    < 1/255 at all its pixels."""
+    < 1/255 at all its pixels.  The set is geometric for every box shape:
+    the large case holds boxes of one tile row, of one tile column and of
+    more than 16 tile rows."""
     tw, th = tile
-    W, H = 160, 120
-    rng = np.random.default_rng(5)
+    W, H = (320, 240) if large else (160, 120)
+    rng = np.random.default_rng(6 if large else 5)
     R, t = scenes.random_pose(rng, 0.3, 20.0)
     view = scenes.camera(W, H, 150.0, 150.0, R=R, t=t)
     n = 300
     q = rng.normal(size=(n, 4))
+    ls = rng.normal(-3.5, 0.8, (n, 3))
+    if large:  # a third of them large, the rest small enough for one-row boxes
+        ls = np.where(np.arange(n)[:, None] < n // 3, rng.normal(-2.2, 0.9, (n, 3)),
+                      rng.normal(-4.5, 0.8, (n, 3)))
     p = dict(means=rng.uniform(-0.6, 0.6, (n, 3)) + np.array([0, 0, 2.0]),
-             log_scales=rng.normal(-3.5, 0.8, (n, 3)), quats=q / np.linalg.norm(q, axis=1)[:, None],
+             log_scales=ls, quats=q / np.linalg.norm(q, axis=1)[:, None],
              opacity_logits=rng.normal(-1.0, 2.0, n), sh=np.zeros((1, n, 3)), sh_degree=0)
     sq = oracle.project(p, view, tw, th, tight=False)
     ti = oracle.project(p, view, tw, th, tight=True)
@@ -346,13 +352,7 @@ def test_tight_tiles_are_exactly_those_meeting_the_ellipse(tile):
                 inside = ty * tx_n + tx in tiles_of[i]
                 qmin = _min_q_over_rect(a, b, c, tx * tw - mx, tx * tw + tw - 1 - mx,
                                         ty * th - my, ty * th + th - 1 - my)
-                t0 = ti["rect"][i]
-                rows, cols = t0[3] - t0[1], t0[2] - t0[0]
-                if rows > 16 or rows < 2 or cols < 2:  # such a box keeps its tiles
-                    meets = (ti["tiles_touched"][i] > 0 and t0[0] <= tx < t0[2]
-                             and t0[1] <= ty < t0[3])
-                else:
-                    meets = lvl >= 0 and qmin <= lvl
+                meets = lvl >= 0 and qmin <= lvl
                 if ti["guard"][i] & oracle.GUARD_TIGHT == 0 and abs(qmin - lvl) > 1e-9 * (1 + lvl):
                     assert inside == meets, (i, tx, ty, qmin, lvl)
                 if not inside:
@@ -362,3 +362,9 @@ def test_tight_tiles_are_exactly_those_meeting_the_ellipse(tile):
                 else:
                     kept += 1
     assert dropped > 50 and kept > 50  # the cut is not vacuous on this scene
+    if large:
+        vis = ti["tiles_touched"] > 0
+        rows = (ti["rect"][:, 3] - ti["rect"][:, 1])[vis]
+        cols = (ti["rect"][:, 2] - ti["rect"][:, 0])[vis]
+        assert (rows > 16).sum() >= 3 and (rows == 1).sum() >= 3 and (cols == 1).sum() >= 3, (
+            (rows > 16).sum(), (rows == 1).sum(), (cols == 1).sum())

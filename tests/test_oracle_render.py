@@ -224,3 +224,51 @@ def test_render_bwd_matches_central_differences(channels):
             assert abs(fd - gflat[j]) <= 1e-6 * max(1.0, abs(fd)), (key, j, fd, gflat[j])
             checked += 1
     assert checked > 0.95 * (checked + skipped)
+
+
+def test_guard_attribution_closed_form():
+    """A Gaussian whose alpha equals 1/255 exactly on a ring of pixels is
+    named in guard_g (GPX_ALPHA), and so are those pixels in guard_px; a
+    second Gaussian, with no pixel near a threshold, is not named."""
+    W, H, f = 64, 48, 100.0
+    view = scenes.camera(W, H, f, f, 20.0, 24.0)
+    z, logit = 2.0, 0.4
+    o = 1 / (1 + math.exp(-logit))
+    var = 9.0 / (2.0 * math.log(255.0 * o))  # alpha(3 px from the centre) = 1/255
+    s = z * math.sqrt(var - 0.3) / f
+    a = one_gaussian([0.0, 0.0, z], math.log(s), logit, [0.5, 0.5, 0.5])
+    b = one_gaussian([0.9307, 0.013, z + 1.0], math.log(0.01), 1.0, [0.5, 0.5, 0.5])
+    p = {k: (np.concatenate([a[k], b[k]], axis=1 if k == "sh" else 0) if k != "sh_degree" else 0)
+         for k in a}
+    proj, st, lst, out = oracle.forward_view(p, view, 16, 16)
+    assert out["guard_g"][0] & oracle.GPX_ALPHA
+    assert out["guard_g"][1] == 0
+    for dx, dy in ((3, 0), (-3, 0), (0, 3), (0, -3)):
+        assert out["guard_px"][24 + dy, 20 + dx] & oracle.GPX_ALPHA
+    # the centre pixel sits exactly on the mean: power 0, its own guard
+    assert out["guard_px"][24, 20] == oracle.GPX_POWER
+    assert out["guard_px"][24, 24] == 0
+
+
+def test_guard_attribution_matches_pixel_bits():
+    """On a random scene every guarded pixel has, among the list entries it
+    examined, a Gaussian whose own decision there is in the guard band
+    (alpha within 5e-5 relative of 1/255, recomputed here), and that
+    Gaussian is named in guard_g; guard_g names no Gaussian for a bit that
+    no pixel carries."""
+    p, view = scenes.tiny_scene(3000, 128, 96, seed=8)
+    proj, st, lst, out = oracle.forward_view(p, view, 8, 8)
+    gpx, gg = out["guard_px"], out["guard_g"]
+    assert np.bitwise_or.reduce(gg.ravel()) == np.bitwise_or.reduce(gpx.ravel())
+    tx = (view["width"] + 7) // 8
+    ys, xs = np.nonzero(gpx & oracle.GPX_ALPHA)
+    assert len(ys) > 0
+    for py, px in zip(ys, xs):
+        t = (py // 8) * tx + px // 8
+        ids = lst[st[t]:st[t + 1]][: out["n_eval"][py, px]]
+        dx, dy = proj["mean2d"][ids, 0] - px, proj["mean2d"][ids, 1] - py
+        a, b, c = proj["conic"][ids].T
+        oG = proj["opacity"][ids] * np.exp(-0.5 * (a * dx * dx + c * dy * dy) - b * dx * dy)
+        near = np.abs(oG * 255.0 - 1.0) < 5e-5
+        assert near.any(), (py, px)
+        assert np.all(gg[ids[near]] & oracle.GPX_ALPHA)
