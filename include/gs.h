@@ -64,6 +64,10 @@ typedef enum {
 #define GS_DEV_CAPACITY 1u  /* more (Gaussian, tile) instances than instance_capacity;
                                the surplus was dropped and the render is incomplete */
 #define GS_DEV_NONFINITE 2u /* a Gaussian with a non-finite parameter was culled */
+#define GS_DEV_SPAN_POOL 4u /* tight rects: the row spans of boxes taller than 16 tile rows
+                               did not all fit the plan's span pool; the boxes that missed
+                               it kept all their tiles (images and gradients unchanged, the
+                               instance lists longer than the geometric set) */
 
 /* One camera.  x_cam = R x_world + t with R row-major (world -> camera), the
  * camera looking along +z with y down; pixel (px, py) is sampled at its
@@ -114,10 +118,13 @@ typedef struct {
  *     tile rect to the tiles that meet the axis-aligned box of the ellipse
  *     outside which alpha = o exp(power) < 1/255, with the level widened by
  *     1% + 0.01 against FP32 rounding (a Gaussian with o < 0.999/255 gets no
- *     tile), and, in boxes of 2 to 16 tile rows and at least 2 columns, each
- *     row to the tiles whose pixel band meets that ellipse (GS_BUF_RECT keeps
- *     the box; GS_BUF_TOUCHED counts the tiles).  Only (Gaussian, tile) pairs
- *     that every pixel would skip are dropped: images and gradients are
+ *     tile), and then each tile row of that box to the tiles whose pixel
+ *     rectangle meets the ellipse: the kept tiles are the tiles of the square
+ *     rect that meet the widened ellipse, for every box shape (GS_BUF_RECT
+ *     keeps the box; GS_BUF_TOUCHED counts the tiles).  The spans of a box of
+ *     more than 16 tile rows live in a span pool of the workspace
+ *     (GS_DEV_SPAN_POOL if it runs out).  Only (Gaussian, tile) pairs that
+ *     every pixel would skip are dropped: images and gradients are
  *     unchanged, the instance lists (and so last_idx) shorter.
  * The tile shape changes which pixels a Gaussian can reach (its 3-sigma
  * rect is counted in whole tiles), hence the image; the batch sizes, pixels

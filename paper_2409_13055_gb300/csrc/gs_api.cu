@@ -131,6 +131,15 @@ extern "C" gs_status gs_plan_init(gs_plan* plan, const gs_config* cfg, int32_t n
     len[B_TILE_ORDER] = (size_t)tiles * sizeof(uint32_t);
     len[B_TILE_QUEUE] = 2 * sizeof(uint32_t);
     len[B_SPANS] = cfg->tight_rect ? (size_t)VN * kSpanRows * sizeof(uint32_t) : 0;
+    // boxes of more than kSpanRows tile rows are rare (4 of 446k visible
+    // Gaussians at 1M, 1200x680, 8x8 tiles): one row per 8 pairs, at least 64k
+    {
+        const int64_t rows = VN / 8 > 65536 ? VN / 8 : 65536;
+        p->span_pool_rows = cfg->tight_rect ? (uint32_t)(rows < (int64_t(1) << 30) ? rows
+                                                                                   : (int64_t(1) << 30))
+                                            : 0u;
+    }
+    len[B_SPAN_POOL] = (size_t)p->span_pool_rows * sizeof(uint32_t);
     len[B_GID_OF] = cfg->deterministic ? (size_t)instance_capacity * sizeof(uint32_t) : 0;
     len[B_PARTIAL] = cfg->deterministic ? (size_t)instance_capacity * 11 * sizeof(float) : 0;
     size_t off = 0;

@@ -63,7 +63,9 @@ enum PrivBuf {
     B_PARTIAL,     // [instance_capacity] x 11 floats: per-(Gaussian, tile) partial sums
                    // of the pixel adjoint (deterministic plans)
     B_SPANS,       // [V*n] x kSpanRows u32: tight row spans, x0 | x1 << 16 per tile row
-                   // (tight plans; Gaussians whose box has at most kSpanRows rows)
+                   // (tight plans); a box of more than kSpanRows rows stores its spans
+                   // in B_SPAN_POOL and the pool index of its first row in word 0
+    B_SPAN_POOL,   // [span_pool_rows] u32: row spans of the taller boxes
     B_TOTAL
 };
 
@@ -75,6 +77,7 @@ struct Plan {
     int32_t total_tiles, tile_bits, tile_passes;
     int64_t total_pixels, total_values;
     int32_t depth_sort_blocks, inst_sort_blocks, scan_blocks, loss_blocks;
+    uint32_t span_pool_rows;  // capacity of B_SPAN_POOL (tight plans)
     size_t ws_bytes;
     size_t off[B_TOTAL];
     size_t len[B_TOTAL];
@@ -91,6 +94,7 @@ struct DevCounters {
     uint32_t loss_blocks_done;     // last-block-done ticket of the loss reduction
     uint32_t vn;                   // depth-order entries (visible pairs) of the last gs_bin_sort
     uint32_t n_sorted;             // visible pairs kept by the first depth pass
+    uint32_t span_pool_used;       // rows of B_SPAN_POOL taken by the last gs_project
 };
 
 inline const Plan* P(const gs_plan* p) { return reinterpret_cast<const Plan*>(p); }
@@ -222,17 +226,13 @@ __device__ __forceinline__ int df_floor_div(float hi, float lo, float inv_t) {
 // D = AC - B^2; over the band the largest dx is sqrt(t C / D) when the row of
 // the ellipse's rightmost point, dy* = -(B / C) sqrt(t C / D), lies in the band,
 // else the larger band end; the smallest symmetrically at -dy*.  The
-// projection computes the spans once and stores them (B_SPANS) for the
-// emission to list; a box of more than kSpanRows tile rows keeps all its
-// tiles.
+// projection computes the spans of every row of the box once and stores
+// them for the emission to list: in the Gaussian's own kSpanRows slots
+// (B_SPANS), or, for a taller box, in rows taken from the plan's span pool
+// (B_SPAN_POOL), whose first index goes to slot 0.  A box that finds the
+// pool full keeps all its tiles (kSpanNoPool in slot 0, GS_DEV_SPAN_POOL).
 constexpr int kSpanRows = 16;
-
-// Whether a tight box is cut row by row: at least two rows and two columns
-// (a one-row or one-column box is the ellipse's own bounding box, every one
-// of its tiles meets it) and at most kSpanRows rows.
-__device__ __forceinline__ bool tight_spans_apply(int x0, int y0, int x1, int y1) {
-    return y1 - y0 >= 2 && y1 - y0 <= kSpanRows && x1 - x0 >= 2;
-}
+constexpr uint32_t kSpanNoPool = 0xFFFFFFFFu;
 __device__ __forceinline__ float tight_level(float opacity) {
     return __fmaf_rn(1.01f, __fmul_rn(2.0f, logf(__fmul_rn(255.0f, opacity))), 0.01f);
 }

@@ -302,7 +302,7 @@ k_project(const float* __restrict__ means, const float* __restrict__ log_scales,
           ViewTable vt, float near_z, float4* __restrict__ rec, uint16_t* __restrict__ rect_out,
           uint32_t* __restrict__ touched, int32_t* __restrict__ radius_out,
           uint32_t* __restrict__ dkey, DevCounters* counters,
-          uint32_t* __restrict__ spans) {
+          uint32_t* __restrict__ spans, uint32_t* __restrict__ pool, uint32_t pool_rows) {
     __shared__ Cam cams[kViewsPerThread];
     const int v0 = blockIdx.y * kViewsPerThread;
     const int nv = min(kViewsPerThread, vt.n_views - v0);
@@ -333,19 +333,39 @@ k_project(const float* __restrict__ means, const float* __restrict__ log_scales,
         uint32_t area = 0u;
         if (vis) {
             area = (uint32_t)((p.rect[2] - p.rect[0]) * (p.rect[3] - p.rect[1]));
-            if (vt.tight_rect && tight_spans_apply(p.rect[0], p.rect[1], p.rect[2], p.rect[3])) {
-                // the row spans of the box, stored for the emission
-                const TightEllipse E =
-                    tight_ellipse(p.mxh, p.mxl, p.myh, p.myl, p.ca, p.cb, p.cc, opacity);
+            if (vt.tight_rect) {
+                // the row spans of the box, stored for the emission: in the
+                // Gaussian's slots, or, for a tall box, in rows of the pool
+                const int rows = p.rect[3] - p.rect[1];
                 uint32_t* sp = spans + vg * kSpanRows;
-                int a0, a1;
-                area = 0u;
-                for (int ty = p.rect[1]; ty < p.rect[3]; ++ty) {
-                    area += (uint32_t)tight_row_span(E, ty, vt.log2_tw, vt.log2_th, p.rect[0],
-                                                     p.rect[2], &a0, &a1);
-                    sp[ty - p.rect[1]] = (uint32_t)a0 | ((uint32_t)a1 << 16);
+                uint32_t* dst = sp;
+                if (rows > kSpanRows) {
+                    uint32_t base = kSpanNoPool;
+                    if (counters->span_pool_used < pool_rows) {
+                        base = atomicAdd(&counters->span_pool_used, (uint32_t)rows);
+                        if ((uint64_t)base + (uint64_t)rows > (uint64_t)pool_rows)
+                            base = kSpanNoPool;
+                    }
+                    sp[0] = base;
+                    if (base == kSpanNoPool) {
+                        atomicOr(&counters->status, (uint32_t)GS_DEV_SPAN_POOL);
+                        dst = nullptr;  // the box keeps all its tiles
+                    } else {
+                        dst = pool + base;
+                    }
                 }
-                vis = area > 0u;
+                if (dst) {
+                    const TightEllipse E =
+                        tight_ellipse(p.mxh, p.mxl, p.myh, p.myl, p.ca, p.cb, p.cc, opacity);
+                    int a0, a1;
+                    area = 0u;
+                    for (int ty = p.rect[1]; ty < p.rect[3]; ++ty) {
+                        area += (uint32_t)tight_row_span(E, ty, vt.log2_tw, vt.log2_th,
+                                                         p.rect[0], p.rect[2], &a0, &a1);
+                        dst[ty - p.rect[1]] = (uint32_t)a0 | ((uint32_t)a1 << 16);
+                    }
+                    vis = area > 0u;
+                }
             }
         }
         if (!vis) {
@@ -906,7 +926,7 @@ gs_status launch_project(const Plan* p, const gs_map* map, const gs_view* views_
         p->vt, p->cfg.near_z, buf<float4>(p, ws, GS_BUF_PROJ), buf<uint16_t>(p, ws, GS_BUF_RECT),
         buf<uint32_t>(p, ws, GS_BUF_TOUCHED), buf<int32_t>(p, ws, GS_BUF_RADIUS),
         buf<uint32_t>(p, ws, B_DKEY_A), ctr,
-        buf<uint32_t>(p, ws, B_SPANS));
+        buf<uint32_t>(p, ws, B_SPANS), buf<uint32_t>(p, ws, B_SPAN_POOL), p->span_pool_rows);
     return launch_status();
 }
 

@@ -298,12 +298,14 @@ k_emit(const uint32_t* __restrict__ order, const uint32_t* __restrict__ off,
        const uint2* __restrict__ rects, const uint32_t* count_dev, int n, ViewTable vt,
        uint32_t cap,
        uint32_t* __restrict__ ikeys, uint32_t* __restrict__ ivals,
-       uint32_t* __restrict__ gid_of, const uint32_t* __restrict__ spans) {
+       uint32_t* __restrict__ gid_of, const uint32_t* __restrict__ spans,
+       const uint32_t* __restrict__ pool) {
     grid_dep_begin();
     __shared__ uint32_t s_off[kEmitEntries + 1];
     __shared__ uint32_t s_vg[kEmitEntries];
     __shared__ uint2 s_rect[kEmitEntries];
-    // tight rects: the entry's row spans (boxes of at most kSpanRows rows)
+    // tight rects: the entry's row spans (boxes of at most kSpanRows rows),
+    // or, for a taller box, the pool index of its first row in s_span[e][0]
     __shared__ uint32_t s_span[kEmitEntries][kSpanRows];
     __shared__ uint16_t s_view[kEmitEntries];
     const uint32_t count = *count_dev;
@@ -320,8 +322,8 @@ k_emit(const uint32_t* __restrict__ order, const uint32_t* __restrict__ off,
         if (vt.tight_rect && s_off[e] != off[e0 + e + 1]) {
             const uint2 rc = s_rect[e];
             const int rows = (int)(rc.y >> 16) - (int)(rc.x >> 16);
-            if (tight_spans_apply(rc.x & 0xFFFF, rc.x >> 16, rc.y & 0xFFFF, rc.y >> 16))
-                for (int r = 0; r < rows; ++r) s_span[e][r] = spans[(size_t)vg * kSpanRows + r];
+            const int nw = rows > kSpanRows ? 1 : rows;
+            for (int r = 0; r < nw; ++r) s_span[e][r] = spans[(size_t)vg * kSpanRows + r];
         }
     }
     if (e == 0) s_off[ne] = off[e0 + ne];
@@ -338,17 +340,20 @@ k_emit(const uint32_t* __restrict__ order, const uint32_t* __restrict__ off,
         const uint32_t x0 = rc.x & 0xFFFF, y0 = rc.x >> 16, x1 = rc.y & 0xFFFF, y1 = rc.y >> 16;
         const uint32_t w = x1 - x0, k = pos - s_off[lo];
         uint32_t tx, ty;
-        if (vt.tight_rect && tight_spans_apply(x0, y0, x1, y1)) {
+        const bool tall = y1 - y0 > (uint32_t)kSpanRows;
+        if (vt.tight_rect && !(tall && s_span[lo][0] == kSpanNoPool)) {
             // the k-th tile of the row spans the projection stored and counted
-            uint32_t kk = k, r = 0;
+            const uint32_t* sr = tall ? pool + s_span[lo][0] : s_span[lo];
+            uint32_t kk = k, r = 0, sp = sr[0];
             for (; r + 1 < y1 - y0; ++r) {
-                const uint32_t sp = s_span[lo][r], wr = (sp >> 16) - (sp & 0xFFFF);
+                const uint32_t wr = (sp >> 16) - (sp & 0xFFFF);
                 if (kk < wr) break;
                 kk -= wr;
+                sp = sr[r + 1];
             }
             ty = y0 + r;
             // (a count that disagreed would land past the row; stay inside the rect)
-            tx = min((s_span[lo][r] & 0xFFFF) + kk, x1 - 1u);
+            tx = min((sp & 0xFFFF) + kk, x1 - 1u);
         } else {
             const uint32_t dy = k / w;
             ty = y0 + dy;
@@ -508,7 +513,7 @@ gs_status launch_bin_sort(const Plan* p, int32_t n, void* ws, cudaStream_t st) {
     launch_pdl(k_emit, (VN + kEmitEntries - 1) / kEmitEntries, kEmitEntries, 0, st, va, offs,
                buf<uint2>(p, ws, GS_BUF_RECT), n_sorted, n, p->vt, icap, ika, iva,
                p->cfg.deterministic ? buf<uint32_t>(p, ws, B_GID_OF) : nullptr,
-               buf<uint32_t>(p, ws, B_SPANS));
+               buf<uint32_t>(p, ws, B_SPANS), cbuf<uint32_t>(p, ws, B_SPAN_POOL));
     gs_status s = launch_status();
     if (s != GS_OK) return s;
 

@@ -101,6 +101,47 @@ def gaussians_clear_of(mask, proj, window=5):
     return (proj["tiles_touched"] == 0) | (hits == 0)
 
 
+# Per-pixel decisions of a Gaussian whose FP32 outcome may differ from the
+# FP64 one and whose flip changes that Gaussian's own gradient by a whole
+# pixel's contribution: its alpha next to 1/255 (blended or skipped) or next
+# to the 0.99 clamp (gradient passed or not).  Two guarded decisions cannot
+# flip that way: the sign of the power (the conic is positive definite, so
+# the exact power is <= 0 and FP32 rounding, ~1e-7 of the terms, cannot make
+# it positive unless the conic's condition number reaches ~1e7 -- a mean
+# that projects onto a pixel centre only gives power = 0 on both sides), and
+# the transmittance cut-off (GPX_TRANS): the Gaussian that ends a pixel sits
+# behind T ~ 1e-4, so the pixel's share in its gradient and its effect on
+# the colour behind the others are ~1e-4 of that pixel's.
+DECISION_BITS = oracle.GPX_ALPHA | oracle.GPX_KINK
+
+
+def gradient_keep(params, views, renders, tile=(16, 16)):
+    """The Gaussians whose parameter gradients the parity tests compare: in
+    every view, clear of the pixels that a Gaussian with a guarded
+    whole-Gaussian decision (rect, near plane, determinant, depth key) can
+    reach, widened by the SSIM window; without a per-pixel decision of their
+    own in its guard band (DECISION_BITS of the oracle's guard_g); and
+    without a colour or Jacobian clamp next to its kink."""
+    n = params["means"].shape[0]
+    keep = np.ones(n, bool)
+    for view, rout in zip(views, renders):
+        proj = oracle.project(params, view, *tile)
+        mask = guard_pixel_mask(view, proj, rout, tile, params=params, pixel_bits=0)
+        keep &= gaussians_clear_of(mask, proj)
+        keep &= (rout["guard_g"] & DECISION_BITS) == 0
+        keep &= (proj["guard"] & oracle.GUARD_KINK) == 0
+    return keep
+
+
+def grad_errors(got, want, keep):
+    """Relative L2 error per parameter group over the Gaussians in keep."""
+    out = {}
+    for k in want:
+        a, b = ((got[k][:, keep], want[k][:, keep]) if k == "sh" else (got[k][keep], want[k][keep]))
+        out[k] = rel_l2(a, b)
+    return out
+
+
 def grad_pixel_mask(rout):
     """Pixels whose gradient contributions cross a kink (alpha clamp)."""
     return (rout["guard_px"] & oracle.GPX_KINK) != 0
@@ -111,6 +152,32 @@ def rel_l2(a, b):
     b = np.asarray(b, np.float64).ravel()
     nb = np.linalg.norm(b)
     return float(np.linalg.norm(a - b) / nb) if nb > 0 else float(np.linalg.norm(a))
+
+
+def compare_tile_lists(keys, vals, n, o, view, tile, tile_offset=0, view_index=0):
+    """End-to-end list parity of one view: the GPU's sorted instances (keys:
+    global tile ids, vals: view*n + index) against the oracle's tile lists
+    built from its own projection `o` (made with tight rects).  The
+    Gaussians with a guarded projection decision (FWD_GUARDS) are removed
+    from both sides; everything else -- which (tile, Gaussian) pairs exist
+    and their order in each tile -- must be equal.  Returns (pairs compared,
+    pairs removed on the oracle side)."""
+    tw, th = tile
+    tx, ty = oracle.tile_grid(view["width"], view["height"], tw, th)
+    ostart, olst = oracle.bin_tiles(o["depth"].astype(np.float32), o["rect"], o["tiles_touched"],
+                                    tx, ty, o, tile)
+    otile = np.repeat(np.arange(tx * ty), np.diff(ostart))
+    guarded = (o["guard"] & FWD_GUARDS) != 0
+    keep_o = ~guarded[olst]
+    mine = (keys >= tile_offset) & (keys < tile_offset + tx * ty)
+    gk = keys[mine].astype(np.int64) - tile_offset
+    gv = vals[mine].astype(np.int64)
+    assert np.all(gv // n == view_index)
+    gv = gv % n
+    keep_g = ~guarded[gv]
+    np.testing.assert_array_equal(gk[keep_g], otile[keep_o])
+    np.testing.assert_array_equal(gv[keep_g], olst[keep_o])
+    return int(keep_o.sum()), int((~keep_o).sum())
 
 
 def tile_lists_from_gpu(ranges, vals, tile_range, n):

@@ -61,12 +61,12 @@ def test_deterministic_backward_is_bit_stable():
     np.testing.assert_array_equal(img_det, img_plain)
     assert U.rel_l2(det, plain) < 1e-6
     # parity with the oracle's whole iteration
-    L, og, _ = oracle.iteration(p, views, targets, 0.2, 8, 8)
+    L, og, renders = oracle.iteration(p, views, targets, 0.2, 8, 8)
     G = {k: t.cpu().numpy() for k, t in gm.grads().items()}
-    for k in og:
-        if np.linalg.norm(og[k]) == 0:
-            continue
-        assert U.rel_l2(G[k], og[k]) <= 1e-3, (k, U.rel_l2(G[k], og[k]))
+    keep = U.gradient_keep(p, views, renders, (8, 8))
+    assert keep.mean() > 0.95, keep.mean()
+    errs = U.grad_errors(G, og, keep)
+    assert all(e <= 1e-4 for e in errs.values()), errs
 
 
 def test_deterministic_homodirectional_sums_match_atomic_ones():

@@ -6,12 +6,14 @@ rects, the map stored in Z-order).
 * 1M Gaussians, SH-3, 1200x680 (the headline): one whole mapping iteration
   against the FP64 oracle's whole iteration on the same seeded inputs (a
   seeded noise target; ~10 s of oracle time): loss, image on every pixel
-  outside the guard bands, every parameter-gradient group over the
-  Gaussians whose footprint stays clear of the guard pixels.
+  outside the guard bands, tile lists bit-exact outside the guarded
+  Gaussians, every parameter-gradient group over the Gaussians of
+  gpu_util.gradient_keep.
 * 500k Gaussians, 16 views of three kinds (the batched form): the batched
-  launch's images of one view of each kind against the oracle's forward of
-  that view, and the batched iteration against the loop of 16 single-view
-  plans (loss and gradients; a property that holds at any size).
+  iteration's loss and gradients (summed over the 16 views) against the
+  oracle's 16-view iteration (~1 min of oracle time), the images of one
+  view of each kind against the oracle's, and the batched iteration against
+  the loop of 16 single-view plans.
 """
 import numpy as np
 import pytest
@@ -25,17 +27,17 @@ from tests import gpu_util as U
 pytestmark = pytest.mark.gpu
 
 IMG_TOL = 1e-5
-# Gradient bar at full size.  The 1e-4 bar of the oracle-size cases assumes
-# short per-pixel lists; here a pixel walks ~144 list entries (117M pairs on
-# 816k pixels), and the backward recovers T_i by dividing by (1 - alpha) at
-# every step (reading C10), so T carries ~144 u (u = 2^-24, ~1e-5) of relative
-# error, which dL/dalpha = T_i (g.c) - (g.S)/(1 - alpha), a difference of
-# similar terms (cancellation ~10x), turns into ~1e-4 per pixel before the
-# sums over pixels cancel further for the conic and quaternion terms.
-# Measured: means 6.8e-5, log-scales 1.3e-4, quaternions 3.4e-4, opacity
-# 6.1e-5, SH 3.6e-5; the same with the deterministic adjoint, so none of it
-# is the order of the float atomics.
-GRAD_TOL = 5e-4
+# Gradients: 1e-4 relative L2 per group, as at the oracle sizes, over the
+# Gaussians of gpu_util.gradient_keep.  With a noise target a Gaussian's
+# gradient is a random-sign sum over its pixels, so a single pixel where FP32
+# and FP64 take its alpha-vs-1/255 decision differently moves it by several
+# per cent; the oracle names those Gaussians (guard_g), ~0.2% of the visible
+# ones here.  Without that exclusion the groups read 6.9e-5 (means) to
+# 3.5e-4 (quaternions), 99% of it from the named Gaussians; with it 1.1e-5 to
+# 1.3e-5.  Neither recovering T by division (reading C10) nor the FP32 pixel
+# sums contribute at this level: the same errors came out with T carried in
+# double precision and with an IEEE reciprocal.
+GRAD_TOL = 1e-4
 LAUNCH = dict(tile=(8, 8), smem_batch=128, pixels_per_thread=1, smem_batch_bwd=64,
               pixels_per_thread_bwd=2)
 
@@ -62,6 +64,7 @@ def test_headline_iteration_matches_oracle():
     rast.render_bwd(m, g)
     torch.cuda.synchronize()
     assert rast.counters().status == 0
+    _, keys, vals, _ = U.gpu_tile_lists(rast)
     img = rast.view_slice(rast.images, 0).cpu().numpy()
     loss = rast.loss.item()
     grads = {k: t.cpu().numpy() for k, t in gm.grads().items()}
@@ -77,22 +80,18 @@ def test_headline_iteration_matches_oracle():
           f"pixels, loss {loss:.8f} vs {L:.8f}")
     assert err.max() <= IMG_TOL
     assert abs(loss - L) <= 1e-5 * abs(L)
-    # gradients of the Gaussians whose footprint (dilated by the SSIM window)
-    # stays clear of the pixels reached by a Gaussian with a guarded rect,
-    # depth key or cull decision, where whole blends can differ.  Pixels with
-    # a guarded per-pixel decision (alpha at 1/255, T at 1e-4) stay in: there
-    # the two sides differ by one Gaussian of alpha ~1/255 or behind T ~1e-4,
-    # below the gradient bar
-    clear = U.gaussians_clear_of(
-        U.guard_pixel_mask(view, proj, renders[0], (8, 8), params=p, pixel_bits=0), proj)
+    # tile lists: bit-exact outside the Gaussians with a guarded decision
+    compared, removed = U.compare_tile_lists(keys, vals, p["means"].shape[0], proj, view, (8, 8))
+    print(f"  tile lists: {compared} pairs bit-exact, {removed} pairs of guarded Gaussians removed")
+    assert removed <= 0.01 * compared
+    keep = U.gradient_keep(p, views, renders, (8, 8))
     vis = proj["tiles_touched"] > 0
-    assert (clear & vis).sum() >= 0.95 * vis.sum(), ((clear & vis).sum(), vis.sum())
-    for k in og:
-        a, b = (grads[k][:, clear], og[k][:, clear]) if k == "sh" else (grads[k][clear], og[k][clear])
-        e = U.rel_l2(a, b)
-        print(f"  gradient {k}: rel L2 {e:.2e} over {100 * (clear & vis).sum() / vis.sum():.1f}% "
+    assert (keep & vis).sum() >= 0.95 * vis.sum(), ((keep & vis).sum(), vis.sum())
+    errs = U.grad_errors(grads, og, keep)
+    for k, e in errs.items():
+        print(f"  gradient {k}: rel L2 {e:.2e} over {100 * (keep & vis).sum() / vis.sum():.2f}% "
               f"of the visible Gaussians (all: {U.rel_l2(grads[k], og[k]):.2e})")
-        assert e <= GRAD_TOL, (k, e)
+    assert all(e <= GRAD_TOL for e in errs.values()), errs
 
 
 def test_batched16_views_match_oracle_and_per_view_loop():
@@ -110,6 +109,7 @@ def test_batched16_views_match_oracle_and_per_view_loop():
             assert rast.counters().status == 0
             loss = rast.loss.item()
             imgs = {v: rast.view_slice(rast.images, v).cpu().numpy() for v in (0, 6, 12)}
+            grads = {k: t.cpu().numpy() for k, t in gm.grads().items()}
         else:
             it = mapping.PerViewLoop(gm, views, targets, lam, keep_grads=True, **LAUNCH)
             it()
@@ -120,9 +120,18 @@ def test_batched16_views_match_oracle_and_per_view_loop():
         torch.cuda.empty_cache()
     assert abs(out[0][1] - out[1][1]) <= 1e-6 * abs(out[1][1])
     assert U.rel_l2(out[0][0], out[1][0]) < 1e-5
+    # the batched iteration against the oracle's 16-view iteration
+    L, og, renders = oracle.iteration(p, views, targets, lam, 8, 8)
+    assert abs(out[0][1] - L) <= 1e-5 * abs(L), (out[0][1], L)
+    keep = U.gradient_keep(p, views, renders, (8, 8))
+    errs = U.grad_errors(grads, og, keep)
+    print(f"16 views: loss {out[0][1]:.8f} vs {L:.8f}; gradients over {keep.mean() * 100:.2f}% "
+          f"of the Gaussians: " + ", ".join(f"{k} {e:.2e}" for k, e in errs.items()))
+    assert all(e <= GRAD_TOL for e in errs.values()), errs
     # one view of each kind (640x480 RGB, 752x480 gray, 1200x680 RGB) against the oracle
     for v, img in imgs.items():
-        proj, st, lst, o = oracle.forward_view(p, views[v], 8, 8)
+        o = renders[v]
+        proj = oracle.project(p, views[v], 8, 8)
         mask = U.guard_pixel_mask(views[v], proj, o, (8, 8), params=p)
         assert mask.mean() < 0.02, (v, mask.mean())
         err = np.abs(img - o["image"])[:, ~mask]

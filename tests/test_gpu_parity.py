@@ -84,13 +84,14 @@ def test_projection_parity(case):
 
 
 @pytest.mark.parametrize("case", list(CASES))
-def test_binning_bit_exact(case):
+@pytest.mark.parametrize("tile", [(16, 16), (8, 8)])
+def test_binning_bit_exact(case, tile):
     p, view = CASES[case]()
-    gm, rast = run_forward(p, view)
+    gm, rast = run_forward(p, view, tile=tile)
     g = U.gpu_projection(rast, gm.n)
     ranges, keys, vals, c = U.gpu_tile_lists(rast)
     assert c.status == 0 and c.n_instances == c.n_instances_raw
-    tx, ty = oracle.tile_grid(view["width"], view["height"], 16, 16)
+    tx, ty = oracle.tile_grid(view["width"], view["height"], *tile)
     # 1. the integer part alone: the GPU's own (tile, Gaussian) pairs, each
     #    Gaussian with as many as it counted, inside its rect, and in the
     #    (tile, FP32 depth key, index) order
@@ -104,13 +105,12 @@ def test_binning_bit_exact(case):
     np.testing.assert_array_equal(ranges[:, 0], start[:-1])
     np.testing.assert_array_equal(ranges[:, 1], start[1:])
     assert len(np.unique(keys.astype(np.int64) * gm.n + vals)) == len(vals)  # no pair twice
-    # 2. end to end: lists from the oracle's own projection, where no
-    #    Gaussian of the scene sits in a guard band
-    o = oracle.project(p, view)
-    if not np.any(o["guard"] & U.FWD_GUARDS):
-        ostart, olst = oracle.bin_tiles(o["depth"].astype(np.float32), o["rect"],
-                                        o["tiles_touched"], tx, ty, o, (16, 16))
-        np.testing.assert_array_equal(vals, olst)
+    # 2. end to end: lists from the oracle's own projection and binning, the
+    #    Gaussians with a guarded projection decision removed from both sides
+    o = oracle.project(p, view, *tile)
+    compared, removed = U.compare_tile_lists(keys, vals, gm.n, o, view, tile)
+    print(f"{case} {tile}: {compared} pairs bit-exact, {removed} of guarded Gaussians removed")
+    assert compared > 100 and removed <= max(50, 0.01 * compared)
 
 
 def test_depth_order_holds_the_visible_pairs_and_binning_repeats():
@@ -505,10 +505,11 @@ def test_full_iteration_matches_oracle():
     mask = U.guard_pixel_mask(view, oracle.project(p, view), renders[0])
     assert mask.mean() < 0.02
     gg = {k: t.cpu().numpy() for k, t in gm.grads().items()}
-    for k in og:
-        if np.linalg.norm(og[k]) == 0:
-            continue
-        assert U.rel_l2(gg[k], og[k]) <= 10 * GRAD_TOL, (k, U.rel_l2(gg[k], og[k]))
+    keep = U.gradient_keep(p, v, renders)
+    assert keep.mean() > 0.97, keep.mean()
+    og = {k: g for k, g in og.items() if np.linalg.norm(g) > 0}  # identity rotations, SH-0
+    errs = U.grad_errors(gg, og, keep)
+    assert all(e <= GRAD_TOL for e in errs.values()), errs
 
 
 def test_recompute_is_bit_identical():
@@ -554,9 +555,14 @@ def test_autograd_function_and_recompute_mode():
     for a, b in zip(*grads):
         assert torch.allclose(a, b, rtol=1e-5, atol=1e-9)
     # against the oracle: L1 loss gradient through the same path
-    o_L, og, _ = oracle.iteration(p, [view], [target.view(3, view["height"], view["width"]).cpu().numpy()], 0.0)
-    for name, gk in zip(("means", "log_scales", "quats", "opacity_logits", "sh"), grads[0]):
-        assert U.rel_l2(gk.cpu().numpy(), og[name]) < 5e-4, name
+    o_L, og, renders = oracle.iteration(
+        p, [view], [target.view(3, view["height"], view["width"]).cpu().numpy()], 0.0)
+    keep = U.gradient_keep(p, [view], renders)
+    assert keep.mean() > 0.95, keep.mean()
+    got = dict(zip(("means", "log_scales", "quats", "opacity_logits", "sh"),
+                   (g.cpu().numpy() for g in grads[0])))
+    errs = U.grad_errors(got, og, keep)
+    assert all(e <= GRAD_TOL for e in errs.values()), errs
 
 
 @pytest.mark.parametrize("sh_degree", [3, 1])

@@ -4,8 +4,9 @@ training from smoothed, down-sampled keyframe images to full resolution).
 Bars: a pyramid level within 1e-6 max-abs of the FP64 oracle's (values in
 [0, 1]; one FP32 rounding per tap); a mapping iteration at a coarse level
 matching the oracle's iteration on the oracle's own pyramid target and
-level camera (loss 1e-5 relative, gradients 1e-3 relative L2 per group with
-the FP32 floor of the whole-iteration bar).
+level camera (loss 1e-5 relative, gradients 1e-4 relative L2 per group over
+the Gaussians clear of guarded decisions, with the FP32 floor of the
+streaming test for the near-zero rotation gradient of isotropic insertions).
 """
 import numpy as np
 import pytest
@@ -14,6 +15,7 @@ import torch
 import oracle
 from paper_2409_13055_gb300 import binding as B
 from paper_2409_13055_gb300 import pyramid, scenes
+from tests import gpu_util as U
 
 pytestmark = pytest.mark.gpu
 
@@ -62,9 +64,13 @@ def test_coarse_to_fine_iterations_match_oracle():
             views = [w[0] if level == 0 else oracle.pyr_view(w[0]) for w in window]
             targets = [w[1].astype(np.float64) if level == 0 else oracle.pyr_down(w[1])
                        for w in window]
-            L, og, _ = oracle.iteration(before, views, targets, 0.2)
+            L, og, renders = oracle.iteration(before, views, targets, 0.2)
             assert abs(loss - L) <= 1e-5 * abs(L), (level, loss, L)
+            keep = U.gradient_keep(before, views, renders)
+            assert keep.mean() > 0.95, (level, keep.mean())
             floor = 1e-6 * np.sqrt(sum(np.sum(np.square(og[g])) for g in GROUPS))
             for g in GROUPS:
-                err = np.linalg.norm(grads[g].astype(np.float64) - og[g])
-                assert err <= 1e-3 * np.linalg.norm(og[g]) + floor, (level, g, err)
+                a, b = ((grads[g][:, keep], og[g][:, keep]) if g == "sh"
+                        else (grads[g][keep], og[g][keep]))
+                err = np.linalg.norm(a.astype(np.float64) - b)
+                assert err <= 1e-4 * np.linalg.norm(b) + floor, (level, g, err)
