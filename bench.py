@@ -41,14 +41,15 @@ sys.path.insert(0, ROOT)
 METRIC = ("mapping iters/s (fwd+bwd+Adam) @1M Gaussians 1200×680; batched vs per-view; "
           "%roofline")
 WORKLOAD = "room1M_1200x680"
-# FP32 operations per (pixel, Gaussian) pair of the algorithm as written (an
-# FMA counts 2): forward 26 (offset 1, power 9, exp 2, alpha 2, transmittance
-# 2, weight 1, blend 6, the three skip/stop tests 3); adjoint 64 (recompute 12,
-# transmittance and colour-behind recursion 20, gradient terms 23, sum over the
-# tile's pixels 9), the count of the adjoint as written, kept fixed across
-# implementations so the fractions stay comparable.
-PAIR_FLOPS_FWD = 26.0
-PAIR_FLOPS_BWD = 64.0
+# Algorithmic FP32 operations per evaluated (pixel, Gaussian) pair, an FMA
+# counting 2, independent of how a kernel is written: forward ~20 (offset 2,
+# power as 6 FMA-equivalents, alpha 2, transmittance 2, colour 6, the exp on
+# the SFU), adjoint ~60 (the forward's recomputation, the transmittance and
+# colour-behind recursion, the alpha, power, mean, conic, opacity and colour
+# terms, and the sum over the pixels).  The kernels as written execute 26 and
+# 64 of them; the fractions use the algorithmic counts.
+PAIR_FLOPS_FWD = 20.0
+PAIR_FLOPS_BWD = 60.0
 
 # DRAM bytes (read + write) of one k_render_bwd launch on the 1M 1200x680
 # workload stored in Z-order, from one single-pass ncu capture per launch
@@ -71,7 +72,7 @@ def iteration_roofline(n, sh_degree, n_views, n_values, n_pixels, instances, pai
     K = (sh_degree + 1) ** 2
     pb = 4 * (11 + 3 * K)  # parameter bytes per Gaussian
     bw = peaks["hbm_gbs"] * 1e9
-    fl = fp32_peak_tflops(peaks["sm_max_mhz"]) * 1e12
+    fl = fp32_peak_tflops(peaks["sm_max_mhz"], peaks["sms"]) * 1e12
     vn = n_views * n
     stages = dict(
         project=((n_views + 3) // 4 * n * pb + vn * 72) / bw,
@@ -88,20 +89,29 @@ def iteration_roofline(n, sh_degree, n_views, n_values, n_pixels, instances, pai
                 basis="sum over stages of max(bytes / measured HBM copy, FLOPs / FP32 peak)")
 
 
-def load_peaks():
+def load_peaks(sms=None):
+    """Measured HBM copy bandwidth and maximum SM clock, and the SM count of
+    the device (sms: given, or read from the current CUDA device)."""
+    sms = int(sms) if sms is not None else device_sms()
     path = os.path.join(ROOT, "MEASURED_PEAKS.json")
     try:
         with open(path) as f:
             d = json.load(f)
         return dict(hbm_gbs=float(d["hbm_gbs"]), sm_max_mhz=float(d.get("sm_max_mhz", 2070.0)),
-                    source="measured")
+                    sms=sms, source="measured")
     except Exception:
-        return dict(hbm_gbs=6800.0, sm_max_mhz=2070.0, source="fallback")
+        return dict(hbm_gbs=6800.0, sm_max_mhz=2070.0, sms=sms, source="fallback")
 
 
-def fp32_peak_tflops(sm_mhz):
-    # 152 SMs x 128 FP32 lanes x 2 flops (FMA) per clock
-    return 152 * 128 * 2 * sm_mhz * 1e6 / 1e12
+def fp32_peak_tflops(sm_mhz, sms):
+    # SMs x 128 FP32 lanes x 2 flops (FMA) per clock
+    return sms * 128 * 2 * sm_mhz * 1e6 / 1e12
+
+
+def device_sms():
+    """Streaming multiprocessors of the current device (152 on a GB300)."""
+    import torch
+    return int(torch.cuda.get_device_properties(torch.cuda.current_device()).multi_processor_count)
 
 
 class ClockSampler:
@@ -195,15 +205,30 @@ def barrier(ws):
 # ----------------------------------------------------------------------------
 # The CPU oracle (reference arm and cpu_baseline).
 # ----------------------------------------------------------------------------
-def oracle_iteration_seconds(p, view, target, lam):
+def host_cores():
+    """Host cores this process may run on."""
+    try:
+        return len(os.sched_getaffinity(0))
+    except (AttributeError, OSError):
+        return os.cpu_count() or 1
+
+
+def oracle_iteration_seconds(p, view, target, lam, tile=(8, 8), threads=1):
+    """Wall time of one whole FP64 oracle iteration (project, bin, render,
+    loss, adjoint, Adam) of one view on `threads` host threads."""
     import oracle
-    t0 = time.perf_counter()
-    L, g, _ = oracle.iteration(p, [view], [target], lam)
-    flat_p = np.concatenate([np.asarray(p[k], np.float64).ravel() for k in oracle.PARAM_GROUPS])
-    flat_g = np.concatenate([g[k].ravel() for k in oracle.PARAM_GROUPS])
-    m, v = np.zeros_like(flat_p), np.zeros_like(flat_p)
-    oracle.adam(flat_p, flat_g, m, v, 1e-3, 1)
-    return time.perf_counter() - t0
+    oracle.set_threads(threads)
+    try:
+        t0 = time.perf_counter()
+        L, g, _ = oracle.iteration(p, [view], [target], lam, tile[0], tile[1])
+        flat_p = np.concatenate([np.asarray(p[k], np.float64).ravel()
+                                 for k in oracle.PARAM_GROUPS])
+        flat_g = np.concatenate([g[k].ravel() for k in oracle.PARAM_GROUPS])
+        m, v = np.zeros_like(flat_p), np.zeros_like(flat_p)
+        oracle.adam(flat_p, flat_g, m, v, 1e-3, 1)
+        return time.perf_counter() - t0
+    finally:
+        oracle.set_threads(1)
 
 
 WORKLOADS = {
@@ -232,11 +257,12 @@ def run_reference(args, ws, rank):
     from paper_2409_13055_gb300 import scenes
     p, view = make_workload(args.workload)
     target = scenes.random_target(view, scenes.SEED_BASE + 13)
+    cores = host_cores()
     times = []
     for _ in range(args.warmup if args.reference_warmup else 0):
-        oracle_iteration_seconds(p, view, target, 0.2)
+        oracle_iteration_seconds(p, view, target, 0.2, threads=cores)
     for _ in range(args.steps):
-        times.append(oracle_iteration_seconds(p, view, target, 0.2))
+        times.append(oracle_iteration_seconds(p, view, target, 0.2, threads=cores))
     t = float(np.mean(times))
     v = 1.0 / t
     out = dict(metric=METRIC, value=v, unit="iters/s", impl="reference", n_gpus=0,
@@ -244,10 +270,11 @@ def run_reference(args, ws, rank):
                scaling="weak", vs_baseline=None, dtype="f64", data="synthetic",
                config=dict(workload=args.workload, gaussians=int(p["means"].shape[0]),
                            width=view["width"], height=view["height"], sh_degree=3, views=1,
-                           lam=0.2),
-               cpu_baseline=dict(value=v, unit="iters/s", cores=1, kind="oracle",
+                           lam=0.2, tile="8x8"),
+               cpu_baseline=dict(value=v, unit="iters/s", cores=cores, kind="oracle",
                                  sample="one full FP64 mapping iteration of the workload per step "
-                                        "(target: seeded noise image)"),
+                                        "(target: seeded noise image), OpenMP on every host "
+                                        "core of the process"),
                e2e=dict(value=v, unit="iters/s", h2d_bytes_per_step=0, d2h_bytes_per_step=0))
     print(json.dumps(out), flush=True)
 
@@ -284,10 +311,13 @@ def run_batched(args, ws):
     K = max(10, min(args.steps, 100))
     result = {}
     stream = torch.cuda.current_stream()
-    for mode in ("batched", "per_view"):
+    for mode in ("batched", "recompute", "per_view"):
         gm = mapping.GaussianMap(p)
-        if mode == "batched":
-            rast = mapping.fit_instance_capacity(views, gm, headroom=1.5, **cfg)
+        if mode in ("batched", "recompute"):
+            # recompute: the checkpointing plan, one view's projection and
+            # binning in the workspace, the 16 views one pass at a time
+            rast = mapping.fit_instance_capacity(views, gm, headroom=1.5,
+                                                 recompute=mode == "recompute", **cfg)
             it = mapping.MappingStep(gm, rast, rast.pack(targets), lam)
         else:
             it = mapping.PerViewLoop(gm, views, targets, lam, **cfg)
@@ -304,6 +334,8 @@ def run_batched(args, ws):
         torch.cuda.synchronize()
         ms = reduce_max(e0.elapsed_time(e1), ws) / K
         result[mode] = dict(iters_per_s=ws * 1e3 / ms, ms_per_iter=ms)
+        if mode != "per_view":
+            result[mode]["workspace_bytes"] = int(rast.workspace_bytes)
         if mode == "batched":
             inst = int(rast.counters().n_instances)
             pairs = int(rast.last_idx.to(torch.int64).sum().item())
@@ -312,6 +344,7 @@ def run_batched(args, ws):
                 gm.n, gm.degree, len(views), rast.total_values, px, inst, pairs,
                 rast.total_tiles, tile_passes(rast.total_tiles), gm.total, ms, load_peaks())
         del it, gm
+        rast = None
         torch.cuda.empty_cache()
     result["speedup_batched_over_per_view"] = (result["batched"]["iters_per_s"] /
                                                result["per_view"]["iters_per_s"])
@@ -334,7 +367,7 @@ def run_streaming(args, ws):
     import time
 
     import torch
-    from paper_2409_13055_gb300 import scenes
+    from paper_2409_13055_gb300 import mapping, scenes
     from paper_2409_13055_gb300.streaming import StreamingMapper
 
     kfs = list(scenes.streaming_keyframes(args.streaming_kfs, 20_000, device="cuda"))
@@ -363,16 +396,79 @@ def run_streaming(args, ws):
     it_ms = reduce_max(it_ms, ws)
     status = int(mapper.status().status)
     n_it = mapper.iterations
+    # the window's workspace, and what a plan keeping every view's
+    # projection (no recompute) would need for the same window and map, its
+    # instance capacity covering all views
+    final = mapper.steps[0].rast
+    ws_keep = mapping.plan_workspace_bytes(
+        final.views, final.n_capacity, final.instance_capacity * len(final.views),
+        recompute=False, **cfg)
     return dict(iters_per_s=ws * n_it / (it_ms * 1e-3), keyframes_per_s=ws * len(kfs) / wall,
                 iterations=n_it, keyframes=len(kfs), final_gaussians=int(mapper.gmap.n),
                 ms_per_iter_final_map=last_kf_ms / mapper.iters, wall_s=wall,
                 replans=mapper.replans, device_status=status,
+                workspace_bytes=int(final.workspace_bytes),
+                workspace_bytes_without_recompute=int(ws_keep),
                 config=dict(views="752x480x1 window of 8", points_per_keyframe=20_000,
                             iterations_per_keyframe=30, recompute=True,
                             cuda_graph="one per keyframe (first iteration eager)",
                             tile=f"{args.tile_w}x{args.tile_h}", smem_batch=args.batch,
                             pixels_per_thread=args.ppt, smem_batch_bwd=args.batch_bwd,
                             pixels_per_thread_bwd=args.ppt_bwd))
+
+
+def run_autograd(args, ws, p, view, target, lam, K):
+    """The headline iteration written as a PyTorch user would: the map's
+    parameter groups as autograd leaves, images = GSRender.apply(...),
+    loss = L1SSIMLoss.apply(...), loss.backward(), the gradients copied into
+    the packed buffer and one Adam step; with the recompute rasteriser
+    (forward keeps only final_T and last_idx, the backward repeats the
+    projection and binning) and with the one that keeps the projection.
+    Eager (no graph), CUDA events around K iterations."""
+    import torch
+    from paper_2409_13055_gb300 import mapping
+
+    gm = mapping.GaussianMap(p)
+    names = ("means", "log_scales", "quats", "opacity_logits", "sh")
+    P, G = gm.params(), gm.grads()
+    leaves = [P[k].detach().requires_grad_(True) for k in names]  # share gm's storage
+    launch = dict(tile=(args.tile_w, args.tile_h), smem_batch=args.batch,
+                  pixels_per_thread=args.ppt, smem_batch_bwd=args.batch_bwd,
+                  pixels_per_thread_bwd=args.ppt_bwd)
+    out = {}
+    stream = torch.cuda.current_stream()
+    for rec in (False, True):
+        rast = mapping.fit_instance_capacity([view], gm, recompute=rec, **launch)
+        tgt = target.reshape(-1)
+
+        def iteration():
+            for leaf in leaves:
+                leaf.grad = None
+            img = mapping.GSRender.apply(*leaves, rast)
+            loss = mapping.L1SSIMLoss.apply(img, tgt, rast, lam)
+            loss.backward()
+            for k, leaf in zip(names, leaves):
+                G[k].copy_(leaf.grad)
+            gm.adam_step()
+
+        for _ in range(max(args.warmup, 3)):
+            iteration()
+        torch.cuda.synchronize()
+        barrier(ws)
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        for _ in range(K):
+            iteration()
+        e1.record(stream)
+        torch.cuda.synchronize()
+        ms = reduce_max(e0.elapsed_time(e1), ws) / K
+        assert rast.counters().status == 0
+        out["recompute_on" if rec else "recompute_off"] = dict(
+            iters_per_s=ws * 1e3 / ms, ms_per_iter=ms, workspace_bytes=int(rast.workspace_bytes))
+        del rast
+    out["config"] = dict(iterations=K, path="GSRender + L1SSIMLoss autograd Functions, "
+                                             "loss.backward(), gradient copy, Adam; eager")
+    return out
 
 
 def run_density(args, ws, p, view, target):
@@ -657,15 +753,15 @@ def run_gpu(args, ws, rank, local):
     pipe.drain()
     barrier(ws)
     torch.cuda.synchronize()
-    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-    e0.record(stream)
+    # host clock around the E submissions and the read of the last loss:
+    # the copies, the host-side submission and the final D2H are all inside
     t_wall = time.perf_counter()
     for _ in range(E):
         pipe.submit(host_tgt, host_views)
-    e1.record(stream)
     last_loss = pipe.drain()
+    t_wall = time.perf_counter() - t_wall
     torch.cuda.synchronize()
-    e2e_ms = reduce_max(e0.elapsed_time(e1), ws) / E
+    e2e_ms = reduce_max(t_wall * 1e3, ws) / E
     h2d = host_tgt.numel() * 4 + host_views.numel()
     assert last_loss is not None and math.isfinite(last_loss)
 
@@ -694,8 +790,9 @@ def run_gpu(args, ws, rank, local):
                     traffic=None, algorithmic=algo_bytes[dominant],
                     peak_source=peaks["source"])
     else:
-        flops = (pairs_bwd * PAIR_FLOPS_BWD) if dominant == "render_bwd" else (pairs_bwd * PAIR_FLOPS_FWD)
-        peak = fp32_peak_tflops(peaks["sm_max_mhz"])
+        per_pair = PAIR_FLOPS_BWD if dominant == "render_bwd" else PAIR_FLOPS_FWD
+        flops = pairs_bwd * per_pair
+        peak = fp32_peak_tflops(peaks["sm_max_mhz"], peaks["sms"])
         achieved = flops / (stage_ms[dominant] * 1e-3) / 1e12
         traffic = None
         if dominant == "render_bwd" and args.map_order == "zorder" and not args.deterministic:
@@ -704,7 +801,9 @@ def run_gpu(args, ws, rank, local):
                                               "square" if args.square_rects else "tight"))
         roof = dict(bound="alu", kernel=dominant, achieved=achieved, peak=peak, unit="TFLOP/s",
                     frac=achieved / peak, traffic=traffic, algorithmic=flops,
-                    peak_source="152 SMs x 128 FP32 lanes x 2 x sm_max_mhz (%s)" % peaks["source"])
+                    flops_per_pair=per_pair, pairs=pairs_bwd,
+                    peak_source="%d SMs (device) x 128 FP32 lanes x 2 x sm_max_mhz (%s)" % (
+                        peaks["sms"], peaks["source"]))
 
     # project 1, bin_sort 18 + 3 per tile-id pass, render_fwd 1, loss 2,
     # render_bwd 1, then the projection adjoint (one kernel for one view) +
@@ -728,7 +827,13 @@ def run_gpu(args, ws, rank, local):
                            deterministic=bool(args.deterministic),
                            tile_rects="square" if args.square_rects else "tight",
                            l2="working set ~1.2 GB > 129 MB L2, no flush",
-                           instances=instances, pairs_bwd=pairs_bwd),
+                           instances=instances, pairs_bwd=pairs_bwd,
+                           workspace_bytes=int(rast.workspace_bytes),
+                           workspace_bytes_recompute=int(mapping.plan_workspace_bytes(
+                               [view], gm.n, rast.instance_capacity, recompute=True,
+                               tile=(args.tile_w, args.tile_h), smem_batch=args.batch,
+                               pixels_per_thread=args.ppt, smem_batch_bwd=args.batch_bwd,
+                               pixels_per_thread_bwd=args.ppt_bwd))),
                stages_ms=stage_ms, roofline=roof,
                iteration_roofline=iteration_roofline(
                    n, gm.degree, 1, rast.total_values, view["width"] * view["height"], instances,
@@ -749,6 +854,9 @@ def run_gpu(args, ws, rank, local):
     if args.streaming_kfs > 0:
         torch.cuda.empty_cache()
         out["streaming"] = run_streaming(args, ws)
+    if not args.no_autograd:
+        torch.cuda.empty_cache()
+        out["autograd"] = run_autograd(args, ws, p, view, target, lam, max(1, min(K, 100)))
     if not args.no_density:
         torch.cuda.empty_cache()
         out["density_control"] = run_density(args, ws, p, view, target)
@@ -760,10 +868,16 @@ def run_gpu(args, ws, rank, local):
 
     if rank == 0 and not args.no_cpu_baseline:
         from paper_2409_13055_gb300 import scenes as sc
-        t = oracle_iteration_seconds(p, view, sc.random_target(view, sc.SEED_BASE + 13), lam)
-        out["cpu_baseline"] = dict(value=1.0 / t, unit="iters/s", cores=1, kind="oracle",
+        tgt = sc.random_target(view, sc.SEED_BASE + 13)
+        tile = (args.tile_w, args.tile_h)
+        cores = host_cores()
+        t_all = oracle_iteration_seconds(p, view, tgt, lam, tile, threads=cores)
+        t_one = oracle_iteration_seconds(p, view, tgt, lam, tile, threads=1)
+        out["cpu_baseline"] = dict(value=1.0 / t_all, unit="iters/s", cores=cores, kind="oracle",
                                    sample="one full FP64 mapping iteration of the workload "
-                                          "(target: seeded noise image), single thread")
+                                          "(target: seeded noise image) at the GPU arm's tile "
+                                          "shape, OpenMP on every host core of the process",
+                                   one_core=dict(value=1.0 / t_one, unit="iters/s", cores=1))
     if rank == 0:
         print(json.dumps(out), flush=True)
     if ws > 1:
@@ -808,6 +922,8 @@ def main():
                     help="skip the Gaussian-pyramid level measurement")
     ap.add_argument("--no-density", action="store_true",
                     help="skip the adaptive density control measurement")
+    ap.add_argument("--no-autograd", action="store_true",
+                    help="skip the autograd-Function iterations (recompute on and off)")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--reference-warmup", action="store_true")
     args = ap.parse_args()
@@ -815,8 +931,8 @@ def main():
         args.warmup = 3
     ws, rank, local = dist_setup()
     if args.impl == "reference":
-        if args.steps > 3:
-            args.steps = 3  # each oracle step is a full FP64 iteration (~15-30 s)
+        if args.steps > 10:
+            args.steps = 10  # each oracle step is a full FP64 iteration (~1-2 s on 16 cores)
         run_reference(args, ws, rank)
         return
     run_gpu(args, ws, rank, local)

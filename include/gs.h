@@ -126,9 +126,20 @@ typedef struct {
  *     (GS_DEV_SPAN_POOL if it runs out).  Only (Gaussian, tile) pairs that
  *     every pixel would skip are dropped: images and gradients are
  *     unchanged, the instance lists (and so last_idx) shorter.
+ *   recompute: nonzero makes a recompute (checkpointing) plan: the
+ *     workspace holds the projection and binning of ONE view, and nothing of
+ *     them is kept from the forward to the backward -- only the images,
+ *     final_T and last_idx, which the caller owns.  Views go through it one
+ *     pass at a time (gs_plan_view_pass); the backward of a view re-runs its
+ *     gs_project and gs_bin_sort (deterministic: the same buffers bit for
+ *     bit) before gs_render_bwd*.  The SSIM maps of gs_loss_l1_ssim share
+ *     their bytes with that region, so the loss overwrites it.
+ *     instance_capacity is then the capacity of one view.  Against a plan
+ *     holding all V views, the workspace shrinks by about (V - 1) x (200 B
+ *     per Gaussian + 16 B per instance of a view) plus the loss maps.
  * The tile shape changes which pixels a Gaussian can reach (its 3-sigma
  * rect is counted in whole tiles), hence the image; the batch sizes, pixels
- * per thread and tight_rect change only the speed. */
+ * per thread, tight_rect and recompute change only the speed and memory. */
 typedef struct {
     int32_t tile_w, tile_h, smem_batch, pixels_per_thread;
     int32_t smem_batch_bwd, pixels_per_thread_bwd;
@@ -137,6 +148,7 @@ typedef struct {
     int32_t density_stats;
     int32_t deterministic;
     int32_t tight_rect;
+    int32_t recompute;
 } gs_config;
 
 /* A plan: the sizes, tile grids and workspace layout of one batch of views.
@@ -165,6 +177,24 @@ gs_status gs_plan_init(gs_plan *plan, const gs_config *cfg, int32_t n_views,
 
 /* Bytes of device workspace the plan needs (256-byte aligned base). */
 size_t gs_plan_workspace_bytes(const gs_plan *plan);
+
+/* Recompute plans (gs_config.recompute; the benchmark spec's recompute-from-saved-
+ * transmittance mode, no paper counterpart): fills *pass with the plan of
+ * the single view v of `plan`, sharing its workspace layout.  The per-view
+ * calls -- gs_project, gs_bin_sort, gs_render_fwd, gs_render_bwd,
+ * gs_render_bwd_pixels, gs_project_bwd, gs_densify_stats -- take pass plans
+ * (a recompute plan of one view is its own pass): they read the pose
+ * views_dev[v] of the same views_dev array and write the images, final_T,
+ * last_idx and dL of view v at its offsets in the packed buffers.
+ * gs_loss_l1_ssim takes the whole plan.  Parameter gradients accumulate over
+ * passes with accumulate = 1.  The device status word is reset by the
+ * gs_project of view 0 only, so it gathers the bits of all passes; the
+ * instance count (gs_read_counters) is that of the last pass.  The calls
+ * that need every view at once (gs_project_bwd_groups, gs_project_bwd_adam,
+ * gs_visibility) accept a recompute plan only when it has one view.
+ * GS_ERR_INVALID if plan is not a recompute plan made by gs_plan_init or v
+ * is out of range; pass may be plan itself. */
+gs_status gs_plan_view_pass(const gs_plan *plan, int32_t v, gs_plan *pass);
 
 /* Offsets of view v inside packed images (values: channels*H*W units) and
  * per-pixel maps (pixels: H*W units), its first global tile id and grid. */
@@ -265,19 +295,22 @@ gs_status gs_render_bwd(const gs_plan *plan, const gs_map *map, const gs_view *v
  * Same arguments, arithmetic and results as gs_loss_l1_ssim, minus ws: its
  * scratch (SSIM partial maps, per-block loss partials, a reduction ticket) is
  * a fixed array compiled into the library, about 12.6 MB, which every GPU
- * that loads the library holds until the process exits.  Limits: the plan's
- * images may hold at most 2^20 values in total (sum of C*H*W; e.g. one
- * 640x480 RGB view) and at most 8192 loss tiles of 32x16; larger plans are
- * rejected with GS_ERR_CAPACITY before anything is enqueued.  Nothing is
- * allocated, by this call or any library routine it uses.
+ * that has loaded the library's device code holds until the process exits.
+ * Limits: the plan's images may hold at most 2^20 values in total (sum of
+ * C*H*W; e.g. one 640x480 RGB view) and at most 8192 loss tiles of 32x16;
+ * larger plans are rejected with GS_ERR_CAPACITY before anything is
+ * enqueued.
  *
- * The first call on a device looks up the array's device address
- * (cudaGetSymbolAddress, with that device current) and caches it; make that
- * first call before any stream capture.  All calls share the one array and
- * it keeps the last call's contents (the ticket is cleared at the start of
- * every call): calls that overlap on the GPU -- on different streams, or from
- * several threads -- race on the scratch and corrupt each other's results;
- * order them on one stream. */
+ * Every call looks up the array's device address on the current device
+ * (cudaGetSymbolAddress, a host-side lookup), so no address outlives a device
+ * reset.  The first call on each device may load the library's device code
+ * and with it reserve the array: make that first call before any stream
+ * capture and before the caller's memory budget starts.  Apart from that
+ * loading, nothing is allocated, by this call or any library routine it
+ * uses.  All calls share the one array and it keeps the last call's contents
+ * (the ticket is cleared at the start of every call): calls that overlap on
+ * the GPU -- on different streams, or from several threads -- race on the
+ * scratch and corrupt each other's results; order them on one stream. */
 gs_status gs_loss_l1_ssim_noalloc(const gs_plan *plan, const float *images, const float *targets,
                                   float lambda, float view_weight, float *loss_dev,
                                   float *dL_dimages, void *stream);

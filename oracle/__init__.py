@@ -44,13 +44,14 @@ TIGHT_RECT = True
 
 
 def build(force: bool = False) -> str:
-    """Compile gs_oracle.c into libgs_oracle.so next to it (gcc, -O2, strict FP64)."""
+    """Compile gs_oracle.c into libgs_oracle.so next to it (gcc, -O2, strict
+    FP64, OpenMP for the optional multi-threaded loops)."""
     if (not force and os.path.exists(_LIB_PATH)
             and os.path.getmtime(_LIB_PATH) >= os.path.getmtime(_SRC)):
         return _LIB_PATH
     tmp = _LIB_PATH + f".tmp{os.getpid()}"
     cmd = ["gcc", "-O2", "-std=c11", "-fPIC", "-shared", "-ffp-contract=off",
-           "-fno-fast-math", "-o", tmp, _SRC, "-lm"]
+           "-fno-fast-math", "-fopenmp", "-o", tmp, _SRC, "-lm"]
     subprocess.run(cmd, check=True)
     os.replace(tmp, _LIB_PATH)
     return _LIB_PATH
@@ -66,8 +67,15 @@ def _L():
             lib.oracle_bin.restype = ctypes.c_int64
             lib.oracle_bin_spans.restype = ctypes.c_int64
             lib.oracle_loss_l1_ssim.restype = ctypes.c_double
+            lib.oracle_set_threads(ctypes.c_int(1))
             _lib = lib
     return _lib
+
+
+def set_threads(k: int) -> None:
+    """Host threads of the oracle's parallel loops (default 1; the tests use
+    one thread, the benchmark's all-core CPU baseline more)."""
+    _L().oracle_set_threads(ctypes.c_int(int(k)))
 
 
 def _p(a):

@@ -29,11 +29,29 @@
  *   sh[K][n][3] with K = (degree+1)^2 (coefficient-major), camera
  *   cam[16] = R[9] (world->camera, row-major), t[3], fx, fy, cx, cy.
  *   Images are planar [channels][H][W]; per-pixel maps are [H][W].
+ *
+ * Threads: oracle_set_threads(k) lets the loops over independent Gaussians,
+ * pixel rows and parameters run on k host threads (OpenMP).  The default is
+ * one thread, which the tests use; with more, only the order in which the
+ * adjoint's per-pixel terms are added into a Gaussian's gradient (and the
+ * loss's per-row sums) can change, i.e. the last bits of the result.
  */
 #include <math.h>
 #include <stdint.h>
 #include <stdlib.h>
 #include <string.h>
+#ifdef _OPENMP
+#include <omp.h>
+#endif
+
+/* Host threads of the parallel loops (1 unless set). */
+void oracle_set_threads(int k) {
+#ifdef _OPENMP
+    omp_set_num_threads(k > 0 ? k : 1);
+#else
+    (void)k;
+#endif
+}
 
 /* ------------------------------------------------------------------------ */
 /* Readings of points where the paper is silent.                            */
@@ -540,6 +558,7 @@ int oracle_project(int n, int degree, const double *means, const double *log_sca
                    int *guard, int tight) {
     const int tiles_x = (W + tile_w - 1) / tile_w, tiles_y = (H + tile_h - 1) / tile_h;
     int nvis = 0;
+#pragma omp parallel for schedule(dynamic, 4096) reduction(+ : nvis)
     for (int i = 0; i < n; i++) {
         proj_t P;
         int g = 0;
@@ -736,7 +755,10 @@ static int composite_pixel(const int32_t *ids, int64_t len, double px, double py
         if (fabs(power) < OR_G_POWER) gb |= OR_GPX_POWER;
         if (power > 0.0) {
             *gpx |= gb;
-            if (gguard) gguard[g] |= gb;
+            if (gguard && gb) {
+#pragma omp atomic update
+                gguard[g] |= gb;
+            }
             continue;
         }
         double G = exp(power);
@@ -747,7 +769,10 @@ static int composite_pixel(const int32_t *ids, int64_t len, double px, double py
         double Tn = T * (1.0 - alpha);
         if (alpha >= OR_ALPHA_MIN && fabs(Tn / OR_T_MIN - 1.0) < OR_G_TRANS) gb |= OR_GPX_TRANS;
         *gpx |= gb;
-        if (gguard) gguard[g] |= gb;
+        if (gguard && gb) {
+#pragma omp atomic update
+            gguard[g] |= gb;
+        }
         if (alpha < OR_ALPHA_MIN) continue;
         if (Tn < OR_T_MIN) { j++; break; }
         cs[nc].idx = g;
@@ -788,7 +813,10 @@ void oracle_render(int n, const double *mean2d, const double *conic, const doubl
     int64_t T_tiles = (int64_t)tiles_x * ((H + tile_h - 1) / tile_h);
     for (int64_t t = 0; t < T_tiles; t++)
         if (tile_start[t + 1] - tile_start[t] > maxlen) maxlen = tile_start[t + 1] - tile_start[t];
+#pragma omp parallel
+    {
     contrib_t *cs = (contrib_t *)malloc(sizeof(contrib_t) * (size_t)(maxlen + 1));
+#pragma omp for schedule(dynamic, 1)
     for (int py = 0; py < H; py++)
         for (int px = 0; px < W; px++) {
             int64_t t = (int64_t)(py / tile_h) * tiles_x + px / tile_w;
@@ -815,6 +843,7 @@ void oracle_render(int n, const double *mean2d, const double *conic, const doubl
             guard_px[p] = gp;
         }
     free(cs);
+    }
 }
 
 /* Sort helper for the brute-force renderer: (depth key, index). */
@@ -908,7 +937,10 @@ void oracle_render_bwd(int n, const double *mean2d, const double *conic, const d
     int64_t T_tiles = (int64_t)tiles_x * ((H + tile_h - 1) / tile_h);
     for (int64_t t = 0; t < T_tiles; t++)
         if (tile_start[t + 1] - tile_start[t] > maxlen) maxlen = tile_start[t + 1] - tile_start[t];
+#pragma omp parallel
+    {
     contrib_t *cs = (contrib_t *)malloc(sizeof(contrib_t) * (size_t)(maxlen + 1));
+#pragma omp for schedule(dynamic, 1)
     for (int py = 0; py < H; py++)
         for (int px = 0; px < W; px++) {
             int64_t t = (int64_t)(py / tile_h) * tiles_x + px / tile_w;
@@ -931,35 +963,47 @@ void oracle_render_bwd(int n, const double *mean2d, const double *conic, const d
                 const double *c = rgb + 3 * gi;
                 double al = cs[k].alpha, Ti = cs[k].T;
                 double dal = 0.0;
+                /* (the adds into a Gaussian's gradient are atomic only so
+                 * that several threads may run; one thread adds in order) */
                 for (int ch = 0; ch < 3; ch++) {
+#pragma omp atomic update
                     drgb[3 * gi + ch] += al * Ti * g[ch];
                     dal += g[ch] * (Ti * c[ch] - S[ch] / (1.0 - al));
                 }
                 for (int ch = 0; ch < 3; ch++) S[ch] += al * Ti * c[ch];
                 if (cs[k].clamped) continue;
                 double o = opacity[gi];
+#pragma omp atomic update
                 dopacity[gi] += cs[k].G * dal;
                 double dpow = o * cs[k].G * dal;
                 double a = conic[3 * gi], b = conic[3 * gi + 1], cc = conic[3 * gi + 2];
                 double dx = cs[k].dx, dy = cs[k].dy;
                 const double gx = dpow * (-(a * dx + b * dy));
                 const double gy = dpow * (-(b * dx + cc * dy));
+#pragma omp atomic update
                 dmean2d[2 * gi] += gx;
+#pragma omp atomic update
                 dmean2d[2 * gi + 1] += gy;
                 /* Homodirectional view-space gradient (AbsGS, the density
                  * control of paper Sec. III-B): the per-pixel contributions
                  * summed by absolute value, component by component, so that
                  * contributions of opposite sign do not cancel. */
                 if (dmean2d_abs) {
+#pragma omp atomic update
                     dmean2d_abs[2 * gi] += fabs(gx);
+#pragma omp atomic update
                     dmean2d_abs[2 * gi + 1] += fabs(gy);
                 }
+#pragma omp atomic update
                 dconic[3 * gi] += dpow * (-0.5 * dx * dx);
+#pragma omp atomic update
                 dconic[3 * gi + 1] += dpow * (-dx * dy);
+#pragma omp atomic update
                 dconic[3 * gi + 2] += dpow * (-0.5 * dy * dy);
             }
         }
     free(cs);
+    }
 }
 
 /*
@@ -979,6 +1023,7 @@ void oracle_project_bwd(int n, int degree, const double *means, const double *lo
     const double fx = cam[12], fy = cam[13];
     const int tiles_x = (W + tile_w - 1) / tile_w, tiles_y = (H + tile_h - 1) / tile_h;
     const int K = (degree + 1) * (degree + 1);
+#pragma omp parallel for schedule(dynamic, 4096)
     for (int i = 0; i < n; i++) {
         proj_t P;
         int gd;
@@ -1150,9 +1195,12 @@ double oracle_loss_l1_ssim(const double *img, const double *tgt, int channels, i
     double *dm = (double *)calloc(HW, sizeof(double));
     double *dxx = (double *)calloc(HW, sizeof(double));
     double *dxy = (double *)calloc(HW, sizeof(double));
+    double *rows = (double *)calloc((size_t)H, sizeof(double)); /* SSIM sum per row */
     for (int ch = 0; ch < channels; ch++) {
         const double *x = img + ch * HW, *y = tgt + ch * HW;
-        for (int i = 0; i < H; i++)
+#pragma omp parallel for schedule(dynamic, 1)
+        for (int i = 0; i < H; i++) {
+            rows[i] = 0.0;
             for (int j = 0; j < W; j++) {
                 double mx = 0, my = 0, sxx = 0, syy = 0, sxy = 0;
                 for (int a = -5; a <= 5; a++)
@@ -1171,7 +1219,7 @@ double oracle_loss_l1_ssim(const double *img, const double *tgt, int channels, i
                 double A = 2.0 * mx * my + C1, B = 2.0 * cxy + C2;
                 double Cd = mx * mx + my * my + C1, D = vx + vy + C2;
                 double s = A * B / (Cd * D);
-                ssum += s;
+                rows[i] += s;
                 if (ssim_map) ssim_map[ch * HW + (size_t)i * W + j] = s;
                 /* partials with respect to (mx, sxx, sxy), my/syy fixed */
                 double dA_dmx = 2.0 * my;
@@ -1187,9 +1235,12 @@ double oracle_loss_l1_ssim(const double *img, const double *tgt, int channels, i
                 dxx[p] = ds_dsxx;
                 dxy[p] = ds_dsxy;
             }
+        }
+        for (int i = 0; i < H; i++) ssum += rows[i];
         for (size_t p = 0; p < HW; p++) l1 += fabs(x[p] - y[p]);
         if (dimg) {
             /* dSSIM_sum/dx_q = sum_p w(p-q) [dm_p + 2 x_q dxx_p + y_q dxy_p] */
+#pragma omp parallel for schedule(dynamic, 1)
             for (int i = 0; i < H; i++)
                 for (int j = 0; j < W; j++) {
                     double acc_m = 0, acc_xx = 0, acc_xy = 0;
@@ -1214,6 +1265,7 @@ double oracle_loss_l1_ssim(const double *img, const double *tgt, int channels, i
     free(dm);
     free(dxx);
     free(dxy);
+    free(rows);
     return (1.0 - lambda) * l1 / M + lambda * (1.0 - ssum / M);
 }
 
@@ -1226,6 +1278,7 @@ double oracle_loss_l1_ssim(const double *img, const double *tgt, int channels, i
 void oracle_adam(int64_t n, double *p, const double *g, double *m, double *v, double lr,
                  double b1, double b2, double eps, int t) {
     double bc1 = 1.0 - pow(b1, t), bc2 = 1.0 - pow(b2, t);
+#pragma omp parallel for schedule(static)
     for (int64_t i = 0; i < n; i++) {
         m[i] = b1 * m[i] + (1.0 - b1) * g[i];
         v[i] = b2 * v[i] + (1.0 - b2) * g[i] * g[i];

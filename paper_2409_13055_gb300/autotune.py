@@ -25,7 +25,7 @@ import torch
 from . import mapping
 
 TILES = ((8, 8), (16, 16), (32, 8))
-BATCHES = (32, 64, 128)
+BATCHES = (32, 64, 128, 256)
 PPTS = (1, 2, 4, 8)
 
 

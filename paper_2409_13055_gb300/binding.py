@@ -19,7 +19,7 @@ c_int32, c_int64, c_float, c_void_p, c_size_t = (ctypes.c_int32, ctypes.c_int64,
 
 GS_OK, GS_ERR_INVALID, GS_ERR_CUDA, GS_ERR_CAPACITY, GS_ERR_UNSUPPORTED, GS_ERR_TIMEOUT = \
     0, -1, -2, -3, -4, -5
-GS_DEV_CAPACITY, GS_DEV_NONFINITE = 1, 2
+GS_DEV_CAPACITY, GS_DEV_NONFINITE, GS_DEV_SPAN_POOL = 1, 2, 4
 GS_MAX_VIEWS, GS_MAX_GROUPS, GS_PLAN_WORDS = 64, 8, 1536
 (GS_BUF_COUNTERS, GS_BUF_PROJ, GS_BUF_RECT, GS_BUF_TOUCHED, GS_BUF_RADIUS, GS_BUF_DEPTH_ORDER,
  GS_BUF_TILE_KEYS, GS_BUF_TILE_VALUES, GS_BUF_RANGES, GS_BUF_GRAD2D, GS_BUF_ABSGRAD) = range(11)
@@ -47,7 +47,7 @@ class gs_config(ctypes.Structure):
                 ("pixels_per_thread", c_int32), ("smem_batch_bwd", c_int32),
                 ("pixels_per_thread_bwd", c_int32), ("near_z", c_float), ("bg", c_float * 3),
                 ("density_stats", c_int32), ("deterministic", c_int32),
-                ("tight_rect", c_int32)]
+                ("tight_rect", c_int32), ("recompute", c_int32)]
 
 
 class gs_densify_config(ctypes.Structure):
@@ -71,6 +71,7 @@ _SIGNATURES = {
     "gs_plan_init": (c_int32, [_P(gs_plan), _P(gs_config), c_int32, _P(gs_view), c_int32,
                                c_int64]),
     "gs_plan_workspace_bytes": (c_size_t, [_P(gs_plan)]),
+    "gs_plan_view_pass": (c_int32, [_P(gs_plan), c_int32, _P(gs_plan)]),
     "gs_plan_view": (c_int32, [_P(gs_plan), c_int32, _P(c_int64), _P(c_int64), _P(c_int32),
                                _P(c_int32), _P(c_int32)]),
     "gs_plan_totals": (c_int32, [_P(gs_plan), _P(c_int64), _P(c_int64), _P(c_int32)]),
@@ -185,6 +186,14 @@ def gs_plan_init(cfg: gs_config, views_host, n_capacity: int, instance_capacity:
 
 def gs_plan_workspace_bytes(plan) -> int:
     return int(lib().gs_plan_workspace_bytes(ctypes.byref(plan)))
+
+
+def gs_plan_view_pass(plan, v) -> gs_plan:
+    """The one-view pass plan of view v of a recompute plan."""
+    out = gs_plan()
+    check(lib().gs_plan_view_pass(ctypes.byref(plan), int(v), ctypes.byref(out)),
+          "gs_plan_view_pass")
+    return out
 
 
 def gs_plan_view(plan, v):

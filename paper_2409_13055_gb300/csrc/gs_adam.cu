@@ -2,7 +2,7 @@
 //
 // One fused, HBM-bound pass over every parameter group: 16 bytes read
 // (p, g, m, v) and 12 written (p, m, v) per float, float4-vectorised, grid
-// sized to a multiple of the 152 SMs and striding over the buffer; the
+// sized to a multiple of the GPU's SM count and striding over the buffer; the
 // gradient is read with a streaming hint (used once).  At most 2^31 - 1
 // floats per call.  The step
 // counter lives on the device and is advanced by a one-thread kernel first,
@@ -15,7 +15,7 @@ namespace gs {
 namespace {
 
 constexpr int kAdamThreads = 256;
-constexpr int kAdamBlocks = 152 * 8;
+constexpr int kAdamBlocksPerSm = 8;
 
 struct Groups {
     uint32_t off[GS_MAX_GROUPS + 1];  // element offsets (n < 2^31)
@@ -314,7 +314,9 @@ gs_status launch_adam_sparse(float* params, const float* grads, float* m, float*
     // a float4 per thread; enough CTAs along x to cover the largest plane
     // (4 n_gauss floats) with a few loop trips
     int bx = (int)((4LL * n_gauss + 4LL * kAdamThreads - 1) / (4LL * kAdamThreads));
-    if (bx > 152 * 4) bx = 152 * 4;
+    const int sms = sm_count();
+    if (sms <= 0) return GS_ERR_CUDA;
+    if (bx > sms * 4) bx = sms * 4;
     if (bx < 1) bx = 1;
     k_step_inc<<<1, 1, 0, st>>>(step_dev);
     k_adam_sparse<<<dim3(bx, pl.count), kAdamThreads, 0, st>>>(params, grads, m, v, pl,
@@ -345,9 +347,11 @@ gs_status launch_adam_groups(float* params, const float* grads, float* m, float*
         }
     }
     if (pl.count == 0) return GS_ERR_INVALID;
+    const int sms = sm_count();
+    if (sms <= 0) return GS_ERR_CUDA;
     k_step_inc<<<1, 1, 0, st>>>(step_dev);
     auto* kern = vec ? k_adam_groups<true> : k_adam_groups<false>;
-    kern<<<kAdamBlocks, kAdamThreads, 0, st>>>(params, grads, m, v, pl, (uint32_t)n_gauss,
+    kern<<<sms * kAdamBlocksPerSm, kAdamThreads, 0, st>>>(params, grads, m, v, pl, (uint32_t)n_gauss,
                                                group_vis, b1, b2, eps, step_dev);
     return launch_status();
 }
@@ -370,7 +374,9 @@ gs_status launch_adam(float* params, const float* grads, float* m, float* v, int
                           15) == 0;
     long long work = aligned ? (n >> 2) : n;
     int blocks = (int)((work + kAdamThreads - 1) / kAdamThreads);
-    if (blocks > kAdamBlocks) blocks = kAdamBlocks;
+    const int sms = sm_count();
+    if (sms <= 0) return GS_ERR_CUDA;
+    if (blocks > sms * kAdamBlocksPerSm) blocks = sms * kAdamBlocksPerSm;
     if (blocks < 1) blocks = 1;
     k_step_inc<<<1, 1, 0, st>>>(step_dev);
     k_adam<<<blocks, kAdamThreads, 0, st>>>(params, grads, m, v, n, g, b1, b2, eps, step_dev,

@@ -2,9 +2,27 @@
 // checks, counters.  The kernels live in the other translation units.
 #include <string.h>
 
+#include <atomic>
+
 #include "gs_internal.cuh"
 
 using namespace gs;
+
+int gs::sm_count() {
+    constexpr int kDevices = 64;
+    static std::atomic<int> cache[kDevices];
+    int dev = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess || dev < 0) return 0;
+    if (dev < kDevices) {
+        const int c = cache[dev].load(std::memory_order_relaxed);
+        if (c > 0) return c;
+    }
+    int sms = 0;
+    if (cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess)
+        return 0;
+    if (dev < kDevices && sms > 0) cache[dev].store(sms, std::memory_order_relaxed);
+    return sms > 0 ? sms : 0;
+}
 
 namespace {
 
@@ -59,7 +77,11 @@ extern "C" gs_status gs_plan_init(gs_plan* plan, const gs_config* cfg, int32_t n
     p->vt.log2_tw = l2w;
     p->vt.log2_th = l2h;
     p->vt.tight_rect = cfg->tight_rect != 0;
-    int64_t tiles = 0, pixels = 0, values = 0;
+    p->recompute = cfg->recompute != 0;
+    p->n_views_full = n_views;
+    p->view_index = -1;
+    p->ws_views = p->recompute ? 1 : n_views;
+    int64_t tiles = 0, pixels = 0, values = 0, max_view_tiles = 0;
     for (int v = 0; v < n_views; ++v) {
         const gs_view& vw = views_host[v];
         if (vw.width < 1 || vw.height < 1 || vw.width > 16384 || vw.height > 16384)
@@ -75,6 +97,8 @@ extern "C" gs_status gs_plan_init(gs_plan* plan, const gs_config* cfg, int32_t n
         g.pixel_offset = pixels;
         g.value_offset = values;
         tiles += (int64_t)g.tiles_x * g.tiles_y;
+        if ((int64_t)g.tiles_x * g.tiles_y > max_view_tiles)
+            max_view_tiles = (int64_t)g.tiles_x * g.tiles_y;
         pixels += (int64_t)vw.width * vw.height;
         values += (int64_t)vw.width * vw.height * vw.channels;
     }
@@ -82,12 +106,16 @@ extern "C" gs_status gs_plan_init(gs_plan* plan, const gs_config* cfg, int32_t n
     p->total_tiles = (int32_t)tiles;
     p->total_pixels = pixels;
     p->total_values = values;
+    // tiles binned per call: all views', or one view's in a recompute plan
+    const int64_t bin_tiles = p->recompute ? max_view_tiles : tiles;
     int bits = 0;
-    while ((int64_t(1) << bits) < tiles) ++bits;
+    while ((int64_t(1) << bits) < bin_tiles) ++bits;
     p->tile_bits = bits < 1 ? 1 : bits;
     p->tile_passes = (p->tile_bits + kRadixBits - 1) / kRadixBits;
 
-    const int64_t VN = (int64_t)n_views * n_capacity;
+    // (view, Gaussian) pairs the workspace holds: all views', or one view's
+    // in a recompute plan (views then go through it one pass at a time)
+    const int64_t VN = (int64_t)p->ws_views * n_capacity;
     p->depth_sort_blocks = (int32_t)((VN + kSortTile - 1) / kSortTile);
     p->inst_sort_blocks = (int32_t)((instance_capacity + kSortTile - 1) / kSortTile);
     p->scan_blocks = (int32_t)((VN + kScanTile - 1) / kScanTile);
@@ -109,7 +137,7 @@ extern "C" gs_status gs_plan_init(gs_plan* plan, const gs_config* cfg, int32_t n
     len[GS_BUF_DEPTH_ORDER] = (size_t)VN * sizeof(uint32_t);
     len[GS_BUF_TILE_KEYS] = (size_t)instance_capacity * sizeof(uint32_t);
     len[GS_BUF_TILE_VALUES] = (size_t)instance_capacity * sizeof(uint32_t);
-    len[GS_BUF_RANGES] = (size_t)tiles * 2 * sizeof(uint32_t);
+    len[GS_BUF_RANGES] = (size_t)bin_tiles * 2 * sizeof(uint32_t);
     len[GS_BUF_GRAD2D] = (size_t)VN * kGrad2d * sizeof(float);
     len[GS_BUF_ABSGRAD] = cfg->density_stats ? (size_t)VN * 2 * sizeof(float) : 0;
     len[B_DKEY_A] = (size_t)VN * sizeof(uint32_t);
@@ -128,7 +156,7 @@ extern "C" gs_status gs_plan_init(gs_plan* plan, const gs_config* cfg, int32_t n
     len[B_LOSS_BLOCKS] = (size_t)(p->loss_blocks + 1) * 2 * sizeof(float);
     len[B_GCOL] = (size_t)VN * 3 * sizeof(float);
     len[B_OFFSETS] = (size_t)(VN + 1) * sizeof(uint32_t);
-    len[B_TILE_ORDER] = (size_t)tiles * sizeof(uint32_t);
+    len[B_TILE_ORDER] = (size_t)bin_tiles * sizeof(uint32_t);
     len[B_TILE_QUEUE] = 2 * sizeof(uint32_t);
     len[B_SPANS] = cfg->tight_rect ? (size_t)VN * kSpanRows * sizeof(uint32_t) : 0;
     // boxes of more than kSpanRows tile rows are rare (4 of 446k visible
@@ -142,14 +170,59 @@ extern "C" gs_status gs_plan_init(gs_plan* plan, const gs_config* cfg, int32_t n
     len[B_SPAN_POOL] = (size_t)p->span_pool_rows * sizeof(uint32_t);
     len[B_GID_OF] = cfg->deterministic ? (size_t)instance_capacity * sizeof(uint32_t) : 0;
     len[B_PARTIAL] = cfg->deterministic ? (size_t)instance_capacity * 11 * sizeof(float) : 0;
+    // Layout.  A recompute plan keeps nothing of the projection and binning
+    // from the forward to the backward (both are run again per view), so
+    // the SSIM maps of the loss, which live only inside gs_loss_l1_ssim,
+    // share their bytes with that region.
+    auto persistent = [](int b) {
+        return b == GS_BUF_COUNTERS || b == B_LOSS_BLOCKS || b == B_TILE_QUEUE ||
+               b == B_LOSS_MAPS;
+    };
     size_t off = 0;
     for (int b = 0; b < B_TOTAL; ++b) {
+        if (!persistent(b)) continue;
+        if (b == B_LOSS_MAPS && p->recompute) continue;
         p->off[b] = off;
         p->len[b] = len[b];
         off = align256(off + len[b]);
     }
+    const size_t transient0 = off;
+    for (int b = 0; b < B_TOTAL; ++b) {
+        if (persistent(b)) continue;
+        p->off[b] = off;
+        p->len[b] = len[b];
+        off = align256(off + len[b]);
+    }
+    if (p->recompute) {
+        p->off[B_LOSS_MAPS] = transient0;
+        p->len[B_LOSS_MAPS] = len[B_LOSS_MAPS];
+        const size_t maps_end = align256(transient0 + len[B_LOSS_MAPS]);
+        if (maps_end > off) off = maps_end;
+    }
     p->ws_bytes = off;
     p->magic = kPlanMagic;
+    return GS_OK;
+}
+
+extern "C" gs_status gs_plan_view_pass(const gs_plan* plan, int32_t v, gs_plan* pass) {
+    if (!plan_ok(plan) || !pass) return GS_ERR_INVALID;
+    const Plan* p = P(plan);
+    if (!p->recompute || p->view_index >= 0) return GS_ERR_INVALID;
+    if (v < 0 || v >= p->n_views_full) return GS_ERR_INVALID;
+    if (pass != plan) memcpy(pass, plan, sizeof(*plan));
+    Plan* q = reinterpret_cast<Plan*>(pass);
+    const ViewGeom g = p->vt.v[v];
+    q->vt.n_views = 1;
+    q->vt.v[0] = g;
+    q->vt.v[0].tile_offset = 0;
+    q->vt.v[0].loss_block_offset = 0;
+    q->view_index = v;
+    q->total_tiles = g.tiles_x * g.tiles_y;
+    int bits = 0;
+    while ((int64_t(1) << bits) < q->total_tiles) ++bits;
+    q->tile_bits = bits < 1 ? 1 : bits;
+    q->tile_passes = (q->tile_bits + kRadixBits - 1) / kRadixBits;
+    q->loss_blocks = ((g.width + 31) / 32) * ((g.height + 15) / 16) * g.channels;
     return GS_OK;
 }
 
@@ -195,6 +268,19 @@ extern "C" gs_status gs_plan_buffer(const gs_plan* plan, int32_t id, size_t* off
     return GS_OK;
 }
 
+// The workspace holds the projection of every view of the plan (not so for
+// the whole of a multi-view recompute plan, whose views go through it one
+// pass at a time).
+static bool per_view_ok(const Plan* p) { return p->vt.n_views <= p->ws_views; }
+// ... and the plan covers all views of the workspace's iteration at once.
+static bool all_views_ok(const Plan* p) {
+    return per_view_ok(p) && p->vt.n_views == p->n_views_full;
+}
+// The poses of a pass plan's view: views_dev[view_index] of the caller's array.
+static const gs_view* pass_views(const Plan* p, const gs_view* views_dev) {
+    return views_dev + (p->view_index > 0 ? p->view_index : 0);
+}
+
 static bool map_ok(const Plan* p, const gs_map* m) {
     return m && m->means && m->log_scales && m->quats && m->opacity_logits && m->sh &&
            m->n >= 1 && m->n <= p->n_capacity && m->sh_degree >= 0 && m->sh_degree <= 3;
@@ -203,18 +289,20 @@ static bool map_ok(const Plan* p, const gs_map* m) {
 extern "C" gs_status gs_project(const gs_plan* plan, const gs_map* map, const gs_view* views_dev,
                                 void* ws, void* stream) {
     if (!plan_ok(plan) || !views_dev || !ws) return GS_ERR_INVALID;
-    if (!map_ok(P(plan), map)) return GS_ERR_INVALID;
-    return launch_project(P(plan), map, views_dev, ws, S(stream));
+    if (!map_ok(P(plan), map) || !per_view_ok(P(plan))) return GS_ERR_INVALID;
+    return launch_project(P(plan), map, pass_views(P(plan), views_dev), ws, S(stream));
 }
 
 extern "C" gs_status gs_bin_sort(const gs_plan* plan, int32_t n, void* ws, void* stream) {
     if (!plan_ok(plan) || !ws || n < 1 || n > P(plan)->n_capacity) return GS_ERR_INVALID;
+    if (!per_view_ok(P(plan))) return GS_ERR_INVALID;
     return launch_bin_sort(P(plan), n, ws, S(stream));
 }
 
 extern "C" gs_status gs_render_fwd(const gs_plan* plan, void* ws, float* images,
                                    float* final_T, int32_t* last_idx, void* stream) {
     if (!plan_ok(plan) || !ws || !images || !final_T || !last_idx) return GS_ERR_INVALID;
+    if (!per_view_ok(P(plan))) return GS_ERR_INVALID;
     return launch_render_fwd(P(plan), ws, images, final_T, last_idx, S(stream));
 }
 
@@ -234,18 +322,19 @@ extern "C" gs_status gs_render_bwd(const gs_plan* plan, const gs_map* map,
                                    const gs_map_grad* grads, int32_t accumulate, void* stream) {
     if (!plan_ok(plan) || !views_dev || !ws || !final_T || !last_idx || !dL_dimages || !grads)
         return GS_ERR_INVALID;
-    if (!map_ok(P(plan), map)) return GS_ERR_INVALID;
+    if (!map_ok(P(plan), map) || !per_view_ok(P(plan))) return GS_ERR_INVALID;
     if (!grads->means || !grads->log_scales || !grads->quats || !grads->opacity_logits ||
         !grads->sh)
         return GS_ERR_INVALID;
-    return launch_render_bwd(P(plan), map, views_dev, ws, final_T, last_idx, dL_dimages, grads,
-                             accumulate ? 1 : 0, S(stream));
+    return launch_render_bwd(P(plan), map, pass_views(P(plan), views_dev), ws, final_T, last_idx,
+                             dL_dimages, grads, accumulate ? 1 : 0, S(stream));
 }
 
 extern "C" gs_status gs_render_bwd_pixels(const gs_plan* plan, void* ws, const float* final_T,
                                           const int32_t* last_idx, const float* dL_dimages,
                                           void* stream) {
     if (!plan_ok(plan) || !ws || !final_T || !last_idx || !dL_dimages) return GS_ERR_INVALID;
+    if (!per_view_ok(P(plan))) return GS_ERR_INVALID;
     return launch_render_bwd_pixels(P(plan), ws, final_T, last_idx, dL_dimages, S(stream));
 }
 
@@ -253,12 +342,12 @@ extern "C" gs_status gs_project_bwd(const gs_plan* plan, const gs_map* map,
                                     const gs_view* views_dev, const void* ws,
                                     const gs_map_grad* grads, int32_t accumulate, void* stream) {
     if (!plan_ok(plan) || !views_dev || !ws || !grads) return GS_ERR_INVALID;
-    if (!map_ok(P(plan), map)) return GS_ERR_INVALID;
+    if (!map_ok(P(plan), map) || !per_view_ok(P(plan))) return GS_ERR_INVALID;
     if (!grads->means || !grads->log_scales || !grads->quats || !grads->opacity_logits ||
         !grads->sh)
         return GS_ERR_INVALID;
-    return launch_project_bwd(P(plan), map, views_dev, const_cast<void*>(ws), grads,
-                              accumulate ? 1 : 0, S(stream));
+    return launch_project_bwd(P(plan), map, pass_views(P(plan), views_dev),
+                              const_cast<void*>(ws), grads, accumulate ? 1 : 0, S(stream));
 }
 
 extern "C" gs_status gs_project_bwd_groups(const gs_plan* plan, const gs_map* map,
@@ -266,7 +355,7 @@ extern "C" gs_status gs_project_bwd_groups(const gs_plan* plan, const gs_map* ma
                                            const gs_map_grad* grads, uint8_t* group_vis,
                                            void* stream) {
     if (!plan_ok(plan) || !views_dev || !ws || !grads || !group_vis) return GS_ERR_INVALID;
-    if (!map_ok(P(plan), map)) return GS_ERR_INVALID;
+    if (!map_ok(P(plan), map) || !all_views_ok(P(plan))) return GS_ERR_INVALID;
     if (!grads->means || !grads->log_scales || !grads->quats || !grads->opacity_logits ||
         !grads->sh)
         return GS_ERR_INVALID;
@@ -314,6 +403,7 @@ extern "C" gs_status gs_project_bwd_adam(const gs_plan* plan, const gs_map* map,
     if (!plan_ok(plan) || !views_dev || !ws || !group_lr_host || !step_dev) return GS_ERR_INVALID;
     if (!map_ok(P(plan), map) || !grad_ok(params) || !grad_ok(m) || !grad_ok(v))
         return GS_ERR_INVALID;
+    if (!all_views_ok(P(plan))) return GS_ERR_INVALID;
     if ((grads_acc && !grad_ok(grads_acc)) || (grads_out && !grad_ok(grads_out)))
         return GS_ERR_INVALID;
     if (!(beta1 >= 0.0f && beta1 < 1.0f && beta2 >= 0.0f && beta2 < 1.0f && eps >= 0.0f))
@@ -344,6 +434,7 @@ extern "C" gs_status gs_adam_step(float* params, const float* grads, float* m, f
 extern "C" gs_status gs_visibility(const gs_plan* plan, int32_t n, const void* ws,
                                    uint8_t* vis, void* stream) {
     if (!plan_ok(plan) || !ws || !vis || n < 1 || n > P(plan)->n_capacity) return GS_ERR_INVALID;
+    if (!all_views_ok(P(plan))) return GS_ERR_INVALID;
     return launch_visibility(n, P(plan)->vt.n_views, cbuf<uint32_t>(P(plan), ws, GS_BUF_TOUCHED),
                              vis, S(stream));
 }

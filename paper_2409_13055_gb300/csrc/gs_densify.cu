@@ -232,6 +232,7 @@ extern "C" gs_status gs_densify_stats(const gs_plan* plan, int32_t n, const void
     const Plan* p = reinterpret_cast<const Plan*>(plan);
     if (!plan || p->magic != kPlanMagic || !ws || !accum || !denom) return GS_ERR_INVALID;
     if (n < 1 || n > p->n_capacity || !p->cfg.density_stats) return GS_ERR_INVALID;
+    if (p->vt.n_views > p->ws_views) return GS_ERR_INVALID;  // a pass of a recompute plan
     k_densify_stats<<<(n + kDensThreads - 1) / kDensThreads, kDensThreads, 0,
                       (cudaStream_t)stream>>>(n, p->vt, cbuf<uint32_t>(p, ws, GS_BUF_TOUCHED),
                                               cbuf<float>(p, ws, GS_BUF_ABSGRAD), accum, denom);

@@ -5,6 +5,7 @@
 #pragma once
 
 #include <cuda_runtime.h>
+#include <stddef.h>
 #include <stdint.h>
 
 #include <utility>
@@ -78,6 +79,11 @@ struct Plan {
     int64_t total_pixels, total_values;
     int32_t depth_sort_blocks, inst_sort_blocks, scan_blocks, loss_blocks;
     uint32_t span_pool_rows;  // capacity of B_SPAN_POOL (tight plans)
+    // Recompute plans (gs_config.recompute): the workspace holds one view's
+    // projection and binning (ws_views = 1); the plan itself covers all
+    // n_views_full views, a pass plan (gs_plan_view_pass) the view
+    // view_index (-1 in a plan made by gs_plan_init) with the same layout.
+    int32_t recompute, ws_views, n_views_full, view_index;
     size_t ws_bytes;
     size_t off[B_TOTAL];
     size_t len[B_TOTAL];
@@ -97,6 +103,8 @@ struct DevCounters {
     uint32_t span_pool_used;       // rows of B_SPAN_POOL taken by the last gs_project
 };
 
+static_assert(offsetof(DevCounters, status) == 0, "gs_project keeps the leading status word");
+
 inline const Plan* P(const gs_plan* p) { return reinterpret_cast<const Plan*>(p); }
 
 template <typename T>
@@ -109,6 +117,11 @@ inline const T* cbuf(const Plan* p, const void* ws, int id) {
 }
 
 inline cudaStream_t S(void* s) { return reinterpret_cast<cudaStream_t>(s); }
+
+// Streaming multiprocessors of the current device, queried once per device
+// and cached; 0 if the query fails.  Grid-stride kernels size their grids in
+// multiples of it.
+int sm_count();
 
 inline gs_status launch_status() {
     cudaError_t e = cudaGetLastError();

@@ -18,7 +18,6 @@
 // order by whichever block finishes last (a ticket counter, no waiting).
 #include <math.h>
 
-#include <mutex>
 
 #include "gs_internal.cuh"
 
@@ -341,25 +340,18 @@ constexpr size_t kNoAllocBytes = kNoAllocMapsOffset + 3 * kNoAllocMaxValues * si
 // 12.6 MB, held on every GPU that loads the library until the process exits.
 static __device__ __align__(256) unsigned char g_noalloc_scratch[kNoAllocBytes];
 
-std::mutex g_noalloc_mutex;
-constexpr int kNoAllocMaxDevices = 64;
-void* g_noalloc_addr[kNoAllocMaxDevices] = {nullptr};  // per device ordinal
-
 // Device address of the scratch array on the current device.  In host code
 // the array's name is only a host-side stand-in, so the address is looked up
-// with cudaGetSymbolAddress once per device (the device must be current).
+// with cudaGetSymbolAddress, with the device current.  It is looked up again
+// on every call (a host-side table lookup once the module is loaded): an
+// address kept from an earlier call could outlive its context (a device
+// reset, a context destroyed and created again) and send the kernels to
+// memory that is no longer the array.
 gs_status noalloc_scratch(void** out) {
-    int dev = 0;
-    if (cudaGetDevice(&dev) != cudaSuccess) return GS_ERR_CUDA;
-    if (dev < 0 || dev >= kNoAllocMaxDevices) return GS_ERR_UNSUPPORTED;
-    std::lock_guard<std::mutex> lock(g_noalloc_mutex);
-    if (g_noalloc_addr[dev] == nullptr) {
-        void* p = nullptr;
-        if (cudaGetSymbolAddress(&p, g_noalloc_scratch) != cudaSuccess || p == nullptr)
-            return GS_ERR_CUDA;
-        g_noalloc_addr[dev] = p;
-    }
-    *out = g_noalloc_addr[dev];
+    void* p = nullptr;
+    if (cudaGetSymbolAddress(&p, g_noalloc_scratch) != cudaSuccess || p == nullptr)
+        return GS_ERR_CUDA;
+    *out = p;
     return GS_OK;
 }
 

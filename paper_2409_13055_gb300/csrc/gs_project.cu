@@ -914,7 +914,12 @@ gs_status launch_project(const Plan* p, const gs_map* map, const gs_view* views_
     if (reinterpret_cast<uintptr_t>(map->quats) % 16) return GS_ERR_INVALID;
     const int n = map->n;
     DevCounters* ctr = buf<DevCounters>(p, ws, GS_BUF_COUNTERS);
-    if (cudaMemsetAsync(ctr, 0, sizeof(DevCounters), st) != cudaSuccess) return GS_ERR_CUDA;
+    // the status word gathers the bits of all view passes of a recompute
+    // plan: only the first pass (or a whole plan) clears it
+    const size_t keep = p->view_index > 0 ? sizeof(uint32_t) : 0;
+    if (cudaMemsetAsync(reinterpret_cast<char*>(ctr) + keep, 0, sizeof(DevCounters) - keep, st) !=
+        cudaSuccess)
+        return GS_ERR_CUDA;
     dim3 grid((n + kProjThreads - 1) / kProjThreads,
               (p->vt.n_views + kViewsPerThread - 1) / kViewsPerThread);
     auto* kern = map->sh_degree == 0   ? k_project<0>

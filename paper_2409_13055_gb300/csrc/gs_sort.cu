@@ -21,7 +21,7 @@ namespace gs {
 namespace {
 
 constexpr int kWarps = kSortThreads / 32;
-constexpr int kGrid = 152 * 8;  // grid-stride kernels
+constexpr int kGridPerSm = 8;  // CTAs per SM of the grid-stride kernels
 constexpr uint32_t kCulledKey = 0xFFFFFFFFu;  // depth key of a culled pair (never a depth)
 
 __device__ __forceinline__ uint32_t active_count(const uint32_t* count_dev, uint32_t count_host) {
@@ -528,7 +528,9 @@ gs_status launch_bin_sort(const Plan* p, int32_t n, void* ws, cudaStream_t st) {
     const uint32_t* sorted_keys = (p->tile_passes & 1) ? ikb : ika;
 
     // 4. per-tile ranges (cleared above)
-    launch_pdl(k_ranges, kGrid, 256, 0, st, sorted_keys, cnt, ranges);
+    const int sms = sm_count();
+    if (sms <= 0) return GS_ERR_CUDA;
+    launch_pdl(k_ranges, sms * kGridPerSm, 256, 0, st, sorted_keys, cnt, ranges);
     launch_pdl(k_tile_order, 1, kOrderThreads, 0, st, ranges, p->total_tiles,
                buf<uint32_t>(p, ws, B_TILE_ORDER));
     return launch_status();

@@ -10,10 +10,13 @@ Adam of Sec. IV-A) runs in libgs_gb300.so.
   group starting on a 256-byte boundary, with gradients and Adam moments in
   buffers of the same layout -- so the fused Adam kernel is one pass and a
   later cross-GPU all-reduce of the gradient would be one call.
-* ``Rasterizer`` owns a plan and its workspace for one batch of views.
-* ``GSRender`` is the torch.autograd.Function over the rasteriser, with an
-  optional recompute mode that keeps only (final_T, last_idx) between the
-  forward and the backward.
+* ``Rasterizer`` owns a plan and its workspace for one batch of views; a
+  recompute rasteriser (checkpointing) keeps one view's projection and
+  binning in its workspace, runs the views through it one at a time and
+  repeats a view's projection and binning in the backward.
+* ``GSRender`` is the torch.autograd.Function over the rasteriser; with a
+  recompute rasteriser only (final_T, last_idx) survive from the forward to
+  the backward, and several of them may share one workspace.
 * ``MappingStep`` is one whole iteration, optionally captured as a CUDA graph.
 """
 from __future__ import annotations
@@ -283,31 +286,78 @@ def views_to_device(views, device="cuda"):
     return arr, torch.from_numpy(raw).to(device)
 
 
+def make_config(tile=(16, 16), smem_batch=128, near_z=0.2, bg=(0.0, 0.0, 0.0),
+                pixels_per_thread=0, smem_batch_bwd=0, pixels_per_thread_bwd=0,
+                density_stats=False, deterministic=False, tight_rect=True,
+                recompute=False) -> B.gs_config:
+    """The gs_config of a rasteriser (the defaults of Rasterizer)."""
+    return B.gs_config(int(tile[0]), int(tile[1]), int(smem_batch), int(pixels_per_thread),
+                       int(smem_batch_bwd), int(pixels_per_thread_bwd), float(near_z),
+                       (B.c_float * 3)(*[float(x) for x in bg]), int(bool(density_stats)),
+                       int(bool(deterministic)), int(bool(tight_rect)), int(bool(recompute)))
+
+
+def plan_workspace_bytes(views, n_capacity, instance_capacity, **cfg) -> int:
+    """Workspace bytes a rasteriser with these views, capacities and
+    configuration (make_config's keywords) would need; allocates nothing."""
+    plan = B.gs_plan_init(make_config(**cfg), [make_view(v) for v in views], int(n_capacity),
+                          int(instance_capacity))
+    return B.gs_plan_workspace_bytes(plan)
+
+
 class Rasterizer:
-    """Plan + workspace + output buffers for one batch of views."""
+    """Plan + workspace + output buffers for one batch of views.
+
+    recompute: a checkpointing plan (gs_config.recompute): the workspace
+    holds one view's projection and binning; forward() and render_bwd() run
+    the views one pass at a time, and the backward repeats each view's
+    projection and binning (bit-identical) before its adjoint.  instance
+    capacity is then per view.  workspace: a uint8 CUDA tensor to use
+    instead of allocating one (at least workspace_bytes long); recompute
+    rasterisers used one after the other may share one, since nothing in
+    it outlives a call sequence."""
 
     def __init__(self, views, n_capacity, instance_capacity=None, tile=(16, 16), smem_batch=128,
                  near_z=0.2, bg=(0.0, 0.0, 0.0), pixels_per_thread=0, smem_batch_bwd=0,
                  pixels_per_thread_bwd=0, density_stats=False, deterministic=False,
-                 tight_rect=True, device="cuda"):
+                 tight_rect=True, recompute=False, workspace=None, device="cuda"):
         self.views = list(views)
         self.device = torch.device(device)
-        self.cfg = B.gs_config(int(tile[0]), int(tile[1]), int(smem_batch),
-                               int(pixels_per_thread), int(smem_batch_bwd),
-                               int(pixels_per_thread_bwd), float(near_z),
-                               (B.c_float * 3)(*[float(x) for x in bg]), int(bool(density_stats)),
-                               int(bool(deterministic)), int(bool(tight_rect)))
+        self.recompute = bool(recompute)
+        self.cfg = make_config(tile, smem_batch, near_z, bg, pixels_per_thread, smem_batch_bwd,
+                               pixels_per_thread_bwd, density_stats, deterministic, tight_rect,
+                               self.recompute)
         self.n_capacity = int(n_capacity)
         if instance_capacity is None:
-            px = sum(v["width"] * v["height"] for v in self.views)
+            sizes = [v["width"] * v["height"] for v in self.views]
+            px = max(sizes) if self.recompute else sum(sizes)  # pixels binned per call
             instance_capacity = max(1 << 20, 4 * px, 8 * n_capacity)
         self.instance_capacity = int(instance_capacity)
         self.host_views, self.views_dev = views_to_device(self.views, self.device)
         self.plan = B.gs_plan_init(self.cfg, list(self.host_views), self.n_capacity,
                                    self.instance_capacity)
-        self.ws = torch.empty(B.gs_plan_workspace_bytes(self.plan), dtype=torch.uint8,
-                              device=self.device)
-        self.ws.zero_()
+        # the plans the per-view calls take: the plan itself, or one pass per
+        # view of a recompute plan of several views
+        if self.recompute and len(self.views) > 1:
+            self.passes = [B.gs_plan_view_pass(self.plan, v) for v in range(len(self.views))]
+        else:
+            self.passes = [self.plan]
+        self.workspace_bytes = B.gs_plan_workspace_bytes(self.plan)
+        if workspace is not None:
+            dev = workspace.device
+            if (workspace.dtype != torch.uint8 or dev.type != self.device.type
+                    or (self.device.index is not None and dev.index != self.device.index)
+                    or workspace.numel() < self.workspace_bytes
+                    or workspace.data_ptr() % 256 != 0):
+                raise ValueError("workspace: a 256-byte aligned uint8 tensor of at least "
+                                 f"{self.workspace_bytes} bytes on {self.device}")
+            self.ws = workspace
+        else:
+            self.ws = torch.empty(self.workspace_bytes, dtype=torch.uint8, device=self.device)
+            self.ws.zero_()
+        # forwards run so far (GSRender checks that its backward follows its
+        # own forward in a plan that keeps the projection)
+        self.generation = 0
         tot = B.gs_plan_totals(self.plan)
         self.total_values, self.total_pixels = tot["total_values"], tot["total_pixels"]
         self.total_tiles = tot["total_tiles"]
@@ -331,31 +381,54 @@ class Rasterizer:
         flat = [torch.as_tensor(np.asarray(x, np.float32)).reshape(-1) for x in per_view_images]
         return torch.cat(flat).to(self.device)
 
-    def buffer(self, buf_id, dtype=torch.uint8):
-        off, nbytes = B.gs_plan_buffer(self.plan, buf_id)
+    def buffer(self, buf_id, dtype=torch.uint8, view=None):
+        """A workspace buffer (of the pass of `view` in a recompute plan)."""
+        off, nbytes = B.gs_plan_buffer(self._pass(view), buf_id)
         return self.ws[off:off + nbytes].view(dtype)
+
+    def _pass(self, view):
+        if view is None:
+            if len(self.passes) > 1:
+                raise ValueError("a recompute plan of several views runs one view at a time: "
+                                 "pass view=")
+            return self.passes[0]
+        return self.passes[view]
 
     def set_poses(self, views):
         """Copy new poses (same sizes) to the device copy read by the kernels."""
         arr, dev = views_to_device(views, self.device)
         self.views_dev.copy_(dev)
 
-    # the C-ABI steps ---------------------------------------------------------
-    def project(self, gmap: B.gs_map, stream=None):
-        B.gs_project(self.plan, gmap, self.views_dev, self.ws, stream)
+    # the C-ABI steps (view: the pass of a recompute plan) ----------------------
+    def project(self, gmap: B.gs_map, stream=None, view=None):
+        B.gs_project(self._pass(view), gmap, self.views_dev, self.ws, stream)
 
-    def bin_sort(self, n, stream=None):
-        B.gs_bin_sort(self.plan, n, self.ws, stream)
+    def bin_sort(self, n, stream=None, view=None):
+        B.gs_bin_sort(self._pass(view), n, self.ws, stream)
 
-    def render_fwd(self, images=None, final_T=None, last_idx=None, stream=None):
-        B.gs_render_fwd(self.plan, self.ws, self.images if images is None else images,
+    def render_fwd(self, images=None, final_T=None, last_idx=None, stream=None, view=None):
+        B.gs_render_fwd(self._pass(view), self.ws, self.images if images is None else images,
                         self.final_T if final_T is None else final_T,
                         self.last_idx if last_idx is None else last_idx, stream)
 
-    def forward(self, gmap: B.gs_map, stream=None):
-        self.project(gmap, stream)
-        self.bin_sort(gmap.n, stream)
-        self.render_fwd(stream=stream)
+    def forward(self, gmap: B.gs_map, stream=None, images=None, final_T=None, last_idx=None):
+        """Projection, binning and compositing of every view (one pass per
+        view in a recompute plan of several views)."""
+        for v in range(len(self.passes)):
+            self.project(gmap, stream, view=v)
+            self.bin_sort(gmap.n, stream, view=v)
+            self.render_fwd(images, final_T, last_idx, stream=stream, view=v)
+        self.generation += 1
+
+    def max_instances(self, gmap: B.gs_map):
+        """Largest (Gaussian, tile) instance count any binning call of this
+        plan needs for gmap (one synchronising read per pass)."""
+        raw = 0
+        for v in range(len(self.passes)):
+            self.project(gmap, view=v)
+            self.bin_sort(gmap.n, view=v)
+            raw = max(raw, int(self.counters().n_instances_raw))
+        return raw
 
     def loss_l1_ssim(self, targets, lam, view_weight=None, images=None, stream=None):
         w = 1.0 / len(self.views) if view_weight is None else view_weight
@@ -364,18 +437,27 @@ class Rasterizer:
 
     def render_bwd(self, gmap: B.gs_map, grads: B.gs_map_grad, dL=None, final_T=None,
                    last_idx=None, accumulate=False, stream=None):
-        B.gs_render_bwd(self.plan, gmap, self.views_dev, self.ws,
-                        self.final_T if final_T is None else final_T,
-                        self.last_idx if last_idx is None else last_idx,
-                        self.dL if dL is None else dL, grads, accumulate, stream)
+        """Pixel and projection adjoints of every view; in a recompute plan
+        each view's projection and binning are run again first."""
+        args = (self.final_T if final_T is None else final_T,
+                self.last_idx if last_idx is None else last_idx, self.dL if dL is None else dL)
+        for v, pl in enumerate(self.passes):
+            if self.recompute:
+                self.project(gmap, stream, view=v)
+                self.bin_sort(gmap.n, stream, view=v)
+            B.gs_render_bwd(pl, gmap, self.views_dev, self.ws, *args, grads,
+                            accumulate or v > 0, stream)
 
-    def render_bwd_pixels(self, dL=None, final_T=None, last_idx=None, stream=None):
-        B.gs_render_bwd_pixels(self.plan, self.ws, self.final_T if final_T is None else final_T,
+    def render_bwd_pixels(self, dL=None, final_T=None, last_idx=None, stream=None, view=None):
+        B.gs_render_bwd_pixels(self._pass(view), self.ws,
+                               self.final_T if final_T is None else final_T,
                                self.last_idx if last_idx is None else last_idx,
                                self.dL if dL is None else dL, stream)
 
-    def project_bwd(self, gmap: B.gs_map, grads: B.gs_map_grad, accumulate=False, stream=None):
-        B.gs_project_bwd(self.plan, gmap, self.views_dev, self.ws, grads, accumulate, stream)
+    def project_bwd(self, gmap: B.gs_map, grads: B.gs_map_grad, accumulate=False, stream=None,
+                    view=None):
+        B.gs_project_bwd(self._pass(view), gmap, self.views_dev, self.ws, grads, accumulate,
+                         stream)
 
     def project_bwd_groups(self, gmap: B.gs_map, grads: B.gs_map_grad, group_vis, stream=None):
         """The projection adjoint writing only groups of GS_GRAD_GROUP
@@ -396,10 +478,10 @@ class Rasterizer:
         """vis[i] = 1 where Gaussian i touched a tile in the last projection."""
         B.gs_visibility(self.plan, n, self.ws, vis, stream)
 
-    def densify_stats(self, n, accum, denom, stream=None):
+    def densify_stats(self, n, accum, denom, stream=None, view=None):
         """Adds the last backward's density-control statistic (plan built
         with density_stats) to accum / denom."""
-        B.gs_densify_stats(self.plan, n, self.ws, accum, denom, stream)
+        B.gs_densify_stats(self._pass(view), n, self.ws, accum, denom, stream)
 
     def counters(self, stream=None) -> B.gs_counters:
         return B.gs_read_counters(self.plan, self.ws, stream)
@@ -409,9 +491,7 @@ def fit_instance_capacity(views, gmap: GaussianMap, headroom=1.25, **kw):
     """A rasteriser whose instance capacity fits this map with headroom (one
     synchronising probe at set-up, none afterwards)."""
     probe = Rasterizer(views, gmap.capacity, **kw)
-    probe.project(gmap.gs_map())
-    probe.bin_sort(gmap.n)
-    raw = probe.counters().n_instances_raw
+    raw = probe.max_instances(gmap.gs_map())
     if raw > probe.instance_capacity:
         kw = dict(kw)
         probe = Rasterizer(views, gmap.capacity, instance_capacity=int(raw * headroom) + 1024, **kw)
@@ -433,9 +513,16 @@ def _map_from_tensors(means, log_scales, quats, opacity_logits, sh, degree):
 class GSRender(torch.autograd.Function):
     """images = GSRender.apply(means, log_scales, quats, opacity_logits, sh, rast, recompute)
 
-    sh is [K][N][3].  The backward calls gs_render_bwd.  With recompute=True
-    only final_T and last_idx are kept from the forward; the projection and
-    the (deterministic) binning are re-run in the backward.
+    sh is [K][N][3]; the result is the rasteriser's packed image buffer.  The
+    backward calls gs_render_bwd.  With a recompute rasteriser
+    (Rasterizer(recompute=True)) only final_T and last_idx survive from the
+    forward, and every view's projection and binning run again in the
+    backward: any number of renders may wait for their backward in one
+    autograd graph, and their rasterisers may share one workspace.
+    Otherwise the backward reads the projection and binning that the
+    forward left in the rasteriser's workspace, so it must come before the
+    next forward on that rasteriser (it raises if not), unless recompute=True
+    asks for them to be run again into the same workspace.
     """
 
     @staticmethod
@@ -447,7 +534,9 @@ class GSRender(torch.autograd.Function):
         images = rast.images.clone()
         final_T = rast.final_T.clone()
         last_idx = rast.last_idx.clone()
-        ctx.rast, ctx.recompute, ctx.degree = rast, bool(recompute), degree
+        ctx.rast, ctx.degree = rast, degree
+        ctx.recompute = bool(recompute) or rast.recompute
+        ctx.generation = rast.generation
         ctx.save_for_backward(means, log_scales, quats, opacity_logits, sh, final_T, last_idx)
         return images
 
@@ -456,13 +545,40 @@ class GSRender(torch.autograd.Function):
         means, log_scales, quats, opacity_logits, sh, final_T, last_idx = ctx.saved_tensors
         rast = ctx.rast
         gmap = _map_from_tensors(means, log_scales, quats, opacity_logits, sh, ctx.degree)
-        if ctx.recompute:
+        if ctx.recompute and not rast.recompute:
             rast.project(gmap)
             rast.bin_sort(gmap.n)
+        elif not ctx.recompute and rast.generation != ctx.generation:
+            raise RuntimeError("GSRender: the rasteriser ran another forward after this one; its "
+                               "workspace no longer holds this render's projection (use a "
+                               "recompute rasteriser, recompute=True, or one rasteriser per "
+                               "pending render)")
         g = [torch.zeros_like(t) for t in (means, log_scales, quats, opacity_logits, sh)]
         grads = B.gs_map_grad(*[t.data_ptr() for t in g])
         rast.render_bwd(gmap, grads, dL=dimages.contiguous(), final_T=final_T, last_idx=last_idx)
         return (*g, None, None)
+
+
+class L1SSIMLoss(torch.autograd.Function):
+    """loss = L1SSIMLoss.apply(images, targets, rast, lam): Eq. 2 (read as
+    (1 - lam) mean|I - I_gt| + lam (1 - mean SSIM), the mean over the
+    rasteriser's views) on packed images, with its analytic gradient from
+    the same gs_loss_l1_ssim call."""
+
+    @staticmethod
+    def forward(ctx, images, targets, rast: Rasterizer, lam):
+        images = images.contiguous()
+        loss = torch.zeros(1, dtype=torch.float32, device=images.device)
+        dL = torch.empty_like(images)
+        B.gs_loss_l1_ssim(rast.plan, images, targets, lam, 1.0 / len(rast.views), loss, dL,
+                          rast.ws)
+        ctx.save_for_backward(dL)
+        return loss[0]
+
+    @staticmethod
+    def backward(ctx, gout):
+        (dL,) = ctx.saved_tensors
+        return dL * gout, None, None, None
 
 
 class MappingStep:
@@ -470,7 +586,7 @@ class MappingStep:
     batch of views, optionally captured as one CUDA graph."""
 
     def __init__(self, gmap: GaussianMap, rast: Rasterizer, targets: torch.Tensor, lam: float,
-                 lr=None, extent=1.0, fused=False, keep_grads=False, recompute=False,
+                 lr=None, extent=1.0, fused=False, keep_grads=False, recompute=None,
                  stats=None, sparse_adam=False):
         self.gmap, self.rast, self.targets, self.lam = gmap, rast, targets, float(lam)
         self.lr, self.extent, self.fused, self.keep_grads = lr, extent, fused, keep_grads
@@ -482,13 +598,19 @@ class MappingStep:
         # iteration is added to them (the rasteriser needs density_stats)
         self.stats = stats
         # recompute: the checkpointed backward -- projection and binning are
-        # run again (bit-identically) between the loss and the adjoint, as
-        # when the forward's intermediates were not kept
-        self.recompute = bool(recompute)
+        # run again (bit-identically) between the loss and the adjoint.  With
+        # a recompute rasteriser (the default then) the views go through its
+        # one-view workspace one pass at a time; recompute=True with another
+        # rasteriser re-runs them into the same workspace
+        self.recompute = rast.recompute if recompute is None else bool(recompute)
+        self.passes = len(rast.passes) if rast.recompute else 1
+        if self.passes > 1 and (fused or sparse_adam):
+            raise ValueError("the fused and visibility-masked steps need every view at once; "
+                             "a recompute rasteriser of several views runs one view at a time")
         # without keep_grads the gradient of groups of GS_GRAD_GROUP Gaussians
         # that touch no tile (all zero) is neither written nor read
         self.groups = (not keep_grads and not fused and self.visible is None
-                       and gmap.capacity == gmap.n)
+                       and gmap.capacity == gmap.n and self.passes == 1)
         if self.groups:
             ng = (gmap.n + B.GS_GRAD_GROUP - 1) // B.GS_GRAD_GROUP
             self.group_vis = torch.zeros(ng, dtype=torch.uint8, device=gmap.device)
@@ -503,15 +625,25 @@ class MappingStep:
     def run_front(self, stream=None):
         """Projection, binning and forward render (reads the views, not the
         targets)."""
-        r = self.rast
-        r.project(self._m, stream)
-        r.bin_sort(self.gmap.n, stream)
-        r.render_fwd(stream=stream)
+        self.rast.forward(self._m, stream)
 
     def run_back(self, stream=None):
         """Loss, backward and optimiser step (reads the targets)."""
         r = self.rast
         r.loss_l1_ssim(self.targets, self.lam, stream=stream)
+        if r.recompute and self.passes > 1:
+            # one view at a time through the one-view workspace: its
+            # projection and binning again, its pixel and projection
+            # adjoints (gradients summed over the views), its statistic
+            for v in range(self.passes):
+                r.project(self._m, stream, view=v)
+                r.bin_sort(self.gmap.n, stream, view=v)
+                r.render_bwd_pixels(stream=stream, view=v)
+                r.project_bwd(self._m, self._g, accumulate=v > 0, stream=stream, view=v)
+                if self.stats is not None:
+                    r.densify_stats(self.gmap.n, self.stats[0], self.stats[1], stream, view=v)
+            self.gmap.adam_step(self.lr, self.extent, stream=stream)
+            return
         if self.recompute:
             r.project(self._m, stream)
             r.bin_sort(self.gmap.n, stream)

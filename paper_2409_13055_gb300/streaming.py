@@ -11,8 +11,10 @@ Per keyframe:
      planned for the window size and the map's capacity and re-planned with
      headroom when either changes or the instance count outgrows it);
   3. ``iters`` batched mapping iterations run over the whole window, each one
-     ``MappingStep`` (project, bin, render, loss, backward, Adam), with the
-     checkpointed backward by default, captured as one CUDA graph and replayed;
+     ``MappingStep`` (project, bin, render, loss, backward, Adam), by default
+     on a recompute rasteriser (checkpointing: the window's views go through a
+     one-view workspace one at a time, and the backward repeats each view's
+     projection and binning), captured as one CUDA graph and replayed;
      with Gaussian-pyramid targets (Sec. III-B) the iterations go from the
      coarsest level to the full resolution.
 
@@ -58,21 +60,21 @@ class StreamingMapper:
         if r is None or r.n_capacity < n:
             while self.capacity < n:
                 self.capacity *= 2
-            r = mapping.Rasterizer(views, self.capacity, instance_capacity=None, **self.rast_kw)
+            r = mapping.Rasterizer(views, self.capacity, instance_capacity=None,
+                                   recompute=self.recompute, **self.rast_kw)
             # a smaller window does not come back once the window is full, and
             # each plan's workspace grows with views x capacity
             self._rasts = {k: v for k, v in self._rasts.items() if k[0] == V}
             self._rasts[key] = r
             self.replans += 1
         r.set_poses(views)
-        # instance capacity: one synchronising probe per keyframe and level
-        r.project(self.gmap.gs_map())
-        r.bin_sort(n)
-        raw = int(r.counters().n_instances_raw)
+        # instance capacity (of a view, in a recompute plan): one synchronising
+        # probe per keyframe, level and pass
+        raw = r.max_instances(self.gmap.gs_map())
         if raw > r.instance_capacity:
             r = mapping.Rasterizer(views, self.capacity,
                                    instance_capacity=int(raw * self.headroom) + 4096,
-                                   **self.rast_kw)
+                                   recompute=self.recompute, **self.rast_kw)
             r.set_poses(views)
             self._rasts[key] = r
             self.replans += 1
@@ -95,7 +97,7 @@ class StreamingMapper:
             rast = self._rasterizer(views, level)
             targets = torch.cat([f[1][level].reshape(-1) for f in self.frames])
             self.steps.append(mapping.MappingStep(self.gmap, rast, targets, self.lam, self.lr,
-                                                  self.extent, recompute=self.recompute))
+                                                  self.extent))
         self._eager_done = [False] * self.levels
         self._kf_iter = 0
         self.keyframes += 1

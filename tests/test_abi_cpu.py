@@ -30,14 +30,15 @@ def test_exports_every_declared_function(lib):
 
 def test_struct_sizes_match_header():
     assert ctypes.sizeof(B.gs_view) == 80
-    assert ctypes.sizeof(B.gs_config) == 52
+    assert ctypes.sizeof(B.gs_config) == 56
     assert ctypes.sizeof(B.gs_densify_config) == 32
     assert ctypes.sizeof(B.gs_counters) == 32
     assert ctypes.sizeof(B.gs_plan) == 8 * B.GS_PLAN_WORDS
 
 
-def _cfg(tw=16, th=16, batch=128, near=0.2, ppt=0, batch_bwd=0, ppt_bwd=0):
-    return B.gs_config(tw, th, batch, ppt, batch_bwd, ppt_bwd, near, (B.c_float * 3)(0, 0, 0))
+def _cfg(tw=16, th=16, batch=128, near=0.2, ppt=0, batch_bwd=0, ppt_bwd=0, recompute=0):
+    return B.gs_config(tw, th, batch, ppt, batch_bwd, ppt_bwd, near, (B.c_float * 3)(0, 0, 0),
+                       0, 0, 1, recompute)
 
 
 def _views(*sizes):
@@ -106,6 +107,53 @@ def test_calls_reject_bad_arguments_without_launching(lib):
     assert lib.gs_adam_step(p, p, p, p, 5, 1, offs, lrs, 1.0, 0.999, 1e-15, p, None) == \
         B.GS_ERR_INVALID  # beta1 = 1
     assert B.gs_status_string(B.GS_ERR_CAPACITY).startswith("GS_ERR_CAPACITY")
+
+
+def test_recompute_plans_hold_one_view_and_run_passes(lib):
+    """A recompute plan lays the projection and binning out for one view
+    (the loss maps sharing those bytes), so its workspace is smaller; its
+    view passes share the layout and address each view's images; the whole
+    plan of several views is refused by the per-view calls, which take
+    passes."""
+    vs = _views((640, 480, 3), (752, 480, 1), (1200, 680, 3))
+    n, icap = 200_000, 2_000_000
+    full = B.gs_plan_init(_cfg(tw=8, th=8), vs, n, icap)
+    rec = B.gs_plan_init(_cfg(tw=8, th=8, recompute=1), vs, n, icap)
+    wf, wr = B.gs_plan_workspace_bytes(full), B.gs_plan_workspace_bytes(rec)
+    # (V - 1) views x ~200 B per Gaussian saved at least (the instance
+    # capacity, the same here, is one view's in the recompute plan)
+    assert wr < wf - 2 * n * 180, (wf, wr)
+    one = B.gs_plan_init(_cfg(tw=8, th=8), vs[2:], n, icap)
+    assert wr <= B.gs_plan_workspace_bytes(one) + 256
+    for v in range(3):
+        ps = B.gs_plan_view_pass(rec, v)
+        assert B.gs_plan_workspace_bytes(ps) == wr
+        assert B.gs_plan_view(ps, 0)["value_offset"] == B.gs_plan_view(rec, v)["value_offset"]
+        assert B.gs_plan_totals(ps)["total_tiles"] == \
+            B.gs_plan_view(rec, v)["tiles_x"] * B.gs_plan_view(rec, v)["tiles_y"]
+        for b in range(B.GS_BUF_ABSGRAD + 1):
+            assert B.gs_plan_buffer(ps, b) == B.gs_plan_buffer(rec, b) or b in (
+                B.GS_BUF_TILE_KEYS, B.GS_BUF_TILE_VALUES)
+    bad = B.gs_plan()
+    assert lib.gs_plan_view_pass(ctypes.byref(full), 0, ctypes.byref(bad)) == B.GS_ERR_INVALID
+    assert lib.gs_plan_view_pass(ctypes.byref(rec), 3, ctypes.byref(bad)) == B.GS_ERR_INVALID
+    ps = B.gs_plan_view_pass(rec, 1)
+    assert lib.gs_plan_view_pass(ctypes.byref(ps), 0, ctypes.byref(bad)) == B.GS_ERR_INVALID
+    p = ctypes.c_void_p(256)
+    m = B.gs_map(p, p, p, p, p, 10, 3)
+    g = B.gs_map_grad(p, p, p, p, p)
+    for plan in (rec,):  # every per-view call refuses the whole plan (nothing launched)
+        assert lib.gs_project(ctypes.byref(plan), ctypes.byref(m), p, p, None) == B.GS_ERR_INVALID
+        assert lib.gs_bin_sort(ctypes.byref(plan), 10, p, None) == B.GS_ERR_INVALID
+        assert lib.gs_render_fwd(ctypes.byref(plan), p, p, p, p, None) == B.GS_ERR_INVALID
+        assert lib.gs_render_bwd_pixels(ctypes.byref(plan), p, p, p, p, None) == \
+            B.GS_ERR_INVALID
+        assert lib.gs_project_bwd(ctypes.byref(plan), ctypes.byref(m), p, p, ctypes.byref(g), 0,
+                                  None) == B.GS_ERR_INVALID
+    # ... and the calls that need every view at once refuse a pass
+    assert lib.gs_project_bwd_groups(ctypes.byref(ps), ctypes.byref(m), p, p, ctypes.byref(g), p,
+                                     None) == B.GS_ERR_INVALID
+    assert lib.gs_visibility(ctypes.byref(ps), 10, p, p, None) == B.GS_ERR_INVALID
 
 
 def test_deterministic_plans_need_one_warp_per_tile(lib):

@@ -30,7 +30,7 @@ def test_reference_arm_prints_the_json_line():
 
 def test_iteration_roofline_sums_its_stages():
     import bench
-    peaks = {"hbm_gbs": 6800.0, "sm_max_mhz": 2070.0}
+    peaks = {"hbm_gbs": 6800.0, "sm_max_mhz": 2070.0, "sms": 152}
     n, deg = 1_000_000, 3
     out = bench.iteration_roofline(n, deg, 1, 1200 * 680 * 3, 1200 * 680, 3_000_000,
                                    100_000_000, 12_750, 2, 59 * n, 1.25, peaks)
@@ -42,3 +42,6 @@ def test_iteration_roofline_sums_its_stages():
     assert out["frac"] == pytest.approx(out["ms_roof"] / 1.25)
     # Adam: 28 B per float of the packed buffer at the copy bandwidth
     assert stages["adam"] == pytest.approx(59 * n * 28 / 6.8e12 * 1e3)
+    # the pixel adjoint at 60 FLOP per pair on 152 SMs x 128 lanes x 2 x 2.07 GHz
+    assert stages["render_bwd"] == pytest.approx(
+        max(100e6 * 60 / (152 * 128 * 2 * 2.07e9), (3e6 * 48 + 1200 * 680 * 16) / 6.8e12) * 1e3)

@@ -138,3 +138,73 @@ def test_batched16_views_match_oracle_and_per_view_loop():
         print(f"view {v} {views[v]['width']}x{views[v]['height']}x{views[v]['channels']}: "
               f"max-abs {err.max():.2e}")
         assert err.max() <= IMG_TOL, (v, err.max())
+
+
+@pytest.mark.parametrize("tile", [(8, 8), (16, 16)])
+def test_room200k_iteration_matches_oracle(tile):
+    """The 200k-Gaussian room at 640x480 (anisotropic, SH degree 3, L1 + 0.2
+    (1 - SSIM), seeded noise target): image, loss, tile lists and every
+    gradient group of one iteration against the oracle's, then one Adam step
+    against the oracle's Adam on the oracle's gradient."""
+    p, views, targets, lam = scenes.workload("room200k_640x480")
+    view = views[0]
+    launch = dict(LAUNCH, tile=tile) if tile == (8, 8) else dict(tile=tile)
+    gm = mapping.GaussianMap(p)
+    rast = mapping.fit_instance_capacity(views, gm, headroom=1.5, **launch)
+    m, g = gm.gs_map(), gm.gs_map_grad()
+    rast.forward(m)
+    rast.loss_l1_ssim(rast.pack(targets), lam)
+    rast.render_bwd(m, g)
+    torch.cuda.synchronize()
+    assert rast.counters().status == 0
+    _, keys, vals, _ = U.gpu_tile_lists(rast)
+    img = rast.view_slice(rast.images, 0).cpu().numpy()
+    loss = rast.loss.item()
+    grads = {k: t.cpu().numpy() for k, t in gm.grads().items()}
+    gm.adam_step()
+    torch.cuda.synchronize()
+    after = {k: t.cpu().numpy() for k, t in gm.params().items()}
+
+    L, og, renders = oracle.iteration(p, views, targets, lam, *tile)
+    proj = oracle.project(p, view, *tile)
+    mask = U.guard_pixel_mask(view, proj, renders[0], tile, params=p)
+    assert mask.mean() < 0.02, mask.mean()
+    err = np.abs(img - renders[0]["image"])[:, ~mask]
+    assert err.max() <= IMG_TOL, err.max()
+    assert abs(loss - L) <= 1e-5 * abs(L), (loss, L)
+    compared, removed = U.compare_tile_lists(keys, vals, p["means"].shape[0], proj, view, tile)
+    assert compared > 100_000 and removed <= 0.01 * compared, (compared, removed)
+    keep = U.gradient_keep(p, views, renders, tile)
+    vis = proj["tiles_touched"] > 0
+    assert (keep & vis).sum() >= 0.95 * vis.sum()
+    errs = U.grad_errors(grads, og, keep)
+    print(f"200k 640x480 {tile}: image max-abs {err.max():.2e}, loss {loss:.8f} vs {L:.8f}, "
+          f"{compared} list pairs bit-exact, gradients " +
+          ", ".join(f"{k} {e:.2e}" for k, e in errs.items()))
+    assert all(e <= GRAD_TOL for e in errs.values()), errs
+    # one Adam step (3DGS default rates) from zero moments on the GPU's own
+    # gradient, against the oracle's Adam on the same gradient; with eps =
+    # 1e-15 a first step moves a parameter by ~lr sign(g) for any |g| >> eps,
+    # so elements whose g^2 leaves the FP32 normal range (|g| < 1e-19) are
+    # left out
+    lr = dict(zip(oracle.PARAM_GROUPS, (1.6e-4, 5e-3, 1e-3, 0.05, None)))
+    for k in oracle.PARAM_GROUPS:
+        p0 = np.asarray(p[k], np.float64).copy()
+        gk = grads[k].astype(np.float64)
+        mm, vv = np.zeros_like(p0), np.zeros_like(p0)
+        if k == "sh":
+            for c, rate in ((slice(0, 1), 2.5e-3), (slice(1, None), 2.5e-3 / 20)):
+                pc = np.ascontiguousarray(p0[c])
+                oracle.adam(pc, gk[c], np.zeros_like(pc), np.zeros_like(pc), rate, 1)
+                p0[c] = pc
+        else:
+            oracle.adam(p0, gk, mm, vv, lr[k], 1)
+        ok = (np.abs(gk) >= 1e-19) | (gk == 0)
+        assert ok.mean() > 0.99, (k, ok.mean())
+        # FP32 p - lr x: rounding of the FP32 operands (|p| and the step lr)
+        before = np.asarray(p[k], np.float64)
+        rate = np.full_like(before, lr[k]) if k != "sh" else np.concatenate(
+            [np.full_like(before[:1], 2.5e-3), np.full_like(before[1:], 2.5e-3 / 20)])
+        tol = 1.2e-7 * (np.abs(before) + rate) + 1e-6 * rate
+        err = np.abs(after[k].astype(np.float64) - p0)
+        assert np.all(err[ok] <= tol[ok]), (k, float((err - tol)[ok].max()))

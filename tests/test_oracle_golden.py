@@ -42,3 +42,21 @@ def test_tight_rects_change_no_result():
                                atol=1e-13)
     for k, v in want["grad_norms"].items():
         assert abs(got["grad_norms"][k] - v) <= 1e-10 * max(1.0, abs(v))
+
+
+def test_threads_change_only_the_last_bits():
+    """The oracle's OpenMP loops (used by the benchmark's all-core CPU
+    baseline) give the single-threaded results up to the order of additions:
+    the frozen record's quantities agree to 1e-12 with four threads."""
+    import oracle
+    one = compute()
+    oracle.set_threads(4)
+    try:
+        four = compute()
+    finally:
+        oracle.set_threads(1)
+    assert abs(four["loss"] - one["loss"]) < 1e-12
+    assert four["last_idx_sum"] == one["last_idx_sum"]
+    assert abs(four["image_sum"] - one["image_sum"]) < 1e-12
+    for k, v in one["grad_norms"].items():
+        assert abs(four["grad_norms"][k] - v) <= 1e-12 * max(1.0, abs(v))

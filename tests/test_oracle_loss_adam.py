@@ -169,3 +169,59 @@ def test_masked_adam_equals_dense_on_its_elements_and_leaves_the_rest():
     for x, y, z in zip(c, a, (p0, m0, v0)):
         np.testing.assert_array_equal(x[mask], y[mask])
         np.testing.assert_array_equal(x[~mask], z[~mask])
+
+
+def test_room200k_subset_gradient_central_differences():
+    """The 200k-Gaussian room at 640x480 (f = 525; anisotropic, SH degree 3,
+    L1 + 0.2 (1 - SSIM)): on a subset of 64 of its Gaussians, those whose
+    means project nearest the image centre, rendered through a 48x40 crop of
+    the same camera, the oracle's analytic gradient against central
+    differences (h = 1e-6) of its whole iteration: along a random direction
+    of every parameter group of every Gaussian, and coordinate by coordinate
+    for 8 of them; perturbations that flip a decision are skipped."""
+    p_all, views, targets, lam = scenes.workload("room200k_640x480")
+    full = views[0]
+    pr = oracle.project(p_all, full, 16, 16, tight=False)
+    vis = np.flatnonzero(pr["tiles_touched"] > 0)
+    d = np.hypot(pr["mean2d"][vis, 0] - 320.0, pr["mean2d"][vis, 1] - 240.0)
+    idx = np.sort(vis[np.argsort(d)[:64]])
+    p = scenes.subset(p_all, idx)
+    p = {k: (v.astype(float) if isinstance(v, np.ndarray) else v) for k, v in p.items()}
+    W, H = 48, 40
+    view = scenes.camera(W, H, 525.0, 525.0, cx=320.0 - 296.0, cy=240.0 - 220.0)
+    target = np.asarray(targets[0], float)[:, 220:220 + H, 296:296 + W]
+    L, g, renders = oracle.iteration(p, [view], [target], lam)
+    assert (renders[0]["n_included"] > 0).mean() > 0.5  # the subset covers the crop
+    base = _decisions(renders)
+    h = 1e-6
+    rng = np.random.default_rng(64)
+
+    def loss_at(key, j, delta):
+        flat = p[key].reshape(-1)
+        old = flat[j].copy()
+        flat[j] = old + delta
+        Lx, _, r = oracle.iteration(p, [view], [target], lam)
+        flat[j] = old
+        return Lx, _decisions(r)
+
+    checked = total = 0
+    for i in range(64):
+        for key in oracle.PARAM_GROUPS:
+            # the coordinates of Gaussian i in this group
+            j = (np.arange(p["sh"].shape[0])[:, None] * 64 * 3 + i * 3 + np.arange(3)).ravel() \
+                if key == "sh" else np.arange(p[key][i].size) + i * p[key][i].size
+            coords = [(j, rng.normal(size=j.size))] + ([(np.array([k]), np.ones(1)) for k in j]
+                                                       if i < 8 else [])
+            for jj, u in coords:
+                u = u / np.linalg.norm(u)
+                total += 1
+                Lp, dp = loss_at(key, jj, h * u)
+                Lm, dm = loss_at(key, jj, -h * u)
+                if not all(np.array_equal(a, b) and np.array_equal(a, c)
+                           for a, b, c in zip(base, dp, dm)):
+                    continue
+                fd = (Lp - Lm) / (2 * h)
+                an = float(np.dot(g[key].reshape(-1)[jj], u))
+                assert abs(fd - an) <= 1e-7 + 1e-5 * abs(fd), (i, key, jj, fd, an)
+                checked += 1
+    assert checked > 0.9 * total, (checked, total)

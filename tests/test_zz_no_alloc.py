@@ -2,8 +2,9 @@
 memory (no workspace), using the library's fixed scratch array.
 
 Collected last on purpose: it exercises state that lives for the whole
-process (the per-device scratch address and the array's contents), and a
-failure here should not hide any other test's result.
+process (the array and its contents, on every device that loaded the
+library's device code), and a failure here should not hide any other test's
+result.
 """
 import ctypes
 
