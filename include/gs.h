@@ -297,7 +297,7 @@ gs_status gs_render_bwd(const gs_plan *plan, const gs_map *map, const gs_view *v
  * a fixed array compiled into the library, about 12.6 MB, which every GPU
  * that has loaded the library's device code holds until the process exits.
  * Limits: the plan's images may hold at most 2^20 values in total (sum of
- * C*H*W; e.g. one 640x480 RGB view) and at most 8192 loss tiles of 32x16;
+ * C*H*W; e.g. one 640x480 RGB view) and at most 8192 loss tiles of 32x32;
  * larger plans are rejected with GS_ERR_CAPACITY before anything is
  * enqueued.
  *

@@ -124,7 +124,8 @@ extern "C" gs_status gs_plan_init(gs_plan* plan, const gs_config* cfg, int32_t n
     for (int v = 0; v < n_views; ++v) {
         ViewGeom& g = p->vt.v[v];
         g.loss_block_offset = (int32_t)lb;
-        lb += (int64_t)((g.width + 31) / 32) * ((g.height + 15) / 16) * g.channels;
+        lb += (int64_t)((g.width + kLossTileW - 1) / kLossTileW) *
+              ((g.height + kLossTileH - 1) / kLossTileH) * g.channels;
     }
     p->loss_blocks = (int32_t)lb;
 
@@ -222,7 +223,8 @@ extern "C" gs_status gs_plan_view_pass(const gs_plan* plan, int32_t v, gs_plan* 
     while ((int64_t(1) << bits) < q->total_tiles) ++bits;
     q->tile_bits = bits < 1 ? 1 : bits;
     q->tile_passes = (q->tile_bits + kRadixBits - 1) / kRadixBits;
-    q->loss_blocks = ((g.width + 31) / 32) * ((g.height + 15) / 16) * g.channels;
+    q->loss_blocks = ((g.width + kLossTileW - 1) / kLossTileW) *
+                     ((g.height + kLossTileH - 1) / kLossTileH) * g.channels;
     return GS_OK;
 }
 

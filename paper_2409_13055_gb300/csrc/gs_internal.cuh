@@ -24,6 +24,7 @@ constexpr int kScanThreads = 256;
 constexpr int kScanItems = 8;
 constexpr int kScanTile = kScanThreads * kScanItems;  // elements per scan block
 constexpr int kProjFloats = 12;                       // floats per projected record
+constexpr int kLossTileW = 32, kLossTileH = 32;       // output tile of the loss kernels
 constexpr int kGrad2d = 9;                            // floats per screen-space gradient
 
 // Per-view geometry derived by gs_plan_init; passed to kernels by value.

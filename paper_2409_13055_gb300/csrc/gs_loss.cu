@@ -7,7 +7,7 @@
 // C1 = 0.01^2, C2 = 0.03^2, per channel, means over C*H*W of the view, and
 // L = view_weight * sum over views (1/n_views: the mean).
 //
-// Two kernels, each over 32x16 output tiles of every channel plane of every
+// Two kernels, each over 32x32 output tiles of every channel plane of every
 // view.  The forward stages the tile plus a 5-pixel halo of both images in
 // shared memory and forms the five window moments (E[x], E[y], E[x^2],
 // E[y^2], E[xy]) with separable 11-tap passes; per pixel it keeps the partial
@@ -24,11 +24,13 @@
 namespace gs {
 namespace {
 
-constexpr int kTX = 32, kTY = 16, kHalo = 5, kWin = 11;
-constexpr int kRows = kTY + 2 * kHalo;  // 26
+constexpr int kTX = kLossTileW, kTY = kLossTileH, kHalo = 5, kWin = 11;
+constexpr int kRows = kTY + 2 * kHalo;  // 42
 constexpr int kCols = kTX + 2 * kHalo;  // 42
 constexpr int kLossThreads = 256;       // 32 x 8
 constexpr int kSeg = 4;                 // outputs per thread in the horizontal passes
+constexpr int kOut = kTY / (kLossThreads / 32);  // output rows per thread in the vertical passes
+static_assert(kTX == 32 && kTY % (kLossThreads / 32) == 0, "one warp per tile row band");
 
 struct Win {
     float w[kWin];
@@ -70,18 +72,24 @@ __device__ __forceinline__ float block_sum(float x, float* red) {
     return t;  // valid in thread 0
 }
 
+// Loads of the tile and its halo issued by every thread before any store.
+constexpr int kLoads = (kRows * kCols + kLossThreads - 1) / kLossThreads;
+
+// Forward: the five window moments of every output value by two separable
+// 11-tap passes (horizontal over the tile's 42 halo rows, then vertical),
+// SSIM, and its partial derivatives with respect to E[x], E[x^2] and E[xy]
+// (the maps the backward correlates).  x and y share one float2 of shared
+// memory; the horizontal pass forms x^2, y^2 and xy once per input value.
 __global__ void __launch_bounds__(kLossThreads)
 k_ssim_fwd(ViewTable vt, Win win, const float* __restrict__ img, const float* __restrict__ tgt,
            float lambda, float inv_views, int64_t total_values, float* __restrict__ maps,
            float* __restrict__ partials, int nblocks, DevCounters* ctr,
            float* __restrict__ loss_dev) {
-    __shared__ float sx[kRows][kCols + 1], sy[kRows][kCols + 1];
+    __shared__ float2 sxy[kRows][kCols + 1];
     __shared__ float h[5][kRows][kTX + 1];
     __shared__ float red[32];
     __shared__ bool is_last;
     const BlockPos bp = block_pos(vt, blockIdx.x);
-    // the tile and its halo: every load of a thread issued before any store
-    constexpr int kLoads = (kRows * kCols + kLossThreads - 1) / kLossThreads;
     {
         float a[kLoads], b[kLoads];
 #pragma unroll
@@ -100,33 +108,37 @@ k_ssim_fwd(ViewTable vt, Win win, const float* __restrict__ img, const float* __
             const int i = threadIdx.x + it * kLossThreads;
             if (i < kRows * kCols) {
                 const int r = i / kCols, c = i - r * kCols;
-                sx[r][c] = a[it];
-                sy[r][c] = b[it];
+                sxy[r][c] = make_float2(a[it], b[it]);
             }
         }
     }
     __syncthreads();
-    // horizontal pass, register-blocked: a thread takes kSeg consecutive
-    // outputs of one row, reading their kSeg + 10 inputs once
+    // horizontal pass: a thread takes kSeg consecutive outputs of one row,
+    // reading their kSeg + 10 inputs once
     for (int i = threadIdx.x; i < kRows * (kTX / kSeg); i += blockDim.x) {
         const int r = i / (kTX / kSeg), c0 = (i - r * (kTX / kSeg)) * kSeg;
-        float a[kSeg + kWin - 1], b[kSeg + kWin - 1];
+        float u[kSeg + kWin - 1], v[kSeg + kWin - 1], uu[kSeg + kWin - 1], vv[kSeg + kWin - 1],
+            uv[kSeg + kWin - 1];
 #pragma unroll
         for (int k = 0; k < kSeg + kWin - 1; ++k) {
-            a[k] = sx[r][c0 + k];
-            b[k] = sy[r][c0 + k];
+            const float2 p = sxy[r][c0 + k];
+            u[k] = p.x;
+            v[k] = p.y;
+            uu[k] = p.x * p.x;
+            vv[k] = p.y * p.y;
+            uv[k] = p.x * p.y;
         }
 #pragma unroll
         for (int o = 0; o < kSeg; ++o) {
             float mx = 0.f, my = 0.f, xx = 0.f, yy = 0.f, xy = 0.f;
 #pragma unroll
             for (int k = 0; k < kWin; ++k) {
-                const float u = a[o + k], v = b[o + k], w = win.w[k];
-                mx = fmaf(w, u, mx);
-                my = fmaf(w, v, my);
-                xx = fmaf(w, u * u, xx);
-                yy = fmaf(w, v * v, yy);
-                xy = fmaf(w, u * v, xy);
+                const float w = win.w[k];
+                mx = fmaf(w, u[o + k], mx);
+                my = fmaf(w, v[o + k], my);
+                xx = fmaf(w, uu[o + k], xx);
+                yy = fmaf(w, vv[o + k], yy);
+                xy = fmaf(w, uv[o + k], xy);
             }
             h[0][r][c0 + o] = mx;
             h[1][r][c0 + o] = my;
@@ -139,28 +151,31 @@ k_ssim_fwd(ViewTable vt, Win win, const float* __restrict__ img, const float* __
     const float C1 = 0.01f * 0.01f, C2 = 0.03f * 0.03f;
     const int tx = threadIdx.x & 31, ty = threadIdx.x >> 5;
     float l1 = 0.0f, ss = 0.0f;
-    // vertical pass, register-blocked: a thread takes two consecutive rows
-    // of one column, reading their 12 rows of horizontal sums once
-    static_assert(kTY == 2 * (kLossThreads / 32), "two output rows per thread");
-    const int r0 = 2 * ty;
-    float m2[2][5] = {{0.f, 0.f, 0.f, 0.f, 0.f}, {0.f, 0.f, 0.f, 0.f, 0.f}};
+    // vertical pass: a thread takes kOut consecutive rows of one column,
+    // reading their kOut + 10 rows of horizontal sums once
+    const int r0 = kOut * ty;
+    float m[kOut][5];
 #pragma unroll
-    for (int k = 0; k < kWin + 1; ++k) {
+    for (int o = 0; o < kOut; ++o)
+#pragma unroll
+        for (int q = 0; q < 5; ++q) m[o][q] = 0.0f;
+#pragma unroll
+    for (int k = 0; k < kWin + kOut - 1; ++k) {
 #pragma unroll
         for (int q = 0; q < 5; ++q) {
             const float hv = h[q][r0 + k][tx];
-            if (k < kWin) m2[0][q] = fmaf(win.w[k], hv, m2[0][q]);
-            if (k >= 1) m2[1][q] = fmaf(win.w[k - 1], hv, m2[1][q]);
+#pragma unroll
+            for (int o = 0; o < kOut; ++o)
+                if (k - o >= 0 && k - o < kWin) m[o][q] = fmaf(win.w[k - o], hv, m[o][q]);
         }
     }
 #pragma unroll
-    for (int o = 0; o < 2; ++o) {
+    for (int o = 0; o < kOut; ++o) {
         const int rr = r0 + o;
         const int x = bp.x0 + tx, y = bp.y0 + rr;
         if (x >= bp.width || y >= bp.height) continue;
-        const float* m = m2[o];
-        const float mx = m[0], my = m[1];
-        const float vx = m[2] - mx * mx, vy = m[3] - my * my, cxy = m[4] - mx * my;
+        const float mx = m[o][0], my = m[o][1];
+        const float vx = m[o][2] - mx * mx, vy = m[o][3] - my * my, cxy = m[o][4] - mx * my;
         const float A = 2.0f * mx * my + C1, B = 2.0f * cxy + C2;
         const float Cd = mx * mx + my * my + C1, D = vx + vy + C2;
         const float iCD = 1.0f / (Cd * D);
@@ -174,7 +189,8 @@ k_ssim_fwd(ViewTable vt, Win win, const float* __restrict__ img, const float* __
         maps[total_values + idx] = ds_dxx;
         maps[2 * total_values + idx] = ds_dxy;
         ss += s;
-        l1 += fabsf(sx[rr + kHalo][tx + kHalo] - sy[rr + kHalo][tx + kHalo]);
+        const float2 p = sxy[rr + kHalo][tx + kHalo];
+        l1 += fabsf(p.x - p.y);
     }
     const ViewGeom& g = vt.v[bp.view];
     const float invM = 1.0f / ((float)g.channels * (float)g.width * (float)g.height);
@@ -200,6 +216,8 @@ k_ssim_fwd(ViewTable vt, Win win, const float* __restrict__ img, const float* __
     }
 }
 
+// Backward: the three maps correlated with the window (two separable passes,
+// as the forward), combined per value with x and y, plus the L1 term.
 __global__ void __launch_bounds__(kLossThreads)
 k_ssim_bwd(ViewTable vt, Win win, const float* __restrict__ img, const float* __restrict__ tgt,
            float lambda, float inv_views, int64_t total_values, const float* __restrict__ maps,
@@ -207,7 +225,6 @@ k_ssim_bwd(ViewTable vt, Win win, const float* __restrict__ img, const float* __
     __shared__ float sm[3][kRows][kCols + 1];
     __shared__ float h[3][kRows][kTX + 1];
     const BlockPos bp = block_pos(vt, blockIdx.x);
-    constexpr int kLoads = (kRows * kCols + kLossThreads - 1) / kLossThreads;
     {
         float a[kLoads], b[kLoads], d[kLoads];
 #pragma unroll
@@ -263,27 +280,31 @@ k_ssim_bwd(ViewTable vt, Win win, const float* __restrict__ img, const float* __
     const ViewGeom& g = vt.v[bp.view];
     const float scale = inv_views / ((float)g.channels * (float)g.width * (float)g.height);
     const int tx = threadIdx.x & 31, ty = threadIdx.x >> 5;
-    const int r0 = 2 * ty;
-    float u2[2][3] = {{0.f, 0.f, 0.f}, {0.f, 0.f, 0.f}};
+    const int r0 = kOut * ty;
+    float m[kOut][3];
 #pragma unroll
-    for (int k = 0; k < kWin + 1; ++k) {
+    for (int o = 0; o < kOut; ++o)
+#pragma unroll
+        for (int q = 0; q < 3; ++q) m[o][q] = 0.0f;
+#pragma unroll
+    for (int k = 0; k < kWin + kOut - 1; ++k) {
 #pragma unroll
         for (int q = 0; q < 3; ++q) {
             const float hv = h[q][r0 + k][tx];
-            if (k < kWin) u2[0][q] = fmaf(win.w[k], hv, u2[0][q]);
-            if (k >= 1) u2[1][q] = fmaf(win.w[k - 1], hv, u2[1][q]);
+#pragma unroll
+            for (int o = 0; o < kOut; ++o)
+                if (k - o >= 0 && k - o < kWin) m[o][q] = fmaf(win.w[k - o], hv, m[o][q]);
         }
     }
 #pragma unroll
-    for (int o = 0; o < 2; ++o) {
+    for (int o = 0; o < kOut; ++o) {
         const int x = bp.x0 + tx, y = bp.y0 + r0 + o;
         if (x >= bp.width || y >= bp.height) continue;
-        const float a = u2[o][0], b = u2[o][1], d = u2[o][2];
         const int64_t idx = bp.plane + (int64_t)y * bp.width + x;
         const float xv = img[idx], yv = tgt[idx];
         const float diff = xv - yv;
         const float sgn = diff > 0.0f ? 1.0f : (diff < 0.0f ? -1.0f : 0.0f);
-        const float dssim = a + 2.0f * xv * b + yv * d;
+        const float dssim = m[o][0] + 2.0f * xv * m[o][1] + yv * m[o][2];
         dL[idx] = scale * ((1.0f - lambda) * sgn - lambda * dssim);
     }
 }
@@ -329,7 +350,7 @@ namespace gs {
 namespace {
 
 constexpr size_t kNoAllocMaxValues = size_t(1) << 20;  // image values (C*H*W over all views)
-constexpr int kNoAllocMaxBlocks = 8192;                // 32x16 loss tiles over all planes
+constexpr int kNoAllocMaxBlocks = 8192;                // 32x32 loss tiles over all planes
 constexpr size_t kNoAllocPartialsOffset = 256;         // after the counters
 constexpr size_t kNoAllocMapsOffset =
     kNoAllocPartialsOffset + ((size_t(kNoAllocMaxBlocks + 1) * 2 * sizeof(float) + 255) & ~size_t(255));
