@@ -314,10 +314,11 @@ def run_batched(args, ws):
     for mode in ("batched", "recompute", "per_view"):
         gm = mapping.GaussianMap(p)
         if mode in ("batched", "recompute"):
-            # recompute: the checkpointing plan, one view's projection and
-            # binning in the workspace, the 16 views one pass at a time
+            # recompute: the checkpointing plan, the projection and binning
+            # of 4 views in the workspace, the 16 views in 4 passes
             rast = mapping.fit_instance_capacity(views, gm, headroom=1.5,
-                                                 recompute=mode == "recompute", **cfg)
+                                                 recompute=4 if mode == "recompute" else 0,
+                                                 **cfg)
             it = mapping.MappingStep(gm, rast, rast.pack(targets), lam)
         else:
             it = mapping.PerViewLoop(gm, views, targets, lam, **cfg)
@@ -374,7 +375,7 @@ def run_streaming(args, ws):
     cfg = dict(tile=(args.tile_w, args.tile_h), smem_batch=args.batch,
                pixels_per_thread=args.ppt, smem_batch_bwd=args.batch_bwd,
                pixels_per_thread_bwd=args.ppt_bwd)
-    mapper = StreamingMapper(window=8, iters=30, lam=0.2, recompute=True,
+    mapper = StreamingMapper(window=8, iters=30, lam=0.2, recompute=4,
                              capacity=1 << 20, **cfg)
     stream = torch.cuda.current_stream()
     it_ms = 0.0
@@ -410,7 +411,7 @@ def run_streaming(args, ws):
                 workspace_bytes=int(final.workspace_bytes),
                 workspace_bytes_without_recompute=int(ws_keep),
                 config=dict(views="752x480x1 window of 8", points_per_keyframe=20_000,
-                            iterations_per_keyframe=30, recompute=True,
+                            iterations_per_keyframe=30, recompute="4 views per pass",
                             cuda_graph="one per keyframe (first iteration eager)",
                             tile=f"{args.tile_w}x{args.tile_h}", smem_batch=args.batch,
                             pixels_per_thread=args.ppt, smem_batch_bwd=args.batch_bwd,

@@ -126,17 +126,19 @@ typedef struct {
  *     (GS_DEV_SPAN_POOL if it runs out).  Only (Gaussian, tile) pairs that
  *     every pixel would skip are dropped: images and gradients are
  *     unchanged, the instance lists (and so last_idx) shorter.
- *   recompute: nonzero makes a recompute (checkpointing) plan: the
- *     workspace holds the projection and binning of ONE view, and nothing of
+ *   recompute: k > 0 makes a recompute (checkpointing) plan: the workspace
+ *     holds the projection and binning of at most k views, and nothing of
  *     them is kept from the forward to the backward -- only the images,
- *     final_T and last_idx, which the caller owns.  Views go through it one
- *     pass at a time (gs_plan_view_pass); the backward of a view re-runs its
- *     gs_project and gs_bin_sort (deterministic: the same buffers bit for
- *     bit) before gs_render_bwd*.  The SSIM maps of gs_loss_l1_ssim share
- *     their bytes with that region, so the loss overwrites it.
- *     instance_capacity is then the capacity of one view.  Against a plan
- *     holding all V views, the workspace shrinks by about (V - 1) x (200 B
- *     per Gaussian + 16 B per instance of a view) plus the loss maps.
+ *     final_T and last_idx, which the caller owns.  The views go through it
+ *     in passes of k (the last one fewer; gs_plan_view_pass); the backward of
+ *     a pass re-runs its gs_project and gs_bin_sort (deterministic: the same
+ *     buffers bit for bit) before gs_render_bwd*.  The SSIM maps of
+ *     gs_loss_l1_ssim share their bytes with that region, so the loss
+ *     overwrites it.  instance_capacity is then the capacity of one pass.
+ *     Against a plan holding all V views, the workspace shrinks by about
+ *     (V - k) x (200 B per Gaussian + 16 B per instance of a view) plus the
+ *     loss maps; k = 4 keeps the projection reading each Gaussian once per
+ *     4 views, as in a plan without recompute.
  * The tile shape changes which pixels a Gaussian can reach (its 3-sigma
  * rect is counted in whole tiles), hence the image; the batch sizes, pixels
  * per thread, tight_rect and recompute change only the speed and memory. */
@@ -178,23 +180,28 @@ gs_status gs_plan_init(gs_plan *plan, const gs_config *cfg, int32_t n_views,
 /* Bytes of device workspace the plan needs (256-byte aligned base). */
 size_t gs_plan_workspace_bytes(const gs_plan *plan);
 
-/* Recompute plans (gs_config.recompute; the benchmark spec's recompute-from-saved-
- * transmittance mode, no paper counterpart): fills *pass with the plan of
- * the single view v of `plan`, sharing its workspace layout.  The per-view
- * calls -- gs_project, gs_bin_sort, gs_render_fwd, gs_render_bwd,
- * gs_render_bwd_pixels, gs_project_bwd, gs_densify_stats -- take pass plans
- * (a recompute plan of one view is its own pass): they read the pose
- * views_dev[v] of the same views_dev array and write the images, final_T,
- * last_idx and dL of view v at its offsets in the packed buffers.
- * gs_loss_l1_ssim takes the whole plan.  Parameter gradients accumulate over
- * passes with accumulate = 1.  The device status word is reset by the
- * gs_project of view 0 only, so it gathers the bits of all passes; the
- * instance count (gs_read_counters) is that of the last pass.  The calls
- * that need every view at once (gs_project_bwd_groups, gs_project_bwd_adam,
- * gs_visibility) accept a recompute plan only when it has one view.
- * GS_ERR_INVALID if plan is not a recompute plan made by gs_plan_init or v
- * is out of range; pass may be plan itself. */
-gs_status gs_plan_view_pass(const gs_plan *plan, int32_t v, gs_plan *pass);
+/* Recompute plans (gs_config.recompute = k; the recompute-from-saved-
+ * transmittance checkpointing mode, no paper counterpart).
+ * gs_plan_passes: the number of passes of a plan, ceil(n_views / k) (1 for a
+ * plan without recompute or for a pass; 0 for an invalid plan).
+ * gs_plan_view_pass: fills *pass with the plan of pass p, the views
+ * [p k, min((p + 1) k, n_views)) of `plan`, sharing its workspace layout.
+ * The per-view calls -- gs_project, gs_bin_sort, gs_render_fwd,
+ * gs_render_bwd, gs_render_bwd_pixels, gs_project_bwd, gs_densify_stats --
+ * take pass plans (a recompute plan with at most k views is its own pass):
+ * they read the poses views_dev[p k ...] of the same views_dev array and
+ * write the images, final_T, last_idx and dL of those views at their
+ * offsets in the packed buffers.  gs_loss_l1_ssim takes the whole plan.
+ * Parameter gradients accumulate over passes with accumulate = 1.  The
+ * device status word is reset by the gs_project of pass 0 only, so it
+ * gathers the bits of all passes; the instance count (gs_read_counters) is
+ * that of the last pass.  The calls that need every view at once
+ * (gs_project_bwd_groups, gs_project_bwd_adam, gs_visibility) accept a
+ * recompute plan only when it has a single pass.  GS_ERR_INVALID if plan is
+ * not a recompute plan made by gs_plan_init or p is out of range; pass may
+ * be plan itself. */
+int32_t gs_plan_passes(const gs_plan *plan);
+gs_status gs_plan_view_pass(const gs_plan *plan, int32_t p, gs_plan *pass);
 
 /* Offsets of view v inside packed images (values: channels*H*W units) and
  * per-pixel maps (pixels: H*W units), its first global tile id and grid. */

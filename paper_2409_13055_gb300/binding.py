@@ -72,6 +72,7 @@ _SIGNATURES = {
                                c_int64]),
     "gs_plan_workspace_bytes": (c_size_t, [_P(gs_plan)]),
     "gs_plan_view_pass": (c_int32, [_P(gs_plan), c_int32, _P(gs_plan)]),
+    "gs_plan_passes": (c_int32, [_P(gs_plan)]),
     "gs_plan_view": (c_int32, [_P(gs_plan), c_int32, _P(c_int64), _P(c_int64), _P(c_int32),
                                _P(c_int32), _P(c_int32)]),
     "gs_plan_totals": (c_int32, [_P(gs_plan), _P(c_int64), _P(c_int64), _P(c_int32)]),
@@ -188,10 +189,14 @@ def gs_plan_workspace_bytes(plan) -> int:
     return int(lib().gs_plan_workspace_bytes(ctypes.byref(plan)))
 
 
-def gs_plan_view_pass(plan, v) -> gs_plan:
-    """The one-view pass plan of view v of a recompute plan."""
+def gs_plan_passes(plan) -> int:
+    return int(lib().gs_plan_passes(ctypes.byref(plan)))
+
+
+def gs_plan_view_pass(plan, k) -> gs_plan:
+    """The plan of pass k of a recompute plan."""
     out = gs_plan()
-    check(lib().gs_plan_view_pass(ctypes.byref(plan), int(v), ctypes.byref(out)),
+    check(lib().gs_plan_view_pass(ctypes.byref(plan), int(k), ctypes.byref(out)),
           "gs_plan_view_pass")
     return out
 

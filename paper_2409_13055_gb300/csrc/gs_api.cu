@@ -77,11 +77,13 @@ extern "C" gs_status gs_plan_init(gs_plan* plan, const gs_config* cfg, int32_t n
     p->vt.log2_tw = l2w;
     p->vt.log2_th = l2h;
     p->vt.tight_rect = cfg->tight_rect != 0;
-    p->recompute = cfg->recompute != 0;
+    if (cfg->recompute < 0) return GS_ERR_INVALID;
+    p->recompute = cfg->recompute;
     p->n_views_full = n_views;
     p->view_index = -1;
-    p->ws_views = p->recompute ? 1 : n_views;
-    int64_t tiles = 0, pixels = 0, values = 0, max_view_tiles = 0;
+    // views per pass: all of them, or at most `recompute` in a recompute plan
+    p->ws_views = (p->recompute && p->recompute < n_views) ? p->recompute : n_views;
+    int64_t tiles = 0, pixels = 0, values = 0, max_pass_tiles = 0, pass_tiles = 0;
     for (int v = 0; v < n_views; ++v) {
         const gs_view& vw = views_host[v];
         if (vw.width < 1 || vw.height < 1 || vw.width > 16384 || vw.height > 16384)
@@ -97,8 +99,9 @@ extern "C" gs_status gs_plan_init(gs_plan* plan, const gs_config* cfg, int32_t n
         g.pixel_offset = pixels;
         g.value_offset = values;
         tiles += (int64_t)g.tiles_x * g.tiles_y;
-        if ((int64_t)g.tiles_x * g.tiles_y > max_view_tiles)
-            max_view_tiles = (int64_t)g.tiles_x * g.tiles_y;
+        if (v % p->ws_views == 0) pass_tiles = 0;  // the first view of a pass
+        pass_tiles += (int64_t)g.tiles_x * g.tiles_y;
+        if (pass_tiles > max_pass_tiles) max_pass_tiles = pass_tiles;
         pixels += (int64_t)vw.width * vw.height;
         values += (int64_t)vw.width * vw.height * vw.channels;
     }
@@ -106,8 +109,8 @@ extern "C" gs_status gs_plan_init(gs_plan* plan, const gs_config* cfg, int32_t n
     p->total_tiles = (int32_t)tiles;
     p->total_pixels = pixels;
     p->total_values = values;
-    // tiles binned per call: all views', or one view's in a recompute plan
-    const int64_t bin_tiles = p->recompute ? max_view_tiles : tiles;
+    // tiles binned per call: all views', or one pass's in a recompute plan
+    const int64_t bin_tiles = max_pass_tiles;
     int bits = 0;
     while ((int64_t(1) << bits) < bin_tiles) ++bits;
     p->tile_bits = bits < 1 ? 1 : bits;
@@ -205,26 +208,44 @@ extern "C" gs_status gs_plan_init(gs_plan* plan, const gs_config* cfg, int32_t n
     return GS_OK;
 }
 
-extern "C" gs_status gs_plan_view_pass(const gs_plan* plan, int32_t v, gs_plan* pass) {
+extern "C" int32_t gs_plan_passes(const gs_plan* plan) {
+    if (!plan_ok(plan)) return 0;
+    const Plan* p = P(plan);
+    if (p->view_index >= 0) return 1;
+    return (p->n_views_full + p->ws_views - 1) / p->ws_views;
+}
+
+extern "C" gs_status gs_plan_view_pass(const gs_plan* plan, int32_t k, gs_plan* pass) {
     if (!plan_ok(plan) || !pass) return GS_ERR_INVALID;
     const Plan* p = P(plan);
     if (!p->recompute || p->view_index >= 0) return GS_ERR_INVALID;
-    if (v < 0 || v >= p->n_views_full) return GS_ERR_INVALID;
+    const int first = k * p->ws_views;
+    if (k < 0 || first >= p->n_views_full) return GS_ERR_INVALID;
+    const int count = p->n_views_full - first < p->ws_views ? p->n_views_full - first
+                                                           : p->ws_views;
+    ViewTable vt = p->vt;
     if (pass != plan) memcpy(pass, plan, sizeof(*plan));
     Plan* q = reinterpret_cast<Plan*>(pass);
-    const ViewGeom g = p->vt.v[v];
-    q->vt.n_views = 1;
-    q->vt.v[0] = g;
-    q->vt.v[0].tile_offset = 0;
-    q->vt.v[0].loss_block_offset = 0;
-    q->view_index = v;
-    q->total_tiles = g.tiles_x * g.tiles_y;
+    // views [first, first + count): their own tile ids and loss blocks from 0,
+    // their offsets in the packed images kept
+    int32_t tile = 0, blocks = 0;
+    q->vt.n_views = count;
+    for (int i = 0; i < count; ++i) {
+        ViewGeom g = vt.v[first + i];
+        g.tile_offset = tile;
+        g.loss_block_offset = blocks;
+        tile += g.tiles_x * g.tiles_y;
+        blocks += ((g.width + kLossTileW - 1) / kLossTileW) *
+                  ((g.height + kLossTileH - 1) / kLossTileH) * g.channels;
+        q->vt.v[i] = g;
+    }
+    q->view_index = first;
+    q->total_tiles = tile;
     int bits = 0;
     while ((int64_t(1) << bits) < q->total_tiles) ++bits;
     q->tile_bits = bits < 1 ? 1 : bits;
     q->tile_passes = (q->tile_bits + kRadixBits - 1) / kRadixBits;
-    q->loss_blocks = ((g.width + kLossTileW - 1) / kLossTileW) *
-                     ((g.height + kLossTileH - 1) / kLossTileH) * g.channels;
+    q->loss_blocks = blocks;
     return GS_OK;
 }
 

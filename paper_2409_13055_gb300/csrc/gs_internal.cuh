@@ -80,10 +80,11 @@ struct Plan {
     int64_t total_pixels, total_values;
     int32_t depth_sort_blocks, inst_sort_blocks, scan_blocks, loss_blocks;
     uint32_t span_pool_rows;  // capacity of B_SPAN_POOL (tight plans)
-    // Recompute plans (gs_config.recompute): the workspace holds one view's
-    // projection and binning (ws_views = 1); the plan itself covers all
-    // n_views_full views, a pass plan (gs_plan_view_pass) the view
-    // view_index (-1 in a plan made by gs_plan_init) with the same layout.
+    // Recompute plans (gs_config.recompute = views per pass): the workspace
+    // holds the projection and binning of ws_views views; the plan itself
+    // covers all n_views_full views, a pass plan (gs_plan_view_pass) the
+    // views from view_index on (-1 in a plan made by gs_plan_init), with the
+    // same layout.
     int32_t recompute, ws_views, n_views_full, view_index;
     size_t ws_bytes;
     size_t off[B_TOTAL];

@@ -11,9 +11,9 @@ Adam of Sec. IV-A) runs in libgs_gb300.so.
   buffers of the same layout -- so the fused Adam kernel is one pass and a
   later cross-GPU all-reduce of the gradient would be one call.
 * ``Rasterizer`` owns a plan and its workspace for one batch of views; a
-  recompute rasteriser (checkpointing) keeps one view's projection and
-  binning in its workspace, runs the views through it one at a time and
-  repeats a view's projection and binning in the backward.
+  recompute rasteriser (checkpointing) keeps the projection and binning of
+  a few views in its workspace, runs the views through it a pass at a time
+  and repeats a pass's projection and binning in the backward.
 * ``GSRender`` is the torch.autograd.Function over the rasteriser; with a
   recompute rasteriser only (final_T, last_idx) survive from the forward to
   the backward, and several of them may share one workspace.
@@ -294,7 +294,7 @@ def make_config(tile=(16, 16), smem_batch=128, near_z=0.2, bg=(0.0, 0.0, 0.0),
     return B.gs_config(int(tile[0]), int(tile[1]), int(smem_batch), int(pixels_per_thread),
                        int(smem_batch_bwd), int(pixels_per_thread_bwd), float(near_z),
                        (B.c_float * 3)(*[float(x) for x in bg]), int(bool(density_stats)),
-                       int(bool(deterministic)), int(bool(tight_rect)), int(bool(recompute)))
+                       int(bool(deterministic)), int(bool(tight_rect)), int(recompute))
 
 
 def plan_workspace_bytes(views, n_capacity, instance_capacity, **cfg) -> int:
@@ -309,10 +309,10 @@ class Rasterizer:
     """Plan + workspace + output buffers for one batch of views.
 
     recompute: a checkpointing plan (gs_config.recompute): the workspace
-    holds one view's projection and binning; forward() and render_bwd() run
-    the views one pass at a time, and the backward repeats each view's
-    projection and binning (bit-identical) before its adjoint.  instance
-    capacity is then per view.  workspace: a uint8 CUDA tensor to use
+    holds the projection and binning of `recompute` views (True: one);
+    forward() and render_bwd() run the views in passes of that many, and
+    the backward repeats each pass's projection and binning (bit-identical)
+    before its adjoint.  instance capacity is then per pass.  workspace: a uint8 CUDA tensor to use
     instead of allocating one (at least workspace_bytes long); recompute
     rasterisers used one after the other may share one, since nothing in
     it outlives a call sequence."""
@@ -323,23 +323,26 @@ class Rasterizer:
                  tight_rect=True, recompute=False, workspace=None, device="cuda"):
         self.views = list(views)
         self.device = torch.device(device)
+        self.views_per_pass = (int(recompute) if recompute else len(self.views))
         self.recompute = bool(recompute)
         self.cfg = make_config(tile, smem_batch, near_z, bg, pixels_per_thread, smem_batch_bwd,
                                pixels_per_thread_bwd, density_stats, deterministic, tight_rect,
-                               self.recompute)
+                               self.views_per_pass if self.recompute else 0)
         self.n_capacity = int(n_capacity)
         if instance_capacity is None:
+            k = self.views_per_pass
             sizes = [v["width"] * v["height"] for v in self.views]
-            px = max(sizes) if self.recompute else sum(sizes)  # pixels binned per call
+            px = max(sum(sizes[i:i + k]) for i in range(0, len(sizes), k))  # per binning call
             instance_capacity = max(1 << 20, 4 * px, 8 * n_capacity)
         self.instance_capacity = int(instance_capacity)
         self.host_views, self.views_dev = views_to_device(self.views, self.device)
         self.plan = B.gs_plan_init(self.cfg, list(self.host_views), self.n_capacity,
                                    self.instance_capacity)
-        # the plans the per-view calls take: the plan itself, or one pass per
-        # view of a recompute plan of several views
-        if self.recompute and len(self.views) > 1:
-            self.passes = [B.gs_plan_view_pass(self.plan, v) for v in range(len(self.views))]
+        # the plans the per-view calls take: the plan itself, or the passes of
+        # a recompute plan whose views do not fit one pass
+        n_passes = B.gs_plan_passes(self.plan)
+        if self.recompute and n_passes > 1:
+            self.passes = [B.gs_plan_view_pass(self.plan, k) for k in range(n_passes)]
         else:
             self.passes = [self.plan]
         self.workspace_bytes = B.gs_plan_workspace_bytes(self.plan)
@@ -382,15 +385,15 @@ class Rasterizer:
         return torch.cat(flat).to(self.device)
 
     def buffer(self, buf_id, dtype=torch.uint8, view=None):
-        """A workspace buffer (of the pass of `view` in a recompute plan)."""
+        """A workspace buffer (of pass `view` in a recompute plan)."""
         off, nbytes = B.gs_plan_buffer(self._pass(view), buf_id)
         return self.ws[off:off + nbytes].view(dtype)
 
     def _pass(self, view):
         if view is None:
             if len(self.passes) > 1:
-                raise ValueError("a recompute plan of several views runs one view at a time: "
-                                 "pass view=")
+                raise ValueError("a recompute plan of several passes runs one pass at a time: "
+                                 "pass view= (the pass index)")
             return self.passes[0]
         return self.passes[view]
 
@@ -399,7 +402,7 @@ class Rasterizer:
         arr, dev = views_to_device(views, self.device)
         self.views_dev.copy_(dev)
 
-    # the C-ABI steps (view: the pass of a recompute plan) ----------------------
+    # the C-ABI steps (view: the pass index of a recompute plan) ----------------
     def project(self, gmap: B.gs_map, stream=None, view=None):
         B.gs_project(self._pass(view), gmap, self.views_dev, self.ws, stream)
 
@@ -412,8 +415,8 @@ class Rasterizer:
                         self.last_idx if last_idx is None else last_idx, stream)
 
     def forward(self, gmap: B.gs_map, stream=None, images=None, final_T=None, last_idx=None):
-        """Projection, binning and compositing of every view (one pass per
-        view in a recompute plan of several views)."""
+        """Projection, binning and compositing of every view (pass by pass in
+        a recompute plan)."""
         for v in range(len(self.passes)):
             self.project(gmap, stream, view=v)
             self.bin_sort(gmap.n, stream, view=v)
@@ -438,7 +441,7 @@ class Rasterizer:
     def render_bwd(self, gmap: B.gs_map, grads: B.gs_map_grad, dL=None, final_T=None,
                    last_idx=None, accumulate=False, stream=None):
         """Pixel and projection adjoints of every view; in a recompute plan
-        each view's projection and binning are run again first."""
+        each pass's projection and binning are run again first."""
         args = (self.final_T if final_T is None else final_T,
                 self.last_idx if last_idx is None else last_idx, self.dL if dL is None else dL)
         for v, pl in enumerate(self.passes):
@@ -600,13 +603,13 @@ class MappingStep:
         # recompute: the checkpointed backward -- projection and binning are
         # run again (bit-identically) between the loss and the adjoint.  With
         # a recompute rasteriser (the default then) the views go through its
-        # one-view workspace one pass at a time; recompute=True with another
-        # rasteriser re-runs them into the same workspace
+        # workspace a pass at a time; recompute=True with another rasteriser
+        # re-runs them into the same workspace
         self.recompute = rast.recompute if recompute is None else bool(recompute)
         self.passes = len(rast.passes) if rast.recompute else 1
         if self.passes > 1 and (fused or sparse_adam):
             raise ValueError("the fused and visibility-masked steps need every view at once; "
-                             "a recompute rasteriser of several views runs one view at a time")
+                             "a recompute rasteriser of several passes runs them a pass at a time")
         # without keep_grads the gradient of groups of GS_GRAD_GROUP Gaussians
         # that touch no tile (all zero) is neither written nor read
         self.groups = (not keep_grads and not fused and self.visible is None
@@ -632,9 +635,9 @@ class MappingStep:
         r = self.rast
         r.loss_l1_ssim(self.targets, self.lam, stream=stream)
         if r.recompute and self.passes > 1:
-            # one view at a time through the one-view workspace: its
-            # projection and binning again, its pixel and projection
-            # adjoints (gradients summed over the views), its statistic
+            # a pass at a time through the workspace: its projection and
+            # binning again, its pixel and projection adjoints (gradients
+            # summed over the passes), its statistic
             for v in range(self.passes):
                 r.project(self._m, stream, view=v)
                 r.bin_sort(self.gmap.n, stream, view=v)

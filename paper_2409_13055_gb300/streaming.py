@@ -13,8 +13,8 @@ Per keyframe:
   3. ``iters`` batched mapping iterations run over the whole window, each one
      ``MappingStep`` (project, bin, render, loss, backward, Adam), by default
      on a recompute rasteriser (checkpointing: the window's views go through a
-     one-view workspace one at a time, and the backward repeats each view's
-     projection and binning), captured as one CUDA graph and replayed;
+     workspace of four views a pass at a time, and the backward repeats each
+     pass's projection and binning), captured as one CUDA graph and replayed;
      with Gaussian-pyramid targets (Sec. III-B) the iterations go from the
      coarsest level to the full resolution.
 
@@ -35,10 +35,12 @@ class StreamingMapper:
     iterations run coarse to fine, see ``pyramid.level_for``)."""
 
     def __init__(self, degree=3, window=8, iters=30, lam=0.2, lr=None, extent=1.0,
-                 recompute=True, capacity=1 << 20, instance_headroom=1.25, graphs=True,
+                 recompute=4, capacity=1 << 20, instance_headroom=1.25, graphs=True,
                  pyramid_levels=1, device="cuda", **rast_kw):
+        # recompute: views per pass of the checkpointing rasteriser (True:
+        # 1, False/0: none, every view's projection kept)
         self.degree, self.window, self.iters, self.lam = int(degree), int(window), int(iters), lam
-        self.lr, self.extent, self.recompute = lr, extent, bool(recompute)
+        self.lr, self.extent, self.recompute = lr, extent, int(recompute)
         self.capacity, self.headroom, self.graphs = int(capacity), float(instance_headroom), graphs
         self.levels = max(1, int(pyramid_levels))
         self.device = torch.device(device)

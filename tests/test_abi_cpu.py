@@ -134,7 +134,19 @@ def test_recompute_plans_hold_one_view_and_run_passes(lib):
         for b in range(B.GS_BUF_ABSGRAD + 1):
             assert B.gs_plan_buffer(ps, b) == B.gs_plan_buffer(rec, b) or b in (
                 B.GS_BUF_TILE_KEYS, B.GS_BUF_TILE_VALUES)
+    assert B.gs_plan_passes(rec) == 3 and B.gs_plan_passes(full) == 1
+    # passes of two views: [0, 1] and [2]
+    two = B.gs_plan_init(_cfg(tw=8, th=8, recompute=2), vs, n, icap)
+    assert B.gs_plan_passes(two) == 2
+    p0, p1 = B.gs_plan_view_pass(two, 0), B.gs_plan_view_pass(two, 1)
+    v1 = B.gs_plan_view(rec, 1)
+    assert B.gs_plan_totals(p0)["total_tiles"] == 80 * 60 + 94 * 60  # 640x480 and 752x480 at 8x8
+    assert B.gs_plan_view(p0, 1)["tile_offset"] == 80 * 60
+    assert B.gs_plan_view(p0, 1)["value_offset"] == v1["value_offset"]
+    assert B.gs_plan_view(p1, 0)["value_offset"] == B.gs_plan_view(rec, 2)["value_offset"]
+    assert wr < B.gs_plan_workspace_bytes(two) < wf
     bad = B.gs_plan()
+    assert lib.gs_plan_view_pass(ctypes.byref(two), 2, ctypes.byref(bad)) == B.GS_ERR_INVALID
     assert lib.gs_plan_view_pass(ctypes.byref(full), 0, ctypes.byref(bad)) == B.GS_ERR_INVALID
     assert lib.gs_plan_view_pass(ctypes.byref(rec), 3, ctypes.byref(bad)) == B.GS_ERR_INVALID
     ps = B.gs_plan_view_pass(rec, 1)
