@@ -10,9 +10,10 @@ target rendered from a perturbed copy of the map.  Inputs are resident in HBM
 for `value`; `e2e` adds, per step, the pinned-host -> device copy of the
 step's target image and pose and the device -> host read of the loss.
 
-The timed region replays the iteration as seven CUDA graphs (one per stage)
-with CUDA events between them on the launching stream, so every stage's
-device time comes from the timed region itself.  The working set (map,
+The timed region replays one CUDA graph of the whole iteration per step, with
+CUDA events around the K steps on the launching stream; the per-stage times
+come from a separate pass that replays one graph per stage with events
+between them.  The working set (map,
 gradients, Adam moments: ~0.95 GB, plus the workspace) is far larger than the
 129 MB L2, so no explicit flush is needed between steps.
 
