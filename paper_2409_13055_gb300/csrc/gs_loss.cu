@@ -9,8 +9,10 @@
 //
 // Two kernels, each over 32x32 output tiles of every channel plane of every
 // view.  The forward stages the tile plus a 5-pixel halo of both images in
-// shared memory and forms the five window moments (E[x], E[y], E[x^2],
-// E[y^2], E[xy]) with separable 11-tap passes; per pixel it keeps the partial
+// shared memory and forms the window moments E[x], E[y], E[xy] and
+// E[x^2 + y^2] with separable 11-tap passes (E[x^2] and E[y^2] enter SSIM
+// only through the sum of the variances, and the derivative with respect to
+// E[x^2] is the one with respect to that sum); per pixel it keeps the partial
 // derivatives of SSIM with respect to E[x], E[x^2] and E[xy].  The backward
 // correlates those three maps with the same window (the adjoint of a
 // zero-padded symmetric correlation is itself) and adds the L1 term.  The
@@ -72,43 +74,71 @@ __device__ __forceinline__ float block_sum(float x, float* red) {
     return t;  // valid in thread 0
 }
 
-// Loads of the tile and its halo issued by every thread before any store.
-constexpr int kLoads = (kRows * kCols + kLossThreads - 1) / kLossThreads;
+// The tile and its halo are loaded row by row: warp w takes rows w, w + 8,
+// ... (kRowIters of them), lane l columns l and 32 + l (the latter for the
+// 10 halo columns only); every load of a thread is issued before its stores.
+constexpr int kWarpsL = kLossThreads / 32;
+constexpr int kRowIters = (kRows + kWarpsL - 1) / kWarpsL;  // 6
+static_assert(kCols - 32 <= 32, "two columns per lane");
 
-// Forward: the five window moments of every output value by two separable
+struct RowLoader {
+    int lane, warp;
+    bool ok_a, ok_b;  // columns lane and 32 + lane inside the image (and the halo)
+    int xa;
+    __device__ __forceinline__ RowLoader(const BlockPos& bp) {
+        lane = threadIdx.x & 31;
+        warp = threadIdx.x >> 5;
+        xa = bp.x0 - kHalo + lane;
+        ok_a = xa >= 0 && xa < bp.width;
+        ok_b = lane < kCols - 32 && xa + 32 >= 0 && xa + 32 < bp.width;
+    }
+    // global offset of tile row r's column lane (which may lie left of the
+    // image: then ok_a is false); row_ok: the row is inside the halo and the image
+    __device__ __forceinline__ int64_t row_base(const BlockPos& bp, int r, bool& row_ok) const {
+        const int y = bp.y0 - kHalo + r;
+        row_ok = r < kRows && y >= 0 && y < bp.height;
+        return bp.plane + (int64_t)y * bp.width + xa;
+    }
+};
+
+// Forward: the four window moments of every output value by two separable
 // 11-tap passes (horizontal over the tile's 42 halo rows, then vertical),
 // SSIM, and its partial derivatives with respect to E[x], E[x^2] and E[xy]
 // (the maps the backward correlates).  x and y share one float2 of shared
-// memory; the horizontal pass forms x^2, y^2 and xy once per input value.
-__global__ void __launch_bounds__(kLossThreads)
+// memory; the horizontal pass forms x^2 + y^2 and xy once per input value.
+__global__ void __launch_bounds__(kLossThreads, 5)
 k_ssim_fwd(ViewTable vt, Win win, const float* __restrict__ img, const float* __restrict__ tgt,
            float lambda, float inv_views, int64_t total_values, float* __restrict__ maps,
            float* __restrict__ partials, int nblocks, DevCounters* ctr,
            float* __restrict__ loss_dev) {
     __shared__ float2 sxy[kRows][kCols + 1];
-    __shared__ float h[5][kRows][kTX + 1];
+    __shared__ float h[4][kRows][kTX + 1];
     __shared__ float red[32];
     __shared__ bool is_last;
     const BlockPos bp = block_pos(vt, blockIdx.x);
     {
-        float a[kLoads], b[kLoads];
+        const RowLoader ld(bp);
+        float a[kRowIters], b[kRowIters], c[kRowIters], d[kRowIters];
 #pragma unroll
-        for (int it = 0; it < kLoads; ++it) {
-            const int i = threadIdx.x + it * kLossThreads;
-            const int r = i / kCols, c = i - r * kCols;
-            const int y = bp.y0 - kHalo + r, x = bp.x0 - kHalo + c;
-            a[it] = b[it] = 0.0f;
-            if (i < kRows * kCols && x >= 0 && x < bp.width && y >= 0 && y < bp.height) {
-                a[it] = img[bp.plane + (int64_t)y * bp.width + x];
-                b[it] = tgt[bp.plane + (int64_t)y * bp.width + x];
+        for (int k = 0; k < kRowIters; ++k) {
+            bool row_ok;
+            const int64_t base = ld.row_base(bp, ld.warp + kWarpsL * k, row_ok);
+            a[k] = b[k] = c[k] = d[k] = 0.0f;
+            if (row_ok && ld.ok_a) {
+                a[k] = img[base];
+                b[k] = tgt[base];
+            }
+            if (row_ok && ld.ok_b) {
+                c[k] = img[base + 32];
+                d[k] = tgt[base + 32];
             }
         }
 #pragma unroll
-        for (int it = 0; it < kLoads; ++it) {
-            const int i = threadIdx.x + it * kLossThreads;
-            if (i < kRows * kCols) {
-                const int r = i / kCols, c = i - r * kCols;
-                sxy[r][c] = make_float2(a[it], b[it]);
+        for (int k = 0; k < kRowIters; ++k) {
+            const int r = ld.warp + kWarpsL * k;
+            if (r < kRows) {
+                sxy[r][ld.lane] = make_float2(a[k], b[k]);
+                if (ld.lane < kCols - 32) sxy[r][32 + ld.lane] = make_float2(c[k], d[k]);
             }
         }
     }
@@ -117,34 +147,30 @@ k_ssim_fwd(ViewTable vt, Win win, const float* __restrict__ img, const float* __
     // reading their kSeg + 10 inputs once
     for (int i = threadIdx.x; i < kRows * (kTX / kSeg); i += blockDim.x) {
         const int r = i / (kTX / kSeg), c0 = (i - r * (kTX / kSeg)) * kSeg;
-        float u[kSeg + kWin - 1], v[kSeg + kWin - 1], uu[kSeg + kWin - 1], vv[kSeg + kWin - 1],
-            uv[kSeg + kWin - 1];
+        float u[kSeg + kWin - 1], v[kSeg + kWin - 1], sq[kSeg + kWin - 1], uv[kSeg + kWin - 1];
 #pragma unroll
         for (int k = 0; k < kSeg + kWin - 1; ++k) {
             const float2 p = sxy[r][c0 + k];
             u[k] = p.x;
             v[k] = p.y;
-            uu[k] = p.x * p.x;
-            vv[k] = p.y * p.y;
+            sq[k] = fmaf(p.x, p.x, p.y * p.y);
             uv[k] = p.x * p.y;
         }
 #pragma unroll
         for (int o = 0; o < kSeg; ++o) {
-            float mx = 0.f, my = 0.f, xx = 0.f, yy = 0.f, xy = 0.f;
+            float mx = 0.f, my = 0.f, ss = 0.f, xy = 0.f;
 #pragma unroll
             for (int k = 0; k < kWin; ++k) {
                 const float w = win.w[k];
                 mx = fmaf(w, u[o + k], mx);
                 my = fmaf(w, v[o + k], my);
-                xx = fmaf(w, uu[o + k], xx);
-                yy = fmaf(w, vv[o + k], yy);
+                ss = fmaf(w, sq[o + k], ss);
                 xy = fmaf(w, uv[o + k], xy);
             }
             h[0][r][c0 + o] = mx;
             h[1][r][c0 + o] = my;
-            h[2][r][c0 + o] = xx;
-            h[3][r][c0 + o] = yy;
-            h[4][r][c0 + o] = xy;
+            h[2][r][c0 + o] = ss;
+            h[3][r][c0 + o] = xy;
         }
     }
     __syncthreads();
@@ -154,15 +180,15 @@ k_ssim_fwd(ViewTable vt, Win win, const float* __restrict__ img, const float* __
     // vertical pass: a thread takes kOut consecutive rows of one column,
     // reading their kOut + 10 rows of horizontal sums once
     const int r0 = kOut * ty;
-    float m[kOut][5];
+    float m[kOut][4];
 #pragma unroll
     for (int o = 0; o < kOut; ++o)
 #pragma unroll
-        for (int q = 0; q < 5; ++q) m[o][q] = 0.0f;
+        for (int q = 0; q < 4; ++q) m[o][q] = 0.0f;
 #pragma unroll
     for (int k = 0; k < kWin + kOut - 1; ++k) {
 #pragma unroll
-        for (int q = 0; q < 5; ++q) {
+        for (int q = 0; q < 4; ++q) {
             const float hv = h[q][r0 + k][tx];
 #pragma unroll
             for (int o = 0; o < kOut; ++o)
@@ -175,14 +201,17 @@ k_ssim_fwd(ViewTable vt, Win win, const float* __restrict__ img, const float* __
         const int x = bp.x0 + tx, y = bp.y0 + rr;
         if (x >= bp.width || y >= bp.height) continue;
         const float mx = m[o][0], my = m[o][1];
-        const float vx = m[o][2] - mx * mx, vy = m[o][3] - my * my, cxy = m[o][4] - mx * my;
+        const float mm = fmaf(mx, mx, my * my);
+        const float vxy = m[o][2] - mm, cxy = m[o][3] - mx * my;  // sum of variances, covariance
         const float A = 2.0f * mx * my + C1, B = 2.0f * cxy + C2;
-        const float Cd = mx * mx + my * my + C1, D = vx + vy + C2;
+        const float Cd = mm + C1, D = vxy + C2;
+        // one division: 1/Cd = D/(Cd D), 1/D = Cd/(Cd D) (Cd >= C1, D >= C2)
         const float iCD = 1.0f / (Cd * D);
+        const float iC = D * iCD, iD = Cd * iCD;
         const float s = A * B * iCD;
         // dSSIM/dE[x], dSSIM/dE[x^2], dSSIM/dE[xy] (E[y], E[y^2] held fixed)
-        const float ds_dm = (2.0f * my * B - 2.0f * my * A) * iCD - s * (2.0f * mx / Cd - 2.0f * mx / D);
-        const float ds_dxx = -s / D;
+        const float ds_dm = 2.0f * my * (B - A) * iCD - 2.0f * mx * s * (iC - iD);
+        const float ds_dxx = -s * iD;
         const float ds_dxy = 2.0f * A * iCD;
         const int64_t idx = bp.plane + (int64_t)y * bp.width + x;
         maps[idx] = ds_dm;
@@ -218,36 +247,60 @@ k_ssim_fwd(ViewTable vt, Win win, const float* __restrict__ img, const float* __
 
 // Backward: the three maps correlated with the window (two separable passes,
 // as the forward), combined per value with x and y, plus the L1 term.
-__global__ void __launch_bounds__(kLossThreads)
+__global__ void __launch_bounds__(kLossThreads, 5)
 k_ssim_bwd(ViewTable vt, Win win, const float* __restrict__ img, const float* __restrict__ tgt,
            float lambda, float inv_views, int64_t total_values, const float* __restrict__ maps,
            float* __restrict__ dL) {
     __shared__ float sm[3][kRows][kCols + 1];
     __shared__ float h[3][kRows][kTX + 1];
     const BlockPos bp = block_pos(vt, blockIdx.x);
-    {
-        float a[kLoads], b[kLoads], d[kLoads];
+    const int tx = threadIdx.x & 31, ty = threadIdx.x >> 5;
+    const int r0 = kOut * ty;
+    // this thread's output values of both images, loaded with the maps
+    float xo[kOut], yo[kOut];
 #pragma unroll
-        for (int it = 0; it < kLoads; ++it) {
-            const int i = threadIdx.x + it * kLossThreads;
-            const int r = i / kCols, c = i - r * kCols;
-            const int y = bp.y0 - kHalo + r, x = bp.x0 - kHalo + c;
-            a[it] = b[it] = d[it] = 0.0f;
-            if (i < kRows * kCols && x >= 0 && x < bp.width && y >= 0 && y < bp.height) {
-                const int64_t idx = bp.plane + (int64_t)y * bp.width + x;
-                a[it] = maps[idx];
-                b[it] = maps[total_values + idx];
-                d[it] = maps[2 * total_values + idx];
-            }
+    for (int o = 0; o < kOut; ++o) {
+        const int x = bp.x0 + tx, y = bp.y0 + r0 + o;
+        xo[o] = yo[o] = 0.0f;
+        if (x < bp.width && y < bp.height) {
+            xo[o] = img[bp.plane + (int64_t)y * bp.width + x];
+            yo[o] = tgt[bp.plane + (int64_t)y * bp.width + x];
         }
+    }
+    {
+        // the three maps over the tile and its halo, in two halves of rows
+        const RowLoader ld(bp);
+        constexpr int kHalf = (kRowIters + 1) / 2;
 #pragma unroll
-        for (int it = 0; it < kLoads; ++it) {
-            const int i = threadIdx.x + it * kLossThreads;
-            if (i < kRows * kCols) {
-                const int r = i / kCols, c = i - r * kCols;
-                sm[0][r][c] = a[it];
-                sm[1][r][c] = b[it];
-                sm[2][r][c] = d[it];
+        for (int h0 = 0; h0 < kRowIters; h0 += kHalf) {
+            float a[kHalf][2], b[kHalf][2], d[kHalf][2];
+#pragma unroll
+            for (int k = 0; k < kHalf; ++k) {
+                bool row_ok;
+                const int64_t base = ld.row_base(bp, ld.warp + kWarpsL * (h0 + k), row_ok);
+#pragma unroll
+                for (int s = 0; s < 2; ++s) {
+                    a[k][s] = b[k][s] = d[k][s] = 0.0f;
+                    if (row_ok && (s == 0 ? ld.ok_a : ld.ok_b)) {
+                        const int64_t idx = base + 32 * s;
+                        a[k][s] = maps[idx];
+                        b[k][s] = maps[total_values + idx];
+                        d[k][s] = maps[2 * total_values + idx];
+                    }
+                }
+            }
+#pragma unroll
+            for (int k = 0; k < kHalf; ++k) {
+                const int r = ld.warp + kWarpsL * (h0 + k);
+                if (r < kRows) {
+#pragma unroll
+                    for (int s = 0; s < 2; ++s) {
+                        if (s == 1 && ld.lane >= kCols - 32) continue;
+                        sm[0][r][32 * s + ld.lane] = a[k][s];
+                        sm[1][r][32 * s + ld.lane] = b[k][s];
+                        sm[2][r][32 * s + ld.lane] = d[k][s];
+                    }
+                }
             }
         }
     }
@@ -279,8 +332,6 @@ k_ssim_bwd(ViewTable vt, Win win, const float* __restrict__ img, const float* __
     __syncthreads();
     const ViewGeom& g = vt.v[bp.view];
     const float scale = inv_views / ((float)g.channels * (float)g.width * (float)g.height);
-    const int tx = threadIdx.x & 31, ty = threadIdx.x >> 5;
-    const int r0 = kOut * ty;
     float m[kOut][3];
 #pragma unroll
     for (int o = 0; o < kOut; ++o)
@@ -301,7 +352,7 @@ k_ssim_bwd(ViewTable vt, Win win, const float* __restrict__ img, const float* __
         const int x = bp.x0 + tx, y = bp.y0 + r0 + o;
         if (x >= bp.width || y >= bp.height) continue;
         const int64_t idx = bp.plane + (int64_t)y * bp.width + x;
-        const float xv = img[idx], yv = tgt[idx];
+        const float xv = xo[o], yv = yo[o];
         const float diff = xv - yv;
         const float sgn = diff > 0.0f ? 1.0f : (diff < 0.0f ? -1.0f : 0.0f);
         const float dssim = m[o][0] + 2.0f * xv * m[o][1] + yv * m[o][2];
