@@ -160,7 +160,8 @@ extern "C" gs_status gs_plan_init(gs_plan* plan, const gs_config* cfg, int32_t n
     len[B_LOSS_BLOCKS] = (size_t)(p->loss_blocks + 1) * 2 * sizeof(float);
     len[B_GCOL] = (size_t)VN * 3 * sizeof(float);
     len[B_OFFSETS] = (size_t)(VN + 1) * sizeof(uint32_t);
-    len[B_TILE_ORDER] = (size_t)bin_tiles * sizeof(uint32_t);
+    // the order, then the counts and cursors of its length buckets
+    len[B_TILE_ORDER] = ((size_t)bin_tiles + 2 * kOrderBuckets) * sizeof(uint32_t);
     len[B_TILE_QUEUE] = 2 * sizeof(uint32_t);
     len[B_SPANS] = cfg->tight_rect ? (size_t)VN * kSpanRows * sizeof(uint32_t) : 0;
     // boxes of more than kSpanRows tile rows are rare (4 of 446k visible

@@ -15,6 +15,7 @@
 namespace gs {
 
 constexpr uint32_t kPlanMagic = 0x67733330u;  // "gs30"
+constexpr int kOrderBuckets = 33;  // tile-order buckets: bit length of a list length
 constexpr int kRadixBits = 8;
 constexpr int kRadix = 1 << kRadixBits;
 constexpr int kSortThreads = 256;
@@ -58,7 +59,8 @@ enum PrivBuf {
     B_LOSS_BLOCKS,
     B_GCOL,     // [V*n] x 3: colour gradient as it reaches the SH coefficients
     B_OFFSETS,  // [V*n + 1] instance offsets of the entries in depth order
-    B_TILE_ORDER,  // [total_tiles] render order of the tiles, longest lists first
+    B_TILE_ORDER,  // [total_tiles] render order of the tiles, longest lists first;
+                   // then 2 x kOrderBuckets words of scratch for building it
     B_TILE_QUEUE,  // [2] u32 next-tile counters of the forward and backward render
     B_GID_OF,      // [instance_capacity] u32 (view*n + index) of each emitted instance
                    // (deterministic plans: the sort then carries emission positions)

@@ -140,6 +140,17 @@ k_radix_scatter(const uint32_t* __restrict__ keys_in, const uint32_t* __restrict
     const uint32_t start = blockIdx.x * (uint32_t)TILE;
     if (start >= count) return;
     const int tid = threadIdx.x, lane = tid & 31, w = tid >> 5;
+    // the block's keys and values are loaded first, so that their latency
+    // overlaps the loads and the scan of the digit offsets below
+    uint32_t key[ITEMS], val[ITEMS], rank[ITEMS];
+    const uint32_t wstart = start + (uint32_t)w * kWarpItems;
+#pragma unroll
+    for (int r = 0; r < ITEMS; ++r) {
+        const uint32_t i = wstart + (uint32_t)r * 32u + lane;
+        const bool in = i < count;
+        key[r] = in ? keys_in[i] : 0u;
+        val[r] = in ? (vals_in ? vals_in[i] : i) : 0u;
+    }
     {
         uint32_t tot;
         uint32_t ex = block_exclusive_scan(totals[tid], wt, tot);
@@ -150,15 +161,11 @@ k_radix_scatter(const uint32_t* __restrict__ keys_in, const uint32_t* __restrict
     for (int k = 0; k < kWarps; ++k) wcnt[k][tid] = 0u;
     __syncthreads();
 
-    uint32_t key[ITEMS], val[ITEMS], rank[ITEMS];
     const uint32_t lt = (1u << lane) - 1u;
-    const uint32_t wstart = start + (uint32_t)w * kWarpItems;
 #pragma unroll
     for (int r = 0; r < ITEMS; ++r) {
         const uint32_t i = wstart + (uint32_t)r * 32u + lane;
         const bool in = i < count;
-        key[r] = in ? keys_in[i] : 0u;
-        val[r] = in ? (vals_in ? vals_in[i] : i) : 0u;
         const bool ok = in && !(drop && key[r] == kCulledKey);
         const uint32_t d = ok ? ((key[r] >> shift) & (kRadix - 1)) : 0x10000u;
         const uint32_t peers = __match_any_sync(0xffffffffu, d);
@@ -306,7 +313,7 @@ k_emit(const uint32_t* __restrict__ order, const uint32_t* __restrict__ off,
     __shared__ uint2 s_rect[kEmitEntries];
     // tight rects: the entry's row spans (boxes of at most kSpanRows rows),
     // or, for a taller box, the pool index of its first row in s_span[e][0]
-    __shared__ uint32_t s_span[kEmitEntries][kSpanRows];
+    __shared__ __align__(16) uint32_t s_span[kEmitEntries][kSpanRows];
     __shared__ uint16_t s_view[kEmitEntries];
     const uint32_t count = *count_dev;
     const uint32_t e0 = blockIdx.x * (uint32_t)kEmitEntries;
@@ -323,7 +330,10 @@ k_emit(const uint32_t* __restrict__ order, const uint32_t* __restrict__ off,
             const uint2 rc = s_rect[e];
             const int rows = (int)(rc.y >> 16) - (int)(rc.x >> 16);
             const int nw = rows > kSpanRows ? 1 : rows;
-            for (int r = 0; r < nw; ++r) s_span[e][r] = spans[(size_t)vg * kSpanRows + r];
+            // whole 16-byte groups of the entry's 64-byte span record
+            const uint4* src = reinterpret_cast<const uint4*>(spans + (size_t)vg * kSpanRows);
+            uint4* dst = reinterpret_cast<uint4*>(s_span[e]);
+            for (int q = 0; q < (nw + 3) / 4; ++q) dst[q] = src[q];
         }
     }
     if (e == 0) s_off[ne] = off[e0 + ne];
@@ -372,8 +382,10 @@ k_emit(const uint32_t* __restrict__ order, const uint32_t* __restrict__ off,
 }
 
 __global__ void k_ranges(const uint32_t* __restrict__ keys, const uint32_t* count_dev,
-                         uint32_t* __restrict__ ranges) {
+                         uint32_t* __restrict__ ranges, uint32_t* __restrict__ order_scratch) {
     grid_dep_begin();
+    // the tile order's bucket counts and cursors start at zero
+    if (blockIdx.x == 0 && threadIdx.x < 2 * kOrderBuckets) order_scratch[threadIdx.x] = 0u;
     const uint32_t count = *count_dev;
     for (uint32_t i = blockIdx.x * blockDim.x + threadIdx.x; i < count;
          i += gridDim.x * blockDim.x) {
@@ -386,10 +398,11 @@ __global__ void k_ranges(const uint32_t* __restrict__ keys, const uint32_t* coun
 // Heavy-first order of the tiles for the render kernels: tiles bucketed by
 // the bit length of their list length, longest bucket first, so the CTAs of
 // the longest lists start in the first wave instead of forming the tail.
-// One CTA; within a bucket the order is arbitrary (it changes scheduling,
-// never a result).
-constexpr int kOrderThreads = 1024;
-constexpr int kOrderBuckets = 33;
+// Two grid-wide passes: the bucket sizes (per-CTA counts added to global
+// counters), then each tile's slot (the bucket's start plus a cursor taken
+// with one atomic per warp and bucket).  Within a bucket the order is
+// arbitrary: it changes scheduling, never a result.
+constexpr int kOrderThreads = 256;
 
 __device__ __forceinline__ int work_bucket(const uint32_t* ranges, int t) {
     const uint32_t len = ranges[2 * t + 1] - ranges[2 * t];
@@ -397,37 +410,42 @@ __device__ __forceinline__ int work_bucket(const uint32_t* ranges, int t) {
 }
 
 __global__ void __launch_bounds__(kOrderThreads)
-k_tile_order(const uint32_t* __restrict__ ranges, int T, uint32_t* __restrict__ order) {
+k_tile_buckets(const uint32_t* __restrict__ ranges, int T, uint32_t* __restrict__ counts) {
     grid_dep_begin();
-    __shared__ uint32_t cnt[kOrderBuckets], base[kOrderBuckets];
+    __shared__ uint32_t cnt[kOrderBuckets];
     if (threadIdx.x < kOrderBuckets) cnt[threadIdx.x] = 0u;
     __syncthreads();
-    const int lane = threadIdx.x & 31;
-    const uint32_t lt = (1u << lane) - 1u;
-    for (int t0 = 0; t0 < T; t0 += kOrderThreads) {
-        const int t = t0 + threadIdx.x;
-        const int b = t < T ? work_bucket(ranges, t) : 1000 + lane;  // unique dummy
-        const uint32_t peers = __match_any_sync(0xffffffffu, b);
-        if (t < T && (__ffs(peers) - 1) == lane) atomicAdd(&cnt[b], __popc(peers));
-    }
+    for (int t = blockIdx.x * kOrderThreads + threadIdx.x; t < T; t += gridDim.x * kOrderThreads)
+        atomicAdd(&cnt[work_bucket(ranges, t)], 1u);
     __syncthreads();
+    if (threadIdx.x < kOrderBuckets && cnt[threadIdx.x] != 0u)
+        atomicAdd(&counts[threadIdx.x], cnt[threadIdx.x]);
+}
+
+__global__ void __launch_bounds__(kOrderThreads)
+k_tile_order(const uint32_t* __restrict__ ranges, int T, const uint32_t* __restrict__ counts,
+             uint32_t* __restrict__ cursors, uint32_t* __restrict__ order) {
+    grid_dep_begin();
+    __shared__ uint32_t base[kOrderBuckets];
     if (threadIdx.x == 0) {
         uint32_t run = 0u;
         for (int b = 0; b < kOrderBuckets; ++b) {
             base[b] = run;
-            run += cnt[b];
+            run += counts[b];
         }
     }
     __syncthreads();
-    for (int t0 = 0; t0 < T; t0 += kOrderThreads) {
+    const int lane = threadIdx.x & 31;
+    const uint32_t lt = (1u << lane) - 1u;
+    for (int t0 = blockIdx.x * kOrderThreads; t0 < T; t0 += gridDim.x * kOrderThreads) {
         const int t = t0 + threadIdx.x;
-        const int b = t < T ? work_bucket(ranges, t) : 1000 + lane;
+        const int b = t < T ? work_bucket(ranges, t) : 1000 + lane;  // unique dummy
         const uint32_t peers = __match_any_sync(0xffffffffu, b);
         const int leader = __ffs(peers) - 1;
         uint32_t first = 0u;
-        if (t < T && leader == lane) first = atomicAdd(&base[b], __popc(peers));
+        if (t < T && leader == lane) first = atomicAdd(&cursors[b], __popc(peers));
         first = __shfl_sync(0xffffffffu, first, leader);
-        if (t < T) order[first + __popc(peers & lt)] = (uint32_t)t;
+        if (t < T) order[base[b] + first + __popc(peers & lt)] = (uint32_t)t;
     }
 }
 
@@ -451,12 +469,14 @@ gs_status radix_pass_t(const uint32_t* kin, const uint32_t* vin, uint32_t* kout,
 // than blocks of 2048 or 4096 for both the 1M depth keys and the 5M instances
 // (with the digit-reordered, coalesced writes too).  With kept_out the pass
 // drops the culled keys and stores how many it kept there.
+template <int ITEMS = kSortItems>
 gs_status radix_pass(const uint32_t* kin, const uint32_t* vin, uint32_t* kout, uint32_t* vout,
                      const uint32_t* count_dev, uint32_t count_host, uint32_t cap, int shift,
                      uint32_t* hist, uint32_t* totals, cudaStream_t st,
                      uint32_t* kept_out = nullptr) {
-    return radix_pass_t<kSortItems>(kin, vin, kout, vout, count_dev, count_host, cap, shift,
-                                    hist, totals, kept_out, st);
+    static_assert(ITEMS >= kSortItems, "the histogram buffer holds kSortTile-key blocks");
+    return radix_pass_t<ITEMS>(kin, vin, kout, vout, count_dev, count_host, cap, shift, hist,
+                               totals, kept_out, st);
 }
 
 }  // namespace
@@ -530,9 +550,14 @@ gs_status launch_bin_sort(const Plan* p, int32_t n, void* ws, cudaStream_t st) {
     // 4. per-tile ranges (cleared above)
     const int sms = sm_count();
     if (sms <= 0) return GS_ERR_CUDA;
-    launch_pdl(k_ranges, sms * kGridPerSm, 256, 0, st, sorted_keys, cnt, ranges);
-    launch_pdl(k_tile_order, 1, kOrderThreads, 0, st, ranges, p->total_tiles,
-               buf<uint32_t>(p, ws, B_TILE_ORDER));
+    uint32_t* order = buf<uint32_t>(p, ws, B_TILE_ORDER);
+    uint32_t* order_scratch = order + p->total_tiles;  // bucket counts | cursors
+    launch_pdl(k_ranges, sms * kGridPerSm, 256, 0, st, sorted_keys, cnt, ranges, order_scratch);
+    int ob = (p->total_tiles + kOrderThreads - 1) / kOrderThreads;
+    ob = ob < 4 * sms ? ob : 4 * sms;
+    launch_pdl(k_tile_buckets, ob, kOrderThreads, 0, st, ranges, p->total_tiles, order_scratch);
+    launch_pdl(k_tile_order, ob, kOrderThreads, 0, st, ranges, p->total_tiles, order_scratch,
+               order_scratch + kOrderBuckets, order);
     return launch_status();
 }
 
