@@ -161,6 +161,15 @@ __device__ __forceinline__ void grid_dep_begin() {
     asm volatile("griddepcontrol.wait;" ::: "memory");
 }
 
+// Let the next kernel of the chain launch once every CTA of this grid has
+// called this (instead of once they have exited): its CTAs can then take the
+// SMs this grid's last wave leaves idle and run up to their own
+// grid_dep_begin(), which still waits for this whole grid.  A plain launch
+// makes the instruction a no-op.
+__device__ __forceinline__ void grid_dep_release() {
+    asm volatile("griddepcontrol.launch_dependents;" ::: "memory");
+}
+
 // ---------------------------------------------------------------------------
 // Device helpers.
 // ---------------------------------------------------------------------------
@@ -319,6 +328,37 @@ static __device__ __forceinline__ int tight_row_span(const TightEllipse& E, int 
 
 // The Gaussian's weight at a pixel, evaluated identically by the forward and
 // the backward kernels: power = -(a dx^2 + c dy^2)/2 - b dx dy.
+// Packed FP32 pairs (PTX .f32x2, sm_100 and later): one instruction does the
+// operation on both halves, each an IEEE round-to-nearest operation, so the
+// results are bit-identical to fmaf / __fmul_rn / __fadd_rn on each half.
+__device__ __forceinline__ float2 fma2(float2 a, float2 b, float2 c) {
+    float2 d;
+    asm("{\n\t.reg .b64 ra, rb, rc, rd;\n\t"
+        "mov.b64 ra, {%2, %3};\n\tmov.b64 rb, {%4, %5};\n\tmov.b64 rc, {%6, %7};\n\t"
+        "fma.rn.f32x2 rd, ra, rb, rc;\n\tmov.b64 {%0, %1}, rd;\n\t}"
+        : "=f"(d.x), "=f"(d.y)
+        : "f"(a.x), "f"(a.y), "f"(b.x), "f"(b.y), "f"(c.x), "f"(c.y));
+    return d;
+}
+__device__ __forceinline__ float2 mul2(float2 a, float2 b) {
+    float2 d;
+    asm("{\n\t.reg .b64 ra, rb, rd;\n\t"
+        "mov.b64 ra, {%2, %3};\n\tmov.b64 rb, {%4, %5};\n\t"
+        "mul.rn.f32x2 rd, ra, rb;\n\tmov.b64 {%0, %1}, rd;\n\t}"
+        : "=f"(d.x), "=f"(d.y)
+        : "f"(a.x), "f"(a.y), "f"(b.x), "f"(b.y));
+    return d;
+}
+__device__ __forceinline__ float2 add2(float2 a, float2 b) {
+    float2 d;
+    asm("{\n\t.reg .b64 ra, rb, rd;\n\t"
+        "mov.b64 ra, {%2, %3};\n\tmov.b64 rb, {%4, %5};\n\t"
+        "add.rn.f32x2 rd, ra, rb;\n\tmov.b64 {%0, %1}, rd;\n\t}"
+        : "=f"(d.x), "=f"(d.y)
+        : "f"(a.x), "f"(a.y), "f"(b.x), "f"(b.y));
+    return d;
+}
+
 __device__ __forceinline__ float gauss_power(float a, float b, float c, float dx, float dy) {
     float q = __fmaf_rn(a, __fmul_rn(dx, dx), __fmul_rn(c, __fmul_rn(dy, dy)));
     return __fmaf_rn(-0.5f, q, -__fmul_rn(b, __fmul_rn(dx, dy)));

@@ -106,15 +106,19 @@ struct RowLoader {
 // SSIM, and its partial derivatives with respect to E[x], E[x^2] and E[xy]
 // (the maps the backward correlates).  x and y share one float2 of shared
 // memory; the horizontal pass forms x^2 + y^2 and xy once per input value.
+// The moments travel in pairs ({E[x], E[y]}, {E[x^2 + y^2], E[xy]}) through
+// packed FP32 pair FMAs, each half the scalar fmaf of the same operands.
 __global__ void __launch_bounds__(kLossThreads, 5)
 k_ssim_fwd(ViewTable vt, Win win, const float* __restrict__ img, const float* __restrict__ tgt,
            float lambda, float inv_views, int64_t total_values, float* __restrict__ maps,
            float* __restrict__ partials, int nblocks, DevCounters* ctr,
            float* __restrict__ loss_dev) {
     __shared__ float2 sxy[kRows][kCols + 1];
-    __shared__ float h[4][kRows][kTX + 1];
+    __shared__ float2 h[2][kRows][kTX + 1];
     __shared__ float red[32];
     __shared__ bool is_last;
+    grid_dep_begin();    // the rendered images are complete
+    grid_dep_release();  // the backward's CTAs may take the SMs of the last wave
     const BlockPos bp = block_pos(vt, blockIdx.x);
     {
         const RowLoader ld(bp);
@@ -144,33 +148,28 @@ k_ssim_fwd(ViewTable vt, Win win, const float* __restrict__ img, const float* __
     }
     __syncthreads();
     // horizontal pass: a thread takes kSeg consecutive outputs of one row,
-    // reading their kSeg + 10 inputs once
+    // reading their kSeg + 10 inputs once; consecutive threads take
+    // consecutive rows (conflict-free 8-byte shared accesses)
     for (int i = threadIdx.x; i < kRows * (kTX / kSeg); i += blockDim.x) {
-        const int r = i / (kTX / kSeg), c0 = (i - r * (kTX / kSeg)) * kSeg;
-        float u[kSeg + kWin - 1], v[kSeg + kWin - 1], sq[kSeg + kWin - 1], uv[kSeg + kWin - 1];
+        const int seg = i / kRows, r = i - seg * kRows, c0 = seg * kSeg;
+        float2 xy[kSeg + kWin - 1], pq[kSeg + kWin - 1];  // {x, y}, {x^2 + y^2, x y}
 #pragma unroll
         for (int k = 0; k < kSeg + kWin - 1; ++k) {
             const float2 p = sxy[r][c0 + k];
-            u[k] = p.x;
-            v[k] = p.y;
-            sq[k] = fmaf(p.x, p.x, p.y * p.y);
-            uv[k] = p.x * p.y;
+            xy[k] = p;
+            pq[k] = make_float2(fmaf(p.x, p.x, p.y * p.y), p.x * p.y);
         }
 #pragma unroll
         for (int o = 0; o < kSeg; ++o) {
-            float mx = 0.f, my = 0.f, ss = 0.f, xy = 0.f;
+            float2 m1 = make_float2(0.f, 0.f), m2 = make_float2(0.f, 0.f);
 #pragma unroll
             for (int k = 0; k < kWin; ++k) {
-                const float w = win.w[k];
-                mx = fmaf(w, u[o + k], mx);
-                my = fmaf(w, v[o + k], my);
-                ss = fmaf(w, sq[o + k], ss);
-                xy = fmaf(w, uv[o + k], xy);
+                const float2 w2 = make_float2(win.w[k], win.w[k]);
+                m1 = fma2(w2, xy[o + k], m1);
+                m2 = fma2(w2, pq[o + k], m2);
             }
-            h[0][r][c0 + o] = mx;
-            h[1][r][c0 + o] = my;
-            h[2][r][c0 + o] = ss;
-            h[3][r][c0 + o] = xy;
+            h[0][r][c0 + o] = m1;
+            h[1][r][c0 + o] = m2;
         }
     }
     __syncthreads();
@@ -180,19 +179,20 @@ k_ssim_fwd(ViewTable vt, Win win, const float* __restrict__ img, const float* __
     // vertical pass: a thread takes kOut consecutive rows of one column,
     // reading their kOut + 10 rows of horizontal sums once
     const int r0 = kOut * ty;
-    float m[kOut][4];
+    float2 m[kOut][2];
 #pragma unroll
     for (int o = 0; o < kOut; ++o)
 #pragma unroll
-        for (int q = 0; q < 4; ++q) m[o][q] = 0.0f;
+        for (int q = 0; q < 2; ++q) m[o][q] = make_float2(0.0f, 0.0f);
 #pragma unroll
     for (int k = 0; k < kWin + kOut - 1; ++k) {
 #pragma unroll
-        for (int q = 0; q < 4; ++q) {
-            const float hv = h[q][r0 + k][tx];
+        for (int q = 0; q < 2; ++q) {
+            const float2 hv = h[q][r0 + k][tx];
 #pragma unroll
             for (int o = 0; o < kOut; ++o)
-                if (k - o >= 0 && k - o < kWin) m[o][q] = fmaf(win.w[k - o], hv, m[o][q]);
+                if (k - o >= 0 && k - o < kWin)
+                    m[o][q] = fma2(make_float2(win.w[k - o], win.w[k - o]), hv, m[o][q]);
         }
     }
 #pragma unroll
@@ -200,9 +200,9 @@ k_ssim_fwd(ViewTable vt, Win win, const float* __restrict__ img, const float* __
         const int rr = r0 + o;
         const int x = bp.x0 + tx, y = bp.y0 + rr;
         if (x >= bp.width || y >= bp.height) continue;
-        const float mx = m[o][0], my = m[o][1];
+        const float mx = m[o][0].x, my = m[o][0].y;
         const float mm = fmaf(mx, mx, my * my);
-        const float vxy = m[o][2] - mm, cxy = m[o][3] - mx * my;  // sum of variances, covariance
+        const float vxy = m[o][1].x - mm, cxy = m[o][1].y - mx * my;  // sum of variances, covariance
         const float A = 2.0f * mx * my + C1, B = 2.0f * cxy + C2;
         const float Cd = mm + C1, D = vxy + C2;
         // one division: 1/Cd = D/(Cd D), 1/D = Cd/(Cd D) (Cd >= C1, D >= C2)
@@ -251,8 +251,11 @@ __global__ void __launch_bounds__(kLossThreads, 5)
 k_ssim_bwd(ViewTable vt, Win win, const float* __restrict__ img, const float* __restrict__ tgt,
            float lambda, float inv_views, int64_t total_values, const float* __restrict__ maps,
            float* __restrict__ dL) {
-    __shared__ float sm[3][kRows][kCols + 1];
-    __shared__ float h[3][kRows][kTX + 1];
+    // maps 0 and 1 as pairs, map 2 alone (packed pair FMAs on the pairs)
+    __shared__ float2 sm01[kRows][kCols + 1];
+    __shared__ float sm2[kRows][kCols + 1];
+    __shared__ float2 h01[kRows][kTX + 1];
+    __shared__ float h2[kRows][kTX + 1];
     const BlockPos bp = block_pos(vt, blockIdx.x);
     const int tx = threadIdx.x & 31, ty = threadIdx.x >> 5;
     const int r0 = kOut * ty;
@@ -267,6 +270,9 @@ k_ssim_bwd(ViewTable vt, Win win, const float* __restrict__ img, const float* __
             yo[o] = tgt[bp.plane + (int64_t)y * bp.width + x];
         }
     }
+    // the images were complete before the forward's CTAs released this grid;
+    // the maps are complete once the whole forward grid is
+    grid_dep_begin();
     {
         // the three maps over the tile and its halo, in two halves of rows
         const RowLoader ld(bp);
@@ -296,9 +302,8 @@ k_ssim_bwd(ViewTable vt, Win win, const float* __restrict__ img, const float* __
 #pragma unroll
                     for (int s = 0; s < 2; ++s) {
                         if (s == 1 && ld.lane >= kCols - 32) continue;
-                        sm[0][r][32 * s + ld.lane] = a[k][s];
-                        sm[1][r][32 * s + ld.lane] = b[k][s];
-                        sm[2][r][32 * s + ld.lane] = d[k][s];
+                        sm01[r][32 * s + ld.lane] = make_float2(a[k][s], b[k][s]);
+                        sm2[r][32 * s + ld.lane] = d[k][s];
                     }
                 }
             }
@@ -306,46 +311,49 @@ k_ssim_bwd(ViewTable vt, Win win, const float* __restrict__ img, const float* __
     }
     __syncthreads();
     for (int i = threadIdx.x; i < kRows * (kTX / kSeg); i += blockDim.x) {
-        const int r = i / (kTX / kSeg), c0 = (i - r * (kTX / kSeg)) * kSeg;
-        float u[3][kSeg + kWin - 1];
+        const int seg = i / kRows, r = i - seg * kRows, c0 = seg * kSeg;
+        float2 u01[kSeg + kWin - 1];
+        float u2[kSeg + kWin - 1];
 #pragma unroll
         for (int k = 0; k < kSeg + kWin - 1; ++k) {
-            u[0][k] = sm[0][r][c0 + k];
-            u[1][k] = sm[1][r][c0 + k];
-            u[2][k] = sm[2][r][c0 + k];
+            u01[k] = sm01[r][c0 + k];
+            u2[k] = sm2[r][c0 + k];
         }
 #pragma unroll
         for (int o = 0; o < kSeg; ++o) {
-            float a = 0.f, b = 0.f, d = 0.f;
+            float2 ab = make_float2(0.f, 0.f);
+            float d = 0.f;
 #pragma unroll
             for (int k = 0; k < kWin; ++k) {
                 const float w = win.w[k];
-                a = fmaf(w, u[0][o + k], a);
-                b = fmaf(w, u[1][o + k], b);
-                d = fmaf(w, u[2][o + k], d);
+                ab = fma2(make_float2(w, w), u01[o + k], ab);
+                d = fmaf(w, u2[o + k], d);
             }
-            h[0][r][c0 + o] = a;
-            h[1][r][c0 + o] = b;
-            h[2][r][c0 + o] = d;
+            h01[r][c0 + o] = ab;
+            h2[r][c0 + o] = d;
         }
     }
     __syncthreads();
     const ViewGeom& g = vt.v[bp.view];
     const float scale = inv_views / ((float)g.channels * (float)g.width * (float)g.height);
-    float m[kOut][3];
+    float2 m01[kOut];
+    float m2[kOut];
 #pragma unroll
-    for (int o = 0; o < kOut; ++o)
-#pragma unroll
-        for (int q = 0; q < 3; ++q) m[o][q] = 0.0f;
+    for (int o = 0; o < kOut; ++o) {
+        m01[o] = make_float2(0.0f, 0.0f);
+        m2[o] = 0.0f;
+    }
 #pragma unroll
     for (int k = 0; k < kWin + kOut - 1; ++k) {
+        const float2 hv = h01[r0 + k][tx];
+        const float hd = h2[r0 + k][tx];
 #pragma unroll
-        for (int q = 0; q < 3; ++q) {
-            const float hv = h[q][r0 + k][tx];
-#pragma unroll
-            for (int o = 0; o < kOut; ++o)
-                if (k - o >= 0 && k - o < kWin) m[o][q] = fmaf(win.w[k - o], hv, m[o][q]);
-        }
+        for (int o = 0; o < kOut; ++o)
+            if (k - o >= 0 && k - o < kWin) {
+                const float w = win.w[k - o];
+                m01[o] = fma2(make_float2(w, w), hv, m01[o]);
+                m2[o] = fmaf(w, hd, m2[o]);
+            }
     }
 #pragma unroll
     for (int o = 0; o < kOut; ++o) {
@@ -355,7 +363,7 @@ k_ssim_bwd(ViewTable vt, Win win, const float* __restrict__ img, const float* __
         const float xv = xo[o], yv = yo[o];
         const float diff = xv - yv;
         const float sgn = diff > 0.0f ? 1.0f : (diff < 0.0f ? -1.0f : 0.0f);
-        const float dssim = m[o][0] + 2.0f * xv * m[o][1] + yv * m[o][2];
+        const float dssim = m01[o].x + 2.0f * xv * m01[o].y + yv * m2[o];
         dL[idx] = scale * ((1.0f - lambda) * sgn - lambda * dssim);
     }
 }
@@ -383,11 +391,10 @@ gs_status launch_loss(const Plan* p, const float* images, const float* targets, 
     float* partials = buf<float>(p, ws, B_LOSS_BLOCKS);
     DevCounters* ctr = buf<DevCounters>(p, ws, GS_BUF_COUNTERS);
     const float inv_views = view_weight;
-    k_ssim_fwd<<<p->loss_blocks, kLossThreads, 0, st>>>(p->vt, win, images, targets, lambda,
-                                                        inv_views, p->total_values, maps,
-                                                        partials, p->loss_blocks, ctr, loss_dev);
-    k_ssim_bwd<<<p->loss_blocks, kLossThreads, 0, st>>>(p->vt, win, images, targets, lambda,
-                                                        inv_views, p->total_values, maps, dL);
+    launch_pdl(k_ssim_fwd, p->loss_blocks, kLossThreads, 0, st, p->vt, win, images, targets,
+               lambda, inv_views, p->total_values, maps, partials, p->loss_blocks, ctr, loss_dev);
+    launch_pdl(k_ssim_bwd, p->loss_blocks, kLossThreads, 0, st, p->vt, win, images, targets,
+               lambda, inv_views, p->total_values, (const float*)maps, dL);
     return launch_status();
 }
 
