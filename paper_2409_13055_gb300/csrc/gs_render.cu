@@ -453,9 +453,15 @@ __device__ void render_bwd_tile(const TM& tm, const ViewTable& vt, const TileCtx
     const float ly = (float)pr.ly;
     const int64_t plane = (int64_t)tc.width * tc.height;
     const float bgg = (bg[0] + bg[1] + bg[2]) * (1.0f / 3.0f);
+    // gS holds -dL/dC . S (the colour behind the current Gaussian), negated
     float T[PPT], g[PPT][CH], gS[PPT];
     int32_t last[PPT];
     int mylast = 0;
+    // the negated tile-local x of the lane's pixels, in pairs
+    float2 nlx[PPT / 2 > 0 ? PPT / 2 : 1];
+#pragma unroll
+    for (int p = 0; p < PPT / 2; ++p)
+        nlx[p] = make_float2(-(float)(pr.lx0 + 2 * p), -(float)(pr.lx0 + 2 * p + 1));
 #pragma unroll
     for (int k = 0; k < PPT; ++k) {
         const int px = tc.tx0 + pr.lx0 + k;
@@ -474,7 +480,7 @@ __device__ void render_bwd_tile(const TM& tm, const ViewTable& vt, const TileCtx
                 g[k][c] = dL[tc.val_base + c * plane + pix];
                 gb = fmaf(g[k][c], CH == 3 ? bg[c] : bgg, gb);
             }
-            gS[k] = T[k] * gb;  // the background seen through T_final
+            gS[k] = T[k] * -gb;  // minus the background seen through T_final
             mylast = max(mylast, last[k]);
         }
     }
@@ -515,53 +521,134 @@ __device__ void render_bwd_tile(const TM& tm, const ViewTable& vt, const TileCtx
             const float4 q = cur[3 * j + 1];
             const float4 col = cur[3 * j + 2];
             const float dy = gm.y - ly;
-            // phase 1: alpha and the blend decision of every pixel of the
-            // lane; a Gaussian that no pixel of the warp blends is done here
-            float dxk[PPT], oGk[PPT], alk[PPT];
-            bool hk[PPT];
-            bool contrib = false;
-#pragma unroll
-            for (int k = 0; k < PPT; ++k) {
-                dxk[k] = gm.x - (float)(pr.lx0 + k);
-                const float power = gauss_power(gm.z, gm.w, q.z, dxk[k], dy);
-                oGk[k] = __fmul_rn(q.w, __expf(power));
-                alk[k] = fminf(kAlphaMax, oGk[k]);
-                hk[k] = pos < last[k] && power <= 0.0f && alk[k] >= kAlphaMin;
-                contrib |= hk[k];
-            }
-            if (!__any_sync(0xffffffffu, contrib)) continue;
-            // phase 2, predicated: a lane whose pixel is not blended here
-            // contributes zeros and keeps its state
             float P0 = 0.0f, P1 = 0.0f, P3 = 0.0f, cw[CH], Hx = 0.0f, Hy = 0.0f;
+            if constexpr (PPT % 2 == 0) {
+                // the lane's pixels in pairs, on packed FP32 pair operations:
+                // each half is the scalar operation of the PPT = 1 path below
+                // on the same operands, and the state is kept negated
+                // (-gS; -alpha, -o G for the decisions; the sums negated) so
+                // that no pair needs a sign flip; the decisions and the
+                // per-pixel T and gS are the same bits as the scalar path's
+                constexpr int NP = PPT / 2;
+                const float cdd = __fmul_rn(q.z, __fmul_rn(dy, dy));
+                const float2 gx2 = make_float2(gm.x, gm.x), a2 = make_float2(gm.z, gm.z);
+                const float2 cdd2 = make_float2(cdd, cdd), dy2 = make_float2(dy, dy);
+                const float2 nb2 = make_float2(-gm.w, -gm.w), no2 = make_float2(-q.w, -q.w);
+                float2 dx[NP], noG[NP], na[NP];
+                bool hk[PPT];
+                bool contrib = false;
 #pragma unroll
-            for (int c = 0; c < CH; ++c) cw[c] = 0.0f;
+                for (int p = 0; p < NP; ++p) {
+                    dx[p] = add2(gx2, nlx[p]);
+                    const float2 qq = fma2(a2, mul2(dx[p], dx[p]), cdd2);
+                    const float2 pw =
+                        fma2(make_float2(-0.5f, -0.5f), qq, mul2(nb2, mul2(dx[p], dy2)));
+                    noG[p] = mul2(no2, make_float2(__expf(pw.x), __expf(pw.y)));
+                    na[p] = make_float2(fmaxf(-kAlphaMax, noG[p].x), fmaxf(-kAlphaMax, noG[p].y));
+                    hk[2 * p] = pos < last[2 * p] && pw.x <= 0.0f && na[p].x <= -kAlphaMin;
+                    hk[2 * p + 1] = pos < last[2 * p + 1] && pw.y <= 0.0f && na[p].y <= -kAlphaMin;
+                    contrib |= hk[2 * p] | hk[2 * p + 1];
+                }
+                if (!__any_sync(0xffffffffu, contrib)) continue;
+                float2 nP0 = make_float2(0.f, 0.f), nP1 = nP0, nP3 = nP0, ncw[CH];
 #pragma unroll
-            for (int k = 0; k < PPT; ++k) {
-                const float alpha = alk[k], oG = oGk[k], dx = dxk[k];
-                const bool hit = hk[k];
-                const float inv = rcp_approx(1.0f - alpha);
-                const float Ti = T[k] * inv;
-                const float w = hit ? alpha * Ti : 0.0f;
-                float gc;
-                if (CH == 3)
-                    gc = fmaf(g[k][2], col.z, fmaf(g[k][1], col.y, g[k][0] * col.x));
-                else
-                    gc = g[k][0] * col.w;
-                const float dal = fmaf(Ti, gc, -inv * gS[k]);
-                gS[k] = fmaf(w, gc, gS[k]);
+                for (int c = 0; c < CH; ++c) ncw[c] = nP0;
 #pragma unroll
-                for (int c = 0; c < CH; ++c) cw[c] = fmaf(w, g[k][c], cw[c]);
-                T[k] = hit ? Ti : T[k];
-                // alpha = o G when unclamped; a clamped alpha passes no gradient
-                const float dp = (hit && oG < kAlphaMax) ? oG * dal : 0.0f;
-                const float t = dp * dx;
-                P0 += dp;
-                P1 += t;
-                P3 = fmaf(t, dx, P3);
-                if (ABS) {
-                    // this pixel's own contribution to dL/dmean2d, by magnitude
-                    Hx += fabsf(dp * fmaf(gm.z, dx, gm.w * dy));
-                    Hy += fabsf(dp * fmaf(gm.w, dx, q.z * dy));
+                for (int p = 0; p < NP; ++p) {
+                    const int k0 = 2 * p, k1 = 2 * p + 1;
+                    const float2 inv =
+                        make_float2(rcp_approx(1.0f + na[p].x), rcp_approx(1.0f + na[p].y));
+                    const float2 Ti = mul2(make_float2(T[k0], T[k1]), inv);
+                    const float2 nwr = mul2(na[p], Ti);
+                    const float2 nw = make_float2(hk[k0] ? nwr.x : 0.0f, hk[k1] ? nwr.y : 0.0f);
+                    float2 gc;
+                    if (CH == 3)
+                        gc = fma2(make_float2(g[k0][2], g[k1][2]), make_float2(col.z, col.z),
+                                  fma2(make_float2(g[k0][1], g[k1][1]), make_float2(col.y, col.y),
+                                       mul2(make_float2(g[k0][0], g[k1][0]),
+                                            make_float2(col.x, col.x))));
+                    else
+                        gc = mul2(make_float2(g[k0][0], g[k1][0]), make_float2(col.w, col.w));
+                    const float2 nS = make_float2(gS[k0], gS[k1]);
+                    const float2 dal = fma2(Ti, gc, mul2(inv, nS));
+                    const float2 nS1 = fma2(nw, gc, nS);
+                    gS[k0] = nS1.x;
+                    gS[k1] = nS1.y;
+#pragma unroll
+                    for (int c = 0; c < CH; ++c)
+                        ncw[c] = fma2(nw, make_float2(g[k0][c], g[k1][c]), ncw[c]);
+                    T[k0] = hk[k0] ? Ti.x : T[k0];
+                    T[k1] = hk[k1] ? Ti.y : T[k1];
+                    // alpha = o G when unclamped; a clamped alpha passes no gradient
+                    const float2 ndr = mul2(noG[p], dal);
+                    const float2 ndp =
+                        make_float2((hk[k0] && noG[p].x > -kAlphaMax) ? ndr.x : 0.0f,
+                                    (hk[k1] && noG[p].y > -kAlphaMax) ? ndr.y : 0.0f);
+                    const float2 nt = mul2(ndp, dx[p]);
+                    nP0 = add2(nP0, ndp);
+                    nP1 = add2(nP1, nt);
+                    nP3 = fma2(nt, dx[p], nP3);
+                    if (ABS) {
+                        Hx += fabsf(ndp.x * fmaf(gm.z, dx[p].x, gm.w * dy));
+                        Hx += fabsf(ndp.y * fmaf(gm.z, dx[p].y, gm.w * dy));
+                        Hy += fabsf(ndp.x * fmaf(gm.w, dx[p].x, q.z * dy));
+                        Hy += fabsf(ndp.y * fmaf(gm.w, dx[p].y, q.z * dy));
+                    }
+                }
+                P0 = -(nP0.x + nP0.y);
+                P1 = -(nP1.x + nP1.y);
+                P3 = -(nP3.x + nP3.y);
+#pragma unroll
+                for (int c = 0; c < CH; ++c) cw[c] = -(ncw[c].x + ncw[c].y);
+            } else {
+                // phase 1: alpha and the blend decision of every pixel of the
+                // lane; a Gaussian that no pixel of the warp blends is done here
+                float dxk[PPT], oGk[PPT], alk[PPT];
+                bool hk[PPT];
+                bool contrib = false;
+#pragma unroll
+                for (int k = 0; k < PPT; ++k) {
+                    dxk[k] = gm.x - (float)(pr.lx0 + k);
+                    const float power = gauss_power(gm.z, gm.w, q.z, dxk[k], dy);
+                    oGk[k] = __fmul_rn(q.w, __expf(power));
+                    alk[k] = fminf(kAlphaMax, oGk[k]);
+                    hk[k] = pos < last[k] && power <= 0.0f && alk[k] >= kAlphaMin;
+                    contrib |= hk[k];
+                }
+                if (!__any_sync(0xffffffffu, contrib)) continue;
+                // phase 2, predicated: a lane whose pixel is not blended here
+                // contributes zeros and keeps its state (gS kept negated, as
+                // in the paired path)
+#pragma unroll
+                for (int c = 0; c < CH; ++c) cw[c] = 0.0f;
+#pragma unroll
+                for (int k = 0; k < PPT; ++k) {
+                    const float alpha = alk[k], oG = oGk[k], dx = dxk[k];
+                    const bool hit = hk[k];
+                    const float inv = rcp_approx(1.0f - alpha);
+                    const float Ti = T[k] * inv;
+                    const float w = hit ? alpha * Ti : 0.0f;
+                    float gc;
+                    if (CH == 3)
+                        gc = fmaf(g[k][2], col.z, fmaf(g[k][1], col.y, g[k][0] * col.x));
+                    else
+                        gc = g[k][0] * col.w;
+                    const float dal = fmaf(Ti, gc, inv * gS[k]);
+                    gS[k] = fmaf(-w, gc, gS[k]);
+#pragma unroll
+                    for (int c = 0; c < CH; ++c) cw[c] = fmaf(w, g[k][c], cw[c]);
+                    T[k] = hit ? Ti : T[k];
+                    // alpha = o G when unclamped; a clamped alpha passes no gradient
+                    const float dp = (hit && oG < kAlphaMax) ? oG * dal : 0.0f;
+                    const float t = dp * dx;
+                    P0 += dp;
+                    P1 += t;
+                    P3 = fmaf(t, dx, P3);
+                    if (ABS) {
+                        // this pixel's own contribution to dL/dmean2d, by magnitude
+                        Hx += fabsf(dp * fmaf(gm.z, dx, gm.w * dy));
+                        Hy += fabsf(dp * fmaf(gm.w, dx, q.z * dy));
+                    }
                 }
             }
             {
