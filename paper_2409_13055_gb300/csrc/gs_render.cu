@@ -152,10 +152,15 @@ __device__ __forceinline__ void issue_batch(const TM& tm, float4* stage, uint32_
 // are sqrt(2 ln(255 o) (Q^-1)_xx) and sqrt(2 ln(255 o) (Q^-1)_yy); the box is
 // grown by 0.1% + 0.01 px, far beyond FP32 rounding, so every skipped
 // evaluation would have been skipped by the alpha test itself.
+// With masks false the warp masks are neither formed nor written: for a team
+// of one warp over tight tile sets, whose listed Gaussians all reach the
+// tile's ellipse box up to the margins, the mask would leave the warp out of
+// almost nothing.  Culling is only a shortcut: without it every listed
+// Gaussian is evaluated and the alpha test decides.
 template <class TM>
 __device__ __forceinline__ void localise_batch(const TM& tm, float4* stage, uint32_t* wmask,
                                                int cnt, float tx0, float ty0, int tile_w, int rows,
-                                               int nwarps) {
+                                               int nwarps, bool masks = true) {
     for (int j = tm.tid; j < cnt; j += tm.size) {
         float4 m = stage[3 * j];
         const float4 q = stage[3 * j + 1];
@@ -167,6 +172,7 @@ __device__ __forceinline__ void localise_batch(const TM& tm, float4* stage, uint
         stage[3 * j] = m;
         col.w = (col.x + col.y + col.z) * (1.0f / 3.0f);
         stage[3 * j + 2] = col;
+        if (!masks) continue;
         const uint32_t all = nwarps >= 32 ? 0xffffffffu : ((1u << nwarps) - 1u);
         uint32_t bits = 0u;
         const float tau = logf(255.0f * q.w);
@@ -448,6 +454,9 @@ __device__ void render_bwd_tile(const TM& tm, const ViewTable& vt, const TileCtx
     const int nwarps = tm.size >> 5;
     const int rows = (32 * PPT) >> vt.log2_tw;
     const uint32_t wbit = 1u << (tm.tid >> 5);
+    // per-warp culling only where a warp covers part of the tile or the
+    // tile lists are the square rects
+    const bool cull = nwarps > 1 || !vt.tight_rect;
     const PixelRun pr = pixel_run(tm.tid, PPT, vt.log2_tw, vt.tile_w);
     const int py = tc.ty0 + pr.ly;
     const float ly = (float)pr.ly;
@@ -512,10 +521,11 @@ __device__ void render_bwd_tile(const TM& tm, const ViewTable& vt, const TileCtx
             cp_async_wait_all();
         }
         tm.sync();
-        localise_batch(tm, cur, cmask, cnt, (float)tc.tx0, (float)tc.ty0, vt.tile_w, rows, nwarps);
+        localise_batch(tm, cur, cmask, cnt, (float)tc.tx0, (float)tc.ty0, vt.tile_w, rows, nwarps,
+                       cull);
         tm.sync();
         for (int j = cnt - 1; j >= 0; --j) {
-            if (!(cmask[j] & wbit)) continue;
+            if (cull && !(cmask[j] & wbit)) continue;
             const int32_t pos = lo + j;
             const float4 gm = cur[3 * j];
             const float4 q = cur[3 * j + 1];
