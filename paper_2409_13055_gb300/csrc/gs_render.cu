@@ -421,6 +421,112 @@ __device__ __forceinline__ float rcp_approx(float x) {
     return y;
 }
 
+// The pixel adjoint's per-Gaussian work for a lane holding an even number of
+// pixels, in pairs on packed FP32 pair operations: each half is the scalar
+// operation of the one-pixel path in render_bwd_tile on the same operands,
+// with the state kept negated (-gS; -alpha and -o G for the decisions; the
+// sums negated) so that no pair needs a sign flip.  The decisions and the
+// per-pixel T and gS are the same bits as the one-pixel path's.
+template <int PPT>
+struct PairEval {
+    float2 dx[PPT / 2], noG[PPT / 2], na[PPT / 2];
+    bool hk[PPT];
+};
+
+// Phase 1: alpha and the blend decision of every pixel of the lane; returns
+// whether the lane blends the Gaussian at any of its pixels.
+template <int PPT>
+__device__ __forceinline__ bool pair_phase1(const float4& gm, const float4& q, float dy, int pos,
+                                            const int32_t* last, const float2* nlx,
+                                            PairEval<PPT>& e) {
+    constexpr int NP = PPT / 2;
+    const float cdd = __fmul_rn(q.z, __fmul_rn(dy, dy));
+    const float2 gx2 = make_float2(gm.x, gm.x), a2 = make_float2(gm.z, gm.z);
+    const float2 cdd2 = make_float2(cdd, cdd), dy2 = make_float2(dy, dy);
+    const float2 nb2 = make_float2(-gm.w, -gm.w), no2 = make_float2(-q.w, -q.w);
+    bool contrib = false;
+#pragma unroll
+    for (int p = 0; p < NP; ++p) {
+        e.dx[p] = add2(gx2, nlx[p]);
+        const float2 qq = fma2(a2, mul2(e.dx[p], e.dx[p]), cdd2);
+        const float2 pw = fma2(make_float2(-0.5f, -0.5f), qq, mul2(nb2, mul2(e.dx[p], dy2)));
+        e.noG[p] = mul2(no2, make_float2(__expf(pw.x), __expf(pw.y)));
+        e.na[p] = make_float2(fmaxf(-kAlphaMax, e.noG[p].x), fmaxf(-kAlphaMax, e.noG[p].y));
+        e.hk[2 * p] = pos < last[2 * p] && pw.x <= 0.0f && e.na[p].x <= -kAlphaMin;
+        e.hk[2 * p + 1] = pos < last[2 * p + 1] && pw.y <= 0.0f && e.na[p].y <= -kAlphaMin;
+        contrib |= e.hk[2 * p] | e.hk[2 * p + 1];
+    }
+    return contrib;
+}
+
+// Phase 2, predicated (a pixel not blended here contributes zeros and keeps
+// its state): updates T and gS and writes the lane's NC values of the
+// Gaussian (moments, colour weights, and with ABS the two magnitude sums).
+template <int CH, int PPT, bool ABS>
+__device__ __forceinline__ void pair_phase2(const PairEval<PPT>& e, const float4& gm,
+                                            const float4& q, const float4& col, float dy,
+                                            float* T, float (*g)[CH], float* gS, float* v) {
+    constexpr int NP = PPT / 2;
+    constexpr int NC0 = CH == 3 ? kGrad2d : 7;
+    float2 nP0 = make_float2(0.f, 0.f), nP1 = nP0, nP3 = nP0, ncw[CH];
+    float Hx = 0.0f, Hy = 0.0f;
+#pragma unroll
+    for (int c = 0; c < CH; ++c) ncw[c] = nP0;
+#pragma unroll
+    for (int p = 0; p < NP; ++p) {
+        const int k0 = 2 * p, k1 = 2 * p + 1;
+        const float2 inv = make_float2(rcp_approx(1.0f + e.na[p].x), rcp_approx(1.0f + e.na[p].y));
+        const float2 Ti = mul2(make_float2(T[k0], T[k1]), inv);
+        const float2 nwr = mul2(e.na[p], Ti);
+        const float2 nw = make_float2(e.hk[k0] ? nwr.x : 0.0f, e.hk[k1] ? nwr.y : 0.0f);
+        float2 gc;
+        if (CH == 3)
+            gc = fma2(make_float2(g[k0][2], g[k1][2]), make_float2(col.z, col.z),
+                      fma2(make_float2(g[k0][1], g[k1][1]), make_float2(col.y, col.y),
+                           mul2(make_float2(g[k0][0], g[k1][0]), make_float2(col.x, col.x))));
+        else
+            gc = mul2(make_float2(g[k0][0], g[k1][0]), make_float2(col.w, col.w));
+        const float2 nS = make_float2(gS[k0], gS[k1]);
+        const float2 dal = fma2(Ti, gc, mul2(inv, nS));
+        const float2 nS1 = fma2(nw, gc, nS);
+        gS[k0] = nS1.x;
+        gS[k1] = nS1.y;
+#pragma unroll
+        for (int c = 0; c < CH; ++c) ncw[c] = fma2(nw, make_float2(g[k0][c], g[k1][c]), ncw[c]);
+        T[k0] = e.hk[k0] ? Ti.x : T[k0];
+        T[k1] = e.hk[k1] ? Ti.y : T[k1];
+        // alpha = o G when unclamped; a clamped alpha passes no gradient
+        const float2 ndr = mul2(e.noG[p], dal);
+        const float2 ndp = make_float2((e.hk[k0] && e.noG[p].x > -kAlphaMax) ? ndr.x : 0.0f,
+                                       (e.hk[k1] && e.noG[p].y > -kAlphaMax) ? ndr.y : 0.0f);
+        const float2 nt = mul2(ndp, e.dx[p]);
+        nP0 = add2(nP0, ndp);
+        nP1 = add2(nP1, nt);
+        nP3 = fma2(nt, e.dx[p], nP3);
+        if (ABS) {
+            // each pixel's own contribution to dL/dmean2d, by magnitude
+            Hx += fabsf(ndp.x * fmaf(gm.z, e.dx[p].x, gm.w * dy));
+            Hx += fabsf(ndp.y * fmaf(gm.z, e.dx[p].y, gm.w * dy));
+            Hy += fabsf(ndp.x * fmaf(gm.w, e.dx[p].x, q.z * dy));
+            Hy += fabsf(ndp.y * fmaf(gm.w, e.dx[p].y, q.z * dy));
+        }
+    }
+    // the pixels of a run share dy: A2 = dy A0, A4 = dy A1, A5 = dy A2
+    const float P0 = -(nP0.x + nP0.y), P1 = -(nP1.x + nP1.y);
+    v[0] = P0;
+    v[1] = P1;
+    v[2] = dy * P0;
+    v[3] = -(nP3.x + nP3.y);
+    v[4] = dy * P1;
+    v[5] = dy * v[2];
+#pragma unroll
+    for (int c = 0; c < CH; ++c) v[6 + c] = -(ncw[c].x + ncw[c].y);
+    if (ABS) {
+        v[NC0] = Hx;
+        v[NC0 + 1] = Hy;
+    }
+}
+
 // Back-to-front adjoint of one tile (Eq. 1 differentiated; the transmittance
 // before each Gaussian is recovered by dividing by 1 - alpha).  Per pixel the
 // colour accumulated behind the current Gaussian enters only through its dot
@@ -499,6 +605,13 @@ __device__ void render_bwd_tile(const TM& tm, const ViewTable& vt, const TileCtx
     const int comp_r = reduce_component<NC>(threadIdx.x & 31);
     // the shared slot of the reduced value this lane holds
     const int comp = comp_r < NC0 ? comp_r : (comp_r < 0 ? -1 : kGrad2d + comp_r - NC0);
+    // ... and of the joint reduction of two Gaussians' 2 NC values: the slot,
+    // and whether it belongs to the second (front) Gaussian
+    const int comp2_r = reduce_component<2 * NC>(threadIdx.x & 31);
+    const int comp2_b = comp2_r >= NC ? 1 : 0;
+    const int comp2_c = comp2_r - NC * comp2_b;
+    const int comp2 =
+        comp2_r < 0 ? -1 : (comp2_c < NC0 ? comp2_c : kGrad2d + comp2_c - NC0);
     // batch k covers list positions [max(0, maxlast - (k+1) batch), maxlast - k batch)
     if (nb > 0) {
         const int lo = max(0, maxlast - batch);
@@ -524,93 +637,67 @@ __device__ void render_bwd_tile(const TM& tm, const ViewTable& vt, const TileCtx
         localise_batch(tm, cur, cmask, cnt, (float)tc.tx0, (float)tc.ty0, vt.tile_w, rows, nwarps,
                        cull);
         tm.sync();
-        for (int j = cnt - 1; j >= 0; --j) {
-            if (cull && !(cmask[j] & wbit)) continue;
-            const int32_t pos = lo + j;
-            const float4 gm = cur[3 * j];
-            const float4 q = cur[3 * j + 1];
-            const float4 col = cur[3 * j + 2];
-            const float dy = gm.y - ly;
-            float P0 = 0.0f, P1 = 0.0f, P3 = 0.0f, cw[CH], Hx = 0.0f, Hy = 0.0f;
-            if constexpr (PPT % 2 == 0) {
-                // the lane's pixels in pairs, on packed FP32 pair operations:
-                // each half is the scalar operation of the PPT = 1 path below
-                // on the same operands, and the state is kept negated
-                // (-gS; -alpha, -o G for the decisions; the sums negated) so
-                // that no pair needs a sign flip; the decisions and the
-                // per-pixel T and gS are the same bits as the scalar path's
-                constexpr int NP = PPT / 2;
-                const float cdd = __fmul_rn(q.z, __fmul_rn(dy, dy));
-                const float2 gx2 = make_float2(gm.x, gm.x), a2 = make_float2(gm.z, gm.z);
-                const float2 cdd2 = make_float2(cdd, cdd), dy2 = make_float2(dy, dy);
-                const float2 nb2 = make_float2(-gm.w, -gm.w), no2 = make_float2(-q.w, -q.w);
-                float2 dx[NP], noG[NP], na[NP];
-                bool hk[PPT];
-                bool contrib = false;
-#pragma unroll
-                for (int p = 0; p < NP; ++p) {
-                    dx[p] = add2(gx2, nlx[p]);
-                    const float2 qq = fma2(a2, mul2(dx[p], dx[p]), cdd2);
-                    const float2 pw =
-                        fma2(make_float2(-0.5f, -0.5f), qq, mul2(nb2, mul2(dx[p], dy2)));
-                    noG[p] = mul2(no2, make_float2(__expf(pw.x), __expf(pw.y)));
-                    na[p] = make_float2(fmaxf(-kAlphaMax, noG[p].x), fmaxf(-kAlphaMax, noG[p].y));
-                    hk[2 * p] = pos < last[2 * p] && pw.x <= 0.0f && na[p].x <= -kAlphaMin;
-                    hk[2 * p + 1] = pos < last[2 * p + 1] && pw.y <= 0.0f && na[p].y <= -kAlphaMin;
-                    contrib |= hk[2 * p] | hk[2 * p + 1];
-                }
-                if (!__any_sync(0xffffffffu, contrib)) continue;
-                float2 nP0 = make_float2(0.f, 0.f), nP1 = nP0, nP3 = nP0, ncw[CH];
-#pragma unroll
-                for (int c = 0; c < CH; ++c) ncw[c] = nP0;
-#pragma unroll
-                for (int p = 0; p < NP; ++p) {
-                    const int k0 = 2 * p, k1 = 2 * p + 1;
-                    const float2 inv =
-                        make_float2(rcp_approx(1.0f + na[p].x), rcp_approx(1.0f + na[p].y));
-                    const float2 Ti = mul2(make_float2(T[k0], T[k1]), inv);
-                    const float2 nwr = mul2(na[p], Ti);
-                    const float2 nw = make_float2(hk[k0] ? nwr.x : 0.0f, hk[k1] ? nwr.y : 0.0f);
-                    float2 gc;
-                    if (CH == 3)
-                        gc = fma2(make_float2(g[k0][2], g[k1][2]), make_float2(col.z, col.z),
-                                  fma2(make_float2(g[k0][1], g[k1][1]), make_float2(col.y, col.y),
-                                       mul2(make_float2(g[k0][0], g[k1][0]),
-                                            make_float2(col.x, col.x))));
-                    else
-                        gc = mul2(make_float2(g[k0][0], g[k1][0]), make_float2(col.w, col.w));
-                    const float2 nS = make_float2(gS[k0], gS[k1]);
-                    const float2 dal = fma2(Ti, gc, mul2(inv, nS));
-                    const float2 nS1 = fma2(nw, gc, nS);
-                    gS[k0] = nS1.x;
-                    gS[k1] = nS1.y;
-#pragma unroll
-                    for (int c = 0; c < CH; ++c)
-                        ncw[c] = fma2(nw, make_float2(g[k0][c], g[k1][c]), ncw[c]);
-                    T[k0] = hk[k0] ? Ti.x : T[k0];
-                    T[k1] = hk[k1] ? Ti.y : T[k1];
-                    // alpha = o G when unclamped; a clamped alpha passes no gradient
-                    const float2 ndr = mul2(noG[p], dal);
-                    const float2 ndp =
-                        make_float2((hk[k0] && noG[p].x > -kAlphaMax) ? ndr.x : 0.0f,
-                                    (hk[k1] && noG[p].y > -kAlphaMax) ? ndr.y : 0.0f);
-                    const float2 nt = mul2(ndp, dx[p]);
-                    nP0 = add2(nP0, ndp);
-                    nP1 = add2(nP1, nt);
-                    nP3 = fma2(nt, dx[p], nP3);
-                    if (ABS) {
-                        Hx += fabsf(ndp.x * fmaf(gm.z, dx[p].x, gm.w * dy));
-                        Hx += fabsf(ndp.y * fmaf(gm.z, dx[p].y, gm.w * dy));
-                        Hy += fabsf(ndp.x * fmaf(gm.w, dx[p].x, q.z * dy));
-                        Hy += fabsf(ndp.y * fmaf(gm.w, dx[p].y, q.z * dy));
+        if constexpr (PPT % 2 == 0) {
+            // one Gaussian, its values reduced alone
+            auto one = [&](int j) {
+                const float4 gm = cur[3 * j], q = cur[3 * j + 1];
+                const float dy = gm.y - ly;
+                PairEval<PPT> e;
+                if (!__any_sync(0xffffffffu, pair_phase1<PPT>(gm, q, dy, lo + j, last, nlx, e)))
+                    return;
+                float v[NC];
+                pair_phase2<CH, PPT, ABS>(e, gm, q, cur[3 * j + 2], dy, T, g, gS, v);
+                const float tot = warp_reduce_split<NC>(v);
+                if (comp >= 0) tm.add(acc + j * KA + comp, tot);
+            };
+            if (cull) {
+                for (int j = cnt - 1; j >= 0; --j)
+                    if (cmask[j] & wbit) one(j);
+            } else {
+                // two Gaussians per step, j (behind) then j - 1, whose values
+                // are reduced together when the warp blends both: one split
+                // reduce-scatter of 2 NC values costs fewer shuffles and adds
+                // than two of NC
+                int j = cnt - 1;
+                for (; j >= 1; j -= 2) {
+                    const float4 gA = cur[3 * j], qA = cur[3 * j + 1];
+                    const float4 gB = cur[3 * j - 3], qB = cur[3 * j - 2];
+                    const float dyA = gA.y - ly, dyB = gB.y - ly;
+                    PairEval<PPT> eA, eB;
+                    const bool anyA = __any_sync(
+                        0xffffffffu, pair_phase1<PPT>(gA, qA, dyA, lo + j, last, nlx, eA));
+                    const bool anyB = __any_sync(
+                        0xffffffffu, pair_phase1<PPT>(gB, qB, dyB, lo + j - 1, last, nlx, eB));
+                    if (anyA && anyB) {
+                        float v[2 * NC];
+                        pair_phase2<CH, PPT, ABS>(eA, gA, qA, cur[3 * j + 2], dyA, T, g, gS, v);
+                        pair_phase2<CH, PPT, ABS>(eB, gB, qB, cur[3 * j - 1], dyB, T, g, gS,
+                                                  v + NC);
+                        const float tot = warp_reduce_split<2 * NC>(v);
+                        if (comp2 >= 0) tm.add(acc + (j - comp2_b) * KA + comp2, tot);
+                    } else if (anyA) {
+                        float v[NC];
+                        pair_phase2<CH, PPT, ABS>(eA, gA, qA, cur[3 * j + 2], dyA, T, g, gS, v);
+                        const float tot = warp_reduce_split<NC>(v);
+                        if (comp >= 0) tm.add(acc + j * KA + comp, tot);
+                    } else if (anyB) {
+                        float v[NC];
+                        pair_phase2<CH, PPT, ABS>(eB, gB, qB, cur[3 * j - 1], dyB, T, g, gS, v);
+                        const float tot = warp_reduce_split<NC>(v);
+                        if (comp >= 0) tm.add(acc + (j - 1) * KA + comp, tot);
                     }
                 }
-                P0 = -(nP0.x + nP0.y);
-                P1 = -(nP1.x + nP1.y);
-                P3 = -(nP3.x + nP3.y);
-#pragma unroll
-                for (int c = 0; c < CH; ++c) cw[c] = -(ncw[c].x + ncw[c].y);
-            } else {
+                if (j == 0) one(0);
+            }
+        } else {
+            for (int j = cnt - 1; j >= 0; --j) {
+                if (cull && !(cmask[j] & wbit)) continue;
+                const int32_t pos = lo + j;
+                const float4 gm = cur[3 * j];
+                const float4 q = cur[3 * j + 1];
+                const float4 col = cur[3 * j + 2];
+                const float dy = gm.y - ly;
+                float P0 = 0.0f, P1 = 0.0f, P3 = 0.0f, cw[CH], Hx = 0.0f, Hy = 0.0f;
                 // phase 1: alpha and the blend decision of every pixel of the
                 // lane; a Gaussian that no pixel of the warp blends is done here
                 float dxk[PPT], oGk[PPT], alk[PPT];
@@ -660,8 +747,6 @@ __device__ void render_bwd_tile(const TM& tm, const ViewTable& vt, const TileCtx
                         Hy += fabsf(dp * fmaf(gm.w, dx, q.z * dy));
                     }
                 }
-            }
-            {
                 // the pixels of a run share dy: A2 = dy A0, A4 = dy A1, A5 = dy A2
                 float v[NC];
                 v[0] = P0;
