@@ -127,19 +127,39 @@ struct Team {
 // Gather records [first, first+cnt) of the tile list into stage (3 float4
 // each) and the list values into ids: the (view*n + index) id, or, in a
 // deterministic plan (gid_of given), the emission position, whose id is
-// gid_of[position].
+// gid_of[position].  A thread takes whole records, kR at a time, and loads
+// their list values (then their ids) before the first copy: the copies'
+// addresses wait for one round trip per kR records, not one per record.
 template <class TM>
 __device__ __forceinline__ void issue_batch(const TM& tm, float4* stage, uint32_t* ids,
                                             const uint32_t* __restrict__ ivals,
                                             const uint32_t* __restrict__ gid_of,
                                             const float4* __restrict__ rec, uint32_t first,
                                             int cnt) {
-    for (int c = tm.tid; c < 3 * cnt; c += tm.size) {
-        const int j = c / 3, part = c - 3 * j;
-        const uint32_t x = __ldg(ivals + first + j);
-        const uint32_t vg = gid_of ? __ldg(gid_of + x) : x;
-        cp_async16(stage + 3 * j + part, rec + (size_t)vg * 3 + part);
-        if (part == 0 && ids) ids[j] = x;
+    constexpr int kR = 2;
+    for (int j0 = 0; j0 < cnt; j0 += kR * tm.size) {
+        uint32_t x[kR], vg[kR];
+#pragma unroll
+        for (int r = 0; r < kR; ++r) {
+            const int j = j0 + tm.tid + r * tm.size;
+            x[r] = j < cnt ? __ldg(ivals + first + j) : 0u;
+        }
+#pragma unroll
+        for (int r = 0; r < kR; ++r) {
+            const int j = j0 + tm.tid + r * tm.size;
+            vg[r] = (gid_of && j < cnt) ? __ldg(gid_of + x[r]) : x[r];
+        }
+#pragma unroll
+        for (int r = 0; r < kR; ++r) {
+            const int j = j0 + tm.tid + r * tm.size;
+            if (j < cnt) {
+                const float4* src = rec + (size_t)vg[r] * 3;
+                cp_async16(stage + 3 * j, src);
+                cp_async16(stage + 3 * j + 1, src + 1);
+                cp_async16(stage + 3 * j + 2, src + 2);
+                if (ids) ids[j] = x[r];
+            }
+        }
     }
 }
 
