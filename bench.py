@@ -58,9 +58,7 @@ PAIR_FLOPS_BWD = 60.0
 # of the kernel as committed; other shapes and modes report null.  Summarised with its command in
 # profiles/launches_room1M_1200x680.md.
 RENDER_BWD_TRAFFIC = {
-    ("room1M_1200x680", "8x8", 32, 2, "square"): 60.67e6 + 0.83e6,
-    ("room1M_1200x680", "8x8", 64, 2, "square"): 60.67e6 + 0.82e6,
-    ("room1M_1200x680", "8x8", 64, 2, "tight"): 54.41e6 + 0.06e6,
+    ("room1M_1200x680", "8x8", 64, 2, "tight"): 54.52e6 + 0.02e6,
 }
 
 
