@@ -240,14 +240,88 @@ __device__ __forceinline__ PixelRun pixel_run(int tid, int ppt, int log2_tw, int
 // (a lane whose pixels are done runs predicated) so the warp can vote: a
 // Gaussian that no pixel of the warp blends costs only its alpha evaluation,
 // and the warp leaves the batch once none of its pixels is live.
+//
+// With an even PPT the pixels go in pairs on packed FP32 pair operations,
+// each half the scalar operation of the odd-PPT path on the same operands;
+// -alpha, -o G and the colour (C holds -C) are kept negated so that no pair
+// needs a sign flip: the decisions, T and the image are the same bits.
+// nlx: the negated tile-local x of the pixel pairs; cull: test the warp masks.
 template <int CH, int PPT>
 __device__ __forceinline__ void blend_batch(int tid, const float4* stage, const uint32_t* wmask,
                                             int cnt, uint32_t pos0, int lx0, float ly, float* T,
-                                            float (*C)[CH], int32_t* last, unsigned& live) {
+                                            float (*C)[CH], int32_t* last, unsigned& live,
+                                            const float2* nlx, bool cull) {
     const uint32_t wbit = 1u << (tid >> 5);
     if (!__any_sync(0xffffffffu, live != 0u)) return;
+    if constexpr (PPT % 2 == 0) {
+        constexpr int NP = PPT / 2;
+        for (int j = 0; j < cnt; ++j) {
+            if (cull && !(wmask[j] & wbit)) continue;
+            const float4 g = stage[3 * j];
+            const float4 q = stage[3 * j + 1];
+            const float dy = g.y - ly;
+            const float cdd = __fmul_rn(q.z, __fmul_rn(dy, dy));
+            const float2 gx2 = make_float2(g.x, g.x), a2 = make_float2(g.z, g.z);
+            const float2 cdd2 = make_float2(cdd, cdd), dy2 = make_float2(dy, dy);
+            const float2 nb2 = make_float2(-g.w, -g.w), no2 = make_float2(-q.w, -q.w);
+            float2 na[NP];
+            unsigned hits = 0u;
+#pragma unroll
+            for (int p = 0; p < NP; ++p) {
+                const float2 dx = add2(gx2, nlx[p]);
+                const float2 qq = fma2(a2, mul2(dx, dx), cdd2);
+                const float2 pw = fma2(make_float2(-0.5f, -0.5f), qq, mul2(nb2, mul2(dx, dy2)));
+                const float2 noG = mul2(no2, make_float2(__expf(pw.x), __expf(pw.y)));
+                na[p] = make_float2(fmaxf(-kAlphaMax, noG.x), fmaxf(-kAlphaMax, noG.y));
+                if (((live >> (2 * p)) & 1u) && pw.x <= 0.0f && na[p].x <= -kAlphaMin)
+                    hits |= 1u << (2 * p);
+                if (((live >> (2 * p + 1)) & 1u) && pw.y <= 0.0f && na[p].y <= -kAlphaMin)
+                    hits |= 1u << (2 * p + 1);
+            }
+            if (!__any_sync(0xffffffffu, hits != 0u)) continue;
+            const float4 col = stage[3 * j + 2];
+#pragma unroll
+            for (int p = 0; p < NP; ++p) {
+                const int k0 = 2 * p, k1 = 2 * p + 1;
+                const bool h0 = (hits >> k0) & 1u, h1 = (hits >> k1) & 1u;
+                const float2 T2 = make_float2(T[k0], T[k1]);
+                const float2 Tn = mul2(T2, add2(make_float2(1.0f, 1.0f), na[p]));
+                const bool s0 = h0 && Tn.x < kTMin, s1 = h1 && Tn.y < kTMin;
+                const bool a0 = h0 && !s0, a1 = h1 && !s1;
+                const float2 nwr = mul2(na[p], T2);
+                const float2 nw = make_float2(a0 ? nwr.x : 0.0f, a1 ? nwr.y : 0.0f);
+                if (CH == 3) {
+                    const float2 c0 = fma2(nw, make_float2(col.x, col.x),
+                                           make_float2(C[k0][0], C[k1][0]));
+                    const float2 c1 = fma2(nw, make_float2(col.y, col.y),
+                                           make_float2(C[k0][1], C[k1][1]));
+                    const float2 c2 = fma2(nw, make_float2(col.z, col.z),
+                                           make_float2(C[k0][2], C[k1][2]));
+                    C[k0][0] = c0.x;
+                    C[k1][0] = c0.y;
+                    C[k0][1] = c1.x;
+                    C[k1][1] = c1.y;
+                    C[k0][2] = c2.x;
+                    C[k1][2] = c2.y;
+                } else {
+                    const float2 c0 = fma2(nw, make_float2(col.w, col.w),
+                                           make_float2(C[k0][0], C[k1][0]));
+                    C[k0][0] = c0.x;
+                    C[k1][0] = c0.y;
+                }
+                T[k0] = a0 ? Tn.x : T[k0];
+                T[k1] = a1 ? Tn.y : T[k1];
+                last[k0] = a0 ? (int32_t)(pos0 + j + 1) : last[k0];
+                last[k1] = a1 ? (int32_t)(pos0 + j + 1) : last[k1];
+                live = s0 ? (live & ~(1u << k0)) : live;
+                live = s1 ? (live & ~(1u << k1)) : live;
+            }
+            if (!__any_sync(0xffffffffu, live != 0u)) return;
+        }
+        return;
+    }
     for (int j = 0; j < cnt; ++j) {
-        if (!(wmask[j] & wbit)) continue;
+        if (cull && !(wmask[j] & wbit)) continue;
         const float4 g = stage[3 * j];
         const float4 q = stage[3 * j + 1];
         const float dy = g.y - ly;
@@ -296,6 +370,15 @@ __device__ void render_fwd_tile(const TM& tm, const ViewTable& vt, const TileCtx
     const int rows = (32 * PPT) >> vt.log2_tw;
     const PixelRun pr = pixel_run(tm.tid, PPT, vt.log2_tw, vt.tile_w);
     const int py = tc.ty0 + pr.ly;
+    // per-warp culling only where a warp covers part of the tile or the
+    // tile lists are the square rects
+    const bool cull = nwarps > 1 || !vt.tight_rect;
+    // the negated tile-local x of the thread's pixels, in pairs (even PPT)
+    float2 nlx[PPT / 2 > 0 ? PPT / 2 : 1];
+#pragma unroll
+    for (int p = 0; p < PPT / 2; ++p)
+        nlx[p] = make_float2(-(float)(pr.lx0 + 2 * p), -(float)(pr.lx0 + 2 * p + 1));
+    // C holds the accumulated colour, negated with an even PPT
     float T[PPT], C[PPT][CH];
     int32_t last[PPT];
     unsigned live = 0u;
@@ -326,10 +409,11 @@ __device__ void render_fwd_tile(const TM& tm, const ViewTable& vt, const TileCtx
         }
         tm.sync();
         uint32_t* cmask = mask0 + (b & 1) * batch;
-        localise_batch(tm, cur, cmask, cnt, (float)tc.tx0, (float)tc.ty0, vt.tile_w, rows, nwarps);
+        localise_batch(tm, cur, cmask, cnt, (float)tc.tx0, (float)tc.ty0, vt.tile_w, rows, nwarps,
+                       cull);
         tm.sync();
         blend_batch<CH, PPT>(tm.tid, cur, cmask, cnt, (uint32_t)(b * batch), pr.lx0,
-                             (float)pr.ly, T, C, last, live);
+                             (float)pr.ly, T, C, last, live, nlx, cull);
         if (!tm.any(live != 0u)) {
             cp_async_wait_all();  // nothing may still be landing in shared memory
             break;
@@ -338,6 +422,7 @@ __device__ void render_fwd_tile(const TM& tm, const ViewTable& vt, const TileCtx
     if (py >= tc.height) return;
     const int64_t plane = (int64_t)tc.width * tc.height;
     const float bgg = (bg[0] + bg[1] + bg[2]) * (1.0f / 3.0f);
+    constexpr float sC = PPT % 2 == 0 ? -1.0f : 1.0f;  // undo the negation (exact)
 #pragma unroll
     for (int k = 0; k < PPT; ++k) {
         const int px = tc.tx0 + pr.lx0 + k;
@@ -346,9 +431,9 @@ __device__ void render_fwd_tile(const TM& tm, const ViewTable& vt, const TileCtx
         if (CH == 3) {
 #pragma unroll
             for (int c = 0; c < CH; ++c)
-                images[tc.val_base + c * plane + pix] = fmaf(T[k], bg[c], C[k][c]);
+                images[tc.val_base + c * plane + pix] = fmaf(T[k], bg[c], sC * C[k][c]);
         } else {
-            images[tc.val_base + pix] = fmaf(T[k], bgg, C[k][0]);
+            images[tc.val_base + pix] = fmaf(T[k], bgg, sC * C[k][0]);
         }
         final_T[tc.pix_base + pix] = T[k];
         last_idx[tc.pix_base + pix] = last[k];
