@@ -55,8 +55,9 @@ PAIR_FLOPS_BWD = 60.0
 # DRAM bytes (read + write) of one k_render_bwd launch on the 1M 1200x680
 # workload stored in Z-order, from one single-pass ncu capture per launch
 # shape (tile, backward batch, backward pixels per thread) and tile-rect mode
-# of the kernel as committed; other shapes and modes report null.  Summarised with its command in
-# profiles/launches_room1M_1200x680.md.
+# of the kernel as committed; other shapes and modes report null.  The
+# capture's command and its other counters are kept with the launch-list
+# profile of this workload.
 RENDER_BWD_TRAFFIC = {
     ("room1M_1200x680", "8x8", 64, 2, "tight"): 54.52e6 + 0.02e6,
 }
