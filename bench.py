@@ -47,8 +47,9 @@ WORKLOAD = "room1M_1200x680"
 # power as 6 FMA-equivalents, alpha 2, transmittance 2, colour 6, the exp on
 # the SFU), adjoint ~60 (the forward's recomputation, the transmittance and
 # colour-behind recursion, the alpha, power, mean, conic, opacity and colour
-# terms, and the sum over the pixels).  The kernels as written execute 26 and
-# 64 of them; the fractions use the algorithmic counts.
+# terms, and the sum over the pixels).  The kernels as written execute a few
+# more (the blend tests, the negations of the packed forms); the fractions
+# use the algorithmic counts.
 PAIR_FLOPS_FWD = 20.0
 PAIR_FLOPS_BWD = 60.0
 
