@@ -300,7 +300,7 @@ gs_status gs_render_bwd(const gs_plan *plan, const gs_map *map, const gs_view *v
  * its own to lend.  The paper has no counterpart to this entry point.
  *
  * Same arguments, arithmetic and results as gs_loss_l1_ssim, minus ws: its
- * scratch (SSIM partial maps, per-block loss partials, a reduction ticket) is
+ * scratch (SSIM partial maps, per-block loss partials, the loss) is
  * a fixed array compiled into the library, about 12.6 MB, which every GPU
  * that has loaded the library's device code holds until the process exits.
  * Limits: the plan's images may hold at most 2^20 values in total (sum of
@@ -315,7 +315,7 @@ gs_status gs_render_bwd(const gs_plan *plan, const gs_map *map, const gs_view *v
  * capture and before the caller's memory budget starts.  Apart from that
  * loading, nothing is allocated, by this call or any library routine it
  * uses.  All calls share the one array and it keeps the last call's contents
- * (the ticket is cleared at the start of every call): calls that overlap on
+ * (every call overwrites what it reads): calls that overlap on
  * the GPU -- on different streams, or from several threads -- race on the
  * scratch and corrupt each other's results; order them on one stream. */
 gs_status gs_loss_l1_ssim_noalloc(const gs_plan *plan, const float *images, const float *targets,

@@ -101,7 +101,7 @@ struct DevCounters {
     uint32_t n_instances;          // clamped to capacity
     unsigned long long n_raw;      // before clamping
     float loss;
-    uint32_t loss_blocks_done;     // last-block-done ticket of the loss reduction
+    uint32_t loss_blocks_done;     // reserved (zero)
     uint32_t vn;                   // depth-order entries (visible pairs) of the last gs_bin_sort
     uint32_t n_sorted;             // visible pairs kept by the first depth pass
     uint32_t span_pool_used;       // rows of B_SPAN_POOL taken by the last gs_project

@@ -16,8 +16,8 @@
 // derivatives of SSIM with respect to E[x], E[x^2] and E[xy].  The backward
 // correlates those three maps with the same window (the adjoint of a
 // zero-padded symmetric correlation is itself) and adds the L1 term.  The
-// loss is reduced deterministically: per-block partials, summed in block
-// order by whichever block finishes last (a ticket counter, no waiting).
+// loss is reduced deterministically: the forward's per-block partials,
+// summed in block order by the backward's first CTA beside its own tile.
 #include <math.h>
 
 
@@ -116,7 +116,6 @@ k_ssim_fwd(ViewTable vt, Win win, const float* __restrict__ img, const float* __
     __shared__ float2 sxy[kRows][kCols + 1];
     __shared__ float2 h[2][kRows][kTX + 1];
     __shared__ float red[32];
-    __shared__ bool is_last;
     grid_dep_begin();    // the rendered images are complete
     grid_dep_release();  // the backward's CTAs may take the SMs of the last wave
     const BlockPos bp = block_pos(vt, blockIdx.x);
@@ -225,23 +224,21 @@ k_ssim_fwd(ViewTable vt, Win win, const float* __restrict__ img, const float* __
     const float invM = 1.0f / ((float)g.channels * (float)g.width * (float)g.height);
     const float part = inv_views * invM * ((1.0f - lambda) * l1 - lambda * ss);
     const float tot = block_sum(part, red);
-    if (threadIdx.x == 0) {
-        partials[blockIdx.x] = tot;
-        __threadfence();
-        const uint32_t ticket = atomicAdd(&ctr->loss_blocks_done, 1u);
-        is_last = (ticket == (uint32_t)nblocks - 1);
-    }
-    __syncthreads();
-    if (!is_last) return;
-    __threadfence();
+    if (threadIdx.x == 0) partials[blockIdx.x] = tot;
+}
+
+// The loss: the forward's per-block partials summed in block order (one CTA).
+__device__ __forceinline__ void loss_total(const ViewTable& vt, float lambda, float inv_views,
+                                           const float* __restrict__ partials, int nblocks,
+                                           DevCounters* ctr, float* __restrict__ loss_dev,
+                                           float* red) {
     float acc = 0.0f;
-    for (int i = threadIdx.x; i < nblocks; i += blockDim.x) acc += ((volatile float*)partials)[i];
+    for (int i = threadIdx.x; i < nblocks; i += blockDim.x) acc += partials[i];
     const float all = block_sum(acc, red);
     if (threadIdx.x == 0) {
         const float L = lambda * inv_views * (float)vt.n_views + all;
         *loss_dev = L;
         ctr->loss = L;
-        ctr->loss_blocks_done = 0u;
     }
 }
 
@@ -250,7 +247,9 @@ k_ssim_fwd(ViewTable vt, Win win, const float* __restrict__ img, const float* __
 __global__ void __launch_bounds__(kLossThreads, 5)
 k_ssim_bwd(ViewTable vt, Win win, const float* __restrict__ img, const float* __restrict__ tgt,
            float lambda, float inv_views, int64_t total_values, const float* __restrict__ maps,
-           float* __restrict__ dL) {
+           float* __restrict__ dL, const float* __restrict__ partials, int nblocks,
+           DevCounters* ctr, float* __restrict__ loss_dev) {
+    __shared__ float red[32];
     // maps 0 and 1 as pairs, map 2 alone (packed pair FMAs on the pairs)
     __shared__ float2 sm01[kRows][kCols + 1];
     __shared__ float sm2[kRows][kCols + 1];
@@ -271,8 +270,10 @@ k_ssim_bwd(ViewTable vt, Win win, const float* __restrict__ img, const float* __
         }
     }
     // the images were complete before the forward's CTAs released this grid;
-    // the maps are complete once the whole forward grid is
+    // the maps and the loss partials are complete once the whole forward grid is
     grid_dep_begin();
+    // CTA 0 also sums the loss (in block order), beside the other CTAs' work
+    if (blockIdx.x == 0) loss_total(vt, lambda, inv_views, partials, nblocks, ctr, loss_dev, red);
     {
         // the three maps over the tile and its halo, in two halves of rows
         const RowLoader ld(bp);
@@ -394,7 +395,8 @@ gs_status launch_loss(const Plan* p, const float* images, const float* targets, 
     launch_pdl(k_ssim_fwd, p->loss_blocks, kLossThreads, 0, st, p->vt, win, images, targets,
                lambda, inv_views, p->total_values, maps, partials, p->loss_blocks, ctr, loss_dev);
     launch_pdl(k_ssim_bwd, p->loss_blocks, kLossThreads, 0, st, p->vt, win, images, targets,
-               lambda, inv_views, p->total_values, (const float*)maps, dL);
+               lambda, inv_views, p->total_values, (const float*)maps, dL,
+               (const float*)partials, p->loss_blocks, ctr, loss_dev);
     return launch_status();
 }
 
@@ -414,8 +416,8 @@ constexpr size_t kNoAllocMapsOffset =
     kNoAllocPartialsOffset + ((size_t(kNoAllocMaxBlocks + 1) * 2 * sizeof(float) + 255) & ~size_t(255));
 constexpr size_t kNoAllocBytes = kNoAllocMapsOffset + 3 * kNoAllocMaxValues * sizeof(float);
 
-// Scratch of gs_loss_l1_ssim_noalloc: counters (ticket of the loss reduction)
-// | per-block loss partials | the three SSIM partial-derivative maps.  About
+// Scratch of gs_loss_l1_ssim_noalloc: counters (the loss) | per-block loss
+// partials | the three SSIM partial-derivative maps.  About
 // 12.6 MB, held on every GPU that loads the library until the process exits.
 static __device__ __align__(256) unsigned char g_noalloc_scratch[kNoAllocBytes];
 
@@ -456,14 +458,13 @@ extern "C" gs_status gs_loss_l1_ssim_noalloc(const gs_plan* plan, const float* i
     DevCounters* ctr = reinterpret_cast<DevCounters*>(base);
     float* partials = reinterpret_cast<float*>(base + kNoAllocPartialsOffset);
     float* maps = reinterpret_cast<float*>(base + kNoAllocMapsOffset);
-    // the array keeps whatever the last call left: the ticket must start at zero
-    if (cudaMemsetAsync(ctr, 0, sizeof(DevCounters), st) != cudaSuccess) return GS_ERR_CUDA;
     const Win win = loss_window();
     k_ssim_fwd<<<p->loss_blocks, kLossThreads, 0, st>>>(p->vt, win, images, targets, lambda,
                                                         view_weight, p->total_values, maps,
                                                         partials, p->loss_blocks, ctr, loss_dev);
     k_ssim_bwd<<<p->loss_blocks, kLossThreads, 0, st>>>(p->vt, win, images, targets, lambda,
                                                         view_weight, p->total_values, maps,
-                                                        dL_dimages);
+                                                        dL_dimages, partials, p->loss_blocks, ctr,
+                                                        loss_dev);
     return launch_status();
 }
