@@ -63,7 +63,8 @@ __device__ __forceinline__ uint32_t block_exclusive_scan(uint32_t x, uint32_t* w
 template <int ITEMS>
 __global__ void __launch_bounds__(kSortThreads)
 k_radix_hist(const uint32_t* __restrict__ keys, const uint32_t* count_dev, uint32_t count_host,
-             uint32_t cap, int shift, int nb, int drop, uint32_t* __restrict__ hist) {
+             uint32_t cap, int shift, uint32_t mask, int nb, int drop,
+             uint32_t* __restrict__ hist) {
     grid_dep_begin();
     constexpr int TILE = kSortThreads * ITEMS;
     __shared__ uint32_t h[kRadix];
@@ -75,7 +76,7 @@ k_radix_hist(const uint32_t* __restrict__ keys, const uint32_t* count_dev, uint3
     const uint32_t end = min(start + (uint32_t)TILE, count);
     for (uint32_t i = start + threadIdx.x; i < end; i += kSortThreads) {
         const uint32_t k = keys[i];
-        if (!(drop && k == kCulledKey)) atomicAdd(&h[(k >> shift) & (kRadix - 1)], 1u);
+        if (!(drop && k == kCulledKey)) atomicAdd(&h[(k >> shift) & mask], 1u);
     }
     __syncthreads();
     hist[(size_t)threadIdx.x * nb + blockIdx.x] = h[threadIdx.x];
@@ -125,7 +126,8 @@ template <int ITEMS>
 __global__ void __launch_bounds__(kSortThreads)
 k_radix_scatter(const uint32_t* __restrict__ keys_in, const uint32_t* __restrict__ vals_in,
                 uint32_t* __restrict__ keys_out, uint32_t* __restrict__ vals_out,
-                const uint32_t* count_dev, uint32_t count_host, uint32_t cap, int shift, int nb,
+                const uint32_t* count_dev, uint32_t count_host, uint32_t cap, int shift,
+                uint32_t mask, int nb,
                 const uint32_t* __restrict__ hist, const uint32_t* __restrict__ totals, int drop,
                 uint32_t* __restrict__ kept_out) {
     grid_dep_begin();
@@ -167,7 +169,7 @@ k_radix_scatter(const uint32_t* __restrict__ keys_in, const uint32_t* __restrict
         const uint32_t i = wstart + (uint32_t)r * 32u + lane;
         const bool in = i < count;
         const bool ok = in && !(drop && key[r] == kCulledKey);
-        const uint32_t d = ok ? ((key[r] >> shift) & (kRadix - 1)) : 0x10000u;
+        const uint32_t d = ok ? ((key[r] >> shift) & mask) : 0x10000u;
         const uint32_t peers = __match_any_sync(0xffffffffu, d);
         uint32_t rk = 0u;
         if (ok) rk = wcnt[w][d] + __popc(peers & lt);
@@ -191,7 +193,7 @@ k_radix_scatter(const uint32_t* __restrict__ keys_in, const uint32_t* __restrict
     for (int r = 0; r < ITEMS; ++r) {
         const uint32_t i = wstart + (uint32_t)r * 32u + lane;
         if (i < count && !(drop && key[r] == kCulledKey)) {
-            const uint32_t d = (key[r] >> shift) & (kRadix - 1);
+            const uint32_t d = (key[r] >> shift) & mask;
             const uint32_t s = local[d] + wcnt[w][d] + rank[r];
             skey[s] = key[r];
             sval[s] = val[r];
@@ -203,7 +205,7 @@ k_radix_scatter(const uint32_t* __restrict__ keys_in, const uint32_t* __restrict
         const int s = r * kSortThreads + tid;
         if ((uint32_t)s < n_kept) {
             const uint32_t k = skey[s];
-            const uint32_t d = (k >> shift) & (kRadix - 1);
+            const uint32_t d = (k >> shift) & mask;
             const uint32_t pos = base[d] + ((uint32_t)s - local[d]);
             keys_out[pos] = k;
             vals_out[pos] = sval[s];
@@ -452,19 +454,21 @@ k_tile_order(const uint32_t* __restrict__ ranges, int T, const uint32_t* __restr
 template <int ITEMS>
 gs_status radix_pass_t(const uint32_t* kin, const uint32_t* vin, uint32_t* kout, uint32_t* vout,
                        const uint32_t* count_dev, uint32_t count_host, uint32_t cap, int shift,
-                       uint32_t* hist, uint32_t* totals, uint32_t* kept_out, cudaStream_t st) {
+                       int bits, uint32_t* hist, uint32_t* totals, uint32_t* kept_out,
+                       cudaStream_t st) {
     const int nb = (int)((cap + kSortThreads * ITEMS - 1) / (kSortThreads * ITEMS));
     const int drop = kept_out != nullptr;
+    const uint32_t mask = (1u << bits) - 1u;
     launch_pdl(k_radix_hist<ITEMS>, nb, kSortThreads, 0, st, kin, count_dev, count_host, cap,
-               shift, nb, drop, hist);
+               shift, mask, nb, drop, hist);
     launch_pdl(k_radix_scan<ITEMS>, kRadix, kSortThreads, 0, st, hist, count_dev, count_host,
                cap, nb, totals);
     launch_pdl(k_radix_scatter<ITEMS>, nb, kSortThreads, 0, st, kin, vin, kout, vout, count_dev,
-               count_host, cap, shift, nb, hist, totals, drop, kept_out);
+               count_host, cap, shift, mask, nb, hist, totals, drop, kept_out);
     return launch_status();
 }
 
-// One stable pass on 8 bits at `shift` over up to `cap` keys (the real count
+// One stable pass on `bits` (<= 8) bits at `shift` over up to `cap` keys (the real count
 // comes from count_dev when given), in blocks of 1024 keys: measured faster
 // than blocks of 2048 or 4096 for both the 1M depth keys and the 5M instances
 // (with the digit-reordered, coalesced writes too).  With kept_out the pass
@@ -472,11 +476,11 @@ gs_status radix_pass_t(const uint32_t* kin, const uint32_t* vin, uint32_t* kout,
 template <int ITEMS = kSortItems>
 gs_status radix_pass(const uint32_t* kin, const uint32_t* vin, uint32_t* kout, uint32_t* vout,
                      const uint32_t* count_dev, uint32_t count_host, uint32_t cap, int shift,
-                     uint32_t* hist, uint32_t* totals, cudaStream_t st,
+                     int bits, uint32_t* hist, uint32_t* totals, cudaStream_t st,
                      uint32_t* kept_out = nullptr) {
     static_assert(ITEMS >= kSortItems, "the histogram buffer holds kSortTile-key blocks");
-    return radix_pass_t<ITEMS>(kin, vin, kout, vout, count_dev, count_host, cap, shift, hist,
-                               totals, kept_out, st);
+    return radix_pass_t<ITEMS>(kin, vin, kout, vout, count_dev, count_host, cap, shift, bits,
+                               hist, totals, kept_out, st);
 }
 
 }  // namespace
@@ -507,13 +511,14 @@ gs_status launch_bin_sort(const Plan* p, int32_t n, void* ws, cudaStream_t st) {
     uint32_t* kc = buf<uint32_t>(p, ws, B_DKEY_C);
     uint32_t* va = buf<uint32_t>(p, ws, GS_BUF_DEPTH_ORDER);
     uint32_t* n_sorted = &ctr->n_sorted;
-    gs_status s0 = radix_pass(kp, nullptr, kb, vb, nullptr, VN, VN, 0, hist, totals, st,
-                              n_sorted);
+    gs_status s0 = radix_pass(kp, nullptr, kb, vb, nullptr, VN, VN, 0, kRadixBits, hist, totals,
+                              st, n_sorted);
     if (s0 != GS_OK) return s0;
     for (int pass = 1; pass < 4; ++pass) {
         const bool odd = (pass & 1) != 0;
         gs_status s = radix_pass(odd ? kb : kc, odd ? vb : va, odd ? kc : kb, odd ? va : vb,
-                                 n_sorted, VN, VN, pass * kRadixBits, hist, totals, st);
+                                 n_sorted, VN, VN, pass * kRadixBits, kRadixBits, hist, totals,
+                                 st);
         if (s != GS_OK) return s;
     }
 
@@ -537,12 +542,15 @@ gs_status launch_bin_sort(const Plan* p, int32_t n, void* ws, cudaStream_t st) {
     gs_status s = launch_status();
     if (s != GS_OK) return s;
 
-    // 3. tile-id digits over the instances
+    // 3. tile-id digits over the instances, the id's bits split evenly over
+    //    the passes (14 bits: 7 + 7 rather than 8 + 6, so that both passes
+    //    write runs of similar length)
     const uint32_t* cnt = &ctr->n_instances;
+    const int tbits = (p->tile_bits + p->tile_passes - 1) / p->tile_passes;
     for (int pass = 0; pass < p->tile_passes; ++pass) {
         const bool even = (pass & 1) == 0;
         s = radix_pass(even ? ika : ikb, even ? iva : ivb, even ? ikb : ika, even ? ivb : iva, cnt,
-                       0u, icap, pass * kRadixBits, hist, totals, st);
+                       0u, icap, pass * tbits, tbits, hist, totals, st);
         if (s != GS_OK) return s;
     }
     const uint32_t* sorted_keys = (p->tile_passes & 1) ? ikb : ika;
