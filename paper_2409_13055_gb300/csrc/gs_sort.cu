@@ -232,49 +232,49 @@ k_scan_reduce(const uint32_t* __restrict__ order, const uint32_t* __restrict__ t
     if (threadIdx.x == 0) block_sums[blockIdx.x] = tot;
 }
 
-// Exclusive scan of the block sums (one block), total instance count; vn =
-// the number of depth-order entries (visible pairs) for later readers.
-__global__ void __launch_bounds__(kSortThreads)
-k_scan_blocks(uint32_t* __restrict__ block_sums, int nb, uint32_t cap,
-              const uint32_t* vn, DevCounters* ctr) {
-    grid_dep_begin();
-    __shared__ uint32_t wt[33];
-    unsigned long long carry = 0;
-    for (int base = 0; base < nb; base += kSortThreads * 4) {
-        uint32_t v[4], s = 0;
-        for (int k = 0; k < 4; ++k) {
-            int i = base + threadIdx.x * 4 + k;
-            v[k] = i < nb ? block_sums[i] : 0u;
-            s += v[k];
-        }
-        uint32_t tot;
-        uint32_t ex = block_exclusive_scan(s, wt, tot);
-        unsigned long long run = carry + ex;
-        for (int k = 0; k < 4; ++k) {
-            int i = base + threadIdx.x * 4 + k;
-            if (i < nb) block_sums[i] = (uint32_t)min(run, (unsigned long long)0xFFFFFFFFu);
-            run += v[k];
-        }
-        carry += tot;
-    }
-    if (threadIdx.x == 0) {
-        ctr->n_raw = carry;
-        ctr->vn = *vn;
-        ctr->n_instances = (uint32_t)min(carry, (unsigned long long)cap);
-        if (carry > cap) atomicOr(&ctr->status, (uint32_t)GS_DEV_CAPACITY);
-    }
+// Sum over the CTA of one 64-bit value per thread (kScanThreads threads);
+// valid in every thread.
+__device__ __forceinline__ unsigned long long block_sum_u64(unsigned long long x,
+                                                          unsigned long long* red) {
+    const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) x += __shfl_xor_sync(0xffffffffu, x, o);
+    if (lane == 0) red[w] = x;
+    __syncthreads();
+    unsigned long long t = 0;
+    for (int k = 0; k < (int)(blockDim.x >> 5); ++k) t += red[k];
+    __syncthreads();
+    return t;
 }
 
 // Global exclusive offsets of the instances of every visible (view,
 // Gaussian) entry in depth order: off[i] for i < count, off[count] = total
-// (count = *count_dev).
+// (count = *count_dev).  Each CTA forms its own starting offset from the
+// block sums before it (a few hundred words), so no separate scan of the
+// block sums runs; CTA 0 also forms the total and the instance counters
+// (vn = the number of depth-order entries, for later readers).
 __global__ void __launch_bounds__(kScanThreads)
 k_scan_offsets(const uint32_t* __restrict__ order, const uint32_t* __restrict__ touched,
-               const uint32_t* __restrict__ block_off, const uint32_t* count_dev,
-               uint32_t* __restrict__ off) {
+               const uint32_t* __restrict__ block_sums, int nb, uint32_t cap,
+               const uint32_t* count_dev, DevCounters* ctr, uint32_t* __restrict__ off) {
     grid_dep_begin();
     __shared__ uint32_t wt[33];
+    __shared__ unsigned long long red[kScanThreads / 32];
     const uint32_t count = *count_dev;
+    unsigned long long pre = 0;
+    for (int i = threadIdx.x; i < (int)blockIdx.x; i += blockDim.x) pre += block_sums[i];
+    pre = block_sum_u64(pre, red);
+    if (blockIdx.x == 0) {
+        unsigned long long tot = 0;
+        for (int i = threadIdx.x; i < nb; i += blockDim.x) tot += block_sums[i];
+        tot = block_sum_u64(tot, red);
+        if (threadIdx.x == 0) {
+            ctr->n_raw = tot;
+            ctr->vn = count;
+            ctr->n_instances = (uint32_t)min(tot, (unsigned long long)cap);
+            if (tot > cap) atomicOr(&ctr->status, (uint32_t)GS_DEV_CAPACITY);
+        }
+    }
     const uint32_t start = blockIdx.x * (uint32_t)kScanTile;
     uint32_t t[kScanItems], s = 0;
     for (int k = 0; k < kScanItems; ++k) {
@@ -283,7 +283,8 @@ k_scan_offsets(const uint32_t* __restrict__ order, const uint32_t* __restrict__ 
         s += t[k];
     }
     uint32_t tot;
-    uint32_t o = block_exclusive_scan(s, wt, tot) + block_off[blockIdx.x];
+    uint32_t o = block_exclusive_scan(s, wt, tot) +
+                 (uint32_t)min(pre, (unsigned long long)0xFFFFFFFFu);
     for (int k = 0; k < kScanItems; ++k) {
         const uint32_t i = start + threadIdx.x * kScanItems + k;
         if (i < count) {
@@ -528,13 +529,13 @@ gs_status launch_bin_sort(const Plan* p, int32_t n, void* ws, cudaStream_t st) {
     uint32_t* bsums = buf<uint32_t>(p, ws, B_SCAN_BLOCKS);
     const uint32_t* touched = buf<uint32_t>(p, ws, GS_BUF_TOUCHED);
     launch_pdl(k_scan_reduce, snb, kScanThreads, 0, st, va, touched, n_sorted, bsums);
-    launch_pdl(k_scan_blocks, 1, kSortThreads, 0, st, bsums, snb, icap, n_sorted, ctr);
     uint32_t* ika = buf<uint32_t>(p, ws, GS_BUF_TILE_KEYS);
     uint32_t* iva = buf<uint32_t>(p, ws, GS_BUF_TILE_VALUES);
     uint32_t* ikb = buf<uint32_t>(p, ws, B_IKEY_B);
     uint32_t* ivb = buf<uint32_t>(p, ws, B_IVAL_B);
     uint32_t* offs = buf<uint32_t>(p, ws, B_OFFSETS);
-    launch_pdl(k_scan_offsets, snb, kScanThreads, 0, st, va, touched, bsums, n_sorted, offs);
+    launch_pdl(k_scan_offsets, snb, kScanThreads, 0, st, va, touched, bsums, snb, icap, n_sorted,
+               ctr, offs);
     launch_pdl(k_emit, (VN + kEmitEntries - 1) / kEmitEntries, kEmitEntries, 0, st, va, offs,
                buf<uint2>(p, ws, GS_BUF_RECT), n_sorted, n, p->vt, icap, ika, iva,
                p->cfg.deterministic ? buf<uint32_t>(p, ws, B_GID_OF) : nullptr,
