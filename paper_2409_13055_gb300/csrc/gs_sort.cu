@@ -15,6 +15,8 @@
 // passes, the scan and the emission run over the visible pairs only, whose
 // count stays on the device like the instance count.  No kernel waits on
 // another block, so nothing can spin.
+#include <atomic>
+
 #include "gs_internal.cuh"
 
 namespace gs {
@@ -69,17 +71,19 @@ k_radix_hist(const uint32_t* __restrict__ keys, const uint32_t* count_dev, uint3
     constexpr int TILE = kSortThreads * ITEMS;
     __shared__ uint32_t h[kRadix];
     const uint32_t count = min(active_count(count_dev, count_host), cap);
-    const uint32_t start = blockIdx.x * (uint32_t)TILE;
-    if (start >= count) return;
-    h[threadIdx.x] = 0u;
-    __syncthreads();
-    const uint32_t end = min(start + (uint32_t)TILE, count);
-    for (uint32_t i = start + threadIdx.x; i < end; i += kSortThreads) {
-        const uint32_t k = keys[i];
-        if (!(drop && k == kCulledKey)) atomicAdd(&h[(k >> shift) & mask], 1u);
+    // a grid of resident CTAs striding over the sort blocks of the active keys
+    for (uint32_t blk = blockIdx.x; blk * (uint32_t)TILE < count; blk += gridDim.x) {
+        const uint32_t start = blk * (uint32_t)TILE;
+        h[threadIdx.x] = 0u;
+        __syncthreads();
+        const uint32_t end = min(start + (uint32_t)TILE, count);
+        for (uint32_t i = start + threadIdx.x; i < end; i += kSortThreads) {
+            const uint32_t k = keys[i];
+            if (!(drop && k == kCulledKey)) atomicAdd(&h[(k >> shift) & mask], 1u);
+        }
+        __syncthreads();
+        hist[(size_t)threadIdx.x * nb + blk] = h[threadIdx.x];
     }
-    __syncthreads();
-    hist[(size_t)threadIdx.x * nb + blockIdx.x] = h[threadIdx.x];
 }
 
 // One block per digit: exclusive scan of the digit's per-block counts (in
@@ -139,77 +143,80 @@ k_radix_scatter(const uint32_t* __restrict__ keys_in, const uint32_t* __restrict
     __shared__ uint32_t wt[33];
     __shared__ uint32_t skey[TILE], sval[TILE];
     const uint32_t count = min(active_count(count_dev, count_host), cap);
-    const uint32_t start = blockIdx.x * (uint32_t)TILE;
-    if (start >= count) return;
     const int tid = threadIdx.x, lane = tid & 31, w = tid >> 5;
-    // the block's keys and values are loaded first, so that their latency
-    // overlaps the loads and the scan of the digit offsets below
-    uint32_t key[ITEMS], val[ITEMS], rank[ITEMS];
-    const uint32_t wstart = start + (uint32_t)w * kWarpItems;
+    // a grid of resident CTAs striding over the sort blocks of the active keys
+    for (uint32_t blk = blockIdx.x; blk * (uint32_t)TILE < count; blk += gridDim.x) {
+        const uint32_t start = blk * (uint32_t)TILE;
+        // the block's keys and values are loaded first, so that their latency
+        // overlaps the loads and the scan of the digit offsets below
+        uint32_t key[ITEMS], val[ITEMS], rank[ITEMS];
+        const uint32_t wstart = start + (uint32_t)w * kWarpItems;
 #pragma unroll
-    for (int r = 0; r < ITEMS; ++r) {
-        const uint32_t i = wstart + (uint32_t)r * 32u + lane;
-        const bool in = i < count;
-        key[r] = in ? keys_in[i] : 0u;
-        val[r] = in ? (vals_in ? vals_in[i] : i) : 0u;
-    }
-    {
-        uint32_t tot;
-        uint32_t ex = block_exclusive_scan(totals[tid], wt, tot);
-        base[tid] = ex + hist[(size_t)tid * nb + blockIdx.x];
-        if (kept_out && blockIdx.x == 0 && tid == 0) *kept_out = tot;  // keys of all digits
-    }
+        for (int r = 0; r < ITEMS; ++r) {
+            const uint32_t i = wstart + (uint32_t)r * 32u + lane;
+            const bool in = i < count;
+            key[r] = in ? keys_in[i] : 0u;
+            val[r] = in ? (vals_in ? vals_in[i] : i) : 0u;
+        }
+        {
+            uint32_t tot;
+            uint32_t ex = block_exclusive_scan(totals[tid], wt, tot);
+            base[tid] = ex + hist[(size_t)tid * nb + blk];
+            if (kept_out && blk == 0 && tid == 0) *kept_out = tot;  // keys of all digits
+        }
 #pragma unroll
-    for (int k = 0; k < kWarps; ++k) wcnt[k][tid] = 0u;
-    __syncthreads();
+        for (int k = 0; k < kWarps; ++k) wcnt[k][tid] = 0u;
+        __syncthreads();
 
-    const uint32_t lt = (1u << lane) - 1u;
+        const uint32_t lt = (1u << lane) - 1u;
 #pragma unroll
-    for (int r = 0; r < ITEMS; ++r) {
-        const uint32_t i = wstart + (uint32_t)r * 32u + lane;
-        const bool in = i < count;
-        const bool ok = in && !(drop && key[r] == kCulledKey);
-        const uint32_t d = ok ? ((key[r] >> shift) & mask) : 0x10000u;
-        const uint32_t peers = __match_any_sync(0xffffffffu, d);
-        uint32_t rk = 0u;
-        if (ok) rk = wcnt[w][d] + __popc(peers & lt);
-        __syncwarp();
-        if (ok && (__ffs(peers) - 1) == lane) wcnt[w][d] += __popc(peers);
-        __syncwarp();
-        rank[r] = rk;
-    }
-    __syncthreads();
-    uint32_t digit_count = 0u;
-#pragma unroll
-    for (int k = 0; k < kWarps; ++k) {
-        const uint32_t c = wcnt[k][tid];
-        wcnt[k][tid] = digit_count;
-        digit_count += c;
-    }
-    uint32_t n_kept;  // keys of this block that are written (all of them without drop)
-    local[tid] = block_exclusive_scan(digit_count, wt, n_kept);
-    __syncthreads();
-#pragma unroll
-    for (int r = 0; r < ITEMS; ++r) {
-        const uint32_t i = wstart + (uint32_t)r * 32u + lane;
-        if (i < count && !(drop && key[r] == kCulledKey)) {
-            const uint32_t d = (key[r] >> shift) & mask;
-            const uint32_t s = local[d] + wcnt[w][d] + rank[r];
-            skey[s] = key[r];
-            sval[s] = val[r];
+        for (int r = 0; r < ITEMS; ++r) {
+            const uint32_t i = wstart + (uint32_t)r * 32u + lane;
+            const bool in = i < count;
+            const bool ok = in && !(drop && key[r] == kCulledKey);
+            const uint32_t d = ok ? ((key[r] >> shift) & mask) : 0x10000u;
+            const uint32_t peers = __match_any_sync(0xffffffffu, d);
+            uint32_t rk = 0u;
+            if (ok) rk = wcnt[w][d] + __popc(peers & lt);
+            __syncwarp();
+            if (ok && (__ffs(peers) - 1) == lane) wcnt[w][d] += __popc(peers);
+            __syncwarp();
+            rank[r] = rk;
         }
-    }
-    __syncthreads();
+        __syncthreads();
+        uint32_t digit_count = 0u;
 #pragma unroll
-    for (int r = 0; r < ITEMS; ++r) {
-        const int s = r * kSortThreads + tid;
-        if ((uint32_t)s < n_kept) {
-            const uint32_t k = skey[s];
-            const uint32_t d = (k >> shift) & mask;
-            const uint32_t pos = base[d] + ((uint32_t)s - local[d]);
-            keys_out[pos] = k;
-            vals_out[pos] = sval[s];
+        for (int k = 0; k < kWarps; ++k) {
+            const uint32_t c = wcnt[k][tid];
+            wcnt[k][tid] = digit_count;
+            digit_count += c;
         }
+        uint32_t n_kept;  // keys of this block that are written (all of them without drop)
+        local[tid] = block_exclusive_scan(digit_count, wt, n_kept);
+        __syncthreads();
+#pragma unroll
+        for (int r = 0; r < ITEMS; ++r) {
+            const uint32_t i = wstart + (uint32_t)r * 32u + lane;
+            if (i < count && !(drop && key[r] == kCulledKey)) {
+                const uint32_t d = (key[r] >> shift) & mask;
+                const uint32_t s = local[d] + wcnt[w][d] + rank[r];
+                skey[s] = key[r];
+                sval[s] = val[r];
+            }
+        }
+        __syncthreads();
+#pragma unroll
+        for (int r = 0; r < ITEMS; ++r) {
+            const int s = r * kSortThreads + tid;
+            if ((uint32_t)s < n_kept) {
+                const uint32_t k = skey[s];
+                const uint32_t d = (k >> shift) & mask;
+                const uint32_t pos = base[d] + ((uint32_t)s - local[d]);
+                keys_out[pos] = k;
+                vals_out[pos] = sval[s];
+            }
+        }
+        __syncthreads();  // the next block reuses the shared arrays
     }
 }
 
@@ -297,11 +304,20 @@ k_scan_offsets(const uint32_t* __restrict__ order, const uint32_t* __restrict__ 
 
 // Emit one instance per (Gaussian, tile in its rect), walking the depth
 // order; tiles of a rect in row-major order.  Each CTA takes kEmitEntries
-// consecutive entries and writes their instances consecutively, every thread
-// locating the entry of its output slot by binary search over the entries'
-// offsets in shared memory: coalesced writes and no thread left alone with a
+// consecutive entries and writes their instances consecutively, in rounds
+// of kEmitRun * kEmitEntries output slots: every thread fills a run of
+// kEmitRun consecutive slots (one binary search over the entries' offsets in
+// shared memory for the run's first slot, then tile after tile of the entry
+// and on to the next entry) into a shared-memory copy of the round, which the
+// CTA then writes out with coalesced stores.  No thread is left alone with a
 // large rect.
 constexpr int kEmitEntries = 256;
+constexpr int kEmitRun = 8;
+constexpr int kEmitRound = kEmitRun * kEmitEntries;
+// shared-memory slot of round position q: one pad word per 32, so that the
+// runs' writes (stride kEmitRun) and the write-out's reads (stride 1) are free
+// of bank conflicts
+__device__ __forceinline__ int emit_slot(int q) { return q + (q >> 5); }
 
 __global__ void __launch_bounds__(kEmitEntries)
 k_emit(const uint32_t* __restrict__ order, const uint32_t* __restrict__ off,
@@ -318,83 +334,158 @@ k_emit(const uint32_t* __restrict__ order, const uint32_t* __restrict__ off,
     // or, for a taller box, the pool index of its first row in s_span[e][0]
     __shared__ __align__(16) uint32_t s_span[kEmitEntries][kSpanRows];
     __shared__ uint16_t s_view[kEmitEntries];
+    // the round's instances: tile keys and (view, Gaussian) indices
+    __shared__ uint32_t s_key[kEmitRound + kEmitRound / 32];
+    __shared__ uint32_t s_val[kEmitRound + kEmitRound / 32];
     const uint32_t count = *count_dev;
-    const uint32_t e0 = blockIdx.x * (uint32_t)kEmitEntries;
-    if (e0 >= count) return;
-    const uint32_t ne = min((uint32_t)kEmitEntries, count - e0);
-    const int e = threadIdx.x;
-    if ((uint32_t)e < ne) {
-        const uint32_t vg = order[e0 + e];
-        s_off[e] = off[e0 + e];
-        s_vg[e] = vg;
-        s_rect[e] = rects[vg];
-        s_view[e] = (uint16_t)(vg / (uint32_t)n);
-        if (vt.tight_rect && s_off[e] != off[e0 + e + 1]) {
-            const uint2 rc = s_rect[e];
-            const int rows = (int)(rc.y >> 16) - (int)(rc.x >> 16);
-            const int nw = rows > kSpanRows ? 1 : rows;
-            // whole 16-byte groups of the entry's 64-byte span record
+    // a grid of resident CTAs striding over the groups of entries
+    for (uint32_t e0 = blockIdx.x * (uint32_t)kEmitEntries; e0 < count;
+         e0 += gridDim.x * (uint32_t)kEmitEntries) {
+        const uint32_t ne = min((uint32_t)kEmitEntries, count - e0);
+        const int e = threadIdx.x;
+        if ((uint32_t)e < ne) {
+            const uint32_t vg = order[e0 + e];
+            const uint32_t o0 = off[e0 + e], o1 = off[e0 + e + 1];
+            const uint2 rc = rects[vg];
+            // whole 16-byte groups of the entry's 64-byte span record; the
+            // first (rows 0-3) is loaded beside the rect, the others only for
+            // taller boxes
             const uint4* src = reinterpret_cast<const uint4*>(spans + (size_t)vg * kSpanRows);
-            uint4* dst = reinterpret_cast<uint4*>(s_span[e]);
-            for (int q = 0; q < (nw + 3) / 4; ++q) dst[q] = src[q];
-        }
-    }
-    if (e == 0) s_off[ne] = off[e0 + ne];
-    __syncthreads();
-    const uint32_t first = s_off[0], last = s_off[ne];
-    for (uint32_t pos = first + threadIdx.x; pos < last; pos += blockDim.x) {
-        if (pos >= cap) break;
-        int lo = 0, hi = (int)ne;  // invariant: s_off[lo] <= pos < s_off[hi]
-        while (hi - lo > 1) {
-            const int mid = (lo + hi) >> 1;
-            if (s_off[mid] <= pos) lo = mid; else hi = mid;
-        }
-        const uint2 rc = s_rect[lo];
-        const uint32_t x0 = rc.x & 0xFFFF, y0 = rc.x >> 16, x1 = rc.y & 0xFFFF, y1 = rc.y >> 16;
-        const uint32_t w = x1 - x0, k = pos - s_off[lo];
-        uint32_t tx, ty;
-        const bool tall = y1 - y0 > (uint32_t)kSpanRows;
-        if (vt.tight_rect && !(tall && s_span[lo][0] == kSpanNoPool)) {
-            // the k-th tile of the row spans the projection stored and counted
-            const uint32_t* sr = tall ? pool + s_span[lo][0] : s_span[lo];
-            uint32_t kk = k, r = 0, sp = sr[0];
-            for (; r + 1 < y1 - y0; ++r) {
-                const uint32_t wr = (sp >> 16) - (sp & 0xFFFF);
-                if (kk < wr) break;
-                kk -= wr;
-                sp = sr[r + 1];
+            const uint4 sp0 = vt.tight_rect ? src[0] : make_uint4(0u, 0u, 0u, 0u);
+            s_off[e] = o0;
+            s_vg[e] = vg;
+            s_rect[e] = rc;
+            s_view[e] = (uint16_t)(vg / (uint32_t)n);
+            if (vt.tight_rect && o0 != o1) {
+                const int rows = (int)(rc.y >> 16) - (int)(rc.x >> 16);
+                const int nw = rows > kSpanRows ? 1 : rows;
+                uint4* dst = reinterpret_cast<uint4*>(s_span[e]);
+                dst[0] = sp0;
+                for (int q = 1; q < (nw + 3) / 4; ++q) dst[q] = src[q];
             }
-            ty = y0 + r;
-            // (a count that disagreed would land past the row; stay inside the rect)
-            tx = min((sp & 0xFFFF) + kk, x1 - 1u);
-        } else {
-            const uint32_t dy = k / w;
-            ty = y0 + dy;
-            tx = x0 + (k - dy * w);
         }
-        const ViewGeom& geo = vt.v[s_view[lo]];
-        ikeys[pos] = (uint32_t)geo.tile_offset + ty * (uint32_t)geo.tiles_x + tx;
-        if (gid_of) {
-            // deterministic plans: the sort carries the emission position
-            ivals[pos] = pos;
-            gid_of[pos] = s_vg[lo];
-        } else {
-            ivals[pos] = s_vg[lo];
+        if (e == 0) s_off[ne] = off[e0 + ne];
+        __syncthreads();
+        const uint32_t first = s_off[0], stop = min(s_off[ne], cap);
+        for (uint32_t base = first; base < stop; base += kEmitRound) {
+            const uint32_t nr = min((uint32_t)kEmitRound, stop - base);  // slots of this round
+            uint32_t p = base + (uint32_t)threadIdx.x * kEmitRun;
+            const uint32_t p_end = min(p + kEmitRun, base + nr);
+            if (p < p_end) {
+                int lo = 0, hi = (int)ne;  // invariant: s_off[lo] <= p < s_off[hi]
+                while (hi - lo > 1) {
+                    const int mid = (lo + hi) >> 1;
+                    if (s_off[mid] <= p) lo = mid; else hi = mid;
+                }
+                for (;;) {
+                    // entry lo's tiles k = p - s_off[lo], ... of this run
+                    const uint32_t e_end = min(s_off[lo + 1], p_end);
+                    const uint2 rc = s_rect[lo];
+                    const uint32_t x0 = rc.x & 0xFFFF, y0 = rc.x >> 16, x1 = rc.y & 0xFFFF,
+                                   y1 = rc.y >> 16;
+                    const ViewGeom& geo = vt.v[s_view[lo]];
+                    const uint32_t kbase = (uint32_t)geo.tile_offset, tiles_x = (uint32_t)geo.tiles_x;
+                    const uint32_t vg = s_vg[lo];
+                    const uint32_t k = p - s_off[lo];
+                    const bool tall = y1 - y0 > (uint32_t)kSpanRows;
+                    if (vt.tight_rect && !(tall && s_span[lo][0] == kSpanNoPool)) {
+                        // the k-th tile of the row spans the projection stored and
+                        // counted, then the ones after it (row r, kk-th tile of the row)
+                        const uint32_t* sr = tall ? pool + s_span[lo][0] : s_span[lo];
+                        const uint32_t nrows = y1 - y0;
+                        uint32_t kk = k, r = 0, sp = sr[0];
+                        for (;;) {
+                            for (; r + 1 < nrows; ++r) {
+                                const uint32_t wr = (sp >> 16) - (sp & 0xFFFF);
+                                if (kk < wr) break;
+                                kk -= wr;
+                                sp = sr[r + 1];
+                            }
+                            // (a count that disagreed would land past the row; stay
+                            // inside the rect)
+                            const uint32_t tx = min((sp & 0xFFFF) + kk, x1 - 1u);
+                            const int q = emit_slot((int)(p - base));
+                            s_key[q] = kbase + (y0 + r) * tiles_x + tx;
+                            s_val[q] = vg;
+                            if (++p == e_end) break;
+                            ++kk;
+                        }
+                    } else {
+                        const uint32_t w = x1 - x0;
+                        const uint32_t dy = k / w;
+                        uint32_t ty = y0 + dy, tx = x0 + (k - dy * w);
+                        for (;;) {
+                            const int q = emit_slot((int)(p - base));
+                            s_key[q] = kbase + ty * tiles_x + tx;
+                            s_val[q] = vg;
+                            if (++p == e_end) break;
+                            if (++tx == x1) {
+                                tx = x0;
+                                ++ty;
+                            }
+                        }
+                    }
+                    if (p == p_end) break;
+                    // the next entry with instances
+                    do {
+                        ++lo;
+                    } while (s_off[lo + 1] <= p);
+                }
+            }
+            __syncthreads();
+            for (uint32_t q = threadIdx.x; q < nr; q += kEmitEntries) {
+                const uint32_t pos = base + q;
+                const int sq = emit_slot((int)q);
+                ikeys[pos] = s_key[sq];
+                if (gid_of) {
+                    // deterministic plans: the sort carries the emission position
+                    ivals[pos] = pos;
+                    gid_of[pos] = s_val[sq];
+                } else {
+                    ivals[pos] = s_val[sq];
+                }
+            }
+            __syncthreads();
         }
+        __syncthreads();  // the next group reuses the shared arrays
     }
 }
 
+// Per-tile [begin, end) of the sorted instance keys: a tile's range starts
+// where the key differs from the one before it and ends where it differs from
+// the one after.  Each thread takes four consecutive keys (one 16-byte load;
+// the workspace's buffers are 256-byte aligned) and the keys on either side.
 __global__ void k_ranges(const uint32_t* __restrict__ keys, const uint32_t* count_dev,
                          uint32_t* __restrict__ ranges, uint32_t* __restrict__ order_scratch) {
     grid_dep_begin();
     // the tile order's bucket counts and cursors start at zero
     if (blockIdx.x == 0 && threadIdx.x < 2 * kOrderBuckets) order_scratch[threadIdx.x] = 0u;
+    constexpr uint32_t kNone = 0xFFFFFFFFu;  // past either end (never a tile id)
     const uint32_t count = *count_dev;
-    for (uint32_t i = blockIdx.x * blockDim.x + threadIdx.x; i < count;
-         i += gridDim.x * blockDim.x) {
-        const uint32_t k = keys[i];
-        if (i == 0 || keys[i - 1] != k) ranges[2 * k] = i;
-        if (i + 1 == count || keys[i + 1] != k) ranges[2 * k + 1] = i + 1;
+    const uint32_t ngroups = (count + 3) / 4;
+    for (uint32_t g = blockIdx.x * blockDim.x + threadIdx.x; g < ngroups;
+         g += gridDim.x * blockDim.x) {
+        const uint32_t i0 = 4 * g;
+        uint32_t k[6];  // the keys at i0 - 1 .. i0 + 4
+        if (i0 + 4 <= count) {
+            const uint4 v = reinterpret_cast<const uint4*>(keys)[g];
+            k[1] = v.x;
+            k[2] = v.y;
+            k[3] = v.z;
+            k[4] = v.w;
+        } else {
+#pragma unroll
+            for (int j = 0; j < 4; ++j) k[1 + j] = i0 + j < count ? keys[i0 + j] : kNone;
+        }
+        k[0] = i0 > 0 ? keys[i0 - 1] : kNone;
+        k[5] = i0 + 4 < count ? keys[i0 + 4] : kNone;
+#pragma unroll
+        for (int j = 0; j < 4; ++j) {
+            const uint32_t key = k[1 + j];
+            if (key == kNone) break;
+            if (k[j] != key) ranges[2 * key] = i0 + j;
+            if (k[2 + j] != key) ranges[2 * key + 1] = i0 + j + 1;
+        }
     }
 }
 
@@ -452,6 +543,24 @@ k_tile_order(const uint32_t* __restrict__ ranges, int T, const uint32_t* __restr
     }
 }
 
+// CTAs of a grid-stride kernel resident at once on this GPU (its occupancy
+// per SM, cached per kernel, times the SMs): the binning's kernels whose work
+// is counted on the device launch this many at most, so that no CTA is
+// launched only to find nothing to do.
+template <auto Kernel>
+int resident_grid(int threads) {
+    static std::atomic<int> per_sm{0};
+    int b = per_sm.load(std::memory_order_relaxed);
+    if (b <= 0) {
+        if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&b, Kernel, threads, 0) !=
+                cudaSuccess ||
+            b < 1)
+            b = 1;
+        per_sm.store(b, std::memory_order_relaxed);
+    }
+    return b * sm_count();
+}
+
 template <int ITEMS>
 gs_status radix_pass_t(const uint32_t* kin, const uint32_t* vin, uint32_t* kout, uint32_t* vout,
                        const uint32_t* count_dev, uint32_t count_host, uint32_t cap, int shift,
@@ -460,11 +569,13 @@ gs_status radix_pass_t(const uint32_t* kin, const uint32_t* vin, uint32_t* kout,
     const int nb = (int)((cap + kSortThreads * ITEMS - 1) / (kSortThreads * ITEMS));
     const int drop = kept_out != nullptr;
     const uint32_t mask = (1u << bits) - 1u;
-    launch_pdl(k_radix_hist<ITEMS>, nb, kSortThreads, 0, st, kin, count_dev, count_host, cap,
+    const int hg = min(nb, resident_grid<k_radix_hist<ITEMS>>(kSortThreads));
+    const int sg = min(nb, resident_grid<k_radix_scatter<ITEMS>>(kSortThreads));
+    launch_pdl(k_radix_hist<ITEMS>, hg, kSortThreads, 0, st, kin, count_dev, count_host, cap,
                shift, mask, nb, drop, hist);
     launch_pdl(k_radix_scan<ITEMS>, kRadix, kSortThreads, 0, st, hist, count_dev, count_host,
                cap, nb, totals);
-    launch_pdl(k_radix_scatter<ITEMS>, nb, kSortThreads, 0, st, kin, vin, kout, vout, count_dev,
+    launch_pdl(k_radix_scatter<ITEMS>, sg, kSortThreads, 0, st, kin, vin, kout, vout, count_dev,
                count_host, cap, shift, mask, nb, hist, totals, drop, kept_out);
     return launch_status();
 }
@@ -536,7 +647,9 @@ gs_status launch_bin_sort(const Plan* p, int32_t n, void* ws, cudaStream_t st) {
     uint32_t* offs = buf<uint32_t>(p, ws, B_OFFSETS);
     launch_pdl(k_scan_offsets, snb, kScanThreads, 0, st, va, touched, bsums, snb, icap, n_sorted,
                ctr, offs);
-    launch_pdl(k_emit, (VN + kEmitEntries - 1) / kEmitEntries, kEmitEntries, 0, st, va, offs,
+    const int eg = (int)min((VN + kEmitEntries - 1) / kEmitEntries,
+                            (uint32_t)resident_grid<k_emit>(kEmitEntries));
+    launch_pdl(k_emit, eg, kEmitEntries, 0, st, va, offs,
                buf<uint2>(p, ws, GS_BUF_RECT), n_sorted, n, p->vt, icap, ika, iva,
                p->cfg.deterministic ? buf<uint32_t>(p, ws, B_GID_OF) : nullptr,
                buf<uint32_t>(p, ws, B_SPANS), cbuf<uint32_t>(p, ws, B_SPAN_POOL));
