@@ -294,6 +294,28 @@ __device__ __forceinline__ void project_one(const float* mean, const Shape& sh, 
     p.visible = true;
 }
 
+// Ask the L2 for the cache lines of Gaussian g's K SH coefficients
+// (coefficient-major, three floats each), so that the loads that come after
+// the long arithmetic before them find them there.
+template <int K>
+__device__ __forceinline__ void prefetch_sh(const float* __restrict__ sh, int n, int g) {
+#pragma unroll
+    for (int k = 0; k < K; ++k)
+        asm volatile("prefetch.global.L2 [%0];" ::"l"(sh + ((size_t)k * n + g) * 3));
+}
+
+// ... and the lines of Gaussian g's mean, log-scales, quaternion and opacity
+// logit.
+__device__ __forceinline__ void prefetch_params(const float* __restrict__ means,
+                                                const float* __restrict__ log_scales,
+                                                const float* __restrict__ quats,
+                                                const float* __restrict__ opacity_logits, int g) {
+    asm volatile("prefetch.global.L2 [%0];" ::"l"(means + 3 * (size_t)g));
+    asm volatile("prefetch.global.L2 [%0];" ::"l"(log_scales + 3 * (size_t)g));
+    asm volatile("prefetch.global.L2 [%0];" ::"l"(quats + 4 * (size_t)g));
+    asm volatile("prefetch.global.L2 [%0];" ::"l"(opacity_logits + g));
+}
+
 template <int DEG>
 __global__ void __launch_bounds__(kProjThreads, 4)
 k_project(const float* __restrict__ means, const float* __restrict__ log_scales,
@@ -332,6 +354,7 @@ k_project(const float* __restrict__ means, const float* __restrict__ log_scales,
         bool vis = finite && p.visible;
         uint32_t area = 0u;
         if (vis) {
+            prefetch_sh<K>(sh, n, g);
             area = (uint32_t)((p.rect[2] - p.rect[0]) * (p.rect[3] - p.rect[1]));
             if (vt.tight_rect) {
                 // the row spans of the box, stored for the emission: in the
@@ -450,11 +473,16 @@ __device__ __forceinline__ void adjoint_one(
     float gm[3] = {0.f, 0.f, 0.f};
     float gsig[6] = {0.f, 0.f, 0.f, 0.f, 0.f, 0.f};  // dL/dSigma as a symmetric matrix
     float gop = 0.0f;
-    bool sh_written = false;
+    bool sh_written = false, sh_fetched = false;
 
     for (int v = 0; v < vt.n_views; ++v) {
         const size_t vg = (size_t)v * n + g;
         if (touched[vg] == 0u) continue;
+        if (!sh_fetched) {
+            // the SH coefficients are read after the projection below
+            prefetch_sh<K>(sh, n, g);
+            sh_fetched = true;
+        }
         const float* g2 = grad2d + vg * kGrad2d;
         float gmx = g2[0], gmy = g2[1], gA = g2[2], gB = g2[3], gC = g2[4], gO = g2[5];
         float gcol[3] = {g2[6], g2[7], g2[8]};
@@ -647,31 +675,42 @@ k_project_bwd(const float* __restrict__ means, const float* __restrict__ log_sca
     extern __shared__ Cam cam_all[];
     for (int v = threadIdx.x; v < vt.n_views; v += blockDim.x) load_cam(views[v], cam_all[v]);
     __syncthreads();
-    const int g = blockIdx.x * blockDim.x + threadIdx.x;
-    if (group_vis && !group_touched(g, n, vt.n_views, touched, group_vis)) return;
-    if (g >= n) return;
-    float gm[3], gls[3], glog;
-    float4 gq4;
-    adjoint_one<DEG, DIRECT ? kShDirect : kShViaGcol>(
-        g, means, log_scales, quats, opacity_logits, sh, n, cam_all, vt, near_z, touched, grad2d,
-        gcol_out, DIRECT ? g_sh + (size_t)g * 3 : nullptr, (size_t)3 * n, accumulate, gm, gls,
-        gq4, glog);
-    if (accumulate) {
-        for (int e = 0; e < 3; ++e) {
-            g_means[3 * g + e] += gm[e];
-            g_ls[3 * g + e] += gls[e];
+    // a grid of resident CTAs striding over the Gaussians (whole warps: the
+    // group vote stays warp-wide); a thread's next Gaussian's touched words
+    // and parameters go to the L2 while it works on this one
+    const int stride = gridDim.x * blockDim.x;
+    for (int g0 = blockIdx.x * blockDim.x; g0 < n; g0 += stride) {
+        const int g = g0 + threadIdx.x;
+        if (g + stride < n) {
+            for (int v = 0; v < vt.n_views; ++v)
+                asm volatile("prefetch.global.L2 [%0];" ::"l"(touched + (size_t)v * n + g + stride));
+            prefetch_params(means, log_scales, quats, opacity_logits, g + stride);
         }
-        float4 o = reinterpret_cast<float4*>(g_quats)[g];
-        o.x += gq4.x; o.y += gq4.y; o.z += gq4.z; o.w += gq4.w;
-        reinterpret_cast<float4*>(g_quats)[g] = o;
-        g_logit[g] += glog;
-    } else {
-        for (int e = 0; e < 3; ++e) {
-            g_means[3 * g + e] = gm[e];
-            g_ls[3 * g + e] = gls[e];
+        if (group_vis && !group_touched(g, n, vt.n_views, touched, group_vis)) continue;
+        if (g >= n) continue;
+        float gm[3], gls[3], glog;
+        float4 gq4;
+        adjoint_one<DEG, DIRECT ? kShDirect : kShViaGcol>(
+            g, means, log_scales, quats, opacity_logits, sh, n, cam_all, vt, near_z, touched, grad2d,
+            gcol_out, DIRECT ? g_sh + (size_t)g * 3 : nullptr, (size_t)3 * n, accumulate, gm, gls,
+            gq4, glog);
+        if (accumulate) {
+            for (int e = 0; e < 3; ++e) {
+                g_means[3 * g + e] += gm[e];
+                g_ls[3 * g + e] += gls[e];
+            }
+            float4 o = reinterpret_cast<float4*>(g_quats)[g];
+            o.x += gq4.x; o.y += gq4.y; o.z += gq4.z; o.w += gq4.w;
+            reinterpret_cast<float4*>(g_quats)[g] = o;
+            g_logit[g] += glog;
+        } else {
+            for (int e = 0; e < 3; ++e) {
+                g_means[3 * g + e] = gm[e];
+                g_ls[3 * g + e] = gls[e];
+            }
+            reinterpret_cast<float4*>(g_quats)[g] = gq4;
+            g_logit[g] = glog;
         }
-        reinterpret_cast<float4*>(g_quats)[g] = gq4;
-        g_logit[g] = glog;
     }
 }
 
@@ -907,6 +946,19 @@ k_adjoint_adam(const float* __restrict__ means, const float* __restrict__ log_sc
                      stage + (11 + 3 * k) * C, k == 0 ? fa.lr[4] : fa.lr[5], fa.lr[5]);
 }
 
+// The CTAs of a grid-stride kernel resident at once on this GPU (its
+// occupancy per SM times the SMs), and no more than `needed`.
+template <class K>
+int resident_grid(K kernel, int threads, size_t smem, int needed) {
+    int per_sm = 0;
+    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kernel, threads, smem) !=
+            cudaSuccess ||
+        per_sm < 1)
+        per_sm = 1;
+    const int r = per_sm * sm_count();
+    return needed < r ? needed : (r > 0 ? r : 1);
+}
+
 }  // namespace
 
 gs_status launch_project(const Plan* p, const gs_map* map, const gs_view* views_dev, void* ws,
@@ -920,12 +972,12 @@ gs_status launch_project(const Plan* p, const gs_map* map, const gs_view* views_
     if (cudaMemsetAsync(reinterpret_cast<char*>(ctr) + keep, 0, sizeof(DevCounters) - keep, st) !=
         cudaSuccess)
         return GS_ERR_CUDA;
-    dim3 grid((n + kProjThreads - 1) / kProjThreads,
-              (p->vt.n_views + kViewsPerThread - 1) / kViewsPerThread);
     auto* kern = map->sh_degree == 0   ? k_project<0>
                  : map->sh_degree == 1 ? k_project<1>
                  : map->sh_degree == 2 ? k_project<2>
                                        : k_project<3>;
+    dim3 grid((n + kProjThreads - 1) / kProjThreads,
+              (p->vt.n_views + kViewsPerThread - 1) / kViewsPerThread);
     kern<<<grid, kProjThreads, 0, st>>>(
         map->means, map->log_scales, map->quats, map->opacity_logits, map->sh, n, views_dev,
         p->vt, p->cfg.near_z, buf<float4>(p, ws, GS_BUF_PROJ), buf<uint16_t>(p, ws, GS_BUF_RECT),
@@ -941,7 +993,6 @@ static gs_status launch_project_adjoint(const Plan* p, const gs_map* map,
                                         uint8_t* group_vis, cudaStream_t st) {
     const int n = map->n;
     const size_t smem = sizeof(Cam) * p->vt.n_views;
-    const int blocks = (n + kProjThreads - 1) / kProjThreads;
     const bool direct = p->vt.n_views == 1;
     auto* kern = direct ? (map->sh_degree == 0   ? k_project_bwd<0, true>
                            : map->sh_degree == 1 ? k_project_bwd<1, true>
@@ -951,6 +1002,8 @@ static gs_status launch_project_adjoint(const Plan* p, const gs_map* map,
                            : map->sh_degree == 1 ? k_project_bwd<1, false>
                            : map->sh_degree == 2 ? k_project_bwd<2, false>
                                                  : k_project_bwd<3, false>);
+    const int blocks =
+        resident_grid(kern, kProjThreads, smem, (n + kProjThreads - 1) / kProjThreads);
     kern<<<blocks, kProjThreads, smem, st>>>(
         map->means, map->log_scales, map->quats, map->opacity_logits, map->sh, n, views_dev,
         p->vt, p->cfg.near_z, buf<uint32_t>(p, ws, GS_BUF_TOUCHED),
