@@ -113,6 +113,37 @@ def test_binning_bit_exact(case, tile):
     assert compared > 100 and removed <= max(50, 0.01 * compared)
 
 
+def test_emission_of_large_gaussians_in_several_rounds():
+    """Gaussians that cover the whole image (768 tiles each, taller than the
+    16 stored span rows, so their rows come from the span pool) among small
+    ones: an emission CTA's entries then hold ~10k instances, written in
+    several rounds of per-thread runs.  The lists are checked as in
+    test_binning_bit_exact, against the GPU's own counts and the oracle."""
+    tile = (8, 8)
+    p, view = scenes.tiny_scene(400, 256, 192, seed=41, sh_degree=1)
+    big = np.arange(0, 400, 13)  # 31 Gaussians
+    p["log_scales"][big] = np.log(1.5)
+    p["opacity_logits"][big] = 3.0
+    gm, rast = run_forward(p, view, tile=tile)
+    g = U.gpu_projection(rast, gm.n)
+    ranges, keys, vals, c = U.gpu_tile_lists(rast)
+    assert c.status == 0 and c.n_instances == c.n_instances_raw
+    tx, ty = oracle.tile_grid(view["width"], view["height"], *tile)
+    assert np.sum(g["touched"][big] == tx * ty) >= 10  # whole-image boxes
+    assert c.n_instances > 2 * 2048
+    np.testing.assert_array_equal(np.bincount(vals, minlength=gm.n), g["touched"])
+    order = np.lexsort((vals, g["depth32"][vals], keys))
+    np.testing.assert_array_equal(order, np.arange(len(vals)))
+    start = np.concatenate([[0], np.cumsum(np.bincount(keys, minlength=tx * ty))])
+    np.testing.assert_array_equal(ranges[:, 0], start[:-1])
+    np.testing.assert_array_equal(ranges[:, 1], start[1:])
+    o = oracle.project(p, view, *tile)
+    compared, removed = U.compare_tile_lists(keys, vals, gm.n, o, view, tile)
+    # a whole-image box meets many tile edges, so a few of them are guarded
+    # (6 of the 400 Gaussians here, 3844 of 28156 pairs)
+    assert compared > 20000 and np.count_nonzero(o["guard"]) <= 10
+
+
 def test_depth_order_holds_the_visible_pairs_and_binning_repeats():
     """The first depth pass drops the culled pairs: the depth order lists
     exactly the Gaussians with a tile, by (FP32 depth key, index), and a
