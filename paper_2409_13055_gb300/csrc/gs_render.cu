@@ -239,7 +239,10 @@ __device__ __forceinline__ PixelRun pixel_run(int tid, int ppt, int log2_tw, int
 // live: bit k set while pixel k still accumulates.  The loop is warp-uniform
 // (a lane whose pixels are done runs predicated) so the warp can vote: a
 // Gaussian that no pixel of the warp blends costs only its alpha evaluation,
-// and the warp leaves the batch once none of its pixels is live.
+// and the warp leaves the batch once none of its pixels is live.  That test
+// runs only where no pixel blended the Gaussian: a pixel that is done
+// blends nothing, so once all are done the next Gaussian lands there, and a
+// blended Gaussian carries no second vote.
 //
 // With an even PPT the pixels go in pairs on packed FP32 pair operations,
 // each half the scalar operation of the odd-PPT path on the same operands;
@@ -278,7 +281,10 @@ __device__ __forceinline__ void blend_batch(int tid, const float4* stage, const 
                 if (((live >> (2 * p + 1)) & 1u) && pw.y <= 0.0f && na[p].y <= -kAlphaMin)
                     hits |= 1u << (2 * p + 1);
             }
-            if (!__any_sync(0xffffffffu, hits != 0u)) continue;
+            if (!__any_sync(0xffffffffu, hits != 0u)) {
+                if (!__any_sync(0xffffffffu, live != 0u)) return;
+                continue;
+            }
             const float4 col = stage[3 * j + 2];
 #pragma unroll
             for (int p = 0; p < NP; ++p) {
@@ -316,7 +322,6 @@ __device__ __forceinline__ void blend_batch(int tid, const float4* stage, const 
                 live = s0 ? (live & ~(1u << k0)) : live;
                 live = s1 ? (live & ~(1u << k1)) : live;
             }
-            if (!__any_sync(0xffffffffu, live != 0u)) return;
         }
         return;
     }
@@ -334,7 +339,10 @@ __device__ __forceinline__ void blend_batch(int tid, const float4* stage, const 
             al[k] = alpha_of(q.w, power);
             if (((live >> k) & 1u) && power <= 0.0f && al[k] >= kAlphaMin) hits |= 1u << k;
         }
-        if (!__any_sync(0xffffffffu, hits != 0u)) continue;
+        if (!__any_sync(0xffffffffu, hits != 0u)) {
+            if (!__any_sync(0xffffffffu, live != 0u)) return;
+            continue;
+        }
         const float4 col = stage[3 * j + 2];
 #pragma unroll
         for (int k = 0; k < PPT; ++k) {
@@ -354,7 +362,6 @@ __device__ __forceinline__ void blend_batch(int tid, const float4* stage, const 
             last[k] = add ? (int32_t)(pos0 + j + 1) : last[k];
             live = stop ? (live & ~(1u << k)) : live;
         }
-        if (!__any_sync(0xffffffffu, live != 0u)) return;
     }
 }
 
