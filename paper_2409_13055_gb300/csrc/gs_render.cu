@@ -235,6 +235,18 @@ __device__ __forceinline__ PixelRun pixel_run(int tid, int ppt, int log2_tw, int
     return r;
 }
 
+// The Gaussians j0 .. j0 + 31 of a batch of cnt that a warp evaluates, as a
+// warp-uniform bitmask: all that exist, or with cull those whose warp mask
+// names the warp (bit wbit).  The blend loops walk its set bits, so a
+// Gaussian culled for the warp costs nothing.
+__device__ __forceinline__ unsigned chunk_todo(int j0, int cnt, const uint32_t* wmask,
+                                               uint32_t wbit, bool cull) {
+    const int n = cnt - j0;
+    if (!cull) return n >= 32 ? 0xffffffffu : ((1u << n) - 1u);
+    const int j = j0 + (int)(threadIdx.x & 31);
+    return __ballot_sync(0xffffffffu, j < cnt && (wmask[j] & wbit) != 0u);
+}
+
 // Front-to-back blending of one staged batch for the PPT pixels of a thread.
 // live: bit k set while pixel k still accumulates.  The loop is warp-uniform
 // (a lane whose pixels are done runs predicated) so the warp can vote: a
@@ -258,28 +270,93 @@ __device__ __forceinline__ void blend_batch(int tid, const float4* stage, const 
     if (!__any_sync(0xffffffffu, live != 0u)) return;
     if constexpr (PPT % 2 == 0) {
         constexpr int NP = PPT / 2;
-        for (int j = 0; j < cnt; ++j) {
-            if (cull && !(wmask[j] & wbit)) continue;
+        for (int j0 = 0; j0 < cnt; j0 += 32) {
+            unsigned todo = chunk_todo(j0, cnt, wmask, wbit, cull);
+            while (todo != 0u) {
+                const int j = j0 + __ffs(todo) - 1;
+                todo &= todo - 1u;
+                const float4 g = stage[3 * j];
+                const float4 q = stage[3 * j + 1];
+                const float dy = g.y - ly;
+                const float cdd = __fmul_rn(q.z, __fmul_rn(dy, dy));
+                const float2 gx2 = make_float2(g.x, g.x), a2 = make_float2(g.z, g.z);
+                const float2 cdd2 = make_float2(cdd, cdd), dy2 = make_float2(dy, dy);
+                const float2 nb2 = make_float2(-g.w, -g.w), no2 = make_float2(-q.w, -q.w);
+                float2 na[NP];
+                unsigned hits = 0u;
+#pragma unroll
+                for (int p = 0; p < NP; ++p) {
+                    const float2 dx = add2(gx2, nlx[p]);
+                    const float2 qq = fma2(a2, mul2(dx, dx), cdd2);
+                    const float2 pw = fma2(make_float2(-0.5f, -0.5f), qq, mul2(nb2, mul2(dx, dy2)));
+                    const float2 noG = mul2(no2, make_float2(__expf(pw.x), __expf(pw.y)));
+                    na[p] = make_float2(fmaxf(-kAlphaMax, noG.x), fmaxf(-kAlphaMax, noG.y));
+                    if (((live >> (2 * p)) & 1u) && pw.x <= 0.0f && na[p].x <= -kAlphaMin)
+                        hits |= 1u << (2 * p);
+                    if (((live >> (2 * p + 1)) & 1u) && pw.y <= 0.0f && na[p].y <= -kAlphaMin)
+                        hits |= 1u << (2 * p + 1);
+                }
+                if (!__any_sync(0xffffffffu, hits != 0u)) {
+                    if (!__any_sync(0xffffffffu, live != 0u)) return;
+                    continue;
+                }
+                const float4 col = stage[3 * j + 2];
+#pragma unroll
+                for (int p = 0; p < NP; ++p) {
+                    const int k0 = 2 * p, k1 = 2 * p + 1;
+                    const bool h0 = (hits >> k0) & 1u, h1 = (hits >> k1) & 1u;
+                    const float2 T2 = make_float2(T[k0], T[k1]);
+                    const float2 Tn = mul2(T2, add2(make_float2(1.0f, 1.0f), na[p]));
+                    const bool s0 = h0 && Tn.x < kTMin, s1 = h1 && Tn.y < kTMin;
+                    const bool a0 = h0 && !s0, a1 = h1 && !s1;
+                    const float2 nwr = mul2(na[p], T2);
+                    const float2 nw = make_float2(a0 ? nwr.x : 0.0f, a1 ? nwr.y : 0.0f);
+                    if (CH == 3) {
+                        const float2 c0 = fma2(nw, make_float2(col.x, col.x),
+                                               make_float2(C[k0][0], C[k1][0]));
+                        const float2 c1 = fma2(nw, make_float2(col.y, col.y),
+                                               make_float2(C[k0][1], C[k1][1]));
+                        const float2 c2 = fma2(nw, make_float2(col.z, col.z),
+                                               make_float2(C[k0][2], C[k1][2]));
+                        C[k0][0] = c0.x;
+                        C[k1][0] = c0.y;
+                        C[k0][1] = c1.x;
+                        C[k1][1] = c1.y;
+                        C[k0][2] = c2.x;
+                        C[k1][2] = c2.y;
+                    } else {
+                        const float2 c0 = fma2(nw, make_float2(col.w, col.w),
+                                               make_float2(C[k0][0], C[k1][0]));
+                        C[k0][0] = c0.x;
+                        C[k1][0] = c0.y;
+                    }
+                    T[k0] = a0 ? Tn.x : T[k0];
+                    T[k1] = a1 ? Tn.y : T[k1];
+                    last[k0] = a0 ? (int32_t)(pos0 + j + 1) : last[k0];
+                    last[k1] = a1 ? (int32_t)(pos0 + j + 1) : last[k1];
+                    live = s0 ? (live & ~(1u << k0)) : live;
+                    live = s1 ? (live & ~(1u << k1)) : live;
+                }
+            }
+        }
+        return;
+    }
+    for (int j0 = 0; j0 < cnt; j0 += 32) {
+        unsigned todo = chunk_todo(j0, cnt, wmask, wbit, cull);
+        while (todo != 0u) {
+            const int j = j0 + __ffs(todo) - 1;
+            todo &= todo - 1u;
             const float4 g = stage[3 * j];
             const float4 q = stage[3 * j + 1];
             const float dy = g.y - ly;
-            const float cdd = __fmul_rn(q.z, __fmul_rn(dy, dy));
-            const float2 gx2 = make_float2(g.x, g.x), a2 = make_float2(g.z, g.z);
-            const float2 cdd2 = make_float2(cdd, cdd), dy2 = make_float2(dy, dy);
-            const float2 nb2 = make_float2(-g.w, -g.w), no2 = make_float2(-q.w, -q.w);
-            float2 na[NP];
+            float al[PPT];
             unsigned hits = 0u;
 #pragma unroll
-            for (int p = 0; p < NP; ++p) {
-                const float2 dx = add2(gx2, nlx[p]);
-                const float2 qq = fma2(a2, mul2(dx, dx), cdd2);
-                const float2 pw = fma2(make_float2(-0.5f, -0.5f), qq, mul2(nb2, mul2(dx, dy2)));
-                const float2 noG = mul2(no2, make_float2(__expf(pw.x), __expf(pw.y)));
-                na[p] = make_float2(fmaxf(-kAlphaMax, noG.x), fmaxf(-kAlphaMax, noG.y));
-                if (((live >> (2 * p)) & 1u) && pw.x <= 0.0f && na[p].x <= -kAlphaMin)
-                    hits |= 1u << (2 * p);
-                if (((live >> (2 * p + 1)) & 1u) && pw.y <= 0.0f && na[p].y <= -kAlphaMin)
-                    hits |= 1u << (2 * p + 1);
+            for (int k = 0; k < PPT; ++k) {
+                // the same decisions as the backward, from the same rounded ops
+                const float power = gauss_power(g.z, g.w, q.z, g.x - (float)(lx0 + k), dy);
+                al[k] = alpha_of(q.w, power);
+                if (((live >> k) & 1u) && power <= 0.0f && al[k] >= kAlphaMin) hits |= 1u << k;
             }
             if (!__any_sync(0xffffffffu, hits != 0u)) {
                 if (!__any_sync(0xffffffffu, live != 0u)) return;
@@ -287,80 +364,23 @@ __device__ __forceinline__ void blend_batch(int tid, const float4* stage, const 
             }
             const float4 col = stage[3 * j + 2];
 #pragma unroll
-            for (int p = 0; p < NP; ++p) {
-                const int k0 = 2 * p, k1 = 2 * p + 1;
-                const bool h0 = (hits >> k0) & 1u, h1 = (hits >> k1) & 1u;
-                const float2 T2 = make_float2(T[k0], T[k1]);
-                const float2 Tn = mul2(T2, add2(make_float2(1.0f, 1.0f), na[p]));
-                const bool s0 = h0 && Tn.x < kTMin, s1 = h1 && Tn.y < kTMin;
-                const bool a0 = h0 && !s0, a1 = h1 && !s1;
-                const float2 nwr = mul2(na[p], T2);
-                const float2 nw = make_float2(a0 ? nwr.x : 0.0f, a1 ? nwr.y : 0.0f);
+            for (int k = 0; k < PPT; ++k) {
+                const bool hit = (hits >> k) & 1u;
+                const float Tn = __fmul_rn(T[k], __fsub_rn(1.0f, al[k]));
+                const bool stop = hit && Tn < kTMin;
+                const bool add = hit && !stop;
+                const float wgt = add ? al[k] * T[k] : 0.0f;
                 if (CH == 3) {
-                    const float2 c0 = fma2(nw, make_float2(col.x, col.x),
-                                           make_float2(C[k0][0], C[k1][0]));
-                    const float2 c1 = fma2(nw, make_float2(col.y, col.y),
-                                           make_float2(C[k0][1], C[k1][1]));
-                    const float2 c2 = fma2(nw, make_float2(col.z, col.z),
-                                           make_float2(C[k0][2], C[k1][2]));
-                    C[k0][0] = c0.x;
-                    C[k1][0] = c0.y;
-                    C[k0][1] = c1.x;
-                    C[k1][1] = c1.y;
-                    C[k0][2] = c2.x;
-                    C[k1][2] = c2.y;
+                    C[k][0] = fmaf(wgt, col.x, C[k][0]);
+                    C[k][1] = fmaf(wgt, col.y, C[k][1]);
+                    C[k][2] = fmaf(wgt, col.z, C[k][2]);
                 } else {
-                    const float2 c0 = fma2(nw, make_float2(col.w, col.w),
-                                           make_float2(C[k0][0], C[k1][0]));
-                    C[k0][0] = c0.x;
-                    C[k1][0] = c0.y;
+                    C[k][0] = fmaf(wgt, col.w, C[k][0]);
                 }
-                T[k0] = a0 ? Tn.x : T[k0];
-                T[k1] = a1 ? Tn.y : T[k1];
-                last[k0] = a0 ? (int32_t)(pos0 + j + 1) : last[k0];
-                last[k1] = a1 ? (int32_t)(pos0 + j + 1) : last[k1];
-                live = s0 ? (live & ~(1u << k0)) : live;
-                live = s1 ? (live & ~(1u << k1)) : live;
+                T[k] = add ? Tn : T[k];
+                last[k] = add ? (int32_t)(pos0 + j + 1) : last[k];
+                live = stop ? (live & ~(1u << k)) : live;
             }
-        }
-        return;
-    }
-    for (int j = 0; j < cnt; ++j) {
-        if (cull && !(wmask[j] & wbit)) continue;
-        const float4 g = stage[3 * j];
-        const float4 q = stage[3 * j + 1];
-        const float dy = g.y - ly;
-        float al[PPT];
-        unsigned hits = 0u;
-#pragma unroll
-        for (int k = 0; k < PPT; ++k) {
-            // the same decisions as the backward, from the same rounded ops
-            const float power = gauss_power(g.z, g.w, q.z, g.x - (float)(lx0 + k), dy);
-            al[k] = alpha_of(q.w, power);
-            if (((live >> k) & 1u) && power <= 0.0f && al[k] >= kAlphaMin) hits |= 1u << k;
-        }
-        if (!__any_sync(0xffffffffu, hits != 0u)) {
-            if (!__any_sync(0xffffffffu, live != 0u)) return;
-            continue;
-        }
-        const float4 col = stage[3 * j + 2];
-#pragma unroll
-        for (int k = 0; k < PPT; ++k) {
-            const bool hit = (hits >> k) & 1u;
-            const float Tn = __fmul_rn(T[k], __fsub_rn(1.0f, al[k]));
-            const bool stop = hit && Tn < kTMin;
-            const bool add = hit && !stop;
-            const float wgt = add ? al[k] * T[k] : 0.0f;
-            if (CH == 3) {
-                C[k][0] = fmaf(wgt, col.x, C[k][0]);
-                C[k][1] = fmaf(wgt, col.y, C[k][1]);
-                C[k][2] = fmaf(wgt, col.z, C[k][2]);
-            } else {
-                C[k][0] = fmaf(wgt, col.w, C[k][0]);
-            }
-            T[k] = add ? Tn : T[k];
-            last[k] = add ? (int32_t)(pos0 + j + 1) : last[k];
-            live = stop ? (live & ~(1u << k)) : live;
         }
     }
 }
