@@ -341,6 +341,11 @@ __device__ __forceinline__ void blend_batch(int tid, const float4* stage, const 
         }
         return;
     }
+    // the batch index of each pixel's last blended Gaussian (-1: none yet),
+    // turned into the list position when the batch is left
+    int lj[PPT];
+#pragma unroll
+    for (int k = 0; k < PPT; ++k) lj[k] = -1;
     for (int j0 = 0; j0 < cnt; j0 += 32) {
         unsigned todo = chunk_todo(j0, cnt, wmask, wbit, cull);
         while (todo != 0u) {
@@ -359,7 +364,7 @@ __device__ __forceinline__ void blend_batch(int tid, const float4* stage, const 
                 if (((live >> k) & 1u) && power <= 0.0f && al[k] >= kAlphaMin) hits |= 1u << k;
             }
             if (!__any_sync(0xffffffffu, hits != 0u)) {
-                if (!__any_sync(0xffffffffu, live != 0u)) return;
+                if (!__any_sync(0xffffffffu, live != 0u)) goto done;
                 continue;
             }
             const float4 col = stage[3 * j + 2];
@@ -378,11 +383,15 @@ __device__ __forceinline__ void blend_batch(int tid, const float4* stage, const 
                     C[k][0] = fmaf(wgt, col.w, C[k][0]);
                 }
                 T[k] = add ? Tn : T[k];
-                last[k] = add ? (int32_t)(pos0 + j + 1) : last[k];
+                lj[k] = add ? j : lj[k];
                 live = stop ? (live & ~(1u << k)) : live;
             }
         }
     }
+done:
+#pragma unroll
+    for (int k = 0; k < PPT; ++k)
+        if (lj[k] >= 0) last[k] = (int32_t)(pos0 + (uint32_t)lj[k] + 1u);
 }
 
 template <int CH, int PPT, class TM>
