@@ -217,9 +217,9 @@ __device__ __forceinline__ void groups_plane(float* __restrict__ params,
         const uint32_t n4 = len >> 2;
         for (uint32_t f = t0; f < n4; f += stride) {
             const uint32_t j = 4u * f, q = (base + j) >> 2;
-            float4 p = reinterpret_cast<float4*>(params)[q];
-            float4 mm = reinterpret_cast<float4*>(m)[q];
-            float4 vv = reinterpret_cast<float4*>(v)[q];
+            float4 p = __ldcs(reinterpret_cast<float4*>(params) + q);
+            float4 mm = __ldcs(reinterpret_cast<float4*>(m) + q);
+            float4 vv = __ldcs(reinterpret_cast<float4*>(v) + q);
             const uint32_t ga = (j / S) >> 5, gb = ((j + 3) / S) >> 5;
             const bool va = gvis[ga] != 0, vb = ga == gb ? va : gvis[gb] != 0;
             float4 g = make_float4(0.0f, 0.0f, 0.0f, 0.0f);
@@ -236,9 +236,9 @@ __device__ __forceinline__ void groups_plane(float* __restrict__ params,
             adam1(p.y, g.y, mm.y, vv.y, lr, b1, b2, eps, ibc1, ibc2);
             adam1(p.z, g.z, mm.z, vv.z, lr, b1, b2, eps, ibc1, ibc2);
             adam1(p.w, g.w, mm.w, vv.w, lr, b1, b2, eps, ibc1, ibc2);
-            reinterpret_cast<float4*>(params)[q] = p;
-            reinterpret_cast<float4*>(m)[q] = mm;
-            reinterpret_cast<float4*>(v)[q] = vv;
+            __stcs(reinterpret_cast<float4*>(params) + q, p);
+            __stcs(reinterpret_cast<float4*>(m) + q, mm);
+            __stcs(reinterpret_cast<float4*>(v) + q, vv);
         }
         if (t0 < (len & 3u)) scalar(4u * n4 + t0);  // the last len % 4 floats
     } else {
