@@ -332,13 +332,17 @@ k_project(const float* __restrict__ means, const float* __restrict__ log_scales,
     __syncthreads();
     const int g = blockIdx.x * blockDim.x + threadIdx.x;
     if (g >= n) return;
-    const float mean[3] = {means[3 * g], means[3 * g + 1], means[3 * g + 2]};
-    const float ls[3] = {log_scales[3 * g], log_scales[3 * g + 1], log_scales[3 * g + 2]};
-    const float4 q = reinterpret_cast<const float4*>(quats)[g];
+    // the map is streamed once per projection: evict-first loads, so that
+    // the records written here stay in the L2 for the render kernels
+    const float mean[3] = {__ldcs(means + 3 * g), __ldcs(means + 3 * g + 1),
+                           __ldcs(means + 3 * g + 2)};
+    const float ls[3] = {__ldcs(log_scales + 3 * g), __ldcs(log_scales + 3 * g + 1),
+                         __ldcs(log_scales + 3 * g + 2)};
+    const float4 q = __ldcs(reinterpret_cast<const float4*>(quats) + g);
     const float q4[4] = {q.x, q.y, q.z, q.w};
     Shape shp;
     make_shape(ls, q4, shp);
-    const float logit = opacity_logits[g];
+    const float logit = __ldcs(opacity_logits + g);
     const bool finite = shp.finite && isfinite(logit) && isfinite(mean[0]) &&
                         isfinite(mean[1]) && isfinite(mean[2]);
     if (!finite && v0 == 0) atomicOr(&counters->status, (uint32_t)GS_DEV_NONFINITE);
@@ -404,9 +408,9 @@ k_project(const float* __restrict__ means, const float* __restrict__ log_scales,
 #pragma unroll
         for (int k = 0; k < K; ++k) {
             const float* c = sh + ((size_t)k * n + g) * 3;
-            col[0] = fmaf(Y[k], c[0], col[0]);
-            col[1] = fmaf(Y[k], c[1], col[1]);
-            col[2] = fmaf(Y[k], c[2], col[2]);
+            col[0] = fmaf(Y[k], __ldcs(c), col[0]);
+            col[1] = fmaf(Y[k], __ldcs(c + 1), col[1]);
+            col[2] = fmaf(Y[k], __ldcs(c + 2), col[2]);
         }
 #pragma unroll
         for (int ch = 0; ch < 3; ++ch) col[ch] = fmaxf(col[ch] + 0.5f, 0.0f);
